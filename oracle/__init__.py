@@ -1,0 +1,377 @@
+"""FP64 CPU oracle for the GCMe nonbonded force/energy path.
+
+TEST INFRASTRUCTURE ONLY.  This package is the slow, plainly written
+reference that the CUDA library is checked against.  It shares no code with
+the CUDA path (``paper_2403_08148_gb300``) and neither imports the other;
+the only common module is ``synth`` (seeded inputs, no model arithmetic).
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may use it.
+
+The numerical core is ``gcme_oracle.c`` (plain loops, FP64, optional
+OpenMP), compiled on first use with gcc.  This module assembles the pieces
+of the paper's energy for each boundary condition:
+
+* bulk periodic:  U = U_gc + U_real + U_recip + U_corr + U_self (Eq. ewald)
+  + harmonic bonds (Illustrative example section);
+* nonmetal slab (electrode permittivity equal to the solvent's, so image
+  charges vanish): tripled box + Yeh-Berkowitz term + electrode walls;
+* perfectly conducting slab (method of image charges section): a doubled
+  box holding every charged bead's mirror image (x, y, -z) with charge -z_i;
+  the physical electrostatic energy is half that of the doubled system,
+  forces on the real beads are the doubled-system forces.
+
+Parity status of each function is listed in its docstring; all are pinned
+by tests/test_oracle_pins.py.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import Dict, Optional
+
+import numpy as np
+
+from synth import GEOM_BULK, GEOM_SLAB_NM, GEOM_SLAB_PC, System
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gcme_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I32 = ctypes.POINTER(ctypes.c_int32)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+
+
+def build(force: bool = False) -> str:
+    """Compile gcme_oracle.c into oracle/_build/liboracle.so (gcc, -O2)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+        return _SO
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+            "-fno-fast-math", _SRC, "-o", _SO + ".tmp", "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(_SO + ".tmp", _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            L.orc_num_threads.restype = ctypes.c_int
+            L.orc_bspline.restype = ctypes.c_double
+            L.orc_bspline.argtypes = [ctypes.c_int, ctypes.c_double]
+            L.orc_pair_set.restype = ctypes.c_int64
+            _lib = L
+    return _lib
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def _p(a, t=_D):
+    return a.ctypes.data_as(t)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+# ---------------------------------------------------------------------------
+# Thin wrappers over the C routines
+# ---------------------------------------------------------------------------
+def wrap(pos, box):
+    pos = _f64(pos)
+    out = np.empty_like(pos)
+    lib().orc_wrap(ctypes.c_int64(pos.shape[0]), _p(pos), _p(_f64(box)), _p(out))
+    return out
+
+
+def bspline(p: int, u: float) -> float:
+    """Cardinal B-spline M_p(u) (Essmann et al. 1995, recursion)."""
+    return float(lib().orc_bspline(int(p), float(u)))
+
+
+def bspline_moduli(p: int, K: int) -> np.ndarray:
+    out = np.empty(K)
+    lib().orc_bspline_moduli(ctypes.c_int(p), ctypes.c_int(K), _p(out))
+    return out
+
+
+def cell_counts(box, rc: float, margin: float = 1e-4):
+    """Cells per axis: floor(L / (rc (1 + margin))), at least 1.
+
+    The margin keeps every cell side above rc by far more than FP32 rounding
+    of coordinates, so the 27-cell stencil reaches every in-cutoff pair.
+    """
+    return np.array([max(1, int(np.floor(b / (rc * (1.0 + margin))))) for b in box],
+                    dtype=np.int32)
+
+
+def cell_list(pos, box, nc, cls, ncls: int = 3):
+    """Counting-sort cell list; beads inside a cell ordered by (class, index)."""
+    pos = _f64(pos)
+    n = pos.shape[0]
+    nc = _i32(nc)
+    ncell = int(np.prod(nc))
+    cell_of = np.empty(n, np.int32)
+    start = np.empty(ncell + 1, np.int32)
+    order = np.empty(n, np.int32)
+    lib().orc_cell_list(ctypes.c_int64(n), _p(pos), _p(_f64(box)), _p(nc, _I32),
+                        _p(_i32(cls), _I32), ctypes.c_int32(ncls), _p(cell_of, _I32),
+                        _p(start, _I32), _p(order, _I32))
+    return cell_of, start, order
+
+
+def pair_set(pos, box, rc: float):
+    """All ordered in-cutoff triples (i, j, shift code) by brute force."""
+    pos = _f64(pos)
+    n = pos.shape[0]
+    L = lib()
+    cnt = L.orc_pair_set(ctypes.c_int64(n), _p(pos), _p(_f64(box)), ctypes.c_double(rc),
+                         ctypes.c_int64(0), _p(np.zeros(3, np.int32), _I32))
+    out = np.empty((max(cnt, 1), 3), np.int32)
+    L.orc_pair_set(ctypes.c_int64(n), _p(pos), _p(_f64(box)), ctypes.c_double(rc),
+                   ctypes.c_int64(cnt), _p(out, _I32))
+    return out[:cnt]
+
+
+def pairs(pos, q, types, A_tab, sig_tab, a_tab, box, rc, kappa, lB,
+          do_gc=True, do_real=True, per_bead=False):
+    """Real-space pair sums (Eq. u_ex and the real part of Eq. ewald)."""
+    pos = _f64(pos)
+    n = pos.shape[0]
+    A_tab = _f64(A_tab)
+    nt = int(A_tab.shape[0])
+    e = np.zeros(2)
+    f = np.zeros((n, 3))
+    vir = np.zeros(9)
+    npairs = ctypes.c_int64(0)
+    eb = np.zeros((n, 2)) if per_bead else None
+    lib().orc_pairs(ctypes.c_int64(n), _p(pos), _p(_f64(q)), _p(_i32(types), _I32),
+                    ctypes.c_int32(nt), _p(A_tab), _p(_f64(sig_tab)), _p(_f64(a_tab)),
+                    _p(_f64(box)), ctypes.c_double(rc), ctypes.c_double(kappa),
+                    ctypes.c_double(lB), ctypes.c_int32(int(do_gc)),
+                    ctypes.c_int32(int(do_real)), _p(e), _p(f), _p(vir),
+                    ctypes.byref(npairs), _p(eb) if per_bead else None)
+    out = dict(gc=e[0], real=e[1], forces=f, virial=vir.reshape(3, 3),
+               npairs=int(npairs.value))
+    if per_bead:
+        out["per_bead"] = eb
+    return out
+
+
+def pairs_subset(pos, q, types, A_tab, sig_tab, a_tab, box, rc, kappa, lB, idx):
+    pos = _f64(pos)
+    n = pos.shape[0]
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    A_tab = _f64(A_tab)
+    f = np.zeros((idx.shape[0], 3))
+    eb = np.zeros((idx.shape[0], 2))
+    lib().orc_pairs_subset(ctypes.c_int64(n), _p(pos), _p(_f64(q)), _p(_i32(types), _I32),
+                           ctypes.c_int32(A_tab.shape[0]), _p(A_tab), _p(_f64(sig_tab)),
+                           _p(_f64(a_tab)), _p(_f64(box)), ctypes.c_double(rc),
+                           ctypes.c_double(kappa), ctypes.c_double(lB),
+                           ctypes.c_int64(idx.shape[0]), _p(idx, _I64), _p(f), _p(eb))
+    return f, eb
+
+
+def ewald_recip(pos, q, box, kappa, lB, tol=1e-16, forces=True):
+    """Direct reciprocal k-sum of Eq. ewald (tin-foil, k != 0)."""
+    pos = _f64(pos)
+    n = pos.shape[0]
+    e = ctypes.c_double(0.0)
+    f = np.zeros((n, 3)) if forces else None
+    vir = np.zeros(9)
+    lib().orc_ewald_recip(ctypes.c_int64(n), _p(pos), _p(_f64(q)), _p(_f64(box)),
+                          ctypes.c_double(kappa), ctypes.c_double(lB),
+                          ctypes.c_double(tol), ctypes.byref(e),
+                          _p(f) if forces else None, _p(vir))
+    return dict(recip=e.value, forces=f, virial=vir.reshape(3, 3))
+
+
+def spme(pos, q, box, K, p, kappa, lB, forces=True):
+    """FP64 smooth PME (Essmann et al. 1995) with direct separable DFTs."""
+    pos = _f64(pos)
+    n = pos.shape[0]
+    e = ctypes.c_double(0.0)
+    f = np.zeros((n, 3)) if forces else None
+    vir = np.zeros(9)
+    lib().orc_spme(ctypes.c_int64(n), _p(pos), _p(_f64(q)), _p(_f64(box)),
+                   _p(_i32(K), _I32), ctypes.c_int32(p), ctypes.c_double(kappa),
+                   ctypes.c_double(lB), ctypes.byref(e), _p(f) if forces else None,
+                   _p(vir))
+    return dict(recip=e.value, forces=f, virial=vir.reshape(3, 3))
+
+
+def ewald_constants(q, a_bead, kappa, lB):
+    c = ctypes.c_double(0.0)
+    s = ctypes.c_double(0.0)
+    q = _f64(q)
+    lib().orc_ewald_constants(ctypes.c_int64(q.shape[0]), _p(q), _p(_f64(a_bead)),
+                              ctypes.c_double(kappa), ctypes.c_double(lB),
+                              ctypes.byref(c), ctypes.byref(s))
+    return c.value, s.value
+
+
+def slab_yb(pos, q, box, lB):
+    pos = _f64(pos)
+    e = ctypes.c_double(0.0)
+    fz = np.zeros(pos.shape[0])
+    lib().orc_slab_yb(ctypes.c_int64(pos.shape[0]), _p(pos), _p(_f64(q)), _p(_f64(box)),
+                      ctypes.c_double(lB), ctypes.byref(e), _p(fz))
+    return e.value, fz
+
+
+def walls(pos, H, wallA, s_w):
+    pos = _f64(pos)
+    e = ctypes.c_double(0.0)
+    fz = np.zeros(pos.shape[0])
+    lib().orc_walls(ctypes.c_int64(pos.shape[0]), _p(pos), ctypes.c_double(H),
+                    ctypes.c_double(wallA), ctypes.c_double(s_w), ctypes.byref(e),
+                    _p(fz))
+    return e.value, fz
+
+
+def bonds(pairs_ij, pos, box, periodic, k, r0):
+    pos = _f64(pos)
+    pairs_ij = _i32(pairs_ij).reshape(-1, 2)
+    e = ctypes.c_double(0.0)
+    f = np.zeros_like(pos)
+    vir = np.zeros(9)
+    lib().orc_bonds(ctypes.c_int64(pairs_ij.shape[0]), _p(pairs_ij, _I32),
+                    ctypes.c_int64(pos.shape[0]), _p(pos), _p(_f64(box)),
+                    _p(_i32(periodic), _I32), ctypes.c_double(k), ctypes.c_double(r0),
+                    ctypes.byref(e), _p(f), _p(vir))
+    return e.value, f, vir.reshape(3, 3)
+
+
+# ---------------------------------------------------------------------------
+# Whole-model assembly per boundary condition
+# ---------------------------------------------------------------------------
+TERMS = ("gc", "real", "recip", "corr", "self", "slab", "wall", "bond")
+
+# bead classes of the cell order: images, charged reals, neutral reals
+CLS_IMAGE, CLS_CHARGED, CLS_NEUTRAL = 0, 1, 2
+
+
+def electrostatic_beads(s: System, pos=None):
+    """Beads that carry the electrostatics: the reals, plus mirror images
+    (x, y, -z) with charge -z_i for every charged real in the conducting-slab
+    geometry.  Returns (pos, q, type, n_real) with type 1 = image (no core)."""
+    pos = s.pos if pos is None else pos
+    q = s.q
+    n = pos.shape[0]
+    types = np.zeros(n, np.int32)
+    if s.geometry != GEOM_SLAB_PC:
+        return pos, q, types, n
+    qi = np.nonzero(q)[0]
+    img = pos[qi].copy()
+    img[:, 2] = -img[:, 2]
+    return (np.concatenate([pos, img]), np.concatenate([q, -q[qi]]),
+            np.concatenate([types, np.ones(qi.shape[0], np.int32)]), n)
+
+
+def bead_classes(s: System):
+    """Class of every bead of the (possibly doubled) electrostatic system."""
+    pos, q, types, n = electrostatic_beads(s)
+    cls = np.where(q != 0.0, CLS_CHARGED, CLS_NEUTRAL).astype(np.int32)
+    cls[types == 1] = CLS_IMAGE
+    return cls
+
+
+def _tables(s: System):
+    A_tab = np.array([[s.A, 0.0], [0.0, 0.0]])
+    sig = np.array([s.sigma, s.sigma])
+    a = np.array([s.a, s.a])
+    return A_tab, sig, a
+
+
+def energy_forces(s: System, pos=None, recip: str = "spme",
+                  ewald_tol: float = 1e-16) -> Dict:
+    """Total energy by term, forces on the real beads and the virial.
+
+    recip = "spme" (same grid and order as the system) or "ewald" (direct
+    k-sum; the converged reciprocal sum).  Returns a dict with the terms of
+    ``TERMS``, "potential", "forces" (n,3), "virial" (3,3, pair + reciprocal
+    + bonds) and "npairs" (unordered in-cutoff triples, images included).
+    """
+    pos = s.pos if pos is None else np.asarray(pos, np.float64)
+    n = pos.shape[0]
+    epos, eq, etype, _ = electrostatic_beads(s, pos)
+    A_tab, sig, a = _tables(s)
+    pr = pairs(epos, eq, etype, A_tab, sig, a, s.box, s.rc, s.kappa, s.lB)
+    if recip == "spme":
+        rr = spme(epos, eq, s.box, s.K, s.order, s.kappa, s.lB)
+    else:
+        rr = ewald_recip(epos, eq, s.box, s.kappa, s.lB, tol=ewald_tol)
+    corr, self_e = ewald_constants(eq, np.full(eq.shape[0], s.a), s.kappa, s.lB)
+    half = 0.5 if s.geometry == GEOM_SLAB_PC else 1.0
+    E = dict(gc=pr["gc"], real=half * pr["real"], recip=half * rr["recip"],
+             corr=half * corr, self=half * self_e, slab=0.0, wall=0.0, bond=0.0)
+    F = pr["forces"][:n] + rr["forces"][:n]
+    vir = pr["virial"] + rr["virial"]
+    if s.geometry == GEOM_SLAB_NM:
+        e, fz = slab_yb(pos, s.q, s.box, s.lB)
+        E["slab"] = e
+        F[:, 2] += fz
+    if s.geometry in (GEOM_SLAB_NM, GEOM_SLAB_PC):
+        e, fz = walls(pos, s.H, s.wall_A, s.wall_sigma2)
+        E["wall"] = e
+        F[:, 2] += fz
+    if s.bonds.shape[0] > 0:
+        per = (1, 1, 1) if s.geometry == GEOM_BULK else (1, 1, 0)
+        e, fb, vb = bonds(s.bonds, pos, s.box, per, s.bond_k, s.bond_r0)
+        E["bond"] = e
+        F += fb
+        vir = vir + vb
+    E["potential"] = sum(E[t] for t in TERMS)
+    E["forces"] = F
+    E["virial"] = vir
+    E["npairs"] = pr["npairs"]
+    return E
+
+
+def forces_subset(s: System, idx, pos=None):
+    """Real-space forces and per-bead pair energies for the beads ``idx``."""
+    pos = s.pos if pos is None else pos
+    epos, eq, etype, _ = electrostatic_beads(s, pos)
+    A_tab, sig, a = _tables(s)
+    return pairs_subset(epos, eq, etype, A_tab, sig, a, s.box, s.rc, s.kappa, s.lB, idx)
+
+
+def velocity_verlet(s: System, nsteps: int, recip: str = "spme", record=None):
+    """NVE velocity Verlet, unit masses, FP64:
+        v += dt/2 F;  x += dt v;  F = F(x);  v += dt/2 F.
+    Returns (pos, vel, list of per-step dicts {potential, kinetic})."""
+    pos = s.pos.copy()
+    vel = s.vel.copy()
+    dt = s.dt
+    ef = energy_forces(s, pos, recip=recip)
+    F = ef["forces"]
+    hist = [dict(potential=ef["potential"], kinetic=0.5 * float(np.sum(vel * vel)))]
+    for _ in range(nsteps):
+        vel += 0.5 * dt * F
+        pos += dt * vel
+        ef = energy_forces(s, pos, recip=recip)
+        F = ef["forces"]
+        vel += 0.5 * dt * F
+        hist.append(dict(potential=ef["potential"], kinetic=0.5 * float(np.sum(vel * vel))))
+    return pos, vel, hist
