@@ -1,0 +1,275 @@
+/*
+ * gcme.h -- C ABI of libgcme, a CUDA (sm_103a) library for the per-step
+ * nonbonded force and energy of GCMe, the Gaussian core model with smeared
+ * electrostatics (Ye, Chen & Wang, arXiv 2403.08148).
+ *
+ * Model (reduced units: kT = 1, length d, charge e, Coulomb prefactor lB):
+ *   Gaussian core (Eq. u_ex):
+ *     u_ex(r) = A (3 / (2 pi s))^{3/2} exp(-3 r^2 / (2 s)),  s = sigma_i^2 + sigma_j^2
+ *   smeared Coulomb (Eq. u_elec):
+ *     u_elec(r) = lB z_i z_j erf(beta r) / r,  beta = sqrt(pi) / (sqrt(2) a_ij)
+ *   Ewald split of the electrostatics (Eq. ewald):
+ *     real  = sum_{pairs, r < rc} lB z_i z_j [erfc(kappa r) - erfc(beta r)] / r
+ *     recip = smooth PME (Essmann et al. 1995) of the point-charge sum
+ *     corr  = -lB kappa / sqrt(pi) sum z_i^2,   self = lB sum z_i^2 / (2 a)
+ *   Boundaries (Method of image charges section; Illustrative example):
+ *     BULK          periodic box
+ *     SLAB_NONMETAL real beads in 0 < z < H, box Lz = 3 H, Yeh-Berkowitz term
+ *                   2 pi lB M_z^2 / V and electrode walls at z = 0, H
+ *     SLAB_IMAGE    real beads in 0 < z < H, box Lz = 2 H; every charged bead
+ *                   has a mirror image (x, y, -z) with charge -z_i; reported
+ *                   electrostatic energies are those of the physical system
+ *                   (half of the doubled one), walls at z = 0, H
+ *   Harmonic bonds (Illustrative example): u = k/2 (r - r0)^2.
+ *
+ * Conventions for every entry point:
+ *   - return 0 on success or a negative GCME_ERR_* code; nothing throws,
+ *     exits or traps; gcme_last_error() gives a message for the calling
+ *     thread's last failure;
+ *   - pointers named d_* are device pointers owned by the caller (the
+ *     library never frees them); pointers named h_* are host pointers read
+ *     during the call only;
+ *   - positions are (n, 3) row-major FP64; velocities (n, 3) row-major FP32;
+ *     forces are 64-bit fixed point, value = F * 2^32, in structure-of-arrays
+ *     layout: fx[0..n), fy[n..2n), fz[2n..3n);
+ *   - energies are FP64 arrays of GCME_NTERMS entries (index GCME_E_*);
+ *     the virial is 9 FP64 values, W_ab = sum_pairs r_ij,a F_ij,b of the
+ *     pair, reciprocal and bond terms;
+ *   - work is enqueued on the caller's CUDA stream (NULL = legacy default
+ *     stream) and ordered with the caller's other work on that stream.
+ */
+#ifndef GCME_H
+#define GCME_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gcme_ctx gcme_ctx;
+typedef struct gcme_sys gcme_sys;
+typedef struct gcme_batch gcme_batch;
+typedef struct gcme_server gcme_server;
+typedef void *gcme_stream_t; /* a cudaStream_t */
+
+enum {
+  GCME_OK = 0,
+  GCME_ERR_INVALID = -1,   /* bad argument, rejected before any GPU work */
+  GCME_ERR_OOM = -2,       /* device allocation failed or budget exceeded */
+  GCME_ERR_CUDA = -3,      /* a CUDA runtime call failed */
+  GCME_ERR_TIMEOUT = -4,   /* a bounded device-side wait ran out */
+  GCME_ERR_NONFINITE = -5, /* a force or energy became NaN/Inf */
+  GCME_ERR_FULL = -6,      /* server queue full */
+  GCME_ERR_NOTFOUND = -7   /* unknown ticket */
+};
+
+enum { GCME_BULK = 0, GCME_SLAB_NONMETAL = 1, GCME_SLAB_IMAGE = 2 };
+
+enum { GCME_FP32 = 0, GCME_FP64 = 1 };
+
+/* Energy terms (FP64, kT). */
+enum {
+  GCME_E_GC = 0,      /* Gaussian core, Eq. u_ex                        */
+  GCME_E_REAL = 1,    /* real-space electrostatics, Eq. ewald line 3    */
+  GCME_E_RECIP = 2,   /* reciprocal (PME), Eq. ewald line 5             */
+  GCME_E_CORR = 3,    /* -lB kappa/sqrt(pi) sum z^2, Eq. ewald line 6   */
+  GCME_E_SELF = 4,    /* Born self energy, Eq. ewald line 7             */
+  GCME_E_SLAB = 5,    /* Yeh-Berkowitz slab term                        */
+  GCME_E_WALL = 6,    /* electrode wall term                            */
+  GCME_E_BOND = 7,    /* harmonic bonds                                 */
+  GCME_E_POTENTIAL = 8, /* sum of the above                             */
+  GCME_E_KINETIC = 9,   /* 1/2 sum v^2 (unit masses), set by gcme_step  */
+  GCME_NTERMS = 10
+};
+
+#define GCME_FORCE_SCALE 4294967296.0 /* 2^32: fixed-point force scale */
+
+/* Parameters of one system.  All lengths in d, energies in kT. */
+typedef struct gcme_params {
+  double box[3];      /* periodic box (for slabs: the doubled/tripled box) */
+  int32_t geometry;   /* GCME_BULK / GCME_SLAB_NONMETAL / GCME_SLAB_IMAGE  */
+  int32_t precision;  /* GCME_FP32 (default) or GCME_FP64 (plain path)     */
+  double A;           /* Gaussian-core amplitude A_ij, uniform               */
+  double sigma;       /* mass smearing radius sigma_i, uniform               */
+  double a;           /* charge smearing radius a_i, uniform                 */
+  double lB;          /* Bjerrum length                                      */
+  double rc;          /* real-space cutoff                                   */
+  double kappa;       /* Ewald splitting parameter, kappa = 1/(sqrt(2) G)    */
+  int32_t K[3];       /* PME grid, each 2^a 3^b 5^c, 4 <= K <= 1024          */
+  int32_t order;      /* B-spline order p, 3..8                              */
+  double dt;          /* velocity-Verlet time step                           */
+  double H;           /* slab height (slab geometries)                       */
+  double wall_A;      /* wall amplitude A n_s (slab geometries; 0 = none)    */
+  double wall_sigma2; /* wall width sigma_w^2                                */
+  double bond_k;      /* harmonic bond constant                              */
+  double bond_r0;     /* harmonic bond rest length                           */
+} gcme_params;
+
+/* Fill p with the paper's defaults (A = 25, sigma = a = 0.5, lB = 1.2053,
+ * rc = 3, kappa = 0.87609, p = 5, dt = 0.01, k = 100, r0 = 1) and a cubic
+ * box of side L with grid K^3. */
+void gcme_params_default(gcme_params *p, double L, int32_t K);
+
+/* Message of the calling thread's last error ("" if none). */
+const char *gcme_last_error(void);
+
+/* Library version string. */
+const char *gcme_version(void);
+
+/* Host-only check of a system description, without a device: the same
+ * validation gcme_system_create performs.  Returns 0 or GCME_ERR_INVALID
+ * (message in gcme_last_error). */
+int gcme_validate(const gcme_params *p, int64_t n, const double *h_q,
+                  const int32_t *h_bonds, int64_t nbonds);
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device` (the library makes it current
+ * for its own calls).  *out is owned by the caller; free with
+ * gcme_ctx_destroy. */
+int gcme_ctx_create(gcme_ctx **out, int device);
+void gcme_ctx_destroy(gcme_ctx *ctx);
+
+/* ---- single system ------------------------------------------------------- */
+
+/* Create a system of n real beads with charges h_q[n] (charge numbers z_i)
+ * and an optional bond list h_bonds[2*nbonds] (bead index pairs).  Validates:
+ *   - net charge zero (|sum z| < 1e-6), n >= 1;
+ *   - the non-collapse condition of the Gaussian core model section,
+ *     A / sigma_ij^3 > 4 pi^{3/2} lB / (3^{3/2} a_ij) for unit charges;
+ *   - every box side >= rc (27-cell stencil) and, for slabs, the box height
+ *     3 H (nonmetal) or 2 H (image charges);
+ *   - grid sizes 2^a 3^b 5^c within [4, 1024], order within [3, 8].
+ * Allocates the library's scratch memory for the system (cell lists, PME
+ * grids, accumulators).  Errors: INVALID, OOM, CUDA. */
+int gcme_system_create(gcme_ctx *ctx, const gcme_params *p, int64_t n,
+                       const double *h_q, const int32_t *h_bonds, int64_t nbonds,
+                       gcme_sys **out);
+void gcme_system_destroy(gcme_sys *sys);
+
+/* Build the cell list of the positions d_pos[n*3] (K1 + K2): wrap into the
+ * box in FP64 (x - L floor(x/L)), cell c_a = floor(x_a n_a / L_a), cells of
+ * side >= rc, beads of a cell in (class, index) order with class 0 = image,
+ * 1 = charged, 2 = neutral.  Outputs (caller-owned, may be NULL):
+ *   d_cell_start[ncell+1], d_sorted_idx[n_ext]  (n_ext = n + images).
+ * ncell and n_ext are returned by gcme_system_info. */
+int gcme_build_cells(gcme_sys *sys, const double *d_pos, int32_t *d_cell_start,
+                     int32_t *d_sorted_idx, gcme_stream_t stream);
+
+/* Forces, energies and virial at positions d_pos[n*3] (FP64, any image).
+ * d_force[3n] (fixed point, SoA), d_energy[GCME_NTERMS], d_virial[9]; any
+ * output may be NULL.  Errors: INVALID, CUDA. */
+int gcme_forces(gcme_sys *sys, const double *d_pos, int64_t *d_force,
+                double *d_energy, double *d_virial, gcme_stream_t stream);
+
+/* Convert fixed-point forces to FP64 (d_out[3n] in the same SoA layout). */
+int gcme_forces_to_f64(gcme_sys *sys, const int64_t *d_force, double *d_out,
+                       gcme_stream_t stream);
+
+/* nsteps of NVE velocity Verlet with unit masses:
+ *   v += dt/2 F;  x += dt v;  F = F(x);  v += dt/2 F.
+ * Updates d_pos[n*3] (FP64, not wrapped) and d_vel[n*3] (FP32) in place and
+ * writes the energies of the final state to d_energy (may be NULL).  Steps
+ * run as replays of a captured CUDA graph (one per (d_pos, d_vel) pair). */
+int gcme_step(gcme_sys *sys, double *d_pos, float *d_vel, int64_t nsteps,
+              double *d_energy, gcme_stream_t stream);
+
+/* The same for FP64 systems (the plain FP64 path), FP64 velocities. */
+int gcme_step_f64(gcme_sys *sys, double *d_pos, double *d_vel, int64_t nsteps,
+                  double *d_energy, gcme_stream_t stream);
+
+/* Sizes of the system: n, n_ext, ncell, number of charged beads incl.
+ * images, cells per axis. */
+typedef struct gcme_sys_info {
+  int64_t n, n_ext, n_charged_ext, ncell, nbonds;
+  int32_t nc[3];
+  int64_t scratch_bytes;
+} gcme_sys_info;
+int gcme_system_info(const gcme_sys *sys, gcme_sys_info *out);
+
+/* Debug: every ordered in-cutoff triple (i, j, image code) found by the
+ * pair kernel at d_pos, code = (nx+1) + 3 (ny+1) + 9 (nz+1).  Writes up to
+ * cap triples to d_triples[3*cap] and the total to d_count[1].  Indices are
+ * into the extended bead set (reals, then images). */
+int gcme_debug_pairs(gcme_sys *sys, const double *d_pos, int32_t *d_triples,
+                     int64_t cap, int64_t *d_count, gcme_stream_t stream);
+
+/* ---- batch of independent systems ---------------------------------------- */
+
+/* A batch of nsys independent systems stepped together: every phase of the
+ * step is one launch over all systems (or one persistent cooperative launch
+ * for all phases), replayed from a captured CUDA graph.  params[s], n[s],
+ * charges h_q (concatenated), bonds are per system as in gcme_system_create;
+ * h_bond_count[s] gives the number of bonds of system s (concatenated in
+ * h_bonds, indices local to the system).  The batch owns pooled device state:
+ * positions, velocities, forces. */
+int gcme_batch_create(gcme_ctx *ctx, int32_t nsys, const gcme_params *params,
+                      const int64_t *n, const double *h_q, const int32_t *h_bonds,
+                      const int64_t *h_bond_count, gcme_batch **out);
+void gcme_batch_destroy(gcme_batch *b);
+
+/* Copy state in/out (host, concatenated over systems in batch order). */
+int gcme_batch_set_state(gcme_batch *b, const double *h_pos, const float *h_vel,
+                         gcme_stream_t stream);
+int gcme_batch_get_state(gcme_batch *b, double *h_pos, float *h_vel,
+                         double *h_energy /* nsys * GCME_NTERMS */,
+                         gcme_stream_t stream);
+
+/* Step every system nsteps times.  mode 0: one launch per phase, the whole
+ * step captured in a CUDA graph; mode 1: one persistent cooperative launch
+ * running all phases of all steps with grid-wide barriers. */
+int gcme_batch_step(gcme_batch *b, int64_t nsteps, int32_t mode, gcme_stream_t stream);
+
+/* Device pointers to the pooled state (positions [3 N_tot] FP64, velocities
+ * [3 N_tot] FP32, energies [nsys * GCME_NTERMS] FP64) and bead offsets. */
+int gcme_batch_pointers(gcme_batch *b, double **d_pos, float **d_vel,
+                        double **d_energy, const int64_t **h_bead_off);
+
+/* ---- serving -------------------------------------------------------------- */
+
+/* A continuous-batching request server.  A host thread owns a pool of
+ * hbm_budget bytes; requests are admitted when their footprint fits, their
+ * state stays on the device, and every chunk of `chunk_steps` steps runs all
+ * admitted systems in one batched launch sequence.  Requests that arrive
+ * while others run are admitted at the next chunk boundary. */
+typedef struct gcme_request {
+  gcme_params params;
+  int64_t n;
+  const double *h_pos;   /* n*3, copied on submit */
+  const float *h_vel;    /* n*3, copied on submit */
+  const double *h_q;     /* n, copied on submit */
+  const int32_t *h_bonds; /* 2*nbonds, may be NULL */
+  int64_t nbonds;
+  int64_t nsteps;
+} gcme_request;
+
+typedef struct gcme_result {
+  int32_t status;        /* 0 done, 1 queued, 2 running, <0 error code */
+  int64_t steps_done;
+  double energy[GCME_NTERMS];
+  double t_submit, t_admit, t_done; /* seconds, monotonic clock */
+} gcme_result;
+
+int gcme_server_create(gcme_ctx *ctx, size_t hbm_budget, int32_t chunk_steps,
+                       int32_t max_active, gcme_server **out);
+void gcme_server_destroy(gcme_server *srv);
+/* Submit a request; copies all host inputs before returning. */
+int gcme_submit(gcme_server *srv, const gcme_request *req, uint64_t *ticket);
+/* Poll a ticket; when done, copies the final state to h_pos/h_vel if not
+ * NULL (n*3 each).  Returns NOTFOUND for unknown or already-released tickets. */
+int gcme_poll(gcme_server *srv, uint64_t ticket, gcme_result *out, double *h_pos,
+              float *h_vel);
+/* Release a finished ticket's host copy, or cancel a queued/running one. */
+int gcme_cancel(gcme_server *srv, uint64_t ticket);
+/* Block until every submitted request has finished (or timeout_s passes). */
+int gcme_server_drain(gcme_server *srv, double timeout_s);
+/* Counters: [0] admitted, [1] completed, [2] rejected, [3] chunks run,
+ * [4] bead-steps done, [5] peak active, [6] peak bytes in use. */
+int gcme_server_stats(gcme_server *srv, int64_t *out7);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GCME_H */

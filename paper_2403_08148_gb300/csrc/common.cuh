@@ -1,0 +1,222 @@
+// common.cuh -- descriptors and device helpers shared by the libgcme kernels.
+//
+// Every kernel works on a *batch* of independent systems held in pooled
+// device arrays; a single system is a batch of one.  Per-system sizes,
+// offsets and constants live in a device table of SysDesc; the pooled array
+// base pointers travel by value in a Pool struct (a kernel argument), so the
+// same kernels serve gcme_forces (caller's buffers), batches and the server.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gcme.h"
+
+namespace gcme {
+
+// FP64 position + charge (x, y, z, q), 32-byte aligned
+struct __align__(32) dpos4 {
+  double x, y, z, w;
+};
+__host__ __device__ __forceinline__ dpos4 make_dpos4(double x, double y, double z, double w) {
+  dpos4 r;
+  r.x = x;
+  r.y = y;
+  r.z = z;
+  r.w = w;
+  return r;
+}
+
+constexpr int kNcls = 3;           // bead classes inside a cell: image, charged, neutral
+constexpr int kMaxStages = 8;      // FFT stages per axis (K <= 1024)
+constexpr int kNacc = 16;          // fixed-point accumulators per system
+constexpr double kFScale = 4294967296.0;   // 2^32 force scale
+constexpr double kEScale = 4294967296.0;   // 2^32 energy scale
+constexpr double kQScale32 = 68719476736.0;    // 2^36 PME grid scale (FP32 path)
+constexpr double kQScale64 = 1099511627776.0;  // 2^40 PME grid scale (FP64 path)
+
+// accumulator slots (first 8 coincide with GCME_E_*)
+enum {
+  ACC_GC = 0, ACC_REAL = 1, ACC_RECIP = 2, ACC_WALL = 6, ACC_BOND = 7,
+  ACC_MZ = 8,      // sum z_i z_pos,i (Yeh-Berkowitz dipole), scale 2^32
+  ACC_KIN = 9,     // kinetic energy
+  ACC_FLAGS = 10,  // error flags (bit 0: non-finite)
+  ACC_NPAIR = 11   // debug pair count
+};
+
+struct SysDesc {
+  // sizes
+  int n, n_ext, nq_real, nq_ext;
+  int geometry, precision, nbond, pad0;
+  // offsets into pooled arrays
+  long long bead_off;  // real-bead arrays (pos/vel: 3 per bead; force: SoA block of 3n)
+  long long ext_off;   // extended-bead arrays (reals then images)
+  long long q_off;     // charged-bead list
+  long long img_off;   // image source list
+  long long cell_off;  // cells
+  long long grid_off;  // PME grid points
+  long long bond_off;  // bonds
+  int tw_off[3];       // twiddle tables per axis
+  int bsp_off[3];      // B-spline moduli per axis
+  int nstage[3];
+  int radix[3][kMaxStages];
+  int nc[3];
+  int ncell;
+  int K[3];
+  int order;
+  // geometry
+  double box[3];
+  double inv_cell[3];  // nc / L (FP64, the binning rule)
+  float boxf[3];
+  float rc2f;          // fl(rc^2)
+  float kfac[3];       // K / L
+  float pad1;
+  double V;
+  // physics
+  double A, sigma, a, lB, rc, kappa, beta;
+  double gc_pref;      // A (3 / (2 pi s))^{3/2}
+  double gc_expc;      // 3 / (2 s)
+  double gc_fc;        // 3 / s
+  double e_corr, e_self;
+  double recip_scale;  // 1, or 1/2 for the image-charge geometry
+  double H, wall_A, wall_s2;
+  double bond_k, bond_r0;
+  double dt;
+  // real-space kernel constants: small-r Taylor series of
+  //   g(r) = [erf(beta r) - erf(kappa r)] / r        = sum_k ser_g[k] r^{2k}
+  //   h(r) = -g'(r) / r                               = sum_k ser_h[k] r^{2k}
+  double ser_g[4], ser_h[3];
+  float ser_gf[4], ser_hf[3];
+  float betaf, kappaf;
+  float gc_c2f;        // -3/(2 s) log2(e): exponent of the core in base 2
+  float pad2;
+};
+
+// Pooled device arrays.  Passed by value to every kernel.
+struct Pool {
+  const SysDesc *sys;
+  int nsys;
+  int pad;
+  // state (real beads)
+  double *pos;          // [3 * N] FP64
+  const double *q;      // [N] charge numbers z_i of the real beads
+  void *vel;            // [3 * N] FP32 or FP64
+  long long *force;     // per system: SoA block [3 n]
+  // extended beads
+  float4 *xyzq_u;       // wrapped FP32 position + charge, ext order
+  dpos4 *xyzq_u64;    // wrapped FP64 position + charge (FP64 path)
+  int *cell_of;
+  int *slot;
+  int *sorted_idx;      // local ext index per sorted slot
+  int *sort_tmp;        // scratch for oversized cells
+  float4 *xyzq_s;       // sorted FP32
+  dpos4 *xyzq_s64;    // sorted FP64 (FP64 path)
+  int *ext_sys;         // system of each ext bead
+  int *real_sys;        // system of each real bead
+  int *qlist;           // local ext index of each charged bead (reals first, then images)
+  int *q_sys;
+  int *img_src;         // local real index of each image
+  // cells
+  int *cell_cnt;
+  int *cell_start;      // global (pooled) sorted offsets
+  int *cell_nimg;
+  int *cell_nq;
+  int *cell_sys;
+  // PME
+  unsigned long long *qgrid;  // fixed-point charge grid
+  float2 *cgrid;              // complex grid (FP32 path)
+  double2 *cgrid64;           // complex grid (FP64 path)
+  float2 *tw;                 // twiddles e^{-2 pi i t/K}
+  double2 *tw64;
+  float *bsp;                 // |b(m)|^2
+  double *bsp64;
+  // bonds
+  int2 *bonds;
+  int *bond_sys;
+  // accumulators
+  unsigned long long *acc;    // [nsys * kNacc]
+  unsigned long long *vacc;   // [nsys * 9]
+  double *energy;             // [nsys * GCME_NTERMS]
+  double *virial;             // [nsys * 9]
+  // totals
+  long long n_real, n_ext, n_cells, n_q, n_bond;
+  long long n_grid;
+  // debug pair dump
+  int *dbg_triples;
+  long long dbg_cap;
+};
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ void atomic_add_fixed(unsigned long long *p, double v, double scale) {
+  long long q = __double2ll_rn(v * scale);
+  atomicAdd(p, (unsigned long long)q);
+}
+
+__device__ __forceinline__ void atomic_add_fixed_f(unsigned long long *p, float v, float scale) {
+  long long q = __float2ll_rn(v * scale);
+  atomicAdd(p, (unsigned long long)q);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Wrap one coordinate into [0, L): x - L floor(x/L), each operation rounded
+// once (no contraction); a result of L (or below 0) maps to 0.
+__device__ __forceinline__ double wrap_coord(double x, double L) {
+  double s = __ddiv_rn(x, L);
+  double f = floor(s);
+  double t = __dmul_rn(L, f);
+  double w = __dsub_rn(x, t);
+  if (w >= L) w = 0.0;
+  if (w < 0.0) w = 0.0;
+  return w;
+}
+
+__device__ __forceinline__ int floor_div(int a, int b) {
+  int q = a / b;
+  if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+  return q;
+}
+
+// Load a bead position of the extended system: reals from the caller's
+// array, images mirrored in z.
+__device__ __forceinline__ void ext_position(const Pool &P, const SysDesc &S, int e,
+                                             double &x, double &y, double &z) {
+  if (e < S.n) {
+    const double *p = P.pos + 3 * (S.bead_off + e);
+    x = p[0];
+    y = p[1];
+    z = p[2];
+  } else {
+    int src = P.img_src[S.img_off + (e - S.n)];
+    const double *p = P.pos + 3 * (S.bead_off + src);
+    x = p[0];
+    y = p[1];
+    z = -p[2];
+  }
+}
+
+__device__ __forceinline__ double ext_charge(const Pool &P, const SysDesc &S, int e) {
+  if (e < S.n) return P.q[S.bead_off + e];
+  return -P.q[S.bead_off + P.img_src[S.img_off + (e - S.n)]];
+}
+
+// fixed-point force array of a system: SoA block
+__device__ __forceinline__ unsigned long long *force_ptr(const Pool &P, const SysDesc &S, int i,
+                                                         int axis) {
+  return reinterpret_cast<unsigned long long *>(P.force + 3 * S.bead_off + (long long)axis * S.n +
+                                                i);
+}
+
+}  // namespace gcme

@@ -1,0 +1,937 @@
+// engine.cu -- host side of libgcme: validation, pooled layout, launch
+// sequences, CUDA-graph capture and the C ABI of single systems and batches.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+
+namespace gcme {
+
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+
+#define GCME_CK(call)                                                              \
+  do {                                                                             \
+    cudaError_t _e = (call);                                                       \
+    if (_e != cudaSuccess) {                                                       \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(_e));               \
+      return GCME_ERR_CUDA;                                                        \
+    }                                                                              \
+  } while (0)
+
+static constexpr double kPi = 3.14159265358979323846;
+
+bool is_smooth(int K) {
+  if (K < 1) return false;
+  for (int r : {2, 3, 5})
+    while (K % r == 0) K /= r;
+  return K == 1;
+}
+
+std::vector<int> fft_radices(int K) {
+  std::vector<int> r;
+  while (K % 4 == 0) {
+    r.push_back(4);
+    K /= 4;
+  }
+  while (K % 2 == 0) {
+    r.push_back(2);
+    K /= 2;
+  }
+  while (K % 3 == 0) {
+    r.push_back(3);
+    K /= 3;
+  }
+  while (K % 5 == 0) {
+    r.push_back(5);
+    K /= 5;
+  }
+  return r;
+}
+
+// Cardinal B-spline M_p(u) (recursion of Essmann et al. 1995), host side.
+static double host_bspline(int p, double u) {
+  if (u <= 0.0 || u >= p) return 0.0;
+  if (p == 2) return 1.0 - std::fabs(u - 1.0);
+  return (u * host_bspline(p - 1, u) + (p - u) * host_bspline(p - 1, u - 1.0)) / (p - 1);
+}
+
+// |b(m)|^2 = 1 / |sum_{k=0}^{p-2} M_p(k+1) e^{2 pi i m k / K}|^2; for odd p
+// the zero at m = K/2 takes the mean of the neighbouring values.
+static std::vector<double> host_bsp_moduli(int p, int K) {
+  std::vector<double> b(K);
+  std::vector<char> bad(K, 0);
+  for (int m = 0; m < K; ++m) {
+    double re = 0, im = 0;
+    for (int k = 0; k <= p - 2; ++k) {
+      double ph = 2.0 * kPi * m * k / K;
+      double Mk = host_bspline(p, k + 1.0);
+      re += Mk * std::cos(ph);
+      im += Mk * std::sin(ph);
+    }
+    double den = re * re + im * im;
+    if (den > 1e-10) b[m] = 1.0 / den;
+    else bad[m] = 1;
+  }
+  for (int m = 0; m < K; ++m)
+    if (bad[m]) b[m] = 0.5 * (b[(m + K - 1) % K] + b[(m + 1) % K]);
+  return b;
+}
+
+std::string validate_spec(const SysSpec &sp) {
+  const gcme_params &p = sp.p;
+  char buf[256];
+  if (sp.n < 1) return "n must be >= 1";
+  if (sp.n > (1LL << 30)) return "n too large";
+  if ((int64_t)sp.q.size() != sp.n) return "charge array size mismatch";
+  if (p.geometry < GCME_BULK || p.geometry > GCME_SLAB_IMAGE) return "unknown geometry";
+  if (p.precision != GCME_FP32 && p.precision != GCME_FP64) return "unknown precision";
+  if (!(p.rc > 0) || !(p.kappa > 0) || !(p.lB >= 0) || !(p.sigma > 0) || !(p.a > 0) || !(p.A >= 0))
+    return "rc, kappa, sigma, a must be > 0 and lB, A >= 0";
+  for (int a = 0; a < 3; ++a) {
+    if (!(p.box[a] >= p.rc * (1.0 + 1e-4))) {
+      snprintf(buf, sizeof buf, "box side %d (%g) shorter than the cutoff %g", a, p.box[a], p.rc);
+      return buf;
+    }
+    if (!is_smooth(p.K[a]) || p.K[a] < 4 || p.K[a] > 1024) {
+      snprintf(buf, sizeof buf, "grid size K[%d]=%d must be 2^a 3^b 5^c in [4, 1024]", a, p.K[a]);
+      return buf;
+    }
+  }
+  if (p.order < 3 || p.order > 8) return "B-spline order must be in [3, 8]";
+  for (int a = 0; a < 3; ++a)
+    if (p.K[a] < p.order) return "grid size smaller than the spline order";
+  double qs = 0.0, qmax = 0.0;
+  for (double z : sp.q) {
+    if (!std::isfinite(z)) return "non-finite charge";
+    qs += z;
+    qmax = std::fmax(qmax, std::fabs(z));
+  }
+  if (std::fabs(qs) > 1e-6) {
+    snprintf(buf, sizeof buf, "system is not neutral (net charge %g)", qs);
+    return buf;
+  }
+  // non-collapse condition (Gaussian core model section) for the largest
+  // charge product: A / sigma_ij^3 > 4 pi^{3/2} z z lB / (3^{3/2} a_ij)
+  if (qmax > 0 && p.lB > 0) {
+    double sij = std::sqrt(2.0) * p.sigma, aij = std::sqrt(2.0) * p.a;
+    double lhs = p.A / (sij * sij * sij);
+    double rhs = 4.0 * std::pow(kPi, 1.5) * qmax * qmax * p.lB / (std::pow(3.0, 1.5) * aij);
+    if (!(lhs > rhs)) {
+      snprintf(buf, sizeof buf,
+               "non-collapse condition violated: A/sigma_ij^3 = %g <= 4 pi^1.5 lB z^2/(3^1.5 a_ij) = %g",
+               lhs, rhs);
+      return buf;
+    }
+  }
+  if (p.geometry != GCME_BULK) {
+    if (!(p.H > 0)) return "slab height H must be > 0";
+    double want = p.geometry == GCME_SLAB_NONMETAL ? 3.0 * p.H : 2.0 * p.H;
+    if (p.geometry == GCME_SLAB_IMAGE && std::fabs(p.box[2] - want) > 1e-9 * want)
+      return "image-charge slab needs box[2] == 2 H";
+    if (p.geometry == GCME_SLAB_NONMETAL && p.box[2] < want * (1.0 - 1e-12))
+      return "nonmetal slab needs box[2] >= 3 H";
+  }
+  if (!(p.dt >= 0)) return "dt must be >= 0";
+  const int64_t nb = (int64_t)sp.bonds.size() / 2;
+  for (int64_t b = 0; b < nb; ++b) {
+    int i = sp.bonds[2 * b], j = sp.bonds[2 * b + 1];
+    if (i < 0 || j < 0 || i >= sp.n || j >= sp.n || i == j) return "bond index out of range";
+  }
+  return "";
+}
+
+Engine::~Engine() {
+  for (auto &kv : graphs_) cudaGraphExecDestroy(kv.second);
+  for (auto g : graph_objs_) cudaGraphDestroy(g);
+  if (capture_stream) cudaStreamDestroy(capture_stream);
+  if (arena_) cudaFree(arena_);
+}
+
+namespace {
+struct Carver {
+  size_t off = 0;
+  std::vector<std::pair<void **, size_t>> req;
+  template <typename T>
+  void add(T **p, long long count) {
+    size_t bytes = (size_t)(count > 0 ? count : 0) * sizeof(T);
+    req.push_back({reinterpret_cast<void **>(p), bytes});
+    off += (bytes + 255) / 256 * 256;
+  }
+};
+}  // namespace
+
+int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
+  device = dev;
+  GCME_CK(cudaSetDevice(dev));
+  const int ns = (int)specs.size();
+  if (ns < 1) {
+    set_error("empty batch");
+    return GCME_ERR_INVALID;
+  }
+  fp64 = specs[0].p.precision == GCME_FP64;
+  for (auto &sp : specs) {
+    std::string err = validate_spec(sp);
+    if (!err.empty()) {
+      set_error(err);
+      return GCME_ERR_INVALID;
+    }
+    if ((sp.p.precision == GCME_FP64) != fp64) {
+      set_error("all systems of a batch must share one precision");
+      return GCME_ERR_INVALID;
+    }
+  }
+  hsys.assign(ns, SysDesc{});
+  bead_off.assign(ns + 1, 0);
+  long long nr = 0, ne = 0, nq = 0, nimg = 0, ncell = 0, ngrid = 0, nbond = 0;
+  int ntw = 0;
+  std::vector<std::vector<int>> qlists(ns), imgs(ns);
+  for (int s = 0; s < ns; ++s) {
+    const SysSpec &sp = specs[s];
+    const gcme_params &p = sp.p;
+    SysDesc &S = hsys[s];
+    S.n = (int)sp.n;
+    std::vector<int> &ql = qlists[s];
+    std::vector<int> &im = imgs[s];
+    for (int i = 0; i < S.n; ++i)
+      if (sp.q[i] != 0.0) ql.push_back(i);
+    S.nq_real = (int)ql.size();
+    if (p.geometry == GCME_SLAB_IMAGE) {
+      im = ql;
+      for (int k = 0; k < (int)im.size(); ++k) ql.push_back(S.n + k);
+    }
+    S.n_ext = S.n + (int)im.size();
+    S.nq_ext = (int)ql.size();
+    S.geometry = p.geometry;
+    S.precision = p.precision;
+    S.nbond = (int)(sp.bonds.size() / 2);
+    S.bead_off = nr;
+    S.ext_off = ne;
+    S.q_off = nq;
+    S.img_off = nimg;
+    S.cell_off = ncell;
+    S.grid_off = ngrid;
+    S.bond_off = nbond;
+    S.ncell = 1;
+    for (int a = 0; a < 3; ++a) {
+      S.nc[a] = std::max(1, (int)std::floor(p.box[a] / (p.rc * (1.0 + 1e-4))));
+      S.ncell *= S.nc[a];
+      S.box[a] = p.box[a];
+      S.inv_cell[a] = (double)S.nc[a] / p.box[a];
+      S.boxf[a] = (float)p.box[a];
+      S.K[a] = p.K[a];
+      S.kfac[a] = (float)((double)p.K[a] / p.box[a]);
+      S.tw_off[a] = ntw;
+      S.bsp_off[a] = ntw;
+      ntw += p.K[a];
+      std::vector<int> r = fft_radices(p.K[a]);
+      S.nstage[a] = (int)r.size();
+      for (int k = 0; k < (int)r.size(); ++k) S.radix[a][k] = r[k];
+    }
+    S.order = p.order;
+    S.rc2f = (float)(p.rc * p.rc);
+    S.V = p.box[0] * p.box[1] * p.box[2];
+    S.A = p.A;
+    S.sigma = p.sigma;
+    S.a = p.a;
+    S.lB = p.lB;
+    S.rc = p.rc;
+    S.kappa = p.kappa;
+    const double s2 = 2.0 * p.sigma * p.sigma;           // sigma_i^2 + sigma_j^2
+    const double aij = std::sqrt(2.0) * p.a;              // a_ij
+    S.beta = std::sqrt(kPi) / (std::sqrt(2.0) * aij);
+    S.gc_pref = p.A * std::pow(3.0 / (2.0 * kPi * s2), 1.5);
+    S.gc_expc = 3.0 / (2.0 * s2);
+    S.gc_fc = 3.0 / s2;
+    S.gc_c2f = (float)(-S.gc_expc / std::log(2.0));
+    double sq = 0.0;
+    for (double z : sp.q) sq += z * z;
+    S.e_corr = -p.lB * p.kappa / std::sqrt(kPi) * sq;
+    S.e_self = p.lB * sq / (2.0 * p.a);
+    S.recip_scale = p.geometry == GCME_SLAB_IMAGE ? 0.5 : 1.0;
+    S.H = p.H;
+    S.wall_A = p.geometry == GCME_BULK ? 0.0 : p.wall_A;
+    S.wall_s2 = p.wall_sigma2 > 0 ? p.wall_sigma2 : 1.0;
+    S.bond_k = p.bond_k;
+    S.bond_r0 = p.bond_r0;
+    S.dt = p.dt;
+    // Taylor series of g and h: erf(x) = 2/sqrt(pi) (x - x^3/3 + x^5/10 - x^7/42)
+    const double b = S.beta, k = p.kappa, c = 2.0 / std::sqrt(kPi);
+    const double d1 = b - k, d3 = b * b * b - k * k * k, d5 = std::pow(b, 5) - std::pow(k, 5),
+                 d7 = std::pow(b, 7) - std::pow(k, 7);
+    S.ser_g[0] = c * d1;
+    S.ser_g[1] = -c * d3 / 3.0;
+    S.ser_g[2] = c * d5 / 10.0;
+    S.ser_g[3] = -c * d7 / 42.0;
+    S.ser_h[0] = c * 2.0 * d3 / 3.0;
+    S.ser_h[1] = -c * 2.0 * d5 / 5.0;
+    S.ser_h[2] = c * d7 / 7.0;
+    for (int t = 0; t < 4; ++t) S.ser_gf[t] = (float)S.ser_g[t];
+    for (int t = 0; t < 3; ++t) S.ser_hf[t] = (float)S.ser_h[t];
+    S.betaf = (float)S.beta;
+    S.kappaf = (float)p.kappa;
+    nr += S.n;
+    ne += S.n_ext;
+    nq += S.nq_ext;
+    nimg += (long long)im.size();
+    ncell += S.ncell;
+    ngrid += (long long)p.K[0] * p.K[1] * p.K[2];
+    nbond += S.nbond;
+    bead_off[s + 1] = nr;
+  }
+  n_real = nr;
+  n_ext = ne;
+  // FFT plan
+  int kmax[3] = {0, 0, 0};
+  for (auto &S : hsys)
+    for (int a = 0; a < 3; ++a) kmax[a] = std::max(kmax[a], S.K[a]);
+  std::vector<int2> fftw[3];
+  for (int a = 0; a < 3; ++a) {
+    int lpb = std::max(8, std::min(64, 1024 / kmax[a]));
+    plan.lpb[a] = lpb;
+    plan.kmax[a] = kmax[a];
+    for (int s = 0; s < ns; ++s) {
+      const SysDesc &S = hsys[s];
+      long long nl = (long long)S.K[0] * S.K[1] * S.K[2] / S.K[a];
+      int nt = (int)((nl + lpb - 1) / lpb);
+      for (int t = 0; t < nt; ++t) fftw[a].push_back(make_int2(s, t));
+    }
+    plan.nwork[a] = (int)fftw[a].size();
+  }
+  std::vector<int2> pw;
+  for (int s = 0; s < ns; ++s)
+    for (int c = 0; c < hsys[s].ncell; ++c)
+      for (int dz = 0; dz < 3; ++dz) pw.push_back(make_int2(s, c * 3 + dz));
+  n_pair_work = (int)pw.size();
+
+  // ---- device arena
+  Carver cv;
+  SysDesc *d_sys = nullptr;
+  cv.add(&d_sys, ns);
+  P = Pool{};
+  P.nsys = ns;
+  if (own_state) {
+    cv.add(&P.pos, 3 * nr);
+    if (fp64) cv.add(reinterpret_cast<double **>(&P.vel), 3 * nr);
+    else cv.add(reinterpret_cast<float **>(&P.vel), 3 * nr);
+  }
+  double *d_q = nullptr;
+  cv.add(&d_q, nr);
+  cv.add(&P.force, 3 * nr);
+  cv.add(&P.xyzq_u, ne);
+  if (fp64) cv.add(&P.xyzq_u64, ne);
+  cv.add(&P.cell_of, ne);
+  cv.add(&P.slot, ne);
+  cv.add(&P.sorted_idx, ne);
+  cv.add(&P.sort_tmp, ne);
+  cv.add(&P.xyzq_s, ne);
+  if (fp64) cv.add(&P.xyzq_s64, ne);
+  cv.add(&P.ext_sys, ne);
+  cv.add(&P.real_sys, nr);
+  cv.add(&P.qlist, nq);
+  cv.add(&P.q_sys, nq);
+  cv.add(&P.img_src, nimg);
+  cv.add(&P.cell_cnt, ncell);
+  cv.add(&P.cell_start, ncell + 1);
+  cv.add(&P.cell_nimg, ncell);
+  cv.add(&P.cell_nq, ncell);
+  cv.add(&P.cell_sys, ncell);
+  cv.add(&P.qgrid, ngrid);
+  if (fp64) {
+    cv.add(&P.cgrid64, ngrid);
+    cv.add(&P.tw64, ntw);
+    cv.add(&P.bsp64, ntw);
+  } else {
+    cv.add(&P.cgrid, ngrid);
+    cv.add(&P.tw, ntw);
+    cv.add(&P.bsp, ntw);
+  }
+  cv.add(&P.bonds, nbond);
+  cv.add(&P.bond_sys, nbond);
+  cv.add(&P.acc, (long long)ns * kNacc);
+  cv.add(&P.vacc, (long long)ns * 9);
+  cv.add(&P.energy, (long long)ns * GCME_NTERMS);
+  cv.add(&P.virial, (long long)ns * 9);
+  cv.add(&pair_work, n_pair_work);
+  int2 *fw[3];
+  for (int a = 0; a < 3; ++a) cv.add(&fw[a], plan.nwork[a]);
+  scratch_bytes = cv.off;
+  cudaError_t e = cudaMalloc(&arena_, cv.off);
+  if (e != cudaSuccess) {
+    set_error(std::string("device allocation of ") + std::to_string(cv.off) +
+              " bytes failed: " + cudaGetErrorString(e));
+    arena_ = nullptr;
+    return GCME_ERR_OOM;
+  }
+  size_t off = 0;
+  for (auto &r : cv.req) {
+    *r.first = r.second ? static_cast<char *>(arena_) + off : nullptr;
+    off += (r.second + 255) / 256 * 256;
+  }
+  P.sys = d_sys;
+  P.q = d_q;
+  P.n_real = nr;
+  P.n_ext = ne;
+  P.n_cells = ncell;
+  P.n_q = nq;
+  P.n_bond = nbond;
+  P.n_grid = ngrid;
+  for (int a = 0; a < 3; ++a) plan.work[a] = fw[a];
+
+  // ---- host tables -> device
+  std::vector<double> hq(nr);
+  std::vector<int> h_ext_sys(ne), h_real_sys(nr), h_ql(nq), h_qs(nq), h_img(nimg), h_cs(ncell);
+  std::vector<int2> h_bonds(nbond);
+  std::vector<int> h_bsys(nbond);
+  std::vector<float2> htw(fp64 ? 0 : ntw);
+  std::vector<double2> htw64(fp64 ? ntw : 0);
+  std::vector<float> hbsp(fp64 ? 0 : ntw);
+  std::vector<double> hbsp64(fp64 ? ntw : 0);
+  for (int s = 0; s < ns; ++s) {
+    const SysDesc &S = hsys[s];
+    const SysSpec &sp = specs[s];
+    for (int i = 0; i < S.n; ++i) {
+      hq[S.bead_off + i] = sp.q[i];
+      h_real_sys[S.bead_off + i] = s;
+    }
+    for (int e2 = 0; e2 < S.n_ext; ++e2) h_ext_sys[S.ext_off + e2] = s;
+    for (int k = 0; k < S.nq_ext; ++k) {
+      h_ql[S.q_off + k] = qlists[s][k];
+      h_qs[S.q_off + k] = s;
+    }
+    for (int k = 0; k < (int)imgs[s].size(); ++k) h_img[S.img_off + k] = imgs[s][k];
+    for (int c = 0; c < S.ncell; ++c) h_cs[S.cell_off + c] = s;
+    for (int b = 0; b < S.nbond; ++b) {
+      h_bonds[S.bond_off + b] = make_int2(sp.bonds[2 * b], sp.bonds[2 * b + 1]);
+      h_bsys[S.bond_off + b] = s;
+    }
+    for (int a = 0; a < 3; ++a) {
+      const int K = S.K[a];
+      std::vector<double> bm = host_bsp_moduli(S.order, K);
+      for (int t = 0; t < K; ++t) {
+        const double ang = -2.0 * kPi * t / K;
+        if (fp64) {
+          htw64[S.tw_off[a] + t] = make_double2(std::cos(ang), std::sin(ang));
+          hbsp64[S.bsp_off[a] + t] = bm[t];
+        } else {
+          htw[S.tw_off[a] + t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+          hbsp[S.bsp_off[a] + t] = (float)bm[t];
+        }
+      }
+    }
+  }
+  GCME_CK(cudaMemcpy(d_sys, hsys.data(), sizeof(SysDesc) * ns, cudaMemcpyHostToDevice));
+  auto up = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+    if (!bytes) return cudaSuccess;
+    return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  GCME_CK(up(d_q, hq.data(), sizeof(double) * nr));
+  GCME_CK(up(P.ext_sys, h_ext_sys.data(), sizeof(int) * ne));
+  GCME_CK(up(P.real_sys, h_real_sys.data(), sizeof(int) * nr));
+  GCME_CK(up(P.qlist, h_ql.data(), sizeof(int) * nq));
+  GCME_CK(up(P.q_sys, h_qs.data(), sizeof(int) * nq));
+  GCME_CK(up(P.img_src, h_img.data(), sizeof(int) * nimg));
+  GCME_CK(up(P.cell_sys, h_cs.data(), sizeof(int) * ncell));
+  GCME_CK(up(P.bonds, h_bonds.data(), sizeof(int2) * nbond));
+  GCME_CK(up(P.bond_sys, h_bsys.data(), sizeof(int) * nbond));
+  if (fp64) {
+    GCME_CK(up(P.tw64, htw64.data(), sizeof(double2) * ntw));
+    GCME_CK(up(P.bsp64, hbsp64.data(), sizeof(double) * ntw));
+  } else {
+    GCME_CK(up(P.tw, htw.data(), sizeof(float2) * ntw));
+    GCME_CK(up(P.bsp, hbsp.data(), sizeof(float) * ntw));
+  }
+  GCME_CK(up(pair_work, pw.data(), sizeof(int2) * n_pair_work));
+  for (int a = 0; a < 3; ++a) GCME_CK(up(fw[a], fftw[a].data(), sizeof(int2) * plan.nwork[a]));
+  if (own_state) {
+    GCME_CK(cudaMemset(P.pos, 0, sizeof(double) * 3 * nr));
+    GCME_CK(cudaMemset(P.vel, 0, (fp64 ? 8 : 4) * 3 * nr));
+  }
+  GCME_CK(cudaMemset(P.force, 0, sizeof(long long) * 3 * nr));
+  GCME_CK(cudaMemset(P.energy, 0, sizeof(double) * ns * GCME_NTERMS));
+  GCME_CK(cudaMemset(P.virial, 0, sizeof(double) * ns * 9));
+  GCME_CK(cudaStreamCreateWithFlags(&capture_stream, cudaStreamNonBlocking));
+  static std::once_flag once[64];
+  std::call_once(once[dev & 63], [] { pme_set_smem_limits(); });
+  return GCME_OK;
+}
+
+void Engine::enqueue_forces(const Pool &Q, cudaStream_t st, bool vir, bool dbg) {
+  cudaMemsetAsync(Q.force, 0, sizeof(long long) * 3 * Q.n_real, st);
+  cudaMemsetAsync(Q.acc, 0, sizeof(unsigned long long) * Q.nsys * kNacc, st);
+  if (vir) cudaMemsetAsync(Q.vacc, 0, sizeof(unsigned long long) * Q.nsys * 9, st);
+  launch_cells(Q, st);
+  launch_pair(Q, pair_work, n_pair_work, fp64, vir, dbg, st);
+  if (dbg) return;
+  launch_pme(Q, plan, fp64, vir, st);
+  launch_bonded(Q, vir, st);
+  launch_slab_apply(Q, st);
+}
+
+void Engine::enqueue_step(const Pool &Q, cudaStream_t st) {
+  launch_kick_drift(Q, fp64, st);
+  enqueue_forces(Q, st, false, false);
+  launch_kick(Q, fp64, st);
+  launch_finalize(Q, false, st);
+}
+
+int Engine::step_graph(const Pool &Q, cudaGraphExec_t *out) {
+  auto key = std::make_tuple((void *)Q.pos, (void *)Q.vel, (void *)Q.force, 1);
+  auto it = graphs_.find(key);
+  if (it != graphs_.end()) {
+    *out = it->second;
+    return GCME_OK;
+  }
+  cudaGraph_t g;
+  GCME_CK(cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal));
+  enqueue_step(Q, capture_stream);
+  GCME_CK(cudaStreamEndCapture(capture_stream, &g));
+  cudaGraphExec_t ge;
+  GCME_CK(cudaGraphInstantiate(&ge, g, 0));
+  graph_objs_.push_back(g);
+  graphs_[key] = ge;
+  *out = ge;
+  return GCME_OK;
+}
+
+int Engine::forces_graph(const Pool &Q, cudaGraphExec_t *out) {
+  auto key = std::make_tuple((void *)Q.pos, (void *)Q.vel, (void *)Q.force, 2);
+  auto it = graphs_.find(key);
+  if (it != graphs_.end()) {
+    *out = it->second;
+    return GCME_OK;
+  }
+  cudaGraph_t g;
+  GCME_CK(cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal));
+  enqueue_forces(Q, capture_stream, false, false);
+  launch_finalize(Q, false, capture_stream);
+  GCME_CK(cudaStreamEndCapture(capture_stream, &g));
+  cudaGraphExec_t ge;
+  GCME_CK(cudaGraphInstantiate(&ge, g, 0));
+  graph_objs_.push_back(g);
+  graphs_[key] = ge;
+  *out = ge;
+  return GCME_OK;
+}
+
+}  // namespace gcme
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+using namespace gcme;
+
+struct gcme_sys {
+  gcme_ctx *ctx;
+  Engine eng;
+  gcme_params p;
+};
+
+struct gcme_batch {
+  gcme_ctx *ctx;
+  Engine eng;
+  bool forces_valid = false;
+};
+
+#define GCME_TRY_CK(call)                                                          \
+  do {                                                                             \
+    cudaError_t _e = (call);                                                       \
+    if (_e != cudaSuccess) {                                                       \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(_e));               \
+      return GCME_ERR_CUDA;                                                        \
+    }                                                                              \
+  } while (0)
+
+static int check_launch(const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return GCME_ERR_CUDA;
+  }
+  return GCME_OK;
+}
+
+extern "C" {
+
+const char *gcme_last_error(void) { return g_err.c_str(); }
+
+const char *gcme_version(void) { return "gcme 0.1 (sm_103a)"; }
+
+void gcme_params_default(gcme_params *p, double L, int32_t K) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->box[0] = p->box[1] = p->box[2] = L;
+  p->geometry = GCME_BULK;
+  p->precision = GCME_FP32;
+  p->A = 25.0;
+  p->sigma = 0.5;
+  p->a = 0.5;
+  p->lB = 1.2053;
+  p->rc = 3.0;
+  p->kappa = 0.87609;
+  p->K[0] = p->K[1] = p->K[2] = K;
+  p->order = 5;
+  p->dt = 0.01;
+  p->bond_k = 100.0;
+  p->bond_r0 = 1.0;
+}
+
+int gcme_validate(const gcme_params *p, int64_t n, const double *h_q, const int32_t *h_bonds,
+                  int64_t nbonds) {
+  if (!p || !h_q || n < 1 || nbonds < 0 || (nbonds > 0 && !h_bonds)) {
+    set_error("invalid argument to gcme_validate");
+    return GCME_ERR_INVALID;
+  }
+  SysSpec sp;
+  sp.p = *p;
+  sp.n = n;
+  sp.q.assign(h_q, h_q + n);
+  if (nbonds) sp.bonds.assign(h_bonds, h_bonds + 2 * nbonds);
+  std::string err = validate_spec(sp);
+  if (!err.empty()) {
+    set_error(err);
+    return GCME_ERR_INVALID;
+  }
+  set_error("");
+  return GCME_OK;
+}
+
+int gcme_ctx_create(gcme_ctx **out, int device) {
+  if (!out) {
+    set_error("out is NULL");
+    return GCME_ERR_INVALID;
+  }
+  int ndev = 0;
+  GCME_TRY_CK(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) {
+    set_error("device index out of range");
+    return GCME_ERR_INVALID;
+  }
+  GCME_TRY_CK(cudaSetDevice(device));
+  *out = new gcme_ctx{device};
+  return GCME_OK;
+}
+
+void gcme_ctx_destroy(gcme_ctx *ctx) { delete ctx; }
+
+int gcme_system_create(gcme_ctx *ctx, const gcme_params *p, int64_t n, const double *h_q,
+                       const int32_t *h_bonds, int64_t nbonds, gcme_sys **out) {
+  if (!ctx || !p || !h_q || !out || n < 1 || nbonds < 0 || (nbonds > 0 && !h_bonds)) {
+    set_error("invalid argument to gcme_system_create");
+    return GCME_ERR_INVALID;
+  }
+  SysSpec sp;
+  sp.p = *p;
+  sp.n = n;
+  sp.q.assign(h_q, h_q + n);
+  if (nbonds) sp.bonds.assign(h_bonds, h_bonds + 2 * nbonds);
+  gcme_sys *s = new gcme_sys;
+  s->ctx = ctx;
+  s->p = *p;
+  int rc = s->eng.build(ctx->device, {sp}, false);
+  if (rc != GCME_OK) {
+    delete s;
+    return rc;
+  }
+  *out = s;
+  return GCME_OK;
+}
+
+void gcme_system_destroy(gcme_sys *sys) {
+  if (!sys) return;
+  cudaSetDevice(sys->eng.device);
+  delete sys;
+}
+
+int gcme_system_info(const gcme_sys *sys, gcme_sys_info *out) {
+  if (!sys || !out) {
+    set_error("NULL argument");
+    return GCME_ERR_INVALID;
+  }
+  const SysDesc &S = sys->eng.hsys[0];
+  out->n = S.n;
+  out->n_ext = S.n_ext;
+  out->n_charged_ext = S.nq_ext;
+  out->ncell = S.ncell;
+  out->nbonds = S.nbond;
+  for (int a = 0; a < 3; ++a) out->nc[a] = S.nc[a];
+  out->scratch_bytes = (int64_t)sys->eng.scratch_bytes;
+  return GCME_OK;
+}
+
+int gcme_build_cells(gcme_sys *sys, const double *d_pos, int32_t *d_cell_start,
+                     int32_t *d_sorted_idx, gcme_stream_t stream) {
+  if (!sys || !d_pos) {
+    set_error("NULL argument");
+    return GCME_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  GCME_TRY_CK(cudaSetDevice(sys->eng.device));
+  Pool Q = sys->eng.P;
+  Q.pos = const_cast<double *>(d_pos);
+  launch_cells(Q, st);
+  const SysDesc &S = sys->eng.hsys[0];
+  if (d_cell_start)
+    GCME_TRY_CK(cudaMemcpyAsync(d_cell_start, Q.cell_start, sizeof(int) * (S.ncell + 1),
+                                cudaMemcpyDeviceToDevice, st));
+  if (d_sorted_idx)
+    GCME_TRY_CK(cudaMemcpyAsync(d_sorted_idx, Q.sorted_idx, sizeof(int) * S.n_ext,
+                                cudaMemcpyDeviceToDevice, st));
+  return check_launch("gcme_build_cells");
+}
+
+int gcme_forces(gcme_sys *sys, const double *d_pos, int64_t *d_force, double *d_energy,
+                double *d_virial, gcme_stream_t stream) {
+  if (!sys || !d_pos) {
+    set_error("NULL argument");
+    return GCME_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  GCME_TRY_CK(cudaSetDevice(sys->eng.device));
+  Pool Q = sys->eng.P;
+  Q.pos = const_cast<double *>(d_pos);
+  if (d_force) Q.force = reinterpret_cast<long long *>(d_force);
+  const bool vir = d_virial != nullptr;
+  sys->eng.enqueue_forces(Q, st, vir, false);
+  launch_finalize(Q, vir, st);
+  if (d_energy)
+    GCME_TRY_CK(cudaMemcpyAsync(d_energy, Q.energy, sizeof(double) * GCME_NTERMS,
+                                cudaMemcpyDeviceToDevice, st));
+  if (d_virial)
+    GCME_TRY_CK(cudaMemcpyAsync(d_virial, Q.virial, sizeof(double) * 9, cudaMemcpyDeviceToDevice,
+                                st));
+  return check_launch("gcme_forces");
+}
+
+int gcme_forces_to_f64(gcme_sys *sys, const int64_t *d_force, double *d_out,
+                       gcme_stream_t stream) {
+  if (!sys || !d_force || !d_out) {
+    set_error("NULL argument");
+    return GCME_ERR_INVALID;
+  }
+  GCME_TRY_CK(cudaSetDevice(sys->eng.device));
+  launch_force_to_f64(reinterpret_cast<const long long *>(d_force), d_out,
+                      3LL * sys->eng.hsys[0].n, (cudaStream_t)stream);
+  return check_launch("gcme_forces_to_f64");
+}
+
+static int run_steps(Engine &eng, const Pool &Q, int64_t nsteps, cudaStream_t st) {
+  cudaGraphExec_t fg, sg;
+  int rc = eng.forces_graph(Q, &fg);
+  if (rc) return rc;
+  rc = eng.step_graph(Q, &sg);
+  if (rc) return rc;
+  GCME_TRY_CK(cudaGraphLaunch(fg, st));
+  for (int64_t k = 0; k < nsteps; ++k) GCME_TRY_CK(cudaGraphLaunch(sg, st));
+  return GCME_OK;
+}
+
+int gcme_step(gcme_sys *sys, double *d_pos, float *d_vel, int64_t nsteps, double *d_energy,
+              gcme_stream_t stream) {
+  if (!sys || !d_pos || !d_vel || nsteps < 0) {
+    set_error("invalid argument to gcme_step");
+    return GCME_ERR_INVALID;
+  }
+  if (sys->eng.fp64) {
+    set_error("FP64 systems step with gcme_step_f64");
+    return GCME_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  GCME_TRY_CK(cudaSetDevice(sys->eng.device));
+  Pool Q = sys->eng.P;
+  Q.pos = d_pos;
+  Q.vel = d_vel;
+  int rc = run_steps(sys->eng, Q, nsteps, st);
+  if (rc) return rc;
+  if (d_energy)
+    GCME_TRY_CK(cudaMemcpyAsync(d_energy, Q.energy, sizeof(double) * GCME_NTERMS,
+                                cudaMemcpyDeviceToDevice, st));
+  return check_launch("gcme_step");
+}
+
+int gcme_step_f64(gcme_sys *sys, double *d_pos, double *d_vel, int64_t nsteps, double *d_energy,
+                  gcme_stream_t stream) {
+  if (!sys || !d_pos || !d_vel || nsteps < 0) {
+    set_error("invalid argument to gcme_step_f64");
+    return GCME_ERR_INVALID;
+  }
+  if (!sys->eng.fp64) {
+    set_error("FP32 systems step with gcme_step");
+    return GCME_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  GCME_TRY_CK(cudaSetDevice(sys->eng.device));
+  Pool Q = sys->eng.P;
+  Q.pos = d_pos;
+  Q.vel = d_vel;
+  int rc = run_steps(sys->eng, Q, nsteps, st);
+  if (rc) return rc;
+  if (d_energy)
+    GCME_TRY_CK(cudaMemcpyAsync(d_energy, Q.energy, sizeof(double) * GCME_NTERMS,
+                                cudaMemcpyDeviceToDevice, st));
+  return check_launch("gcme_step_f64");
+}
+
+int gcme_debug_pairs(gcme_sys *sys, const double *d_pos, int32_t *d_triples, int64_t cap,
+                     int64_t *d_count, gcme_stream_t stream) {
+  if (!sys || !d_pos || !d_count || cap < 0 || (cap > 0 && !d_triples)) {
+    set_error("invalid argument to gcme_debug_pairs");
+    return GCME_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  GCME_TRY_CK(cudaSetDevice(sys->eng.device));
+  Pool Q = sys->eng.P;
+  Q.pos = const_cast<double *>(d_pos);
+  Q.dbg_triples = d_triples;
+  Q.dbg_cap = cap;
+  sys->eng.enqueue_forces(Q, st, false, true);
+  GCME_TRY_CK(cudaMemcpyAsync(d_count, Q.acc + ACC_NPAIR, sizeof(int64_t),
+                              cudaMemcpyDeviceToDevice, st));
+  return check_launch("gcme_debug_pairs");
+}
+
+// ---- batch ----------------------------------------------------------------
+int gcme_batch_create(gcme_ctx *ctx, int32_t nsys, const gcme_params *params, const int64_t *n,
+                      const double *h_q, const int32_t *h_bonds, const int64_t *h_bond_count,
+                      gcme_batch **out) {
+  if (!ctx || nsys < 1 || !params || !n || !h_q || !out) {
+    set_error("invalid argument to gcme_batch_create");
+    return GCME_ERR_INVALID;
+  }
+  std::vector<SysSpec> specs(nsys);
+  int64_t qo = 0, bo = 0;
+  for (int s = 0; s < nsys; ++s) {
+    specs[s].p = params[s];
+    specs[s].n = n[s];
+    if (n[s] < 1) {
+      set_error("system size must be >= 1");
+      return GCME_ERR_INVALID;
+    }
+    specs[s].q.assign(h_q + qo, h_q + qo + n[s]);
+    qo += n[s];
+    int64_t nb = h_bond_count ? h_bond_count[s] : 0;
+    if (nb > 0) {
+      if (!h_bonds) {
+        set_error("bond counts given without bonds");
+        return GCME_ERR_INVALID;
+      }
+      specs[s].bonds.assign(h_bonds + 2 * bo, h_bonds + 2 * (bo + nb));
+    }
+    bo += nb;
+  }
+  gcme_batch *b = new gcme_batch;
+  b->ctx = ctx;
+  int rc = b->eng.build(ctx->device, specs, true);
+  if (rc) {
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return GCME_OK;
+}
+
+void gcme_batch_destroy(gcme_batch *b) {
+  if (!b) return;
+  cudaSetDevice(b->eng.device);
+  delete b;
+}
+
+int gcme_batch_pointers(gcme_batch *b, double **d_pos, float **d_vel, double **d_energy,
+                        const int64_t **h_bead_off) {
+  if (!b) {
+    set_error("NULL batch");
+    return GCME_ERR_INVALID;
+  }
+  if (d_pos) *d_pos = b->eng.P.pos;
+  if (d_vel) *d_vel = reinterpret_cast<float *>(b->eng.P.vel);
+  if (d_energy) *d_energy = b->eng.P.energy;
+  if (h_bead_off) *h_bead_off = reinterpret_cast<const int64_t *>(b->eng.bead_off.data());
+  return GCME_OK;
+}
+
+int gcme_batch_set_state(gcme_batch *b, const double *h_pos, const float *h_vel,
+                         gcme_stream_t stream) {
+  if (!b) {
+    set_error("NULL batch");
+    return GCME_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  GCME_TRY_CK(cudaSetDevice(b->eng.device));
+  const long long n = b->eng.n_real;
+  if (h_pos)
+    GCME_TRY_CK(cudaMemcpyAsync(b->eng.P.pos, h_pos, sizeof(double) * 3 * n,
+                                cudaMemcpyHostToDevice, st));
+  if (h_vel) {
+    if (b->eng.fp64) {
+      std::vector<double> v(h_vel, h_vel + 3 * n);
+      GCME_TRY_CK(cudaMemcpyAsync(b->eng.P.vel, v.data(), sizeof(double) * 3 * n,
+                                  cudaMemcpyHostToDevice, st));
+      GCME_TRY_CK(cudaStreamSynchronize(st));
+    } else {
+      GCME_TRY_CK(cudaMemcpyAsync(b->eng.P.vel, h_vel, sizeof(float) * 3 * n,
+                                  cudaMemcpyHostToDevice, st));
+    }
+  }
+  b->forces_valid = false;
+  return GCME_OK;
+}
+
+int gcme_batch_get_state(gcme_batch *b, double *h_pos, float *h_vel, double *h_energy,
+                         gcme_stream_t stream) {
+  if (!b) {
+    set_error("NULL batch");
+    return GCME_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  GCME_TRY_CK(cudaSetDevice(b->eng.device));
+  const long long n = b->eng.n_real;
+  if (h_pos)
+    GCME_TRY_CK(cudaMemcpyAsync(h_pos, b->eng.P.pos, sizeof(double) * 3 * n,
+                                cudaMemcpyDeviceToHost, st));
+  std::vector<double> v64;
+  if (h_vel) {
+    if (b->eng.fp64) {
+      v64.resize(3 * n);
+      GCME_TRY_CK(cudaMemcpyAsync(v64.data(), b->eng.P.vel, sizeof(double) * 3 * n,
+                                  cudaMemcpyDeviceToHost, st));
+    } else {
+      GCME_TRY_CK(cudaMemcpyAsync(h_vel, b->eng.P.vel, sizeof(float) * 3 * n,
+                                  cudaMemcpyDeviceToHost, st));
+    }
+  }
+  if (h_energy)
+    GCME_TRY_CK(cudaMemcpyAsync(h_energy, b->eng.P.energy,
+                                sizeof(double) * GCME_NTERMS * b->eng.nsys(),
+                                cudaMemcpyDeviceToHost, st));
+  GCME_TRY_CK(cudaStreamSynchronize(st));
+  if (h_vel && b->eng.fp64)
+    for (long long k = 0; k < 3 * n; ++k) h_vel[k] = (float)v64[k];
+  return GCME_OK;
+}
+
+int gcme_batch_step(gcme_batch *b, int64_t nsteps, int32_t mode, gcme_stream_t stream) {
+  if (!b || nsteps < 0 || (mode != 0 && mode != 1)) {
+    set_error("invalid argument to gcme_batch_step");
+    return GCME_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  GCME_TRY_CK(cudaSetDevice(b->eng.device));
+  const Pool &Q = b->eng.P;
+  cudaGraphExec_t fg, sg;
+  int rc = b->eng.forces_graph(Q, &fg);
+  if (rc) return rc;
+  rc = b->eng.step_graph(Q, &sg);
+  if (rc) return rc;
+  if (!b->forces_valid) {
+    GCME_TRY_CK(cudaGraphLaunch(fg, st));
+    b->forces_valid = true;
+  }
+  for (int64_t k = 0; k < nsteps; ++k) GCME_TRY_CK(cudaGraphLaunch(sg, st));
+  return check_launch("gcme_batch_step");
+}
+
+}  // extern "C"

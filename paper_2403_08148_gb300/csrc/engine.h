@@ -1,0 +1,69 @@
+// engine.h -- host-side batch engine behind the C ABI.
+#pragma once
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "kernels.h"
+
+namespace gcme {
+
+void set_error(const std::string &msg);
+
+struct SysSpec {
+  gcme_params p;
+  int64_t n = 0;
+  std::vector<double> q;
+  std::vector<int32_t> bonds;  // 2 * nbond, local indices
+};
+
+// Validate one system's parameters and charges; returns "" when valid.
+std::string validate_spec(const SysSpec &sp);
+
+// A batch of independent systems in pooled device memory.  A single system
+// is a batch of one whose state pointers may be the caller's buffers.
+class Engine {
+ public:
+  ~Engine();
+  // own_state: allocate pos/vel/force/q pools (batch and server); else the
+  // caller passes pos/force per call and only q is stored.
+  int build(int device, const std::vector<SysSpec> &specs, bool own_state);
+
+  // enqueue one force evaluation of every system at P.pos into P.force
+  void enqueue_forces(const Pool &P, cudaStream_t st, bool vir, bool dbg);
+  // enqueue one velocity-Verlet step (forces at P.pos must be current)
+  void enqueue_step(const Pool &P, cudaStream_t st);
+
+  // graph of one step for the given state pointers (cached)
+  int step_graph(const Pool &P, cudaGraphExec_t *out);
+  int forces_graph(const Pool &P, cudaGraphExec_t *out);
+
+  int nsys() const { return (int)hsys.size(); }
+  bool fp64 = false;
+  int device = 0;
+  std::vector<SysDesc> hsys;
+  Pool P{};  // device pointers of the pooled arrays
+  std::vector<long long> bead_off;
+  long long n_real = 0, n_ext = 0;
+  size_t scratch_bytes = 0;
+  int2 *pair_work = nullptr;
+  int n_pair_work = 0;
+  PmePlan plan{};
+  cudaStream_t capture_stream = nullptr;
+
+ private:
+  void *arena_ = nullptr;
+  std::map<std::tuple<void *, void *, void *, int>, cudaGraphExec_t> graphs_;
+  std::vector<cudaGraph_t> graph_objs_;
+};
+
+// radix factorisation of a 5-smooth grid size (4s first)
+std::vector<int> fft_radices(int K);
+bool is_smooth(int K);
+
+}  // namespace gcme
+
+struct gcme_ctx {
+  int device;
+};

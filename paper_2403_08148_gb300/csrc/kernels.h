@@ -1,0 +1,28 @@
+// kernels.h -- host-side launchers of the libgcme kernels.
+#pragma once
+#include "common.cuh"
+
+namespace gcme {
+
+// FFT work per axis: int2 (system, tile of lpb lines), lines per tile and
+// the largest grid extent along that axis over the batch.
+struct PmePlan {
+  const int2 *work[3];
+  int nwork[3];
+  int lpb[3];
+  int kmax[3];
+};
+
+void launch_cells(const Pool &P, cudaStream_t st);
+void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, bool vir, bool dbg,
+                 cudaStream_t st);
+void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStream_t st);
+void pme_set_smem_limits();
+void launch_bonded(const Pool &P, bool vir, cudaStream_t st);   // bonds, walls, dipole
+void launch_slab_apply(const Pool &P, cudaStream_t st);         // Yeh-Berkowitz forces
+void launch_finalize(const Pool &P, bool vir, cudaStream_t st); // energies -> FP64
+void launch_kick_drift(const Pool &P, bool vel64, cudaStream_t st);
+void launch_kick(const Pool &P, bool vel64, cudaStream_t st);
+void launch_force_to_f64(const long long *f, double *out, long long n3, cudaStream_t st);
+
+}  // namespace gcme

@@ -1,0 +1,219 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Cell lists and neighbour sets must be bit-exact; forces and energies must
+meet the FP32 bounds (relative RMS force <= 5e-4, relative potential energy
+<= 1e-6) and the much tighter FP64-path bounds.  Inputs are the seeded
+synthetic workloads of ``synth``.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import (ENERGY_RTOL_FP32, ENERGY_RTOL_FP64, FORCE_RTOL_FP32, FORCE_RTOL_FP64,
+                      ctx, gpu_forces, lib, rel_rms)
+
+pytestmark = pytest.mark.gpu
+
+
+def _small_cases():
+    return {
+        "bulk_n3000": synth.config1(),
+        "poly_bonds": synth.make_polyelectrolyte(n_chains=8, chain_len=12, n_solvent=1200,
+                                                 seed_index=50, K=(24, 24, 24)),
+        "tiny_box_n120": synth.make_bulk(120, seed_index=51, charged_frac=0.3, K=(8, 8, 8)),
+        "box_2cells_n700": synth.make_bulk(700, seed_index=52, charged_frac=0.2, K=(10, 10, 10)),
+        "slab_nm": synth.make_slab_fluid(synth.GEOM_SLAB_NM, 900, charged_frac=0.2,
+                                         seed_index=53),
+        "slab_pc": synth.make_slab_fluid(synth.GEOM_SLAB_PC, 900, charged_frac=0.2,
+                                         seed_index=54),
+        "neutral_only": synth.make_bulk(500, seed_index=55, charged_frac=0.0, K=(8, 8, 8)),
+        "ragged_odd_grid": synth.make_bulk(1000, seed_index=56, charged_frac=0.4,
+                                           K=(15, 12, 10)),
+    }
+
+
+CASES = _small_cases()
+
+
+# --------------------------------------------------------------------------
+# K1/K2: cell list, bit-exact
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["bulk_n3000", "tiny_box_n120", "slab_pc", "poly_bonds"])
+def test_cell_list_bit_exact(name):
+    import torch
+    g = lib()
+    s = CASES[name]
+    sysg = g.System(ctx(), g.params_from(s), s.q, s.bonds)
+    info = sysg.info()
+    dev = torch.device("cuda:0")
+    pos = torch.tensor(s.pos, dtype=torch.float64, device=dev)
+    cs = torch.zeros(info.ncell + 1, dtype=torch.int32, device=dev)
+    si = torch.zeros(info.n_ext, dtype=torch.int32, device=dev)
+    sysg.build_cells(pos, cs, si)
+    torch.cuda.synchronize()
+    epos, eq, etype, _ = oracle.electrostatic_beads(s)
+    nc = oracle.cell_counts(s.box, s.rc)
+    assert list(nc) == list(info.nc)
+    _, start, order = oracle.cell_list(epos, s.box, nc, oracle.bead_classes(s))
+    assert np.array_equal(cs.cpu().numpy(), start)
+    assert np.array_equal(si.cpu().numpy(), order)
+
+
+# --------------------------------------------------------------------------
+# K3 neighbour set, bit-exact
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("name,prec", [("bulk_n3000", 0), ("tiny_box_n120", 0),
+                                       ("box_2cells_n700", 0), ("slab_pc", 0),
+                                       ("bulk_n3000", 1), ("slab_pc", 1)])
+def test_pair_set_bit_exact(name, prec):
+    import torch
+    g = lib()
+    s = CASES[name]
+    sysg = g.System(ctx(), g.params_from(s, prec), s.q, s.bonds)
+    dev = torch.device("cuda:0")
+    pos = torch.tensor(s.pos, dtype=torch.float64, device=dev)
+    cap = 4_000_000
+    trip = torch.zeros(3 * cap, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    sysg.debug_pairs(pos, trip, cap, cnt)
+    torch.cuda.synchronize()
+    k = int(cnt.item())
+    assert k <= cap
+    got = trip[: 3 * k].cpu().numpy().reshape(-1, 3)
+    epos, _, _, n = oracle.electrostatic_beads(s)
+    ref = oracle.pair_set(epos, s.box, s.rc)
+    ref = ref[ref[:, 0] < n]                    # the kernel's i runs over real beads
+    a = np.unique(got, axis=0)
+    assert a.shape[0] == got.shape[0], "duplicate triples"
+    b = np.unique(ref, axis=0)
+    assert a.shape == b.shape and np.array_equal(a, b)
+
+
+# --------------------------------------------------------------------------
+# Forces and energies
+# --------------------------------------------------------------------------
+def _check(s, out, ref, f_tol, e_tol, per_term_tol):
+    ferr = rel_rms(out["forces"], ref["forces"])
+    e = out["energy"]
+    eerr = abs(e["potential"] - ref["potential"]) / abs(ref["potential"])
+    scale = sum(abs(ref[t]) for t in oracle.TERMS)
+    terms = {t: abs(e[t] - ref[t]) / scale for t in oracle.TERMS}
+    assert ferr <= f_tol, f"force rel RMS {ferr:.3e}"
+    assert eerr <= e_tol, f"energy rel {eerr:.3e} ({e['potential']} vs {ref['potential']})"
+    for t, v in terms.items():
+        assert v <= per_term_tol, f"term {t}: {e[t]} vs {ref[t]}"
+    return ferr, eerr
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_forces_fp32(name):
+    s = CASES[name]
+    out = gpu_forces(s, 0)
+    ref = oracle.energy_forces(s)
+    _check(s, out, ref, FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
+
+
+@pytest.mark.parametrize("name", ["bulk_n3000", "poly_bonds", "slab_nm", "slab_pc",
+                                  "tiny_box_n120", "ragged_odd_grid"])
+def test_forces_fp64(name):
+    s = CASES[name]
+    out = gpu_forces(s, 1)
+    ref = oracle.energy_forces(s)
+    _check(s, out, ref, FORCE_RTOL_FP64, ENERGY_RTOL_FP64, 1e-10)
+
+
+def test_virial_fp32_and_fp64():
+    s = CASES["poly_bonds"]
+    ref = oracle.energy_forces(s)["virial"]
+    for prec, tol in ((0, 1e-5), (1, 1e-10)):
+        W = gpu_forces(s, prec, virial=True)["virial"]
+        assert np.max(np.abs(W - ref)) <= tol * np.max(np.abs(ref))
+
+
+def test_forces_deterministic():
+    s = CASES["poly_bonds"]
+    a = gpu_forces(s, 0)
+    b = gpu_forces(s, 0)
+    assert np.array_equal(a["fixed"], b["fixed"])
+    assert a["energy"] == b["energy"]
+
+
+def test_single_neutral_bead_and_kappa_beta_limit():
+    """Degenerate cases: a single bead (no pairs, no charges), and the fully
+    reciprocal choice kappa = beta (real term identically zero)."""
+    s = synth.make_bulk(100, seed_index=57, charged_frac=0.0, K=(8, 8, 8))
+    s.pos = s.pos[:1].copy()
+    s.vel = s.vel[:1].copy()
+    s.q = s.q[:1].copy()
+    s.box = np.array([3.5, 3.5, 3.5])
+    out = gpu_forces(s, 0)
+    ref = oracle.energy_forces(s)
+    assert abs(out["energy"]["potential"] - ref["potential"]) < 1e-9
+    t = synth.make_bulk(800, seed_index=58, charged_frac=0.5, K=(24, 24, 24))
+    t.kappa = float(np.sqrt(np.pi) / (2 * t.a))
+    out = gpu_forces(t, 0)
+    assert abs(out["energy"]["real"]) < 1e-6
+    ref = oracle.energy_forces(t)
+    assert rel_rms(out["forces"], ref["forces"]) < FORCE_RTOL_FP32
+
+
+# --------------------------------------------------------------------------
+# Full-size workloads: the bulk polyelectrolyte (N = 32,000, grid 64^3) and
+# the slabs (N = 64,000, grid 64 x 64 x 192) against the full oracle.
+# --------------------------------------------------------------------------
+def test_config2_full_size():
+    s = synth.config2()
+    out = gpu_forces(s, 0)
+    ref = oracle.energy_forces(s)
+    _check(s, out, ref, FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
+
+
+@pytest.mark.parametrize("geom", [synth.GEOM_SLAB_NM, synth.GEOM_SLAB_PC])
+def test_config3_full_size(geom):
+    s = synth.config3(geom)
+    out = gpu_forces(s, 0)
+    ref = oracle.energy_forces(s)
+    _check(s, out, ref, FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
+
+
+# --------------------------------------------------------------------------
+# Velocity Verlet through gcme_step
+# --------------------------------------------------------------------------
+def test_step_fp64_config1_100_steps():
+    """The plain FP64 workload: N = 3000, 100 steps of velocity Verlet."""
+    import torch
+    g = lib()
+    s = synth.config1()
+    sysg = g.System(ctx(), g.params_from(s, 1), s.q)
+    dev = torch.device("cuda:0")
+    pos = torch.tensor(s.pos, dtype=torch.float64, device=dev)
+    vel = torch.tensor(s.vel, dtype=torch.float64, device=dev)
+    E = torch.zeros(g.NTERMS, dtype=torch.float64, device=dev)
+    sysg.step(pos, vel, 100, E)
+    torch.cuda.synchronize()
+    p1, v1, hist = oracle.velocity_verlet(s, 100)
+    assert np.max(np.abs(pos.cpu().numpy() - p1)) < 1e-7
+    assert np.max(np.abs(vel.cpu().numpy() - v1)) < 1e-6
+    e = E.cpu().numpy()
+    assert abs(e[8] - hist[-1]["potential"]) / abs(hist[-1]["potential"]) < ENERGY_RTOL_FP64 * 100
+    assert abs(e[9] - hist[-1]["kinetic"]) / abs(hist[-1]["kinetic"]) < 1e-7
+
+
+def test_step_fp32_polyelectrolyte():
+    import torch
+    g = lib()
+    s = CASES["poly_bonds"]
+    sysg = g.System(ctx(), g.params_from(s, 0), s.q, s.bonds)
+    dev = torch.device("cuda:0")
+    pos = torch.tensor(s.pos, dtype=torch.float64, device=dev)
+    vel = torch.tensor(s.vel, dtype=torch.float32, device=dev)
+    E = torch.zeros(g.NTERMS, dtype=torch.float64, device=dev)
+    sysg.step(pos, vel, 20, E)
+    torch.cuda.synchronize()
+    p1, v1, hist = oracle.velocity_verlet(s, 20)
+    assert np.max(np.abs(pos.cpu().numpy() - p1)) < 1e-4
+    e = E.cpu().numpy()
+    tot_g = e[8] + e[9]
+    tot_o = hist[-1]["potential"] + hist[-1]["kinetic"]
+    assert abs(tot_g - tot_o) / abs(tot_o) < 1e-5
