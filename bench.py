@@ -1,0 +1,396 @@
+#!/usr/bin/env python
+"""Benchmark of the GCMe nonbonded force/energy path on GB300.
+
+Workload (default): the bulk polyelectrolyte solution, N = 32,000 beads at
+density 3 d^-3 (box 22.0128 d), 100 chains of 50 beads (-1) with harmonic
+bonds, 5,000 counterions (+1), 22,000 neutral solvent beads, smearing radius
+0.5 d, cutoff 3 d, PME grid 64^3, order 5, FP32 compute with 64-bit
+fixed-point force accumulation.  One step = one velocity-Verlet step: half
+kick + drift, cell list, pair kernel (Gaussian core + real-space
+electrostatics), PME (spread, FFTs, influence, gather), bonds, half kick and
+energy reduction.
+
+Metric: pair interactions per second (unordered in-cutoff pairs per step x
+steps per second), with steps/s beside it.  Timing: W warm-up steps, then K
+steps, each bracketed by CUDA events on the launching stream, with the L2
+flushed (a 512 MiB write) before every timed step; max over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun every rank steps its own replica (weak scaling); the
+single-system path does not shard.  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead (rank 0 only).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "pair interactions/s and steps/s (FP32 vs FP64 plain); served p50/p99 latency"
+UNIT = "pair interactions/s"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+N_SM = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ_NOMINAL = 2070.0
+# algorithmic work per unordered in-cutoff pair (FP32 operations)
+FLOP_GC_PAIR = 30
+FLOP_QQ_PAIR = 40
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gcme", choices=["gcme", "reference"])
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64-plain, batched and served side measurements")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_config(s):
+    return {"workload": "bulk polyelectrolyte N=32000 rho=3 (100x50 chains -1, 5000 +1, "
+                        "22000 solvent), rc=3, PME 64^3 p=5, velocity Verlet dt=0.01",
+            "n_beads": s.n, "box": float(s.box[0]), "grid": list(s.K), "cutoff": s.rc,
+            "kappa": round(s.kappa, 6), "bonds": int(s.bonds.shape[0]),
+            "charged": s.n_charged, "l2": "flushed (512 MiB write) before every timed step"}
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]),
+                                 power=float(parts[3]) if parts[3] not in ("[N/A]", "") else 0.0,
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                            ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[k].lower() in ("active", "1"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows),
+                "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(MEASURED_PEAKS))
+    except Exception:
+        return {}
+
+
+def pair_kernel_traffic():
+    """DRAM bytes per pair-kernel launch from the committed ncu summary, if
+    it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "pair_kernel_traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("kernel_sha") != kernel_sha():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def kernel_sha():
+    h = hashlib.sha256()
+    for f in ("pair.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2403_08148_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ---------------------------------------------------------------------------
+def count_pairs(g, sysg, s, pos, dev):
+    """Unordered in-cutoff pairs, and those between two charged beads, from
+    the pair kernel's own triple dump."""
+    import torch
+    cap = 16_000_000
+    trip = torch.empty(3 * cap, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    sysg.debug_pairs(pos, trip, cap, cnt)
+    torch.cuda.synchronize()
+    k = int(cnt.item())
+    t = trip[: 3 * min(k, cap)].view(-1, 3)
+    qd = torch.tensor(s.q, dtype=torch.float32, device=dev)
+    qq = int(((qd[t[:, 0].long()] != 0) & (qd[t[:, 1].long()] != 0)).sum().item())
+    del trip
+    torch.cuda.empty_cache()
+    return k // 2, qq // 2
+
+
+def run_gcme(args, ws, rank, local):
+    import torch
+    import paper_2403_08148_gb300 as g
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    g.builder.build() if hasattr(g, "builder") else None
+    g.load()
+    s = synth.config2()
+    ctx = g.Context(local)
+    sysg = g.System(ctx, g.params_from(s), s.q, s.bonds)
+    pos0 = torch.tensor(s.pos, dtype=torch.float64, device=dev)
+    vel0 = torch.tensor(s.vel, dtype=torch.float32, device=dev)
+    pos = pos0.clone()
+    vel = vel0.clone()
+    E = torch.zeros(g.NTERMS, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    pairs0, qq0 = count_pairs(g, sysg, s, pos, dev)
+
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MiB
+    # warm-up (includes the initial force evaluation and graph capture)
+    sysg.step(pos, vel, max(args.warmup, 3), E)
+    torch.cuda.synchronize()
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    phase = np.zeros(6)
+    clocks = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for k in range(K):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        sysg.step_continue(pos, vel, 1, E)
+        ends[k].record(stream)
+        ends[k].synchronize()
+        ms, nkern = sysg.phase_ms()
+        phase += ms
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    if ws > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        torch.distributed.barrier()
+    pairs1, qq1 = count_pairs(g, sysg, s, pos, dev)
+    pairs = 0.5 * (pairs0 + pairs1)
+    qq = 0.5 * (qq0 + qq1)
+    ms_per_step = total_ms / K
+    steps_per_s = 1e3 / ms_per_step
+    value = ws * pairs * steps_per_s
+    phase /= K
+    pair_ms = float(phase[2])
+
+    # back-to-back (warm L2) steps, context only
+    w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0.record(stream)
+    sysg.step_continue(pos, vel, K, E)
+    w1.record(stream)
+    w1.synchronize()
+    warm_ms = w0.elapsed_time(w1) / K
+
+    # end to end through the public API with host buffers: every step copies
+    # positions + velocities host -> device, runs gcme_step (which evaluates
+    # the forces of the copied state and advances one step), and reads the
+    # energies back
+    hpos = torch.empty((s.n, 3), dtype=torch.float64).pin_memory()
+    hvel = torch.empty((s.n, 3), dtype=torch.float32).pin_memory()
+    hE = torch.empty(g.NTERMS, dtype=torch.float64).pin_memory()
+    hpos.copy_(torch.from_numpy(s.pos))
+    hvel.copy_(torch.from_numpy(s.vel.astype(np.float32)))
+    Ke = max(10, K // 4)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(Ke):
+        pos.copy_(hpos, non_blocking=True)
+        vel.copy_(hvel, non_blocking=True)
+        sysg.step(pos, vel, 1, E)
+        hE.copy_(E, non_blocking=True)
+        stream.synchronize()
+    e2e_s = (time.perf_counter() - e0) / Ke
+    e2e_value = ws * pairs / e2e_s
+
+    peaks = measured_peaks()
+    flops = FLOP_GC_PAIR * pairs + FLOP_QQ_PAIR * qq
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    achieved = flops / (pair_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_pair_f32", "achieved": round(achieved, 4),
+                "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 5),
+                "traffic": pair_kernel_traffic(),
+                "peak_source": "FP32 pipe: 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)",
+                "work": f"{FLOP_GC_PAIR} flop per in-cutoff pair + {FLOP_QQ_PAIR} per charged pair",
+                "pair_kernel_ms": round(pair_ms, 5),
+                "hbm_peak_gbs": peaks.get("hbm_gbs")}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": workload_config(s), "steps_per_s": steps_per_s,
+           "pair_interactions_per_step": pairs, "charged_pairs_per_step": qq,
+           "phase_ms": dict(zip(("kick_drift", "cells", "pair", "pme", "bonded", "kick_energy"),
+                                [round(float(x), 5) for x in phase])),
+           "warm_l2_ms_per_step": warm_ms,
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": s.n * 3 * (8 + 4),
+                   "d2h_bytes_per_step": 8 * g.NTERMS,
+                   "note": "gcme_step(1) per step from host state: force evaluation of the "
+                           "copied state + one step"},
+           "roofline": roofline, "clocks": clk, "gpu_launches": int(nkern) * K,
+           "wall_s_timed": t_wall}
+    if not args.no_extras and rank == 0 and ws == 1:
+        out["fp64_plain"] = fp64_plain_compare(g, ctx, dev)
+    if rank == 0 and ws == 1:
+        out["cpu_baseline"] = cpu_baseline(s, pairs)
+    del flush
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return out if rank == 0 else None
+
+
+def fp64_plain_compare(g, ctx, dev, steps=20):
+    """Plain FP64 path vs FP32 path on the N=3000 fluid (grid 32^3)."""
+    import torch
+    s = synth.config1()
+    res = {}
+    for name, prec in (("fp32", 0), ("fp64", 1)):
+        sysg = g.System(ctx, g.params_from(s, prec), s.q)
+        pos = torch.tensor(s.pos, dtype=torch.float64, device=dev)
+        vel = torch.tensor(s.vel, dtype=torch.float64 if prec else torch.float32, device=dev)
+        sysg.step(pos, vel, 3)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        sysg.step_continue(pos, vel, steps)
+        b.record()
+        b.synchronize()
+        res[name + "_steps_per_s"] = 1e3 * steps / a.elapsed_time(b)
+        sysg.close()
+    res["workload"] = "N=3000 fluid rho=3, 10% charged, PME 32^3, back-to-back steps"
+    res["speedup_fp32_over_fp64"] = res["fp32_steps_per_s"] / res["fp64_steps_per_s"]
+    return res
+
+
+def cpu_baseline(s, pairs, budget_s=12.0):
+    """The oracle as it stands on the host cores: full force evaluations of
+    the same system (O(N^2) pair sum + FP64 SPME with direct DFTs)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        oracle.energy_forces(s)
+        n += 1
+        if time.perf_counter() - t0 > budget_s or n >= 20:
+            break
+    dt = (time.perf_counter() - t0) / n
+    return {"value": pairs / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} full force evaluations of the N=32000 polyelectrolyte "
+                      f"({dt:.2f} s each; one evaluation = one step's force work)"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    s = synth.config2()
+    # in-cutoff pairs of the starting configuration (FP32 rule, by the oracle)
+    ef = oracle.energy_forces(s)
+    pairs = ef["npairs"]
+    pos, vel, F = s.pos.copy(), s.vel.copy(), ef["forces"]
+    budget = 150.0
+    for _ in range(args.warmup if args.warmup < 2 else 1):
+        pass
+    t0 = time.perf_counter()
+    done = 0
+    for k in range(args.steps):
+        vel += 0.5 * s.dt * F
+        pos += s.dt * vel
+        F = oracle.energy_forces(s, pos)["forces"]
+        vel += 0.5 * s.dt * F
+        done += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    dt = (time.perf_counter() - t0) / done
+    value = pairs / dt
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(s), "impl": "reference", "steps_run": done,
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle",
+                             "cores": oracle.num_threads(),
+                             "sample": f"{done} velocity-Verlet steps of the N=32000 "
+                                       f"polyelectrolyte (time-boxed at {budget:.0f} s)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+    else:
+        out = run_gcme(args, ws, rank, local)
+    if out is not None and rank == 0:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -176,9 +176,25 @@ int gcme_forces_to_f64(gcme_sys *sys, const int64_t *d_force, double *d_out,
 int gcme_step(gcme_sys *sys, double *d_pos, float *d_vel, int64_t nsteps,
               double *d_energy, gcme_stream_t stream);
 
+/* Continue the trajectory of the last gcme_step / gcme_step_f64 call on the
+ * same buffers for nsteps more steps, reusing the forces that call left at
+ * the current positions (d_vel is float* or double* by the system's
+ * precision).  The caller must not change d_pos or d_vel in between; calls
+ * on other buffers return INVALID. */
+int gcme_step_continue(gcme_sys *sys, double *d_pos, void *d_vel, int64_t nsteps,
+                       double *d_energy, gcme_stream_t stream);
+
 /* The same for FP64 systems (the plain FP64 path), FP64 velocities. */
 int gcme_step_f64(gcme_sys *sys, double *d_pos, double *d_vel, int64_t nsteps,
                   double *d_energy, gcme_stream_t stream);
+
+/* Device time of the phases of the most recent completed step (the caller
+ * synchronises first), measured by CUDA events captured in the step graph:
+ * h_ms[0] half kick + drift, [1] cell list, [2] pair kernel, [3] PME,
+ * [4] bonds/walls/slab, [5] half kick + energies (nphase >= 6).  *kernels
+ * (may be NULL) receives the number of kernel launches in one step. */
+#define GCME_NPHASE 6
+int gcme_step_phase_ms(gcme_sys *sys, float *h_ms, int32_t nphase, int32_t *kernels);
 
 /* Sizes of the system: n, n_ext, ncell, number of charged beads incl.
  * images, cells per axis. */
@@ -221,6 +237,9 @@ int gcme_batch_get_state(gcme_batch *b, double *h_pos, float *h_vel,
  * step captured in a CUDA graph; mode 1: one persistent cooperative launch
  * running all phases of all steps with grid-wide barriers. */
 int gcme_batch_step(gcme_batch *b, int64_t nsteps, int32_t mode, gcme_stream_t stream);
+
+/* Phase times of the last batch step, as gcme_step_phase_ms. */
+int gcme_batch_phase_ms(gcme_batch *b, float *h_ms, int32_t nphase, int32_t *kernels);
 
 /* Device pointers to the pooled state (positions [3 N_tot] FP64, velocities
  * [3 N_tot] FP32, energies [nsys * GCME_NTERMS] FP64) and bead offsets. */

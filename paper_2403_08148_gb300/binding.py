@@ -84,6 +84,9 @@ _SIGS = {
     "gcme_forces_to_f64": ([_vp, _vp, _vp, _vp], ctypes.c_int),
     "gcme_step": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
     "gcme_step_f64": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
+    "gcme_step_continue": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
+    "gcme_step_phase_ms": ([_vp, _vp, _i32, _vp], ctypes.c_int),
+    "gcme_batch_phase_ms": ([_vp, _vp, _i32, _vp], ctypes.c_int),
     "gcme_debug_pairs": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
     "gcme_batch_create": ([_vp, _i32, ctypes.POINTER(Params), _vp, _vp, _vp, _vp,
                            ctypes.POINTER(_vp)], ctypes.c_int),
@@ -240,6 +243,17 @@ class System:
         _check(fn(self.h, _ptr(d_pos), _ptr(d_vel), int(nsteps), _ptr(d_energy),
                   _stream(stream)))
 
+    def step_continue(self, d_pos, d_vel, nsteps: int, d_energy=None, stream=None):
+        _check(load().gcme_step_continue(self.h, _ptr(d_pos), _ptr(d_vel), int(nsteps),
+                                         _ptr(d_energy), _stream(stream)))
+
+    def phase_ms(self):
+        """Device ms of the phases of the last step, and kernels per step."""
+        ms = np.zeros(6, np.float32)
+        k = np.zeros(1, np.int32)
+        _check(load().gcme_step_phase_ms(self.h, ms.ctypes.data, 6, k.ctypes.data))
+        return ms, int(k[0])
+
     def debug_pairs(self, d_pos, d_triples, cap: int, d_count, stream=None):
         _check(load().gcme_debug_pairs(self.h, _ptr(d_pos), _ptr(d_triples), int(cap),
                                        _ptr(d_count), _stream(stream)))
@@ -300,6 +314,12 @@ class Batch:
 
     def step(self, nsteps: int, mode: int = 0, stream=None):
         _check(load().gcme_batch_step(self.h, int(nsteps), int(mode), _stream(stream)))
+
+    def phase_ms(self):
+        ms = np.zeros(6, np.float32)
+        k = np.zeros(1, np.int32)
+        _check(load().gcme_batch_phase_ms(self.h, ms.ctypes.data, 6, k.ctypes.data))
+        return ms, int(k[0])
 
     def pointers(self):
         p, v, e, o = _vp(), _vp(), _vp(), _vp()

@@ -147,6 +147,8 @@ std::string validate_spec(const SysSpec &sp) {
 
 Engine::~Engine() {
   for (auto &kv : graphs_) cudaGraphExecDestroy(kv.second);
+  for (auto e : phase_ev)
+    if (e) cudaEventDestroy(e);
   for (auto g : graph_objs_) cudaGraphDestroy(g);
   if (capture_stream) cudaStreamDestroy(capture_stream);
   if (arena_) cudaFree(arena_);
@@ -473,10 +475,24 @@ void Engine::enqueue_forces(const Pool &Q, cudaStream_t st, bool vir, bool dbg) 
 }
 
 void Engine::enqueue_step(const Pool &Q, cudaStream_t st) {
+  const bool ev = phase_ev[0] != nullptr;
+  if (ev) cudaEventRecordWithFlags(phase_ev[0], st, cudaEventRecordExternal);
   launch_kick_drift(Q, fp64, st);
-  enqueue_forces(Q, st, false, false);
+  if (ev) cudaEventRecordWithFlags(phase_ev[1], st, cudaEventRecordExternal);
+  cudaMemsetAsync(Q.force, 0, sizeof(long long) * 3 * Q.n_real, st);
+  cudaMemsetAsync(Q.acc, 0, sizeof(unsigned long long) * Q.nsys * kNacc, st);
+  launch_cells(Q, st);
+  if (ev) cudaEventRecordWithFlags(phase_ev[2], st, cudaEventRecordExternal);
+  launch_pair(Q, pair_work, n_pair_work, fp64, false, false, st);
+  if (ev) cudaEventRecordWithFlags(phase_ev[3], st, cudaEventRecordExternal);
+  launch_pme(Q, plan, fp64, false, st);
+  if (ev) cudaEventRecordWithFlags(phase_ev[4], st, cudaEventRecordExternal);
+  launch_bonded(Q, false, st);
+  launch_slab_apply(Q, st);
+  if (ev) cudaEventRecordWithFlags(phase_ev[5], st, cudaEventRecordExternal);
   launch_kick(Q, fp64, st);
   launch_finalize(Q, false, st);
+  if (ev) cudaEventRecordWithFlags(phase_ev[6], st, cudaEventRecordExternal);
 }
 
 int Engine::step_graph(const Pool &Q, cudaGraphExec_t *out) {
@@ -487,9 +503,24 @@ int Engine::step_graph(const Pool &Q, cudaGraphExec_t *out) {
     return GCME_OK;
   }
   cudaGraph_t g;
+  if (!phase_ev[0])
+    for (int k = 0; k < kNPhaseEv; ++k) GCME_CK(cudaEventCreate(&phase_ev[k]));
   GCME_CK(cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal));
   enqueue_step(Q, capture_stream);
   GCME_CK(cudaStreamEndCapture(capture_stream, &g));
+  {
+    size_t nn = 0;
+    GCME_CK(cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    GCME_CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+    int nk = 0;
+    for (auto nd : nodes) {
+      cudaGraphNodeType t;
+      GCME_CK(cudaGraphNodeGetType(nd, &t));
+      nk += t == cudaGraphNodeTypeKernel;
+    }
+    step_kernels = nk;
+  }
   cudaGraphExec_t ge;
   GCME_CK(cudaGraphInstantiate(&ge, g, 0));
   graph_objs_.push_back(g);
@@ -529,6 +560,9 @@ struct gcme_sys {
   gcme_ctx *ctx;
   Engine eng;
   gcme_params p;
+  // buffers of the last gcme_step call: the internal force array then holds
+  // F at their current positions, so a continuation can skip that evaluation
+  const void *last_pos = nullptr, *last_vel = nullptr;
 };
 
 struct gcme_batch {
@@ -730,6 +764,35 @@ static int run_steps(Engine &eng, const Pool &Q, int64_t nsteps, cudaStream_t st
   return GCME_OK;
 }
 
+static int continue_steps(gcme_sys *sys, double *d_pos, void *d_vel, int64_t nsteps,
+                          double *d_energy, cudaStream_t st) {
+  if (d_pos != sys->last_pos || d_vel != sys->last_vel) {
+    set_error("gcme_step_continue: no preceding gcme_step on these buffers");
+    return GCME_ERR_INVALID;
+  }
+  Pool Q = sys->eng.P;
+  Q.pos = d_pos;
+  Q.vel = d_vel;
+  cudaGraphExec_t sg;
+  int rc = sys->eng.step_graph(Q, &sg);
+  if (rc) return rc;
+  for (int64_t k = 0; k < nsteps; ++k) GCME_TRY_CK(cudaGraphLaunch(sg, st));
+  if (d_energy)
+    GCME_TRY_CK(cudaMemcpyAsync(d_energy, Q.energy, sizeof(double) * GCME_NTERMS,
+                                cudaMemcpyDeviceToDevice, st));
+  return check_launch("gcme_step_continue");
+}
+
+int gcme_step_continue(gcme_sys *sys, double *d_pos, void *d_vel, int64_t nsteps,
+                       double *d_energy, gcme_stream_t stream) {
+  if (!sys || !d_pos || !d_vel || nsteps < 0) {
+    set_error("invalid argument to gcme_step_continue");
+    return GCME_ERR_INVALID;
+  }
+  GCME_TRY_CK(cudaSetDevice(sys->eng.device));
+  return continue_steps(sys, d_pos, d_vel, nsteps, d_energy, (cudaStream_t)stream);
+}
+
 int gcme_step(gcme_sys *sys, double *d_pos, float *d_vel, int64_t nsteps, double *d_energy,
               gcme_stream_t stream) {
   if (!sys || !d_pos || !d_vel || nsteps < 0) {
@@ -747,6 +810,8 @@ int gcme_step(gcme_sys *sys, double *d_pos, float *d_vel, int64_t nsteps, double
   Q.vel = d_vel;
   int rc = run_steps(sys->eng, Q, nsteps, st);
   if (rc) return rc;
+  sys->last_pos = d_pos;
+  sys->last_vel = d_vel;
   if (d_energy)
     GCME_TRY_CK(cudaMemcpyAsync(d_energy, Q.energy, sizeof(double) * GCME_NTERMS,
                                 cudaMemcpyDeviceToDevice, st));
@@ -770,10 +835,42 @@ int gcme_step_f64(gcme_sys *sys, double *d_pos, double *d_vel, int64_t nsteps, d
   Q.vel = d_vel;
   int rc = run_steps(sys->eng, Q, nsteps, st);
   if (rc) return rc;
+  sys->last_pos = d_pos;
+  sys->last_vel = d_vel;
   if (d_energy)
     GCME_TRY_CK(cudaMemcpyAsync(d_energy, Q.energy, sizeof(double) * GCME_NTERMS,
                                 cudaMemcpyDeviceToDevice, st));
   return check_launch("gcme_step_f64");
+}
+
+static int phase_ms(Engine &eng, float *h_ms, int32_t nphase, int32_t *kernels) {
+  if (kernels) *kernels = eng.step_kernels;
+  if (!h_ms) return GCME_OK;
+  if (nphase < Engine::kNPhaseEv - 1 || !eng.phase_ev[0]) {
+    set_error("no captured step yet, or output shorter than the phase count");
+    return GCME_ERR_INVALID;
+  }
+  for (int k = 0; k + 1 < Engine::kNPhaseEv; ++k)
+    GCME_TRY_CK(cudaEventElapsedTime(&h_ms[k], eng.phase_ev[k], eng.phase_ev[k + 1]));
+  return GCME_OK;
+}
+
+int gcme_step_phase_ms(gcme_sys *sys, float *h_ms, int32_t nphase, int32_t *kernels) {
+  if (!sys) {
+    set_error("NULL system");
+    return GCME_ERR_INVALID;
+  }
+  GCME_TRY_CK(cudaSetDevice(sys->eng.device));
+  return phase_ms(sys->eng, h_ms, nphase, kernels);
+}
+
+int gcme_batch_phase_ms(gcme_batch *b, float *h_ms, int32_t nphase, int32_t *kernels) {
+  if (!b) {
+    set_error("NULL batch");
+    return GCME_ERR_INVALID;
+  }
+  GCME_TRY_CK(cudaSetDevice(b->eng.device));
+  return phase_ms(b->eng, h_ms, nphase, kernels);
 }
 
 int gcme_debug_pairs(gcme_sys *sys, const double *d_pos, int32_t *d_triples, int64_t cap,

@@ -40,6 +40,12 @@ class Engine {
   int forces_graph(const Pool &P, cudaGraphExec_t *out);
 
   int nsys() const { return (int)hsys.size(); }
+  // Phase marks recorded inside the captured step graph: 0 start, 1 after
+  // the first half kick + drift, 2 after the cell list, 3 after the pair
+  // kernel, 4 after PME, 5 after bonds/walls/slab, 6 after kick + energies.
+  static constexpr int kNPhaseEv = 7;
+  cudaEvent_t phase_ev[kNPhaseEv] = {};
+  int step_kernels = 0;  // kernel nodes in the step graph
   bool fp64 = false;
   int device = 0;
   std::vector<SysDesc> hsys;
