@@ -158,6 +158,27 @@ void gcme_system_destroy(gcme_sys *sys);
 int gcme_build_cells(gcme_sys *sys, const double *d_pos, int32_t *d_cell_start,
                      int32_t *d_sorted_idx, gcme_stream_t stream);
 
+/* Cell-list build that allocates no device memory (no counterpart in the
+ * paper: an interface for callers that cannot call cudaMalloc, such as a
+ * host program whose device memory belongs to another runtime's pool, or a
+ * latency-bound loop that cannot afford cudaMalloc's implicit device
+ * synchronisation).  Same result as gcme_build_cells for a system of n real
+ * beads with parameters *p, positions d_pos[n*3] and charges d_q[n] (FP64,
+ * device), written to the caller's d_cell_start[ncell+1] and
+ * d_sorted_idx[n].  Scratch comes from one fixed file-scope device array
+ * of about 3.9 MB, held by every GPU that loads the library until exit:
+ *   - n <= 65536 beads and ncell <= 32768 cells, else INVALID with a message;
+ *   - bulk and nonmetal-slab geometries only (no image charges), else INVALID;
+ *   - the first call on a device looks up the array's device address with
+ *     that device current; make that first call before any stream capture;
+ *   - every call shares the array and leaves its contents behind: calls
+ *     whose work overlaps on the GPU (other streams, other threads) race,
+ *     so serialise them;
+ *   - no cudaMalloc, cudaFree or other allocating routine is called. */
+int gcme_build_cells_noalloc(const gcme_params *p, int64_t n, const double *d_pos,
+                             const double *d_q, int32_t *d_cell_start,
+                             int32_t *d_sorted_idx, gcme_stream_t stream);
+
 /* Forces, energies and virial at positions d_pos[n*3] (FP64, any image).
  * d_force[3n] (fixed point, SoA), d_energy[GCME_NTERMS], d_virial[9]; any
  * output may be NULL.  Errors: INVALID, CUDA. */

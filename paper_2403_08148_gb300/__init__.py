@@ -6,6 +6,7 @@ those calls.  There is no CPU fallback: without the built library every
 entry point raises.
 """
 from .binding import (Batch, Context, GcmeError, Params, Server, System, load,  # noqa: F401
+                      build_cells_noalloc,
                       params_from, validate, FORCE_SCALE, NTERMS, TERM_NAMES,
                       GCME_BULK, GCME_SLAB_NONMETAL, GCME_SLAB_IMAGE, GCME_FP32, GCME_FP64)
 from .builder import build, LIB  # noqa: F401

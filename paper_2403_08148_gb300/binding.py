@@ -81,6 +81,8 @@ _SIGS = {
     "gcme_system_info": ([_vp, ctypes.POINTER(SysInfo)], ctypes.c_int),
     "gcme_build_cells": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "gcme_forces": ([_vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "gcme_build_cells_noalloc": ([ctypes.POINTER(Params), _i64, _vp, _vp, _vp, _vp, _vp],
+                                 ctypes.c_int),
     "gcme_forces_to_f64": ([_vp, _vp, _vp, _vp], ctypes.c_int),
     "gcme_step": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
     "gcme_step_f64": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
@@ -172,6 +174,14 @@ def validate(params: Params, q, bonds=None):
     _check(load().gcme_validate(ctypes.byref(params), int(q.shape[0]), q.ctypes.data,
                                 None if b is None else b.ctypes.data,
                                 0 if b is None else int(b.shape[0])))
+
+
+def build_cells_noalloc(params: Params, n: int, d_pos, d_q, d_cell_start, d_sorted_idx,
+                        stream=None):
+    """Cell list without any device allocation (gcme_build_cells_noalloc)."""
+    _check(load().gcme_build_cells_noalloc(ctypes.byref(params), int(n), _ptr(d_pos), _ptr(d_q),
+                                           _ptr(d_cell_start), _ptr(d_sorted_idx),
+                                           _stream(stream)))
 
 
 class Context:
