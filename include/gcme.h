@@ -233,6 +233,12 @@ int gcme_system_info(const gcme_sys *sys, gcme_sys_info *out);
 int gcme_debug_pairs(gcme_sys *sys, const double *d_pos, int32_t *d_triples,
                      int64_t cap, int64_t *d_count, gcme_stream_t stream);
 
+/* Debug: launch a grid barrier that one CTA never reaches, so every other
+ * CTA's bounded wait (timeout_s seconds, at most 10) runs out; returns
+ * GCME_ERR_TIMEOUT when the kernel reported the timeout as designed.  Used
+ * to test the failure path of the persistent launch without hanging. */
+int gcme_debug_barrier_timeout(gcme_ctx *ctx, double timeout_s, gcme_stream_t stream);
+
 /* ---- batch of independent systems ---------------------------------------- */
 
 /* A batch of nsys independent systems stepped together: every phase of the

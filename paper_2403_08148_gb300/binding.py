@@ -89,6 +89,7 @@ _SIGS = {
     "gcme_step_continue": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
     "gcme_step_phase_ms": ([_vp, _vp, _i32, _vp], ctypes.c_int),
     "gcme_batch_phase_ms": ([_vp, _vp, _i32, _vp], ctypes.c_int),
+    "gcme_debug_barrier_timeout": ([_vp, ctypes.c_double, _vp], ctypes.c_int),
     "gcme_debug_pairs": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
     "gcme_batch_create": ([_vp, _i32, ctypes.POINTER(Params), _vp, _vp, _vp, _vp,
                            ctypes.POINTER(_vp)], ctypes.c_int),
@@ -191,6 +192,10 @@ class Context:
         _check(L.gcme_ctx_create(ctypes.byref(h), int(device)))
         self.h = h
         self.device = device
+
+    def barrier_timeout_probe(self, timeout_s: float = 0.2, stream=None) -> int:
+        """Run the bounded-wait barrier probe; returns the status code."""
+        return int(load().gcme_debug_barrier_timeout(self.h, float(timeout_s), _stream(stream)))
 
     def close(self):
         if self.h:

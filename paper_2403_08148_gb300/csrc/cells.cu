@@ -1,160 +1,26 @@
-// cells.cu -- K1/K2: wrap + bin, scan, scatter and the per-cell stable order.
-//
-// Cell list of side >= rc (the 27-cell stencil of the pair kernel).  The
-// binning is FP64 and bit-reproducible: wrapped x = x - L floor(x / L) with
-// one rounding per operation, cell = floor(x nc / L) clamped to [0, nc-1].
-// Inside a cell, beads are ordered by (class, index) with class 0 = image,
-// 1 = charged real, 2 = neutral real, so that the pair kernel finds the
-// electrostatic beads (images + charged) and the Gaussian-core beads
-// (charged + neutral reals) as two contiguous ranges.
+// cells.cu -- K1/K2 per-phase kernels: wrap + bin, scan, scatter and the
+// per-cell stable order (bodies in cells.cuh).
+#include "cells.cuh"
 #include "kernels.h"
 
 namespace gcme {
 
-__global__ void k_bin(Pool P) {
-  long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (g >= P.n_ext) return;
-  int s = P.ext_sys[g];
-  const SysDesc &S = P.sys[s];
-  int e = (int)(g - S.ext_off);
-  double x[3];
-  ext_position(P, S, e, x[0], x[1], x[2]);
-  double q = ext_charge(P, S, e);
-  double w[3];
-  int c[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    w[a] = wrap_coord(x[a], S.box[a]);
-    int k = (int)floor(__dmul_rn(w[a], S.inv_cell[a]));
-    k = k > S.nc[a] - 1 ? S.nc[a] - 1 : k;
-    k = k < 0 ? 0 : k;
-    c[a] = k;
-  }
-  int cell = c[0] + S.nc[0] * (c[1] + S.nc[1] * c[2]);
-  P.xyzq_u[g] = make_float4(__double2float_rn(w[0]), __double2float_rn(w[1]),
-                            __double2float_rn(w[2]), (float)q);
-  if (P.xyzq_u64) P.xyzq_u64[g] = make_dpos4(w[0], w[1], w[2], q);
-  P.cell_of[g] = cell;
-  P.slot[g] = atomicAdd(&P.cell_cnt[S.cell_off + cell], 1);
-}
+__global__ void k_bin(Pool P) { dev_bin(P, blockIdx.x * (long long)blockDim.x + threadIdx.x); }
 
-// Exclusive scan of the cell counts of all systems (single CTA of 1024).
 __global__ void __launch_bounds__(1024) k_scan(const int *cnt, int *start, long long n) {
   __shared__ long long warp_tot[32];
-  const int T = blockDim.x;
-  long long chunk = (n + T - 1) / T;
-  long long b = threadIdx.x * chunk;
-  long long e = b + chunk < n ? b + chunk : n;
-  long long loc = 0;
-  for (long long i = b; i < e; ++i) loc += cnt[i];
-  // block exclusive scan of loc
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  long long v = loc;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    long long t = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += t;
-  }
-  if (lane == 31) warp_tot[wid] = v;
-  __syncthreads();
-  if (wid == 0) {
-    long long t = lane < (T >> 5) ? warp_tot[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      long long u = __shfl_up_sync(0xffffffffu, t, o);
-      if (lane >= o) t += u;
-    }
-    warp_tot[lane] = t;  // inclusive
-  }
-  __syncthreads();
-  long long off = v - loc + (wid > 0 ? warp_tot[wid - 1] : 0);
-  for (long long i = b; i < e; ++i) {
-    start[i] = (int)off;
-    off += cnt[i];
-  }
-  if (threadIdx.x == T - 1) start[n] = (int)off;
+  dev_scan_block(cnt, start, n, warp_tot);
 }
 
 __global__ void k_scatter(Pool P) {
-  long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (g >= P.n_ext) return;
-  const SysDesc &S = P.sys[P.ext_sys[g]];
-  int e = (int)(g - S.ext_off);
-  P.sorted_idx[P.cell_start[S.cell_off + P.cell_of[g]] + P.slot[g]] = e;
+  dev_scatter(P, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
-
-// One CTA per cell: stable (class, index) order of the cell's beads and the
-// gather of their wrapped positions into sorted order.
-constexpr int kSortCap = 1024;
 
 __global__ void __launch_bounds__(256) k_cellsort(Pool P) {
   __shared__ long long key[kSortCap];
-  __shared__ int n_img, n_q;
-  long long cg = blockIdx.x;
-  if (cg >= P.n_cells) return;
-  const SysDesc &S = P.sys[P.cell_sys[cg]];
-  int beg = P.cell_start[cg], end = P.cell_start[cg + 1];
-  int cnt = end - beg;
-  if (threadIdx.x == 0) {
-    n_img = 0;
-    n_q = 0;
-  }
-  __syncthreads();
-  bool in_smem = cnt <= kSortCap;
-  // keys: class in the high word, local ext index in the low word
-  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-    int e = P.sorted_idx[beg + t];
-    int cls;
-    if (e >= S.n) cls = 0;
-    else cls = P.xyzq_u[S.ext_off + e].w != 0.0f ? 1 : 2;
-    long long k = ((long long)cls << 32) | (unsigned)e;
-    if (in_smem) key[t] = k;
-    if (cls == 0) atomicAdd(&n_img, 1);
-    if (cls <= 1) atomicAdd(&n_q, 1);
-  }
-  __syncthreads();
-  if (!in_smem) {
-    // Oversized cell: rank against global memory, park the order in
-    // sort_tmp, then move it into place after every rank is known.
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-      int e = P.sorted_idx[beg + t];
-      int cls = e >= S.n ? 0 : (P.xyzq_u[S.ext_off + e].w != 0.0f ? 1 : 2);
-      long long k = ((long long)cls << 32) | (unsigned)e;
-      int rank = 0;
-      for (int u = 0; u < cnt; ++u) {
-        int f = P.sorted_idx[beg + u];
-        int cf = f >= S.n ? 0 : (P.xyzq_u[S.ext_off + f].w != 0.0f ? 1 : 2);
-        rank += (((long long)cf << 32) | (unsigned)f) < k;
-      }
-      P.sort_tmp[beg + rank] = e;
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-      int e = P.sort_tmp[beg + t];
-      P.sorted_idx[beg + t] = e;
-      P.xyzq_s[beg + t] = P.xyzq_u[S.ext_off + e];
-      if (P.xyzq_s64) P.xyzq_s64[beg + t] = P.xyzq_u64[S.ext_off + e];
-    }
-    if (threadIdx.x == 0) {
-      P.cell_nimg[cg] = n_img;
-      P.cell_nq[cg] = n_q;
-    }
-    return;
-  }
-  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-    long long k = key[t];
-    int rank = 0;
-    for (int u = 0; u < cnt; ++u) rank += key[u] < k;
-    int e = (int)(k & 0xffffffffLL);
-    long long dst = beg + rank;
-    P.sorted_idx[dst] = e;
-    P.xyzq_s[dst] = P.xyzq_u[S.ext_off + e];
-    if (P.xyzq_s64) P.xyzq_s64[dst] = P.xyzq_u64[S.ext_off + e];
-  }
-  if (threadIdx.x == 0) {
-    P.cell_nimg[cg] = n_img;
-    P.cell_nq[cg] = n_q;
-  }
+  __shared__ int cnt2[2];
+  if (blockIdx.x >= P.n_cells) return;
+  dev_cellsort_block(P, blockIdx.x, key, cnt2);
 }
 
 void launch_cells(const Pool &P, cudaStream_t st) {

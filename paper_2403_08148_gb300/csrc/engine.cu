@@ -359,6 +359,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   cv.add(&P.energy, (long long)ns * GCME_NTERMS);
   cv.add(&P.virial, (long long)ns * 9);
   cv.add(&pair_work, n_pair_work);
+  cv.add(&bar_words, 4);
   int2 *fw[3];
   for (int a = 0; a < 3; ++a) cv.add(&fw[a], plan.nwork[a]);
   scratch_bytes = cv.off;
@@ -873,6 +874,32 @@ int gcme_batch_phase_ms(gcme_batch *b, float *h_ms, int32_t nphase, int32_t *ker
   return phase_ms(b->eng, h_ms, nphase, kernels);
 }
 
+// Four barrier words for the timeout probe (no allocation needed).
+static __device__ unsigned int g_probe_words[4];
+
+int gcme_debug_barrier_timeout(gcme_ctx *ctx, double timeout_s, gcme_stream_t stream) {
+  if (!ctx || !(timeout_s > 0) || timeout_s > 10.0) {
+    set_error("invalid argument to gcme_debug_barrier_timeout");
+    return GCME_ERR_INVALID;
+  }
+  GCME_TRY_CK(cudaSetDevice(ctx->device));
+  unsigned int *w = nullptr;
+  GCME_TRY_CK(cudaGetSymbolAddress((void **)&w, g_probe_words));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (launch_barrier_probe(w, timeout_s, st) != 0) {
+    set_error(std::string("probe launch failed: ") + cudaGetErrorString(cudaGetLastError()));
+    return GCME_ERR_CUDA;
+  }
+  unsigned int words[4];
+  GCME_TRY_CK(cudaMemcpyAsync(words, w, sizeof(words), cudaMemcpyDeviceToHost, st));
+  GCME_TRY_CK(cudaStreamSynchronize(st));
+  if (words[2] != 0) {
+    set_error("grid barrier wait ran out");
+    return GCME_ERR_TIMEOUT;
+  }
+  return GCME_OK;
+}
+
 int gcme_debug_pairs(gcme_sys *sys, const double *d_pos, int32_t *d_triples, int64_t cap,
                      int64_t *d_count, gcme_stream_t stream) {
   if (!sys || !d_pos || !d_count || cap < 0 || (cap > 0 && !d_triples)) {
@@ -1021,13 +1048,37 @@ int gcme_batch_step(gcme_batch *b, int64_t nsteps, int32_t mode, gcme_stream_t s
   cudaGraphExec_t fg, sg;
   int rc = b->eng.forces_graph(Q, &fg);
   if (rc) return rc;
-  rc = b->eng.step_graph(Q, &sg);
-  if (rc) return rc;
+  if (mode == 0) {
+    rc = b->eng.step_graph(Q, &sg);
+    if (rc) return rc;
+  }
   if (!b->forces_valid) {
     GCME_TRY_CK(cudaGraphLaunch(fg, st));
     b->forces_valid = true;
   }
-  for (int64_t k = 0; k < nsteps; ++k) GCME_TRY_CK(cudaGraphLaunch(sg, st));
+  if (mode == 0) {
+    for (int64_t k = 0; k < nsteps; ++k) GCME_TRY_CK(cudaGraphLaunch(sg, st));
+    return check_launch("gcme_batch_step");
+  }
+  if (b->eng.fp64) {
+    set_error("the persistent launch (mode 1) runs FP32 batches");
+    return GCME_ERR_INVALID;
+  }
+  if (nsteps == 0) return GCME_OK;
+  int lr = launch_persistent(Q, b->eng.pair_work, b->eng.n_pair_work, b->eng.plan, nsteps,
+                             b->eng.bar_words, 2.0, st);
+  if (lr != 0) {
+    cudaError_t e = cudaGetLastError();
+    set_error(std::string("persistent cooperative launch failed: ") + cudaGetErrorString(e));
+    return GCME_ERR_CUDA;
+  }
+  unsigned int words[4] = {0, 0, 0, 0};
+  GCME_TRY_CK(cudaMemcpyAsync(words, b->eng.bar_words, sizeof(words), cudaMemcpyDeviceToHost, st));
+  GCME_TRY_CK(cudaStreamSynchronize(st));
+  if (words[2] != 0) {
+    set_error("persistent launch: a grid barrier wait ran out (2 s)");
+    return GCME_ERR_TIMEOUT;
+  }
   return check_launch("gcme_batch_step");
 }
 

@@ -46,6 +46,7 @@ class Engine {
   static constexpr int kNPhaseEv = 7;
   cudaEvent_t phase_ev[kNPhaseEv] = {};
   int step_kernels = 0;  // kernel nodes in the step graph
+  unsigned int *bar_words = nullptr;  // persistent-launch barrier state (4 words)
   bool fp64 = false;
   int device = 0;
   std::vector<SysDesc> hsys;

@@ -23,6 +23,12 @@ void launch_slab_apply(const Pool &P, cudaStream_t st);         // Yeh-Berkowitz
 void launch_finalize(const Pool &P, bool vir, cudaStream_t st); // energies -> FP64
 void launch_kick_drift(const Pool &P, bool vel64, cudaStream_t st);
 void launch_kick(const Pool &P, bool vel64, cudaStream_t st);
+// one cooperative launch of nsteps steps of the whole batch (FP32); the
+// four words at bar_words hold the barrier state and the error word
+int launch_persistent(const Pool &P, const int2 *pair_work, int n_pair_work, const PmePlan &pl,
+                      long long nsteps, unsigned int *bar_words, double timeout_s,
+                      cudaStream_t st);
+int launch_barrier_probe(unsigned int *bar_words, double timeout_s, cudaStream_t st);
 void launch_force_to_f64(const long long *f, double *out, long long n3, cudaStream_t st);
 
 }  // namespace gcme

@@ -1,0 +1,212 @@
+// misc.cuh -- K9-K12 device bodies: harmonic bonds, electrode walls, Yeh-Berkowitz slab
+// term, velocity Verlet and the FP64 energy/virial finalisation.
+#pragma once
+#include "common.cuh"
+
+
+namespace gcme {
+
+// Add v to the accumulator `slot` of system s from every lane of a warp.
+// Lanes of one warp may belong to different systems (bead-parallel kernels
+// over a batch): the warp reduces when all lanes agree, else each lane adds.
+__device__ __forceinline__ void sys_acc_add(const Pool &P, int s, bool act, int slot, double v) {
+  const unsigned full = 0xffffffffu;
+  const int s0 = __shfl_sync(full, s, 0);
+  const bool same = __all_sync(full, s == s0);
+  if (same) {
+    double t = warp_sum(act ? v : 0.0);
+    if ((threadIdx.x & 31) == 0 && s0 >= 0)
+      atomic_add_fixed(P.acc + (long long)s0 * kNacc + slot, t, kEScale);
+  } else if (act && v != 0.0) {
+    atomic_add_fixed(P.acc + (long long)s * kNacc + slot, v, kEScale);
+  }
+}
+
+__device__ __forceinline__ void sys_vir_add(const Pool &P, int s, bool act, const double W[9]) {
+  const unsigned full = 0xffffffffu;
+  const int s0 = __shfl_sync(full, s, 0);
+  const bool same = __all_sync(full, s == s0);
+  for (int k = 0; k < 9; ++k) {
+    if (same) {
+      double t = warp_sum(act ? W[k] : 0.0);
+      if ((threadIdx.x & 31) == 0 && s0 >= 0)
+        atomic_add_fixed(P.vacc + (long long)s0 * 9 + k, t, kEScale);
+    } else if (act) {
+      atomic_add_fixed(P.vacc + (long long)s * 9 + k, W[k], kEScale);
+    }
+  }
+}
+
+// Harmonic bond u = k/2 (r - r0)^2 on the minimum-image separation (periodic
+// axes only: x, y, z in bulk, x, y in slabs).  FP32 arithmetic on the FP64
+// difference (FP64 throughout for FP64 systems).
+template <bool VIR>
+__device__ __forceinline__ void dev_bonds(const Pool &P, long long b) {
+  const bool act = b < P.n_bond;
+  int s = -1;
+  double E = 0.0;
+  double W[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (act) {
+    s = P.bond_sys[b];
+    const SysDesc &S = P.sys[s];
+    const int2 ij = P.bonds[b];
+    const double *pi = P.pos + 3 * (S.bead_off + ij.x);
+    const double *pj = P.pos + 3 * (S.bead_off + ij.y);
+    const bool per[3] = {true, true, S.geometry == GCME_BULK};
+    double d[3];
+    double fs;
+    if (S.precision == GCME_FP64) {
+      for (int a = 0; a < 3; ++a) {
+        d[a] = pj[a] - pi[a];
+        if (per[a]) d[a] -= S.box[a] * rint(d[a] / S.box[a]);
+      }
+      const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      fs = S.bond_k * (r - S.bond_r0) / r;
+      E = 0.5 * S.bond_k * (r - S.bond_r0) * (r - S.bond_r0);
+    } else {
+      float df[3];
+      for (int a = 0; a < 3; ++a) {
+        df[a] = (float)(pj[a] - pi[a]);
+        if (per[a]) df[a] -= S.boxf[a] * rintf(df[a] / S.boxf[a]);
+        d[a] = df[a];
+      }
+      const float r = sqrtf(df[0] * df[0] + df[1] * df[1] + df[2] * df[2]);
+      const float kf = (float)S.bond_k, r0 = (float)S.bond_r0;
+      fs = (double)(kf * (r - r0) / r);
+      E = (double)(0.5f * kf * (r - r0) * (r - r0));
+    }
+    for (int a = 0; a < 3; ++a) {
+      atomic_add_fixed(force_ptr(P, S, ij.x, a), fs * d[a], kFScale);
+      atomic_add_fixed(force_ptr(P, S, ij.y, a), -fs * d[a], kFScale);
+    }
+    if (VIR)
+      for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) W[3 * a + c] = -fs * d[a] * d[c];
+  }
+  sys_acc_add(P, s, act, ACC_BOND, E);
+  if (VIR) sys_vir_add(P, s, act, W);
+}
+
+// Electrode walls at z = 0 and z = H (continuum Gaussian-core layer)
+//   u_w(h) = (A n_s) (3 / (2 pi s_w))^{1/2} exp(-3 h^2 / (2 s_w))
+// and the slab dipole M_z = sum z_i z_pos,i for the Yeh-Berkowitz term.
+__device__ __forceinline__ void dev_walls(const Pool &P, long long g) {
+  bool act = g < P.n_real;
+  int s = -1;
+  double Ew = 0.0, Mz = 0.0;
+  bool slab = false, nm = false;
+  if (act) {
+    s = P.real_sys[g];
+    const SysDesc &S = P.sys[s];
+    slab = S.geometry != GCME_BULK;
+    nm = S.geometry == GCME_SLAB_NONMETAL;
+    if (slab) {
+      const int i = (int)(g - S.bead_off);
+      const double z = P.pos[3 * g + 2];
+      if (S.wall_A != 0.0) {
+        const double c = S.wall_A * sqrt(3.0 / (2.0 * 3.14159265358979323846 * S.wall_s2));
+        const double h1 = S.H - z;
+        if (S.precision == GCME_FP64) {
+          const double u0 = c * exp(-1.5 * z * z / S.wall_s2);
+          const double u1 = c * exp(-1.5 * h1 * h1 / S.wall_s2);
+          Ew = u0 + u1;
+          const double fz = 3.0 * z / S.wall_s2 * u0 - 3.0 * h1 / S.wall_s2 * u1;
+          atomic_add_fixed(force_ptr(P, S, i, 2), fz, kFScale);
+        } else {
+          const float zf = (float)z, h1f = (float)h1, s2 = (float)S.wall_s2, cf = (float)c;
+          const float u0 = cf * expf(-1.5f * zf * zf / s2);
+          const float u1 = cf * expf(-1.5f * h1f * h1f / s2);
+          Ew = (double)(u0 + u1);
+          const float fz = 3.0f * zf / s2 * u0 - 3.0f * h1f / s2 * u1;
+          atomic_add_fixed_f(force_ptr(P, S, i, 2), fz, (float)kFScale);
+        }
+      }
+      if (nm) Mz = P.q[g] * z;
+    }
+  }
+  sys_acc_add(P, s, act && slab, ACC_WALL, Ew);
+  sys_acc_add(P, s, act && nm, ACC_MZ, Mz);
+}
+
+// Yeh-Berkowitz force F_z,i = -4 pi lB z_i M_z / V (nonmetal slabs).
+__device__ __forceinline__ void dev_slab_apply(const Pool &P, long long g) {
+  if (g >= P.n_real) return;
+  const int s = P.real_sys[g];
+  const SysDesc &S = P.sys[s];
+  if (S.geometry != GCME_SLAB_NONMETAL) return;
+  const double Mz = (double)(long long)P.acc[(long long)s * kNacc + ACC_MZ] / kEScale;
+  const double fz = -4.0 * 3.14159265358979323846 * S.lB * P.q[g] * Mz / S.V;
+  unsigned long long *f = force_ptr(P, S, (int)(g - S.bead_off), 2);
+  *f += (unsigned long long)__double2ll_rn(fz * kFScale);
+}
+
+// Per-system energies (FP64) from the fixed-point accumulators.
+template <bool VIR>
+__device__ __forceinline__ void dev_finalize(const Pool &P, int s) {
+  if (s >= P.nsys) return;
+  const SysDesc &S = P.sys[s];
+  const unsigned long long *a = P.acc + (long long)s * kNacc;
+  auto rd = [&](int k) { return (double)(long long)a[k] / kEScale; };
+  double *E = P.energy + (long long)s * GCME_NTERMS;
+  E[GCME_E_GC] = rd(ACC_GC);
+  E[GCME_E_REAL] = rd(ACC_REAL);
+  E[GCME_E_RECIP] = rd(ACC_RECIP);
+  E[GCME_E_CORR] = S.e_corr;
+  E[GCME_E_SELF] = S.e_self;
+  double slab = 0.0;
+  if (S.geometry == GCME_SLAB_NONMETAL) {
+    const double Mz = rd(ACC_MZ);
+    slab = 2.0 * 3.14159265358979323846 * S.lB * Mz * Mz / S.V;
+  }
+  E[GCME_E_SLAB] = slab;
+  E[GCME_E_WALL] = rd(ACC_WALL);
+  E[GCME_E_BOND] = rd(ACC_BOND);
+  double pot = 0.0;
+  for (int k = 0; k < 8; ++k) pot += E[k];
+  E[GCME_E_POTENTIAL] = pot;
+  E[GCME_E_KINETIC] = rd(ACC_KIN);
+  if (VIR)
+    for (int k = 0; k < 9; ++k)
+      P.virial[(long long)s * 9 + k] = (double)(long long)P.vacc[(long long)s * 9 + k] / kEScale;
+}
+
+// Velocity Verlet, unit masses: v += dt/2 F; x += dt v (FP64 positions).
+template <typename V>
+__device__ __forceinline__ void dev_kick_drift(const Pool &P, long long g) {
+  if (g >= P.n_real) return;
+  const SysDesc &S = P.sys[P.real_sys[g]];
+  V *vel = reinterpret_cast<V *>(P.vel) + 3 * g;
+  const int i = (int)(g - S.bead_off);
+  const V h = V(0.5 * S.dt);
+  for (int a = 0; a < 3; ++a) {
+    const long long fq = *reinterpret_cast<const long long *>(force_ptr(P, S, i, a));
+    const V f = V((double)fq * (1.0 / kFScale));
+    V v = vel[a] + h * f;
+    vel[a] = v;
+    P.pos[3 * g + a] += S.dt * (double)v;
+  }
+}
+
+template <typename V>
+__device__ __forceinline__ void dev_kick(const Pool &P, long long g) {
+  const bool act = g < P.n_real;
+  int s = -1;
+  double ke = 0.0;
+  if (act) {
+    s = P.real_sys[g];
+    const SysDesc &S = P.sys[s];
+    V *vel = reinterpret_cast<V *>(P.vel) + 3 * g;
+    const int i = (int)(g - S.bead_off);
+    const V h = V(0.5 * S.dt);
+    for (int a = 0; a < 3; ++a) {
+      const long long fq = *reinterpret_cast<const long long *>(force_ptr(P, S, i, a));
+      const V f = V((double)fq * (1.0 / kFScale));
+      V v = vel[a] + h * f;
+      vel[a] = v;
+      ke += 0.5 * (double)v * (double)v;
+    }
+  }
+  sys_acc_add(P, s, act, ACC_KIN, ke);
+}
+
+}  // namespace gcme

@@ -1,0 +1,290 @@
+// pair.cuh -- K3 device bodies: Gaussian core + real-space smeared Coulomb over cell pairs.
+//
+// For every ordered in-cutoff triple (i, j, image n) with i a real bead:
+//   Gaussian core (Eq. u_ex), both beads real:
+//     u = A (3/(2 pi s))^{3/2} exp(-3 r^2/(2 s)),  F_i = -(3/s) u d
+//   real-space electrostatics (Eq. ewald, real part), both charged:
+//     u = lB z_i z_j g(r),  g = [erfc(kappa r) - erfc(beta r)] / r
+//     F_i = -lB z_i z_j h(r) d,  h = -g'(r)/r
+// with d = r_j + n L - r_i.  Each bead i sums over all j (full shell), so
+// every unordered pair is visited from both ends and energies are halved.
+// Image beads (conducting-slab geometry) appear only as j; visiting the
+// real-image pairs from the real side only yields exactly the physical
+// energy E_rr + E_ri / 2.
+//
+// In-cutoff rule (bit-exact with the oracle): on the wrapped FP32 positions
+//   d_a = fl(fl(x_j,a - x_i,a) + fl(n_a L_a)),
+//   r2 = fl(fl(fl(d_x^2) + fl(d_y^2)) + fl(d_z^2)),  in iff r2 < fl(rc^2).
+//
+// FP32 path: one CTA of 128 threads per (home cell, z-offset) work item.
+// The 9 neighbour cells of that z-slab are staged in shared memory as
+// float4 (x, y, z, q) and every thread (one home bead) streams over them;
+// within a cell the images, charged and neutral beads are contiguous, so
+// the core and electrostatic loops run over fixed ranges without per-pair
+// class tests.  Forces are summed in FP32 per thread, then added to the
+// 64-bit fixed-point accumulators; energies are reduced per warp in FP64.
+#pragma once
+#include "common.cuh"
+
+
+namespace gcme {
+
+constexpr int kPairThreads = 128;
+constexpr int kPairCap = 2048;  // staged j beads per work item
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kTwoOverSqrtPi = 1.1283791670955126f;
+
+struct PairAcc {
+  float eg, ere;
+  float gx, gy, gz;
+  float fx, fy, fz;
+  float wg[6], we[6];
+};
+
+struct PairSeg {
+  int beg, n, a, b;  // global sorted begin, count, end of images, end of charged
+  int soff;          // offset in shared memory
+  int code;          // image code (nx+1) + 3 (ny+1) + 9 (nz+1)
+  float sh[3];
+  int self;
+  int shifted;
+};
+
+template <bool GC, bool ELEC, bool SHIFT, bool SELF, bool VIR, bool DBG>
+__device__ __forceinline__ void pair_range(const float4 *__restrict__ J, int t0, int t1,
+                                           int jsorted0, const float4 &xi, int isorted,
+                                           const PairSeg &sg, const SysDesc &S, float rc2,
+                                           float gcc, PairAcc &A, const Pool &P, int s) {
+  for (int t = t0; t < t1; ++t) {
+    const float4 xj = J[t];
+    float dx = __fsub_rn(xj.x, xi.x);
+    float dy = __fsub_rn(xj.y, xi.y);
+    float dz = __fsub_rn(xj.z, xi.z);
+    if (SHIFT) {
+      dx = __fadd_rn(dx, sg.sh[0]);
+      dy = __fadd_rn(dy, sg.sh[1]);
+      dz = __fadd_rn(dz, sg.sh[2]);
+    }
+    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    bool in = r2 < rc2;
+    if (SELF) in = in && (jsorted0 + t != isorted);
+    if (GC) {
+      float e = ex2_approx(r2 * gcc);
+      e = in ? e : 0.0f;
+      A.eg += e;
+      A.gx = fmaf(e, dx, A.gx);
+      A.gy = fmaf(e, dy, A.gy);
+      A.gz = fmaf(e, dz, A.gz);
+      if (VIR) {
+        float ex = e * dx, ey = e * dy;
+        A.wg[0] = fmaf(ex, dx, A.wg[0]);
+        A.wg[1] = fmaf(ey, dy, A.wg[1]);
+        A.wg[2] = fmaf(e * dz, dz, A.wg[2]);
+        A.wg[3] = fmaf(ex, dy, A.wg[3]);
+        A.wg[4] = fmaf(ex, dz, A.wg[4]);
+        A.wg[5] = fmaf(ey, dz, A.wg[5]);
+      }
+    }
+    if (ELEC) {
+      const float qq = xi.w * xj.w;
+      if (in && qq != 0.0f) {
+        float g, h;
+        if (r2 < 1e-2f) {
+          g = S.ser_gf[0] + r2 * (S.ser_gf[1] + r2 * (S.ser_gf[2] + r2 * S.ser_gf[3]));
+          h = S.ser_hf[0] + r2 * (S.ser_hf[1] + r2 * S.ser_hf[2]);
+        } else {
+          const float r = sqrtf(r2);
+          const float rinv = 1.0f / r;
+          const float xb = S.betaf * r, xk = S.kappaf * r;
+          g = (erfcf(xk) - erfcf(xb)) * rinv;
+          const float eb = ex2_approx(-xb * xb * kLog2e);
+          const float ek = ex2_approx(-xk * xk * kLog2e);
+          const float dd = kTwoOverSqrtPi * (S.betaf * eb - S.kappaf * ek);
+          h = (g - dd) * (rinv * rinv);
+        }
+        A.ere = fmaf(qq, g, A.ere);
+        const float fq = qq * h;
+        A.fx = fmaf(fq, dx, A.fx);
+        A.fy = fmaf(fq, dy, A.fy);
+        A.fz = fmaf(fq, dz, A.fz);
+        if (VIR) {
+          float ex = fq * dx, ey = fq * dy;
+          A.we[0] = fmaf(ex, dx, A.we[0]);
+          A.we[1] = fmaf(ey, dy, A.we[1]);
+          A.we[2] = fmaf(fq * dz, dz, A.we[2]);
+          A.we[3] = fmaf(ex, dy, A.we[3]);
+          A.we[4] = fmaf(ex, dz, A.we[4]);
+          A.we[5] = fmaf(ey, dz, A.we[5]);
+        }
+      }
+    }
+    if (DBG && in) {
+      unsigned long long k = atomicAdd(&P.acc[(long long)s * kNacc + ACC_NPAIR], 1ull);
+      if ((long long)k < P.dbg_cap) {
+        P.dbg_triples[3 * k + 0] = P.sorted_idx[isorted];
+        P.dbg_triples[3 * k + 1] = P.sorted_idx[jsorted0 + t];
+        P.dbg_triples[3 * k + 2] = sg.code;
+      }
+    }
+  }
+}
+
+// Process one staged segment (the bead ranges of one neighbour cell).
+template <bool VIR, bool DBG>
+__device__ __forceinline__ void pair_segment(const float4 *J, int t0, int t1, int jsorted0,
+                                             const PairSeg &sg, bool anyq, const float4 &xi,
+                                             int isorted, const SysDesc &S, float rc2, float gcc,
+                                             PairAcc &A, const Pool &P, int s) {
+  // [0, a): images (electrostatics only); [a, b): charged reals (both);
+  // [b, n): neutral reals (core only); ranges clipped to [t0, t1).
+  const int a0 = max(t0, min(t1, sg.a)), b0 = max(t0, min(t1, sg.b));
+#define GCME_RANGES(SHIFT, SELF)                                                                  \
+  if (anyq) {                                                                                     \
+    pair_range<false, true, SHIFT, SELF, VIR, DBG>(J, t0, a0, jsorted0, xi, isorted, sg, S, rc2, \
+                                                   gcc, A, P, s);                                 \
+    pair_range<true, true, SHIFT, SELF, VIR, DBG>(J, a0, b0, jsorted0, xi, isorted, sg, S, rc2,  \
+                                                  gcc, A, P, s);                                  \
+  } else {                                                                                        \
+    if (DBG)                                                                                      \
+      pair_range<false, false, SHIFT, SELF, VIR, DBG>(J, t0, a0, jsorted0, xi, isorted, sg, S,   \
+                                                      rc2, gcc, A, P, s);                         \
+    pair_range<true, false, SHIFT, SELF, VIR, DBG>(J, a0, b0, jsorted0, xi, isorted, sg, S, rc2, \
+                                                   gcc, A, P, s);                                 \
+  }                                                                                               \
+  pair_range<true, false, SHIFT, SELF, VIR, DBG>(J, b0, t1, jsorted0, xi, isorted, sg, S, rc2,   \
+                                                 gcc, A, P, s);
+  if (sg.self) {
+    GCME_RANGES(false, true)
+  } else if (sg.shifted) {
+    GCME_RANGES(true, false)
+  } else {
+    GCME_RANGES(false, false)
+  }
+#undef GCME_RANGES
+}
+
+// One (home cell, z-offset) work item by the whole CTA.  Shared memory:
+// sj[kPairCap], seg[9], s_total[1].  Ends with a barrier.
+template <bool VIR, bool DBG>
+__device__ __forceinline__ void dev_pair_f32_item(const Pool &P, const int2 *work, int w,
+                                                  float4 *sj, PairSeg *seg, int *s_total_p) {
+  const int tid = threadIdx.x;
+  int &s_total = *s_total_p;
+  const int s = work[w].x;
+  const int code = work[w].y;
+  const SysDesc &S = P.sys[s];
+  const int cloc = code / 3;
+  const int dzo = code % 3 - 1;
+  const int nc0 = S.nc[0], nc1 = S.nc[1], nc2 = S.nc[2];
+  const int cx = cloc % nc0, cy = (cloc / nc0) % nc1, cz = cloc / (nc0 * nc1);
+  const long long hg = S.cell_off + cloc;
+  const int hbeg = P.cell_start[hg], hend = P.cell_start[hg + 1];
+  const int himg = P.cell_nimg[hg];
+  if (tid < 9) {
+    const int dxo = tid % 3 - 1, dyo = tid / 3 - 1;
+    const int u[3] = {cx + dxo, cy + dyo, cz + dzo};
+    const int ncv[3] = {nc0, nc1, nc2};
+    int v[3], nn[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      nn[a] = floor_div(u[a], ncv[a]);
+      v[a] = u[a] - nn[a] * ncv[a];
+    }
+    const long long cg = S.cell_off + v[0] + nc0 * (v[1] + nc1 * v[2]);
+    PairSeg g;
+    g.beg = P.cell_start[cg];
+    g.n = P.cell_start[cg + 1] - g.beg;
+    g.a = P.cell_nimg[cg];
+    g.b = P.cell_nq[cg];
+    g.code = (nn[0] + 1) + 3 * (nn[1] + 1) + 9 * (nn[2] + 1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) g.sh[a] = (float)nn[a] * S.boxf[a];
+    g.self = (dxo == 0 && dyo == 0 && dzo == 0);
+    g.shifted = (nn[0] != 0 || nn[1] != 0 || nn[2] != 0);
+    g.soff = 0;
+    seg[tid] = g;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int off = 0;
+    for (int k = 0; k < 9; ++k) {
+      seg[k].soff = off;
+      off += seg[k].n;
+    }
+    s_total = off;
+  }
+  __syncthreads();
+  const bool fits = s_total <= kPairCap;
+  if (fits) {
+    for (int k = 0; k < 9; ++k) {
+      const PairSeg &g = seg[k];
+      for (int t = tid; t < g.n; t += blockDim.x) sj[g.soff + t] = P.xyzq_s[g.beg + t];
+    }
+    __syncthreads();
+  }
+  const float rc2 = S.rc2f;
+  const float gcc = S.gc_c2f;
+  for (int ib = hbeg + himg; ib < hend; ib += blockDim.x) {
+    const int i = ib + tid;
+    const bool valid = i < hend;
+    float4 xi = valid ? P.xyzq_s[i] : make_float4(1e30f, 1e30f, 1e30f, 0.0f);
+    PairAcc A;
+    A.eg = A.ere = A.gx = A.gy = A.gz = A.fx = A.fy = A.fz = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) A.wg[k] = A.we[k] = 0.0f;
+    const bool anyq = __syncthreads_or(valid && xi.w != 0.0f);
+    if (fits) {
+      for (int k = 0; k < 9; ++k) {
+        const PairSeg g = seg[k];
+        pair_segment<VIR, DBG>(sj + g.soff, 0, g.n, g.beg, g, anyq, xi, i, S, rc2, gcc, A, P, s);
+      }
+    } else {
+      for (int k = 0; k < 9; ++k) {
+        const PairSeg g = seg[k];
+        for (int c0 = 0; c0 < g.n; c0 += kPairCap) {
+          const int c1 = min(g.n, c0 + kPairCap);
+          __syncthreads();
+          for (int t = c0 + tid; t < c1; t += blockDim.x) sj[t - c0] = P.xyzq_s[g.beg + t];
+          __syncthreads();
+          // ranges are in segment coordinates; shift the staged base
+          pair_segment<VIR, DBG>(sj - c0, c0, c1, g.beg, g, anyq, xi, i, S, rc2, gcc, A, P, s);
+        }
+      }
+    }
+    // --- write back ---
+    const float cg = (float)(S.gc_fc * S.gc_pref);
+    const float lb = (float)S.lB;
+    if (valid) {
+      const int orig = P.sorted_idx[i];
+      const float Fx = -(cg * A.gx + lb * A.fx);
+      const float Fy = -(cg * A.gy + lb * A.fy);
+      const float Fz = -(cg * A.gz + lb * A.fz);
+      atomic_add_fixed_f(force_ptr(P, S, orig, 0), Fx, (float)kFScale);
+      atomic_add_fixed_f(force_ptr(P, S, orig, 1), Fy, (float)kFScale);
+      atomic_add_fixed_f(force_ptr(P, S, orig, 2), Fz, (float)kFScale);
+    }
+    double eg = valid ? 0.5 * S.gc_pref * (double)A.eg : 0.0;
+    double er = valid ? 0.5 * S.lB * (double)A.ere : 0.0;
+    eg = warp_sum(eg);
+    er = warp_sum(er);
+    unsigned long long *acc = P.acc + (long long)s * kNacc;
+    if ((tid & 31) == 0) {
+      atomic_add_fixed(acc + ACC_GC, eg, kEScale);
+      atomic_add_fixed(acc + ACC_REAL, er, kEScale);
+    }
+    if (VIR) {
+      // W_ab = 1/2 sum_visits fs d_a d_b  with fs = (3/s) u or lB qq h
+      const double c1 = 0.5 * S.gc_fc * S.gc_pref, c2 = 0.5 * S.lB;
+      const int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        double v = valid ? c1 * (double)A.wg[map[k]] + c2 * (double)A.we[map[k]] : 0.0;
+        v = warp_sum(v);
+        if ((tid & 31) == 0) atomic_add_fixed(P.vacc + (long long)s * 9 + k, v, kEScale);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace gcme

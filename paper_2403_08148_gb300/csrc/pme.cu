@@ -1,443 +1,21 @@
-// pme.cu -- K5-K8: smooth particle-mesh Ewald for the reciprocal term of
-// Eq. ewald (Essmann et al. 1995), orthorhombic boxes, order p B-splines.
-//
-//   u_a = K_a x_a / L_a
-//   Q(k) = sum_i z_i prod_a M_p(u_ia - k_a)            (spread, periodic wrap)
-//   E = 1/2 sum_{m != 0} B(m) C(m) |F(Q)(m)|^2,
-//   B = prod_a |b_a(m_a)|^2,  C = lB / (pi V) exp(-pi^2 m^2 / kappa^2) / m^2
-//   F_i = -sum_k dQ(k)/dr_i (theta * Q)(k),  theta * Q = F^{-1}[B C F(Q)]
-// with unnormalised forward and backward transforms.
-//
-// GB300 layout: the charge grid is accumulated in 64-bit fixed point
-// (order-independent, so the result is bit-reproducible), eight lanes per
-// charge (one per z-plane of the stencil).  The 3D FFT is a batched
-// mixed-radix (2, 3, 4, 5) Stockham transform along one axis per launch;
-// each CTA moves a tile of lines through shared memory with coalesced loads
-// (lines adjacent in x), the z pass fuses forward transform, influence
-// function (energy, virial) and backward transform.
+// pme.cu -- K5-K8 per-phase kernels (bodies in pme.cuh).
+#include "pme.cuh"
 #include "kernels.h"
 
 namespace gcme {
 
-template <typename R> struct PmeT;
-template <> struct PmeT<float> {
-  using R2 = float2;
-  static constexpr double qscale = kQScale32;
-};
-template <> struct PmeT<double> {
-  using R2 = double2;
-  static constexpr double qscale = kQScale64;
-};
+template <typename R>
+__global__ void k_spread(Pool P) { dev_spread<R>(P, blockIdx.x * (long long)blockDim.x + threadIdx.x); }
 
 template <typename R>
-__device__ __forceinline__ void load_pos(const Pool &P, long long g, R x[3], R &q);
-template <>
-__device__ __forceinline__ void load_pos<float>(const Pool &P, long long g, float x[3], float &q) {
-  float4 p = P.xyzq_u[g];
-  x[0] = p.x;
-  x[1] = p.y;
-  x[2] = p.z;
-  q = p.w;
-}
-template <>
-__device__ __forceinline__ void load_pos<double>(const Pool &P, long long g, double x[3], double &q) {
-  dpos4 p = P.xyzq_u64[g];
-  x[0] = p.x;
-  x[1] = p.y;
-  x[2] = p.z;
-  q = p.w;
-}
-
-// Cardinal B-spline weights W[t] = M_p(fr + t), t = 0..p-1, by the recursion
-// M_n(u) = [u M_{n-1}(u) + (n - u) M_{n-1}(u - 1)] / (n - 1) from
-// M_2(u) = 1 - |u - 1|; optionally dW[t] = M_{p-1}(fr+t) - M_{p-1}(fr+t-1).
-template <typename R>
-__device__ __forceinline__ void bspline_weights(int p, R fr, R *W, R *dW) {
-  W[0] = fr;
-  W[1] = R(1) - fr;
-  for (int n = 3; n <= p; ++n) {
-    if (n == p && dW) {
-      dW[0] = W[0];
-      for (int t = 1; t < n - 1; ++t) dW[t] = W[t] - W[t - 1];
-      dW[n - 1] = -W[n - 2];
-    }
-    const R div = R(1) / R(n - 1);
-    W[n - 1] = (R(1) - fr) * W[n - 2] * div;
-    for (int t = n - 2; t >= 1; --t) W[t] = ((fr + R(t)) * W[t] + (R(n) - fr - R(t)) * W[t - 1]) * div;
-    W[0] = fr * W[0] * div;
-  }
-  if (p == 2 && dW) {
-    dW[0] = R(1);
-    dW[1] = R(-1);
-  }
-}
-
-__device__ __forceinline__ int wrap_index(int k, int K) {
-  k %= K;
-  return k < 0 ? k + K : k;
-}
-
-template <typename R>
-__device__ __forceinline__ R kfac_of(const SysDesc &S, int a);
-template <>
-__device__ __forceinline__ float kfac_of<float>(const SysDesc &S, int a) {
-  return S.kfac[a];
-}
-template <>
-__device__ __forceinline__ double kfac_of<double>(const SysDesc &S, int a) {
-  return (double)S.K[a] / S.box[a];
-}
-
-// --------------------------------------------------------------------------
-// spread: eight lanes per charge, lane tz handles the stencil plane tz
-// --------------------------------------------------------------------------
-template <typename R>
-__global__ void k_spread(Pool P) {
-  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long c = g >> 3;
-  const int tz = (int)(g & 7);
-  if (c >= P.n_q) return;
-  const SysDesc &S = P.sys[P.q_sys[c]];
-  const int p = S.order;
-  if (tz >= p) return;
-  const int e = P.qlist[c];
-  R x[3], q;
-  load_pos<R>(P, S.ext_off + e, x, q);
-  R W[3][8];
-  int base[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    R u = x[a] * kfac_of<R>(S, a);
-    R fl = floor(u);
-    base[a] = (int)fl;
-    bspline_weights<R>(p, u - fl, W[a], (R *)nullptr);
-  }
-  const int K0 = S.K[0], K1 = S.K[1], K2 = S.K[2];
-  const int kz = wrap_index(base[2] - tz, K2);
-  const R wz = W[2][tz] * q * R(PmeT<R>::qscale);
-  unsigned long long *grid = P.qgrid + S.grid_off;
-  for (int ty = 0; ty < p; ++ty) {
-    const int ky = wrap_index(base[1] - ty, K1);
-    const R wyz = W[1][ty] * wz;
-    unsigned long long *row = grid + (long long)K0 * (ky + (long long)K1 * kz);
-    for (int tx = 0; tx < p; ++tx) {
-      const int kx = wrap_index(base[0] - tx, K0);
-      long long v = (long long)llrint(W[0][tx] * wyz);
-      atomicAdd(row + kx, (unsigned long long)v);
-    }
-  }
-}
-
-// --------------------------------------------------------------------------
-// gather: eight lanes per charged real bead, reduced with shuffles
-// --------------------------------------------------------------------------
-template <typename R>
-__global__ void k_gather(Pool P) {
-  using R2 = typename PmeT<R>::R2;
-  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long c = g >> 3;
-  const int tz = (int)(g & 7);
-  bool act = c < P.n_q;
-  const SysDesc *Sp = act ? &P.sys[P.q_sys[c]] : &P.sys[0];
-  const SysDesc &S = *Sp;
-  const int p = S.order;
-  int e = 0;
-  if (act) {
-    const long long loc = c - S.q_off;
-    act = loc < S.nq_real && tz < p;
-    e = P.qlist[c];
-  }
-  R gx = 0, gy = 0, gz = 0, q = 0;
-  if (act) {
-    R x[3];
-    load_pos<R>(P, S.ext_off + e, x, q);
-    R W[3][8], dW[3][8];
-    int base[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      R u = x[a] * kfac_of<R>(S, a);
-      R fl = floor(u);
-      base[a] = (int)fl;
-      bspline_weights<R>(p, u - fl, W[a], dW[a]);
-    }
-    const int K0 = S.K[0], K1 = S.K[1], K2 = S.K[2];
-    const int kz = wrap_index(base[2] - tz, K2);
-    const R2 *grid = (const R2 *)(sizeof(R) == 4 ? (const void *)P.cgrid : (const void *)P.cgrid64) +
-                     S.grid_off;
-    const R wz = W[2][tz], dwz = dW[2][tz];
-    for (int ty = 0; ty < p; ++ty) {
-      const int ky = wrap_index(base[1] - ty, K1);
-      const R2 *row = grid + (long long)K0 * (ky + (long long)K1 * kz);
-      R sx = 0, sy = 0, sz = 0;
-      for (int tx = 0; tx < p; ++tx) {
-        const R v = row[wrap_index(base[0] - tx, K0)].x;
-        sx += dW[0][tx] * v;
-        sy += W[0][tx] * v;
-      }
-      sz = sy;
-      gx += sx * W[1][ty] * wz;
-      gy += sy * dW[1][ty] * wz;
-      gz += sz * W[1][ty] * dwz;
-    }
-    gx *= kfac_of<R>(S, 0);
-    gy *= kfac_of<R>(S, 1);
-    gz *= kfac_of<R>(S, 2);
-  }
-#pragma unroll
-  for (int o = 1; o < 8; o <<= 1) {
-    gx += __shfl_xor_sync(0xffffffffu, gx, o);
-    gy += __shfl_xor_sync(0xffffffffu, gy, o);
-    gz += __shfl_xor_sync(0xffffffffu, gz, o);
-  }
-  if (act && tz == 0) {
-    atomic_add_fixed(force_ptr(P, S, e, 0), (double)(-q * gx), kFScale);
-    atomic_add_fixed(force_ptr(P, S, e, 1), (double)(-q * gy), kFScale);
-    atomic_add_fixed(force_ptr(P, S, e, 2), (double)(-q * gz), kFScale);
-  }
-}
-
-// --------------------------------------------------------------------------
-// batched mixed-radix Stockham FFT along one axis
-// --------------------------------------------------------------------------
-template <typename R2>
-__device__ __forceinline__ R2 cmul(R2 a, R2 b) {
-  R2 r;
-  r.x = a.x * b.x - a.y * b.y;
-  r.y = a.x * b.y + a.y * b.x;
-  return r;
-}
-template <typename R2>
-__device__ __forceinline__ R2 cadd(R2 a, R2 b) {
-  R2 r;
-  r.x = a.x + b.x;
-  r.y = a.y + b.y;
-  return r;
-}
-template <typename R2>
-__device__ __forceinline__ R2 csub(R2 a, R2 b) {
-  R2 r;
-  r.x = a.x - b.x;
-  r.y = a.y - b.y;
-  return r;
-}
-// multiply by -i (forward) or +i (inverse): sgn = -1 forward, +1 inverse
-template <typename R2>
-__device__ __forceinline__ R2 mul_i(R2 a, int sgn) {
-  R2 r;
-  if (sgn < 0) {
-    r.x = a.y;
-    r.y = -a.x;
-  } else {
-    r.x = -a.y;
-    r.y = a.x;
-  }
-  return r;
-}
-
-// Small DFTs b_q = sum_r v_r exp(sgn 2 pi i r q / R).
-template <typename R, typename R2>
-__device__ __forceinline__ void dft_small(R2 *v, int Rd, int sgn) {
-  if (Rd == 2) {
-    R2 a = v[0], b = v[1];
-    v[0] = cadd(a, b);
-    v[1] = csub(a, b);
-  } else if (Rd == 4) {
-    R2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
-    R2 b0 = cadd(v[1], v[3]), b1 = mul_i(csub(v[1], v[3]), sgn);
-    v[0] = cadd(a0, b0);
-    v[2] = csub(a0, b0);
-    v[1] = cadd(a1, b1);
-    v[3] = csub(a1, b1);
-  } else if (Rd == 3) {
-    const R c = R(-0.5), sn = R(0.86602540378443864676);
-    R2 t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
-    R2 m;
-    m.x = v[0].x + c * t1.x;
-    m.y = v[0].y + c * t1.y;
-    R2 u = mul_i(t2, sgn);  // sgn i t2
-    u.x *= sn;
-    u.y *= sn;
-    v[0] = cadd(v[0], t1);
-    v[1] = cadd(m, u);
-    v[2] = csub(m, u);
-  } else if (Rd == 5) {
-    const R c1 = R(0.30901699437494742410), c2 = R(-0.80901699437494742410);
-    const R s1 = R(0.95105651629515357212), s2 = R(0.58778525229247312917);
-    R2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
-    R2 t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
-    R2 a1, a2, b1, b2;
-    a1.x = v[0].x + c1 * t1.x + c2 * t2.x;
-    a1.y = v[0].y + c1 * t1.y + c2 * t2.y;
-    a2.x = v[0].x + c2 * t1.x + c1 * t2.x;
-    a2.y = v[0].y + c2 * t1.y + c1 * t2.y;
-    R2 s1v, s2v;
-    s1v.x = s1 * t3.x + s2 * t4.x;
-    s1v.y = s1 * t3.y + s2 * t4.y;
-    s2v.x = s2 * t3.x - s1 * t4.x;
-    s2v.y = s2 * t3.y - s1 * t4.y;
-    b1 = mul_i(s1v, sgn);
-    b2 = mul_i(s2v, sgn);
-    v[0] = cadd(v[0], cadd(t1, t2));
-    v[1] = cadd(a1, b1);
-    v[4] = csub(a1, b1);
-    v[2] = cadd(a2, b2);
-    v[3] = csub(a2, b2);
-  }
-}
-
-// index of element k of line l of a K0 x K1 x K2 grid along `axis`
-__device__ __forceinline__ long long line_elem(int axis, int K0, int K1, long long l, int k) {
-  if (axis == 0) return k + (long long)K0 * l;
-  if (axis == 1) return (l % K0) + (long long)K0 * (k + (long long)K1 * (l / K0));
-  return l + (long long)K0 * K1 * k;
-}
-
-enum { FFT_FWD_FROM_Q = 0, FFT_FWD = 1, FFT_FWD_INFL_INV = 2, FFT_INV = 3 };
+__global__ void k_gather(Pool P) { dev_gather<R>(P, blockIdx.x * (long long)blockDim.x + threadIdx.x); }
 
 template <typename R, bool VIR>
 __global__ void __launch_bounds__(256) k_fft(Pool P, const int2 *work, int nwork, int axis, int kind,
                                              int lpb) {
-  using R2 = typename PmeT<R>::R2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R2 *smem = reinterpret_cast<R2 *>(smem_raw);
-  R2 *cg_all = (R2 *)(sizeof(R) == 4 ? (void *)P.cgrid : (void *)P.cgrid64);
-  const R2 *tw_all = (const R2 *)(sizeof(R) == 4 ? (const void *)P.tw : (const void *)P.tw64);
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
-    const int s = work[w].x, tile = work[w].y;
-    const SysDesc &S = P.sys[s];
-    const int K0 = S.K[0], K1 = S.K[1], K2 = S.K[2];
-    const int K = S.K[axis];
-    const long long nlines = (long long)K0 * K1 * K2 / K;
-    const long long l0 = (long long)tile * lpb;
-    const int nl = (int)min((long long)lpb, nlines - l0);
-    R2 *grid = cg_all + S.grid_off;
-    R2 *bufA = smem, *bufB = smem + lpb * K;
-    // ---- load (line index fastest for strided axes: coalesced along x)
-    for (int t = tid; t < nl * K; t += nt) {
-      int li, k;
-      if (axis == 0) {
-        li = t / K;
-        k = t % K;
-      } else {
-        li = t % nl;
-        k = t / nl;
-      }
-      const long long gi = line_elem(axis, K0, K1, l0 + li, k);
-      R2 v;
-      if (kind == FFT_FWD_FROM_Q) {
-        const long long qv = (long long)P.qgrid[S.grid_off + gi];
-        v.x = (R)((double)qv * (1.0 / PmeT<R>::qscale));
-        v.y = R(0);
-      } else {
-        v = grid[gi];
-      }
-      bufA[li * K + k] = v;
-    }
-    __syncthreads();
-    const R2 *tw = tw_all + S.tw_off[axis];
-    // one or two passes of stages (forward, then backward for the fused z pass)
-    const int npass = (kind == FFT_FWD_INFL_INV) ? 2 : 1;
-    double e_loc = 0.0;
-    double v_loc[6] = {0, 0, 0, 0, 0, 0};
-    for (int pass = 0; pass < npass; ++pass) {
-      const int sgn = (kind == FFT_INV || pass == 1) ? +1 : -1;
-      int Ns = 1;
-      for (int st = 0; st < S.nstage[axis]; ++st) {
-        const int Rd = S.radix[axis][st];
-        const int T = K / Rd;
-        const int twstep = K / (Ns * Rd);
-        for (int t = tid; t < nl * T; t += nt) {
-          const int li = t / T, j = t % T;
-          const int k = j % Ns;
-          R2 v[5];
-          const R2 *in = bufA + li * K;
-          for (int r = 0; r < Rd; ++r) {
-            R2 x = in[j + r * T];
-            if (r > 0 && k > 0) {
-              R2 wv = tw[(k * r * twstep) % K];
-              if (sgn > 0) wv.y = -wv.y;
-              x = cmul(x, wv);
-            }
-            v[r] = x;
-          }
-          dft_small<R, R2>(v, Rd, sgn);
-          R2 *out = bufB + li * K;
-          const int od = (j / Ns) * Ns * Rd + k;
-          for (int q = 0; q < Rd; ++q) out[od + q * Ns] = v[q];
-        }
-        __syncthreads();
-        R2 *tmp = bufA;
-        bufA = bufB;
-        bufB = tmp;
-        Ns *= Rd;
-      }
-      if (kind == FFT_FWD_INFL_INV && pass == 0) {
-        // influence function B(m) C(m); energy and virial of the spectrum
-        const R *b0 = (const R *)(sizeof(R) == 4 ? (const void *)P.bsp : (const void *)P.bsp64) +
-                      S.bsp_off[0];
-        const R *b1 = (const R *)(sizeof(R) == 4 ? (const void *)P.bsp : (const void *)P.bsp64) +
-                      S.bsp_off[1];
-        const R *b2 = (const R *)(sizeof(R) == 4 ? (const void *)P.bsp : (const void *)P.bsp64) +
-                      S.bsp_off[2];
-        const R pi2k2 = R(9.8696044010893586188 / (S.kappa * S.kappa));
-        const R cpref = R(S.lB / (3.14159265358979323846 * S.V));
-        for (int t = tid; t < nl * K; t += nt) {
-          const int li = t / K, k = t % K;
-          const long long l = l0 + li;
-          const int i0 = (int)(l % K0), i1 = (int)(l / K0), i2 = k;
-          const int m0 = i0 < (K0 + 1) / 2 ? i0 : i0 - K0;
-          const int m1 = i1 < (K1 + 1) / 2 ? i1 : i1 - K1;
-          const int m2 = i2 < (K2 + 1) / 2 ? i2 : i2 - K2;
-          R2 &F = bufA[li * K + k];
-          if (m0 == 0 && m1 == 0 && m2 == 0) {
-            F.x = F.y = R(0);
-            continue;
-          }
-          const R mv0 = R(m0) / R(S.box[0]), mv1 = R(m1) / R(S.box[1]), mv2 = R(m2) / R(S.box[2]);
-          const R msq = mv0 * mv0 + mv1 * mv1 + mv2 * mv2;
-          const R BC = b0[i0] * b1[i1] * b2[i2] * cpref * exp(-pi2k2 * msq) / msq;
-          const double Em = 0.5 * (double)BC * ((double)F.x * F.x + (double)F.y * F.y);
-          e_loc += Em;
-          if (VIR) {
-            const double fac = 2.0 * (1.0 + (double)pi2k2 * msq) / (double)msq;
-            const double mv[3] = {mv0, mv1, mv2};
-            const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
-            for (int q = 0; q < 6; ++q)
-              v_loc[q] += Em * ((ia[q] == ib[q] ? 1.0 : 0.0) - fac * mv[ia[q]] * mv[ib[q]]);
-          }
-          F.x *= BC;
-          F.y *= BC;
-        }
-        __syncthreads();
-      }
-    }
-    // ---- store
-    for (int t = tid; t < nl * K; t += nt) {
-      int li, k;
-      if (axis == 0) {
-        li = t / K;
-        k = t % K;
-      } else {
-        li = t % nl;
-        k = t / nl;
-      }
-      grid[line_elem(axis, K0, K1, l0 + li, k)] = bufA[li * K + k];
-    }
-    if (kind == FFT_FWD_INFL_INV) {
-      const double sc = S.recip_scale;
-      double ev = warp_sum(e_loc * sc);
-      if ((tid & 31) == 0) atomic_add_fixed(P.acc + (long long)s * kNacc + ACC_RECIP, ev, kEScale);
-      if (VIR) {
-        const int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
-        for (int q = 0; q < 9; ++q) {
-          double vv = warp_sum(v_loc[map[q]] * sc);
-          if ((tid & 31) == 0) atomic_add_fixed(P.vacc + (long long)s * 9 + q, vv, kEScale);
-        }
-      }
-    }
-    __syncthreads();
-  }
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x)
+    dev_fft_item<R, VIR>(P, work, w, axis, kind, lpb, smem_raw);
 }
 
 void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStream_t st) {
