@@ -153,7 +153,7 @@ def pair_kernel_traffic():
 
 def kernel_sha():
     h = hashlib.sha256()
-    for f in ("pair.cu", "common.cuh"):
+    for f in ("pair.cu", "pair.cuh", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2403_08148_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

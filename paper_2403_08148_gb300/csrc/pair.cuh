@@ -18,10 +18,12 @@
 //
 // FP32 path: one CTA of 128 threads per (home cell, z-offset) work item.
 // The 9 neighbour cells of that z-slab are staged in shared memory as
-// float4 (x, y, z, q) and every thread (one home bead) streams over them;
-// within a cell the images, charged and neutral beads are contiguous, so
-// the core and electrostatic loops run over fixed ranges without per-pair
-// class tests.  Forces are summed in FP32 per thread, then added to the
+// float4 (x, y, z, q) and every thread (one home bead) streams over them.
+// Within a cell the images, charged and neutral beads are contiguous, so the
+// core loop runs over the real beads and the electrostatic loop over the
+// charged ones without per-pair class tests; the core is evaluated for every
+// candidate (masked), the electrostatics only for the hits of a 64-bit
+// in-cutoff mask.  Forces are summed in FP32 per thread, then added to the
 // 64-bit fixed-point accumulators; energies are reduced per warp in FP64.
 #pragma once
 #include "common.cuh"
@@ -50,73 +52,49 @@ struct PairSeg {
   int shifted;
 };
 
-template <bool GC, bool ELEC, bool SHIFT, bool SELF, bool VIR, bool DBG>
-__device__ __forceinline__ void pair_range(const float4 *__restrict__ J, int t0, int t1,
-                                           int jsorted0, const float4 &xi, int isorted,
-                                           const PairSeg &sg, const SysDesc &S, float rc2,
-                                           float gcc, PairAcc &A, const Pool &P, int s) {
+// In-cutoff test of one candidate (the FP32 rule above).
+template <bool SHIFT>
+__device__ __forceinline__ float pair_r2(const float4 &xj, const float4 &xi, const PairSeg &sg,
+                                         float &dx, float &dy, float &dz) {
+  dx = __fsub_rn(xj.x, xi.x);
+  dy = __fsub_rn(xj.y, xi.y);
+  dz = __fsub_rn(xj.z, xi.z);
+  if (SHIFT) {
+    dx = __fadd_rn(dx, sg.sh[0]);
+    dy = __fadd_rn(dy, sg.sh[1]);
+    dz = __fadd_rn(dz, sg.sh[2]);
+  }
+  return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// Gaussian core over real j in [t0, t1): every lane evaluates every
+// candidate (the exponential is cheap next to the test, so masking beats
+// branching); out-of-cutoff candidates contribute exactly zero.
+template <bool SHIFT, bool SELF, bool VIR, bool DBG>
+__device__ __forceinline__ void pair_core(const float4 *__restrict__ J, int t0, int t1,
+                                          int jsorted0, const float4 &xi, int isorted,
+                                          const PairSeg &sg, float rc2, float gcc, PairAcc &A,
+                                          const Pool &P, int s) {
+#pragma unroll 4
   for (int t = t0; t < t1; ++t) {
-    const float4 xj = J[t];
-    float dx = __fsub_rn(xj.x, xi.x);
-    float dy = __fsub_rn(xj.y, xi.y);
-    float dz = __fsub_rn(xj.z, xi.z);
-    if (SHIFT) {
-      dx = __fadd_rn(dx, sg.sh[0]);
-      dy = __fadd_rn(dy, sg.sh[1]);
-      dz = __fadd_rn(dz, sg.sh[2]);
-    }
-    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    float dx, dy, dz;
+    const float r2 = pair_r2<SHIFT>(J[t], xi, sg, dx, dy, dz);
     bool in = r2 < rc2;
     if (SELF) in = in && (jsorted0 + t != isorted);
-    if (GC) {
-      float e = ex2_approx(r2 * gcc);
-      e = in ? e : 0.0f;
-      A.eg += e;
-      A.gx = fmaf(e, dx, A.gx);
-      A.gy = fmaf(e, dy, A.gy);
-      A.gz = fmaf(e, dz, A.gz);
-      if (VIR) {
-        float ex = e * dx, ey = e * dy;
-        A.wg[0] = fmaf(ex, dx, A.wg[0]);
-        A.wg[1] = fmaf(ey, dy, A.wg[1]);
-        A.wg[2] = fmaf(e * dz, dz, A.wg[2]);
-        A.wg[3] = fmaf(ex, dy, A.wg[3]);
-        A.wg[4] = fmaf(ex, dz, A.wg[4]);
-        A.wg[5] = fmaf(ey, dz, A.wg[5]);
-      }
-    }
-    if (ELEC) {
-      const float qq = xi.w * xj.w;
-      if (in && qq != 0.0f) {
-        float g, h;
-        if (r2 < 1e-2f) {
-          g = S.ser_gf[0] + r2 * (S.ser_gf[1] + r2 * (S.ser_gf[2] + r2 * S.ser_gf[3]));
-          h = S.ser_hf[0] + r2 * (S.ser_hf[1] + r2 * S.ser_hf[2]);
-        } else {
-          const float r = sqrtf(r2);
-          const float rinv = 1.0f / r;
-          const float xb = S.betaf * r, xk = S.kappaf * r;
-          g = (erfcf(xk) - erfcf(xb)) * rinv;
-          const float eb = ex2_approx(-xb * xb * kLog2e);
-          const float ek = ex2_approx(-xk * xk * kLog2e);
-          const float dd = kTwoOverSqrtPi * (S.betaf * eb - S.kappaf * ek);
-          h = (g - dd) * (rinv * rinv);
-        }
-        A.ere = fmaf(qq, g, A.ere);
-        const float fq = qq * h;
-        A.fx = fmaf(fq, dx, A.fx);
-        A.fy = fmaf(fq, dy, A.fy);
-        A.fz = fmaf(fq, dz, A.fz);
-        if (VIR) {
-          float ex = fq * dx, ey = fq * dy;
-          A.we[0] = fmaf(ex, dx, A.we[0]);
-          A.we[1] = fmaf(ey, dy, A.we[1]);
-          A.we[2] = fmaf(fq * dz, dz, A.we[2]);
-          A.we[3] = fmaf(ex, dy, A.we[3]);
-          A.we[4] = fmaf(ex, dz, A.we[4]);
-          A.we[5] = fmaf(ey, dz, A.we[5]);
-        }
-      }
+    float e = ex2_approx(r2 * gcc);
+    e = in ? e : 0.0f;
+    A.eg += e;
+    A.gx = fmaf(e, dx, A.gx);
+    A.gy = fmaf(e, dy, A.gy);
+    A.gz = fmaf(e, dz, A.gz);
+    if (VIR) {
+      float ex = e * dx, ey = e * dy;
+      A.wg[0] = fmaf(ex, dx, A.wg[0]);
+      A.wg[1] = fmaf(ey, dy, A.wg[1]);
+      A.wg[2] = fmaf(e * dz, dz, A.wg[2]);
+      A.wg[3] = fmaf(ex, dy, A.wg[3]);
+      A.wg[4] = fmaf(ex, dz, A.wg[4]);
+      A.wg[5] = fmaf(ey, dz, A.wg[5]);
     }
     if (DBG && in) {
       unsigned long long k = atomicAdd(&P.acc[(long long)s * kNacc + ACC_NPAIR], 1ull);
@@ -129,38 +107,116 @@ __device__ __forceinline__ void pair_range(const float4 *__restrict__ J, int t0,
   }
 }
 
-// Process one staged segment (the bead ranges of one neighbour cell).
+// Real-space electrostatics of a charged i over charged j in [t0, t1)
+// (images and charged reals), 64 candidates at a time: a test pass sets
+// one bit per in-cutoff pair, then the erfc/exp work runs over the set bits
+// only, so a warp pays for it once per hit instead of once per candidate.
+// tg marks the first real j (images below it carry no core and are dumped
+// here in debug mode).
+template <bool SHIFT, bool SELF, bool VIR, bool DBG>
+__device__ __forceinline__ void pair_elec(const float4 *__restrict__ J, int t0, int t1, int tg,
+                                          int jsorted0, const float4 &xi, int isorted,
+                                          const PairSeg &sg, const SysDesc &S, float rc2,
+                                          PairAcc &A, const Pool &P, int s) {
+  const bool qi_nz = xi.w != 0.0f;
+  for (int c0 = t0; c0 < t1; c0 += 64) {
+    const int cn = min(64, t1 - c0);
+    unsigned long long m = 0ull;
+    if (qi_nz) {
+      for (int u = 0; u < cn; ++u) {
+        float dx, dy, dz;
+        const float r2 = pair_r2<SHIFT>(J[c0 + u], xi, sg, dx, dy, dz);
+        bool in = r2 < rc2;
+        if (SELF) in = in && (jsorted0 + c0 + u != isorted);
+        m |= (unsigned long long)in << u;
+      }
+    }
+    while (m) {
+      const int u = __ffsll((long long)m) - 1;
+      m &= m - 1ull;
+      const int t = c0 + u;
+      const float4 xj = J[t];
+      float dx, dy, dz;
+      const float r2 = pair_r2<SHIFT>(xj, xi, sg, dx, dy, dz);
+      const float qq = xi.w * xj.w;
+      float g, h;
+      if (r2 < 1e-2f) {
+        g = S.ser_gf[0] + r2 * (S.ser_gf[1] + r2 * (S.ser_gf[2] + r2 * S.ser_gf[3]));
+        h = S.ser_hf[0] + r2 * (S.ser_hf[1] + r2 * S.ser_hf[2]);
+      } else {
+        const float r = sqrtf(r2);
+        const float rinv = 1.0f / r;
+        const float xb = S.betaf * r, xk = S.kappaf * r;
+        g = (erfcf(xk) - erfcf(xb)) * rinv;
+        const float eb = ex2_approx(-xb * xb * kLog2e);
+        const float ek = ex2_approx(-xk * xk * kLog2e);
+        const float dd = kTwoOverSqrtPi * (S.betaf * eb - S.kappaf * ek);
+        h = (g - dd) * (rinv * rinv);
+      }
+      A.ere = fmaf(qq, g, A.ere);
+      const float fq = qq * h;
+      A.fx = fmaf(fq, dx, A.fx);
+      A.fy = fmaf(fq, dy, A.fy);
+      A.fz = fmaf(fq, dz, A.fz);
+      if (VIR) {
+        float ex = fq * dx, ey = fq * dy;
+        A.we[0] = fmaf(ex, dx, A.we[0]);
+        A.we[1] = fmaf(ey, dy, A.we[1]);
+        A.we[2] = fmaf(fq * dz, dz, A.we[2]);
+        A.we[3] = fmaf(ex, dy, A.we[3]);
+        A.we[4] = fmaf(ex, dz, A.we[4]);
+        A.we[5] = fmaf(ey, dz, A.we[5]);
+      }
+      if (DBG && t < tg) {
+        unsigned long long k = atomicAdd(&P.acc[(long long)s * kNacc + ACC_NPAIR], 1ull);
+        if ((long long)k < P.dbg_cap) {
+          P.dbg_triples[3 * k + 0] = P.sorted_idx[isorted];
+          P.dbg_triples[3 * k + 1] = P.sorted_idx[jsorted0 + t];
+          P.dbg_triples[3 * k + 2] = sg.code;
+        }
+      }
+    }
+  }
+}
+
+// Debug only: in-cutoff images seen by a neutral i (no interaction, but part
+// of the neighbour set).
+template <bool SHIFT>
+__device__ __forceinline__ void pair_dump_images(const float4 *__restrict__ J, int t0, int t1,
+                                                 int jsorted0, const float4 &xi, int isorted,
+                                                 const PairSeg &sg, float rc2, const Pool &P,
+                                                 int s) {
+  if (xi.w != 0.0f) return;
+  for (int t = t0; t < t1; ++t) {
+    float dx, dy, dz;
+    if (!(pair_r2<SHIFT>(J[t], xi, sg, dx, dy, dz) < rc2)) continue;
+    unsigned long long k = atomicAdd(&P.acc[(long long)s * kNacc + ACC_NPAIR], 1ull);
+    if ((long long)k < P.dbg_cap) {
+      P.dbg_triples[3 * k + 0] = P.sorted_idx[isorted];
+      P.dbg_triples[3 * k + 1] = P.sorted_idx[jsorted0 + t];
+      P.dbg_triples[3 * k + 2] = sg.code;
+    }
+  }
+}
+
+// Process one staged segment (the bead ranges of one neighbour cell),
+// candidates clipped to [t0, t1): [0, a) images, [a, b) charged reals,
+// [b, n) neutral reals.
 template <bool VIR, bool DBG>
 __device__ __forceinline__ void pair_segment(const float4 *J, int t0, int t1, int jsorted0,
                                              const PairSeg &sg, bool anyq, const float4 &xi,
                                              int isorted, const SysDesc &S, float rc2, float gcc,
                                              PairAcc &A, const Pool &P, int s) {
-  // [0, a): images (electrostatics only); [a, b): charged reals (both);
-  // [b, n): neutral reals (core only); ranges clipped to [t0, t1).
   const int a0 = max(t0, min(t1, sg.a)), b0 = max(t0, min(t1, sg.b));
-#define GCME_RANGES(SHIFT, SELF)                                                                  \
-  if (anyq) {                                                                                     \
-    pair_range<false, true, SHIFT, SELF, VIR, DBG>(J, t0, a0, jsorted0, xi, isorted, sg, S, rc2, \
-                                                   gcc, A, P, s);                                 \
-    pair_range<true, true, SHIFT, SELF, VIR, DBG>(J, a0, b0, jsorted0, xi, isorted, sg, S, rc2,  \
-                                                  gcc, A, P, s);                                  \
-  } else {                                                                                        \
-    if (DBG)                                                                                      \
-      pair_range<false, false, SHIFT, SELF, VIR, DBG>(J, t0, a0, jsorted0, xi, isorted, sg, S,   \
-                                                      rc2, gcc, A, P, s);                         \
-    pair_range<true, false, SHIFT, SELF, VIR, DBG>(J, a0, b0, jsorted0, xi, isorted, sg, S, rc2, \
-                                                   gcc, A, P, s);                                 \
-  }                                                                                               \
-  pair_range<true, false, SHIFT, SELF, VIR, DBG>(J, b0, t1, jsorted0, xi, isorted, sg, S, rc2,   \
-                                                 gcc, A, P, s);
+#define GCME_SEG(SHIFT, SELF)                                                                      pair_core<SHIFT, SELF, VIR, DBG>(J, a0, t1, jsorted0, xi, isorted, sg, rc2, gcc, A, P, s);       if (anyq)                                                                                          pair_elec<SHIFT, SELF, VIR, DBG>(J, t0, b0, a0, jsorted0, xi, isorted, sg, S, rc2, A, P, s);   if (DBG) pair_dump_images<SHIFT>(J, t0, a0, jsorted0, xi, isorted, sg, rc2, P, s);
   if (sg.self) {
-    GCME_RANGES(false, true)
+    GCME_SEG(false, true)
   } else if (sg.shifted) {
-    GCME_RANGES(true, false)
+    GCME_SEG(true, false)
   } else {
-    GCME_RANGES(false, false)
+    GCME_SEG(false, false)
   }
-#undef GCME_RANGES
+#undef GCME_SEG
 }
 
 // One (home cell, z-offset) work item by the whole CTA.  Shared memory:
