@@ -196,6 +196,7 @@ def run_gcme(args, ws, rank, local):
     vel = vel0.clone()
     E = torch.zeros(g.NTERMS, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
+    tuning = sysg.autotune(pos)
     pairs0, qq0 = count_pairs(g, sysg, s, pos, dev)
 
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MiB
@@ -292,6 +293,7 @@ def run_gcme(args, ws, rank, local):
                    "note": "gcme_step(1) per step from host state: force evaluation of the "
                            "copied state + one step"},
            "roofline": roofline, "clocks": clk, "gpu_launches": int(nkern) * K,
+           "tuning": tuning,
            "wall_s_timed": t_wall}
     if not args.no_extras and rank == 0 and ws == 1:
         out["fp64_plain"] = fp64_plain_compare(g, ctx, dev)
@@ -355,6 +357,7 @@ def batched_c4(g, ctx, dev, nsteps=500):
         b = g.Batch(ctx, [g.params_from(s) for s in systems], [s.q for s in systems])
         b.set_state(np.concatenate([s.pos for s in systems]),
                     np.concatenate([s.vel for s in systems]).astype(np.float32))
+        tuned = b.autotune()
         b.step(3, mode)
         torch.cuda.synchronize()
         a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -364,7 +367,7 @@ def batched_c4(g, ctx, dev, nsteps=500):
         e.synchronize()
         dt = a.elapsed_time(e) / 1e3
         key = "graph_per_phase" if mode == 0 else "persistent_cooperative"
-        out[key] = {"system_steps_per_s": len(systems) * nsteps / dt,
+        out[key] = {"tuning": tuned, "system_steps_per_s": len(systems) * nsteps / dt,
                     "bead_steps_per_s": out["beads"] * nsteps / dt,
                     "pair_interactions_per_s": pairs * nsteps / dt,
                     "ms_per_step": 1e3 * dt / nsteps}

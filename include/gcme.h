@@ -105,6 +105,10 @@ typedef struct gcme_params {
   double wall_sigma2; /* wall width sigma_w^2                                */
   double bond_k;      /* harmonic bond constant                              */
   double bond_r0;     /* harmonic bond rest length                           */
+  int32_t cell_factor; /* cells of side >= rc / cell_factor: 1 (27-cell
+                          stencil) or 2 (blocks of 2^3 cells with culling);
+                          0 lets the library choose                        */
+  int32_t pad0;
 } gcme_params;
 
 /* Fill p with the paper's defaults (A = 25, sigma = a = 0.5, lB = 1.2053,
@@ -151,7 +155,8 @@ void gcme_system_destroy(gcme_sys *sys);
 
 /* Build the cell list of the positions d_pos[n*3] (K1 + K2): wrap into the
  * box in FP64 (x - L floor(x/L)), cell c_a = floor(x_a n_a / L_a), cells of
- * side >= rc, beads of a cell in (class, index) order with class 0 = image,
+ * side >= rc / cell_factor (n_a = floor(L_a / ((rc / cell_factor) (1 + 1e-4)))),
+ * beads of a cell in (class, index) order with class 0 = image,
  * 1 = charged, 2 = neutral.  Outputs (caller-owned, may be NULL):
  *   d_cell_start[ncell+1], d_sorted_idx[n_ext]  (n_ext = n + images).
  * ncell and n_ext are returned by gcme_system_info. */
@@ -222,6 +227,7 @@ int gcme_step_phase_ms(gcme_sys *sys, float *h_ms, int32_t nphase, int32_t *kern
 typedef struct gcme_sys_info {
   int64_t n, n_ext, n_charged_ext, ncell, nbonds;
   int32_t nc[3];
+  int32_t cell_factor;
   int64_t scratch_bytes;
 } gcme_sys_info;
 int gcme_system_info(const gcme_sys *sys, gcme_sys_info *out);
@@ -238,6 +244,29 @@ int gcme_debug_pairs(gcme_sys *sys, const double *d_pos, int32_t *d_triples,
  * GCME_ERR_TIMEOUT when the kernel reported the timeout as designed.  Used
  * to test the failure path of the persistent launch without hanging. */
 int gcme_debug_barrier_timeout(gcme_ctx *ctx, double timeout_s, gcme_stream_t stream);
+
+/* ---- autotuner ------------------------------------------------------------ */
+
+/* Tuned launch shapes: work items per home cell of the pair kernel (3: 9
+ * neighbour cells each; 9: 3 each), pair block size (128 or 160 threads:
+ * 3 or 4 Gaussian-core warps + one electrostatics warp), FFT lines per
+ * tile per axis; device times of the chosen pair kernel and PME. */
+typedef struct gcme_tuning {
+  int32_t pair_split, pair_threads, fft_lpb[3], from_cache, cell_factor, pad;
+  double pair_ms, pme_ms;
+} gcme_tuning;
+
+#define GCME_TUNE_REMEASURE 1 /* ignore a cached entry, time again       */
+#define GCME_TUNE_NO_CACHE 2  /* neither read nor write the cache file   */
+
+/* Time the candidate shapes on this system at positions d_pos (CUDA events
+ * on `stream`), keep the fastest and record it in the tuning cache
+ * (GCME_TUNE_CACHE, else $HOME/.cache/gcme_tune.jsonl) keyed by GPU name and
+ * workload shape; a cached entry is applied without timing.  Results of
+ * later calls are unchanged except for FP32 summation order.  A following
+ * gcme_step_continue must be preceded by gcme_step.  out may be NULL. */
+int gcme_autotune(gcme_sys *sys, const double *d_pos, int32_t flags, gcme_tuning *out,
+                  gcme_stream_t stream);
 
 /* ---- batch of independent systems ---------------------------------------- */
 
@@ -264,6 +293,9 @@ int gcme_batch_get_state(gcme_batch *b, double *h_pos, float *h_vel,
  * step captured in a CUDA graph; mode 1: one persistent cooperative launch
  * running all phases of all steps with grid-wide barriers. */
 int gcme_batch_step(gcme_batch *b, int64_t nsteps, int32_t mode, gcme_stream_t stream);
+
+/* Autotune a batch on its current state (as gcme_autotune). */
+int gcme_batch_autotune(gcme_batch *b, int32_t flags, gcme_tuning *out, gcme_stream_t stream);
 
 /* Phase times of the last batch step, as gcme_step_phase_ms. */
 int gcme_batch_phase_ms(gcme_batch *b, float *h_ms, int32_t nphase, int32_t *kernels);

@@ -115,13 +115,14 @@ def bspline_moduli(p: int, K: int) -> np.ndarray:
     return out
 
 
-def cell_counts(box, rc: float, margin: float = 1e-4):
-    """Cells per axis: floor(L / (rc (1 + margin))), at least 1.
+def cell_counts(box, rc: float, factor: int = 1, margin: float = 1e-4):
+    """Cells per axis: floor(L / ((rc / factor) (1 + margin))), at least 1.
 
-    The margin keeps every cell side above rc by far more than FP32 rounding
-    of coordinates, so the 27-cell stencil reaches every in-cutoff pair.
+    The margin keeps every cell side above rc / factor by far more than FP32
+    rounding of coordinates, so the stencil of +-factor cells reaches every
+    in-cutoff pair.
     """
-    return np.array([max(1, int(np.floor(b / (rc * (1.0 + margin))))) for b in box],
+    return np.array([max(1, int(np.floor(b / ((rc / factor) * (1.0 + margin))))) for b in box],
                     dtype=np.int32)
 
 

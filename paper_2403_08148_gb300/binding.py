@@ -40,14 +40,28 @@ class Params(ctypes.Structure):
                 ("K", ctypes.c_int32 * 3), ("order", ctypes.c_int32), ("dt", ctypes.c_double),
                 ("H", ctypes.c_double), ("wall_A", ctypes.c_double),
                 ("wall_sigma2", ctypes.c_double), ("bond_k", ctypes.c_double),
-                ("bond_r0", ctypes.c_double)]
+                ("bond_r0", ctypes.c_double), ("cell_factor", ctypes.c_int32),
+                ("pad0", ctypes.c_int32)]
 
 
 class SysInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("n_ext", ctypes.c_int64),
                 ("n_charged_ext", ctypes.c_int64), ("ncell", ctypes.c_int64),
                 ("nbonds", ctypes.c_int64), ("nc", ctypes.c_int32 * 3),
-                ("scratch_bytes", ctypes.c_int64)]
+                ("cell_factor", ctypes.c_int32), ("scratch_bytes", ctypes.c_int64)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("pair_split", ctypes.c_int32), ("pair_threads", ctypes.c_int32),
+                ("fft_lpb", ctypes.c_int32 * 3), ("from_cache", ctypes.c_int32),
+                ("cell_factor", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("pair_ms", ctypes.c_double), ("pme_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"pair_split": self.pair_split, "pair_threads": self.pair_threads,
+                "fft_lpb": list(self.fft_lpb), "from_cache": bool(self.from_cache),
+                "cell_factor": self.cell_factor, "pair_ms": self.pair_ms,
+                "pme_ms": self.pme_ms}
 
 
 class Request(ctypes.Structure):
@@ -89,6 +103,8 @@ _SIGS = {
     "gcme_step_continue": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
     "gcme_step_phase_ms": ([_vp, _vp, _i32, _vp], ctypes.c_int),
     "gcme_batch_phase_ms": ([_vp, _vp, _i32, _vp], ctypes.c_int),
+    "gcme_autotune": ([_vp, _vp, _i32, ctypes.POINTER(Tuning), _vp], ctypes.c_int),
+    "gcme_batch_autotune": ([_vp, _i32, ctypes.POINTER(Tuning), _vp], ctypes.c_int),
     "gcme_debug_barrier_timeout": ([_vp, ctypes.c_double, _vp], ctypes.c_int),
     "gcme_debug_pairs": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
     "gcme_batch_create": ([_vp, _i32, ctypes.POINTER(Params), _vp, _vp, _vp, _vp,
@@ -153,9 +169,10 @@ def _stream(stream) -> Optional[int]:
     return getattr(stream, "cuda_stream", stream)
 
 
-def params_from(s, precision: int = GCME_FP32) -> Params:
+def params_from(s, precision: int = GCME_FP32, cell_factor: int = 0) -> Params:
     """gcme_params from a system description with the fields of synth.System."""
     p = Params()
+    p.cell_factor = int(cell_factor)
     for a in range(3):
         p.box[a] = float(s.box[a])
         p.K[a] = int(s.K[a])
@@ -258,6 +275,12 @@ class System:
         _check(fn(self.h, _ptr(d_pos), _ptr(d_vel), int(nsteps), _ptr(d_energy),
                   _stream(stream)))
 
+    def autotune(self, d_pos, flags: int = 0, stream=None) -> dict:
+        t = Tuning()
+        _check(load().gcme_autotune(self.h, _ptr(d_pos), int(flags), ctypes.byref(t),
+                                    _stream(stream)))
+        return t.as_dict()
+
     def step_continue(self, d_pos, d_vel, nsteps: int, d_energy=None, stream=None):
         _check(load().gcme_step_continue(self.h, _ptr(d_pos), _ptr(d_vel), int(nsteps),
                                          _ptr(d_energy), _stream(stream)))
@@ -329,6 +352,11 @@ class Batch:
 
     def step(self, nsteps: int, mode: int = 0, stream=None):
         _check(load().gcme_batch_step(self.h, int(nsteps), int(mode), _stream(stream)))
+
+    def autotune(self, flags: int = 0, stream=None) -> dict:
+        t = Tuning()
+        _check(load().gcme_batch_autotune(self.h, int(flags), ctypes.byref(t), _stream(stream)))
+        return t.as_dict()
 
     def phase_ms(self):
         ms = np.zeros(6, np.float32)

@@ -88,7 +88,13 @@ struct SysDesc {
   float ser_gf[4], ser_hf[3];
   float betaf, kappaf;
   float gc_c2f;        // -3/(2 s) log2(e): exponent of the core in base 2
-  float pad2;
+  // cell decomposition: cells of side >= rc / cell_factor; with factor 2 the
+  // pair kernel works on blocks of 2 x 2 x 2 cells (nb blocks per axis)
+  int cell_factor;
+  int pair_split;      // work items per home cell: 3 (9 neighbour cells each) or 9 (3 each)
+  int nb[3];
+  float cside[3];      // cell side L / nc (FP32, for bounding-box culling)
+  float cull2;         // (rc + 1e-3)^2: cells farther than this are skipped
 };
 
 // Pooled device arrays.  Passed by value to every kernel.

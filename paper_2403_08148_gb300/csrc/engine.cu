@@ -146,12 +146,76 @@ std::string validate_spec(const SysSpec &sp) {
 }
 
 Engine::~Engine() {
-  for (auto &kv : graphs_) cudaGraphExecDestroy(kv.second);
+  clear_graphs();
   for (auto e : phase_ev)
     if (e) cudaEventDestroy(e);
-  for (auto g : graph_objs_) cudaGraphDestroy(g);
   if (capture_stream) cudaStreamDestroy(capture_stream);
   if (arena_) cudaFree(arena_);
+}
+
+std::vector<int2> Engine::make_pair_work(int split) const {
+  // (system, cell * split + part) for the 27-cell kernel, or
+  // (system, block * 3 + z-part) for the fine-cell kernel
+  std::vector<int2> pw;
+  for (int s = 0; s < (int)hsys.size(); ++s) {
+    const SysDesc &S = hsys[s];
+    const int nitem = cell_factor == 2 ? S.nb[0] * S.nb[1] * S.nb[2] : S.ncell;
+    const int parts = cell_factor == 2 ? 3 : split;
+    for (int c = 0; c < nitem; ++c)
+      for (int k = 0; k < parts; ++k) pw.push_back(make_int2(s, c * parts + k));
+  }
+  return pw;
+}
+
+std::vector<int2> Engine::make_fft_work(int axis, int lpb) const {
+  std::vector<int2> w;
+  for (int s = 0; s < (int)hsys.size(); ++s) {
+    const SysDesc &S = hsys[s];
+    const long long nl = (long long)S.K[0] * S.K[1] * S.K[2] / S.K[axis];
+    const int nt = (int)((nl + lpb - 1) / lpb);
+    for (int t = 0; t < nt; ++t) w.push_back(make_int2(s, t));
+  }
+  return w;
+}
+
+void Engine::clear_graphs() {
+  for (auto &kv : graphs_) cudaGraphExecDestroy(kv.second);
+  graphs_.clear();
+  for (auto g : graph_objs_) cudaGraphDestroy(g);
+  graph_objs_.clear();
+}
+
+int Engine::set_pair_config(int split, int threads) {
+  if ((split != 3 && split != 9) || (threads != 128 && threads != 160)) {
+    set_error("pair configuration must be split 3|9 and 128|160 threads");
+    return GCME_ERR_INVALID;
+  }
+  std::vector<int2> pw = make_pair_work(split);
+  pair_split = split;
+  pair_threads = threads;
+  for (auto &S : hsys) S.pair_split = split;
+  GCME_CK(cudaMemcpy(const_cast<SysDesc *>(P.sys), hsys.data(), sizeof(SysDesc) * hsys.size(),
+                     cudaMemcpyHostToDevice));
+  GCME_CK(cudaMemcpy(pair_work, pw.data(), sizeof(int2) * pw.size(), cudaMemcpyHostToDevice));
+  n_pair_work = (int)pw.size();
+  clear_graphs();
+  return GCME_OK;
+}
+
+int Engine::set_fft_lpb(int axis, int lpb) {
+  const size_t rsz = fp64 ? sizeof(double2) : sizeof(float2);
+  if (axis < 0 || axis > 2 || lpb < kMinLpb || lpb > 64 ||
+      2 * (size_t)lpb * plan.kmax[axis] * rsz > kFftSmemLimit) {
+    set_error("FFT lines per tile out of range");
+    return GCME_ERR_INVALID;
+  }
+  std::vector<int2> w = make_fft_work(axis, lpb);
+  GCME_CK(cudaMemcpy(const_cast<int2 *>(plan.work[axis]), w.data(), sizeof(int2) * w.size(),
+                     cudaMemcpyHostToDevice));
+  plan.lpb[axis] = lpb;
+  plan.nwork[axis] = (int)w.size();
+  clear_graphs();
+  return GCME_OK;
 }
 
 namespace {
@@ -176,6 +240,22 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     return GCME_ERR_INVALID;
   }
   fp64 = specs[0].p.precision == GCME_FP64;
+  cell_factor = 0;
+  for (auto &sp : specs) {
+    if (sp.p.cell_factor != 0 && sp.p.cell_factor != 1 && sp.p.cell_factor != 2) {
+      set_error("cell_factor must be 0, 1 or 2");
+      return GCME_ERR_INVALID;
+    }
+    if (sp.p.cell_factor != 0) {
+      if (cell_factor != 0 && cell_factor != sp.p.cell_factor) {
+        set_error("all systems of a batch must share one cell factor");
+        return GCME_ERR_INVALID;
+      }
+      cell_factor = sp.p.cell_factor;
+    }
+  }
+  if (cell_factor == 0) cell_factor = kDefaultCellFactor;
+  if (pair_split != 3 && pair_split != 9) pair_split = kDefaultPairSplit;
   for (auto &sp : specs) {
     std::string err = validate_spec(sp);
     if (!err.empty()) {
@@ -219,8 +299,12 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     S.grid_off = ngrid;
     S.bond_off = nbond;
     S.ncell = 1;
+    S.cell_factor = cell_factor;
+    S.pair_split = pair_split;
     for (int a = 0; a < 3; ++a) {
-      S.nc[a] = std::max(1, (int)std::floor(p.box[a] / (p.rc * (1.0 + 1e-4))));
+      S.nc[a] = std::max(1, (int)std::floor(p.box[a] / ((p.rc / cell_factor) * (1.0 + 1e-4))));
+      S.nb[a] = (S.nc[a] + 1) / 2;
+      S.cside[a] = (float)(p.box[a] / S.nc[a]);
       S.ncell *= S.nc[a];
       S.box[a] = p.box[a];
       S.inv_cell[a] = (double)S.nc[a] / p.box[a];
@@ -236,6 +320,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     }
     S.order = p.order;
     S.rc2f = (float)(p.rc * p.rc);
+    S.cull2 = (float)((p.rc + 1e-3) * (p.rc + 1e-3));
     S.V = p.box[0] * p.box[1] * p.box[2];
     S.A = p.A;
     S.sigma = p.sigma;
@@ -287,28 +372,22 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   }
   n_real = nr;
   n_ext = ne;
-  // FFT plan
-  int kmax[3] = {0, 0, 0};
-  for (auto &S : hsys)
-    for (int a = 0; a < 3; ++a) kmax[a] = std::max(kmax[a], S.K[a]);
-  std::vector<int2> fftw[3];
+  // FFT plan and pair work lists (rebuilt by the autotuner)
   for (int a = 0; a < 3; ++a) {
-    int lpb = std::max(8, std::min(64, 1024 / kmax[a]));
-    plan.lpb[a] = lpb;
-    plan.kmax[a] = kmax[a];
-    for (int s = 0; s < ns; ++s) {
-      const SysDesc &S = hsys[s];
-      long long nl = (long long)S.K[0] * S.K[1] * S.K[2] / S.K[a];
-      int nt = (int)((nl + lpb - 1) / lpb);
-      for (int t = 0; t < nt; ++t) fftw[a].push_back(make_int2(s, t));
-    }
-    plan.nwork[a] = (int)fftw[a].size();
+    plan.kmax[a] = 0;
+    for (auto &S : hsys) plan.kmax[a] = std::max(plan.kmax[a], S.K[a]);
+    plan.lpb[a] = std::max(8, std::min(64, 1024 / plan.kmax[a]));
   }
-  std::vector<int2> pw;
-  for (int s = 0; s < ns; ++s)
-    for (int c = 0; c < hsys[s].ncell; ++c)
-      for (int dz = 0; dz < 3; ++dz) pw.push_back(make_int2(s, c * 3 + dz));
+  std::vector<int2> fftw[3];
+  int fft_cap[3];
+  for (int a = 0; a < 3; ++a) {
+    fftw[a] = make_fft_work(a, plan.lpb[a]);
+    plan.nwork[a] = (int)fftw[a].size();
+    fft_cap[a] = (int)make_fft_work(a, kMinLpb).size();
+  }
+  std::vector<int2> pw = make_pair_work(pair_split);
   n_pair_work = (int)pw.size();
+  const int pair_cap = std::max(n_pair_work, (int)make_pair_work(9).size());
 
   // ---- device arena
   Carver cv;
@@ -358,10 +437,10 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   cv.add(&P.vacc, (long long)ns * 9);
   cv.add(&P.energy, (long long)ns * GCME_NTERMS);
   cv.add(&P.virial, (long long)ns * 9);
-  cv.add(&pair_work, n_pair_work);
+  cv.add(&pair_work, pair_cap);
   cv.add(&bar_words, 4);
   int2 *fw[3];
-  for (int a = 0; a < 3; ++a) cv.add(&fw[a], plan.nwork[a]);
+  for (int a = 0; a < 3; ++a) cv.add(&fw[a], fft_cap[a]);
   scratch_bytes = cv.off;
   cudaError_t e = cudaMalloc(&arena_, cv.off);
   if (e != cudaSuccess) {
@@ -468,7 +547,7 @@ void Engine::enqueue_forces(const Pool &Q, cudaStream_t st, bool vir, bool dbg) 
   cudaMemsetAsync(Q.acc, 0, sizeof(unsigned long long) * Q.nsys * kNacc, st);
   if (vir) cudaMemsetAsync(Q.vacc, 0, sizeof(unsigned long long) * Q.nsys * 9, st);
   launch_cells(Q, st);
-  launch_pair(Q, pair_work, n_pair_work, fp64, vir, dbg, st);
+  launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, vir, dbg, st);
   if (dbg) return;
   launch_pme(Q, plan, fp64, vir, st);
   launch_bonded(Q, vir, st);
@@ -484,7 +563,7 @@ void Engine::enqueue_step(const Pool &Q, cudaStream_t st) {
   cudaMemsetAsync(Q.acc, 0, sizeof(unsigned long long) * Q.nsys * kNacc, st);
   launch_cells(Q, st);
   if (ev) cudaEventRecordWithFlags(phase_ev[2], st, cudaEventRecordExternal);
-  launch_pair(Q, pair_work, n_pair_work, fp64, false, false, st);
+  launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, false, false, st);
   if (ev) cudaEventRecordWithFlags(phase_ev[3], st, cudaEventRecordExternal);
   launch_pme(Q, plan, fp64, false, st);
   if (ev) cudaEventRecordWithFlags(phase_ev[4], st, cudaEventRecordExternal);
@@ -694,6 +773,7 @@ int gcme_system_info(const gcme_sys *sys, gcme_sys_info *out) {
   out->ncell = S.ncell;
   out->nbonds = S.nbond;
   for (int a = 0; a < 3; ++a) out->nc[a] = S.nc[a];
+  out->cell_factor = S.cell_factor;
   out->scratch_bytes = (int64_t)sys->eng.scratch_bytes;
   return GCME_OK;
 }
@@ -918,6 +998,52 @@ int gcme_debug_pairs(gcme_sys *sys, const double *d_pos, int32_t *d_triples, int
   return check_launch("gcme_debug_pairs");
 }
 
+// ---- autotuner -------------------------------------------------------------
+static void fill_tuning(const Engine &eng, double pair_ms, double pme_ms, bool hit,
+                        gcme_tuning *out) {
+  if (!out) return;
+  out->pair_split = eng.pair_split;
+  out->pair_threads = eng.pair_threads;
+  for (int a = 0; a < 3; ++a) out->fft_lpb[a] = eng.plan.lpb[a];
+  out->from_cache = hit ? 1 : 0;
+  out->cell_factor = eng.cell_factor;
+  out->pair_ms = pair_ms;
+  out->pme_ms = pme_ms;
+}
+
+int gcme_autotune(gcme_sys *sys, const double *d_pos, int32_t flags, gcme_tuning *out,
+                  gcme_stream_t stream) {
+  if (!sys || !d_pos) {
+    set_error("invalid argument to gcme_autotune");
+    return GCME_ERR_INVALID;
+  }
+  GCME_TRY_CK(cudaSetDevice(sys->eng.device));
+  Pool Q = sys->eng.P;
+  Q.pos = const_cast<double *>(d_pos);
+  double a = 0, b = 0;
+  bool hit = false;
+  int rc = sys->eng.autotune(Q, (cudaStream_t)stream, flags, &a, &b, &hit);
+  if (rc) return rc;
+  sys->last_pos = sys->last_vel = nullptr;  // forces no longer match a trajectory
+  fill_tuning(sys->eng, a, b, hit, out);
+  return GCME_OK;
+}
+
+int gcme_batch_autotune(gcme_batch *bt, int32_t flags, gcme_tuning *out, gcme_stream_t stream) {
+  if (!bt) {
+    set_error("NULL batch");
+    return GCME_ERR_INVALID;
+  }
+  GCME_TRY_CK(cudaSetDevice(bt->eng.device));
+  double a = 0, b = 0;
+  bool hit = false;
+  int rc = bt->eng.autotune(bt->eng.P, (cudaStream_t)stream, flags, &a, &b, &hit);
+  if (rc) return rc;
+  bt->forces_valid = false;
+  fill_tuning(bt->eng, a, b, hit, out);
+  return GCME_OK;
+}
+
 // ---- batch ----------------------------------------------------------------
 int gcme_batch_create(gcme_ctx *ctx, int32_t nsys, const gcme_params *params, const int64_t *n,
                       const double *h_q, const int32_t *h_bonds, const int64_t *h_bond_count,
@@ -1065,8 +1191,8 @@ int gcme_batch_step(gcme_batch *b, int64_t nsteps, int32_t mode, gcme_stream_t s
     return GCME_ERR_INVALID;
   }
   if (nsteps == 0) return GCME_OK;
-  int lr = launch_persistent(Q, b->eng.pair_work, b->eng.n_pair_work, b->eng.plan, nsteps,
-                             b->eng.bar_words, 2.0, st);
+  int lr = launch_persistent(Q, b->eng.pair_work, b->eng.n_pair_work, b->eng.cell_factor,
+                             b->eng.plan, nsteps, b->eng.bar_words, 2.0, st);
   if (lr != 0) {
     cudaError_t e = cudaGetLastError();
     set_error(std::string("persistent cooperative launch failed: ") + cudaGetErrorString(e));

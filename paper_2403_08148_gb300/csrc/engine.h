@@ -9,6 +9,14 @@
 
 namespace gcme {
 
+// cell factor used when the parameters leave the choice to the library
+constexpr int kDefaultCellFactor = 1;
+// work items per home cell of the 27-cell pair kernel (3 or 9)
+constexpr int kDefaultPairSplit = 9;
+constexpr int kDefaultPairThreads = 128;
+constexpr int kMinLpb = 4;                       // fewest FFT lines per tile
+constexpr size_t kFftSmemLimit = 200 * 1024;     // dynamic smem of k_fft
+
 void set_error(const std::string &msg);
 
 struct SysSpec {
@@ -40,6 +48,15 @@ class Engine {
   int forces_graph(const Pool &P, cudaGraphExec_t *out);
 
   int nsys() const { return (int)hsys.size(); }
+  std::vector<int2> make_pair_work(int split) const;
+  std::vector<int2> make_fft_work(int axis, int lpb) const;
+  int set_pair_config(int split, int threads);
+  int set_fft_lpb(int axis, int lpb);
+  void clear_graphs();
+  // time candidate configurations on the current state and keep the
+  // fastest (tune.cu); from_cache reports a hit of the tuning cache
+  int autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms, double *pme_ms,
+               bool *from_cache);
   // Phase marks recorded inside the captured step graph: 0 start, 1 after
   // the first half kick + drift, 2 after the cell list, 3 after the pair
   // kernel, 4 after PME, 5 after bonds/walls/slab, 6 after kick + energies.
@@ -48,6 +65,9 @@ class Engine {
   int step_kernels = 0;  // kernel nodes in the step graph
   unsigned int *bar_words = nullptr;  // persistent-launch barrier state (4 words)
   bool fp64 = false;
+  int cell_factor = 1;  // 1: 27-cell stencil; 2: fine cells with culling
+  int pair_split = 0;   // 3 or 9 work items per home cell (0: default)
+  int pair_threads = kDefaultPairThreads;  // 128 (3 core warps) or 160 (4)
   int device = 0;
   std::vector<SysDesc> hsys;
   Pool P{};  // device pointers of the pooled arrays

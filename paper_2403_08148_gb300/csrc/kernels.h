@@ -14,8 +14,8 @@ struct PmePlan {
 };
 
 void launch_cells(const Pool &P, cudaStream_t st);
-void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, bool vir, bool dbg,
-                 cudaStream_t st);
+void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell_factor,
+                 int threads, bool vir, bool dbg, cudaStream_t st);
 void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStream_t st);
 void pme_set_smem_limits();
 void launch_bonded(const Pool &P, bool vir, cudaStream_t st);   // bonds, walls, dipole
@@ -25,7 +25,8 @@ void launch_kick_drift(const Pool &P, bool vel64, cudaStream_t st);
 void launch_kick(const Pool &P, bool vel64, cudaStream_t st);
 // one cooperative launch of nsteps steps of the whole batch (FP32); the
 // four words at bar_words hold the barrier state and the error word
-int launch_persistent(const Pool &P, const int2 *pair_work, int n_pair_work, const PmePlan &pl,
+int launch_persistent(const Pool &P, const int2 *pair_work, int n_pair_work, int cell_factor,
+                      const PmePlan &pl,
                       long long nsteps, unsigned int *bar_words, double timeout_s,
                       cudaStream_t st);
 int launch_barrier_probe(unsigned int *bar_words, double timeout_s, cudaStream_t st);

@@ -90,6 +90,11 @@ extern "C" int gcme_build_cells_noalloc(const gcme_params *p, int64_t n, const d
     set_error("gcme_build_cells_noalloc: rc must be > 0");
     return GCME_ERR_INVALID;
   }
+  if (p->cell_factor != 0 && p->cell_factor != 1 && p->cell_factor != 2) {
+    set_error("gcme_build_cells_noalloc: cell_factor must be 0, 1 or 2");
+    return GCME_ERR_INVALID;
+  }
+  const int factor = p->cell_factor ? p->cell_factor : kDefaultCellFactor;
   SysDesc S{};
   long long ncell = 1;
   for (int a = 0; a < 3; ++a) {
@@ -97,7 +102,7 @@ extern "C" int gcme_build_cells_noalloc(const gcme_params *p, int64_t n, const d
       set_error("gcme_build_cells_noalloc: box side shorter than the cutoff");
       return GCME_ERR_INVALID;
     }
-    const double nc = std::floor(p->box[a] / (p->rc * (1.0 + 1e-4)));
+    const double nc = std::floor(p->box[a] / ((p->rc / factor) * (1.0 + 1e-4)));
     if (nc > (double)kNoAllocMaxCells) {
       set_error("gcme_build_cells_noalloc: too many cells");
       return GCME_ERR_INVALID;

@@ -6,7 +6,12 @@
 namespace gcme {
 
 template <bool VIR, bool DBG>
-__global__ void __launch_bounds__(kPairThreads) k_pair_f32(Pool P, const int2 *work, int nwork) {
+__global__ void __launch_bounds__(kPairThreads) k_pair_fine(Pool P, const int2 *work, int nwork) {
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) dev_pair_fine_item<VIR, DBG>(P, work, w);
+}
+
+template <bool VIR, bool DBG>
+__global__ void __launch_bounds__(160, 6) k_pair_f32(Pool P, const int2 *work, int nwork) {
   __shared__ float4 sj[kPairCap];
   __shared__ PairSeg seg[9];
   __shared__ int s_total;
@@ -50,9 +55,10 @@ __global__ void __launch_bounds__(128) k_pair_f64(Pool P) {
                 cz = cell / (S.nc[0] * S.nc[1]);
       double f[3] = {0, 0, 0};
       const double two_sqrtpi = 1.1283791670955126;
-      for (int dzo = -1; dzo <= 1; ++dzo)
-        for (int dyo = -1; dyo <= 1; ++dyo)
-          for (int dxo = -1; dxo <= 1; ++dxo) {
+      const int m = S.cell_factor;
+      for (int dzo = -m; dzo <= m; ++dzo)
+        for (int dyo = -m; dyo <= m; ++dyo)
+          for (int dxo = -m; dxo <= m; ++dxo) {
             const int u[3] = {cx + dxo, cy + dyo, cz + dzo};
             int v[3], nn[3];
             for (int a = 0; a < 3; ++a) {
@@ -129,8 +135,8 @@ __global__ void __launch_bounds__(128) k_pair_f64(Pool P) {
   }
 }
 
-void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, bool vir, bool dbg,
-                 cudaStream_t st) {
+void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell_factor,
+                 int threads, bool vir, bool dbg, cudaStream_t st) {
   if (P.n_ext == 0) return;
   if (fp64) {
     int nb = (int)((P.n_ext + 127) / 128);
@@ -140,9 +146,16 @@ void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, bool vir
     return;
   }
   if (nwork == 0) return;
-  if (dbg) k_pair_f32<false, true><<<nwork, kPairThreads, 0, st>>>(P, work, nwork);
-  else if (vir) k_pair_f32<true, false><<<nwork, kPairThreads, 0, st>>>(P, work, nwork);
-  else k_pair_f32<false, false><<<nwork, kPairThreads, 0, st>>>(P, work, nwork);
+  if (cell_factor == 2) {
+    if (dbg) k_pair_fine<false, true><<<nwork, kPairThreads, 0, st>>>(P, work, nwork);
+    else if (vir) k_pair_fine<true, false><<<nwork, kPairThreads, 0, st>>>(P, work, nwork);
+    else k_pair_fine<false, false><<<nwork, kPairThreads, 0, st>>>(P, work, nwork);
+    return;
+  }
+  const int tb = threads == 160 ? 160 : 128;
+  if (dbg) k_pair_f32<false, true><<<nwork, tb, 0, st>>>(P, work, nwork);
+  else if (vir) k_pair_f32<true, false><<<nwork, tb, 0, st>>>(P, work, nwork);
+  else k_pair_f32<false, false><<<nwork, tb, 0, st>>>(P, work, nwork);
 }
 
 }  // namespace gcme

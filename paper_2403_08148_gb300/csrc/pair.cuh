@@ -31,8 +31,8 @@
 
 namespace gcme {
 
-constexpr int kPairThreads = 128;
-constexpr int kPairCap = 2048;  // staged j beads per work item
+constexpr int kPairThreads = 128;  // block of the fine-cell kernel
+constexpr int kPairCap = 1536;  // staged j beads per work item (8 CTAs of 128 per SM)
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kTwoOverSqrtPi = 1.1283791670955126f;
 
@@ -179,14 +179,15 @@ __device__ __forceinline__ void pair_elec(const float4 *__restrict__ J, int t0, 
   }
 }
 
-// Debug only: in-cutoff images seen by a neutral i (no interaction, but part
-// of the neighbour set).
+// Debug only: in-cutoff images seen by a neutral i (or by every i when
+// every_i is set) -- no interaction of their own here, but part of the
+// neighbour set.
 template <bool SHIFT>
 __device__ __forceinline__ void pair_dump_images(const float4 *__restrict__ J, int t0, int t1,
                                                  int jsorted0, const float4 &xi, int isorted,
                                                  const PairSeg &sg, float rc2, const Pool &P,
-                                                 int s) {
-  if (xi.w != 0.0f) return;
+                                                 int s, bool every_i = false) {
+  if (!every_i && xi.w != 0.0f) return;
   for (int t = t0; t < t1; ++t) {
     float dx, dy, dz;
     if (!(pair_r2<SHIFT>(J[t], xi, sg, dx, dy, dz) < rc2)) continue;
@@ -219,25 +220,104 @@ __device__ __forceinline__ void pair_segment(const float4 *J, int t0, int t1, in
 #undef GCME_SEG
 }
 
-// One (home cell, z-offset) work item by the whole CTA.  Shared memory:
-// sj[kPairCap], seg[9], s_total[1].  Ends with a barrier.
+// Write back one lane's partial sums: fixed-point forces, warp-reduced
+// FP64 energies (core, electrostatics) and virial.
+template <bool VIR>
+__device__ __forceinline__ void pair_write(const Pool &P, const SysDesc &S, int s, bool valid,
+                                           int i, const PairAcc &A) {
+  const float cg = (float)(S.gc_fc * S.gc_pref);
+  const float lb = (float)S.lB;
+  if (valid) {
+    const int orig = P.sorted_idx[i];
+    atomic_add_fixed_f(force_ptr(P, S, orig, 0), -(cg * A.gx + lb * A.fx), (float)kFScale);
+    atomic_add_fixed_f(force_ptr(P, S, orig, 1), -(cg * A.gy + lb * A.fy), (float)kFScale);
+    atomic_add_fixed_f(force_ptr(P, S, orig, 2), -(cg * A.gz + lb * A.fz), (float)kFScale);
+  }
+  double eg = valid ? 0.5 * S.gc_pref * (double)A.eg : 0.0;
+  double er = valid ? 0.5 * S.lB * (double)A.ere : 0.0;
+  eg = warp_sum(eg);
+  er = warp_sum(er);
+  unsigned long long *acc = P.acc + (long long)s * kNacc;
+  if ((threadIdx.x & 31) == 0) {
+    if (eg != 0.0) atomic_add_fixed(acc + ACC_GC, eg, kEScale);
+    if (er != 0.0) atomic_add_fixed(acc + ACC_REAL, er, kEScale);
+  }
+  if (VIR) {
+    // W_ab = 1/2 sum_visits fs d_a d_b  with fs = (3/s) u or lB qq h
+    const double c1 = 0.5 * S.gc_fc * S.gc_pref, c2 = 0.5 * S.lB;
+    const int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      double v = valid ? c1 * (double)A.wg[map[k]] + c2 * (double)A.we[map[k]] : 0.0;
+      v = warp_sum(v);
+      if ((threadIdx.x & 31) == 0) atomic_add_fixed(P.vacc + (long long)s * 9 + k, v, kEScale);
+    }
+  }
+}
+
+// One staged range [t0, t1) of a segment, for one role: the core warps
+// evaluate the Gaussian core over the real beads (and, in debug mode, list
+// the in-cutoff images); the electrostatics warp evaluates the real-space
+// term of its charged home beads over the charged and image beads.
+template <bool VIR, bool DBG>
+__device__ __forceinline__ void pair_role_range(bool core_role, const float4 *J, int t0, int t1,
+                                                const PairSeg &sg, const float4 &xi, int i,
+                                                const SysDesc &S, float rc2, float gcc,
+                                                PairAcc &A, const Pool &P, int s) {
+  const int a0 = max(t0, min(t1, sg.a)), b0 = max(t0, min(t1, sg.b));
+#define GCME_ROLE(SHIFT, SELF)                                                                    \
+  if (core_role) {                                                                                \
+    pair_core<SHIFT, SELF, VIR, DBG>(J, a0, t1, sg.beg, xi, i, sg, rc2, gcc, A, P, s);            \
+    if (DBG) pair_dump_images<SHIFT>(J, t0, a0, sg.beg, xi, i, sg, rc2, P, s, true);              \
+  } else {                                                                                        \
+    pair_elec<SHIFT, SELF, VIR, false>(J, t0, b0, 0, sg.beg, xi, i, sg, S, rc2, A, P, s);         \
+  }
+  if (sg.self) {
+    GCME_ROLE(false, true)
+  } else if (sg.shifted) {
+    GCME_ROLE(true, false)
+  } else {
+    GCME_ROLE(false, false)
+  }
+#undef GCME_ROLE
+}
+
+// One work item by the whole CTA: a home cell and 9 (split 3) or 3
+// (split 9) of its 27 neighbour cells.  Shared memory: sj[kPairCap],
+// seg[9], s_total[1].  Ends with a barrier.
+//
+// Warp roles: warps 0 .. W-2 take the home cell's real beads 32 per warp
+// (Gaussian core over the staged real beads); warp W-1 takes its charged
+// real beads (real-space electrostatics over the staged charged and image
+// beads).  The two kinds of work run concurrently instead of one after the
+// other in the warp that holds the charged beads.
 template <bool VIR, bool DBG>
 __device__ __forceinline__ void dev_pair_f32_item(const Pool &P, const int2 *work, int w,
                                                   float4 *sj, PairSeg *seg, int *s_total_p) {
   const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int ncore = (blockDim.x >> 5) - 1;  // core warps
+  const bool core_role = warp < ncore;
   int &s_total = *s_total_p;
   const int s = work[w].x;
   const int code = work[w].y;
   const SysDesc &S = P.sys[s];
-  const int cloc = code / 3;
-  const int dzo = code % 3 - 1;
+  // split 3: item = (cell, dz), 9 neighbour cells; split 9: item =
+  // (cell, dy, dz), 3 neighbour cells along x
+  const int split = S.pair_split;
+  const int cloc = code / split;
+  const int part = code % split;
+  const int nseg = 27 / split;
+  const int dzo = (split == 3 ? part : part / 3) - 1;
+  const int dyf = split == 3 ? -2 : part % 3 - 1;  // fixed dy (split 9)
   const int nc0 = S.nc[0], nc1 = S.nc[1], nc2 = S.nc[2];
   const int cx = cloc % nc0, cy = (cloc / nc0) % nc1, cz = cloc / (nc0 * nc1);
   const long long hg = S.cell_off + cloc;
   const int hbeg = P.cell_start[hg], hend = P.cell_start[hg + 1];
-  const int himg = P.cell_nimg[hg];
-  if (tid < 9) {
-    const int dxo = tid % 3 - 1, dyo = tid / 3 - 1;
+  const int himg = P.cell_nimg[hg], hq = P.cell_nq[hg];
+  const int rbeg = hbeg + himg;  // first real home bead; charged reals end at hbeg + hq
+  if (tid < nseg) {
+    const int dxo = tid % 3 - 1, dyo = split == 3 ? tid / 3 - 1 : dyf;
     const int u[3] = {cx + dxo, cy + dyo, cz + dzo};
     const int ncv[3] = {nc0, nc1, nc2};
     int v[3], nn[3];
@@ -263,7 +343,7 @@ __device__ __forceinline__ void dev_pair_f32_item(const Pool &P, const int2 *wor
   __syncthreads();
   if (tid == 0) {
     int off = 0;
-    for (int k = 0; k < 9; ++k) {
+    for (int k = 0; k < nseg; ++k) {
       seg[k].soff = off;
       off += seg[k].n;
     }
@@ -272,7 +352,7 @@ __device__ __forceinline__ void dev_pair_f32_item(const Pool &P, const int2 *wor
   __syncthreads();
   const bool fits = s_total <= kPairCap;
   if (fits) {
-    for (int k = 0; k < 9; ++k) {
+    for (int k = 0; k < nseg; ++k) {
       const PairSeg &g = seg[k];
       for (int t = tid; t < g.n; t += blockDim.x) sj[g.soff + t] = P.xyzq_s[g.beg + t];
     }
@@ -280,22 +360,37 @@ __device__ __forceinline__ void dev_pair_f32_item(const Pool &P, const int2 *wor
   }
   const float rc2 = S.rc2f;
   const float gcc = S.gc_c2f;
-  for (int ib = hbeg + himg; ib < hend; ib += blockDim.x) {
-    const int i = ib + tid;
-    const bool valid = i < hend;
-    float4 xi = valid ? P.xyzq_s[i] : make_float4(1e30f, 1e30f, 1e30f, 0.0f);
+  // home-bead chunks of each role; the chunk loop runs the same number of
+  // times on every warp so that the staging barriers of large cells match
+  const int nreal = hend - rbeg, nqr = hbeg + hq - rbeg;
+  const int ncore_chunks = (nreal + 32 * ncore - 1) / (32 * ncore);
+  const int nel_chunks = (nqr + 31) / 32;
+  const int nchunk = max(ncore_chunks, nel_chunks);
+  for (int c = 0; c < nchunk; ++c) {
+    int i;
+    bool valid;
+    if (core_role) {
+      i = rbeg + c * 32 * ncore + tid;
+      valid = i < hend;
+    } else {
+      i = rbeg + c * 32 + lane;
+      valid = i < hbeg + hq;
+    }
+    const float4 xi = valid ? P.xyzq_s[i] : make_float4(1e30f, 1e30f, 1e30f, 0.0f);
+    const bool busy = __any_sync(0xffffffffu, valid);
     PairAcc A;
     A.eg = A.ere = A.gx = A.gy = A.gz = A.fx = A.fy = A.fz = 0.0f;
 #pragma unroll
     for (int k = 0; k < 6; ++k) A.wg[k] = A.we[k] = 0.0f;
-    const bool anyq = __syncthreads_or(valid && xi.w != 0.0f);
     if (fits) {
-      for (int k = 0; k < 9; ++k) {
-        const PairSeg g = seg[k];
-        pair_segment<VIR, DBG>(sj + g.soff, 0, g.n, g.beg, g, anyq, xi, i, S, rc2, gcc, A, P, s);
-      }
+      if (busy)
+        for (int k = 0; k < nseg; ++k) {
+          const PairSeg g = seg[k];
+          pair_role_range<VIR, DBG>(core_role, sj + g.soff, 0, g.n, g, xi, i, S, rc2, gcc, A, P,
+                                    s);
+        }
     } else {
-      for (int k = 0; k < 9; ++k) {
+      for (int k = 0; k < nseg; ++k) {
         const PairSeg g = seg[k];
         for (int c0 = 0; c0 < g.n; c0 += kPairCap) {
           const int c1 = min(g.n, c0 + kPairCap);
@@ -303,44 +398,152 @@ __device__ __forceinline__ void dev_pair_f32_item(const Pool &P, const int2 *wor
           for (int t = c0 + tid; t < c1; t += blockDim.x) sj[t - c0] = P.xyzq_s[g.beg + t];
           __syncthreads();
           // ranges are in segment coordinates; shift the staged base
-          pair_segment<VIR, DBG>(sj - c0, c0, c1, g.beg, g, anyq, xi, i, S, rc2, gcc, A, P, s);
+          if (busy)
+            pair_role_range<VIR, DBG>(core_role, sj - c0, c0, c1, g, xi, i, S, rc2, gcc, A, P, s);
         }
       }
     }
-    // --- write back ---
-    const float cg = (float)(S.gc_fc * S.gc_pref);
+    if (busy) pair_write<VIR>(P, S, s, valid, i, A);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Fine cells (side >= rc / 2), culled per warp.  A work item is one block of
+// up to 2 x 2 x 2 cells and one third of its neighbour z-range.  Each warp
+// takes 32 home beads in the block's Gray-code cell order (consecutive
+// cells adjacent, so a warp's beads span a 2 x 2 x 1 cell box), computes
+// their bounding box, and visits only the neighbour cells whose box lies
+// within rc (+1e-3 margin, far above FP32 rounding) of it; candidates are
+// read from the sorted positions in global memory (L1/L2 resident).  No
+// shared memory and no CTA barriers: warps work independently.
+// ---------------------------------------------------------------------------
+template <bool VIR, bool DBG>
+__device__ __forceinline__ void dev_pair_fine_item(const Pool &P, const int2 *work, int w) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int s = work[w].x, code = work[w].y;
+  const SysDesc &S = P.sys[s];
+  const int blk = code / 3, zpart = code % 3;
+  const int nc0 = S.nc[0], nc1 = S.nc[1], nc2 = S.nc[2];
+  const int bx = blk % S.nb[0], by = (blk / S.nb[0]) % S.nb[1], bz = blk / (S.nb[0] * S.nb[1]);
+  const int lo[3] = {2 * bx, 2 * by, 2 * bz};
+  const int wd[3] = {min(2, nc0 - lo[0]), min(2, nc1 - lo[1]), min(2, nc2 - lo[2])};
+  // home cells in Gray-code order; non-image bead ranges and their prefix
+  const int gray[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0},
+                          {0, 1, 1}, {1, 1, 1}, {1, 0, 1}, {0, 0, 1}};
+  int hb[8], hp[9];
+  hp[0] = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    int b = 0, n = 0;
+    if (gray[k][0] < wd[0] && gray[k][1] < wd[1] && gray[k][2] < wd[2]) {
+      const long long cg = S.cell_off + (lo[0] + gray[k][0]) +
+                           nc0 * ((lo[1] + gray[k][1]) + nc1 * (lo[2] + gray[k][2]));
+      b = P.cell_start[cg] + P.cell_nimg[cg];
+      n = P.cell_start[cg + 1] - b;
+    }
+    hb[k] = b;
+    hp[k + 1] = hp[k] + n;
+  }
+  const int total = hp[8];
+  // neighbour z-range [lo - 2, lo + wd + 1], this item's third of it
+  const int zspan = wd[2] + 4;
+  const int z0 = lo[2] - 2 + (zpart * zspan) / 3, z1 = lo[2] - 2 + ((zpart + 1) * zspan) / 3;
+  const float rc2 = S.rc2f, gcc = S.gc_c2f;
+  for (int c0 = warp * 32; c0 < total; c0 += nwarp * 32) {
+    const int idx = c0 + lane;
+    const bool valid = idx < total;
+    int i = 0;
+    if (valid) {
+      int k = 0;
+#pragma unroll
+      for (int q = 1; q < 8; ++q) k += idx >= hp[q];
+      i = hb[k] + (idx - hp[k]);
+    }
+    const float4 xi = valid ? P.xyzq_s[i] : make_float4(1e30f, 1e30f, 1e30f, 0.0f);
+    // warp bounding box of the valid beads
+    float bmin[3] = {valid ? xi.x : 3e38f, valid ? xi.y : 3e38f, valid ? xi.z : 3e38f};
+    float bmax[3] = {valid ? xi.x : -3e38f, valid ? xi.y : -3e38f, valid ? xi.z : -3e38f};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        bmin[a] = fminf(bmin[a], __shfl_xor_sync(0xffffffffu, bmin[a], o));
+        bmax[a] = fmaxf(bmax[a], __shfl_xor_sync(0xffffffffu, bmax[a], o));
+      }
+    const bool anyq = __any_sync(0xffffffffu, valid && xi.w != 0.0f);
+    PairAcc A;
+    A.eg = A.ere = A.gx = A.gy = A.gz = A.fx = A.fy = A.fz = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) A.wg[k] = A.we[k] = 0.0f;
+    for (int uz = z0; uz < z1; ++uz) {
+      const float gz_ = fmaxf(0.0f, fmaxf(uz * S.cside[2] - bmax[2], bmin[2] - (uz + 1) * S.cside[2]));
+      const float dz2 = gz_ * gz_;
+      if (dz2 > S.cull2) continue;
+      for (int uy = lo[1] - 2; uy < lo[1] + wd[1] + 2; ++uy) {
+        const float gy_ =
+            fmaxf(0.0f, fmaxf(uy * S.cside[1] - bmax[1], bmin[1] - (uy + 1) * S.cside[1]));
+        const float dyz2 = dz2 + gy_ * gy_;
+        if (dyz2 > S.cull2) continue;
+        for (int ux = lo[0] - 2; ux < lo[0] + wd[0] + 2; ++ux) {
+          const float gx_ =
+              fmaxf(0.0f, fmaxf(ux * S.cside[0] - bmax[0], bmin[0] - (ux + 1) * S.cside[0]));
+          if (dyz2 + gx_ * gx_ > S.cull2) continue;
+          const int u[3] = {ux, uy, uz};
+          const int ncv[3] = {nc0, nc1, nc2};
+          int v[3], nn[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            nn[a] = floor_div(u[a], ncv[a]);
+            v[a] = u[a] - nn[a] * ncv[a];
+          }
+          const long long cg = S.cell_off + v[0] + nc0 * (v[1] + nc1 * v[2]);
+          PairSeg sg;
+          sg.beg = P.cell_start[cg];
+          sg.n = P.cell_start[cg + 1] - sg.beg;
+          sg.a = P.cell_nimg[cg];
+          sg.b = P.cell_nq[cg];
+          sg.code = (nn[0] + 1) + 3 * (nn[1] + 1) + 9 * (nn[2] + 1);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) sg.sh[a] = (float)nn[a] * S.boxf[a];
+          sg.shifted = (nn[0] != 0 || nn[1] != 0 || nn[2] != 0);
+          // the cell can hold i itself only unshifted and inside the block
+          sg.self = !sg.shifted && ux >= lo[0] && ux < lo[0] + wd[0] && uy >= lo[1] &&
+                    uy < lo[1] + wd[1] && uz >= lo[2] && uz < lo[2] + wd[2];
+          pair_segment<VIR, DBG>(P.xyzq_s + sg.beg, 0, sg.n, sg.beg, sg, anyq, xi, i, S, rc2, gcc,
+                                 A, P, s);
+        }
+      }
+    }
+    const float cgf = (float)(S.gc_fc * S.gc_pref);
     const float lb = (float)S.lB;
     if (valid) {
       const int orig = P.sorted_idx[i];
-      const float Fx = -(cg * A.gx + lb * A.fx);
-      const float Fy = -(cg * A.gy + lb * A.fy);
-      const float Fz = -(cg * A.gz + lb * A.fz);
-      atomic_add_fixed_f(force_ptr(P, S, orig, 0), Fx, (float)kFScale);
-      atomic_add_fixed_f(force_ptr(P, S, orig, 1), Fy, (float)kFScale);
-      atomic_add_fixed_f(force_ptr(P, S, orig, 2), Fz, (float)kFScale);
+      atomic_add_fixed_f(force_ptr(P, S, orig, 0), -(cgf * A.gx + lb * A.fx), (float)kFScale);
+      atomic_add_fixed_f(force_ptr(P, S, orig, 1), -(cgf * A.gy + lb * A.fy), (float)kFScale);
+      atomic_add_fixed_f(force_ptr(P, S, orig, 2), -(cgf * A.gz + lb * A.fz), (float)kFScale);
     }
     double eg = valid ? 0.5 * S.gc_pref * (double)A.eg : 0.0;
     double er = valid ? 0.5 * S.lB * (double)A.ere : 0.0;
     eg = warp_sum(eg);
     er = warp_sum(er);
     unsigned long long *acc = P.acc + (long long)s * kNacc;
-    if ((tid & 31) == 0) {
+    if (lane == 0) {
       atomic_add_fixed(acc + ACC_GC, eg, kEScale);
       atomic_add_fixed(acc + ACC_REAL, er, kEScale);
     }
     if (VIR) {
-      // W_ab = 1/2 sum_visits fs d_a d_b  with fs = (3/s) u or lB qq h
       const double c1 = 0.5 * S.gc_fc * S.gc_pref, c2 = 0.5 * S.lB;
       const int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
-        double v = valid ? c1 * (double)A.wg[map[k]] + c2 * (double)A.we[map[k]] : 0.0;
-        v = warp_sum(v);
-        if ((tid & 31) == 0) atomic_add_fixed(P.vacc + (long long)s * 9 + k, v, kEScale);
+        double vv = valid ? c1 * (double)A.wg[map[k]] + c2 * (double)A.we[map[k]] : 0.0;
+        vv = warp_sum(vv);
+        if (lane == 0) atomic_add_fixed(P.vacc + (long long)s * 9 + k, vv, kEScale);
       }
     }
   }
-  __syncthreads();
 }
 
 }  // namespace gcme

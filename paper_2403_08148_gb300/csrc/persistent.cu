@@ -58,6 +58,7 @@ __device__ __forceinline__ bool grid_barrier(const Barrier &B) {
 struct PersistArgs {
   const int2 *pair_work;
   int n_pair_work;
+  int cell_factor;
   PmePlan plan;
   long long nsteps;
   Barrier bar;
@@ -100,7 +101,10 @@ __global__ void __launch_bounds__(128) k_persistent(Pool P, PersistArgs A) {
       dev_cellsort_block(P, c, (long long *)smem, (int *)(smem + sizeof(long long) * kSortCap));
     if (!grid_barrier(B)) return;
     // ---- K3 pair kernel and K5 spread (independent outputs)
-    {
+    if (A.cell_factor == 2) {
+      for (int w = blockIdx.x; w < A.n_pair_work; w += gridDim.x)
+        dev_pair_fine_item<false, false>(P, A.pair_work, w);
+    } else {
       float4 *sj = reinterpret_cast<float4 *>(smem);
       PairSeg *seg = reinterpret_cast<PairSeg *>(smem + sizeof(float4) * kPairCap);
       int *st = reinterpret_cast<int *>(smem + sizeof(float4) * kPairCap + sizeof(PairSeg) * 9);
@@ -143,8 +147,8 @@ size_t persistent_smem(const PmePlan &pl) {
   return std::max(pair, std::max(sort, fft));
 }
 
-int launch_persistent(const Pool &P, const int2 *pair_work, int n_pair_work, const PmePlan &pl,
-                      long long nsteps, unsigned int *bar_words, double timeout_s,
+int launch_persistent(const Pool &P, const int2 *pair_work, int n_pair_work, int cell_factor,
+                      const PmePlan &pl, long long nsteps, unsigned int *bar_words, double timeout_s,
                       cudaStream_t st) {
   const size_t smem = persistent_smem(pl);
   cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -157,6 +161,7 @@ int launch_persistent(const Pool &P, const int2 *pair_work, int n_pair_work, con
   PersistArgs A;
   A.pair_work = pair_work;
   A.n_pair_work = n_pair_work;
+  A.cell_factor = cell_factor;
   A.plan = pl;
   A.nsteps = nsteps;
   A.bar.count = bar_words;

@@ -1,0 +1,206 @@
+// tune.cu -- autotuner of the pair-kernel work shape and the PME FFT tiling.
+//
+// Candidates are timed with CUDA events on the caller's stream on the
+// actual system (or batch) at its current positions:
+//   pair kernel: 3 or 9 work items per home cell (9 or 3 neighbour cells
+//                each) x 128 or 160 threads (3 or 4 Gaussian-core warps +
+//                one electrostatics warp);
+//   PME:         lines per FFT tile along each axis in {4, 8, 16, 32, 64}
+//                (shared memory permitting), one axis at a time.
+// The fastest configuration is kept and recorded in a JSON-lines cache
+// (GCME_TUNE_CACHE, else $HOME/.cache/gcme_tune.jsonl) keyed by the GPU
+// name and the workload shape, so later runs apply it without timing.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include <sys/stat.h>
+
+#include "engine.h"
+
+namespace gcme {
+namespace {
+
+std::mutex g_cache_mu;
+
+std::string cache_path() {
+  const char *p = std::getenv("GCME_TUNE_CACHE");
+  if (p && *p) return p;
+  const char *h = std::getenv("HOME");
+  std::string dir = std::string(h && *h ? h : "/tmp") + "/.cache";
+  mkdir(dir.c_str(), 0755);  // may exist already
+  return dir + "/gcme_tune.jsonl";
+}
+
+struct Tuned {
+  int split = 0, threads = 0, lpb[3] = {0, 0, 0};
+  double pair_ms = 0, pme_ms = 0;
+};
+
+bool cache_lookup(const std::string &key, Tuned *t) {
+  std::lock_guard<std::mutex> g(g_cache_mu);
+  std::ifstream f(cache_path());
+  std::string line;
+  bool found = false;
+  while (std::getline(f, line)) {
+    const std::string kk = "\"key\": \"" + key + "\"";
+    if (line.find(kk) == std::string::npos) continue;
+    Tuned x;
+    const char *c = std::strstr(line.c_str(), "\"pair_split\":");
+    if (!c) continue;
+    if (std::sscanf(c,
+                    "\"pair_split\": %d, \"pair_threads\": %d, \"fft_lpb\": [%d, %d, %d], "
+                    "\"pair_ms\": %lf, \"pme_ms\": %lf",
+                    &x.split, &x.threads, &x.lpb[0], &x.lpb[1], &x.lpb[2], &x.pair_ms,
+                    &x.pme_ms) == 7) {
+      *t = x;  // the last entry for a key wins
+      found = true;
+    }
+  }
+  return found;
+}
+
+void cache_store(const std::string &key, const Tuned &t) {
+  std::lock_guard<std::mutex> g(g_cache_mu);
+  std::ofstream f(cache_path(), std::ios::app);
+  if (!f) return;
+  char buf[512];
+  std::snprintf(buf, sizeof buf,
+                "{\"key\": \"%s\", \"pair_split\": %d, \"pair_threads\": %d, \"fft_lpb\": [%d, %d, "
+                "%d], \"pair_ms\": %.6f, \"pme_ms\": %.6f}\n",
+                key.c_str(), t.split, t.threads, t.lpb[0], t.lpb[1], t.lpb[2], t.pair_ms,
+                t.pme_ms);
+  f << buf;
+}
+
+// median device time (ms) of `reps` runs of fn after one warm-up
+template <typename F>
+double time_ms(cudaStream_t st, int reps, F fn) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  fn();
+  std::vector<float> v;
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(a, st);
+    fn();
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    v.push_back(ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  std::sort(v.begin(), v.end());
+  return v[v.size() / 2];
+}
+
+}  // namespace
+
+int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms, double *pme_ms,
+                     bool *from_cache) {
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    set_error("cudaGetDeviceProperties failed");
+    return GCME_ERR_CUDA;
+  }
+  long long ngrid = 0, nq = 0, ncell = 0;
+  int geom = 0;
+  for (auto &S : hsys) {
+    ngrid += (long long)S.K[0] * S.K[1] * S.K[2];
+    nq += S.nq_ext;
+    ncell += S.ncell;
+    geom |= 1 << S.geometry;
+  }
+  std::ostringstream key;
+  key << prop.name << "|nsys=" << hsys.size() << "|n=" << n_real << "|ext=" << n_ext
+      << "|q=" << nq << "|cells=" << ncell << "|grid=" << ngrid << "|fp64=" << (int)fp64
+      << "|cf=" << cell_factor << "|geom=" << geom;
+  const bool remeasure = flags & 1, no_cache = flags & 2;
+  Tuned t;
+  *from_cache = false;
+  if (!remeasure && !no_cache && cache_lookup(key.str(), &t)) {
+    int rc = set_pair_config(t.split, t.threads);
+    for (int a = 0; !rc && a < 3; ++a) rc = set_fft_lpb(a, t.lpb[a]);
+    if (!rc) {
+      *pair_ms = t.pair_ms;
+      *pme_ms = t.pme_ms;
+      *from_cache = true;
+      return GCME_OK;
+    }
+  }
+  // cell lists and charges of the current state for the timed kernels
+  cudaMemsetAsync(Q.force, 0, sizeof(long long) * 3 * Q.n_real, st);
+  cudaMemsetAsync(Q.acc, 0, sizeof(unsigned long long) * Q.nsys * kNacc, st);
+  launch_cells(Q, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    set_error("autotune: cell list failed");
+    return GCME_ERR_CUDA;
+  }
+  const int reps = 5;
+  double best = 1e30;
+  int bs = pair_split, bt = pair_threads;
+  if (cell_factor == 1) {
+    for (int split : {3, 9})
+      for (int threads : {128, 160}) {
+        int rc = set_pair_config(split, threads);
+        if (rc) return rc;
+        double ms = time_ms(st, reps, [&] {
+          launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, false, false, st);
+        });
+        if (ms < best) {
+          best = ms;
+          bs = split;
+          bt = threads;
+        }
+      }
+    int rc = set_pair_config(bs, bt);
+    if (rc) return rc;
+  } else {
+    best = time_ms(st, reps, [&] {
+      launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, false, false, st);
+    });
+  }
+  const size_t rsz = fp64 ? sizeof(double2) : sizeof(float2);
+  double pme_best = 0;
+  for (int a = 0; a < 3; ++a) {
+    double ba = 1e30;
+    int bl = plan.lpb[a];
+    for (int lpb : {4, 8, 16, 32, 64}) {
+      if (2 * (size_t)lpb * plan.kmax[a] * rsz > kFftSmemLimit) continue;
+      int rc = set_fft_lpb(a, lpb);
+      if (rc) return rc;
+      double ms = time_ms(st, reps, [&] { launch_pme(Q, plan, fp64, false, st); });
+      if (ms < ba) {
+        ba = ms;
+        bl = lpb;
+      }
+    }
+    int rc = set_fft_lpb(a, bl);
+    if (rc) return rc;
+    pme_best = ba;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("autotune: ") + cudaGetErrorString(e));
+    return GCME_ERR_CUDA;
+  }
+  t.split = pair_split;
+  t.threads = pair_threads;
+  for (int a = 0; a < 3; ++a) t.lpb[a] = plan.lpb[a];
+  t.pair_ms = best;
+  t.pme_ms = pme_best;
+  if (!no_cache) cache_store(key.str(), t);
+  *pair_ms = best;
+  *pme_ms = pme_best;
+  return GCME_OK;
+}
+
+}  // namespace gcme

@@ -39,12 +39,13 @@ CASES = _small_cases()
 # --------------------------------------------------------------------------
 # K1/K2: cell list, bit-exact
 # --------------------------------------------------------------------------
+@pytest.mark.parametrize("factor", [1, 2])
 @pytest.mark.parametrize("name", ["bulk_n3000", "tiny_box_n120", "slab_pc", "poly_bonds"])
-def test_cell_list_bit_exact(name):
+def test_cell_list_bit_exact(name, factor):
     import torch
     g = lib()
     s = CASES[name]
-    sysg = g.System(ctx(), g.params_from(s), s.q, s.bonds)
+    sysg = g.System(ctx(), g.params_from(s, cell_factor=factor), s.q, s.bonds)
     info = sysg.info()
     dev = torch.device("cuda:0")
     pos = torch.tensor(s.pos, dtype=torch.float64, device=dev)
@@ -53,7 +54,7 @@ def test_cell_list_bit_exact(name):
     sysg.build_cells(pos, cs, si)
     torch.cuda.synchronize()
     epos, eq, etype, _ = oracle.electrostatic_beads(s)
-    nc = oracle.cell_counts(s.box, s.rc)
+    nc = oracle.cell_counts(s.box, s.rc, factor=info.cell_factor)
     assert list(nc) == list(info.nc)
     _, start, order = oracle.cell_list(epos, s.box, nc, oracle.bead_classes(s))
     assert np.array_equal(cs.cpu().numpy(), start)
@@ -63,14 +64,15 @@ def test_cell_list_bit_exact(name):
 # --------------------------------------------------------------------------
 # K3 neighbour set, bit-exact
 # --------------------------------------------------------------------------
+@pytest.mark.parametrize("factor", [1, 2])
 @pytest.mark.parametrize("name,prec", [("bulk_n3000", 0), ("tiny_box_n120", 0),
                                        ("box_2cells_n700", 0), ("slab_pc", 0),
                                        ("bulk_n3000", 1), ("slab_pc", 1)])
-def test_pair_set_bit_exact(name, prec):
+def test_pair_set_bit_exact(name, prec, factor):
     import torch
     g = lib()
     s = CASES[name]
-    sysg = g.System(ctx(), g.params_from(s, prec), s.q, s.bonds)
+    sysg = g.System(ctx(), g.params_from(s, prec, cell_factor=factor), s.q, s.bonds)
     dev = torch.device("cuda:0")
     pos = torch.tensor(s.pos, dtype=torch.float64, device=dev)
     cap = 4_000_000
@@ -106,10 +108,11 @@ def _check(s, out, ref, f_tol, e_tol, per_term_tol):
     return ferr, eerr
 
 
+@pytest.mark.parametrize("factor", [1, 2])
 @pytest.mark.parametrize("name", list(CASES))
-def test_forces_fp32(name):
+def test_forces_fp32(name, factor):
     s = CASES[name]
-    out = gpu_forces(s, 0)
+    out = gpu_forces(s, 0, cell_factor=factor)
     ref = oracle.energy_forces(s)
     _check(s, out, ref, FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
 
@@ -137,6 +140,16 @@ def test_forces_deterministic():
     b = gpu_forces(s, 0)
     assert np.array_equal(a["fixed"], b["fixed"])
     assert a["energy"] == b["energy"]
+
+
+def test_cell_factors_give_identical_fixed_point_forces_up_to_fp32_order():
+    """Both pair-kernel decompositions compute the same pair set; their
+    FP32 per-thread summation orders differ, so forces agree to rounding."""
+    s = CASES["bulk_n3000"]
+    a = gpu_forces(s, 0, cell_factor=1)
+    b = gpu_forces(s, 0, cell_factor=2)
+    assert rel_rms(a["forces"], b["forces"]) < 1e-6
+    assert abs(a["energy"]["gc"] - b["energy"]["gc"]) < 1e-7 * abs(a["energy"]["gc"])
 
 
 def test_single_neutral_bead_and_kappa_beta_limit():
@@ -217,3 +230,31 @@ def test_step_fp32_polyelectrolyte():
     tot_g = e[8] + e[9]
     tot_o = hist[-1]["potential"] + hist[-1]["kinetic"]
     assert abs(tot_g - tot_o) / abs(tot_o) < 1e-5
+
+
+def test_autotune_keeps_parity_and_caches(tmp_path, monkeypatch):
+    """The autotuner times the candidate launch shapes, applies the fastest
+    (results stay within tolerance of the oracle) and records it in the
+    cache file, from which a second call applies it without timing."""
+    import torch
+    monkeypatch.setenv("GCME_TUNE_CACHE", str(tmp_path / "tune.jsonl"))
+    g = lib()
+    s = CASES["poly_bonds"]
+    sysg = g.System(ctx(), g.params_from(s), s.q, s.bonds)
+    pos = torch.tensor(s.pos, dtype=torch.float64, device="cuda:0")
+    t1 = sysg.autotune(pos)
+    assert t1["pair_split"] in (3, 9) and t1["pair_threads"] in (128, 160)
+    assert all(l in (4, 8, 16, 32, 64) for l in t1["fft_lpb"]) and not t1["from_cache"]
+    F = torch.zeros(3 * s.n, dtype=torch.int64, device="cuda:0")
+    E = torch.zeros(g.NTERMS, dtype=torch.float64, device="cuda:0")
+    sysg.forces(pos, F, E)
+    torch.cuda.synchronize()
+    f = F.cpu().numpy().reshape(3, -1).T.astype(np.float64) / g.FORCE_SCALE
+    ref = oracle.energy_forces(s)
+    assert rel_rms(f, ref["forces"]) <= FORCE_RTOL_FP32
+    assert abs(E[8].item() - ref["potential"]) <= ENERGY_RTOL_FP32 * abs(ref["potential"])
+    sys2 = g.System(ctx(), g.params_from(s), s.q, s.bonds)
+    t2 = sys2.autotune(pos)
+    assert t2["from_cache"] and t2["pair_split"] == t1["pair_split"]
+    assert t2["fft_lpb"] == t1["fft_lpb"]
+    assert (tmp_path / "tune.jsonl").read_text().count("pair_split") == 1
