@@ -285,7 +285,8 @@ def run_gcme(args, ws, rank, local):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": workload_config(s), "steps_per_s": steps_per_s,
            "pair_interactions_per_step": pairs, "charged_pairs_per_step": qq,
-           "phase_ms": dict(zip(("kick_drift", "cells", "pair", "pme", "bonded", "kick_energy"),
+           "phase_ms": dict(zip(("kick_drift", "cells", "pair", "pme_concurrent", "bonded",
+                                 "slab_kick_energy"),
                                 [round(float(x), 5) for x in phase])),
            "warm_l2_ms_per_step": warm_ms,
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": s.n * 3 * (8 + 4),

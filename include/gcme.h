@@ -216,8 +216,9 @@ int gcme_step_f64(gcme_sys *sys, double *d_pos, double *d_vel, int64_t nsteps,
 
 /* Device time of the phases of the most recent completed step (the caller
  * synchronises first), measured by CUDA events captured in the step graph:
- * h_ms[0] half kick + drift, [1] cell list, [2] pair kernel, [3] PME,
- * [4] bonds/walls/slab, [5] half kick + energies (nphase >= 6).  *kernels
+ * h_ms[0] half kick + drift, [1] cell list, [2] pair kernel, [3] PME (a
+ * branch on a side stream concurrent with [2] and [4]), [4] bonds/walls,
+ * [5] Yeh-Berkowitz + half kick + energies after the join (nphase >= 6).  *kernels
  * (may be NULL) receives the number of kernel launches in one step. */
 #define GCME_NPHASE 6
 int gcme_step_phase_ms(gcme_sys *sys, float *h_ms, int32_t nphase, int32_t *kernels);

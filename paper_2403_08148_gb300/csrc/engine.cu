@@ -150,6 +150,9 @@ Engine::~Engine() {
   for (auto e : phase_ev)
     if (e) cudaEventDestroy(e);
   if (capture_stream) cudaStreamDestroy(capture_stream);
+  if (side_stream) cudaStreamDestroy(side_stream);
+  if (fork_ev) cudaEventDestroy(fork_ev);
+  if (join_ev) cudaEventDestroy(join_ev);
   if (arena_) cudaFree(arena_);
 }
 
@@ -537,9 +540,31 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   GCME_CK(cudaMemset(P.energy, 0, sizeof(double) * ns * GCME_NTERMS));
   GCME_CK(cudaMemset(P.virial, 0, sizeof(double) * ns * 9));
   GCME_CK(cudaStreamCreateWithFlags(&capture_stream, cudaStreamNonBlocking));
+  {
+    // the PME branch is the longer one: highest priority so its short,
+    // dependent kernels take free SM slots ahead of the pair kernel's CTAs
+    int least = 0, greatest = 0;
+    GCME_CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    GCME_CK(cudaStreamCreateWithPriority(&side_stream, cudaStreamNonBlocking, greatest));
+  }
+  GCME_CK(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+  GCME_CK(cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming));
   static std::once_flag once[64];
   std::call_once(once[dev & 63], [] { pme_set_smem_limits(); });
   return GCME_OK;
+}
+
+// The PME branch (spread, FFTs, gather) is independent of the pair and
+// bonded kernels until the Yeh-Berkowitz and kick kernels: it runs on a
+// side stream forked after the cell list and joined before them, so its
+// latency-bound passes fill the SMs the pair kernel leaves idle.
+void Engine::fork_pme(const Pool &Q, cudaStream_t st, bool vir, bool timed) {
+  cudaEventRecord(fork_ev, st);
+  cudaStreamWaitEvent(side_stream, fork_ev, 0);
+  if (timed) cudaEventRecordWithFlags(phase_ev[5], side_stream, cudaEventRecordExternal);
+  launch_pme(Q, plan, fp64, vir, side_stream);
+  if (timed) cudaEventRecordWithFlags(phase_ev[6], side_stream, cudaEventRecordExternal);
+  cudaEventRecord(join_ev, side_stream);
 }
 
 void Engine::enqueue_forces(const Pool &Q, cudaStream_t st, bool vir, bool dbg) {
@@ -547,10 +572,14 @@ void Engine::enqueue_forces(const Pool &Q, cudaStream_t st, bool vir, bool dbg) 
   cudaMemsetAsync(Q.acc, 0, sizeof(unsigned long long) * Q.nsys * kNacc, st);
   if (vir) cudaMemsetAsync(Q.vacc, 0, sizeof(unsigned long long) * Q.nsys * 9, st);
   launch_cells(Q, st);
-  launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, vir, dbg, st);
-  if (dbg) return;
-  launch_pme(Q, plan, fp64, vir, st);
+  if (dbg) {
+    launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, vir, dbg, st);
+    return;
+  }
+  fork_pme(Q, st, vir, false);
+  launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, vir, false, st);
   launch_bonded(Q, vir, st);
+  cudaStreamWaitEvent(st, join_ev, 0);
   launch_slab_apply(Q, st);
 }
 
@@ -563,16 +592,17 @@ void Engine::enqueue_step(const Pool &Q, cudaStream_t st) {
   cudaMemsetAsync(Q.acc, 0, sizeof(unsigned long long) * Q.nsys * kNacc, st);
   launch_cells(Q, st);
   if (ev) cudaEventRecordWithFlags(phase_ev[2], st, cudaEventRecordExternal);
+  fork_pme(Q, st, false, ev);
   launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, false, false, st);
   if (ev) cudaEventRecordWithFlags(phase_ev[3], st, cudaEventRecordExternal);
-  launch_pme(Q, plan, fp64, false, st);
-  if (ev) cudaEventRecordWithFlags(phase_ev[4], st, cudaEventRecordExternal);
   launch_bonded(Q, false, st);
+  if (ev) cudaEventRecordWithFlags(phase_ev[4], st, cudaEventRecordExternal);
+  cudaStreamWaitEvent(st, join_ev, 0);
+  if (ev) cudaEventRecordWithFlags(phase_ev[7], st, cudaEventRecordExternal);
   launch_slab_apply(Q, st);
-  if (ev) cudaEventRecordWithFlags(phase_ev[5], st, cudaEventRecordExternal);
   launch_kick(Q, fp64, st);
   launch_finalize(Q, false, st);
-  if (ev) cudaEventRecordWithFlags(phase_ev[6], st, cudaEventRecordExternal);
+  if (ev) cudaEventRecordWithFlags(phase_ev[8], st, cudaEventRecordExternal);
 }
 
 int Engine::step_graph(const Pool &Q, cudaGraphExec_t *out) {
@@ -927,12 +957,15 @@ int gcme_step_f64(gcme_sys *sys, double *d_pos, double *d_vel, int64_t nsteps, d
 static int phase_ms(Engine &eng, float *h_ms, int32_t nphase, int32_t *kernels) {
   if (kernels) *kernels = eng.step_kernels;
   if (!h_ms) return GCME_OK;
-  if (nphase < Engine::kNPhaseEv - 1 || !eng.phase_ev[0]) {
+  if (nphase < 6 || !eng.phase_ev[0]) {
     set_error("no captured step yet, or output shorter than the phase count");
     return GCME_ERR_INVALID;
   }
-  for (int k = 0; k + 1 < Engine::kNPhaseEv; ++k)
-    GCME_TRY_CK(cudaEventElapsedTime(&h_ms[k], eng.phase_ev[k], eng.phase_ev[k + 1]));
+  // [0] kick+drift, [1] cells, [2] pair kernel, [3] PME branch (side
+  // stream), [4] bonds/walls, [5] slab + kick + energies after the join
+  const int pairs[6][2] = {{0, 1}, {1, 2}, {2, 3}, {5, 6}, {3, 4}, {7, 8}};
+  for (int k = 0; k < 6; ++k)
+    GCME_TRY_CK(cudaEventElapsedTime(&h_ms[k], eng.phase_ev[pairs[k][0]], eng.phase_ev[pairs[k][1]]));
   return GCME_OK;
 }
 

@@ -42,6 +42,9 @@ class Engine {
   void enqueue_forces(const Pool &P, cudaStream_t st, bool vir, bool dbg);
   // enqueue one velocity-Verlet step (forces at P.pos must be current)
   void enqueue_step(const Pool &P, cudaStream_t st);
+  void fork_pme(const Pool &P, cudaStream_t st, bool vir, bool timed);
+  cudaStream_t side_stream = nullptr;  // PME branch
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 
   // graph of one step for the given state pointers (cached)
   int step_graph(const Pool &P, cudaGraphExec_t *out);
@@ -58,9 +61,10 @@ class Engine {
   int autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms, double *pme_ms,
                bool *from_cache);
   // Phase marks recorded inside the captured step graph: 0 start, 1 after
-  // the first half kick + drift, 2 after the cell list, 3 after the pair
-  // kernel, 4 after PME, 5 after bonds/walls/slab, 6 after kick + energies.
-  static constexpr int kNPhaseEv = 7;
+  // the first half kick + drift, 2 after the cell list (fork), 3 after the
+  // pair kernel, 4 after bonds/walls, 5/6 around the PME branch on the side
+  // stream, 7 after the join, 8 after slab, kick and energies.
+  static constexpr int kNPhaseEv = 9;
   cudaEvent_t phase_ev[kNPhaseEv] = {};
   int step_kernels = 0;  // kernel nodes in the step graph
   unsigned int *bar_words = nullptr;  // persistent-launch barrier state (4 words)
