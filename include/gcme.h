@@ -250,11 +250,13 @@ int gcme_debug_barrier_timeout(gcme_ctx *ctx, double timeout_s, gcme_stream_t st
 
 /* Tuned launch shapes: work items per home cell of the pair kernel (3: 9
  * neighbour cells each; 9: 3 each), pair block size (128 or 160 threads:
- * 3 or 4 Gaussian-core warps + one electrostatics warp), FFT lines per
- * tile per axis; device times of the chosen pair kernel and PME. */
+ * 3 or 4 Gaussian-core warps + one electrostatics warp), resident pair
+ * CTAs per SM fetching work items dynamically (0: one CTA per item), FFT
+ * lines per tile per axis; device times of a whole force evaluation and of
+ * the PME branch alone with the chosen shapes. */
 typedef struct gcme_tuning {
-  int32_t pair_split, pair_threads, fft_lpb[3], from_cache, cell_factor, pad;
-  double pair_ms, pme_ms;
+  int32_t pair_split, pair_threads, pair_ctas_per_sm, fft_lpb[3], from_cache, cell_factor;
+  double forces_ms, pme_ms;
 } gcme_tuning;
 
 #define GCME_TUNE_REMEASURE 1 /* ignore a cached entry, time again       */

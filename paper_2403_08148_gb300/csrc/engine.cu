@@ -188,11 +188,13 @@ void Engine::clear_graphs() {
   graph_objs_.clear();
 }
 
-int Engine::set_pair_config(int split, int threads) {
-  if ((split != 3 && split != 9) || (threads != 128 && threads != 160)) {
-    set_error("pair configuration must be split 3|9 and 128|160 threads");
+int Engine::set_pair_config(int split, int threads, int ctas_per_sm) {
+  if ((split != 3 && split != 9) || (threads != 128 && threads != 160) || ctas_per_sm < 0 ||
+      ctas_per_sm > 8) {
+    set_error("pair configuration must be split 3|9, 128|160 threads, 0..8 CTAs per SM");
     return GCME_ERR_INVALID;
   }
+  pair_ctas_per_sm = ctas_per_sm;
   std::vector<int2> pw = make_pair_work(split);
   pair_split = split;
   pair_threads = threads;
@@ -237,6 +239,7 @@ struct Carver {
 int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   device = dev;
   GCME_CK(cudaSetDevice(dev));
+  GCME_CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   const int ns = (int)specs.size();
   if (ns < 1) {
     set_error("empty batch");
@@ -442,6 +445,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   cv.add(&P.virial, (long long)ns * 9);
   cv.add(&pair_work, pair_cap);
   cv.add(&bar_words, 4);
+  cv.add(&pair_counter, 1);
   int2 *fw[3];
   for (int a = 0; a < 3; ++a) cv.add(&fw[a], fft_cap[a]);
   scratch_bytes = cv.off;
@@ -573,11 +577,13 @@ void Engine::enqueue_forces(const Pool &Q, cudaStream_t st, bool vir, bool dbg) 
   if (vir) cudaMemsetAsync(Q.vacc, 0, sizeof(unsigned long long) * Q.nsys * 9, st);
   launch_cells(Q, st);
   if (dbg) {
-    launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, vir, dbg, st);
+    launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, pair_ctas(), pair_counter,
+                vir, dbg, st);
     return;
   }
   fork_pme(Q, st, vir, false);
-  launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, vir, false, st);
+  launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, pair_ctas(), pair_counter,
+              vir, false, st);
   launch_bonded(Q, vir, st);
   cudaStreamWaitEvent(st, join_ev, 0);
   launch_slab_apply(Q, st);
@@ -593,7 +599,8 @@ void Engine::enqueue_step(const Pool &Q, cudaStream_t st) {
   launch_cells(Q, st);
   if (ev) cudaEventRecordWithFlags(phase_ev[2], st, cudaEventRecordExternal);
   fork_pme(Q, st, false, ev);
-  launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, false, false, st);
+  launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, pair_ctas(), pair_counter,
+              false, false, st);
   if (ev) cudaEventRecordWithFlags(phase_ev[3], st, cudaEventRecordExternal);
   launch_bonded(Q, false, st);
   if (ev) cudaEventRecordWithFlags(phase_ev[4], st, cudaEventRecordExternal);
@@ -1037,10 +1044,11 @@ static void fill_tuning(const Engine &eng, double pair_ms, double pme_ms, bool h
   if (!out) return;
   out->pair_split = eng.pair_split;
   out->pair_threads = eng.pair_threads;
+  out->pair_ctas_per_sm = eng.pair_ctas_per_sm;
   for (int a = 0; a < 3; ++a) out->fft_lpb[a] = eng.plan.lpb[a];
   out->from_cache = hit ? 1 : 0;
   out->cell_factor = eng.cell_factor;
-  out->pair_ms = pair_ms;
+  out->forces_ms = pair_ms;
   out->pme_ms = pme_ms;
 }
 

@@ -53,7 +53,7 @@ class Engine {
   int nsys() const { return (int)hsys.size(); }
   std::vector<int2> make_pair_work(int split) const;
   std::vector<int2> make_fft_work(int axis, int lpb) const;
-  int set_pair_config(int split, int threads);
+  int set_pair_config(int split, int threads, int ctas_per_sm);
   int set_fft_lpb(int axis, int lpb);
   void clear_graphs();
   // time candidate configurations on the current state and keep the
@@ -72,6 +72,10 @@ class Engine {
   int cell_factor = 1;  // 1: 27-cell stencil; 2: fine cells with culling
   int pair_split = 0;   // 3 or 9 work items per home cell (0: default)
   int pair_threads = kDefaultPairThreads;  // 128 (3 core warps) or 160 (4)
+  int pair_ctas_per_sm = 0;  // 0: one CTA per work item; else resident CTAs per SM fetching items
+  int n_sm = 152;
+  int *pair_counter = nullptr;  // dynamic work-item counter of the pair kernel
+  int pair_ctas() const { return pair_ctas_per_sm > 0 ? n_sm * pair_ctas_per_sm : 0; }
   int device = 0;
   std::vector<SysDesc> hsys;
   Pool P{};  // device pointers of the pooled arrays

@@ -14,8 +14,10 @@ struct PmePlan {
 };
 
 void launch_cells(const Pool &P, cudaStream_t st);
+// ctas: grid of the 27-cell kernel (CTAs loop over items fetched from
+// *counter, a device int the launch zeroes first)
 void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell_factor,
-                 int threads, bool vir, bool dbg, cudaStream_t st);
+                 int threads, int ctas, int *counter, bool vir, bool dbg, cudaStream_t st);
 void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStream_t st);
 void pme_set_smem_limits();
 void launch_bonded(const Pool &P, bool vir, cudaStream_t st);   // bonds, walls, dipole

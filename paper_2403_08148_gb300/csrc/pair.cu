@@ -3,6 +3,8 @@
 #include "pair.cuh"
 #include "kernels.h"
 
+#include <algorithm>
+
 namespace gcme {
 
 template <bool VIR, bool DBG>
@@ -10,13 +12,29 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_fine(Pool P, const int2 *
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) dev_pair_fine_item<VIR, DBG>(P, work, w);
 }
 
+// Work items are fetched dynamically from a counter (zeroed before the
+// launch): a CTA takes the next item when it finishes one, so heavy cells do
+// not leave SMs idle at the end, and a grid smaller than the SMs' capacity
+// leaves slots free for the concurrent PME branch.
 template <bool VIR, bool DBG>
-__global__ void __launch_bounds__(160, 6) k_pair_f32(Pool P, const int2 *work, int nwork) {
+__global__ void __launch_bounds__(160, 6) k_pair_f32(Pool P, const int2 *work, int nwork,
+                                                     int *counter) {
   __shared__ float4 sj[kPairCap];
   __shared__ PairSeg seg[9];
   __shared__ int s_total;
-  for (int w = blockIdx.x; w < nwork; w += gridDim.x)
+  __shared__ int s_item;
+  if (!counter) {  // static: one item per CTA (grid = items)
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x)
+      dev_pair_f32_item<VIR, DBG>(P, work, w, sj, seg, &s_total);
+    return;
+  }
+  while (true) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int w = s_item;
+    if (w >= nwork) break;
     dev_pair_f32_item<VIR, DBG>(P, work, w, sj, seg, &s_total);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -136,7 +154,7 @@ __global__ void __launch_bounds__(128) k_pair_f64(Pool P) {
 }
 
 void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell_factor,
-                 int threads, bool vir, bool dbg, cudaStream_t st) {
+                 int threads, int ctas, int *counter, bool vir, bool dbg, cudaStream_t st) {
   if (P.n_ext == 0) return;
   if (fp64) {
     int nb = (int)((P.n_ext + 127) / 128);
@@ -153,9 +171,14 @@ void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell
     return;
   }
   const int tb = threads == 160 ? 160 : 128;
-  if (dbg) k_pair_f32<false, true><<<nwork, tb, 0, st>>>(P, work, nwork);
-  else if (vir) k_pair_f32<true, false><<<nwork, tb, 0, st>>>(P, work, nwork);
-  else k_pair_f32<false, false><<<nwork, tb, 0, st>>>(P, work, nwork);
+  // ctas <= 0: one CTA per item; else a grid of ctas fetching items
+  const bool dyn = ctas > 0;
+  const int grid = dyn ? std::max(1, std::min(nwork, ctas)) : nwork;
+  if (dyn) cudaMemsetAsync(counter, 0, sizeof(int), st);
+  else counter = nullptr;
+  if (dbg) k_pair_f32<false, true><<<grid, tb, 0, st>>>(P, work, nwork, counter);
+  else if (vir) k_pair_f32<true, false><<<grid, tb, 0, st>>>(P, work, nwork, counter);
+  else k_pair_f32<false, false><<<grid, tb, 0, st>>>(P, work, nwork, counter);
 }
 
 }  // namespace gcme

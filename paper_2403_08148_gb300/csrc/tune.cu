@@ -4,9 +4,12 @@
 // actual system (or batch) at its current positions:
 //   pair kernel: 3 or 9 work items per home cell (9 or 3 neighbour cells
 //                each) x 128 or 160 threads (3 or 4 Gaussian-core warps +
-//                one electrostatics warp);
+//                one electrostatics warp) x {one CTA per work item, or 5,
+//                6 or 8 resident CTAs per SM fetching items dynamically so
+//                that the remaining slots host the concurrent PME branch};
 //   PME:         lines per FFT tile along each axis in {4, 8, 16, 32, 64}
-//                (shared memory permitting), one axis at a time.
+//                (shared memory permitting), one axis at a time;
+// each candidate timed on replays of the captured force-evaluation graph.
 // The fastest configuration is kept and recorded in a JSON-lines cache
 // (GCME_TUNE_CACHE, else $HOME/.cache/gcme_tune.jsonl) keyed by the GPU
 // name and the workload shape, so later runs apply it without timing.
@@ -39,7 +42,7 @@ std::string cache_path() {
 }
 
 struct Tuned {
-  int split = 0, threads = 0, lpb[3] = {0, 0, 0};
+  int split = 0, threads = 0, ctas = 0, lpb[3] = {0, 0, 0};
   double pair_ms = 0, pme_ms = 0;
 };
 
@@ -55,10 +58,10 @@ bool cache_lookup(const std::string &key, Tuned *t) {
     const char *c = std::strstr(line.c_str(), "\"pair_split\":");
     if (!c) continue;
     if (std::sscanf(c,
-                    "\"pair_split\": %d, \"pair_threads\": %d, \"fft_lpb\": [%d, %d, %d], "
-                    "\"pair_ms\": %lf, \"pme_ms\": %lf",
-                    &x.split, &x.threads, &x.lpb[0], &x.lpb[1], &x.lpb[2], &x.pair_ms,
-                    &x.pme_ms) == 7) {
+                    "\"pair_split\": %d, \"pair_threads\": %d, \"pair_ctas_per_sm\": %d, "
+                    "\"fft_lpb\": [%d, %d, %d], \"forces_ms\": %lf, \"pme_ms\": %lf",
+                    &x.split, &x.threads, &x.ctas, &x.lpb[0], &x.lpb[1], &x.lpb[2], &x.pair_ms,
+                    &x.pme_ms) == 8) {
       *t = x;  // the last entry for a key wins
       found = true;
     }
@@ -72,9 +75,10 @@ void cache_store(const std::string &key, const Tuned &t) {
   if (!f) return;
   char buf[512];
   std::snprintf(buf, sizeof buf,
-                "{\"key\": \"%s\", \"pair_split\": %d, \"pair_threads\": %d, \"fft_lpb\": [%d, %d, "
-                "%d], \"pair_ms\": %.6f, \"pme_ms\": %.6f}\n",
-                key.c_str(), t.split, t.threads, t.lpb[0], t.lpb[1], t.lpb[2], t.pair_ms,
+                "{\"key\": \"%s\", \"pair_split\": %d, \"pair_threads\": %d, "
+                "\"pair_ctas_per_sm\": %d, \"fft_lpb\": [%d, %d, %d], \"forces_ms\": %.6f, "
+                "\"pme_ms\": %.6f}\n",
+                key.c_str(), t.split, t.threads, t.ctas, t.lpb[0], t.lpb[1], t.lpb[2], t.pair_ms,
                 t.pme_ms);
   f << buf;
 }
@@ -127,7 +131,7 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
   Tuned t;
   *from_cache = false;
   if (!remeasure && !no_cache && cache_lookup(key.str(), &t)) {
-    int rc = set_pair_config(t.split, t.threads);
+    int rc = set_pair_config(t.split, t.threads, t.ctas);
     for (int a = 0; !rc && a < 3; ++a) rc = set_fft_lpb(a, t.lpb[a]);
     if (!rc) {
       *pair_ms = t.pair_ms;
@@ -136,57 +140,56 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
       return GCME_OK;
     }
   }
-  // cell lists and charges of the current state for the timed kernels
-  cudaMemsetAsync(Q.force, 0, sizeof(long long) * 3 * Q.n_real, st);
-  cudaMemsetAsync(Q.acc, 0, sizeof(unsigned long long) * Q.nsys * kNacc, st);
-  launch_cells(Q, st);
-  if (cudaStreamSynchronize(st) != cudaSuccess) {
-    set_error("autotune: cell list failed");
-    return GCME_ERR_CUDA;
-  }
-  const int reps = 5;
+  // Every candidate is timed on the whole force evaluation (cell list,
+  // pair kernel and bonds concurrent with the PME branch), since the
+  // concurrency is what the launch shapes trade against each other.
+  const int reps = 7;
+  // replays of the captured force graph, as production runs it
+  cudaGraphExec_t fg = nullptr;
+  auto forces = [&] { cudaGraphLaunch(fg, st); };
+  auto timed = [&]() -> double {
+    if (forces_graph(Q, &fg) != GCME_OK) return 1e30;
+    return time_ms(st, reps, forces);
+  };
   double best = 1e30;
-  int bs = pair_split, bt = pair_threads;
+  int bs = pair_split, bt = pair_threads, bc = pair_ctas_per_sm;
   if (cell_factor == 1) {
     for (int split : {3, 9})
-      for (int threads : {128, 160}) {
-        int rc = set_pair_config(split, threads);
-        if (rc) return rc;
-        double ms = time_ms(st, reps, [&] {
-          launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, false, false, st);
-        });
-        if (ms < best) {
-          best = ms;
-          bs = split;
-          bt = threads;
+      for (int threads : {128, 160})
+        for (int ctas : {0, 5, 6, 8}) {
+          if (threads == 160 && ctas > 6) continue;  // register-limited residency
+          int rc = set_pair_config(split, threads, ctas);
+          if (rc) return rc;
+          const double ms = timed();
+          if (ms < best) {
+            best = ms;
+            bs = split;
+            bt = threads;
+            bc = ctas;
+          }
         }
-      }
-    int rc = set_pair_config(bs, bt);
+    int rc = set_pair_config(bs, bt, bc);
     if (rc) return rc;
   } else {
-    best = time_ms(st, reps, [&] {
-      launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, false, false, st);
-    });
+    best = timed();
   }
   const size_t rsz = fp64 ? sizeof(double2) : sizeof(float2);
-  double pme_best = 0;
   for (int a = 0; a < 3; ++a) {
-    double ba = 1e30;
     int bl = plan.lpb[a];
     for (int lpb : {4, 8, 16, 32, 64}) {
       if (2 * (size_t)lpb * plan.kmax[a] * rsz > kFftSmemLimit) continue;
       int rc = set_fft_lpb(a, lpb);
       if (rc) return rc;
-      double ms = time_ms(st, reps, [&] { launch_pme(Q, plan, fp64, false, st); });
-      if (ms < ba) {
-        ba = ms;
+      const double ms = timed();
+      if (ms < best) {
+        best = ms;
         bl = lpb;
       }
     }
     int rc = set_fft_lpb(a, bl);
     if (rc) return rc;
-    pme_best = ba;
   }
+  const double pme_best = time_ms(st, reps, [&] { launch_pme(Q, plan, fp64, false, st); });
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("autotune: ") + cudaGetErrorString(e));
@@ -194,6 +197,7 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
   }
   t.split = pair_split;
   t.threads = pair_threads;
+  t.ctas = pair_ctas_per_sm;
   for (int a = 0; a < 3; ++a) t.lpb[a] = plan.lpb[a];
   t.pair_ms = best;
   t.pme_ms = pme_best;
