@@ -23,15 +23,26 @@ __global__ void __launch_bounds__(256) k_cellsort(Pool P) {
   dev_cellsort_block(P, blockIdx.x, key, cnt2);
 }
 
-void launch_cells(const Pool &P, cudaStream_t st) {
+void launch_bin(const Pool &P, cudaStream_t st) {
   if (P.n_ext == 0) return;
-  int tb = 256;
-  int nb = (int)((P.n_ext + tb - 1) / tb);
+  const int tb = 256;
+  const int nb = (int)((P.n_ext + tb - 1) / tb);
   cudaMemsetAsync(P.cell_cnt, 0, sizeof(int) * P.n_cells, st);
   k_bin<<<nb, tb, 0, st>>>(P);
+}
+
+void launch_sort(const Pool &P, cudaStream_t st) {
+  if (P.n_ext == 0) return;
+  const int tb = 256;
+  const int nb = (int)((P.n_ext + tb - 1) / tb);
   k_scan<<<1, 1024, 0, st>>>(P.cell_cnt, P.cell_start, P.n_cells);
   k_scatter<<<nb, tb, 0, st>>>(P);
   k_cellsort<<<(unsigned)P.n_cells, 256, 0, st>>>(P);
+}
+
+void launch_cells(const Pool &P, cudaStream_t st) {
+  launch_bin(P, st);
+  launch_sort(P, st);
 }
 
 }  // namespace gcme

@@ -382,7 +382,9 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   for (int a = 0; a < 3; ++a) {
     plan.kmax[a] = 0;
     for (auto &S : hsys) plan.kmax[a] = std::max(plan.kmax[a], S.K[a]);
-    plan.lpb[a] = std::max(8, std::min(64, 1024 / plan.kmax[a]));
+    int lpb = 64;  // largest power of two <= 1024 / K, within [8, 64]
+    while (lpb > 8 && lpb * plan.kmax[a] > 1024) lpb /= 2;
+    plan.lpb[a] = lpb;
   }
   std::vector<int2> fftw[3];
   int fft_cap[3];
@@ -558,10 +560,11 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   return GCME_OK;
 }
 
-// The PME branch (spread, FFTs, gather) is independent of the pair and
-// bonded kernels until the Yeh-Berkowitz and kick kernels: it runs on a
-// side stream forked after the cell list and joined before them, so its
-// latency-bound passes fill the SMs the pair kernel leaves idle.
+// The PME branch (spread, FFTs, gather) needs only the wrapped positions of
+// K1, and nothing of it is read by the pair or bonded kernels until the
+// Yeh-Berkowitz and kick kernels: it runs on a side stream forked right
+// after binning and joined before them, so its latency-bound passes overlap
+// the cell sort and fill the SMs the pair kernel leaves idle.
 void Engine::fork_pme(const Pool &Q, cudaStream_t st, bool vir, bool timed) {
   cudaEventRecord(fork_ev, st);
   cudaStreamWaitEvent(side_stream, fork_ev, 0);
@@ -575,13 +578,15 @@ void Engine::enqueue_forces(const Pool &Q, cudaStream_t st, bool vir, bool dbg) 
   cudaMemsetAsync(Q.force, 0, sizeof(long long) * 3 * Q.n_real, st);
   cudaMemsetAsync(Q.acc, 0, sizeof(unsigned long long) * Q.nsys * kNacc, st);
   if (vir) cudaMemsetAsync(Q.vacc, 0, sizeof(unsigned long long) * Q.nsys * 9, st);
-  launch_cells(Q, st);
+  launch_bin(Q, st);
   if (dbg) {
+    launch_sort(Q, st);
     launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, pair_ctas(), pair_counter,
                 vir, dbg, st);
     return;
   }
   fork_pme(Q, st, vir, false);
+  launch_sort(Q, st);
   launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, pair_ctas(), pair_counter,
               vir, false, st);
   launch_bonded(Q, vir, st);
@@ -596,9 +601,10 @@ void Engine::enqueue_step(const Pool &Q, cudaStream_t st) {
   if (ev) cudaEventRecordWithFlags(phase_ev[1], st, cudaEventRecordExternal);
   cudaMemsetAsync(Q.force, 0, sizeof(long long) * 3 * Q.n_real, st);
   cudaMemsetAsync(Q.acc, 0, sizeof(unsigned long long) * Q.nsys * kNacc, st);
-  launch_cells(Q, st);
-  if (ev) cudaEventRecordWithFlags(phase_ev[2], st, cudaEventRecordExternal);
+  launch_bin(Q, st);
   fork_pme(Q, st, false, ev);
+  launch_sort(Q, st);
+  if (ev) cudaEventRecordWithFlags(phase_ev[2], st, cudaEventRecordExternal);
   launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, pair_ctas(), pair_counter,
               false, false, st);
   if (ev) cudaEventRecordWithFlags(phase_ev[3], st, cudaEventRecordExternal);

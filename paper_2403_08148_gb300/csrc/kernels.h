@@ -13,7 +13,9 @@ struct PmePlan {
   int kmax[3];
 };
 
-void launch_cells(const Pool &P, cudaStream_t st);
+void launch_cells(const Pool &P, cudaStream_t st);  // launch_bin + launch_sort
+void launch_bin(const Pool &P, cudaStream_t st);    // K1: wrap, cell ids, wrapped float4
+void launch_sort(const Pool &P, cudaStream_t st);   // K2: scan, scatter, per-cell order
 // ctas: grid of the 27-cell kernel (CTAs loop over items fetched from
 // *counter, a device int the launch zeroes first)
 void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell_factor,
