@@ -252,10 +252,12 @@ int gcme_debug_barrier_timeout(gcme_ctx *ctx, double timeout_s, gcme_stream_t st
  * neighbour cells each; 9: 3 each), pair block size (128 or 160 threads:
  * 3 or 4 Gaussian-core warps + one electrostatics warp), resident pair
  * CTAs per SM fetching work items dynamically (0: one CTA per item), FFT
- * lines per tile per axis; device times of a whole force evaluation and of
+ * lines per tile per axis, x-y plane passes (1) or per-axis passes (0);
+ * device times of a whole force evaluation and of
  * the PME branch alone with the chosen shapes. */
 typedef struct gcme_tuning {
-  int32_t pair_split, pair_threads, pair_ctas_per_sm, fft_lpb[3], from_cache, cell_factor;
+  int32_t pair_split, pair_threads, pair_ctas_per_sm, fft_lpb[3], fft_plane, from_cache,
+      cell_factor, pad;
   double forces_ms, pme_ms;
 } gcme_tuning;
 

@@ -54,12 +54,14 @@ class SysInfo(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("pair_split", ctypes.c_int32), ("pair_threads", ctypes.c_int32),
                 ("pair_ctas_per_sm", ctypes.c_int32), ("fft_lpb", ctypes.c_int32 * 3),
-                ("from_cache", ctypes.c_int32), ("cell_factor", ctypes.c_int32),
+                ("fft_plane", ctypes.c_int32), ("from_cache", ctypes.c_int32),
+                ("cell_factor", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("forces_ms", ctypes.c_double), ("pme_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {"pair_split": self.pair_split, "pair_threads": self.pair_threads,
                 "pair_ctas_per_sm": self.pair_ctas_per_sm, "fft_lpb": list(self.fft_lpb),
+                "fft_plane": bool(self.fft_plane),
                 "from_cache": bool(self.from_cache), "cell_factor": self.cell_factor,
                 "forces_ms": self.forces_ms, "pme_ms": self.pme_ms}
 

@@ -207,6 +207,21 @@ int Engine::set_pair_config(int split, int threads, int ctas_per_sm) {
   return GCME_OK;
 }
 
+bool Engine::plane_fits() const {
+  const size_t rsz = fp64 ? sizeof(double2) : sizeof(float2);
+  return plan.plane_elems > 0 && 2 * (size_t)plan.plane_elems * rsz <= kFftSmemLimit;
+}
+
+int Engine::set_fft_plane(bool on) {
+  if (on && !plane_fits()) {
+    set_error("x-y planes of this batch do not fit in shared memory");
+    return GCME_ERR_INVALID;
+  }
+  plan.use_plane = on ? 1 : 0;
+  clear_graphs();
+  return GCME_OK;
+}
+
 int Engine::set_fft_lpb(int axis, int lpb) {
   const size_t rsz = fp64 ? sizeof(double2) : sizeof(float2);
   if (axis < 0 || axis > 2 || lpb < kMinLpb || lpb > 64 ||
@@ -393,6 +408,14 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     plan.nwork[a] = (int)fftw[a].size();
     fft_cap[a] = (int)make_fft_work(a, kMinLpb).size();
   }
+  std::vector<int2> planes;
+  plan.plane_elems = 0;
+  for (int s = 0; s < ns; ++s) {
+    plan.plane_elems = std::max(plan.plane_elems, hsys[s].K[0] * hsys[s].K[1]);
+    for (int z = 0; z < hsys[s].K[2]; ++z) planes.push_back(make_int2(s, z));
+  }
+  plan.nplane = (int)planes.size();
+  plan.use_plane = plane_fits() ? 1 : 0;
   std::vector<int2> pw = make_pair_work(pair_split);
   n_pair_work = (int)pw.size();
   const int pair_cap = std::max(n_pair_work, (int)make_pair_work(9).size());
@@ -450,6 +473,8 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   cv.add(&pair_counter, 1);
   int2 *fw[3];
   for (int a = 0; a < 3; ++a) cv.add(&fw[a], fft_cap[a]);
+  int2 *d_planes = nullptr;
+  cv.add(&d_planes, plan.nplane);
   scratch_bytes = cv.off;
   cudaError_t e = cudaMalloc(&arena_, cv.off);
   if (e != cudaSuccess) {
@@ -472,6 +497,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   P.n_bond = nbond;
   P.n_grid = ngrid;
   for (int a = 0; a < 3; ++a) plan.work[a] = fw[a];
+  plan.plane_work = d_planes;
 
   // ---- host tables -> device
   std::vector<double> hq(nr);
@@ -538,6 +564,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   }
   GCME_CK(up(pair_work, pw.data(), sizeof(int2) * n_pair_work));
   for (int a = 0; a < 3; ++a) GCME_CK(up(fw[a], fftw[a].data(), sizeof(int2) * plan.nwork[a]));
+  GCME_CK(up(d_planes, planes.data(), sizeof(int2) * plan.nplane));
   if (own_state) {
     GCME_CK(cudaMemset(P.pos, 0, sizeof(double) * 3 * nr));
     GCME_CK(cudaMemset(P.vel, 0, (fp64 ? 8 : 4) * 3 * nr));
@@ -1052,6 +1079,7 @@ static void fill_tuning(const Engine &eng, double pair_ms, double pme_ms, bool h
   out->pair_threads = eng.pair_threads;
   out->pair_ctas_per_sm = eng.pair_ctas_per_sm;
   for (int a = 0; a < 3; ++a) out->fft_lpb[a] = eng.plan.lpb[a];
+  out->fft_plane = eng.plan.use_plane;
   out->from_cache = hit ? 1 : 0;
   out->cell_factor = eng.cell_factor;
   out->forces_ms = pair_ms;

@@ -55,6 +55,8 @@ class Engine {
   std::vector<int2> make_fft_work(int axis, int lpb) const;
   int set_pair_config(int split, int threads, int ctas_per_sm);
   int set_fft_lpb(int axis, int lpb);
+  bool plane_fits() const;
+  int set_fft_plane(bool on);
   void clear_graphs();
   // time candidate configurations on the current state and keep the
   // fastest (tune.cu); from_cache reports a hit of the tuning cache

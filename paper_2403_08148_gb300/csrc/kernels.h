@@ -11,6 +11,12 @@ struct PmePlan {
   int nwork[3];
   int lpb[3];
   int kmax[3];
+  // x-y plane passes (one CTA per z-plane of every system) when every
+  // plane fits in shared memory: 3 FFT launches instead of 5
+  const int2 *plane_work;
+  int nplane;
+  int use_plane;
+  int plane_elems;  // largest K0 * K1 of the batch
 };
 
 void launch_cells(const Pool &P, cudaStream_t st);  // launch_bin + launch_sort

@@ -114,13 +114,25 @@ __global__ void __launch_bounds__(128) k_persistent(Pool P, PersistArgs A) {
     for (long long g = gtid; g < P.n_q * 8; g += gthreads) dev_spread<float>(P, g);
     if (!grid_barrier(B)) return;
     // ---- K6/K7 FFT passes with the fused influence function
-    const int axes[5] = {0, 1, 2, 1, 0};
-    const int kinds[5] = {FFT_FWD_FROM_Q, FFT_FWD, FFT_FWD_INFL_INV, FFT_INV, FFT_INV};
-    for (int ps = 0; ps < 5; ++ps) {
-      const int ax = axes[ps];
-      for (int w = blockIdx.x; w < A.plan.nwork[ax]; w += gridDim.x)
-        dev_fft_item<float, false>(P, A.plan.work[ax], w, ax, kinds[ps], A.plan.lpb[ax], smem);
+    if (A.plan.use_plane) {
+      for (int w = blockIdx.x; w < A.plan.nplane; w += gridDim.x)
+        dev_fft_plane<float, false>(P, A.plan.plane_work, w, smem);
       if (!grid_barrier(B)) return;
+      for (int w = blockIdx.x; w < A.plan.nwork[2]; w += gridDim.x)
+        dev_fft_item<float, false>(P, A.plan.work[2], w, 2, FFT_FWD_INFL_INV, A.plan.lpb[2], smem);
+      if (!grid_barrier(B)) return;
+      for (int w = blockIdx.x; w < A.plan.nplane; w += gridDim.x)
+        dev_fft_plane<float, true>(P, A.plan.plane_work, w, smem);
+      if (!grid_barrier(B)) return;
+    } else {
+      const int axes[5] = {0, 1, 2, 1, 0};
+      const int kinds[5] = {FFT_FWD_FROM_Q, FFT_FWD, FFT_FWD_INFL_INV, FFT_INV, FFT_INV};
+      for (int ps = 0; ps < 5; ++ps) {
+        const int ax = axes[ps];
+        for (int w = blockIdx.x; w < A.plan.nwork[ax]; w += gridDim.x)
+          dev_fft_item<float, false>(P, A.plan.work[ax], w, ax, kinds[ps], A.plan.lpb[ax], smem);
+        if (!grid_barrier(B)) return;
+      }
     }
     // ---- K8 gather, K9 bonds, walls and dipole
     GRID_LOOP(g, P.n_q * 8) dev_gather<float>(P, g);
@@ -144,6 +156,7 @@ size_t persistent_smem(const PmePlan &pl) {
   size_t sort = sizeof(long long) * kSortCap + 16;
   size_t fft = 0;
   for (int a = 0; a < 3; ++a) fft = std::max(fft, 2 * (size_t)pl.lpb[a] * pl.kmax[a] * sizeof(float2));
+  if (pl.use_plane) fft = std::max(fft, 2 * (size_t)pl.plane_elems * sizeof(float2));
   return std::max(pair, std::max(sort, fft));
 }
 

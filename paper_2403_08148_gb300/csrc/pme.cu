@@ -10,6 +10,12 @@ __global__ void k_spread(Pool P) { dev_spread<R>(P, blockIdx.x * (long long)bloc
 template <typename R>
 __global__ void k_gather(Pool P) { dev_gather<R>(P, blockIdx.x * (long long)blockDim.x + threadIdx.x); }
 
+template <typename R, bool INV>
+__global__ void __launch_bounds__(512) k_fft_plane(Pool P, const int2 *work, int nwork) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) dev_fft_plane<R, INV>(P, work, w, smem_raw);
+}
+
 template <typename R, bool VIR>
 __global__ void __launch_bounds__(256) k_fft(Pool P, const int2 *work, int nwork, int axis, int kind,
                                              int lpb) {
@@ -26,20 +32,29 @@ void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStrea
   if (fp64) k_spread<double><<<nb, tb, 0, st>>>(P);
   else k_spread<float><<<nb, tb, 0, st>>>(P);
   const size_t rsz = fp64 ? sizeof(double2) : sizeof(float2);
-  const int axes[5] = {0, 1, 2, 1, 0};
-  const int kinds[5] = {FFT_FWD_FROM_Q, FFT_FWD, FFT_FWD_INFL_INV, FFT_INV, FFT_INV};
-  for (int ps = 0; ps < 5; ++ps) {
-    const int ax = axes[ps];
+  auto line_pass = [&](int ax, int kind) {
     const size_t shm = 2 * (size_t)pl.lpb[ax] * pl.kmax[ax] * rsz;
     const int nw = pl.nwork[ax];
-    if (nw == 0) continue;
+    if (nw == 0) return;
     if (fp64) {
-      if (vir) k_fft<double, true><<<nw, 256, shm, st>>>(P, pl.work[ax], nw, ax, kinds[ps], pl.lpb[ax]);
-      else k_fft<double, false><<<nw, 256, shm, st>>>(P, pl.work[ax], nw, ax, kinds[ps], pl.lpb[ax]);
+      if (vir) k_fft<double, true><<<nw, 256, shm, st>>>(P, pl.work[ax], nw, ax, kind, pl.lpb[ax]);
+      else k_fft<double, false><<<nw, 256, shm, st>>>(P, pl.work[ax], nw, ax, kind, pl.lpb[ax]);
     } else {
-      if (vir) k_fft<float, true><<<nw, 256, shm, st>>>(P, pl.work[ax], nw, ax, kinds[ps], pl.lpb[ax]);
-      else k_fft<float, false><<<nw, 256, shm, st>>>(P, pl.work[ax], nw, ax, kinds[ps], pl.lpb[ax]);
+      if (vir) k_fft<float, true><<<nw, 256, shm, st>>>(P, pl.work[ax], nw, ax, kind, pl.lpb[ax]);
+      else k_fft<float, false><<<nw, 256, shm, st>>>(P, pl.work[ax], nw, ax, kind, pl.lpb[ax]);
     }
+  };
+  if (pl.use_plane) {
+    const size_t shm = 2 * (size_t)pl.plane_elems * rsz;
+    if (fp64) k_fft_plane<double, false><<<pl.nplane, 512, shm, st>>>(P, pl.plane_work, pl.nplane);
+    else k_fft_plane<float, false><<<pl.nplane, 512, shm, st>>>(P, pl.plane_work, pl.nplane);
+    line_pass(2, FFT_FWD_INFL_INV);
+    if (fp64) k_fft_plane<double, true><<<pl.nplane, 512, shm, st>>>(P, pl.plane_work, pl.nplane);
+    else k_fft_plane<float, true><<<pl.nplane, 512, shm, st>>>(P, pl.plane_work, pl.nplane);
+  } else {
+    const int axes[5] = {0, 1, 2, 1, 0};
+    const int kinds[5] = {FFT_FWD_FROM_Q, FFT_FWD, FFT_FWD_INFL_INV, FFT_INV, FFT_INV};
+    for (int ps = 0; ps < 5; ++ps) line_pass(axes[ps], kinds[ps]);
   }
   if (fp64) k_gather<double><<<nb, tb, 0, st>>>(P);
   else k_gather<float><<<nb, tb, 0, st>>>(P);
@@ -51,6 +66,10 @@ void pme_set_smem_limits() {
   cudaFuncSetAttribute(k_fft<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_fft<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_fft<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_fft_plane<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_fft_plane<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_fft_plane<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_fft_plane<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
 }  // namespace gcme

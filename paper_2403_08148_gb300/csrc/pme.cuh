@@ -296,6 +296,94 @@ __device__ __forceinline__ long long line_elem(int axis, int K0, int K1, long lo
 
 enum { FFT_FWD_FROM_Q = 0, FFT_FWD = 1, FFT_FWD_INFL_INV = 2, FFT_INV = 3 };
 
+// Stockham transform of nl lines of length K held in shared memory, element
+// k of line l at A[l * ls + k * es] (the result uses the same layout).
+// Threads run line-fastest when lines are adjacent (ls == 1) and
+// element-fastest otherwise, so that a warp touches consecutive words.
+// Ping-pongs between A and B; returns the buffer holding the result.  All
+// threads of the CTA take part; every stage ends with a barrier.
+template <typename R, typename R2>
+__device__ __forceinline__ R2 *smem_fft(R2 *A, R2 *B, int nl, int K, int ls, int es,
+                                        const int *radix, int nstage, const R2 *tw, int sgn) {
+  const bool line_fast = ls == 1;
+  int Ns = 1;
+  for (int st = 0; st < nstage; ++st) {
+    const int Rd = radix[st];
+    const int T = K / Rd;
+    const int twstep = K / (Ns * Rd);
+    for (int t = threadIdx.x; t < nl * T; t += blockDim.x) {
+      const int li = line_fast ? t % nl : t / T;
+      const int j = line_fast ? t / nl : t % T;
+      const int k = j % Ns;
+      R2 v[5];
+      const R2 *in = A + li * ls;
+      for (int r = 0; r < Rd; ++r) {
+        R2 x = in[(j + r * T) * es];
+        if (r > 0 && k > 0) {
+          R2 wv = tw[(k * r * twstep) % K];
+          if (sgn > 0) wv.y = -wv.y;
+          x = cmul(x, wv);
+        }
+        v[r] = x;
+      }
+      dft_small<R, R2>(v, Rd, sgn);
+      R2 *out = B + li * ls;
+      const int od = (j / Ns) * Ns * Rd + k;
+      for (int q = 0; q < Rd; ++q) out[(od + q * Ns) * es] = v[q];
+    }
+    __syncthreads();
+    R2 *tmp = A;
+    A = B;
+    B = tmp;
+    Ns *= Rd;
+  }
+  return A;
+}
+
+// One z-plane (x and y passes) of one system by the whole CTA: forward from
+// the fixed-point charge grid (INV = false) or backward (INV = true) on the
+// complex grid.  smem: 2 * K0 * K1 complex values.  Ends with a barrier.
+template <typename R, bool INV>
+__device__ __forceinline__ void dev_fft_plane(const Pool &P, const int2 *work, int w,
+                                              unsigned char *smem_raw) {
+  using R2 = typename PmeT<R>::R2;
+  R2 *smem = reinterpret_cast<R2 *>(smem_raw);
+  R2 *cg_all = (R2 *)(sizeof(R) == 4 ? (void *)P.cgrid : (void *)P.cgrid64);
+  const R2 *tw_all = (const R2 *)(sizeof(R) == 4 ? (const void *)P.tw : (const void *)P.tw64);
+  const int s = work[w].x, z = work[w].y;
+  const SysDesc &S = P.sys[s];
+  const int K0 = S.K[0], K1 = S.K[1];
+  const int G2 = K0 * K1;
+  const long long base = S.grid_off + (long long)z * G2;
+  R2 *A = smem, *B = smem + G2;
+  for (int t = threadIdx.x; t < G2; t += blockDim.x) {
+    R2 v;
+    if (INV) {
+      v = cg_all[base + t];
+    } else {
+      v.x = (R)((double)(long long)P.qgrid[base + t] * (1.0 / PmeT<R>::qscale));
+      v.y = R(0);
+    }
+    A[t] = v;
+  }
+  __syncthreads();
+  const int sgn = INV ? +1 : -1;
+  R2 *res;
+  if (!INV) {
+    res = smem_fft<R, R2>(A, B, K1, K0, K0, 1, S.radix[0], S.nstage[0], tw_all + S.tw_off[0], sgn);
+    R2 *other = res == smem ? smem + G2 : smem;
+    res = smem_fft<R, R2>(res, other, K0, K1, 1, K0, S.radix[1], S.nstage[1], tw_all + S.tw_off[1],
+                          sgn);
+  } else {
+    res = smem_fft<R, R2>(A, B, K0, K1, 1, K0, S.radix[1], S.nstage[1], tw_all + S.tw_off[1], sgn);
+    R2 *other = res == smem ? smem + G2 : smem;
+    res = smem_fft<R, R2>(res, other, K1, K0, K0, 1, S.radix[0], S.nstage[0], tw_all + S.tw_off[0],
+                          sgn);
+  }
+  for (int t = threadIdx.x; t < G2; t += blockDim.x) cg_all[base + t] = res[t];
+  __syncthreads();
+}
+
 // One tile of lpb lines of one system along `axis` by the whole CTA (any
 // block size).  smem: 2 * lpb * kmax complex values.  Ends with a barrier.
 template <typename R, bool VIR>

@@ -8,7 +8,8 @@
 //                6 or 8 resident CTAs per SM fetching items dynamically so
 //                that the remaining slots host the concurrent PME branch};
 //   PME:         lines per FFT tile along each axis in {4, 8, 16, 32, 64}
-//                (shared memory permitting), one axis at a time;
+//                (shared memory permitting), one axis at a time, and x-y
+//                plane passes (one CTA per z-plane) vs per-axis passes;
 // each candidate timed on replays of the captured force-evaluation graph.
 // The fastest configuration is kept and recorded in a JSON-lines cache
 // (GCME_TUNE_CACHE, else $HOME/.cache/gcme_tune.jsonl) keyed by the GPU
@@ -42,7 +43,7 @@ std::string cache_path() {
 }
 
 struct Tuned {
-  int split = 0, threads = 0, ctas = 0, lpb[3] = {0, 0, 0};
+  int split = 0, threads = 0, ctas = 0, lpb[3] = {0, 0, 0}, plane = 0;
   double pair_ms = 0, pme_ms = 0;
 };
 
@@ -59,9 +60,10 @@ bool cache_lookup(const std::string &key, Tuned *t) {
     if (!c) continue;
     if (std::sscanf(c,
                     "\"pair_split\": %d, \"pair_threads\": %d, \"pair_ctas_per_sm\": %d, "
-                    "\"fft_lpb\": [%d, %d, %d], \"forces_ms\": %lf, \"pme_ms\": %lf",
-                    &x.split, &x.threads, &x.ctas, &x.lpb[0], &x.lpb[1], &x.lpb[2], &x.pair_ms,
-                    &x.pme_ms) == 8) {
+                    "\"fft_lpb\": [%d, %d, %d], \"fft_plane\": %d, \"forces_ms\": %lf, "
+                    "\"pme_ms\": %lf",
+                    &x.split, &x.threads, &x.ctas, &x.lpb[0], &x.lpb[1], &x.lpb[2], &x.plane,
+                    &x.pair_ms, &x.pme_ms) == 9) {
       *t = x;  // the last entry for a key wins
       found = true;
     }
@@ -76,10 +78,10 @@ void cache_store(const std::string &key, const Tuned &t) {
   char buf[512];
   std::snprintf(buf, sizeof buf,
                 "{\"key\": \"%s\", \"pair_split\": %d, \"pair_threads\": %d, "
-                "\"pair_ctas_per_sm\": %d, \"fft_lpb\": [%d, %d, %d], \"forces_ms\": %.6f, "
-                "\"pme_ms\": %.6f}\n",
-                key.c_str(), t.split, t.threads, t.ctas, t.lpb[0], t.lpb[1], t.lpb[2], t.pair_ms,
-                t.pme_ms);
+                "\"pair_ctas_per_sm\": %d, \"fft_lpb\": [%d, %d, %d], \"fft_plane\": %d, "
+                "\"forces_ms\": %.6f, \"pme_ms\": %.6f}\n",
+                key.c_str(), t.split, t.threads, t.ctas, t.lpb[0], t.lpb[1], t.lpb[2], t.plane,
+                t.pair_ms, t.pme_ms);
   f << buf;
 }
 
@@ -133,6 +135,7 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
   if (!remeasure && !no_cache && cache_lookup(key.str(), &t)) {
     int rc = set_pair_config(t.split, t.threads, t.ctas);
     for (int a = 0; !rc && a < 3; ++a) rc = set_fft_lpb(a, t.lpb[a]);
+    if (!rc) rc = set_fft_plane(t.plane != 0);
     if (!rc) {
       *pair_ms = t.pair_ms;
       *pme_ms = t.pme_ms;
@@ -189,6 +192,14 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
     int rc = set_fft_lpb(a, bl);
     if (rc) return rc;
   }
+  if (plane_fits()) {  // x-y plane passes vs per-axis line passes
+    const int cur = plan.use_plane;
+    int rc = set_fft_plane(!cur);
+    if (rc) return rc;
+    const double ms = timed();
+    if (ms < best) best = ms;
+    else if ((rc = set_fft_plane(cur)) != GCME_OK) return rc;
+  }
   const double pme_best = time_ms(st, reps, [&] { launch_pme(Q, plan, fp64, false, st); });
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -198,6 +209,7 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
   t.split = pair_split;
   t.threads = pair_threads;
   t.ctas = pair_ctas_per_sm;
+  t.plane = plan.use_plane;
   for (int a = 0; a < 3; ++a) t.lpb[a] = plan.lpb[a];
   t.pair_ms = best;
   t.pme_ms = pme_best;
