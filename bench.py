@@ -153,7 +153,7 @@ def pair_kernel_traffic():
 
 def kernel_sha():
     h = hashlib.sha256()
-    for f in ("pair.cu", "pair.cuh", "common.cuh"):
+    for f in ("pair.cu", "pair.cuh", "nlist.cu", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2403_08148_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -208,6 +208,8 @@ def run_gcme(args, ws, rank, local):
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     phase = np.zeros(6)
     clocks = ClockSampler(local)
+    info = sysg.info()
+    builds0 = info.list_builds
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -231,6 +233,7 @@ def run_gcme(args, ws, rank, local):
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(tt.item())
         torch.distributed.barrier()
+    builds = sysg.info().list_builds - builds0
     pairs1, qq1 = count_pairs(g, sysg, s, pos, dev)
     pairs = 0.5 * (pairs0 + pairs1)
     qq = 0.5 * (qq0 + qq1)
@@ -251,29 +254,36 @@ def run_gcme(args, ws, rank, local):
     # end to end through the public API with host buffers: every step copies
     # positions + velocities host -> device, runs gcme_step (which evaluates
     # the forces of the copied state and advances one step), and reads the
-    # energies back
-    hpos = torch.empty((s.n, 3), dtype=torch.float64).pin_memory()
-    hvel = torch.empty((s.n, 3), dtype=torch.float32).pin_memory()
+    # energies back.  The host states alternate between the initial one and
+    # the one after the timed steps (beads far more than half the list skin
+    # apart), so every step also rebuilds the neighbour list: the worst case.
+    hpos = [torch.empty((s.n, 3), dtype=torch.float64).pin_memory() for _ in range(2)]
+    hvel = [torch.empty((s.n, 3), dtype=torch.float32).pin_memory() for _ in range(2)]
     hE = torch.empty(g.NTERMS, dtype=torch.float64).pin_memory()
-    hpos.copy_(torch.from_numpy(s.pos))
-    hvel.copy_(torch.from_numpy(s.vel.astype(np.float32)))
+    hpos[0].copy_(torch.from_numpy(s.pos))
+    hvel[0].copy_(torch.from_numpy(s.vel.astype(np.float32)))
+    hpos[1].copy_(pos.view(-1, 3))
+    hvel[1].copy_(vel.view(-1, 3))
     Ke = max(10, K // 4)
+    eb0 = sysg.info().list_builds
     torch.cuda.synchronize()
     e0 = time.perf_counter()
-    for _ in range(Ke):
-        pos.copy_(hpos, non_blocking=True)
-        vel.copy_(hvel, non_blocking=True)
+    for k in range(Ke):
+        pos.copy_(hpos[k % 2].view_as(pos), non_blocking=True)
+        vel.copy_(hvel[k % 2].view_as(vel), non_blocking=True)
         sysg.step(pos, vel, 1, E)
         hE.copy_(E, non_blocking=True)
         stream.synchronize()
     e2e_s = (time.perf_counter() - e0) / Ke
     e2e_value = ws * pairs / e2e_s
+    e2e_builds = sysg.info().list_builds - eb0
 
     peaks = measured_peaks()
     flops = FLOP_GC_PAIR * pairs + FLOP_QQ_PAIR * qq
     fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
     achieved = flops / (pair_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_pair_f32", "achieved": round(achieved, 4),
+    kname = "k_pair_list" if info.pair_path == g.GCME_PAIR_LIST else "k_pair_f32"
+    roofline = {"bound": "alu", "kernel": kname, "achieved": round(achieved, 4),
                 "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 5),
                 "traffic": pair_kernel_traffic(),
                 "peak_source": "FP32 pipe: 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)",
@@ -292,7 +302,13 @@ def run_gcme(args, ws, rank, local):
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": s.n * 3 * (8 + 4),
                    "d2h_bytes_per_step": 8 * g.NTERMS,
                    "note": "gcme_step(1) per step from host state: force evaluation of the "
-                           "copied state + one step"},
+                           "copied state + one step" + (
+                               " (the alternating host states force a neighbour-list rebuild "
+                               "every step)" if info.pair_path == g.GCME_PAIR_LIST else ""),
+                   "list_builds_per_step": e2e_builds / Ke},
+           "pair_path": "verlet_list" if info.pair_path == g.GCME_PAIR_LIST else "cells27",
+           "list_builds_per_step": builds / K,
+           "list_stride": int(info.list_stride),
            "roofline": roofline, "clocks": clk, "gpu_launches": int(nkern) * K,
            "tuning": tuning,
            "wall_s_timed": t_wall}

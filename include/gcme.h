@@ -108,8 +108,25 @@ typedef struct gcme_params {
   int32_t cell_factor; /* cells of side >= rc / cell_factor: 1 (27-cell
                           stencil) or 2 (blocks of 2^3 cells with culling);
                           0 lets the library choose                        */
-  int32_t pad0;
+  int32_t pair_path;   /* GCME_PAIR_AUTO (0), GCME_PAIR_LIST or GCME_PAIR_CELLS */
 } gcme_params;
+
+/* Pair-kernel path of the FP32 precision (the FP64 path always scans cells):
+ * LIST keeps a Verlet neighbour list of every (j, image) within rc + 0.4
+ * (the skin), rebuilt from the cell list when some bead has moved more than
+ * half the skin since the last build, and evaluates the pair terms over it;
+ * CELLS scans the 27 neighbour cells every step.  Both give the same pair
+ * set (the FP32 in-cutoff rule on the wrapped positions of the step); the
+ * FP32 sums differ in order, hence in rounding.  The list sums each bead's
+ * terms in an order fixed by the pairs, so results do not depend on when
+ * the list was rebuilt.  AUTO takes CELLS (the faster path on dense
+ * soft-core fluids, where a bead has ~340 neighbours within rc and the
+ * list is rebuilt every few steps).  A system
+ * whose neighbour count exceeds the list capacity (about 1024 within
+ * rc + skin) is evaluated by the cell kernel instead, step by step. */
+#define GCME_PAIR_AUTO 0
+#define GCME_PAIR_LIST 1
+#define GCME_PAIR_CELLS 2
 
 /* Fill p with the paper's defaults (A = 25, sigma = a = 0.5, lB = 1.2053,
  * rc = 3, kappa = 0.87609, p = 5, dt = 0.01, k = 100, r0 = 1) and a cubic
@@ -230,6 +247,9 @@ typedef struct gcme_sys_info {
   int32_t nc[3];
   int32_t cell_factor;
   int64_t scratch_bytes;
+  int32_t pair_path;    /* path in use: GCME_PAIR_LIST or GCME_PAIR_CELLS */
+  int32_t list_stride;  /* list entries per bead and lane (4 lanes), 0 without list */
+  int64_t list_builds;  /* neighbour-list builds so far (synchronises the device) */
 } gcme_sys_info;
 int gcme_system_info(const gcme_sys *sys, gcme_sys_info *out);
 

@@ -8,5 +8,6 @@ entry point raises.
 from .binding import (Batch, Context, GcmeError, Params, Server, System, load,  # noqa: F401
                       build_cells_noalloc,
                       params_from, validate, FORCE_SCALE, NTERMS, TERM_NAMES,
-                      GCME_BULK, GCME_SLAB_NONMETAL, GCME_SLAB_IMAGE, GCME_FP32, GCME_FP64)
+                      GCME_BULK, GCME_SLAB_NONMETAL, GCME_SLAB_IMAGE, GCME_FP32, GCME_FP64,
+                      GCME_PAIR_AUTO, GCME_PAIR_LIST, GCME_PAIR_CELLS)
 from .builder import build, LIB  # noqa: F401

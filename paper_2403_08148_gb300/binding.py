@@ -17,6 +17,7 @@ from . import builder as _build
 
 GCME_BULK, GCME_SLAB_NONMETAL, GCME_SLAB_IMAGE = 0, 1, 2
 GCME_FP32, GCME_FP64 = 0, 1
+GCME_PAIR_AUTO, GCME_PAIR_LIST, GCME_PAIR_CELLS = 0, 1, 2
 NTERMS = 10
 TERM_NAMES = ("gc", "real", "recip", "corr", "self", "slab", "wall", "bond",
               "potential", "kinetic")
@@ -41,14 +42,16 @@ class Params(ctypes.Structure):
                 ("H", ctypes.c_double), ("wall_A", ctypes.c_double),
                 ("wall_sigma2", ctypes.c_double), ("bond_k", ctypes.c_double),
                 ("bond_r0", ctypes.c_double), ("cell_factor", ctypes.c_int32),
-                ("pad0", ctypes.c_int32)]
+                ("pair_path", ctypes.c_int32)]
 
 
 class SysInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("n_ext", ctypes.c_int64),
                 ("n_charged_ext", ctypes.c_int64), ("ncell", ctypes.c_int64),
                 ("nbonds", ctypes.c_int64), ("nc", ctypes.c_int32 * 3),
-                ("cell_factor", ctypes.c_int32), ("scratch_bytes", ctypes.c_int64)]
+                ("cell_factor", ctypes.c_int32), ("scratch_bytes", ctypes.c_int64),
+                ("pair_path", ctypes.c_int32), ("list_stride", ctypes.c_int32),
+                ("list_builds", ctypes.c_int64)]
 
 
 class Tuning(ctypes.Structure):
@@ -171,10 +174,12 @@ def _stream(stream) -> Optional[int]:
     return getattr(stream, "cuda_stream", stream)
 
 
-def params_from(s, precision: int = GCME_FP32, cell_factor: int = 0) -> Params:
+def params_from(s, precision: int = GCME_FP32, cell_factor: int = 0,
+                pair_path: int = GCME_PAIR_AUTO) -> Params:
     """gcme_params from a system description with the fields of synth.System."""
     p = Params()
     p.cell_factor = int(cell_factor)
+    p.pair_path = int(pair_path)
     for a in range(3):
         p.box[a] = float(s.box[a])
         p.K[a] = int(s.K[a])

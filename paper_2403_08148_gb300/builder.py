@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgcme.so")
-SOURCES = ["cells.cu", "pair.cu", "pme.cu", "misc.cu", "engine.cu", "server.cu", "noalloc.cu", "persistent.cu", "tune.cu"]
+SOURCES = ["cells.cu", "pair.cu", "nlist.cu", "pme.cu", "misc.cu", "engine.cu", "server.cu", "noalloc.cu",
+           "persistent.cu", "tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -7,8 +7,10 @@ namespace gcme {
 
 __global__ void k_bin(Pool P) { dev_bin(P, blockIdx.x * (long long)blockDim.x + threadIdx.x); }
 
-__global__ void __launch_bounds__(1024) k_scan(const int *cnt, int *start, long long n) {
+__global__ void __launch_bounds__(1024) k_scan(const int *cnt, int *start, long long n,
+                                              const int *gate) {
   __shared__ long long warp_tot[32];
+  if (gate && !*gate) return;
   dev_scan_block(cnt, start, n, warp_tot);
 }
 
@@ -20,6 +22,7 @@ __global__ void __launch_bounds__(256) k_cellsort(Pool P) {
   __shared__ long long key[kSortCap];
   __shared__ int cnt2[2];
   if (blockIdx.x >= P.n_cells) return;
+  if (P.gate && !*P.gate) return;
   dev_cellsort_block(P, blockIdx.x, key, cnt2);
 }
 
@@ -35,7 +38,7 @@ void launch_sort(const Pool &P, cudaStream_t st) {
   if (P.n_ext == 0) return;
   const int tb = 256;
   const int nb = (int)((P.n_ext + tb - 1) / tb);
-  k_scan<<<1, 1024, 0, st>>>(P.cell_cnt, P.cell_start, P.n_cells);
+  k_scan<<<1, 1024, 0, st>>>(P.cell_cnt, P.cell_start, P.n_cells, P.gate);
   k_scatter<<<nb, tb, 0, st>>>(P);
   k_cellsort<<<(unsigned)P.n_cells, 256, 0, st>>>(P);
 }

@@ -37,6 +37,11 @@ __device__ __forceinline__ void dev_bin(const Pool &P, long long g) {
   P.xyzq_u[g] = make_float4(__double2float_rn(w[0]), __double2float_rn(w[1]),
                             __double2float_rn(w[2]), (float)q);
   if (P.xyzq_u64) P.xyzq_u64[g] = make_dpos4(w[0], w[1], w[2], q);
+  if (P.img_now) {
+    // periodic image index: x = w + img L exactly up to the wrap rule
+#pragma unroll
+    for (int a = 0; a < 3; ++a) P.img_now[3 * g + a] = (int)rint((x[a] - w[a]) / S.box[a]);
+  }
   P.cell_of[g] = cell;
   P.slot[g] = atomicAdd(&P.cell_cnt[S.cell_off + cell], 1);
 }
@@ -80,6 +85,7 @@ __device__ __forceinline__ void dev_scan_block(const int *cnt, int *start, long 
 
 __device__ __forceinline__ void dev_scatter(const Pool &P, long long g) {
   if (g >= P.n_ext) return;
+  if (P.gate && !*P.gate) return;
   const SysDesc &S = P.sys[P.ext_sys[g]];
   int e = (int)(g - S.ext_off);
   P.sorted_idx[P.cell_start[S.cell_off + P.cell_of[g]] + P.slot[g]] = e;

@@ -95,6 +95,14 @@ struct SysDesc {
   int nb[3];
   float cside[3];      // cell side L / nc (FP32, for bounding-box culling)
   float cull2;         // (rc + 1e-3)^2: cells farther than this are skipped
+  float rl2f;          // (rc + skin)^2: neighbour-list cutoff
+  // The list kernel rounds every pair term to a multiple of 2^-fix_bits and
+  // sums integers, so the sums do not depend on the order of the terms;
+  // fix_bits is the largest b with every pair force, energy and virial term
+  // below 2^30 / 2^b (a bound from the potentials' maxima over r <= rc).
+  float fix_scale;     // 2^fix_bits
+  int fix_bits;
+  int pad3;
 };
 
 // Pooled device arrays.  Passed by value to every kernel.
@@ -149,6 +157,23 @@ struct Pool {
   // debug pair dump
   int *dbg_triples;
   long long dbg_cap;
+  // Verlet neighbour list (FP32 path).  Entry m of sorted slot g sits at
+  // nbr[((m / 4) * n_ext + g) * 4 + m % 4] (lane m % 4 of the bead's four
+  // takes it): sorted slot j | (n_x+1 | (n_y+1) << 2 | (n_z+1) << 4) << 25 |
+  // (j is an image) << 31, the charged and image j first.
+  int *nbr;
+  int *nbr_cnt;        // [n_ext] entries of each slot
+  int *nbr_nq;         // [n_ext] of which charged or image (the first ones)
+  int nbr_stride;      // entries per lane (a bead holds at most 4 x stride)
+  int pad4;
+  int *img_now;        // [3 n_ext] periodic image index of each bead this step
+  int *img_ref;        // [3 n_ext] the same at the last list build
+  int *dimg_s;         // per sorted slot: packed image change since the build
+  double *x_ref;       // [3 n_real] unwrapped positions at the last build
+  int *list_flags;     // [0] rebuild this step, [1] rebuild requested, [2] builds so far
+  int *list_ovf;       // [2 nsys] per system: list overflowed (cell kernel), next build's
+  const int *gate;     // if set, the cell-sort kernels run only when *gate != 0
+  double half_skin2;   // (skin / 2)^2: displacement that forces a rebuild
 };
 
 // ---------------------------------------------------------------------------

@@ -82,6 +82,34 @@ static std::vector<double> host_bsp_moduli(int p, int K) {
   return b;
 }
 
+// Fixed-point resolution of the list kernel's pair terms: the largest b
+// (<= 31) with every term below 2^30 units of 2^-b.  Bounds over r <= rc:
+// the Gaussian-core force (3/s) u r peaks at r = sqrt(s/3); the real-space
+// force lB z^2 |g'(r)| and energy lB z^2 g(r) (g decreasing from
+// g(0) = 2 (beta - kappa) / sqrt(pi)) are bounded by sampling r; the virial
+// terms by force x rc.
+static int pair_fix_bits(const SysDesc &S, double qmax) {
+  const double s2 = S.gc_expc > 0 ? 1.5 / S.gc_expc : 1.0;  // s = sigma_i^2 + sigma_j^2
+  const double f_gc = S.gc_fc * S.gc_pref * std::sqrt(s2 / 3.0) * std::exp(-0.5);
+  double dg = 0.0;
+  const int ns = 4096;
+  for (int k = 1; k <= ns; ++k) {
+    const double r = S.rc * k / ns;
+    const double g = (std::erf(S.beta * r) - std::erf(S.kappa * r)) / r;
+    const double dd = 2.0 / std::sqrt(kPi) *
+                      (S.beta * std::exp(-S.beta * S.beta * r * r) -
+                       S.kappa * std::exp(-S.kappa * S.kappa * r * r));
+    dg = std::max(dg, std::fabs((dd - g) / r));  // |g'(r)|
+  }
+  const double zz = S.lB * qmax * qmax;
+  const double f_el = zz * dg * 1.05;  // sampling margin
+  const double u_el = zz * 2.0 * std::fabs(S.beta - S.kappa) / std::sqrt(kPi);
+  const double f = f_gc + f_el;
+  const double bound = 1.01 * std::max(std::max(f * std::max(1.0, S.rc), S.gc_pref + u_el), 1e-30);
+  int b = (int)std::floor(std::log2(std::ldexp(1.0, 30) / bound));
+  return std::max(0, std::min(31, b));
+}
+
 std::string validate_spec(const SysSpec &sp) {
   const gcme_params &p = sp.p;
   char buf[256];
@@ -90,6 +118,8 @@ std::string validate_spec(const SysSpec &sp) {
   if ((int64_t)sp.q.size() != sp.n) return "charge array size mismatch";
   if (p.geometry < GCME_BULK || p.geometry > GCME_SLAB_IMAGE) return "unknown geometry";
   if (p.precision != GCME_FP32 && p.precision != GCME_FP64) return "unknown precision";
+  if (p.pair_path < GCME_PAIR_AUTO || p.pair_path > GCME_PAIR_CELLS)
+    return "pair_path must be 0 (auto), 1 (list) or 2 (cells)";
   if (!(p.rc > 0) || !(p.kappa > 0) || !(p.lB >= 0) || !(p.sigma > 0) || !(p.a > 0) || !(p.A >= 0))
     return "rc, kappa, sigma, a must be > 0 and lB, A >= 0";
   for (int a = 0; a < 3; ++a) {
@@ -277,6 +307,21 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   }
   if (cell_factor == 0) cell_factor = kDefaultCellFactor;
   if (pair_split != 3 && pair_split != 9) pair_split = kDefaultPairSplit;
+  int path = GCME_PAIR_AUTO;
+  for (auto &sp : specs) {
+    const int pp = sp.p.pair_path;
+    if (pp != GCME_PAIR_AUTO && pp != GCME_PAIR_LIST && pp != GCME_PAIR_CELLS) {
+      set_error("pair_path must be 0 (auto), 1 (list) or 2 (cells)");
+      return GCME_ERR_INVALID;
+    }
+    if (pp != GCME_PAIR_AUTO) {
+      if (path != GCME_PAIR_AUTO && path != pp) {
+        set_error("all systems of a batch must share one pair path");
+        return GCME_ERR_INVALID;
+      }
+      path = pp;
+    }
+  }
   for (auto &sp : specs) {
     std::string err = validate_spec(sp);
     if (!err.empty()) {
@@ -382,6 +427,12 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     for (int t = 0; t < 3; ++t) S.ser_hf[t] = (float)S.ser_h[t];
     S.betaf = (float)S.beta;
     S.kappaf = (float)p.kappa;
+    {
+      double qmax = 0.0;
+      for (double z : sp.q) qmax = std::max(qmax, std::fabs(z));
+      S.fix_bits = pair_fix_bits(S, qmax);
+      S.fix_scale = (float)std::ldexp(1.0, S.fix_bits);
+    }
     nr += S.n;
     ne += S.n_ext;
     nq += S.nq_ext;
@@ -393,6 +444,40 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   }
   n_real = nr;
   n_ext = ne;
+  // Neighbour lists: FP32 path, 27-cell stencil, and the two-cell build
+  // stencil must cover rc + skin (cells of side >= rc >= skin).
+  {
+    bool can = !fp64 && cell_factor == 1 && ne < (1LL << 25);
+    for (auto &sp : specs) can = can && sp.p.rc >= kListSkin;
+    if (path == GCME_PAIR_LIST && !can) {
+      set_error("pair_path LIST needs FP32, cell_factor 1, rc >= 0.4 and fewer than 2^25 beads");
+      return GCME_ERR_INVALID;
+    }
+    // AUTO takes the 27-cell kernel: on dense soft-core fluids (~340
+    // neighbours within rc, a rebuild every few steps) it is the faster path
+    use_list = can && path == GCME_PAIR_LIST;
+  }
+  // list entries per bead and lane: a quarter of the expected count within
+  // rc + skin at the densest system's mean fluid density (slabs: beads over
+  // the slab volume), times 1.6, plus 32
+  int list_stride = 0;
+  if (use_list) {
+    double need = 0.0;
+    for (int s = 0; s < ns; ++s) {
+      const SysDesc &S = hsys[s];
+      const double rl = S.rc + kListSkin;
+      double vol = S.V;
+      if (S.geometry != GCME_BULK && S.H > 0)
+        vol = std::min(vol, S.box[0] * S.box[1] * S.H);
+      const double rho = S.n / vol;
+      need = std::max(need, rho * 4.0 / 3.0 * kPi * rl * rl * rl);
+    }
+    list_stride = (int)std::ceil(1.6 * need / 4.0) + 32;
+    for (auto &S : hsys) {
+      const double rl = S.rc + kListSkin;
+      S.rl2f = (float)(rl * rl);
+    }
+  }
   // FFT plan and pair work lists (rebuilt by the autotuner)
   for (int a = 0; a < 3; ++a) {
     plan.kmax[a] = 0;
@@ -475,6 +560,17 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   for (int a = 0; a < 3; ++a) cv.add(&fw[a], fft_cap[a]);
   int2 *d_planes = nullptr;
   cv.add(&d_planes, plan.nplane);
+  if (use_list) {
+    cv.add(&P.nbr, (long long)list_stride * ne * 4);
+    cv.add(&P.nbr_cnt, ne);
+    cv.add(&P.nbr_nq, ne);
+    cv.add(&P.img_now, 3 * ne);
+    cv.add(&P.img_ref, 3 * ne);
+    cv.add(&P.dimg_s, ne);
+    cv.add(&P.x_ref, 3 * nr);
+    cv.add(&P.list_flags, 4);
+    cv.add(&P.list_ovf, 2 * (long long)ns);
+  }
   scratch_bytes = cv.off;
   cudaError_t e = cudaMalloc(&arena_, cv.off);
   if (e != cudaSuccess) {
@@ -498,6 +594,12 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   P.n_grid = ngrid;
   for (int a = 0; a < 3; ++a) plan.work[a] = fw[a];
   plan.plane_work = d_planes;
+  if (use_list) {
+    P.nbr_stride = list_stride;
+    P.gate = P.list_flags;
+    const double h = 0.5 * kListSkin - 1e-4;  // margin far above FP32 rounding of r
+    P.half_skin2 = h * h;
+  }
 
   // ---- host tables -> device
   std::vector<double> hq(nr);
@@ -570,6 +672,14 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     GCME_CK(cudaMemset(P.vel, 0, (fp64 ? 8 : 4) * 3 * nr));
   }
   GCME_CK(cudaMemset(P.force, 0, sizeof(long long) * 3 * nr));
+  if (use_list) {
+    // reference positions ~1e306: the first check requests a build
+    GCME_CK(cudaMemset(P.x_ref, 0x7f, sizeof(double) * 3 * nr));
+    GCME_CK(cudaMemset(P.list_flags, 0, sizeof(int) * 4));
+    GCME_CK(cudaMemset(P.list_ovf, 0, sizeof(int) * 2 * ns));
+    GCME_CK(cudaMemset(P.nbr_cnt, 0, sizeof(int) * ne));
+    GCME_CK(cudaMemset(P.nbr_nq, 0, sizeof(int) * ne));
+  }
   GCME_CK(cudaMemset(P.energy, 0, sizeof(double) * ns * GCME_NTERMS));
   GCME_CK(cudaMemset(P.virial, 0, sizeof(double) * ns * 9));
   GCME_CK(cudaStreamCreateWithFlags(&capture_stream, cudaStreamNonBlocking));
@@ -601,21 +711,53 @@ void Engine::fork_pme(const Pool &Q, cudaStream_t st, bool vir, bool timed) {
   cudaEventRecord(join_ev, side_stream);
 }
 
+Pool Engine::cell_only(const Pool &Q) const {
+  Pool C = Q;
+  C.gate = nullptr;
+  C.list_ovf = nullptr;
+  C.img_now = nullptr;
+  return C;
+}
+
+void Engine::request_rebuild(cudaStream_t st) {
+  if (use_list) cudaMemsetAsync(P.list_flags + 1, 1, sizeof(int), st);
+}
+
+long long Engine::list_builds() {
+  if (!use_list) return 0;
+  int v[4] = {0, 0, 0, 0};
+  if (cudaMemcpy(v, P.list_flags, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  return v[2];
+}
+
+// Cell sort and pair kernels.  With lists: the sort and the list build run
+// only on rebuild steps (device flag), the refresh every step, then the
+// list kernel, and the 27-cell kernel for the systems whose lists overflowed.
+void Engine::enqueue_sort_pairs(const Pool &Q, cudaStream_t st, bool vir, bool dbg, bool timed) {
+  launch_sort(Q, st);
+  if (use_list) {
+    launch_list_build(Q, st);
+    launch_list_refresh(Q, st);
+  }
+  if (timed) cudaEventRecordWithFlags(phase_ev[2], st, cudaEventRecordExternal);
+  if (use_list) launch_pair_list(Q, vir, dbg, st);
+  launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, pair_ctas(), pair_counter,
+              vir, dbg, st);
+  if (timed) cudaEventRecordWithFlags(phase_ev[3], st, cudaEventRecordExternal);
+}
+
 void Engine::enqueue_forces(const Pool &Q, cudaStream_t st, bool vir, bool dbg) {
   cudaMemsetAsync(Q.force, 0, sizeof(long long) * 3 * Q.n_real, st);
   cudaMemsetAsync(Q.acc, 0, sizeof(unsigned long long) * Q.nsys * kNacc, st);
   if (vir) cudaMemsetAsync(Q.vacc, 0, sizeof(unsigned long long) * Q.nsys * 9, st);
+  if (use_list) launch_list_check(Q, st);
   launch_bin(Q, st);
   if (dbg) {
-    launch_sort(Q, st);
-    launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, pair_ctas(), pair_counter,
-                vir, dbg, st);
+    enqueue_sort_pairs(Q, st, vir, true, false);
     return;
   }
   fork_pme(Q, st, vir, false);
-  launch_sort(Q, st);
-  launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, pair_ctas(), pair_counter,
-              vir, false, st);
+  enqueue_sort_pairs(Q, st, vir, false, false);
   launch_bonded(Q, vir, st);
   cudaStreamWaitEvent(st, join_ev, 0);
   launch_slab_apply(Q, st);
@@ -628,13 +770,10 @@ void Engine::enqueue_step(const Pool &Q, cudaStream_t st) {
   if (ev) cudaEventRecordWithFlags(phase_ev[1], st, cudaEventRecordExternal);
   cudaMemsetAsync(Q.force, 0, sizeof(long long) * 3 * Q.n_real, st);
   cudaMemsetAsync(Q.acc, 0, sizeof(unsigned long long) * Q.nsys * kNacc, st);
+  if (use_list) launch_list_check(Q, st);
   launch_bin(Q, st);
   fork_pme(Q, st, false, ev);
-  launch_sort(Q, st);
-  if (ev) cudaEventRecordWithFlags(phase_ev[2], st, cudaEventRecordExternal);
-  launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, pair_ctas(), pair_counter,
-              false, false, st);
-  if (ev) cudaEventRecordWithFlags(phase_ev[3], st, cudaEventRecordExternal);
+  enqueue_sort_pairs(Q, st, false, false, ev);
   launch_bonded(Q, false, st);
   if (ev) cudaEventRecordWithFlags(phase_ev[4], st, cudaEventRecordExternal);
   cudaStreamWaitEvent(st, join_ev, 0);
@@ -845,6 +984,11 @@ int gcme_system_info(const gcme_sys *sys, gcme_sys_info *out) {
   for (int a = 0; a < 3; ++a) out->nc[a] = S.nc[a];
   out->cell_factor = S.cell_factor;
   out->scratch_bytes = (int64_t)sys->eng.scratch_bytes;
+  gcme_sys *ms = const_cast<gcme_sys *>(sys);
+  out->pair_path = ms->eng.use_list ? GCME_PAIR_LIST : GCME_PAIR_CELLS;
+  out->list_stride = ms->eng.use_list ? ms->eng.P.nbr_stride : 0;
+  GCME_TRY_CK(cudaSetDevice(ms->eng.device));
+  out->list_builds = ms->eng.list_builds();
   return GCME_OK;
 }
 
@@ -856,9 +1000,10 @@ int gcme_build_cells(gcme_sys *sys, const double *d_pos, int32_t *d_cell_start,
   }
   cudaStream_t st = (cudaStream_t)stream;
   GCME_TRY_CK(cudaSetDevice(sys->eng.device));
-  Pool Q = sys->eng.P;
+  Pool Q = sys->eng.cell_only(sys->eng.P);
   Q.pos = const_cast<double *>(d_pos);
   launch_cells(Q, st);
+  sys->eng.request_rebuild(st);  // the lists index the previous cell order
   const SysDesc &S = sys->eng.hsys[0];
   if (d_cell_start)
     GCME_TRY_CK(cudaMemcpyAsync(d_cell_start, Q.cell_start, sizeof(int) * (S.ncell + 1),
@@ -1266,13 +1411,14 @@ int gcme_batch_step(gcme_batch *b, int64_t nsteps, int32_t mode, gcme_stream_t s
     return GCME_ERR_INVALID;
   }
   if (nsteps == 0) return GCME_OK;
-  int lr = launch_persistent(Q, b->eng.pair_work, b->eng.n_pair_work, b->eng.cell_factor,
+  int lr = launch_persistent(b->eng.cell_only(Q), b->eng.pair_work, b->eng.n_pair_work, b->eng.cell_factor,
                              b->eng.plan, nsteps, b->eng.bar_words, 2.0, st);
   if (lr != 0) {
     cudaError_t e = cudaGetLastError();
     set_error(std::string("persistent cooperative launch failed: ") + cudaGetErrorString(e));
     return GCME_ERR_CUDA;
   }
+  b->eng.request_rebuild(st);  // the persistent kernel re-sorted the cells
   unsigned int words[4] = {0, 0, 0, 0};
   GCME_TRY_CK(cudaMemcpyAsync(words, b->eng.bar_words, sizeof(words), cudaMemcpyDeviceToHost, st));
   GCME_TRY_CK(cudaStreamSynchronize(st));

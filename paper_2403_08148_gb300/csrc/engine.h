@@ -16,6 +16,9 @@ constexpr int kDefaultPairSplit = 9;
 constexpr int kDefaultPairThreads = 128;
 constexpr int kMinLpb = 4;                       // fewest FFT lines per tile
 constexpr size_t kFftSmemLimit = 200 * 1024;     // dynamic smem of k_fft
+// Verlet-list skin (bead diameters): the list holds every pair within
+// rc + skin and is rebuilt once a bead has moved more than skin / 2
+constexpr double kListSkin = 0.4;
 
 void set_error(const std::string &msg);
 
@@ -42,6 +45,14 @@ class Engine {
   void enqueue_forces(const Pool &P, cudaStream_t st, bool vir, bool dbg);
   // enqueue one velocity-Verlet step (forces at P.pos must be current)
   void enqueue_step(const Pool &P, cudaStream_t st);
+  // cell sort (gated by the rebuild flag with lists) and the pair kernels
+  void enqueue_sort_pairs(const Pool &P, cudaStream_t st, bool vir, bool dbg, bool timed);
+  // make the next force evaluation rebuild the neighbour lists (after the
+  // cell order was changed outside the list path)
+  void request_rebuild(cudaStream_t st);
+  // the pooled arrays as the cell-only kernels see them (no list fields)
+  Pool cell_only(const Pool &Q) const;
+  long long list_builds();  // synchronises the device
   void fork_pme(const Pool &P, cudaStream_t st, bool vir, bool timed);
   cudaStream_t side_stream = nullptr;  // PME branch
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
@@ -73,6 +84,7 @@ class Engine {
   unsigned int *bar_words = nullptr;  // persistent-launch barrier state (4 words)
   bool fp64 = false;
   int cell_factor = 1;  // 1: 27-cell stencil; 2: fine cells with culling
+  bool use_list = false;  // FP32 pair terms over Verlet neighbour lists
   int pair_split = 0;   // 3 or 9 work items per home cell (0: default)
   int pair_threads = kDefaultPairThreads;  // 128 (3 core warps) or 160 (4)
   int pair_ctas_per_sm = 0;  // 0: one CTA per work item; else resident CTAs per SM fetching items

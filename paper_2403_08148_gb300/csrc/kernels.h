@@ -26,6 +26,14 @@ void launch_sort(const Pool &P, cudaStream_t st);   // K2: scan, scatter, per-ce
 // *counter, a device int the launch zeroes first)
 void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell_factor,
                  int threads, int ctas, int *counter, bool vir, bool dbg, cudaStream_t st);
+// Verlet neighbour list (nlist.cu): rebuild decision (clears the flag,
+// then sets it when a bead moved more than skin/2 since the last build or a
+// rebuild is pending), the gated build, the per-step refresh of the sorted
+// positions and image changes, and the pair kernel over the lists.
+void launch_list_check(const Pool &P, cudaStream_t st);
+void launch_list_build(const Pool &P, cudaStream_t st);
+void launch_list_refresh(const Pool &P, cudaStream_t st);
+void launch_pair_list(const Pool &P, bool vir, bool dbg, cudaStream_t st);
 void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStream_t st);
 void pme_set_smem_limits();
 void launch_bonded(const Pool &P, bool vir, cudaStream_t st);   // bonds, walls, dipole

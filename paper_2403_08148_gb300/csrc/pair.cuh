@@ -301,6 +301,11 @@ __device__ __forceinline__ void dev_pair_f32_item(const Pool &P, const int2 *wor
   int &s_total = *s_total_p;
   const int s = work[w].x;
   const int code = work[w].y;
+  // with neighbour lists, only the systems whose lists overflowed come here
+  if (P.list_ovf && !P.list_ovf[s]) {
+    __syncthreads();
+    return;
+  }
   const SysDesc &S = P.sys[s];
   // split 3: item = (cell, dz), 9 neighbour cells; split 9: item =
   // (cell, dy, dz), 3 neighbour cells along x

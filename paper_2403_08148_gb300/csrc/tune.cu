@@ -2,7 +2,7 @@
 //
 // Candidates are timed with CUDA events on the caller's stream on the
 // actual system (or batch) at its current positions:
-//   pair kernel: 3 or 9 work items per home cell (9 or 3 neighbour cells
+//   pair kernel (27-cell path): 3 or 9 work items per home cell (9 or 3 neighbour cells
 //                each) x 128 or 160 threads (3 or 4 Gaussian-core warps +
 //                one electrostatics warp) x {one CTA per work item, or 5,
 //                6 or 8 resident CTAs per SM fetching items dynamically so
@@ -128,7 +128,7 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
   std::ostringstream key;
   key << prop.name << "|nsys=" << hsys.size() << "|n=" << n_real << "|ext=" << n_ext
       << "|q=" << nq << "|cells=" << ncell << "|grid=" << ngrid << "|fp64=" << (int)fp64
-      << "|cf=" << cell_factor << "|geom=" << geom;
+      << "|cf=" << cell_factor << "|geom=" << geom << "|list=" << (int)use_list;
   const bool remeasure = flags & 1, no_cache = flags & 2;
   Tuned t;
   *from_cache = false;
@@ -156,7 +156,7 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
   };
   double best = 1e30;
   int bs = pair_split, bt = pair_threads, bc = pair_ctas_per_sm;
-  if (cell_factor == 1) {
+  if (cell_factor == 1 && !use_list) {  // with lists the cell kernel only serves overflows
     for (int split : {3, 9})
       for (int threads : {128, 160})
         for (int ctas : {0, 5, 6, 8}) {

@@ -34,10 +34,16 @@ def ctx():
     return _CTX
 
 
-def gpu_forces(s: synth.System, precision=0, virial=False, pos=None, cell_factor=0):
+# FP32 pair-kernel variants: (cell_factor, pair_path) -- Verlet lists,
+# 27-cell stencil, fine cells
+PAIR_VARIANTS = {"list": (1, 1), "cells": (1, 2), "fine": (2, 2)}
+
+
+def gpu_forces(s: synth.System, precision=0, virial=False, pos=None, cell_factor=0,
+               pair_path=0):
     import torch
     g = lib()
-    sysg = g.System(ctx(), g.params_from(s, precision, cell_factor), s.q, s.bonds)
+    sysg = g.System(ctx(), g.params_from(s, precision, cell_factor, pair_path), s.q, s.bonds)
     dev = torch.device("cuda:0")
     p = torch.tensor(s.pos if pos is None else pos, dtype=torch.float64, device=dev)
     F = torch.zeros(3 * s.n, dtype=torch.int64, device=dev)

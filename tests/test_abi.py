@@ -78,6 +78,7 @@ def test_validation_accepts_workloads(g):
     (lambda s, p, q: p.box.__setitem__(1, 2.5), "shorter than the cutoff"),
     (lambda s, p, q: setattr(p, "A", 1.0), "non-collapse"),
     (lambda s, p, q: setattr(p, "geometry", 7), "geometry"),
+    (lambda s, p, q: setattr(p, "pair_path", 3), "pair_path"),
 ])
 def test_validation_rejects(g, mutate, msg):
     s = synth.make_bulk(400, seed_index=40)

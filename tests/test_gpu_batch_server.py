@@ -26,9 +26,9 @@ def _mixed_systems():
             synth.make_bulk(2100, seed_index=74, charged_frac=0.1, K=(15, 15, 15))]
 
 
-def _single_run(g, s, nsteps):
+def _single_run(g, s, nsteps, path=0):
     import torch
-    sysg = g.System(ctx(), g.params_from(s), s.q, s.bonds)
+    sysg = g.System(ctx(), g.params_from(s, pair_path=path), s.q, s.bonds)
     pos = torch.tensor(s.pos, dtype=torch.float64, device="cuda:0")
     vel = torch.tensor(s.vel, dtype=torch.float32, device="cuda:0")
     E = torch.zeros(g.NTERMS, dtype=torch.float64, device="cuda:0")
@@ -39,19 +39,21 @@ def _single_run(g, s, nsteps):
     return out
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_batch_matches_single_systems(mode):
+# the persistent launch (mode 1) evaluates pairs by the 27-cell kernel, so
+# it is compared with single systems on that path; mode 0 on both paths
+@pytest.mark.parametrize("mode,path", [(0, 1), (0, 2), (1, 2)])
+def test_batch_matches_single_systems(mode, path):
     g = lib()
     systems = _mixed_systems()
-    b = g.Batch(ctx(), [g.params_from(s) for s in systems], [s.q for s in systems],
-                [s.bonds for s in systems])
+    b = g.Batch(ctx(), [g.params_from(s, pair_path=path) for s in systems],
+                [s.q for s in systems], [s.bonds for s in systems])
     b.set_state(np.concatenate([s.pos for s in systems]),
                 np.concatenate([s.vel for s in systems]).astype(np.float32))
     b.step(12, mode)
     pos, vel, E = b.get_state()
     for k, s in enumerate(systems):
         lo, hi = b.offsets[k], b.offsets[k + 1]
-        p1, v1, e1 = _single_run(g, s, 12)
+        p1, v1, e1 = _single_run(g, s, 12, path)
         assert np.array_equal(pos[lo:hi], p1), f"system {k} positions differ"
         assert np.array_equal(vel[lo:hi], v1), f"system {k} velocities differ"
         assert np.allclose(E[k], e1, rtol=1e-9, atol=1e-9)

@@ -11,7 +11,7 @@ import pytest
 import oracle
 import synth
 from gpu_util import (ENERGY_RTOL_FP32, ENERGY_RTOL_FP64, FORCE_RTOL_FP32, FORCE_RTOL_FP64,
-                      ctx, gpu_forces, lib, rel_rms)
+                      PAIR_VARIANTS, ctx, gpu_forces, lib, rel_rms)
 
 pytestmark = pytest.mark.gpu
 
@@ -64,15 +64,20 @@ def test_cell_list_bit_exact(name, factor):
 # --------------------------------------------------------------------------
 # K3 neighbour set, bit-exact
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("factor", [1, 2])
+@pytest.mark.parametrize("variant", list(PAIR_VARIANTS))
 @pytest.mark.parametrize("name,prec", [("bulk_n3000", 0), ("tiny_box_n120", 0),
                                        ("box_2cells_n700", 0), ("slab_pc", 0),
                                        ("bulk_n3000", 1), ("slab_pc", 1)])
-def test_pair_set_bit_exact(name, prec, factor):
+def test_pair_set_bit_exact(name, prec, variant):
     import torch
     g = lib()
     s = CASES[name]
-    sysg = g.System(ctx(), g.params_from(s, prec, cell_factor=factor), s.q, s.bonds)
+    factor, path = PAIR_VARIANTS[variant]
+    if prec == 1:
+        path = 0  # the FP64 path scans cells
+    sysg = g.System(ctx(), g.params_from(s, prec, factor, path), s.q, s.bonds)
+    if prec == 0:
+        assert sysg.info().pair_path == path
     dev = torch.device("cuda:0")
     pos = torch.tensor(s.pos, dtype=torch.float64, device=dev)
     cap = 4_000_000
@@ -108,11 +113,12 @@ def _check(s, out, ref, f_tol, e_tol, per_term_tol):
     return ferr, eerr
 
 
-@pytest.mark.parametrize("factor", [1, 2])
+@pytest.mark.parametrize("variant", list(PAIR_VARIANTS))
 @pytest.mark.parametrize("name", list(CASES))
-def test_forces_fp32(name, factor):
+def test_forces_fp32(name, variant):
     s = CASES[name]
-    out = gpu_forces(s, 0, cell_factor=factor)
+    factor, path = PAIR_VARIANTS[variant]
+    out = gpu_forces(s, 0, cell_factor=factor, pair_path=path)
     ref = oracle.energy_forces(s)
     _check(s, out, ref, FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
 
@@ -142,14 +148,20 @@ def test_forces_deterministic():
     assert a["energy"] == b["energy"]
 
 
-def test_cell_factors_give_identical_fixed_point_forces_up_to_fp32_order():
-    """Both pair-kernel decompositions compute the same pair set; their
-    FP32 per-thread summation orders differ, so forces agree to rounding."""
+def test_pair_paths_agree_up_to_fp32_order():
+    """The three pair-kernel decompositions compute the same pair set and the
+    same FP32 pair terms; they sum them differently (the cell kernels in FP32
+    per thread, where terms below half an ulp of the running sum are lost;
+    the list kernel in integers of 2^-b), so forces agree to rounding and
+    energies to the FP32 energy bound."""
     s = CASES["bulk_n3000"]
-    a = gpu_forces(s, 0, cell_factor=1)
-    b = gpu_forces(s, 0, cell_factor=2)
-    assert rel_rms(a["forces"], b["forces"]) < 1e-6
-    assert abs(a["energy"]["gc"] - b["energy"]["gc"]) < 1e-7 * abs(a["energy"]["gc"])
+    outs = [gpu_forces(s, 0, cell_factor=f, pair_path=p) for f, p in PAIR_VARIANTS.values()]
+    for b in outs[1:]:
+        assert rel_rms(outs[0]["forces"], b["forces"]) < 1e-6
+        for t in ("gc", "real"):
+            assert abs(outs[0]["energy"][t] - b["energy"][t]) < ENERGY_RTOL_FP32 * abs(b["energy"][t])
+    # the two cell decompositions share the FP32 summation: much closer
+    assert abs(outs[1]["energy"]["gc"] - outs[2]["energy"]["gc"]) < 1e-7 * abs(outs[1]["energy"]["gc"])
 
 
 def test_single_neutral_bead_and_kappa_beta_limit():
@@ -244,6 +256,9 @@ def test_autotune_keeps_parity_and_caches(tmp_path, monkeypatch):
     pos = torch.tensor(s.pos, dtype=torch.float64, device="cuda:0")
     t1 = sysg.autotune(pos)
     assert t1["pair_split"] in (3, 9) and t1["pair_threads"] in (128, 160)
+    lst = g.System(ctx(), g.params_from(s, pair_path=g.GCME_PAIR_LIST), s.q, s.bonds)
+    t3 = lst.autotune(pos)  # the list path has a cache entry of its own
+    assert not t3["from_cache"]
     assert all(l in (4, 8, 16, 32, 64) for l in t1["fft_lpb"]) and not t1["from_cache"]
     F = torch.zeros(3 * s.n, dtype=torch.int64, device="cuda:0")
     E = torch.zeros(g.NTERMS, dtype=torch.float64, device="cuda:0")
@@ -257,4 +272,4 @@ def test_autotune_keeps_parity_and_caches(tmp_path, monkeypatch):
     t2 = sys2.autotune(pos)
     assert t2["from_cache"] and t2["pair_split"] == t1["pair_split"]
     assert t2["fft_lpb"] == t1["fft_lpb"]
-    assert (tmp_path / "tune.jsonl").read_text().count("pair_split") == 1
+    assert (tmp_path / "tune.jsonl").read_text().count("pair_split") == 2
