@@ -376,3 +376,111 @@ def velocity_verlet(s: System, nsteps: int, recip: str = "spme", record=None):
         vel += 0.5 * dt * F
         hist.append(dict(potential=ef["potential"], kinetic=0.5 * float(np.sum(vel * vel))))
     return pos, vel, hist
+
+
+# ---------------------------------------------------------------------------
+# Langevin dynamics (the paper integrates the Langevin equations of motion in
+# the canonical ensemble, method of image charges and illustrative example
+# sections; it names neither the splitting nor the friction).  Reading: the
+# BAOAB splitting of Leimkuhler and Matthews (2013), unit masses, friction
+# gamma, temperature kT:
+#   B: v += dt/2 F;  A: x += dt/2 v;  O: v = c1 v + c2 xi;  A: x += dt/2 v;
+#   F = F(x);  B: v += dt/2 F,   c1 = exp(-gamma dt), c2 = sqrt((1 - c1^2) kT).
+# The noise xi of bead i at step n comes from a counter-based generator,
+# Philox4x64-10 (Salmon, Moraes, Dror and Shaw, SC'11): counter
+# (n, i, 0, 0), key (seed, 0); its four 64-bit words give uniforms
+# u_k = (floor(w_k / 2^40) + 1/2) / 2^24 and, by the Box-Muller transform,
+#   xi_x = sqrt(-2 ln u_0) cos(2 pi u_1),  xi_y = sqrt(-2 ln u_0) sin(2 pi u_1),
+#   xi_z = sqrt(-2 ln u_2) cos(2 pi u_3).
+# Parity: the generator is pinned word for word to numpy's Philox; the
+# integrator to the exact configurational sampling of BAOAB for harmonic
+# forces, the free-particle velocity autocorrelation exp(-gamma t) and its
+# reduction to velocity Verlet at gamma = 0.
+# ---------------------------------------------------------------------------
+_M64 = (1 << 64) - 1
+PHILOX_M = (0xD2E7470EE14C6C93, 0xCA5A826395121157)   # round multipliers
+PHILOX_W = (0x9E3779B97F4A7C15, 0xBB67AE8584CAA73B)   # key increments (Weyl)
+
+
+def _mulhilo64(a, b):
+    """Full 128-bit product of uint64 arrays a * b as (hi, lo), from 32-bit halves."""
+    m32 = np.uint64(0xFFFFFFFF)
+    s32 = np.uint64(32)
+    a_lo, a_hi = a & m32, a >> s32
+    b_lo, b_hi = b & m32, b >> s32
+    ll = a_lo * b_lo
+    hl = a_hi * b_lo
+    lh = a_lo * b_hi
+    hh = a_hi * b_hi
+    t = hl + (ll >> s32)
+    w = (t & m32) + lh
+    hi = hh + (t >> s32) + (w >> s32)
+    lo = a * b
+    return hi, lo
+
+
+def philox4x64(ctr, key, rounds: int = 10):
+    """Philox4x64-R block function on arrays: ctr (..., 4) and key (..., 2)
+    of uint64; returns (..., 4) uint64."""
+    with np.errstate(over="ignore"):
+        c = [np.asarray(ctr[..., k], dtype=np.uint64).copy() for k in range(4)]
+        k0 = np.asarray(key[..., 0], dtype=np.uint64).copy()
+        k1 = np.asarray(key[..., 1], dtype=np.uint64).copy()
+        m0, m1 = np.uint64(PHILOX_M[0]), np.uint64(PHILOX_M[1])
+        w0, w1 = np.uint64(PHILOX_W[0]), np.uint64(PHILOX_W[1])
+        for r in range(rounds):
+            if r > 0:
+                k0 = k0 + w0
+                k1 = k1 + w1
+            hi0, lo0 = _mulhilo64(m0 * np.ones_like(c[0]), c[0])
+            hi1, lo1 = _mulhilo64(m1 * np.ones_like(c[2]), c[2])
+            c = [hi1 ^ c[1] ^ k0, lo1, hi0 ^ c[3] ^ k1, lo0]
+        return np.stack(c, axis=-1)
+
+
+def langevin_noise(seed: int, step: int, n: int) -> np.ndarray:
+    """Standard normal noise (n, 3) of beads 0..n-1 at step `step`."""
+    ctr = np.zeros((n, 4), dtype=np.uint64)
+    ctr[:, 0] = np.uint64(step)
+    ctr[:, 1] = np.arange(n, dtype=np.uint64)
+    key = np.zeros((n, 2), dtype=np.uint64)
+    key[:, 0] = np.uint64(seed & _M64)
+    w = philox4x64(ctr, key)
+    u = ((w >> np.uint64(40)).astype(np.float64) + 0.5) * 2.0 ** -24
+    r0 = np.sqrt(-2.0 * np.log(u[:, 0]))
+    r2 = np.sqrt(-2.0 * np.log(u[:, 2]))
+    out = np.empty((n, 3))
+    out[:, 0] = r0 * np.cos(2.0 * np.pi * u[:, 1])
+    out[:, 1] = r0 * np.sin(2.0 * np.pi * u[:, 1])
+    out[:, 2] = r2 * np.cos(2.0 * np.pi * u[:, 3])
+    return out
+
+
+def langevin_baoab(s: System, nsteps: int, gamma: float, kT: float, seed: int,
+                   step0: int = 0, recip: str = "spme", force_fn=None):
+    """BAOAB Langevin dynamics, unit masses, FP64 (see the block comment).
+    force_fn(pos) -> (forces, potential) replaces the GCMe forces if given.
+    Returns (pos, vel, list of per-step dicts {potential, kinetic})."""
+    pos = s.pos.copy()
+    vel = s.vel.copy()
+    dt = s.dt
+    c1 = np.exp(-gamma * dt)
+    c2 = np.sqrt((1.0 - c1 * c1) * kT)
+
+    def fe(x):
+        if force_fn is not None:
+            return force_fn(x)
+        ef = energy_forces(s, x, recip=recip)
+        return ef["forces"], ef["potential"]
+
+    F, U = fe(pos)
+    hist = [dict(potential=U, kinetic=0.5 * float(np.sum(vel * vel)))]
+    for n in range(step0, step0 + nsteps):
+        vel += 0.5 * dt * F
+        pos += 0.5 * dt * vel
+        vel = c1 * vel + c2 * langevin_noise(seed, n, pos.shape[0])
+        pos += 0.5 * dt * vel
+        F, U = fe(pos)
+        vel += 0.5 * dt * F
+        hist.append(dict(potential=U, kinetic=0.5 * float(np.sum(vel * vel))))
+    return pos, vel, hist
