@@ -109,7 +109,24 @@ typedef struct gcme_params {
                           stencil) or 2 (blocks of 2^3 cells with culling);
                           0 lets the library choose                        */
   int32_t pair_path;   /* GCME_PAIR_AUTO (0), GCME_PAIR_LIST or GCME_PAIR_CELLS */
+  double gamma;        /* Langevin friction (1/tau); 0 = velocity Verlet (NVE) */
+  double kT;           /* Langevin temperature (kT units; 1 = the reduced unit) */
+  uint64_t seed;       /* Langevin noise key                                    */
 } gcme_params;
+
+/* Langevin dynamics (gamma > 0).  The paper integrates Langevin equations of
+ * motion in the canonical ensemble (method of image charges and illustrative
+ * example sections) without naming a splitting; this library takes BAOAB
+ * (Leimkuhler-Matthews), unit masses:
+ *   v += dt/2 F;  x += dt/2 v;  v = c1 v + c2 z;  x += dt/2 v;  F = F(x);
+ *   v += dt/2 F,  c1 = exp(-gamma dt), c2 = sqrt((1 - c1^2) kT).
+ * z of bead i (index within its system) at step n is counter-based:
+ * Philox4x64-10 with counter (n, i, 0, 0) and key (seed, 0) gives four
+ * words w_k, u_k = (floor(w_k / 2^40) + 1/2) / 2^24, and Box-Muller
+ *   z = (sqrt(-2 ln u0) cos 2pi u1, sqrt(-2 ln u0) sin 2pi u1, sqrt(-2 ln u2) cos 2pi u3).
+ * n is the system's own step counter (0 at creation, +1 per step; see
+ * gcme_system_set_step_count), so a system's trajectory is the same alone,
+ * in a batch or in the server. */
 
 /* Pair-kernel path of the FP32 precision (the FP64 path always scans cells):
  * LIST keeps a Verlet neighbour list of every (j, image) within rc + 0.4
@@ -250,8 +267,14 @@ typedef struct gcme_sys_info {
   int32_t pair_path;    /* path in use: GCME_PAIR_LIST or GCME_PAIR_CELLS */
   int32_t list_stride;  /* list entries per bead and lane (4 lanes), 0 without list */
   int64_t list_builds;  /* neighbour-list builds so far (synchronises the device) */
+  int64_t steps;        /* the system's step counter (synchronises the device)   */
 } gcme_sys_info;
 int gcme_system_info(const gcme_sys *sys, gcme_sys_info *out);
+
+/* Set the system's step counter (the Langevin noise counter of the next
+ * step), e.g. to continue a trajectory from a checkpoint taken after
+ * `steps` steps.  Enqueued on the stream; GCME_ERR_INVALID if steps < 0. */
+int gcme_system_set_step_count(gcme_sys *sys, int64_t steps, gcme_stream_t stream);
 
 /* Debug: every ordered in-cutoff triple (i, j, image code) found by the
  * pair kernel at d_pos, code = (nx+1) + 3 (ny+1) + 9 (nz+1).  Writes up to

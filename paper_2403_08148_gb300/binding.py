@@ -42,7 +42,8 @@ class Params(ctypes.Structure):
                 ("H", ctypes.c_double), ("wall_A", ctypes.c_double),
                 ("wall_sigma2", ctypes.c_double), ("bond_k", ctypes.c_double),
                 ("bond_r0", ctypes.c_double), ("cell_factor", ctypes.c_int32),
-                ("pair_path", ctypes.c_int32)]
+                ("pair_path", ctypes.c_int32), ("gamma", ctypes.c_double),
+                ("kT", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
 
 class SysInfo(ctypes.Structure):
@@ -51,7 +52,7 @@ class SysInfo(ctypes.Structure):
                 ("nbonds", ctypes.c_int64), ("nc", ctypes.c_int32 * 3),
                 ("cell_factor", ctypes.c_int32), ("scratch_bytes", ctypes.c_int64),
                 ("pair_path", ctypes.c_int32), ("list_stride", ctypes.c_int32),
-                ("list_builds", ctypes.c_int64)]
+                ("list_builds", ctypes.c_int64), ("steps", ctypes.c_int64)]
 
 
 class Tuning(ctypes.Structure):
@@ -98,6 +99,7 @@ _SIGS = {
                             ctypes.POINTER(_vp)], ctypes.c_int),
     "gcme_system_destroy": ([_vp], None),
     "gcme_system_info": ([_vp, ctypes.POINTER(SysInfo)], ctypes.c_int),
+    "gcme_system_set_step_count": ([_vp, ctypes.c_int64, _vp], ctypes.c_int),
     "gcme_build_cells": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "gcme_forces": ([_vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "gcme_build_cells_noalloc": ([ctypes.POINTER(Params), _i64, _vp, _vp, _vp, _vp, _vp],
@@ -175,11 +177,14 @@ def _stream(stream) -> Optional[int]:
 
 
 def params_from(s, precision: int = GCME_FP32, cell_factor: int = 0,
-                pair_path: int = GCME_PAIR_AUTO) -> Params:
-    """gcme_params from a system description with the fields of synth.System."""
+                pair_path: int = GCME_PAIR_AUTO, gamma: float = 0.0, kT: float = 1.0,
+                seed: int = 0) -> Params:
+    """gcme_params from a system description with the fields of synth.System;
+    gamma > 0 selects Langevin dynamics at temperature kT with noise key seed."""
     p = Params()
     p.cell_factor = int(cell_factor)
     p.pair_path = int(pair_path)
+    p.gamma, p.kT, p.seed = float(gamma), float(kT), int(seed)
     for a in range(3):
         p.box[a] = float(s.box[a])
         p.K[a] = int(s.K[a])
@@ -265,6 +270,9 @@ class System:
         out = SysInfo()
         _check(load().gcme_system_info(self.h, ctypes.byref(out)))
         return out
+
+    def set_step_count(self, steps: int, stream=None):
+        _check(load().gcme_system_set_step_count(self.h, int(steps), _stream(stream)))
 
     def build_cells(self, d_pos, d_cell_start=None, d_sorted_idx=None, stream=None):
         _check(load().gcme_build_cells(self.h, _ptr(d_pos), _ptr(d_cell_start),

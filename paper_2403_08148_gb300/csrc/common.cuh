@@ -81,6 +81,12 @@ struct SysDesc {
   double H, wall_A, wall_s2;
   double bond_k, bond_r0;
   double dt;
+  // Langevin (BAOAB) when langevin != 0: c1 = exp(-gamma dt),
+  // c2 = sqrt((1 - c1^2) kT); noise keyed by seed
+  double lgv_c1, lgv_c2;
+  unsigned long long seed;
+  int langevin;
+  int pad5;
   // real-space kernel constants: small-r Taylor series of
   //   g(r) = [erf(beta r) - erf(kappa r)] / r        = sum_k ser_g[k] r^{2k}
   //   h(r) = -g'(r) / r                               = sum_k ser_h[k] r^{2k}
@@ -174,6 +180,7 @@ struct Pool {
   int *list_ovf;       // [2 nsys] per system: list overflowed (cell kernel), next build's
   const int *gate;     // if set, the cell-sort kernels run only when *gate != 0
   double half_skin2;   // (skin / 2)^2: displacement that forces a rebuild
+  unsigned long long *step_ctr;  // [nsys] steps taken by each system (Langevin counter)
 };
 
 // ---------------------------------------------------------------------------

@@ -120,6 +120,9 @@ std::string validate_spec(const SysSpec &sp) {
   if (p.precision != GCME_FP32 && p.precision != GCME_FP64) return "unknown precision";
   if (p.pair_path < GCME_PAIR_AUTO || p.pair_path > GCME_PAIR_CELLS)
     return "pair_path must be 0 (auto), 1 (list) or 2 (cells)";
+  if (!(p.gamma >= 0.0) || !std::isfinite(p.gamma)) return "gamma must be finite and >= 0";
+  if (p.gamma > 0.0 && (!(p.kT >= 0.0) || !std::isfinite(p.kT)))
+    return "kT must be finite and >= 0";
   if (!(p.rc > 0) || !(p.kappa > 0) || !(p.lB >= 0) || !(p.sigma > 0) || !(p.a > 0) || !(p.A >= 0))
     return "rc, kappa, sigma, a must be > 0 and lB, A >= 0";
   for (int a = 0; a < 3; ++a) {
@@ -412,6 +415,10 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     S.bond_k = p.bond_k;
     S.bond_r0 = p.bond_r0;
     S.dt = p.dt;
+    S.langevin = p.gamma > 0.0 ? 1 : 0;
+    S.lgv_c1 = std::exp(-p.gamma * p.dt);
+    S.lgv_c2 = S.langevin ? std::sqrt((1.0 - S.lgv_c1 * S.lgv_c1) * p.kT) : 0.0;
+    S.seed = p.seed;
     // Taylor series of g and h: erf(x) = 2/sqrt(pi) (x - x^3/3 + x^5/10 - x^7/42)
     const double b = S.beta, k = p.kappa, c = 2.0 / std::sqrt(kPi);
     const double d1 = b - k, d3 = b * b * b - k * k * k, d5 = std::pow(b, 5) - std::pow(k, 5),
@@ -555,6 +562,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   cv.add(&P.virial, (long long)ns * 9);
   cv.add(&pair_work, pair_cap);
   cv.add(&bar_words, 4);
+  cv.add(&P.step_ctr, ns);
   cv.add(&pair_counter, 1);
   int2 *fw[3];
   for (int a = 0; a < 3; ++a) cv.add(&fw[a], fft_cap[a]);
@@ -672,6 +680,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     GCME_CK(cudaMemset(P.vel, 0, (fp64 ? 8 : 4) * 3 * nr));
   }
   GCME_CK(cudaMemset(P.force, 0, sizeof(long long) * 3 * nr));
+  GCME_CK(cudaMemset(P.step_ctr, 0, sizeof(unsigned long long) * ns));
   if (use_list) {
     // reference positions ~1e306: the first check requests a build
     GCME_CK(cudaMemset(P.x_ref, 0x7f, sizeof(double) * 3 * nr));
@@ -901,6 +910,9 @@ void gcme_params_default(gcme_params *p, double L, int32_t K) {
   p->dt = 0.01;
   p->bond_k = 100.0;
   p->bond_r0 = 1.0;
+  p->gamma = 0.0;
+  p->kT = 1.0;
+  p->seed = 0;
 }
 
 int gcme_validate(const gcme_params *p, int64_t n, const double *h_q, const int32_t *h_bonds,
@@ -989,7 +1001,25 @@ int gcme_system_info(const gcme_sys *sys, gcme_sys_info *out) {
   out->list_stride = ms->eng.use_list ? ms->eng.P.nbr_stride : 0;
   GCME_TRY_CK(cudaSetDevice(ms->eng.device));
   out->list_builds = ms->eng.list_builds();
+  unsigned long long steps = 0;
+  GCME_TRY_CK(cudaMemcpy(&steps, ms->eng.P.step_ctr, sizeof(steps), cudaMemcpyDeviceToHost));
+  out->steps = (int64_t)steps;
   return GCME_OK;
+}
+
+int gcme_system_set_step_count(gcme_sys *sys, int64_t steps, gcme_stream_t stream) {
+  if (!sys || steps < 0) {
+    set_error("invalid argument to gcme_system_set_step_count");
+    return GCME_ERR_INVALID;
+  }
+  GCME_TRY_CK(cudaSetDevice(sys->eng.device));
+  // a kernel-free update: a pageable-source copy would be staged, so the
+  // value is written by a memset of each byte
+  const unsigned long long v = (unsigned long long)steps;
+  for (int b = 0; b < 8; ++b)
+    GCME_TRY_CK(cudaMemsetAsync(reinterpret_cast<unsigned char *>(sys->eng.P.step_ctr) + b,
+                                (int)((v >> (8 * b)) & 0xff), 1, (cudaStream_t)stream));
+  return check_launch("gcme_system_set_step_count");
 }
 
 int gcme_build_cells(gcme_sys *sys, const double *d_pos, int32_t *d_cell_start,

@@ -170,14 +170,88 @@ __device__ __forceinline__ void dev_finalize(const Pool &P, int s) {
       P.virial[(long long)s * 9 + k] = (double)(long long)P.vacc[(long long)s * 9 + k] / kEScale;
 }
 
-// Velocity Verlet, unit masses: v += dt/2 F; x += dt v (FP64 positions).
+// Philox4x64-10 block function (Salmon, Moraes, Dror and Shaw, SC'11):
+// ten rounds of two 64 x 64 -> 128-bit products with the round multipliers,
+// the key bumped by the Weyl increments between rounds.
+__device__ __forceinline__ void philox4x64_10(unsigned long long c[4], unsigned long long k0,
+                                              unsigned long long k1) {
+  const unsigned long long m0 = 0xD2E7470EE14C6C93ull, m1 = 0xCA5A826395121157ull;
+  const unsigned long long w0 = 0x9E3779B97F4A7C15ull, w1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += w0;
+      k1 += w1;
+    }
+    const unsigned long long hi0 = __umul64hi(m0, c[0]), lo0 = m0 * c[0];
+    const unsigned long long hi1 = __umul64hi(m1, c[2]), lo1 = m1 * c[2];
+    const unsigned long long n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+// Langevin noise of bead i at step n: counter (n, i, 0, 0), key (seed, 0);
+// uniforms u_k = (floor(w_k / 2^40) + 1/2) / 2^24; Box-Muller:
+//   z_x = sqrt(-2 ln u0) cos(2 pi u1), z_y = sqrt(-2 ln u0) sin(2 pi u1),
+//   z_z = sqrt(-2 ln u2) cos(2 pi u3).
+// FP32 arithmetic for FP32 velocities, FP64 for FP64 velocities.
+template <typename V>
+__device__ __forceinline__ void langevin_noise(unsigned long long seed, unsigned long long n,
+                                               unsigned long long i, V z[3]) {
+  unsigned long long c[4] = {n, i, 0ull, 0ull};
+  philox4x64_10(c, seed, 0ull);
+  V u[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    u[k] = ((V)(c[k] >> 40) + V(0.5)) * V(1.0 / 16777216.0);
+  if constexpr (sizeof(V) == 4) {
+    const float r0 = sqrtf(-2.0f * logf(u[0])), r2 = sqrtf(-2.0f * logf(u[2]));
+    float s1, c1;
+    sincospif(2.0f * u[1], &s1, &c1);
+    z[0] = r0 * c1;
+    z[1] = r0 * s1;
+    z[2] = r2 * cospif(2.0f * u[3]);
+  } else {
+    const double r0 = sqrt(-2.0 * log(u[0])), r2 = sqrt(-2.0 * log(u[2]));
+    double s1, c1;
+    sincospi(2.0 * u[1], &s1, &c1);
+    z[0] = r0 * c1;
+    z[1] = r0 * s1;
+    z[2] = r2 * cospi(2.0 * u[3]);
+  }
+}
+
+// First half of a step, unit masses, FP64 positions.
+//   velocity Verlet:  v += dt/2 F;  x += dt v.
+//   Langevin (BAOAB): v += dt/2 F;  x += dt/2 v;  v = c1 v + c2 z;  x += dt/2 v
+// with z the noise of this bead at the system's step counter.
 template <typename V>
 __device__ __forceinline__ void dev_kick_drift(const Pool &P, long long g) {
   if (g >= P.n_real) return;
-  const SysDesc &S = P.sys[P.real_sys[g]];
+  const int s = P.real_sys[g];
+  const SysDesc &S = P.sys[s];
   V *vel = reinterpret_cast<V *>(P.vel) + 3 * g;
   const int i = (int)(g - S.bead_off);
   const V h = V(0.5 * S.dt);
+  if (S.langevin) {
+    V z[3];
+    langevin_noise<V>(S.seed, P.step_ctr[s], (unsigned long long)i, z);
+    const V c1 = V(S.lgv_c1), c2 = V(S.lgv_c2);
+    const double hd = 0.5 * S.dt;
+    for (int a = 0; a < 3; ++a) {
+      const long long fq = *reinterpret_cast<const long long *>(force_ptr(P, S, i, a));
+      const V f = V((double)fq * (1.0 / kFScale));
+      V v = vel[a] + h * f;
+      double x = P.pos[3 * g + a] + hd * (double)v;
+      v = c1 * v + c2 * z[a];
+      vel[a] = v;
+      P.pos[3 * g + a] = x + hd * (double)v;
+    }
+    return;
+  }
   for (int a = 0; a < 3; ++a) {
     const long long fq = *reinterpret_cast<const long long *>(force_ptr(P, S, i, a));
     const V f = V((double)fq * (1.0 / kFScale));
@@ -205,6 +279,9 @@ __device__ __forceinline__ void dev_kick(const Pool &P, long long g) {
       vel[a] = v;
       ke += 0.5 * (double)v * (double)v;
     }
+    // the step is complete: advance the system's step counter (read by the
+    // kick-drift kernel of the next step)
+    if (i == 0 && P.step_ctr) P.step_ctr[s] += 1;
   }
   sys_acc_add(P, s, act, ACC_KIN, ke);
 }

@@ -127,6 +127,11 @@ int gcme_server::rebuild(const std::vector<uint64_t> &members) {
                       sizeof(float) * 3 * n, cudaMemcpyHostToDevice, stream);
     }
   }
+  // step counters: each request continues its own (the Langevin noise counter)
+  std::vector<unsigned long long> ctr(members.size());
+  for (size_t k = 0; k < members.size(); ++k) ctr[k] = (unsigned long long)reqs[members[k]]->done;
+  cudaMemcpyAsync(ne->P.step_ctr, ctr.data(), sizeof(unsigned long long) * ctr.size(),
+                  cudaMemcpyHostToDevice, stream);
   cudaError_t e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) {
     set_error(std::string("server rebuild: ") + cudaGetErrorString(e));

@@ -58,6 +58,7 @@ def test_params_layout_matches_c(g):
     assert list(p.K) == [32, 32, 32]
     assert p.dt == 0.01 and p.bond_k == 100.0 and p.bond_r0 == 1.0
     assert p.H == 0.0 and p.wall_A == 0.0
+    assert p.pair_path == 0 and p.gamma == 0.0 and p.kT == 1.0 and p.seed == 0
 
 
 def _params(g, s):
@@ -79,6 +80,7 @@ def test_validation_accepts_workloads(g):
     (lambda s, p, q: setattr(p, "A", 1.0), "non-collapse"),
     (lambda s, p, q: setattr(p, "geometry", 7), "geometry"),
     (lambda s, p, q: setattr(p, "pair_path", 3), "pair_path"),
+    (lambda s, p, q: setattr(p, "gamma", -1.0), "gamma"),
 ])
 def test_validation_rejects(g, mutate, msg):
     s = synth.make_bulk(400, seed_index=40)

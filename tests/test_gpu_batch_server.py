@@ -26,9 +26,13 @@ def _mixed_systems():
             synth.make_bulk(2100, seed_index=74, charged_frac=0.1, K=(15, 15, 15))]
 
 
-def _single_run(g, s, nsteps, path=0):
+def _params(g, s, path=0, gamma=0.0, seed=0):
+    return g.params_from(s, pair_path=path, gamma=gamma, kT=1.0, seed=seed)
+
+
+def _single_run(g, s, nsteps, path=0, gamma=0.0, seed=0):
     import torch
-    sysg = g.System(ctx(), g.params_from(s, pair_path=path), s.q, s.bonds)
+    sysg = g.System(ctx(), _params(g, s, path, gamma, seed), s.q, s.bonds)
     pos = torch.tensor(s.pos, dtype=torch.float64, device="cuda:0")
     vel = torch.tensor(s.vel, dtype=torch.float32, device="cuda:0")
     E = torch.zeros(g.NTERMS, dtype=torch.float64, device="cuda:0")
@@ -41,11 +45,14 @@ def _single_run(g, s, nsteps, path=0):
 
 # the persistent launch (mode 1) evaluates pairs by the 27-cell kernel, so
 # it is compared with single systems on that path; mode 0 on both paths
-@pytest.mark.parametrize("mode,path", [(0, 1), (0, 2), (1, 2)])
-def test_batch_matches_single_systems(mode, path):
+@pytest.mark.parametrize("mode,path,gamma", [(0, 1, 0.0), (0, 2, 0.0), (1, 2, 0.0),
+                                             (0, 2, 1.0), (1, 2, 1.0)])
+def test_batch_matches_single_systems(mode, path, gamma):
+    """Also with Langevin noise: each system draws from its own seed and step
+    counter, so its trajectory does not depend on the batch."""
     g = lib()
     systems = _mixed_systems()
-    b = g.Batch(ctx(), [g.params_from(s, pair_path=path) for s in systems],
+    b = g.Batch(ctx(), [_params(g, s, path, gamma, 100 + k) for k, s in enumerate(systems)],
                 [s.q for s in systems], [s.bonds for s in systems])
     b.set_state(np.concatenate([s.pos for s in systems]),
                 np.concatenate([s.vel for s in systems]).astype(np.float32))
@@ -53,7 +60,7 @@ def test_batch_matches_single_systems(mode, path):
     pos, vel, E = b.get_state()
     for k, s in enumerate(systems):
         lo, hi = b.offsets[k], b.offsets[k + 1]
-        p1, v1, e1 = _single_run(g, s, 12, path)
+        p1, v1, e1 = _single_run(g, s, 12, path, gamma, 100 + k)
         assert np.array_equal(pos[lo:hi], p1), f"system {k} positions differ"
         assert np.array_equal(vel[lo:hi], v1), f"system {k} velocities differ"
         assert np.allclose(E[k], e1, rtol=1e-9, atol=1e-9)
@@ -88,10 +95,11 @@ def test_batch_energies_match_oracle():
         assert abs(E[k, 8] - ref["potential"]) <= 1e-6 * abs(ref["potential"])
 
 
-def test_server_result_same_alone_and_in_mix():
+@pytest.mark.parametrize("gamma", [0.0, 1.0])
+def test_server_result_same_alone_and_in_mix(gamma):
     """Continuous batching: a request's result does not depend on what else
     is on the GPU (different sizes and geometries, admitted at different
-    chunk boundaries)."""
+    chunk boundaries), with or without Langevin noise."""
     g = lib()
     target = synth.make_polyelectrolyte(n_chains=6, chain_len=10, n_solvent=1500,
                                         seed_index=80, K=(12, 12, 12))
@@ -101,7 +109,8 @@ def test_server_result_same_alone_and_in_mix():
     nsteps = 60
 
     def submit(srv, s, n):
-        return srv.submit(g.params_from(s), s.pos, s.vel.astype(np.float32), s.q, n, s.bonds)
+        return srv.submit(_params(g, s, gamma=gamma, seed=s.n), s.pos, s.vel.astype(np.float32),
+                          s.q, n, s.bonds)
 
     srv = g.Server(ctx(), 2 << 30, chunk_steps=7)
     t = submit(srv, target, nsteps)
@@ -130,7 +139,7 @@ def test_server_result_same_alone_and_in_mix():
     st = srv.stats()
     assert st["completed"] == 1 + len(tick) and st["peak_active"] >= 2
     # and the served result equals the single-system path
-    p1, v1, _ = _single_run(g, target, nsteps)
+    p1, v1, _ = _single_run(g, target, nsteps, gamma=gamma, seed=target.n)
     assert np.array_equal(pos_mix, p1)
     srv.close()
 
