@@ -273,36 +273,53 @@ TERMS = ("gc", "real", "recip", "corr", "self", "slab", "wall", "bond")
 CLS_IMAGE, CLS_CHARGED, CLS_NEUTRAL = 0, 1, 2
 
 
+def _species(s: System):
+    """Number of species and the species of every real bead (one species,
+    type 0, when the system has no tables)."""
+    if s.types is None:
+        return 1, np.zeros(s.n, np.int32)
+    return int(s.A_tab.shape[0]), np.asarray(s.types, np.int32)
+
+
 def electrostatic_beads(s: System, pos=None):
     """Beads that carry the electrostatics: the reals, plus mirror images
     (x, y, -z) with charge -z_i for every charged real in the conducting-slab
-    geometry.  Returns (pos, q, type, n_real) with type 1 = image (no core)."""
+    geometry.  Returns (pos, q, type, n_real).  type = the species t of a
+    real bead, nt + t for the image of a bead of species t (images carry the
+    smearing radius of their source and no Gaussian core)."""
     pos = s.pos if pos is None else pos
     q = s.q
     n = pos.shape[0]
-    types = np.zeros(n, np.int32)
+    nt, types = _species(s)
     if s.geometry != GEOM_SLAB_PC:
         return pos, q, types, n
     qi = np.nonzero(q)[0]
     img = pos[qi].copy()
     img[:, 2] = -img[:, 2]
     return (np.concatenate([pos, img]), np.concatenate([q, -q[qi]]),
-            np.concatenate([types, np.ones(qi.shape[0], np.int32)]), n)
+            np.concatenate([types, nt + types[qi]]).astype(np.int32), n)
 
 
 def bead_classes(s: System):
     """Class of every bead of the (possibly doubled) electrostatic system."""
     pos, q, types, n = electrostatic_beads(s)
     cls = np.where(q != 0.0, CLS_CHARGED, CLS_NEUTRAL).astype(np.int32)
-    cls[types == 1] = CLS_IMAGE
+    cls[n:] = CLS_IMAGE
     return cls
 
 
 def _tables(s: System):
-    A_tab = np.array([[s.A, 0.0], [0.0, 0.0]])
-    sig = np.array([s.sigma, s.sigma])
-    a = np.array([s.a, s.a])
-    return A_tab, sig, a
+    """Pair tables over 2 nt bead types: species 0..nt-1 (A_ij, sigma_i, a_i
+    of the system) and their images nt..2nt-1 (same a_i, no Gaussian core)."""
+    if s.types is None:
+        A, sig, a = np.array([[s.A]]), np.array([s.sigma]), np.array([s.a])
+    else:
+        A, sig, a = (np.asarray(s.A_tab, float), np.asarray(s.sig_tab, float),
+                     np.asarray(s.a_tab, float))
+    nt = A.shape[0]
+    A_tab = np.zeros((2 * nt, 2 * nt))
+    A_tab[:nt, :nt] = A
+    return A_tab, np.concatenate([sig, sig]), np.concatenate([a, a])
 
 
 def energy_forces(s: System, pos=None, recip: str = "spme",
@@ -323,7 +340,7 @@ def energy_forces(s: System, pos=None, recip: str = "spme",
         rr = spme(epos, eq, s.box, s.K, s.order, s.kappa, s.lB)
     else:
         rr = ewald_recip(epos, eq, s.box, s.kappa, s.lB, tol=ewald_tol)
-    corr, self_e = ewald_constants(eq, np.full(eq.shape[0], s.a), s.kappa, s.lB)
+    corr, self_e = ewald_constants(eq, a[etype], s.kappa, s.lB)
     half = 0.5 if s.geometry == GEOM_SLAB_PC else 1.0
     E = dict(gc=pr["gc"], real=half * pr["real"], recip=half * rr["recip"],
              corr=half * corr, self=half * self_e, slab=0.0, wall=0.0, bond=0.0)

@@ -114,19 +114,31 @@ class System:
     H: float = 0.0           # slab height for slab geometries (d)
     wall_A: float = 0.0      # continuum wall amplitude A n_s (kT/d^2 x d^3)
     wall_sigma2: float = 0.0  # sigma_w^2 = sigma_i^2 + sigma_e^2
+    # several species (optional): type of each bead and per-type tables;
+    # None means one species with the scalars A, sigma, a above
+    types: Optional[np.ndarray] = None   # (n,) int32 in [0, nt)
+    A_tab: Optional[np.ndarray] = None   # (nt, nt) A_ij, symmetric
+    sig_tab: Optional[np.ndarray] = None  # (nt,) sigma_i
+    a_tab: Optional[np.ndarray] = None   # (nt,) a_i
 
     @property
     def n(self) -> int:
         return int(self.pos.shape[0])
 
     @property
+    def ntypes(self) -> int:
+        return 0 if self.types is None else int(self.A_tab.shape[0])
+
+    @property
     def n_charged(self) -> int:
         return int(np.count_nonzero(self.q))
 
     def copy(self) -> "System":
+        cp = lambda a: None if a is None else a.copy()
         return dataclasses.replace(
             self, box=self.box.copy(), pos=self.pos.copy(), vel=self.vel.copy(),
-            q=self.q.copy(), bonds=self.bonds.copy())
+            q=self.q.copy(), bonds=self.bonds.copy(), types=cp(self.types),
+            A_tab=cp(self.A_tab), sig_tab=cp(self.sig_tab), a_tab=cp(self.a_tab))
 
 
 def _rng(index: int, sub: int = 0) -> np.random.Generator:
@@ -310,6 +322,62 @@ def make_slab_fluid(geometry: int, n: int, rho: float = 3.0,
 
 # ---------------------------------------------------------------------------
 # The five workloads
+def make_mixture(n: int, fractions, charges, A_tab, sig_tab, a_tab, rho: float = 3.0,
+                 seed_index: int = 9, K=None, geometry: int = GEOM_BULK,
+                 sub: int = 0) -> System:
+    """Fluid of several species (Supporting Information, Flory-Huggins
+    section: A/B blends with A_AB = A_AA + Delta A; species may also differ
+    in sigma_i and a_i).  Species t takes a fraction fractions[t] of the
+    beads and charge charges[t]; the charged species' counts are adjusted so
+    that the system is neutral.  Uniform positions; bulk, or a slab between
+    walls at z = 0 and H (box L x L x 3H nonmetal, L x L x 2H conducting)."""
+    rng = _rng(seed_index, sub)
+    fr = np.asarray(fractions, float) / np.sum(fractions)
+    ch = np.asarray(charges, float)
+    cnt = np.floor(fr * n).astype(int)
+    cnt[0] += n - cnt.sum()
+    # neutrality: move beads between the first positive and first negative
+    # charged species until sum(cnt * ch) = 0 (integer charges)
+    pos_t = [t for t in range(len(ch)) if ch[t] > 0]
+    neg_t = [t for t in range(len(ch)) if ch[t] < 0]
+    if pos_t and neg_t:
+        tp, tn = pos_t[0], neg_t[0]
+        for _ in range(4 * n):
+            net = float(np.sum(cnt * ch))
+            if abs(net) < 1e-9:
+                break
+            if net > 0:
+                cnt[tp] -= 1
+                cnt[0] += 1
+            else:
+                cnt[tn] -= 1
+                cnt[0] += 1
+    types = np.repeat(np.arange(len(ch)), cnt).astype(np.int32)
+    rng.shuffle(types)
+    q = ch[types].copy()
+    if geometry == GEOM_BULK:
+        L = (n / rho) ** (1.0 / 3.0)
+        box = np.array([L, L, L])
+        pos = rng.uniform(0.0, 1.0, size=(n, 3)) * box
+        H, wA, ws2 = 0.0, 0.0, 0.0
+    else:  # slab of height H = 2 L between walls, as make_slab_fluid
+        L = (n / (rho * 2.0)) ** (1.0 / 3.0)
+        H = 2.0 * L
+        mult = 3.0 if geometry == GEOM_SLAB_NM else 2.0
+        box = np.array([L, L, mult * H])
+        pos = rng.uniform(0.0, 1.0, size=(n, 3)) * np.array([L, L, 0.0])
+        pos[:, 2] = rng.uniform(0.75, H - 0.75, size=n)
+        wA, ws2 = _wall_params(25.0, 0.5)
+    if K is None:
+        K = tuple(smooth_size(int(math.ceil(b))) for b in box)
+    return System(name=f"mixture_n{n}", geometry=geometry, box=box, pos=pos,
+                  vel=_velocities(rng, n), q=q, bonds=np.zeros((0, 2), np.int32),
+                  kappa=ewald_kappa(3.0), K=tuple(int(k) for k in K), H=H,
+                  wall_A=wA, wall_sigma2=ws2, types=types,
+                  A_tab=np.asarray(A_tab, float), sig_tab=np.asarray(sig_tab, float),
+                  a_tab=np.asarray(a_tab, float))
+
+
 # ---------------------------------------------------------------------------
 def config1() -> System:
     """Plain GCMe fluid: N=3000, rho=3 (L=10), 10% charged, grid 32^3."""
