@@ -85,6 +85,7 @@ enum {
 };
 
 #define GCME_FORCE_SCALE 4294967296.0 /* 2^32: fixed-point force scale */
+#define GCME_MAX_TYPES 8               /* species per system */
 
 /* Parameters of one system.  All lengths in d, energies in kT. */
 typedef struct gcme_params {
@@ -112,7 +113,25 @@ typedef struct gcme_params {
   double gamma;        /* Langevin friction (1/tau); 0 = velocity Verlet (NVE) */
   double kT;           /* Langevin temperature (kT units; 1 = the reduced unit) */
   uint64_t seed;       /* Langevin noise key                                    */
+  /* Several species (0 = one species with A, sigma, a above).  Species t of
+   * ntypes <= GCME_MAX_TYPES has sigma_tab[t] and a_tab[t]; species t and u
+   * interact with A_tab[t * GCME_MAX_TYPES + u] (symmetric).  Beads get
+   * their species from h_types at creation. */
+  int32_t ntypes;
+  int32_t pad1;
+  double A_tab[GCME_MAX_TYPES * GCME_MAX_TYPES];
+  double sigma_tab[GCME_MAX_TYPES];
+  double a_tab[GCME_MAX_TYPES];
 } gcme_params;
+
+/* Several species (Supporting Information, Flory-Huggins section: A/B
+ * monomers with A_AB = A_AA + Delta A; species may also differ in sigma_i
+ * and a_i).  Per pair of species: s = sigma_i^2 + sigma_j^2 in Eq. u_ex,
+ * a_ij^2 = a_i^2 + a_j^2 and beta_ij = sqrt(pi) / (sqrt(2) a_ij) in the
+ * real-space term of Eq. ewald, the Born self energy lB z_i^2 / (2 a_i) per
+ * bead; image beads keep their source's species (a_i, no Gaussian core).
+ * Supported by the 27-cell FP32 kernel (graph and persistent launches) and
+ * the FP64 kernel; the fine-cell and neighbour-list paths reject it. */
 
 /* Langevin dynamics (gamma > 0).  The paper integrates Langevin equations of
  * motion in the canonical ensemble (method of image charges and illustrative
@@ -159,7 +178,7 @@ const char *gcme_version(void);
 /* Host-only check of a system description, without a device: the same
  * validation gcme_system_create performs.  Returns 0 or GCME_ERR_INVALID
  * (message in gcme_last_error). */
-int gcme_validate(const gcme_params *p, int64_t n, const double *h_q,
+int gcme_validate(const gcme_params *p, int64_t n, const double *h_q, const int32_t *h_types,
                   const int32_t *h_bonds, int64_t nbonds);
 
 /* ---- context ------------------------------------------------------------ */
@@ -172,19 +191,22 @@ void gcme_ctx_destroy(gcme_ctx *ctx);
 
 /* ---- single system ------------------------------------------------------- */
 
-/* Create a system of n real beads with charges h_q[n] (charge numbers z_i)
- * and an optional bond list h_bonds[2*nbonds] (bead index pairs).  Validates:
+/* Create a system of n real beads with charges h_q[n] (charge numbers z_i),
+ * species h_types[n] (in [0, p->ntypes); NULL = all of species 0) and an
+ * optional bond list h_bonds[2*nbonds] (bead index pairs).  Validates:
  *   - net charge zero (|sum z| < 1e-6), n >= 1;
  *   - the non-collapse condition of the Gaussian core model section,
- *     A / sigma_ij^3 > 4 pi^{3/2} lB / (3^{3/2} a_ij) for unit charges;
+ *     A_ij / sigma_ij^3 > 4 pi^{3/2} |z_i z_j| lB / (3^{3/2} a_ij), for every
+ *     pair of species present with their largest charges;
+ *   - species tables: A_ij symmetric and >= 0, sigma_i, a_i > 0;
  *   - every box side >= rc (27-cell stencil) and, for slabs, the box height
  *     3 H (nonmetal) or 2 H (image charges);
  *   - grid sizes 2^a 3^b 5^c within [4, 1024], order within [3, 8].
  * Allocates the library's scratch memory for the system (cell lists, PME
  * grids, accumulators).  Errors: INVALID, OOM, CUDA. */
 int gcme_system_create(gcme_ctx *ctx, const gcme_params *p, int64_t n,
-                       const double *h_q, const int32_t *h_bonds, int64_t nbonds,
-                       gcme_sys **out);
+                       const double *h_q, const int32_t *h_types, const int32_t *h_bonds,
+                       int64_t nbonds, gcme_sys **out);
 void gcme_system_destroy(gcme_sys *sys);
 
 /* Build the cell list of the positions d_pos[n*3] (K1 + K2): wrap into the
@@ -321,13 +343,14 @@ int gcme_autotune(gcme_sys *sys, const double *d_pos, int32_t flags, gcme_tuning
 /* A batch of nsys independent systems stepped together: every phase of the
  * step is one launch over all systems (or one persistent cooperative launch
  * for all phases), replayed from a captured CUDA graph.  params[s], n[s],
- * charges h_q (concatenated), bonds are per system as in gcme_system_create;
+ * charges h_q and species h_types (concatenated; h_types may be NULL), bonds
+ * are per system as in gcme_system_create;
  * h_bond_count[s] gives the number of bonds of system s (concatenated in
  * h_bonds, indices local to the system).  The batch owns pooled device state:
  * positions, velocities, forces. */
 int gcme_batch_create(gcme_ctx *ctx, int32_t nsys, const gcme_params *params,
-                      const int64_t *n, const double *h_q, const int32_t *h_bonds,
-                      const int64_t *h_bond_count, gcme_batch **out);
+                      const int64_t *n, const double *h_q, const int32_t *h_types,
+                      const int32_t *h_bonds, const int64_t *h_bond_count, gcme_batch **out);
 void gcme_batch_destroy(gcme_batch *b);
 
 /* Copy state in/out (host, concatenated over systems in batch order). */
@@ -369,6 +392,7 @@ typedef struct gcme_request {
   const int32_t *h_bonds; /* 2*nbonds, may be NULL */
   int64_t nbonds;
   int64_t nsteps;
+  const int32_t *h_types; /* n species, may be NULL (all species 0); copied on submit */
 } gcme_request;
 
 typedef struct gcme_result {

@@ -18,6 +18,7 @@ from . import builder as _build
 GCME_BULK, GCME_SLAB_NONMETAL, GCME_SLAB_IMAGE = 0, 1, 2
 GCME_FP32, GCME_FP64 = 0, 1
 GCME_PAIR_AUTO, GCME_PAIR_LIST, GCME_PAIR_CELLS = 0, 1, 2
+MAX_TYPES = 8
 NTERMS = 10
 TERM_NAMES = ("gc", "real", "recip", "corr", "self", "slab", "wall", "bond",
               "potential", "kinetic")
@@ -43,7 +44,11 @@ class Params(ctypes.Structure):
                 ("wall_sigma2", ctypes.c_double), ("bond_k", ctypes.c_double),
                 ("bond_r0", ctypes.c_double), ("cell_factor", ctypes.c_int32),
                 ("pair_path", ctypes.c_int32), ("gamma", ctypes.c_double),
-                ("kT", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("kT", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("ntypes", ctypes.c_int32), ("pad1", ctypes.c_int32),
+                ("A_tab", ctypes.c_double * (MAX_TYPES * MAX_TYPES)),
+                ("sigma_tab", ctypes.c_double * MAX_TYPES),
+                ("a_tab", ctypes.c_double * MAX_TYPES)]
 
 
 class SysInfo(ctypes.Structure):
@@ -76,7 +81,7 @@ class Request(ctypes.Structure):
                 ("h_vel", ctypes.POINTER(ctypes.c_float)),
                 ("h_q", ctypes.POINTER(ctypes.c_double)),
                 ("h_bonds", ctypes.POINTER(ctypes.c_int32)), ("nbonds", ctypes.c_int64),
-                ("nsteps", ctypes.c_int64)]
+                ("nsteps", ctypes.c_int64), ("h_types", ctypes.POINTER(ctypes.c_int32))]
 
 
 class Result(ctypes.Structure):
@@ -92,10 +97,10 @@ _SIGS = {
     "gcme_last_error": ([], ctypes.c_char_p),
     "gcme_version": ([], ctypes.c_char_p),
     "gcme_params_default": ([ctypes.POINTER(Params), ctypes.c_double, _i32], None),
-    "gcme_validate": ([ctypes.POINTER(Params), _i64, _vp, _vp, _i64], ctypes.c_int),
+    "gcme_validate": ([ctypes.POINTER(Params), _i64, _vp, _vp, _vp, _i64], ctypes.c_int),
     "gcme_ctx_create": ([ctypes.POINTER(_vp), ctypes.c_int], ctypes.c_int),
     "gcme_ctx_destroy": ([_vp], None),
-    "gcme_system_create": ([_vp, ctypes.POINTER(Params), _i64, _vp, _vp, _i64,
+    "gcme_system_create": ([_vp, ctypes.POINTER(Params), _i64, _vp, _vp, _vp, _i64,
                             ctypes.POINTER(_vp)], ctypes.c_int),
     "gcme_system_destroy": ([_vp], None),
     "gcme_system_info": ([_vp, ctypes.POINTER(SysInfo)], ctypes.c_int),
@@ -114,7 +119,7 @@ _SIGS = {
     "gcme_batch_autotune": ([_vp, _i32, ctypes.POINTER(Tuning), _vp], ctypes.c_int),
     "gcme_debug_barrier_timeout": ([_vp, ctypes.c_double, _vp], ctypes.c_int),
     "gcme_debug_pairs": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
-    "gcme_batch_create": ([_vp, _i32, ctypes.POINTER(Params), _vp, _vp, _vp, _vp,
+    "gcme_batch_create": ([_vp, _i32, ctypes.POINTER(Params), _vp, _vp, _vp, _vp, _vp,
                            ctypes.POINTER(_vp)], ctypes.c_int),
     "gcme_batch_destroy": ([_vp], None),
     "gcme_batch_set_state": ([_vp, _vp, _vp, _vp], ctypes.c_int),
@@ -194,14 +199,35 @@ def params_from(s, precision: int = GCME_FP32, cell_factor: int = 0,
     p.rc, p.kappa, p.order, p.dt = float(s.rc), float(s.kappa), int(s.order), float(s.dt)
     p.H, p.wall_A, p.wall_sigma2 = float(s.H), float(s.wall_A), float(s.wall_sigma2)
     p.bond_k, p.bond_r0 = float(s.bond_k), float(s.bond_r0)
+    if getattr(s, "types", None) is not None:  # several species
+        nt = int(s.A_tab.shape[0])
+        if nt > MAX_TYPES:
+            raise ValueError(f"at most {MAX_TYPES} species")
+        p.ntypes = nt
+        for t in range(nt):
+            p.sigma_tab[t] = float(s.sig_tab[t])
+            p.a_tab[t] = float(s.a_tab[t])
+            for u in range(nt):
+                p.A_tab[t * MAX_TYPES + u] = float(s.A_tab[t, u])
     return p
 
 
-def validate(params: Params, q, bonds=None):
+def _types(types, n):
+    if types is None:
+        return None
+    t = np.ascontiguousarray(types, np.int32)
+    if t.shape != (n,):
+        raise ValueError("one species per bead")
+    return t
+
+
+def validate(params: Params, q, bonds=None, types=None):
     """Host-only validation of a system description (no device needed)."""
     q = np.ascontiguousarray(q, dtype=np.float64)
     b = None if bonds is None or len(bonds) == 0 else np.ascontiguousarray(bonds, np.int32)
+    t = _types(types, q.shape[0])
     _check(load().gcme_validate(ctypes.byref(params), int(q.shape[0]), q.ctypes.data,
+                                None if t is None else t.ctypes.data,
                                 None if b is None else b.ctypes.data,
                                 0 if b is None else int(b.shape[0])))
 
@@ -242,15 +268,17 @@ class System:
     """One GCMe system (gcme_system_create)."""
 
     def __init__(self, ctx: Context, params: Params, q: np.ndarray,
-                 bonds: Optional[np.ndarray] = None):
+                 bonds: Optional[np.ndarray] = None, types: Optional[np.ndarray] = None):
         L = load()
         self.ctx = ctx
         self.params = params
         q = np.ascontiguousarray(q, dtype=np.float64)
         self.n = int(q.shape[0])
         b = None if bonds is None or len(bonds) == 0 else np.ascontiguousarray(bonds, np.int32)
+        t = _types(types, self.n)
         h = _vp()
         _check(L.gcme_system_create(ctx.h, ctypes.byref(params), self.n, q.ctypes.data,
+                                    None if t is None else t.ctypes.data,
                                     None if b is None else b.ctypes.data,
                                     0 if b is None else int(b.shape[0]), ctypes.byref(h)))
         self.h = h
@@ -316,7 +344,8 @@ class Batch:
     """Independent systems stepped together (gcme_batch_create)."""
 
     def __init__(self, ctx: Context, params: Sequence[Params], charges: Sequence[np.ndarray],
-                 bonds: Optional[Sequence[np.ndarray]] = None):
+                 bonds: Optional[Sequence[np.ndarray]] = None,
+                 types: Optional[Sequence[Optional[np.ndarray]]] = None):
         L = load()
         ns = len(params)
         parr = (Params * ns)(*params)
@@ -327,8 +356,14 @@ class Batch:
         bc = np.array([len(b) for b in bonds], dtype=np.int64)
         ball = np.ascontiguousarray(np.concatenate([np.asarray(b, np.int32).reshape(-1, 2)
                                                     for b in bonds]), dtype=np.int32)
+        tall = None
+        if types is not None and any(t is not None for t in types):
+            tall = np.ascontiguousarray(np.concatenate(
+                [np.zeros(len(q_), np.int32) if t is None else np.asarray(t, np.int32)
+                 for t, q_ in zip(types, charges)]), dtype=np.int32)
         h = _vp()
         _check(L.gcme_batch_create(ctx.h, ns, parr, n.ctypes.data, q.ctypes.data,
+                                   None if tall is None else tall.ctypes.data,
                                    ball.ctypes.data if ball.size else None, bc.ctypes.data,
                                    ctypes.byref(h)))
         self.h = h
@@ -409,7 +444,7 @@ class Server:
         except Exception:
             pass
 
-    def submit(self, params: Params, pos, vel, q, nsteps: int, bonds=None) -> int:
+    def submit(self, params: Params, pos, vel, q, nsteps: int, bonds=None, types=None) -> int:
         pos = np.ascontiguousarray(pos, np.float64)
         vel = np.ascontiguousarray(vel, np.float32)
         q = np.ascontiguousarray(q, np.float64)
@@ -424,6 +459,9 @@ class Server:
             req.h_bonds = b.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
             req.nbonds = int(b.shape[0])
         req.nsteps = int(nsteps)
+        ty = _types(types, req.n)
+        if ty is not None:
+            req.h_types = ty.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         t = ctypes.c_uint64(0)
         _check(load().gcme_submit(self.h, ctypes.byref(req), ctypes.byref(t)))
         self._keep[t.value] = int(q.shape[0])

@@ -138,6 +138,7 @@ __device__ __forceinline__ void dev_cellsort_block(const Pool &P, long long cg, 
       P.sorted_idx[beg + t] = e;
       P.xyzq_s[beg + t] = P.xyzq_u[S.ext_off + e];
       if (P.xyzq_s64) P.xyzq_s64[beg + t] = P.xyzq_u64[S.ext_off + e];
+      if (P.type_s) P.type_s[beg + t] = P.type_u[S.ext_off + e];
     }
   } else {
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
@@ -149,6 +150,7 @@ __device__ __forceinline__ void dev_cellsort_block(const Pool &P, long long cg, 
       P.sorted_idx[dst] = e;
       P.xyzq_s[dst] = P.xyzq_u[S.ext_off + e];
       if (P.xyzq_s64) P.xyzq_s64[dst] = P.xyzq_u64[S.ext_off + e];
+      if (P.type_s) P.type_s[dst] = P.type_u[S.ext_off + e];
     }
   }
   if (threadIdx.x == 0) {

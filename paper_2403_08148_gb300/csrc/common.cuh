@@ -27,6 +27,7 @@ __host__ __device__ __forceinline__ dpos4 make_dpos4(double x, double y, double 
 }
 
 constexpr int kNcls = 3;           // bead classes inside a cell: image, charged, neutral
+constexpr int kMaxTypes = GCME_MAX_TYPES;  // species per system
 constexpr int kMaxStages = 8;      // FFT stages per axis (K <= 1024)
 constexpr int kNacc = 16;          // fixed-point accumulators per system
 constexpr double kFScale = 4294967296.0;   // 2^32 force scale
@@ -41,6 +42,22 @@ enum {
   ACC_KIN = 9,     // kinetic energy
   ACC_FLAGS = 10,  // error flags (bit 0: non-finite)
   ACC_NPAIR = 11   // debug pair count
+};
+
+// Pair constants of one species pair (i, j), several-species systems:
+//   Gaussian core  u = pref exp(-3 r^2 / (2 s)) = pref 2^(c2 r^2),  F_i = -fc u d
+//   real-space electrostatics with beta_ij, small-r series of g and h
+struct PairTab {
+  float pref, c2, fc, beta;
+  float sg[4];
+  float sh[3];
+  float pad;
+};
+struct PairTab64 {
+  double pref, expc, fc, beta;
+  double sg[4];
+  double sh[3];
+  double pad;
 };
 
 struct SysDesc {
@@ -86,7 +103,8 @@ struct SysDesc {
   double lgv_c1, lgv_c2;
   unsigned long long seed;
   int langevin;
-  int pad5;
+  int ntypes;          // species of this system (several-species engines; else 0)
+  long long tab_off;   // its ntypes x ntypes block of the pooled pair tables
   // real-space kernel constants: small-r Taylor series of
   //   g(r) = [erf(beta r) - erf(kappa r)] / r        = sum_k ser_g[k] r^{2k}
   //   h(r) = -g'(r) / r                               = sum_k ser_h[k] r^{2k}
@@ -181,6 +199,12 @@ struct Pool {
   const int *gate;     // if set, the cell-sort kernels run only when *gate != 0
   double half_skin2;   // (skin / 2)^2: displacement that forces a rebuild
   unsigned long long *step_ctr;  // [nsys] steps taken by each system (Langevin counter)
+  // several species: species of each ext bead (images: their source's),
+  // the same in sorted order, and the pooled per-system pair tables
+  unsigned char *type_u;
+  unsigned char *type_s;
+  const PairTab *ptab;
+  const PairTab64 *ptab64;
 };
 
 // ---------------------------------------------------------------------------

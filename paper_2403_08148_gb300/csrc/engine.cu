@@ -82,6 +82,53 @@ static std::vector<double> host_bsp_moduli(int p, int K) {
   return b;
 }
 
+// Small-r Taylor series of the real-space kernel with beta and kappa:
+//   g(r) = [erf(beta r) - erf(kappa r)] / r = sum_k g_k r^{2k},
+//   h(r) = -g'(r) / r = sum_k h_k r^{2k},
+// from erf(x) = 2/sqrt(pi) (x - x^3/3 + x^5/10 - x^7/42).
+static void real_series(double b, double k, double g[4], double h[3]) {
+  const double c = 2.0 / std::sqrt(kPi);
+  const double d1 = b - k, d3 = b * b * b - k * k * k, d5 = std::pow(b, 5) - std::pow(k, 5),
+               d7 = std::pow(b, 7) - std::pow(k, 7);
+  g[0] = c * d1;
+  g[1] = -c * d3 / 3.0;
+  g[2] = c * d5 / 10.0;
+  g[3] = -c * d7 / 42.0;
+  h[0] = c * 2.0 * d3 / 3.0;
+  h[1] = -c * 2.0 * d5 / 5.0;
+  h[2] = c * d7 / 7.0;
+}
+
+// One species pair's constants (Eq. u_ex with s = sigma_i^2 + sigma_j^2;
+// real-space term with beta_ij = sqrt(pi) / (sqrt(2) a_ij)).
+static void species_pair(double A, double si, double sj, double ai, double aj, double kappa,
+                         PairTab *t32, PairTab64 *t64) {
+  const double s = si * si + sj * sj;
+  const double pref = A * std::pow(3.0 / (2.0 * kPi * s), 1.5);
+  const double expc = 3.0 / (2.0 * s);
+  const double beta = std::sqrt(kPi) / (std::sqrt(2.0) * std::sqrt(ai * ai + aj * aj));
+  double g[4], h[3];
+  real_series(beta, kappa, g, h);
+  if (t32) {
+    t32->pref = (float)pref;
+    t32->c2 = (float)(-expc / std::log(2.0));
+    t32->fc = (float)(3.0 / s);
+    t32->beta = (float)beta;
+    for (int k = 0; k < 4; ++k) t32->sg[k] = (float)g[k];
+    for (int k = 0; k < 3; ++k) t32->sh[k] = (float)h[k];
+    t32->pad = 0.0f;
+  }
+  if (t64) {
+    t64->pref = pref;
+    t64->expc = expc;
+    t64->fc = 3.0 / s;
+    t64->beta = beta;
+    for (int k = 0; k < 4; ++k) t64->sg[k] = g[k];
+    for (int k = 0; k < 3; ++k) t64->sh[k] = h[k];
+    t64->pad = 0.0;
+  }
+}
+
 // Fixed-point resolution of the list kernel's pair terms: the largest b
 // (<= 31) with every term below 2^30 units of 2^-b.  Bounds over r <= rc:
 // the Gaussian-core force (3/s) u r peaks at r = sqrt(s/3); the real-space
@@ -123,8 +170,26 @@ std::string validate_spec(const SysSpec &sp) {
   if (!(p.gamma >= 0.0) || !std::isfinite(p.gamma)) return "gamma must be finite and >= 0";
   if (p.gamma > 0.0 && (!(p.kT >= 0.0) || !std::isfinite(p.kT)))
     return "kT must be finite and >= 0";
-  if (!(p.rc > 0) || !(p.kappa > 0) || !(p.lB >= 0) || !(p.sigma > 0) || !(p.a > 0) || !(p.A >= 0))
-    return "rc, kappa, sigma, a must be > 0 and lB, A >= 0";
+  const int nt = p.ntypes;
+  if (nt < 0 || nt > GCME_MAX_TYPES) return "ntypes must be in [0, 8]";
+  if (!(p.rc > 0) || !(p.kappa > 0) || !(p.lB >= 0)) return "rc, kappa must be > 0 and lB >= 0";
+  if (nt == 0 && (!(p.sigma > 0) || !(p.a > 0) || !(p.A >= 0)))
+    return "sigma, a must be > 0 and A >= 0";
+  for (int t = 0; t < nt; ++t) {
+    if (!(p.sigma_tab[t] > 0) || !(p.a_tab[t] > 0) || !std::isfinite(p.sigma_tab[t]) ||
+        !std::isfinite(p.a_tab[t]))
+      return "species sigma_i and a_i must be finite and > 0";
+    for (int u = 0; u < nt; ++u) {
+      const double A = p.A_tab[t * GCME_MAX_TYPES + u];
+      if (!(A >= 0) || !std::isfinite(A)) return "species A_ij must be finite and >= 0";
+      if (A != p.A_tab[u * GCME_MAX_TYPES + t]) return "species table A_ij must be symmetric";
+    }
+  }
+  if (!sp.types.empty()) {
+    if ((int64_t)sp.types.size() != sp.n) return "species array size mismatch";
+    for (int32_t t : sp.types)
+      if (t < 0 || t >= std::max(nt, 1)) return "bead species out of range [0, ntypes)";
+  }
   for (int a = 0; a < 3; ++a) {
     if (!(p.box[a] >= p.rc * (1.0 + 1e-4))) {
       snprintf(buf, sizeof buf, "box side %d (%g) shorter than the cutoff %g", a, p.box[a], p.rc);
@@ -148,18 +213,34 @@ std::string validate_spec(const SysSpec &sp) {
     snprintf(buf, sizeof buf, "system is not neutral (net charge %g)", qs);
     return buf;
   }
-  // non-collapse condition (Gaussian core model section) for the largest
-  // charge product: A / sigma_ij^3 > 4 pi^{3/2} z z lB / (3^{3/2} a_ij)
+  // non-collapse condition (Gaussian core model section) for every pair of
+  // species present, with their largest charges:
+  //   A_ij / sigma_ij^3 > 4 pi^{3/2} |z_i z_j| lB / (3^{3/2} a_ij)
   if (qmax > 0 && p.lB > 0) {
-    double sij = std::sqrt(2.0) * p.sigma, aij = std::sqrt(2.0) * p.a;
-    double lhs = p.A / (sij * sij * sij);
-    double rhs = 4.0 * std::pow(kPi, 1.5) * qmax * qmax * p.lB / (std::pow(3.0, 1.5) * aij);
-    if (!(lhs > rhs)) {
-      snprintf(buf, sizeof buf,
-               "non-collapse condition violated: A/sigma_ij^3 = %g <= 4 pi^1.5 lB z^2/(3^1.5 a_ij) = %g",
-               lhs, rhs);
-      return buf;
+    const int ns = std::max(nt, 1);
+    std::vector<double> qm(ns, 0.0);
+    for (int64_t i = 0; i < sp.n; ++i) {
+      const int t = sp.types.empty() ? 0 : sp.types[i];
+      qm[t] = std::fmax(qm[t], std::fabs(sp.q[i]));
     }
+    for (int t = 0; t < ns; ++t)
+      for (int u = t; u < ns; ++u) {
+        if (!(qm[t] * qm[u] > 0)) continue;
+        const double st = nt ? p.sigma_tab[t] : p.sigma, su = nt ? p.sigma_tab[u] : p.sigma;
+        const double at = nt ? p.a_tab[t] : p.a, au = nt ? p.a_tab[u] : p.a;
+        const double A = nt ? p.A_tab[t * GCME_MAX_TYPES + u] : p.A;
+        const double sij = std::sqrt(st * st + su * su), aij = std::sqrt(at * at + au * au);
+        const double lhs = A / (sij * sij * sij);
+        const double rhs =
+            4.0 * std::pow(kPi, 1.5) * qm[t] * qm[u] * p.lB / (std::pow(3.0, 1.5) * aij);
+        if (!(lhs > rhs)) {
+          snprintf(buf, sizeof buf,
+                   "non-collapse condition violated (species %d, %d): A/sigma_ij^3 = %g <= "
+                   "4 pi^1.5 lB |z z|/(3^1.5 a_ij) = %g",
+                   t, u, lhs, rhs);
+          return buf;
+        }
+      }
   }
   if (p.geometry != GCME_BULK) {
     if (!(p.H > 0)) return "slab height H must be > 0";
@@ -336,14 +417,30 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
       return GCME_ERR_INVALID;
     }
   }
+  // several species: a system with ntypes >= 2 makes the whole batch take
+  // per-pair constants from tables (a one-species table is the scalars)
+  species = false;
+  for (auto &sp : specs) species = species || sp.p.ntypes >= 2;
+  if (species && (fp64 ? false : (cell_factor == 2))) {
+    set_error("several species need cell_factor 1 (27-cell kernel) or the FP64 path");
+    return GCME_ERR_INVALID;
+  }
   hsys.assign(ns, SysDesc{});
+  std::vector<gcme_params> eff(ns);
   bead_off.assign(ns + 1, 0);
   long long nr = 0, ne = 0, nq = 0, nimg = 0, ncell = 0, ngrid = 0, nbond = 0;
   int ntw = 0;
   std::vector<std::vector<int>> qlists(ns), imgs(ns);
   for (int s = 0; s < ns; ++s) {
     const SysSpec &sp = specs[s];
-    const gcme_params &p = sp.p;
+    gcme_params &p = eff[s];
+    p = sp.p;
+    if (p.ntypes == 1) {  // one species: its table entries are the scalars
+      p.A = p.A_tab[0];
+      p.sigma = p.sigma_tab[0];
+      p.a = p.a_tab[0];
+      p.ntypes = 0;
+    }
     SysDesc &S = hsys[s];
     S.n = (int)sp.n;
     std::vector<int> &ql = qlists[s];
@@ -404,10 +501,16 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     S.gc_expc = 3.0 / (2.0 * s2);
     S.gc_fc = 3.0 / s2;
     S.gc_c2f = (float)(-S.gc_expc / std::log(2.0));
-    double sq = 0.0;
-    for (double z : sp.q) sq += z * z;
+    double sq = 0.0, born = 0.0;  // sum z^2, sum z^2 / (2 a_i)
+    for (int i = 0; i < S.n; ++i) {
+      const double z = sp.q[i];
+      const double ai = (p.ntypes && !sp.types.empty()) ? p.a_tab[sp.types[i]]
+                        : (p.ntypes ? p.a_tab[0] : p.a);
+      sq += z * z;
+      born += z * z / (2.0 * ai);
+    }
     S.e_corr = -p.lB * p.kappa / std::sqrt(kPi) * sq;
-    S.e_self = p.lB * sq / (2.0 * p.a);
+    S.e_self = p.lB * born;
     S.recip_scale = p.geometry == GCME_SLAB_IMAGE ? 0.5 : 1.0;
     S.H = p.H;
     S.wall_A = p.geometry == GCME_BULK ? 0.0 : p.wall_A;
@@ -419,17 +522,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     S.lgv_c1 = std::exp(-p.gamma * p.dt);
     S.lgv_c2 = S.langevin ? std::sqrt((1.0 - S.lgv_c1 * S.lgv_c1) * p.kT) : 0.0;
     S.seed = p.seed;
-    // Taylor series of g and h: erf(x) = 2/sqrt(pi) (x - x^3/3 + x^5/10 - x^7/42)
-    const double b = S.beta, k = p.kappa, c = 2.0 / std::sqrt(kPi);
-    const double d1 = b - k, d3 = b * b * b - k * k * k, d5 = std::pow(b, 5) - std::pow(k, 5),
-                 d7 = std::pow(b, 7) - std::pow(k, 7);
-    S.ser_g[0] = c * d1;
-    S.ser_g[1] = -c * d3 / 3.0;
-    S.ser_g[2] = c * d5 / 10.0;
-    S.ser_g[3] = -c * d7 / 42.0;
-    S.ser_h[0] = c * 2.0 * d3 / 3.0;
-    S.ser_h[1] = -c * 2.0 * d5 / 5.0;
-    S.ser_h[2] = c * d7 / 7.0;
+    real_series(S.beta, p.kappa, S.ser_g, S.ser_h);
     for (int t = 0; t < 4; ++t) S.ser_gf[t] = (float)S.ser_g[t];
     for (int t = 0; t < 3; ++t) S.ser_hf[t] = (float)S.ser_h[t];
     S.betaf = (float)S.beta;
@@ -451,13 +544,46 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   }
   n_real = nr;
   n_ext = ne;
+  // species tables (ntypes x ntypes per system) and the species of every
+  // ext bead (images: their source's)
+  std::vector<PairTab> htab;
+  std::vector<PairTab64> htab64;
+  std::vector<unsigned char> htype;
+  if (species) {
+    htype.assign(ne, 0);
+    for (int s = 0; s < ns; ++s) {
+      SysDesc &S = hsys[s];
+      const gcme_params &p = eff[s];
+      const SysSpec &sp = specs[s];
+      const int nt = std::max(p.ntypes, 1);
+      S.ntypes = nt;
+      S.tab_off = fp64 ? (long long)htab64.size() : (long long)htab.size();
+      for (int t = 0; t < nt; ++t)
+        for (int u = 0; u < nt; ++u) {
+          const double A = p.ntypes ? p.A_tab[t * GCME_MAX_TYPES + u] : p.A;
+          const double st = p.ntypes ? p.sigma_tab[t] : p.sigma;
+          const double su = p.ntypes ? p.sigma_tab[u] : p.sigma;
+          const double at = p.ntypes ? p.a_tab[t] : p.a, au = p.ntypes ? p.a_tab[u] : p.a;
+          PairTab t32;
+          PairTab64 t64;
+          species_pair(A, st, su, at, au, p.kappa, &t32, &t64);
+          if (fp64) htab64.push_back(t64);
+          else htab.push_back(t32);
+        }
+      for (int i = 0; i < S.n; ++i)
+        htype[S.ext_off + i] = (unsigned char)(sp.types.empty() ? 0 : sp.types[i]);
+      for (size_t k = 0; k < imgs[s].size(); ++k)
+        htype[S.ext_off + S.n + k] = htype[S.ext_off + imgs[s][k]];
+    }
+  }
   // Neighbour lists: FP32 path, 27-cell stencil, and the two-cell build
   // stencil must cover rc + skin (cells of side >= rc >= skin).
   {
-    bool can = !fp64 && cell_factor == 1 && ne < (1LL << 25);
+    bool can = !fp64 && cell_factor == 1 && ne < (1LL << 25) && !species;
     for (auto &sp : specs) can = can && sp.p.rc >= kListSkin;
     if (path == GCME_PAIR_LIST && !can) {
-      set_error("pair_path LIST needs FP32, cell_factor 1, rc >= 0.4 and fewer than 2^25 beads");
+      set_error("pair_path LIST needs FP32, one species, cell_factor 1, rc >= 0.4 and fewer "
+                "than 2^25 beads");
       return GCME_ERR_INVALID;
     }
     // AUTO takes the 27-cell kernel: on dense soft-core fluids (~340
@@ -579,6 +705,14 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     cv.add(&P.list_flags, 4);
     cv.add(&P.list_ovf, 2 * (long long)ns);
   }
+  PairTab *d_tab = nullptr;
+  PairTab64 *d_tab64 = nullptr;
+  if (species) {
+    cv.add(&P.type_u, ne);
+    cv.add(&P.type_s, ne);
+    if (fp64) cv.add(&d_tab64, (long long)htab64.size());
+    else cv.add(&d_tab, (long long)htab.size());
+  }
   scratch_bytes = cv.off;
   cudaError_t e = cudaMalloc(&arena_, cv.off);
   if (e != cudaSuccess) {
@@ -602,6 +736,8 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   P.n_grid = ngrid;
   for (int a = 0; a < 3; ++a) plan.work[a] = fw[a];
   plan.plane_work = d_planes;
+  P.ptab = d_tab;
+  P.ptab64 = d_tab64;
   if (use_list) {
     P.nbr_stride = list_stride;
     P.gate = P.list_flags;
@@ -675,6 +811,12 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   GCME_CK(up(pair_work, pw.data(), sizeof(int2) * n_pair_work));
   for (int a = 0; a < 3; ++a) GCME_CK(up(fw[a], fftw[a].data(), sizeof(int2) * plan.nwork[a]));
   GCME_CK(up(d_planes, planes.data(), sizeof(int2) * plan.nplane));
+  if (species) {
+    GCME_CK(up(P.type_u, htype.data(), ne));
+    GCME_CK(up(P.type_s, htype.data(), ne));  // overwritten by the first cell sort
+    if (fp64) GCME_CK(up(d_tab64, htab64.data(), sizeof(PairTab64) * htab64.size()));
+    else GCME_CK(up(d_tab, htab.data(), sizeof(PairTab) * htab.size()));
+  }
   if (own_state) {
     GCME_CK(cudaMemset(P.pos, 0, sizeof(double) * 3 * nr));
     GCME_CK(cudaMemset(P.vel, 0, (fp64 ? 8 : 4) * 3 * nr));
@@ -915,8 +1057,8 @@ void gcme_params_default(gcme_params *p, double L, int32_t K) {
   p->seed = 0;
 }
 
-int gcme_validate(const gcme_params *p, int64_t n, const double *h_q, const int32_t *h_bonds,
-                  int64_t nbonds) {
+int gcme_validate(const gcme_params *p, int64_t n, const double *h_q, const int32_t *h_types,
+                  const int32_t *h_bonds, int64_t nbonds) {
   if (!p || !h_q || n < 1 || nbonds < 0 || (nbonds > 0 && !h_bonds)) {
     set_error("invalid argument to gcme_validate");
     return GCME_ERR_INVALID;
@@ -925,6 +1067,7 @@ int gcme_validate(const gcme_params *p, int64_t n, const double *h_q, const int3
   sp.p = *p;
   sp.n = n;
   sp.q.assign(h_q, h_q + n);
+  if (h_types) sp.types.assign(h_types, h_types + n);
   if (nbonds) sp.bonds.assign(h_bonds, h_bonds + 2 * nbonds);
   std::string err = validate_spec(sp);
   if (!err.empty()) {
@@ -954,7 +1097,8 @@ int gcme_ctx_create(gcme_ctx **out, int device) {
 void gcme_ctx_destroy(gcme_ctx *ctx) { delete ctx; }
 
 int gcme_system_create(gcme_ctx *ctx, const gcme_params *p, int64_t n, const double *h_q,
-                       const int32_t *h_bonds, int64_t nbonds, gcme_sys **out) {
+                       const int32_t *h_types, const int32_t *h_bonds, int64_t nbonds,
+                       gcme_sys **out) {
   if (!ctx || !p || !h_q || !out || n < 1 || nbonds < 0 || (nbonds > 0 && !h_bonds)) {
     set_error("invalid argument to gcme_system_create");
     return GCME_ERR_INVALID;
@@ -963,6 +1107,7 @@ int gcme_system_create(gcme_ctx *ctx, const gcme_params *p, int64_t n, const dou
   sp.p = *p;
   sp.n = n;
   sp.q.assign(h_q, h_q + n);
+  if (h_types) sp.types.assign(h_types, h_types + n);
   if (nbonds) sp.bonds.assign(h_bonds, h_bonds + 2 * nbonds);
   gcme_sys *s = new gcme_sys;
   s->ctx = ctx;
@@ -1296,8 +1441,8 @@ int gcme_batch_autotune(gcme_batch *bt, int32_t flags, gcme_tuning *out, gcme_st
 
 // ---- batch ----------------------------------------------------------------
 int gcme_batch_create(gcme_ctx *ctx, int32_t nsys, const gcme_params *params, const int64_t *n,
-                      const double *h_q, const int32_t *h_bonds, const int64_t *h_bond_count,
-                      gcme_batch **out) {
+                      const double *h_q, const int32_t *h_types, const int32_t *h_bonds,
+                      const int64_t *h_bond_count, gcme_batch **out) {
   if (!ctx || nsys < 1 || !params || !n || !h_q || !out) {
     set_error("invalid argument to gcme_batch_create");
     return GCME_ERR_INVALID;
@@ -1312,6 +1457,7 @@ int gcme_batch_create(gcme_ctx *ctx, int32_t nsys, const gcme_params *params, co
       return GCME_ERR_INVALID;
     }
     specs[s].q.assign(h_q + qo, h_q + qo + n[s]);
+    if (h_types) specs[s].types.assign(h_types + qo, h_types + qo + n[s]);
     qo += n[s];
     int64_t nb = h_bond_count ? h_bond_count[s] : 0;
     if (nb > 0) {

@@ -26,6 +26,7 @@ struct SysSpec {
   gcme_params p;
   int64_t n = 0;
   std::vector<double> q;
+  std::vector<int32_t> types;  // species per bead (empty: all species 0)
   std::vector<int32_t> bonds;  // 2 * nbond, local indices
 };
 
@@ -85,6 +86,7 @@ class Engine {
   bool fp64 = false;
   int cell_factor = 1;  // 1: 27-cell stencil; 2: fine cells with culling
   bool use_list = false;  // FP32 pair terms over Verlet neighbour lists
+  bool species = false;   // several species: per-pair constants from tables
   int pair_split = 0;   // 3 or 9 work items per home cell (0: default)
   int pair_threads = kDefaultPairThreads;  // 128 (3 core warps) or 160 (4)
   int pair_ctas_per_sm = 0;  // 0: one CTA per work item; else resident CTAs per SM fetching items

@@ -16,16 +16,18 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_fine(Pool P, const int2 *
 // launch): a CTA takes the next item when it finishes one, so heavy cells do
 // not leave SMs idle at the end, and a grid smaller than the SMs' capacity
 // leaves slots free for the concurrent PME branch.
-template <bool VIR, bool DBG>
+template <bool VIR, bool DBG, bool MT>
 __global__ void __launch_bounds__(160, 6) k_pair_f32(Pool P, const int2 *work, int nwork,
                                                      int *counter) {
   __shared__ float4 sj[kPairCap];
   __shared__ PairSeg seg[9];
   __shared__ int s_total;
   __shared__ int s_item;
+  __shared__ unsigned char stj[MT ? kPairCap : 1];
+  __shared__ __align__(16) PairTab stab[MT ? kMaxTypes * kMaxTypes : 1];
   if (!counter) {  // static: one item per CTA (grid = items)
     for (int w = blockIdx.x; w < nwork; w += gridDim.x)
-      dev_pair_f32_item<VIR, DBG>(P, work, w, sj, seg, &s_total);
+      dev_pair_f32_item<VIR, DBG, MT>(P, work, w, sj, seg, &s_total, stj, stab);
     return;
   }
   while (true) {
@@ -33,7 +35,7 @@ __global__ void __launch_bounds__(160, 6) k_pair_f32(Pool P, const int2 *work, i
     __syncthreads();
     const int w = s_item;
     if (w >= nwork) break;
-    dev_pair_f32_item<VIR, DBG>(P, work, w, sj, seg, &s_total);
+    dev_pair_f32_item<VIR, DBG, MT>(P, work, w, sj, seg, &s_total, stj, stab);
   }
 }
 
@@ -111,22 +113,35 @@ __global__ void __launch_bounds__(128) k_pair_f64(Pool P) {
               const double d[3] = {pj.x + nn[0] * S.box[0] - pi.x, pj.y + nn[1] * S.box[1] - pi.y,
                                    pj.z + nn[2] * S.box[2] - pi.z};
               const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+              // pair constants: the system's, or the species pair's
+              double pref = S.gc_pref, expc = S.gc_expc, fc = S.gc_fc, beta = S.beta;
+              const double *ser_g = S.ser_g, *ser_h = S.ser_h;
+              if (P.ptab64) {
+                const PairTab64 &T =
+                    P.ptab64[S.tab_off + S.ntypes * (int)P.type_s[gs] + (int)P.type_s[j]];
+                pref = T.pref;
+                expc = T.expc;
+                fc = T.fc;
+                beta = T.beta;
+                ser_g = T.sg;
+                ser_h = T.sh;
+              }
               double fs = 0.0;
               if (j - jb >= ja) {  // real j: Gaussian core
-                const double u = S.gc_pref * exp(-S.gc_expc * r2);
+                const double u = pref * exp(-expc * r2);
                 eg += 0.5 * u;
-                fs += S.gc_fc * u;
+                fs += fc * u;
               }
               const double qq = pi.w * pj.w;
               if (qq != 0.0) {
                 double g, h;
                 if (r2 < 1e-4) {
-                  g = S.ser_g[0] + r2 * (S.ser_g[1] + r2 * (S.ser_g[2] + r2 * S.ser_g[3]));
-                  h = S.ser_h[0] + r2 * (S.ser_h[1] + r2 * S.ser_h[2]);
+                  g = ser_g[0] + r2 * (ser_g[1] + r2 * (ser_g[2] + r2 * ser_g[3]));
+                  h = ser_h[0] + r2 * (ser_h[1] + r2 * ser_h[2]);
                 } else {
                   const double r = sqrt(r2);
-                  g = (erfc(S.kappa * r) - erfc(S.beta * r)) / r;
-                  const double dd = two_sqrtpi * (S.beta * exp(-S.beta * S.beta * r2) -
+                  g = (erfc(S.kappa * r) - erfc(beta * r)) / r;
+                  const double dd = two_sqrtpi * (beta * exp(-beta * beta * r2) -
                                                   S.kappa * exp(-S.kappa * S.kappa * r2));
                   h = (g - dd) / r2;
                 }
@@ -176,9 +191,15 @@ void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell
   const int grid = dyn ? std::max(1, std::min(nwork, ctas)) : nwork;
   if (dyn) cudaMemsetAsync(counter, 0, sizeof(int), st);
   else counter = nullptr;
-  if (dbg) k_pair_f32<false, true><<<grid, tb, 0, st>>>(P, work, nwork, counter);
-  else if (vir) k_pair_f32<true, false><<<grid, tb, 0, st>>>(P, work, nwork, counter);
-  else k_pair_f32<false, false><<<grid, tb, 0, st>>>(P, work, nwork, counter);
+  if (P.ptab) {  // several species
+    if (dbg) k_pair_f32<false, true, true><<<grid, tb, 0, st>>>(P, work, nwork, counter);
+    else if (vir) k_pair_f32<true, false, true><<<grid, tb, 0, st>>>(P, work, nwork, counter);
+    else k_pair_f32<false, false, true><<<grid, tb, 0, st>>>(P, work, nwork, counter);
+    return;
+  }
+  if (dbg) k_pair_f32<false, true, false><<<grid, tb, 0, st>>>(P, work, nwork, counter);
+  else if (vir) k_pair_f32<true, false, false><<<grid, tb, 0, st>>>(P, work, nwork, counter);
+  else k_pair_f32<false, false, false><<<grid, tb, 0, st>>>(P, work, nwork, counter);
 }
 
 }  // namespace gcme

@@ -70,28 +70,41 @@ __device__ __forceinline__ float pair_r2(const float4 &xj, const float4 &xi, con
 // Gaussian core over real j in [t0, t1): every lane evaluates every
 // candidate (the exponential is cheap next to the test, so masking beats
 // branching); out-of-cutoff candidates contribute exactly zero.
-template <bool SHIFT, bool SELF, bool VIR, bool DBG>
+//
+// MT (several species): the pair constants come from row[species of j] (the
+// row of i's species in the system's table), e carries the prefactor and
+// the force sums carry fc, so pair_write scales them by 1 instead.
+template <bool SHIFT, bool SELF, bool VIR, bool DBG, bool MT = false>
 __device__ __forceinline__ void pair_core(const float4 *__restrict__ J, int t0, int t1,
                                           int jsorted0, const float4 &xi, int isorted,
                                           const PairSeg &sg, float rc2, float gcc, PairAcc &A,
-                                          const Pool &P, int s) {
+                                          const Pool &P, int s, const PairTab *row = nullptr,
+                                          const unsigned char *tj = nullptr) {
 #pragma unroll 4
   for (int t = t0; t < t1; ++t) {
     float dx, dy, dz;
     const float r2 = pair_r2<SHIFT>(J[t], xi, sg, dx, dy, dz);
     bool in = r2 < rc2;
     if (SELF) in = in && (jsorted0 + t != isorted);
-    float e = ex2_approx(r2 * gcc);
-    e = in ? e : 0.0f;
+    float e, fs;
+    if (MT) {
+      const float4 T = *reinterpret_cast<const float4 *>(row + tj[t]);  // pref, c2, fc, beta
+      e = in ? T.x * ex2_approx(r2 * T.y) : 0.0f;
+      fs = T.z * e;
+    } else {
+      e = ex2_approx(r2 * gcc);
+      e = in ? e : 0.0f;
+      fs = e;
+    }
     A.eg += e;
-    A.gx = fmaf(e, dx, A.gx);
-    A.gy = fmaf(e, dy, A.gy);
-    A.gz = fmaf(e, dz, A.gz);
+    A.gx = fmaf(fs, dx, A.gx);
+    A.gy = fmaf(fs, dy, A.gy);
+    A.gz = fmaf(fs, dz, A.gz);
     if (VIR) {
-      float ex = e * dx, ey = e * dy;
+      float ex = fs * dx, ey = fs * dy;
       A.wg[0] = fmaf(ex, dx, A.wg[0]);
       A.wg[1] = fmaf(ey, dy, A.wg[1]);
-      A.wg[2] = fmaf(e * dz, dz, A.wg[2]);
+      A.wg[2] = fmaf(fs * dz, dz, A.wg[2]);
       A.wg[3] = fmaf(ex, dy, A.wg[3]);
       A.wg[4] = fmaf(ex, dz, A.wg[4]);
       A.wg[5] = fmaf(ey, dz, A.wg[5]);
@@ -113,11 +126,13 @@ __device__ __forceinline__ void pair_core(const float4 *__restrict__ J, int t0, 
 // only, so a warp pays for it once per hit instead of once per candidate.
 // tg marks the first real j (images below it carry no core and are dumped
 // here in debug mode).
-template <bool SHIFT, bool SELF, bool VIR, bool DBG>
+template <bool SHIFT, bool SELF, bool VIR, bool DBG, bool MT = false>
 __device__ __forceinline__ void pair_elec(const float4 *__restrict__ J, int t0, int t1, int tg,
                                           int jsorted0, const float4 &xi, int isorted,
                                           const PairSeg &sg, const SysDesc &S, float rc2,
-                                          PairAcc &A, const Pool &P, int s) {
+                                          PairAcc &A, const Pool &P, int s,
+                                          const PairTab *row = nullptr,
+                                          const unsigned char *tj = nullptr) {
   const bool qi_nz = xi.w != 0.0f;
   for (int c0 = t0; c0 < t1; c0 += 64) {
     const int cn = min(64, t1 - c0);
@@ -139,18 +154,27 @@ __device__ __forceinline__ void pair_elec(const float4 *__restrict__ J, int t0, 
       float dx, dy, dz;
       const float r2 = pair_r2<SHIFT>(xj, xi, sg, dx, dy, dz);
       const float qq = xi.w * xj.w;
+      const float* sgf = S.ser_gf;
+      const float* shf = S.ser_hf;
+      float betaf = S.betaf;
+      if (MT) {
+        const PairTab &T = row[tj[t]];
+        sgf = T.sg;
+        shf = T.sh;
+        betaf = T.beta;
+      }
       float g, h;
       if (r2 < 1e-2f) {
-        g = S.ser_gf[0] + r2 * (S.ser_gf[1] + r2 * (S.ser_gf[2] + r2 * S.ser_gf[3]));
-        h = S.ser_hf[0] + r2 * (S.ser_hf[1] + r2 * S.ser_hf[2]);
+        g = sgf[0] + r2 * (sgf[1] + r2 * (sgf[2] + r2 * sgf[3]));
+        h = shf[0] + r2 * (shf[1] + r2 * shf[2]);
       } else {
         const float r = sqrtf(r2);
         const float rinv = 1.0f / r;
-        const float xb = S.betaf * r, xk = S.kappaf * r;
+        const float xb = betaf * r, xk = S.kappaf * r;
         g = (erfcf(xk) - erfcf(xb)) * rinv;
         const float eb = ex2_approx(-xb * xb * kLog2e);
         const float ek = ex2_approx(-xk * xk * kLog2e);
-        const float dd = kTwoOverSqrtPi * (S.betaf * eb - S.kappaf * ek);
+        const float dd = kTwoOverSqrtPi * (betaf * eb - S.kappaf * ek);
         h = (g - dd) * (rinv * rinv);
       }
       A.ere = fmaf(qq, g, A.ere);
@@ -222,10 +246,10 @@ __device__ __forceinline__ void pair_segment(const float4 *J, int t0, int t1, in
 
 // Write back one lane's partial sums: fixed-point forces, warp-reduced
 // FP64 energies (core, electrostatics) and virial.
-template <bool VIR>
+template <bool VIR, bool MT = false>
 __device__ __forceinline__ void pair_write(const Pool &P, const SysDesc &S, int s, bool valid,
                                            int i, const PairAcc &A) {
-  const float cg = (float)(S.gc_fc * S.gc_pref);
+  const float cg = MT ? 1.0f : (float)(S.gc_fc * S.gc_pref);
   const float lb = (float)S.lB;
   if (valid) {
     const int orig = P.sorted_idx[i];
@@ -233,7 +257,7 @@ __device__ __forceinline__ void pair_write(const Pool &P, const SysDesc &S, int 
     atomic_add_fixed_f(force_ptr(P, S, orig, 1), -(cg * A.gy + lb * A.fy), (float)kFScale);
     atomic_add_fixed_f(force_ptr(P, S, orig, 2), -(cg * A.gz + lb * A.fz), (float)kFScale);
   }
-  double eg = valid ? 0.5 * S.gc_pref * (double)A.eg : 0.0;
+  double eg = valid ? (MT ? 0.5 : 0.5 * S.gc_pref) * (double)A.eg : 0.0;
   double er = valid ? 0.5 * S.lB * (double)A.ere : 0.0;
   eg = warp_sum(eg);
   er = warp_sum(er);
@@ -244,7 +268,7 @@ __device__ __forceinline__ void pair_write(const Pool &P, const SysDesc &S, int 
   }
   if (VIR) {
     // W_ab = 1/2 sum_visits fs d_a d_b  with fs = (3/s) u or lB qq h
-    const double c1 = 0.5 * S.gc_fc * S.gc_pref, c2 = 0.5 * S.lB;
+    const double c1 = MT ? 0.5 : 0.5 * S.gc_fc * S.gc_pref, c2 = 0.5 * S.lB;
     const int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
@@ -259,18 +283,22 @@ __device__ __forceinline__ void pair_write(const Pool &P, const SysDesc &S, int 
 // evaluate the Gaussian core over the real beads (and, in debug mode, list
 // the in-cutoff images); the electrostatics warp evaluates the real-space
 // term of its charged home beads over the charged and image beads.
-template <bool VIR, bool DBG>
+template <bool VIR, bool DBG, bool MT = false>
 __device__ __forceinline__ void pair_role_range(bool core_role, const float4 *J, int t0, int t1,
                                                 const PairSeg &sg, const float4 &xi, int i,
                                                 const SysDesc &S, float rc2, float gcc,
-                                                PairAcc &A, const Pool &P, int s) {
+                                                PairAcc &A, const Pool &P, int s,
+                                                const PairTab *row = nullptr,
+                                                const unsigned char *tj = nullptr) {
   const int a0 = max(t0, min(t1, sg.a)), b0 = max(t0, min(t1, sg.b));
 #define GCME_ROLE(SHIFT, SELF)                                                                    \
   if (core_role) {                                                                                \
-    pair_core<SHIFT, SELF, VIR, DBG>(J, a0, t1, sg.beg, xi, i, sg, rc2, gcc, A, P, s);            \
+    pair_core<SHIFT, SELF, VIR, DBG, MT>(J, a0, t1, sg.beg, xi, i, sg, rc2, gcc, A, P, s, row,    \
+                                         tj);                                                     \
     if (DBG) pair_dump_images<SHIFT>(J, t0, a0, sg.beg, xi, i, sg, rc2, P, s, true);              \
   } else {                                                                                        \
-    pair_elec<SHIFT, SELF, VIR, false>(J, t0, b0, 0, sg.beg, xi, i, sg, S, rc2, A, P, s);         \
+    pair_elec<SHIFT, SELF, VIR, false, MT>(J, t0, b0, 0, sg.beg, xi, i, sg, S, rc2, A, P, s, row, \
+                                           tj);                                                   \
   }
   if (sg.self) {
     GCME_ROLE(false, true)
@@ -291,9 +319,14 @@ __device__ __forceinline__ void pair_role_range(bool core_role, const float4 *J,
 // real beads (real-space electrostatics over the staged charged and image
 // beads).  The two kinds of work run concurrently instead of one after the
 // other in the warp that holds the charged beads.
-template <bool VIR, bool DBG>
+//
+// MT: stj[kPairCap] (species of the staged beads) and stab[nt * nt] (the
+// system's pair table) in shared memory as well.
+template <bool VIR, bool DBG, bool MT = false>
 __device__ __forceinline__ void dev_pair_f32_item(const Pool &P, const int2 *work, int w,
-                                                  float4 *sj, PairSeg *seg, int *s_total_p) {
+                                                  float4 *sj, PairSeg *seg, int *s_total_p,
+                                                  unsigned char *stj = nullptr,
+                                                  PairTab *stab = nullptr) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int ncore = (blockDim.x >> 5) - 1;  // core warps
@@ -307,6 +340,9 @@ __device__ __forceinline__ void dev_pair_f32_item(const Pool &P, const int2 *wor
     return;
   }
   const SysDesc &S = P.sys[s];
+  const int nt = MT ? S.ntypes : 1;
+  if (MT)
+    for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) stab[k] = P.ptab[S.tab_off + k];
   // split 3: item = (cell, dz), 9 neighbour cells; split 9: item =
   // (cell, dy, dz), 3 neighbour cells along x
   const int split = S.pair_split;
@@ -359,7 +395,10 @@ __device__ __forceinline__ void dev_pair_f32_item(const Pool &P, const int2 *wor
   if (fits) {
     for (int k = 0; k < nseg; ++k) {
       const PairSeg &g = seg[k];
-      for (int t = tid; t < g.n; t += blockDim.x) sj[g.soff + t] = P.xyzq_s[g.beg + t];
+      for (int t = tid; t < g.n; t += blockDim.x) {
+        sj[g.soff + t] = P.xyzq_s[g.beg + t];
+        if (MT) stj[g.soff + t] = P.type_s[g.beg + t];
+      }
     }
     __syncthreads();
   }
@@ -382,6 +421,7 @@ __device__ __forceinline__ void dev_pair_f32_item(const Pool &P, const int2 *wor
       valid = i < hbeg + hq;
     }
     const float4 xi = valid ? P.xyzq_s[i] : make_float4(1e30f, 1e30f, 1e30f, 0.0f);
+    const PairTab *row = MT ? stab + nt * (valid ? (int)P.type_s[i] : 0) : nullptr;
     const bool busy = __any_sync(0xffffffffu, valid);
     PairAcc A;
     A.eg = A.ere = A.gx = A.gy = A.gz = A.fx = A.fy = A.fz = 0.0f;
@@ -391,8 +431,8 @@ __device__ __forceinline__ void dev_pair_f32_item(const Pool &P, const int2 *wor
       if (busy)
         for (int k = 0; k < nseg; ++k) {
           const PairSeg g = seg[k];
-          pair_role_range<VIR, DBG>(core_role, sj + g.soff, 0, g.n, g, xi, i, S, rc2, gcc, A, P,
-                                    s);
+          pair_role_range<VIR, DBG, MT>(core_role, sj + g.soff, 0, g.n, g, xi, i, S, rc2, gcc, A,
+                                        P, s, row, MT ? stj + g.soff : nullptr);
         }
     } else {
       for (int k = 0; k < nseg; ++k) {
@@ -400,15 +440,19 @@ __device__ __forceinline__ void dev_pair_f32_item(const Pool &P, const int2 *wor
         for (int c0 = 0; c0 < g.n; c0 += kPairCap) {
           const int c1 = min(g.n, c0 + kPairCap);
           __syncthreads();
-          for (int t = c0 + tid; t < c1; t += blockDim.x) sj[t - c0] = P.xyzq_s[g.beg + t];
+          for (int t = c0 + tid; t < c1; t += blockDim.x) {
+            sj[t - c0] = P.xyzq_s[g.beg + t];
+            if (MT) stj[t - c0] = P.type_s[g.beg + t];
+          }
           __syncthreads();
           // ranges are in segment coordinates; shift the staged base
           if (busy)
-            pair_role_range<VIR, DBG>(core_role, sj - c0, c0, c1, g, xi, i, S, rc2, gcc, A, P, s);
+            pair_role_range<VIR, DBG, MT>(core_role, sj - c0, c0, c1, g, xi, i, S, rc2, gcc, A, P,
+                                          s, row, MT ? stj - c0 : nullptr);
         }
       }
     }
-    if (busy) pair_write<VIR>(P, S, s, valid, i, A);
+    if (busy) pair_write<VIR, MT>(P, S, s, valid, i, A);
   }
   __syncthreads();
 }

@@ -108,8 +108,16 @@ __global__ void __launch_bounds__(128) k_persistent(Pool P, PersistArgs A) {
       float4 *sj = reinterpret_cast<float4 *>(smem);
       PairSeg *seg = reinterpret_cast<PairSeg *>(smem + sizeof(float4) * kPairCap);
       int *st = reinterpret_cast<int *>(smem + sizeof(float4) * kPairCap + sizeof(PairSeg) * 9);
-      for (int w = blockIdx.x; w < A.n_pair_work; w += gridDim.x)
-        dev_pair_f32_item<false, false>(P, A.pair_work, w, sj, seg, st);
+      // several species: the table (16-byte aligned) and the staged species
+      const size_t toff = (sizeof(float4) * kPairCap + sizeof(PairSeg) * 9 + 16 + 15) / 16 * 16;
+      PairTab *stab = reinterpret_cast<PairTab *>(smem + toff);
+      unsigned char *stj = smem + toff + sizeof(PairTab) * kMaxTypes * kMaxTypes;
+      for (int w = blockIdx.x; w < A.n_pair_work; w += gridDim.x) {
+        if (P.ptab)
+          dev_pair_f32_item<false, false, true>(P, A.pair_work, w, sj, seg, st, stj, stab);
+        else
+          dev_pair_f32_item<false, false, false>(P, A.pair_work, w, sj, seg, st);
+      }
     }
     for (long long g = gtid; g < P.n_q * 8; g += gthreads) dev_spread<float>(P, g);
     if (!grid_barrier(B)) return;
@@ -151,8 +159,10 @@ __global__ void __launch_bounds__(128) k_persistent(Pool P, PersistArgs A) {
 }
 #undef GRID_LOOP
 
-size_t persistent_smem(const PmePlan &pl) {
+size_t persistent_smem(const PmePlan &pl, bool species) {
   size_t pair = sizeof(float4) * kPairCap + sizeof(PairSeg) * 9 + 16;
+  if (species)
+    pair = (pair + 15) / 16 * 16 + sizeof(PairTab) * kMaxTypes * kMaxTypes + kPairCap;
   size_t sort = sizeof(long long) * kSortCap + 16;
   size_t fft = 0;
   for (int a = 0; a < 3; ++a) fft = std::max(fft, 2 * (size_t)pl.lpb[a] * pl.kmax[a] * sizeof(float2));
@@ -163,7 +173,7 @@ size_t persistent_smem(const PmePlan &pl) {
 int launch_persistent(const Pool &P, const int2 *pair_work, int n_pair_work, int cell_factor,
                       const PmePlan &pl, long long nsteps, unsigned int *bar_words, double timeout_s,
                       cudaStream_t st) {
-  const size_t smem = persistent_smem(pl);
+  const size_t smem = persistent_smem(pl, P.ptab != nullptr);
   cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int dev = 0, nsm = 0, per_sm = 0, clock_khz = 0;
   cudaGetDevice(&dev);

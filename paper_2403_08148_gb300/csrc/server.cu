@@ -308,6 +308,7 @@ int gcme_submit(gcme_server *srv, const gcme_request *req, uint64_t *ticket) {
   r->spec.p = req->params;
   r->spec.n = req->n;
   r->spec.q.assign(req->h_q, req->h_q + req->n);
+  if (req->h_types) r->spec.types.assign(req->h_types, req->h_types + req->n);
   if (req->nbonds) r->spec.bonds.assign(req->h_bonds, req->h_bonds + 2 * req->nbonds);
   std::string err = validate_spec(r->spec);
   if (!err.empty()) {

@@ -128,7 +128,8 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
   std::ostringstream key;
   key << prop.name << "|nsys=" << hsys.size() << "|n=" << n_real << "|ext=" << n_ext
       << "|q=" << nq << "|cells=" << ncell << "|grid=" << ngrid << "|fp64=" << (int)fp64
-      << "|cf=" << cell_factor << "|geom=" << geom << "|list=" << (int)use_list;
+      << "|cf=" << cell_factor << "|geom=" << geom << "|list=" << (int)use_list
+      << "|species=" << (int)species;
   const bool remeasure = flags & 1, no_cache = flags & 2;
   Tuned t;
   *from_cache = false;

@@ -106,6 +106,46 @@ def test_validation_rejects_bad_bonds_and_slab_box(g):
         g.validate(p, t.q)
 
 
+def _mixture():
+    A = np.array([[25.0, 27.0], [27.0, 25.0]])
+    return synth.make_mixture(400, (0.8, 0.2), (0.0, 1.0), A, np.array([0.5, 0.6]),
+                              np.array([0.5, 0.4]), seed_index=46)
+
+
+def test_species_validation(g):
+    t = _mixture()
+    t.q = np.where(t.types == 1, 1.0, 0.0)
+    t.q[np.nonzero(t.types == 0)[0][: int(t.q.sum())]] = -1.0  # neutral: species 0 takes -1
+    g.validate(g.params_from(t), t.q, types=t.types)
+    p = g.params_from(t)
+    p.A_tab[1] = 26.0  # A_01 != A_10
+    with pytest.raises(g.GcmeError, match="symmetric"):
+        g.validate(p, t.q, types=t.types)
+    bad = t.types.copy()
+    bad[3] = 2
+    with pytest.raises(g.GcmeError, match="out of range"):
+        g.validate(g.params_from(t), t.q, types=bad)
+    p = g.params_from(t)
+    p.ntypes = 9
+    with pytest.raises(g.GcmeError, match="ntypes"):
+        g.validate(p, t.q, types=t.types)
+    p = g.params_from(t)
+    p.sigma_tab[1] = 0.0
+    with pytest.raises(g.GcmeError, match="sigma"):
+        g.validate(p, t.q, types=t.types)
+    # the non-collapse condition is checked for the pair of charged species:
+    # a tiny a_1 breaks it for (1, 1) even though (0, 0) is fine
+    p = g.params_from(t)
+    p.a_tab[1] = 0.02
+    p.a_tab[0] = 0.02
+    with pytest.raises(g.GcmeError, match="non-collapse"):
+        g.validate(p, t.q, types=t.types)
+    # species ids without tables
+    with pytest.raises(g.GcmeError, match="out of range"):
+        g.validate(g.params_from(synth.make_bulk(100, seed_index=47)),
+                   synth.make_bulk(100, seed_index=47).q, types=np.ones(100, np.int32))
+
+
 def test_no_device_reports_error_not_crash(g):
     import torch
     if torch.cuda.is_available():
