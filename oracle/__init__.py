@@ -350,7 +350,7 @@ def energy_forces(s: System, pos=None, recip: str = "spme",
         e, fz = slab_yb(pos, s.q, s.box, s.lB)
         E["slab"] = e
         F[:, 2] += fz
-    if s.geometry in (GEOM_SLAB_NM, GEOM_SLAB_PC):
+    if s.geometry in (GEOM_SLAB_NM, GEOM_SLAB_PC) and s.wall_A != 0.0:  # no wall: none
         e, fz = walls(pos, s.H, s.wall_A, s.wall_sigma2)
         E["wall"] = e
         F[:, 2] += fz
@@ -375,23 +375,36 @@ def forces_subset(s: System, idx, pos=None):
     return pairs_subset(epos, eq, etype, A_tab, sig, a, s.box, s.rc, s.kappa, s.lB, idx)
 
 
+def mobile(s: System) -> np.ndarray:
+    """(n, 1) weights: 1 for beads that move, 0 for beads of a frozen species
+    (explicit electrodes): the integrators leave their positions and
+    velocities as they are and the kinetic energy omits them."""
+    m = np.ones((s.n, 1))
+    if s.types is not None and s.frozen_mask:
+        m[((s.frozen_mask >> np.asarray(s.types)) & 1) == 1] = 0.0
+    return m
+
+
 def velocity_verlet(s: System, nsteps: int, recip: str = "spme", record=None):
     """NVE velocity Verlet, unit masses, FP64:
-        v += dt/2 F;  x += dt v;  F = F(x);  v += dt/2 F.
+        v += dt/2 F;  x += dt v;  F = F(x);  v += dt/2 F
+    (beads of frozen species keep x and v).
     Returns (pos, vel, list of per-step dicts {potential, kinetic})."""
     pos = s.pos.copy()
     vel = s.vel.copy()
     dt = s.dt
+    m = mobile(s)
     ef = energy_forces(s, pos, recip=recip)
     F = ef["forces"]
-    hist = [dict(potential=ef["potential"], kinetic=0.5 * float(np.sum(vel * vel)))]
+    hist = [dict(potential=ef["potential"], kinetic=0.5 * float(np.sum(m * vel * vel)))]
     for _ in range(nsteps):
-        vel += 0.5 * dt * F
-        pos += dt * vel
+        vel += m * (0.5 * dt * F)
+        pos += m * (dt * vel)
         ef = energy_forces(s, pos, recip=recip)
         F = ef["forces"]
-        vel += 0.5 * dt * F
-        hist.append(dict(potential=ef["potential"], kinetic=0.5 * float(np.sum(vel * vel))))
+        vel += m * (0.5 * dt * F)
+        hist.append(dict(potential=ef["potential"],
+                         kinetic=0.5 * float(np.sum(m * vel * vel))))
     return pos, vel, hist
 
 
@@ -490,14 +503,15 @@ def langevin_baoab(s: System, nsteps: int, gamma: float, kT: float, seed: int,
         ef = energy_forces(s, x, recip=recip)
         return ef["forces"], ef["potential"]
 
+    m = mobile(s) if hasattr(s, "types") else np.ones((pos.shape[0], 1))
     F, U = fe(pos)
-    hist = [dict(potential=U, kinetic=0.5 * float(np.sum(vel * vel)))]
+    hist = [dict(potential=U, kinetic=0.5 * float(np.sum(m * vel * vel)))]
     for n in range(step0, step0 + nsteps):
-        vel += 0.5 * dt * F
-        pos += 0.5 * dt * vel
-        vel = c1 * vel + c2 * langevin_noise(seed, n, pos.shape[0])
-        pos += 0.5 * dt * vel
+        vel += m * (0.5 * dt * F)
+        pos += m * (0.5 * dt * vel)
+        vel = np.where(m > 0, c1 * vel + c2 * langevin_noise(seed, n, pos.shape[0]), vel)
+        pos += m * (0.5 * dt * vel)
         F, U = fe(pos)
-        vel += 0.5 * dt * F
-        hist.append(dict(potential=U, kinetic=0.5 * float(np.sum(vel * vel))))
+        vel += m * (0.5 * dt * F)
+        hist.append(dict(potential=U, kinetic=0.5 * float(np.sum(m * vel * vel))))
     return pos, vel, hist

@@ -120,6 +120,7 @@ class System:
     A_tab: Optional[np.ndarray] = None   # (nt, nt) A_ij, symmetric
     sig_tab: Optional[np.ndarray] = None  # (nt,) sigma_i
     a_tab: Optional[np.ndarray] = None   # (nt,) a_i
+    frozen_mask: int = 0                 # bit t: beads of species t do not move
 
     @property
     def n(self) -> int:
@@ -376,6 +377,62 @@ def make_mixture(n: int, fractions, charges, A_tab, sig_tab, a_tab, rho: float =
                   wall_A=wA, wall_sigma2=ws2, types=types,
                   A_tab=np.asarray(A_tab, float), sig_tab=np.asarray(sig_tab, float),
                   a_tab=np.asarray(a_tab, float))
+
+
+def hcp_layer(nx: int, ny: int, b: float = 0.5, z: float = 0.0) -> np.ndarray:
+    """Triangular (close-packed) layer of nx x ny points of spacing b in the
+    x-y plane at height z; rows alternate by b/2 so that the layer is
+    periodic in a box of nx b by ny b sqrt(3)/2 (ny even)."""
+    j, i = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    x = (i + 0.5 * (j % 2)) * b
+    y = j * b * math.sqrt(3.0) / 2.0
+    return np.stack([x.ravel(), y.ravel(), np.full(x.size, z)], axis=1)
+
+
+def make_electrode_slab(geometry: int, nx: int = 16, ny: int = 18, H: float = 20.0,
+                        n_chains: int = 10, chain_len: int = 20, rho: float = 3.0,
+                        sigma_q: float = 0.005 * bead_diameter_nm() ** 2,
+                        seed_index: int = 10, K=None, margin: float = 0.75) -> System:
+    """Fluid between explicit electrodes (Illustrative example and the
+    performance table's slab systems): at z = 0 and z = H one close-packed
+    layer each of beads of size d/2 (sigma = a = 0.25, species 1, frozen)
+    with spacing d/2, carrying +sigma_q and -sigma_q per unit area (sigma_q
+    in e/d^2; default 0.005 e/nm^2); polyanion chains (-1) with counterions
+    (+1) and solvent (species 0) at density rho in between.  Box nx/2 by
+    ny sqrt(3)/4 by 3H (nonmetal) or 2H (image charges); no continuum wall."""
+    rng = _rng(seed_index)
+    b = 0.5
+    Lx, Ly = nx * b, ny * b * math.sqrt(3.0) / 2.0
+    box = np.array([Lx, Ly, (3.0 if geometry == GEOM_SLAB_NM else 2.0) * H])
+    lo, hi = hcp_layer(nx, ny, b, 0.0), hcp_layer(nx, ny, b, H)
+    ne = lo.shape[0]
+    q_e = sigma_q * (Lx * Ly) / ne
+    n_fluid = int(round(rho * Lx * Ly * (H - 2 * margin)))
+    n_mono = n_chains * chain_len
+    zlim = (margin, H - margin)
+    cpos, bonds = _chains(rng, n_chains, chain_len, box, zlim=zlim)
+    n_other = n_fluid - n_mono
+    other = rng.uniform(0.0, 1.0, size=(n_other, 3)) * box
+    other[:, 2] = rng.uniform(zlim[0], zlim[1], size=n_other)
+    fluid = _wrap(np.concatenate([cpos, other]), box, periodic=(True, True, False))
+    pos = np.concatenate([fluid, lo, hi])
+    n = pos.shape[0]
+    q = np.zeros(n)
+    q[:n_mono] = -1.0
+    q[n_mono: 2 * n_mono] = 1.0
+    q[n_fluid: n_fluid + ne] = q_e
+    q[n_fluid + ne:] = -q_e
+    types = np.zeros(n, np.int32)
+    types[n_fluid:] = 1
+    vel = _velocities(rng, n)
+    vel[n_fluid:] = 0.0
+    if K is None:
+        K = tuple(smooth_size(int(math.ceil(v))) for v in box)
+    return System(name=f"electrodes_{GEOM_NAMES[geometry]}_n{n}", geometry=geometry, box=box,
+                  pos=pos, vel=vel, q=q, bonds=bonds, kappa=ewald_kappa(3.0),
+                  K=tuple(int(k) for k in K), H=H, wall_A=0.0, wall_sigma2=0.0, types=types,
+                  A_tab=np.full((2, 2), 25.0), sig_tab=np.array([0.5, 0.25]),
+                  a_tab=np.array([0.5, 0.25]), frozen_mask=1 << 1)
 
 
 # ---------------------------------------------------------------------------
