@@ -118,7 +118,7 @@ typedef struct gcme_params {
    * interact with A_tab[t * GCME_MAX_TYPES + u] (symmetric).  Beads get
    * their species from h_types at creation. */
   int32_t ntypes;
-  int32_t pad1;
+  int32_t frozen_mask; /* bit t set: beads of species t never move (electrodes) */
   double A_tab[GCME_MAX_TYPES * GCME_MAX_TYPES];
   double sigma_tab[GCME_MAX_TYPES];
   double a_tab[GCME_MAX_TYPES];
@@ -131,7 +131,13 @@ typedef struct gcme_params {
  * real-space term of Eq. ewald, the Born self energy lB z_i^2 / (2 a_i) per
  * bead; image beads keep their source's species (a_i, no Gaussian core).
  * Supported by the 27-cell FP32 kernel (graph and persistent launches) and
- * the FP64 kernel; the fine-cell and neighbour-list paths reject it. */
+ * the FP64 kernel; the fine-cell and neighbour-list paths reject it.
+ *
+ * Frozen species (frozen_mask): explicit electrodes as in the performance
+ * table's slab systems, close-packed layers of beads of size d/2 with a
+ * fixed charge per bead.  Their beads interact like any other but the
+ * integrators leave their positions and velocities unchanged and the
+ * kinetic energy omits them. */
 
 /* Langevin dynamics (gamma > 0).  The paper integrates Langevin equations of
  * motion in the canonical ensemble (method of image charges and illustrative

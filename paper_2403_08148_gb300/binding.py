@@ -45,7 +45,7 @@ class Params(ctypes.Structure):
                 ("bond_r0", ctypes.c_double), ("cell_factor", ctypes.c_int32),
                 ("pair_path", ctypes.c_int32), ("gamma", ctypes.c_double),
                 ("kT", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("ntypes", ctypes.c_int32), ("pad1", ctypes.c_int32),
+                ("ntypes", ctypes.c_int32), ("frozen_mask", ctypes.c_int32),
                 ("A_tab", ctypes.c_double * (MAX_TYPES * MAX_TYPES)),
                 ("sigma_tab", ctypes.c_double * MAX_TYPES),
                 ("a_tab", ctypes.c_double * MAX_TYPES)]
@@ -204,6 +204,7 @@ def params_from(s, precision: int = GCME_FP32, cell_factor: int = 0,
         if nt > MAX_TYPES:
             raise ValueError(f"at most {MAX_TYPES} species")
         p.ntypes = nt
+        p.frozen_mask = int(getattr(s, "frozen_mask", 0))
         for t in range(nt):
             p.sigma_tab[t] = float(s.sig_tab[t])
             p.a_tab[t] = float(s.a_tab[t])

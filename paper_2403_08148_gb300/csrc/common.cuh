@@ -104,6 +104,8 @@ struct SysDesc {
   unsigned long long seed;
   int langevin;
   int ntypes;          // species of this system (several-species engines; else 0)
+  int frozen_mask;     // bit t: beads of species t do not move
+  int pad6;
   long long tab_off;   // its ntypes x ntypes block of the pooled pair tables
   // real-space kernel constants: small-r Taylor series of
   //   g(r) = [erf(beta r) - erf(kappa r)] / r        = sum_k ser_g[k] r^{2k}

@@ -185,6 +185,8 @@ std::string validate_spec(const SysSpec &sp) {
       if (A != p.A_tab[u * GCME_MAX_TYPES + t]) return "species table A_ij must be symmetric";
     }
   }
+  if (p.frozen_mask != 0 && (nt < 2 || (p.frozen_mask & ~((1 << nt) - 1)) != 0))
+    return "frozen_mask needs ntypes >= 2 and bits below ntypes";
   if (!sp.types.empty()) {
     if ((int64_t)sp.types.size() != sp.n) return "species array size mismatch";
     for (int32_t t : sp.types)
@@ -557,6 +559,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
       const SysSpec &sp = specs[s];
       const int nt = std::max(p.ntypes, 1);
       S.ntypes = nt;
+      S.frozen_mask = p.frozen_mask;
       S.tab_off = fp64 ? (long long)htab64.size() : (long long)htab.size();
       for (int t = 0; t < nt; ++t)
         for (int u = 0; u < nt; ++u) {

@@ -228,6 +228,11 @@ __device__ __forceinline__ void langevin_noise(unsigned long long seed, unsigned
 //   velocity Verlet:  v += dt/2 F;  x += dt v.
 //   Langevin (BAOAB): v += dt/2 F;  x += dt/2 v;  v = c1 v + c2 z;  x += dt/2 v
 // with z the noise of this bead at the system's step counter.
+// beads of a frozen species (explicit electrodes) keep x and v
+__device__ __forceinline__ bool frozen_bead(const Pool &P, const SysDesc &S, int i) {
+  return S.frozen_mask && ((S.frozen_mask >> P.type_u[S.ext_off + i]) & 1);
+}
+
 template <typename V>
 __device__ __forceinline__ void dev_kick_drift(const Pool &P, long long g) {
   if (g >= P.n_real) return;
@@ -235,6 +240,7 @@ __device__ __forceinline__ void dev_kick_drift(const Pool &P, long long g) {
   const SysDesc &S = P.sys[s];
   V *vel = reinterpret_cast<V *>(P.vel) + 3 * g;
   const int i = (int)(g - S.bead_off);
+  if (frozen_bead(P, S, i)) return;
   const V h = V(0.5 * S.dt);
   if (S.langevin) {
     V z[3];
@@ -272,7 +278,8 @@ __device__ __forceinline__ void dev_kick(const Pool &P, long long g) {
     V *vel = reinterpret_cast<V *>(P.vel) + 3 * g;
     const int i = (int)(g - S.bead_off);
     const V h = V(0.5 * S.dt);
-    for (int a = 0; a < 3; ++a) {
+    const bool frozen = frozen_bead(P, S, i);
+    for (int a = 0; a < 3 && !frozen; ++a) {
       const long long fq = *reinterpret_cast<const long long *>(force_ptr(P, S, i, a));
       const V f = V((double)fq * (1.0 / kFScale));
       V v = vel[a] + h * f;
