@@ -515,3 +515,60 @@ def langevin_baoab(s: System, nsteps: int, gamma: float, kT: float, seed: int,
         vel += m * (0.5 * dt * F)
         hist.append(dict(potential=U, kinetic=0.5 * float(np.sum(m * vel * vel))))
     return pos, vel, hist
+
+
+# ---------------------------------------------------------------------------
+# Pressure and NpT (Parametrization section).  The pressure is Eq.
+# pres_virial for one configuration, p = N kT / V + tr(W) / (3 V), with W the
+# virial of all forces (pair, reciprocal, bonds; bulk systems).  The
+# paper's NpT runs name no barostat; reading: a Monte Carlo barostat with
+# isotropic moves of ln V (symmetric proposals), every bead's position
+# scaled with the box:
+#   V' = V exp((2 u0 - 1) dlnv),  x' = x (V'/V)^{1/3},
+#   dW = U(x', V') - U(x, V) + p (V' - V) - (N + 1) kT ln(V'/V),
+#   accept iff dW <= 0 or u1 < exp(-dW / kT)
+# (N + 1: the configurational Jacobian V^N and the d ln V measure),
+# u0, u1 = floor(w / 2^11) / 2^53 of Philox4x64-10 at counter (move, 0, 0, 0)
+# with key (seed, 1) (the Langevin noise uses key word 1 = 0).
+# Parity: pinned by the ideal gas, whose NpT volume has <V> = (N + 1) kT / p
+# exactly, and by p_conf = tr(W)/(3V) = -dU/dV under isotropic scaling.
+# ---------------------------------------------------------------------------
+def pressure(s: System, pos=None, kT: float = 1.0) -> float:
+    """Instantaneous virial pressure with the ideal term N kT / V."""
+    pos = s.pos if pos is None else pos
+    ef = energy_forces(s, pos)
+    V = float(np.prod(s.box))
+    return (s.n * kT + float(np.trace(ef["virial"])) / 3.0) / V
+
+
+def barostat_uniforms(seed: int, move: int):
+    ctr = np.array([[move, 0, 0, 0]], dtype=np.uint64)
+    key = np.array([[seed & _M64, 1]], dtype=np.uint64)
+    w = philox4x64(ctr, key)[0]
+    return [float(int(x) >> 11) * 2.0 ** -53 for x in w[:2]]
+
+
+def barostat_move(s: System, pos, box, pressure_: float, kT: float, dlnv: float, seed: int,
+                  move: int, energy_fn=None):
+    """One Monte Carlo volume move (see the block comment).  energy_fn(pos,
+    box) -> potential energy; default: the GCMe energy of s in that box.
+    Returns (pos, box, accepted)."""
+    def energy(p, b):
+        if energy_fn is not None:
+            return energy_fn(p, b)
+        t = s.copy()
+        t.box = np.asarray(b, float).copy()
+        return energy_forces(t, p)["potential"]
+
+    u0, u1 = barostat_uniforms(seed, move)
+    V = float(np.prod(box))
+    lr = (2.0 * u0 - 1.0) * dlnv  # ln(V'/V)
+    V1 = V * np.exp(lr)
+    sc = np.exp(lr / 3.0)
+    pos1 = pos * sc
+    box1 = np.asarray(box, float) * sc
+    dW = energy(pos1, box1) - energy(pos, box) + pressure_ * (V1 - V) - \
+        (pos.shape[0] + 1) * kT * lr
+    if dW <= 0.0 or u1 < np.exp(-dW / kT):
+        return pos1, box1, True
+    return pos, box, False
