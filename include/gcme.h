@@ -296,8 +296,31 @@ typedef struct gcme_sys_info {
   int32_t list_stride;  /* list entries per bead and lane (4 lanes), 0 without list */
   int64_t list_builds;  /* neighbour-list builds so far (synchronises the device) */
   int64_t steps;        /* the system's step counter (synchronises the device)   */
+  double box[3];        /* current box (changes with gcme_system_set_box)       */
 } gcme_sys_info;
 int gcme_system_info(const gcme_sys *sys, gcme_sys_info *out);
+
+/* ---- pressure and NpT (Parametrization section) ---------------------------
+ * Bulk systems only.  gcme_pressure: the configuration's Eq. pres_virial,
+ * p = (N kT + tr W / 3) / V, with W the virial of all forces (pair,
+ * reciprocal, bonds) at d_pos; synchronises the stream.
+ * gcme_system_set_box: change the periodic box (sides >= rc); the cell grid
+ * is kept when its cell counts do not change, else the system's device
+ * scratch is rebuilt (launch shapes kept).  Positions are not touched.
+ * gcme_barostat_move: one Monte Carlo volume move of the NpT ensemble (the
+ * paper's NpT runs name no barostat; reading: isotropic ln V moves),
+ *   V' = V exp((2 u0 - 1) dlnv),  x' = x (V'/V)^{1/3}  (d_pos scaled in place),
+ *   accepted iff dW <= 0 or u1 < exp(-dW / kT),
+ *   dW = U(x', V') - U(x, V) + pressure (V' - V) - (N + 1) kT ln(V'/V),
+ * u0, u1 = floor(w / 2^11) / 2^53 of the first two words of Philox4x64-10
+ * at counter (move, 0, 0, 0) with key (seed, 1).  A rejected move restores
+ * positions and box exactly.  *h_accepted = 1 or 0.  Velocities are not
+ * scaled.  Two force evaluations and two synchronisations per move. */
+int gcme_pressure(gcme_sys *sys, const double *d_pos, double kT, double *h_pressure,
+                  gcme_stream_t stream);
+int gcme_system_set_box(gcme_sys *sys, const double *box, gcme_stream_t stream);
+int gcme_barostat_move(gcme_sys *sys, double *d_pos, double pressure, double kT, double dlnv,
+                       uint64_t seed, uint64_t move, int32_t *h_accepted, gcme_stream_t stream);
 
 /* Set the system's step counter (the Langevin noise counter of the next
  * step), e.g. to continue a trajectory from a checkpoint taken after

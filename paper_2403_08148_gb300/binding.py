@@ -57,7 +57,8 @@ class SysInfo(ctypes.Structure):
                 ("nbonds", ctypes.c_int64), ("nc", ctypes.c_int32 * 3),
                 ("cell_factor", ctypes.c_int32), ("scratch_bytes", ctypes.c_int64),
                 ("pair_path", ctypes.c_int32), ("list_stride", ctypes.c_int32),
-                ("list_builds", ctypes.c_int64), ("steps", ctypes.c_int64)]
+                ("list_builds", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("box", ctypes.c_double * 3)]
 
 
 class Tuning(ctypes.Structure):
@@ -105,6 +106,12 @@ _SIGS = {
     "gcme_system_destroy": ([_vp], None),
     "gcme_system_info": ([_vp, ctypes.POINTER(SysInfo)], ctypes.c_int),
     "gcme_system_set_step_count": ([_vp, ctypes.c_int64, _vp], ctypes.c_int),
+    "gcme_pressure": ([_vp, _vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _vp],
+                      ctypes.c_int),
+    "gcme_system_set_box": ([_vp, ctypes.POINTER(ctypes.c_double), _vp], ctypes.c_int),
+    "gcme_barostat_move": ([_vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                            ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32),
+                            _vp], ctypes.c_int),
     "gcme_build_cells": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "gcme_forces": ([_vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "gcme_build_cells_noalloc": ([ctypes.POINTER(Params), _i64, _vp, _vp, _vp, _vp, _vp],
@@ -299,6 +306,24 @@ class System:
         out = SysInfo()
         _check(load().gcme_system_info(self.h, ctypes.byref(out)))
         return out
+
+    def pressure(self, d_pos, kT: float = 1.0, stream=None) -> float:
+        p = ctypes.c_double(0.0)
+        _check(load().gcme_pressure(self.h, _ptr(d_pos), float(kT), ctypes.byref(p),
+                                    _stream(stream)))
+        return p.value
+
+    def set_box(self, box, stream=None):
+        b = (ctypes.c_double * 3)(*[float(x) for x in box])
+        _check(load().gcme_system_set_box(self.h, b, _stream(stream)))
+
+    def barostat_move(self, d_pos, pressure: float, kT: float, dlnv: float, seed: int,
+                      move: int, stream=None) -> bool:
+        acc = ctypes.c_int32(0)
+        _check(load().gcme_barostat_move(self.h, _ptr(d_pos), float(pressure), float(kT),
+                                         float(dlnv), int(seed), int(move), ctypes.byref(acc),
+                                         _stream(stream)))
+        return bool(acc.value)
 
     def set_step_count(self, steps: int, stream=None):
         _check(load().gcme_system_set_step_count(self.h, int(steps), _stream(stream)))

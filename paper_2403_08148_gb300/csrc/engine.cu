@@ -261,15 +261,25 @@ std::string validate_spec(const SysSpec &sp) {
   return "";
 }
 
-Engine::~Engine() {
+Engine::~Engine() { release(); }
+
+void Engine::release() {
   clear_graphs();
-  for (auto e : phase_ev)
-    if (e) cudaEventDestroy(e);
+  for (auto &e : phase_ev)
+    if (e) {
+      cudaEventDestroy(e);
+      e = nullptr;
+    }
   if (capture_stream) cudaStreamDestroy(capture_stream);
   if (side_stream) cudaStreamDestroy(side_stream);
   if (fork_ev) cudaEventDestroy(fork_ev);
   if (join_ev) cudaEventDestroy(join_ev);
   if (arena_) cudaFree(arena_);
+  capture_stream = side_stream = nullptr;
+  fork_ev = join_ev = nullptr;
+  arena_ = nullptr;
+  P = Pool{};
+  hsys.clear();
 }
 
 std::vector<int2> Engine::make_pair_work(int split) const {
@@ -1003,6 +1013,11 @@ struct gcme_sys {
   gcme_ctx *ctx;
   Engine eng;
   gcme_params p;
+  SysSpec spec;               // as created (the box follows set_box)
+  double *saved_pos = nullptr;  // barostat: positions before a volume move
+  ~gcme_sys() {
+    if (saved_pos) cudaFree(saved_pos);
+  }
   // buffers of the last gcme_step call: the internal force array then holds
   // F at their current positions, so a continuation can skip that evaluation
   const void *last_pos = nullptr, *last_vel = nullptr;
@@ -1115,6 +1130,7 @@ int gcme_system_create(gcme_ctx *ctx, const gcme_params *p, int64_t n, const dou
   gcme_sys *s = new gcme_sys;
   s->ctx = ctx;
   s->p = *p;
+  s->spec = sp;
   int rc = s->eng.build(ctx->device, {sp}, false);
   if (rc != GCME_OK) {
     delete s;
@@ -1152,6 +1168,165 @@ int gcme_system_info(const gcme_sys *sys, gcme_sys_info *out) {
   unsigned long long steps = 0;
   GCME_TRY_CK(cudaMemcpy(&steps, ms->eng.P.step_ctr, sizeof(steps), cudaMemcpyDeviceToHost));
   out->steps = (int64_t)steps;
+  for (int a = 0; a < 3; ++a) out->box[a] = S.box[a];
+  return GCME_OK;
+}
+
+// ---- pressure and NpT -------------------------------------------------------
+// Potential energy (and optionally the virial) of the system at d_pos,
+// using the internal force buffer.  Synchronises the stream.
+static int eval_energy(gcme_sys *sys, const double *d_pos, cudaStream_t st, double *U,
+                       double *W) {
+  Pool Q = sys->eng.P;
+  Q.pos = const_cast<double *>(d_pos);
+  const bool vir = W != nullptr;
+  sys->eng.enqueue_forces(Q, st, vir, false);
+  launch_finalize(Q, vir, st);
+  double e[GCME_NTERMS];
+  GCME_TRY_CK(cudaMemcpyAsync(e, Q.energy, sizeof(e), cudaMemcpyDeviceToHost, st));
+  if (vir) GCME_TRY_CK(cudaMemcpyAsync(W, Q.virial, sizeof(double) * 9, cudaMemcpyDeviceToHost, st));
+  GCME_TRY_CK(cudaStreamSynchronize(st));
+  *U = e[GCME_E_POTENTIAL];
+  sys->last_pos = nullptr;  // the internal forces no longer belong to a step's state
+  return check_launch("energy evaluation");
+}
+
+// Philox4x64-10 on the host (the barostat's two uniforms per move)
+static void host_philox4x64(uint64_t c[4], uint64_t k0, uint64_t k1) {
+  const uint64_t m0 = 0xD2E7470EE14C6C93ull, m1 = 0xCA5A826395121157ull;
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B97F4A7C15ull;
+      k1 += 0xBB67AE8584CAA73Bull;
+    }
+    const unsigned __int128 p0 = (unsigned __int128)m0 * c[0];
+    const unsigned __int128 p1 = (unsigned __int128)m1 * c[2];
+    const uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+    const uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+    const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+int gcme_system_set_box(gcme_sys *sys, const double *box, gcme_stream_t stream) {
+  if (!sys || !box) {
+    set_error("NULL argument");
+    return GCME_ERR_INVALID;
+  }
+  if (sys->p.geometry != GCME_BULK) {
+    set_error("gcme_system_set_box: bulk systems only (a slab's box is tied to its height)");
+    return GCME_ERR_INVALID;
+  }
+  Engine &E = sys->eng;
+  const SysDesc &S0 = E.hsys[0];
+  const double rc = S0.rc;
+  int nc[3];
+  for (int a = 0; a < 3; ++a) {
+    if (!(box[a] >= rc * (1.0 + 1e-4)) || !std::isfinite(box[a])) {
+      set_error("gcme_system_set_box: box side shorter than the cutoff");
+      return GCME_ERR_INVALID;
+    }
+    nc[a] = std::max(1, (int)std::floor(box[a] / ((rc / E.cell_factor) * (1.0 + 1e-4))));
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  GCME_TRY_CK(cudaSetDevice(E.device));
+  for (int a = 0; a < 3; ++a) {
+    sys->p.box[a] = box[a];
+    sys->spec.p.box[a] = box[a];
+  }
+  sys->last_pos = nullptr;
+  if (nc[0] == S0.nc[0] && nc[1] == S0.nc[1] && nc[2] == S0.nc[2]) {
+    // same cell grid: only the box-derived constants change (the kernels
+    // and captured graphs read them from the device table)
+    GCME_TRY_CK(cudaStreamSynchronize(st));
+    SysDesc &S = E.hsys[0];
+    for (int a = 0; a < 3; ++a) {
+      S.box[a] = box[a];
+      S.inv_cell[a] = (double)S.nc[a] / box[a];
+      S.boxf[a] = (float)box[a];
+      S.kfac[a] = (float)((double)S.K[a] / box[a]);
+      S.cside[a] = (float)(box[a] / S.nc[a]);
+    }
+    S.V = box[0] * box[1] * box[2];
+    GCME_TRY_CK(cudaMemcpy(const_cast<SysDesc *>(E.P.sys), &S, sizeof(SysDesc),
+                           cudaMemcpyHostToDevice));
+    E.request_rebuild(st);
+    return check_launch("gcme_system_set_box");
+  }
+  // another cell grid: rebuild the engine for the new box (launch shapes
+  // carried over); the state lives in the caller's buffers
+  GCME_TRY_CK(cudaStreamSynchronize(st));
+  const int split = E.pair_split, threads = E.pair_threads, ctas = E.pair_ctas_per_sm;
+  E.release();
+  E.pair_split = split;
+  int rc2 = E.build(E.device, {sys->spec}, false);
+  if (rc2) return rc2;
+  return E.set_pair_config(split, threads, ctas);
+}
+
+int gcme_pressure(gcme_sys *sys, const double *d_pos, double kT, double *h_pressure,
+                  gcme_stream_t stream) {
+  if (!sys || !d_pos || !h_pressure || !(kT >= 0)) {
+    set_error("invalid argument to gcme_pressure");
+    return GCME_ERR_INVALID;
+  }
+  GCME_TRY_CK(cudaSetDevice(sys->eng.device));
+  double U, W[9];
+  int rc = eval_energy(sys, d_pos, (cudaStream_t)stream, &U, W);
+  if (rc) return rc;
+  const SysDesc &S = sys->eng.hsys[0];
+  *h_pressure = ((double)S.n * kT + (W[0] + W[4] + W[8]) / 3.0) / S.V;
+  return GCME_OK;
+}
+
+int gcme_barostat_move(gcme_sys *sys, double *d_pos, double pressure, double kT, double dlnv,
+                       uint64_t seed, uint64_t move, int32_t *h_accepted, gcme_stream_t stream) {
+  if (!sys || !d_pos || !h_accepted || !(kT > 0) || !(dlnv > 0) || !std::isfinite(pressure)) {
+    set_error("invalid argument to gcme_barostat_move");
+    return GCME_ERR_INVALID;
+  }
+  if (sys->p.geometry != GCME_BULK) {
+    set_error("gcme_barostat_move: bulk systems only");
+    return GCME_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  GCME_TRY_CK(cudaSetDevice(sys->eng.device));
+  const long long n = sys->eng.hsys[0].n;
+  if (!sys->saved_pos) GCME_TRY_CK(cudaMalloc(&sys->saved_pos, sizeof(double) * 3 * n));
+  double U0, U1;
+  int rc = eval_energy(sys, d_pos, st, &U0, nullptr);
+  if (rc) return rc;
+  uint64_t c[4] = {move, 0, 0, 0};
+  host_philox4x64(c, seed, 1);
+  const double u0 = (double)(c[0] >> 11) * 0x1.0p-53, u1 = (double)(c[1] >> 11) * 0x1.0p-53;
+  const double box0[3] = {sys->p.box[0], sys->p.box[1], sys->p.box[2]};
+  const double V = box0[0] * box0[1] * box0[2];
+  const double lr = (2.0 * u0 - 1.0) * dlnv;  // ln(V'/V)
+  const double V1 = V * std::exp(lr), sc = std::exp(lr / 3.0);
+  const double box1[3] = {box0[0] * sc, box0[1] * sc, box0[2] * sc};
+  GCME_TRY_CK(cudaMemcpyAsync(sys->saved_pos, d_pos, sizeof(double) * 3 * n,
+                              cudaMemcpyDeviceToDevice, st));
+  launch_scale(d_pos, 3 * n, sc, st);
+  rc = gcme_system_set_box(sys, box1, stream);
+  if (rc == GCME_OK) rc = eval_energy(sys, d_pos, st, &U1, nullptr);
+  bool accept = false;
+  if (rc == GCME_OK) {
+    const double dW = U1 - U0 + pressure * (V1 - V) - (double)(n + 1) * kT * lr;
+    accept = dW <= 0.0 || u1 < std::exp(-dW / kT);
+  } else if (rc != GCME_ERR_INVALID) {
+    return rc;  // a device error: leave the state to the caller
+  }
+  if (!accept) {  // restore positions and box (a box below the cutoff is a rejection)
+    GCME_TRY_CK(cudaMemcpyAsync(d_pos, sys->saved_pos, sizeof(double) * 3 * n,
+                                cudaMemcpyDeviceToDevice, st));
+    rc = gcme_system_set_box(sys, box0, stream);
+    if (rc) return rc;
+  }
+  *h_accepted = accept ? 1 : 0;
+  set_error("");
   return GCME_OK;
 }
 

@@ -38,6 +38,7 @@ std::string validate_spec(const SysSpec &sp);
 class Engine {
  public:
   ~Engine();
+  void release();  // free everything build() made (build() may then run again)
   // own_state: allocate pos/vel/force/q pools (batch and server); else the
   // caller passes pos/force per call and only q is stored.
   int build(int device, const std::vector<SysSpec> &specs, bool own_state);

@@ -49,5 +49,6 @@ int launch_persistent(const Pool &P, const int2 *pair_work, int n_pair_work, int
                       cudaStream_t st);
 int launch_barrier_probe(unsigned int *bar_words, double timeout_s, cudaStream_t st);
 void launch_force_to_f64(const long long *f, double *out, long long n3, cudaStream_t st);
+void launch_scale(double *x, long long n3, double s, cudaStream_t st);  // x *= s
 
 }  // namespace gcme

@@ -59,4 +59,14 @@ void launch_force_to_f64(const long long *f, double *out, long long n3, cudaStre
   if (n3 > 0) k_force_to_f64<<<(int)((n3 + 255) / 256), 256, 0, st>>>(f, out, n3);
 }
 
+// isotropic scaling of positions with the box (barostat volume moves)
+__global__ void k_scale(double *x, long long n3, double s) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g < n3) x[g] *= s;
+}
+
+void launch_scale(double *x, long long n3, double s, cudaStream_t st) {
+  if (n3 > 0) k_scale<<<(int)((n3 + 255) / 256), 256, 0, st>>>(x, n3, s);
+}
+
 }  // namespace gcme
