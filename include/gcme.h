@@ -343,15 +343,16 @@ int gcme_debug_barrier_timeout(gcme_ctx *ctx, double timeout_s, gcme_stream_t st
 /* ---- autotuner ------------------------------------------------------------ */
 
 /* Tuned launch shapes: work items per home cell of the pair kernel (3: 9
- * neighbour cells each; 9: 3 each), pair block size (128 or 160 threads:
- * 3 or 4 Gaussian-core warps + one electrostatics warp), resident pair
+ * neighbour cells each; 9: 3 each), pair block size (128, 160 or 192
+ * threads) of which pair_nelec (1 or 2) electrostatics warps and the rest
+ * Gaussian-core warps, resident pair
  * CTAs per SM fetching work items dynamically (0: one CTA per item), FFT
  * lines per tile per axis, x-y plane passes (1) or per-axis passes (0);
  * device times of a whole force evaluation and of
  * the PME branch alone with the chosen shapes. */
 typedef struct gcme_tuning {
   int32_t pair_split, pair_threads, pair_ctas_per_sm, fft_lpb[3], fft_plane, from_cache,
-      cell_factor, pad;
+      cell_factor, pair_nelec;
   double forces_ms, pme_ms;
 } gcme_tuning;
 

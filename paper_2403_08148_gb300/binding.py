@@ -65,7 +65,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("pair_split", ctypes.c_int32), ("pair_threads", ctypes.c_int32),
                 ("pair_ctas_per_sm", ctypes.c_int32), ("fft_lpb", ctypes.c_int32 * 3),
                 ("fft_plane", ctypes.c_int32), ("from_cache", ctypes.c_int32),
-                ("cell_factor", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("cell_factor", ctypes.c_int32), ("pair_nelec", ctypes.c_int32),
                 ("forces_ms", ctypes.c_double), ("pme_ms", ctypes.c_double)]
 
     def as_dict(self):
@@ -73,7 +73,8 @@ class Tuning(ctypes.Structure):
                 "pair_ctas_per_sm": self.pair_ctas_per_sm, "fft_lpb": list(self.fft_lpb),
                 "fft_plane": bool(self.fft_plane),
                 "from_cache": bool(self.from_cache), "cell_factor": self.cell_factor,
-                "forces_ms": self.forces_ms, "pme_ms": self.pme_ms}
+                "pair_nelec": self.pair_nelec, "forces_ms": self.forces_ms,
+                "pme_ms": self.pme_ms}
 
 
 class Request(ctypes.Structure):

@@ -105,7 +105,7 @@ struct SysDesc {
   int langevin;
   int ntypes;          // species of this system (several-species engines; else 0)
   int frozen_mask;     // bit t: beads of species t do not move
-  int pad6;
+  int pair_nelec;      // electrostatics warps of a packed pair CTA (1 or 2)
   long long tab_off;   // its ntypes x ntypes block of the pooled pair tables
   // real-space kernel constants: small-r Taylor series of
   //   g(r) = [erf(beta r) - erf(kappa r)] / r        = sum_k ser_g[k] r^{2k}

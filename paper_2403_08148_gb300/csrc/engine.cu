@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <algorithm>
+
 #include "engine.h"
 
 namespace gcme {
@@ -280,6 +282,9 @@ void Engine::release() {
   arena_ = nullptr;
   P = Pool{};
   hsys.clear();
+  snap_cnt.clear();  // the occupancy snapshot belongs to the old cell grid
+  snap_nimg.clear();
+  snap_nq.clear();
 }
 
 std::vector<int2> Engine::make_pair_work(int split) const {
@@ -314,17 +319,72 @@ void Engine::clear_graphs() {
   graph_objs_.clear();
 }
 
-int Engine::set_pair_config(int split, int threads, int ctas_per_sm) {
-  if ((split != 3 && split != 9) || (threads != 128 && threads != 160) || ctas_per_sm < 0 ||
-      ctas_per_sm > 8) {
-    set_error("pair configuration must be split 3|9, 128|160 threads, 0..8 CTAs per SM");
+// Occupancy of every cell (beads, images, images + charged) from the last
+// cell sort, for ordering the pair work items.
+int Engine::snapshot_cells(cudaStream_t st) {
+  const long long nc = P.n_cells;
+  std::vector<int> start(nc + 1);
+  snap_nimg.assign(nc, 0);
+  snap_nq.assign(nc, 0);
+  GCME_CK(cudaStreamSynchronize(st));
+  GCME_CK(cudaMemcpy(start.data(), P.cell_start, sizeof(int) * (nc + 1), cudaMemcpyDeviceToHost));
+  GCME_CK(cudaMemcpy(snap_nimg.data(), P.cell_nimg, sizeof(int) * nc, cudaMemcpyDeviceToHost));
+  GCME_CK(cudaMemcpy(snap_nq.data(), P.cell_nq, sizeof(int) * nc, cudaMemcpyDeviceToHost));
+  snap_cnt.assign(nc, 0);
+  for (long long c = 0; c < nc; ++c) snap_cnt[c] = start[c + 1] - start[c];
+  return GCME_OK;
+}
+
+// Heaviest work items first (longest-processing-time order), so that the
+// last CTAs of the 27-cell kernel are short ones.  Cost of an item: its real
+// home beads x the real beads it stages (Gaussian core) + 4 x its charged
+// home beads x the charged and image beads it stages (electrostatics).
+void Engine::order_by_cost(std::vector<int2> &pw, int split) const {
+  if (snap_cnt.empty() || cell_factor != 1) return;
+  std::vector<std::pair<long long, int>> key(pw.size());
+  for (size_t w = 0; w < pw.size(); ++w) {
+    const SysDesc &S = hsys[pw[w].x];
+    const int cloc = pw[w].y / split, part = pw[w].y % split;
+    const int cx = cloc % S.nc[0], cy = (cloc / S.nc[0]) % S.nc[1], cz = cloc / (S.nc[0] * S.nc[1]);
+    const long long hg = S.cell_off + cloc;
+    const long long hreal = snap_cnt[hg] - snap_nimg[hg], hq = snap_nq[hg] - snap_nimg[hg];
+    const int dz = (split == 3 ? part : part / 3) - 1;
+    long long sreal = 0, sq = 0;
+    for (int k = 0; k < 27 / split; ++k) {
+      const int dx = k % 3 - 1, dy = split == 3 ? k / 3 - 1 : part % 3 - 1;
+      const int u[3] = {cx + dx, cy + dy, cz + dz};
+      long long v[3];
+      for (int a = 0; a < 3; ++a) v[a] = ((u[a] % S.nc[a]) + S.nc[a]) % S.nc[a];
+      const long long cg = S.cell_off + v[0] + S.nc[0] * (v[1] + S.nc[1] * v[2]);
+      sreal += snap_cnt[cg] - snap_nimg[cg];
+      sq += snap_nq[cg];
+    }
+    key[w] = {-(hreal * sreal + 4 * hq * sq), (int)w};
+  }
+  std::stable_sort(key.begin(), key.end());
+  std::vector<int2> out(pw.size());
+  for (size_t w = 0; w < pw.size(); ++w) out[w] = pw[key[w].second];
+  pw.swap(out);
+}
+
+int Engine::set_pair_config(int split, int threads, int ctas_per_sm, int nelec) {
+  if ((split != 3 && split != 9) || (threads != 128 && threads != 160 && threads != 192) ||
+      ctas_per_sm < 0 || ctas_per_sm > 8 || (nelec != 1 && nelec != 2) ||
+      threads / 32 - nelec < 2) {
+    set_error("pair configuration must be split 3|9, 128|160|192 threads, 1|2 electrostatics "
+              "warps (at least 2 core warps), 0..8 CTAs per SM");
     return GCME_ERR_INVALID;
   }
   pair_ctas_per_sm = ctas_per_sm;
   std::vector<int2> pw = make_pair_work(split);
+  order_by_cost(pw, split);
   pair_split = split;
   pair_threads = threads;
-  for (auto &S : hsys) S.pair_split = split;
+  pair_nelec = nelec;
+  for (auto &S : hsys) {
+    S.pair_split = split;
+    S.pair_nelec = nelec;
+  }
   GCME_CK(cudaMemcpy(const_cast<SysDesc *>(P.sys), hsys.data(), sizeof(SysDesc) * hsys.size(),
                      cudaMemcpyHostToDevice));
   GCME_CK(cudaMemcpy(pair_work, pw.data(), sizeof(int2) * pw.size(), cudaMemcpyHostToDevice));
@@ -479,6 +539,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     S.ncell = 1;
     S.cell_factor = cell_factor;
     S.pair_split = pair_split;
+    S.pair_nelec = pair_nelec;
     for (int a = 0; a < 3; ++a) {
       S.nc[a] = std::max(1, (int)std::floor(p.box[a] / ((p.rc / cell_factor) * (1.0 + 1e-4))));
       S.nb[a] = (S.nc[a] + 1) / 2;
@@ -1259,12 +1320,13 @@ int gcme_system_set_box(gcme_sys *sys, const double *box, gcme_stream_t stream) 
   // another cell grid: rebuild the engine for the new box (launch shapes
   // carried over); the state lives in the caller's buffers
   GCME_TRY_CK(cudaStreamSynchronize(st));
-  const int split = E.pair_split, threads = E.pair_threads, ctas = E.pair_ctas_per_sm;
+  const int split = E.pair_split, threads = E.pair_threads, ctas = E.pair_ctas_per_sm,
+            nelec = E.pair_nelec;
   E.release();
   E.pair_split = split;
   int rc2 = E.build(E.device, {sys->spec}, false);
   if (rc2) return rc2;
-  return E.set_pair_config(split, threads, ctas);
+  return E.set_pair_config(split, threads, ctas, nelec);
 }
 
 int gcme_pressure(gcme_sys *sys, const double *d_pos, double kT, double *h_pressure,
@@ -1576,6 +1638,7 @@ static void fill_tuning(const Engine &eng, double pair_ms, double pme_ms, bool h
   out->pair_split = eng.pair_split;
   out->pair_threads = eng.pair_threads;
   out->pair_ctas_per_sm = eng.pair_ctas_per_sm;
+  out->pair_nelec = eng.pair_nelec;
   for (int a = 0; a < 3; ++a) out->fft_lpb[a] = eng.plan.lpb[a];
   out->fft_plane = eng.plan.use_plane;
   out->from_cache = hit ? 1 : 0;

@@ -66,7 +66,12 @@ class Engine {
   int nsys() const { return (int)hsys.size(); }
   std::vector<int2> make_pair_work(int split) const;
   std::vector<int2> make_fft_work(int axis, int lpb) const;
-  int set_pair_config(int split, int threads, int ctas_per_sm);
+  int set_pair_config(int split, int threads, int ctas_per_sm, int nelec = 1);
+  // cell occupancy of the last cell sort (host copy) and the work-item
+  // order it implies (heaviest first)
+  int snapshot_cells(cudaStream_t st);
+  void order_by_cost(std::vector<int2> &pw, int split) const;
+  std::vector<int> snap_cnt, snap_nimg, snap_nq;
   int set_fft_lpb(int axis, int lpb);
   bool plane_fits() const;
   int set_fft_plane(bool on);
@@ -89,7 +94,8 @@ class Engine {
   bool use_list = false;  // FP32 pair terms over Verlet neighbour lists
   bool species = false;   // several species: per-pair constants from tables
   int pair_split = 0;   // 3 or 9 work items per home cell (0: default)
-  int pair_threads = kDefaultPairThreads;  // 128 (3 core warps) or 160 (4)
+  int pair_threads = kDefaultPairThreads;  // 128, 160 or 192 threads per pair CTA
+  int pair_nelec = 1;  // of which electrostatics warps (1 or 2)
   int pair_ctas_per_sm = 0;  // 0: one CTA per work item; else resident CTAs per SM fetching items
   int n_sm = 152;
   int *pair_counter = nullptr;  // dynamic work-item counter of the pair kernel

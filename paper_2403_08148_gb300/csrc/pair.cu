@@ -16,18 +16,23 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_fine(Pool P, const int2 *
 // launch): a CTA takes the next item when it finishes one, so heavy cells do
 // not leave SMs idle at the end, and a grid smaller than the SMs' capacity
 // leaves slots free for the concurrent PME branch.
+// One species without the debug dump runs the packed item (pair_core2).
 template <bool VIR, bool DBG, bool MT>
-__global__ void __launch_bounds__(160, 6) k_pair_f32(Pool P, const int2 *work, int nwork,
+__global__ void __launch_bounds__(192, 5) k_pair_f32(Pool P, const int2 *work, int nwork,
                                                      int *counter) {
-  __shared__ float4 sj[kPairCap];
+  __shared__ __align__(16) unsigned char raw[kPairSmemBytes];
   __shared__ PairSeg seg[9];
-  __shared__ int s_total;
+  __shared__ int s_total[2];
   __shared__ int s_item;
   __shared__ unsigned char stj[MT ? kPairCap : 1];
   __shared__ __align__(16) PairTab stab[MT ? kMaxTypes * kMaxTypes : 1];
+  float4 *sj = reinterpret_cast<float4 *>(raw);
+  constexpr bool PK = !DBG && !MT;
   if (!counter) {  // static: one item per CTA (grid = items)
-    for (int w = blockIdx.x; w < nwork; w += gridDim.x)
-      dev_pair_f32_item<VIR, DBG, MT>(P, work, w, sj, seg, &s_total, stj, stab);
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+      if (PK) dev_pair_f32_item_pk<VIR>(P, work, w, raw, seg, s_total);
+      else dev_pair_f32_item<VIR, DBG, MT>(P, work, w, sj, seg, s_total, stj, stab);
+    }
     return;
   }
   while (true) {
@@ -35,7 +40,8 @@ __global__ void __launch_bounds__(160, 6) k_pair_f32(Pool P, const int2 *work, i
     __syncthreads();
     const int w = s_item;
     if (w >= nwork) break;
-    dev_pair_f32_item<VIR, DBG, MT>(P, work, w, sj, seg, &s_total, stj, stab);
+    if (PK) dev_pair_f32_item_pk<VIR>(P, work, w, raw, seg, s_total);
+    else dev_pair_f32_item<VIR, DBG, MT>(P, work, w, sj, seg, s_total, stj, stab);
   }
 }
 
@@ -185,7 +191,7 @@ void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell
     else k_pair_fine<false, false><<<nwork, kPairThreads, 0, st>>>(P, work, nwork);
     return;
   }
-  const int tb = threads == 160 ? 160 : 128;
+  const int tb = (threads == 160 || threads == 192) ? threads : 128;
   // ctas <= 0: one CTA per item; else a grid of ctas fetching items
   const bool dyn = ctas > 0;
   const int grid = dyn ? std::max(1, std::min(nwork, ctas)) : nwork;

@@ -50,7 +50,17 @@ struct PairSeg {
   float sh[3];
   int self;
   int shifted;
+  int qoff;          // packed items: offset of the charged/image beads' float4
 };
+
+// Packed items: the real beads of the staged cells as three coordinate
+// arrays of kPkCap floats (each cell padded to an even count), the charged
+// and image beads as kPkCapQ float4; this and the scalar items' float4
+// array share one shared-memory block of kPairSmemBytes.
+constexpr int kPkCap = 1280;
+constexpr int kPkCapQ = 640;
+constexpr int kPairSmemBytes =
+    (16 * kPairCap > 12 * kPkCap + 16 * kPkCapQ) ? 16 * kPairCap : 12 * kPkCap + 16 * kPkCapQ;
 
 // In-cutoff test of one candidate (the FP32 rule above).
 template <bool SHIFT>
@@ -199,6 +209,64 @@ __device__ __forceinline__ void pair_elec(const float4 *__restrict__ J, int t0, 
           P.dbg_triples[3 * k + 2] = sg.code;
         }
       }
+    }
+  }
+}
+
+// Gaussian core over the staged real beads of one cell, two candidates per
+// instruction with the sm_100 packed FP32 operations (per component the
+// same IEEE round-to-nearest operations as the scalar rule above, so the
+// in-cutoff decisions are unchanged).  X, Y, Z: n2 (even) coordinates; a
+// pad entry sits far away.  The two halves of each sum are kept apart.
+struct PairAcc2 {
+  float2 eg, gx, gy, gz;
+  float2 wg[6];
+};
+
+template <bool SHIFT, bool SELF, bool VIR>
+__device__ __forceinline__ void pair_core2(const float *__restrict__ X,
+                                           const float *__restrict__ Y,
+                                           const float *__restrict__ Z, int n2, int jsorted0,
+                                           const float4 &xi, int isorted, const PairSeg &sg,
+                                           float rc2, float gcc, PairAcc2 &A) {
+  const float2 mx = make_float2(-xi.x, -xi.x), my = make_float2(-xi.y, -xi.y),
+               mz = make_float2(-xi.z, -xi.z);
+  const float2 hx = make_float2(sg.sh[0], sg.sh[0]), hy = make_float2(sg.sh[1], sg.sh[1]),
+               hz = make_float2(sg.sh[2], sg.sh[2]);
+  const float2 g2 = make_float2(gcc, gcc);
+#pragma unroll 2
+  for (int t = 0; t < n2; t += 2) {
+    float2 dx = __fadd2_rn(*reinterpret_cast<const float2 *>(X + t), mx);
+    float2 dy = __fadd2_rn(*reinterpret_cast<const float2 *>(Y + t), my);
+    float2 dz = __fadd2_rn(*reinterpret_cast<const float2 *>(Z + t), mz);
+    if (SHIFT) {
+      dx = __fadd2_rn(dx, hx);
+      dy = __fadd2_rn(dy, hy);
+      dz = __fadd2_rn(dz, hz);
+    }
+    const float2 r2 =
+        __fadd2_rn(__fadd2_rn(__fmul2_rn(dx, dx), __fmul2_rn(dy, dy)), __fmul2_rn(dz, dz));
+    bool in0 = r2.x < rc2, in1 = r2.y < rc2;
+    if (SELF) {
+      in0 = in0 && (jsorted0 + t != isorted);
+      in1 = in1 && (jsorted0 + t + 1 != isorted);
+    }
+    const float2 arg = __fmul2_rn(r2, g2);
+    float2 e;
+    e.x = in0 ? ex2_approx(arg.x) : 0.0f;
+    e.y = in1 ? ex2_approx(arg.y) : 0.0f;
+    A.eg = __fadd2_rn(A.eg, e);
+    A.gx = __ffma2_rn(e, dx, A.gx);
+    A.gy = __ffma2_rn(e, dy, A.gy);
+    A.gz = __ffma2_rn(e, dz, A.gz);
+    if (VIR) {
+      const float2 ex = __fmul2_rn(e, dx), ey = __fmul2_rn(e, dy);
+      A.wg[0] = __ffma2_rn(ex, dx, A.wg[0]);
+      A.wg[1] = __ffma2_rn(ey, dy, A.wg[1]);
+      A.wg[2] = __ffma2_rn(__fmul2_rn(e, dz), dz, A.wg[2]);
+      A.wg[3] = __ffma2_rn(ex, dy, A.wg[3]);
+      A.wg[4] = __ffma2_rn(ex, dz, A.wg[4]);
+      A.wg[5] = __ffma2_rn(ey, dz, A.wg[5]);
     }
   }
 }
@@ -453,6 +521,174 @@ __device__ __forceinline__ void dev_pair_f32_item(const Pool &P, const int2 *wor
       }
     }
     if (busy) pair_write<VIR, MT>(P, S, s, valid, i, A);
+  }
+  __syncthreads();
+}
+
+// Segment k of a work item of the 27-cell kernel (split 3: the 9 cells at
+// dz = part - 1; split 9: the 3 cells along x at dy, dz = part % 3 - 1,
+// part / 3 - 1), with its periodic shift.
+__device__ __forceinline__ PairSeg item_segment(const Pool &P, const SysDesc &S, int cloc,
+                                                int part, int k) {
+  const int split = S.pair_split;
+  const int nc0 = S.nc[0], nc1 = S.nc[1], nc2 = S.nc[2];
+  const int cx = cloc % nc0, cy = (cloc / nc0) % nc1, cz = cloc / (nc0 * nc1);
+  const int dzo = (split == 3 ? part : part / 3) - 1;
+  const int dxo = k % 3 - 1, dyo = split == 3 ? k / 3 - 1 : part % 3 - 1;
+  const int u[3] = {cx + dxo, cy + dyo, cz + dzo};
+  const int ncv[3] = {nc0, nc1, nc2};
+  int v[3], nn[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    nn[a] = floor_div(u[a], ncv[a]);
+    v[a] = u[a] - nn[a] * ncv[a];
+  }
+  const long long cg = S.cell_off + v[0] + nc0 * (v[1] + nc1 * v[2]);
+  PairSeg g;
+  g.beg = P.cell_start[cg];
+  g.n = P.cell_start[cg + 1] - g.beg;
+  g.a = P.cell_nimg[cg];
+  g.b = P.cell_nq[cg];
+  g.code = (nn[0] + 1) + 3 * (nn[1] + 1) + 9 * (nn[2] + 1);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) g.sh[a] = (float)nn[a] * S.boxf[a];
+  g.self = (dxo == 0 && dyo == 0 && dzo == 0);
+  g.shifted = (nn[0] != 0 || nn[1] != 0 || nn[2] != 0);
+  g.soff = 0;
+  g.qoff = 0;
+  return g;
+}
+
+// Packed variant of dev_pair_f32_item (one species, no debug dump): the
+// core warps run pair_core2 over coordinate arrays, the electrostatics
+// warps (1 or 2, SysDesc::pair_nelec) pair_elec over the staged charged and
+// image beads, each warp a contiguous part of every cell's candidates and
+// each writing its partial sums (fixed-point atomics add them).  Items whose
+// beads exceed the packed capacities take the scalar path.  smem:
+// kPairSmemBytes; seg[9]; s_tot[2].  Ends with a barrier.
+template <bool VIR>
+__device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *work, int w,
+                                                     unsigned char *smem, PairSeg *seg,
+                                                     int *s_tot) {
+  float *sx = reinterpret_cast<float *>(smem);
+  float *sy = sx + kPkCap;
+  float *sz = sy + kPkCap;
+  float4 *sq = reinterpret_cast<float4 *>(sz + kPkCap);
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int s = work[w].x;
+  const int code = work[w].y;
+  if (P.list_ovf && !P.list_ovf[s]) {
+    __syncthreads();
+    return;
+  }
+  const SysDesc &S = P.sys[s];
+  // warps 0 .. ncore-1: Gaussian core; the last nelec warps split every
+  // cell's charged and image candidates into contiguous parts
+  const int nelec = S.pair_nelec > 1 ? 2 : 1;
+  const int ncore = (blockDim.x >> 5) - nelec;
+  const bool core_role = warp < ncore;
+  const int ew = warp - ncore;
+  const int split = S.pair_split;
+  const int cloc = code / split, part = code % split;
+  const int nseg = 27 / split;
+  const long long hg = S.cell_off + cloc;
+  const int hbeg = P.cell_start[hg], hend = P.cell_start[hg + 1];
+  const int himg = P.cell_nimg[hg], hq = P.cell_nq[hg];
+  const int rbeg = hbeg + himg;
+  if (tid < nseg) seg[tid] = item_segment(P, S, cloc, part, tid);
+  __syncthreads();
+  if (tid == 0) {
+    int off = 0, qoff = 0;
+    for (int k = 0; k < nseg; ++k) {
+      seg[k].soff = off;
+      seg[k].qoff = qoff;
+      off += (seg[k].n - seg[k].a + 1) & ~1;
+      qoff += seg[k].b;
+    }
+    s_tot[0] = off;
+    s_tot[1] = qoff;
+  }
+  __syncthreads();
+  if (s_tot[0] > kPkCap || s_tot[1] > kPkCapQ) {
+    dev_pair_f32_item<VIR, false, false>(P, work, w, reinterpret_cast<float4 *>(smem), seg,
+                                         s_tot);
+    return;
+  }
+  for (int k = 0; k < nseg; ++k) {
+    const PairSeg &g = seg[k];
+    const int nr = g.n - g.a, n2 = (nr + 1) & ~1;
+    for (int t = tid; t < n2; t += blockDim.x) {
+      const float4 v = t < nr ? P.xyzq_s[g.beg + g.a + t]
+                              : make_float4(1e30f, 1e30f, 1e30f, 0.0f);  // pad: far away
+      sx[g.soff + t] = v.x;
+      sy[g.soff + t] = v.y;
+      sz[g.soff + t] = v.z;
+    }
+    for (int t = tid; t < g.b; t += blockDim.x) sq[g.qoff + t] = P.xyzq_s[g.beg + t];
+  }
+  __syncthreads();
+  const float rc2 = S.rc2f, gcc = S.gc_c2f;
+  const int nreal = hend - rbeg, nqr = hbeg + hq - rbeg;
+  const int ncore_chunks = (nreal + 32 * ncore - 1) / (32 * ncore);
+  const int nel_chunks = (nqr + 31) / 32;
+  const int nchunk = max(ncore_chunks, nel_chunks);
+  for (int c = 0; c < nchunk; ++c) {
+    int i;
+    bool valid;
+    if (core_role) {
+      i = rbeg + c * 32 * ncore + tid;
+      valid = i < hend;
+    } else {
+      i = rbeg + c * 32 + lane;
+      valid = i < hbeg + hq;
+    }
+    const float4 xi = valid ? P.xyzq_s[i] : make_float4(1e30f, 1e30f, 1e30f, 0.0f);
+    const bool busy = __any_sync(0xffffffffu, valid);
+    PairAcc A;
+    A.eg = A.ere = A.gx = A.gy = A.gz = A.fx = A.fy = A.fz = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) A.wg[k] = A.we[k] = 0.0f;
+    if (busy) {
+      if (core_role) {
+        PairAcc2 B;
+        B.eg = B.gx = B.gy = B.gz = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) B.wg[k] = make_float2(0.0f, 0.0f);
+        for (int k = 0; k < nseg; ++k) {
+          const PairSeg g = seg[k];
+          const int n2 = (g.n - g.a + 1) & ~1;
+          const float *X = sx + g.soff, *Y = sy + g.soff, *Z = sz + g.soff;
+          const int j0 = g.beg + g.a;
+          if (g.self)
+            pair_core2<false, true, VIR>(X, Y, Z, n2, j0, xi, i, g, rc2, gcc, B);
+          else if (g.shifted)
+            pair_core2<true, false, VIR>(X, Y, Z, n2, j0, xi, i, g, rc2, gcc, B);
+          else
+            pair_core2<false, false, VIR>(X, Y, Z, n2, j0, xi, i, g, rc2, gcc, B);
+        }
+        A.eg = B.eg.x + B.eg.y;
+        A.gx = B.gx.x + B.gx.y;
+        A.gy = B.gy.x + B.gy.y;
+        A.gz = B.gz.x + B.gz.y;
+        if (VIR)
+#pragma unroll
+          for (int k = 0; k < 6; ++k) A.wg[k] = B.wg[k].x + B.wg[k].y;
+      } else {
+        for (int k = 0; k < nseg; ++k) {
+          const PairSeg g = seg[k];
+          const float4 *J = sq + g.qoff;
+          const int lo = g.b * ew / nelec, hi = g.b * (ew + 1) / nelec;
+          if (g.self)
+            pair_elec<false, true, VIR, false>(J, lo, hi, 0, g.beg, xi, i, g, S, rc2, A, P, s);
+          else if (g.shifted)
+            pair_elec<true, false, VIR, false>(J, lo, hi, 0, g.beg, xi, i, g, S, rc2, A, P, s);
+          else
+            pair_elec<false, false, VIR, false>(J, lo, hi, 0, g.beg, xi, i, g, S, rc2, A, P, s);
+        }
+      }
+      pair_write<VIR>(P, S, s, valid, i, A);
+    }
   }
   __syncthreads();
 }

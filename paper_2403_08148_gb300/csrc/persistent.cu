@@ -106,17 +106,17 @@ __global__ void __launch_bounds__(128) k_persistent(Pool P, PersistArgs A) {
         dev_pair_fine_item<false, false>(P, A.pair_work, w);
     } else {
       float4 *sj = reinterpret_cast<float4 *>(smem);
-      PairSeg *seg = reinterpret_cast<PairSeg *>(smem + sizeof(float4) * kPairCap);
-      int *st = reinterpret_cast<int *>(smem + sizeof(float4) * kPairCap + sizeof(PairSeg) * 9);
+      PairSeg *seg = reinterpret_cast<PairSeg *>(smem + kPairSmemBytes);
+      int *st = reinterpret_cast<int *>(smem + kPairSmemBytes + sizeof(PairSeg) * 9);
       // several species: the table (16-byte aligned) and the staged species
-      const size_t toff = (sizeof(float4) * kPairCap + sizeof(PairSeg) * 9 + 16 + 15) / 16 * 16;
+      const size_t toff = (kPairSmemBytes + sizeof(PairSeg) * 9 + 16 + 15) / 16 * 16;
       PairTab *stab = reinterpret_cast<PairTab *>(smem + toff);
       unsigned char *stj = smem + toff + sizeof(PairTab) * kMaxTypes * kMaxTypes;
       for (int w = blockIdx.x; w < A.n_pair_work; w += gridDim.x) {
         if (P.ptab)
           dev_pair_f32_item<false, false, true>(P, A.pair_work, w, sj, seg, st, stj, stab);
         else
-          dev_pair_f32_item<false, false, false>(P, A.pair_work, w, sj, seg, st);
+          dev_pair_f32_item_pk<false>(P, A.pair_work, w, smem, seg, st);
       }
     }
     for (long long g = gtid; g < P.n_q * 8; g += gthreads) dev_spread<float>(P, g);
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(128) k_persistent(Pool P, PersistArgs A) {
 #undef GRID_LOOP
 
 size_t persistent_smem(const PmePlan &pl, bool species) {
-  size_t pair = sizeof(float4) * kPairCap + sizeof(PairSeg) * 9 + 16;
+  size_t pair = kPairSmemBytes + sizeof(PairSeg) * 9 + 16;
   if (species)
     pair = (pair + 15) / 16 * 16 + sizeof(PairTab) * kMaxTypes * kMaxTypes + kPairCap;
   size_t sort = sizeof(long long) * kSortCap + 16;

@@ -3,10 +3,11 @@
 // Candidates are timed with CUDA events on the caller's stream on the
 // actual system (or batch) at its current positions:
 //   pair kernel (27-cell path): 3 or 9 work items per home cell (9 or 3 neighbour cells
-//                each) x 128 or 160 threads (3 or 4 Gaussian-core warps +
-//                one electrostatics warp) x {one CTA per work item, or 5,
-//                6 or 8 resident CTAs per SM fetching items dynamically so
-//                that the remaining slots host the concurrent PME branch};
+//                each) x {128 threads with 1 electrostatics warp, 160 with 1
+//                or 2, 192 with 2; the other warps Gaussian core} x {one CTA
+//                per work item, or 5, 6 or 8 resident CTAs per SM fetching
+//                items dynamically so that the remaining slots host the
+//                concurrent PME branch};
 //   PME:         lines per FFT tile along each axis in {4, 8, 16, 32, 64}
 //                (shared memory permitting), one axis at a time, and x-y
 //                plane passes (one CTA per z-plane) vs per-axis passes;
@@ -43,7 +44,7 @@ std::string cache_path() {
 }
 
 struct Tuned {
-  int split = 0, threads = 0, ctas = 0, lpb[3] = {0, 0, 0}, plane = 0;
+  int split = 0, threads = 0, ctas = 0, lpb[3] = {0, 0, 0}, plane = 0, nelec = 1;
   double pair_ms = 0, pme_ms = 0;
 };
 
@@ -64,6 +65,8 @@ bool cache_lookup(const std::string &key, Tuned *t) {
                     "\"pme_ms\": %lf",
                     &x.split, &x.threads, &x.ctas, &x.lpb[0], &x.lpb[1], &x.lpb[2], &x.plane,
                     &x.pair_ms, &x.pme_ms) == 9) {
+      const char *e = std::strstr(line.c_str(), "\"pair_nelec\":");
+      if (e && std::sscanf(e, "\"pair_nelec\": %d", &x.nelec) != 1) x.nelec = 1;
       *t = x;  // the last entry for a key wins
       found = true;
     }
@@ -79,9 +82,9 @@ void cache_store(const std::string &key, const Tuned &t) {
   std::snprintf(buf, sizeof buf,
                 "{\"key\": \"%s\", \"pair_split\": %d, \"pair_threads\": %d, "
                 "\"pair_ctas_per_sm\": %d, \"fft_lpb\": [%d, %d, %d], \"fft_plane\": %d, "
-                "\"forces_ms\": %.6f, \"pme_ms\": %.6f}\n",
+                "\"forces_ms\": %.6f, \"pme_ms\": %.6f, \"pair_nelec\": %d}\n",
                 key.c_str(), t.split, t.threads, t.ctas, t.lpb[0], t.lpb[1], t.lpb[2], t.plane,
-                t.pair_ms, t.pme_ms);
+                t.pair_ms, t.pme_ms, t.nelec);
   f << buf;
 }
 
@@ -133,8 +136,21 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
   const bool remeasure = flags & 1, no_cache = flags & 2;
   Tuned t;
   *from_cache = false;
+  // one force evaluation for the cell occupancy that orders the pair work
+  // items (heaviest first) under every configuration below
+  {
+    cudaGraphExec_t g0 = nullptr;
+    int rc0 = forces_graph(Q, &g0);
+    if (rc0) return rc0;
+    if (cudaGraphLaunch(g0, st) != cudaSuccess) {
+      set_error("autotune: force evaluation failed");
+      return GCME_ERR_CUDA;
+    }
+    rc0 = snapshot_cells(st);
+    if (rc0) return rc0;
+  }
   if (!remeasure && !no_cache && cache_lookup(key.str(), &t)) {
-    int rc = set_pair_config(t.split, t.threads, t.ctas);
+    int rc = set_pair_config(t.split, t.threads, t.ctas, t.nelec);
     for (int a = 0; !rc && a < 3; ++a) rc = set_fft_lpb(a, t.lpb[a]);
     if (!rc) rc = set_fft_plane(t.plane != 0);
     if (!rc) {
@@ -156,13 +172,15 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
     return time_ms(st, reps, forces);
   };
   double best = 1e30;
-  int bs = pair_split, bt = pair_threads, bc = pair_ctas_per_sm;
+  int bs = pair_split, bt = pair_threads, bc = pair_ctas_per_sm, be = pair_nelec;
   if (cell_factor == 1 && !use_list) {  // with lists the cell kernel only serves overflows
+    const int shapes[4][2] = {{128, 1}, {160, 1}, {160, 2}, {192, 2}};  // threads, elec warps
     for (int split : {3, 9})
-      for (int threads : {128, 160})
+      for (const auto &sh : shapes)
         for (int ctas : {0, 5, 6, 8}) {
-          if (threads == 160 && ctas > 6) continue;  // register-limited residency
-          int rc = set_pair_config(split, threads, ctas);
+          const int threads = sh[0], nelec = sh[1];
+          if (ctas > 40 / (threads / 32)) continue;  // register-limited residency (64 regs)
+          int rc = set_pair_config(split, threads, ctas, nelec);
           if (rc) return rc;
           const double ms = timed();
           if (ms < best) {
@@ -170,9 +188,10 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
             bs = split;
             bt = threads;
             bc = ctas;
+            be = nelec;
           }
         }
-    int rc = set_pair_config(bs, bt, bc);
+    int rc = set_pair_config(bs, bt, bc, be);
     if (rc) return rc;
   } else {
     best = timed();
@@ -210,6 +229,7 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
   t.split = pair_split;
   t.threads = pair_threads;
   t.ctas = pair_ctas_per_sm;
+  t.nelec = pair_nelec;
   t.plane = plan.use_plane;
   for (int a = 0; a < 3; ++a) t.lpb[a] = plan.lpb[a];
   t.pair_ms = best;

@@ -255,7 +255,8 @@ def test_autotune_keeps_parity_and_caches(tmp_path, monkeypatch):
     sysg = g.System(ctx(), g.params_from(s), s.q, s.bonds)
     pos = torch.tensor(s.pos, dtype=torch.float64, device="cuda:0")
     t1 = sysg.autotune(pos)
-    assert t1["pair_split"] in (3, 9) and t1["pair_threads"] in (128, 160)
+    assert t1["pair_split"] in (3, 9) and t1["pair_threads"] in (128, 160, 192)
+    assert t1["pair_nelec"] in (1, 2)
     lst = g.System(ctx(), g.params_from(s, pair_path=g.GCME_PAIR_LIST), s.q, s.bonds)
     t3 = lst.autotune(pos)  # the list path has a cache entry of its own
     assert not t3["from_cache"]
