@@ -74,9 +74,11 @@ __device__ __forceinline__ void bspline_weights(int p, R fr, R *W, R *dW) {
   }
 }
 
+// k mod K for -K <= k < 2K: the B-spline grid indices base - t, with base =
+// floor(x K / L) in [0, K] for wrapped x and 0 <= t < p <= K.
 __device__ __forceinline__ int wrap_index(int k, int K) {
-  k %= K;
-  return k < 0 ? k + K : k;
+  k = k < 0 ? k + K : k;
+  return k >= K ? k - K : k;
 }
 
 template <typename R>
@@ -287,10 +289,26 @@ __device__ __forceinline__ void dft_small(R2 *v, int Rd, int sgn) {
   }
 }
 
+// Quotient a / d for 0 <= a < 2^22 and 1 <= d <= 2^12, from the FP32
+// product a * inv (inv = 1/d rounded): its error is below one unit for these
+// ranges, so one correction step gives the exact quotient.  Replaces integer
+// division by a runtime divisor in the FFT index arithmetic.
+__device__ __forceinline__ int qdiv(int a, int d, float inv) {
+  int q = (int)__fmul_rn((float)a, inv);
+  const int r = a - q * d;
+  q += (r >= d) - (r < 0);
+  return q;
+}
+
 // index of element k of line l of a K0 x K1 x K2 grid along `axis`
-__device__ __forceinline__ long long line_elem(int axis, int K0, int K1, long long l, int k) {
+// (lines along y: l = x + K0 z; inv0 = 1/K0)
+__device__ __forceinline__ long long line_elem(int axis, int K0, int K1, int l, int k,
+                                               float inv0) {
   if (axis == 0) return k + (long long)K0 * l;
-  if (axis == 1) return (l % K0) + (long long)K0 * (k + (long long)K1 * (l / K0));
+  if (axis == 1) {
+    const int z = qdiv(l, K0, inv0);
+    return (l - z * K0) + (long long)K0 * (k + (long long)K1 * z);
+  }
   return l + (long long)K0 * K1 * k;
 }
 
@@ -306,21 +324,30 @@ template <typename R, typename R2>
 __device__ __forceinline__ R2 *smem_fft(R2 *A, R2 *B, int nl, int K, int ls, int es,
                                         const int *radix, int nstage, const R2 *tw, int sgn) {
   const bool line_fast = ls == 1;
+  const float inv_nl = 1.0f / (float)nl;
   int Ns = 1;
   for (int st = 0; st < nstage; ++st) {
     const int Rd = radix[st];
     const int T = K / Rd;
     const int twstep = K / (Ns * Rd);
+    const float inv_T = 1.0f / (float)T, inv_Ns = 1.0f / (float)Ns;
     for (int t = threadIdx.x; t < nl * T; t += blockDim.x) {
-      const int li = line_fast ? t % nl : t / T;
-      const int j = line_fast ? t / nl : t % T;
-      const int k = j % Ns;
+      int li, j;
+      if (line_fast) {
+        j = qdiv(t, nl, inv_nl);
+        li = t - j * nl;
+      } else {
+        li = qdiv(t, T, inv_T);
+        j = t - li * T;
+      }
+      const int jq = qdiv(j, Ns, inv_Ns);
+      const int k = j - jq * Ns;
       R2 v[5];
       const R2 *in = A + li * ls;
       for (int r = 0; r < Rd; ++r) {
         R2 x = in[(j + r * T) * es];
         if (r > 0 && k > 0) {
-          R2 wv = tw[(k * r * twstep) % K];
+          R2 wv = tw[k * r * twstep];  // k r twstep < K: no wrap needed
           if (sgn > 0) wv.y = -wv.y;
           x = cmul(x, wv);
         }
@@ -328,7 +355,7 @@ __device__ __forceinline__ R2 *smem_fft(R2 *A, R2 *B, int nl, int K, int ls, int
       }
       dft_small<R, R2>(v, Rd, sgn);
       R2 *out = B + li * ls;
-      const int od = (j / Ns) * Ns * Rd + k;
+      const int od = jq * Ns * Rd + k;
       for (int q = 0; q < Rd; ++q) out[(od + q * Ns) * es] = v[q];
     }
     __syncthreads();
@@ -398,22 +425,23 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
   const SysDesc &S = P.sys[s];
   const int K0 = S.K[0], K1 = S.K[1], K2 = S.K[2];
   const int K = S.K[axis];
-  const long long nlines = (long long)K0 * K1 * K2 / K;
-  const long long l0 = (long long)tile * lpb;
-  const int nl = (int)min((long long)lpb, nlines - l0);
+  const int nlines = K0 * K1 * K2 / K;
+  const int l0 = tile * lpb;
+  const int nl = min(lpb, nlines - l0);
+  const float inv_K = 1.0f / (float)K, inv_nl = 1.0f / (float)nl, inv_K0 = 1.0f / (float)K0;
   R2 *grid = cg_all + S.grid_off;
   R2 *bufA = smem, *bufB = smem + lpb * K;
   // ---- load (line index fastest for strided axes: coalesced along x)
   for (int t = tid; t < nl * K; t += nt) {
     int li, k;
     if (axis == 0) {
-      li = t / K;
-      k = t % K;
+      li = qdiv(t, K, inv_K);
+      k = t - li * K;
     } else {
-      li = t % nl;
-      k = t / nl;
+      k = qdiv(t, nl, inv_nl);
+      li = t - k * nl;
     }
-    const long long gi = line_elem(axis, K0, K1, l0 + li, k);
+    const long long gi = line_elem(axis, K0, K1, l0 + li, k, inv_K0);
     R2 v;
     if (kind == FFT_FWD_FROM_Q) {
       const long long qv = (long long)P.qgrid[S.grid_off + gi];
@@ -437,15 +465,17 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
       const int Rd = S.radix[axis][st];
       const int T = K / Rd;
       const int twstep = K / (Ns * Rd);
+      const float inv_T = 1.0f / (float)T, inv_Ns = 1.0f / (float)Ns;
       for (int t = tid; t < nl * T; t += nt) {
-        const int li = t / T, j = t % T;
-        const int k = j % Ns;
+        const int li = qdiv(t, T, inv_T), j = t - li * T;
+        const int jq = qdiv(j, Ns, inv_Ns);
+        const int k = j - jq * Ns;
         R2 v[5];
         const R2 *in = bufA + li * K;
         for (int r = 0; r < Rd; ++r) {
           R2 x = in[j + r * T];
           if (r > 0 && k > 0) {
-            R2 wv = tw[(k * r * twstep) % K];
+            R2 wv = tw[k * r * twstep];  // k r twstep < K
             if (sgn > 0) wv.y = -wv.y;
             x = cmul(x, wv);
           }
@@ -453,7 +483,7 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
         }
         dft_small<R, R2>(v, Rd, sgn);
         R2 *out = bufB + li * K;
-        const int od = (j / Ns) * Ns * Rd + k;
+        const int od = jq * Ns * Rd + k;
         for (int q = 0; q < Rd; ++q) out[od + q * Ns] = v[q];
       }
       __syncthreads();
@@ -472,10 +502,11 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
                     S.bsp_off[2];
       const R pi2k2 = R(9.8696044010893586188 / (S.kappa * S.kappa));
       const R cpref = R(S.lB / (3.14159265358979323846 * S.V));
+      const R ib0 = R(1.0 / S.box[0]), ib1 = R(1.0 / S.box[1]), ib2 = R(1.0 / S.box[2]);
       for (int t = tid; t < nl * K; t += nt) {
-        const int li = t / K, k = t % K;
-        const long long l = l0 + li;
-        const int i0 = (int)(l % K0), i1 = (int)(l / K0), i2 = k;
+        const int li = qdiv(t, K, inv_K), k = t - li * K;
+        const int l = l0 + li;
+        const int i1 = qdiv(l, K0, inv_K0), i0 = l - i1 * K0, i2 = k;
         const int m0 = i0 < (K0 + 1) / 2 ? i0 : i0 - K0;
         const int m1 = i1 < (K1 + 1) / 2 ? i1 : i1 - K1;
         const int m2 = i2 < (K2 + 1) / 2 ? i2 : i2 - K2;
@@ -484,7 +515,7 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
           F.x = F.y = R(0);
           continue;
         }
-        const R mv0 = R(m0) / R(S.box[0]), mv1 = R(m1) / R(S.box[1]), mv2 = R(m2) / R(S.box[2]);
+        const R mv0 = R(m0) * ib0, mv1 = R(m1) * ib1, mv2 = R(m2) * ib2;
         const R msq = mv0 * mv0 + mv1 * mv1 + mv2 * mv2;
         const R BC = b0[i0] * b1[i1] * b2[i2] * cpref * exp(-pi2k2 * msq) / msq;
         const double Em = 0.5 * (double)BC * ((double)F.x * F.x + (double)F.y * F.y);
@@ -506,13 +537,13 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
   for (int t = tid; t < nl * K; t += nt) {
     int li, k;
     if (axis == 0) {
-      li = t / K;
-      k = t % K;
+      li = qdiv(t, K, inv_K);
+      k = t - li * K;
     } else {
-      li = t % nl;
-      k = t / nl;
+      k = qdiv(t, nl, inv_nl);
+      li = t - k * nl;
     }
-    grid[line_elem(axis, K0, K1, l0 + li, k)] = bufA[li * K + k];
+    grid[line_elem(axis, K0, K1, l0 + li, k, inv_K0)] = bufA[li * K + k];
   }
   if (kind == FFT_FWD_INFL_INV) {
     const double sc = S.recip_scale;
