@@ -707,6 +707,9 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     for (int z = 0; z < hsys[s].K[2]; ++z) planes.push_back(make_int2(s, z));
   }
   plan.nplane = (int)planes.size();
+  plan.order = hsys[0].order;
+  for (auto &S : hsys)
+    if (S.order != plan.order) plan.order = 0;
   plan.use_plane = plane_fits() ? 1 : 0;
   std::vector<int2> pw = make_pair_work(pair_split);
   n_pair_work = (int)pw.size();

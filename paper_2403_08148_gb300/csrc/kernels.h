@@ -17,6 +17,7 @@ struct PmePlan {
   int nplane;
   int use_plane;
   int plane_elems;  // largest K0 * K1 of the batch
+  int order;        // B-spline order shared by every system, else 0
 };
 
 void launch_cells(const Pool &P, cudaStream_t st);  // launch_bin + launch_sort

@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(128) k_persistent(Pool P, PersistArgs A) {
           dev_pair_f32_item_pk<false>(P, A.pair_work, w, smem, seg, st);
       }
     }
-    for (long long g = gtid; g < P.n_q * 8; g += gthreads) dev_spread<float>(P, g);
+    for (long long g = gtid; g < P.n_q * 8; g += gthreads) dev_spread<float, 0>(P, g);
     if (!grid_barrier(B)) return;
     // ---- K6/K7 FFT passes with the fused influence function
     if (A.plan.use_plane) {
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(128) k_persistent(Pool P, PersistArgs A) {
       }
     }
     // ---- K8 gather, K9 bonds, walls and dipole
-    GRID_LOOP(g, P.n_q * 8) dev_gather<float>(P, g);
+    GRID_LOOP(g, P.n_q * 8) dev_gather<float, 0>(P, g);
     GRID_LOOP(b, P.n_bond) dev_bonds<false>(P, b);
     GRID_LOOP(g, P.n_real) dev_walls(P, g);
     if (!grid_barrier(B)) return;

@@ -4,11 +4,34 @@
 
 namespace gcme {
 
-template <typename R>
-__global__ void k_spread(Pool P) { dev_spread<R>(P, blockIdx.x * (long long)blockDim.x + threadIdx.x); }
+template <typename R, int PO>
+__global__ void k_spread(Pool P) {
+  dev_spread<R, PO>(P, blockIdx.x * (long long)blockDim.x + threadIdx.x);
+}
 
+template <typename R, int PO>
+__global__ void k_gather(Pool P) {
+  dev_gather<R, PO>(P, blockIdx.x * (long long)blockDim.x + threadIdx.x);
+}
+
+// spread/gather with the batch's common spline order as a constant (4, 5
+// or 6), else the order read per system
 template <typename R>
-__global__ void k_gather(Pool P) { dev_gather<R>(P, blockIdx.x * (long long)blockDim.x + threadIdx.x); }
+static void launch_spread_gather(const Pool &P, int order, bool gather, int nb, int tb,
+                                 cudaStream_t st) {
+#define GCME_SG(PO)                                          \
+  do {                                                       \
+    if (gather) k_gather<R, PO><<<nb, tb, 0, st>>>(P);       \
+    else k_spread<R, PO><<<nb, tb, 0, st>>>(P);              \
+  } while (0)
+  switch (order) {
+    case 4: GCME_SG(4); break;
+    case 5: GCME_SG(5); break;
+    case 6: GCME_SG(6); break;
+    default: GCME_SG(0); break;
+  }
+#undef GCME_SG
+}
 
 template <typename R, bool INV>
 __global__ void __launch_bounds__(512) k_fft_plane(Pool P, const int2 *work, int nwork) {
@@ -29,8 +52,8 @@ void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStrea
   cudaMemsetAsync(P.qgrid, 0, sizeof(unsigned long long) * P.n_grid, st);
   const int tb = 256;
   const int nb = (int)((P.n_q * 8 + tb - 1) / tb);
-  if (fp64) k_spread<double><<<nb, tb, 0, st>>>(P);
-  else k_spread<float><<<nb, tb, 0, st>>>(P);
+  if (fp64) launch_spread_gather<double>(P, pl.order, false, nb, tb, st);
+  else launch_spread_gather<float>(P, pl.order, false, nb, tb, st);
   const size_t rsz = fp64 ? sizeof(double2) : sizeof(float2);
   auto line_pass = [&](int ax, int kind) {
     const size_t shm = 2 * (size_t)pl.lpb[ax] * pl.kmax[ax] * rsz;
@@ -56,8 +79,8 @@ void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStrea
     const int kinds[5] = {FFT_FWD_FROM_Q, FFT_FWD, FFT_FWD_INFL_INV, FFT_INV, FFT_INV};
     for (int ps = 0; ps < 5; ++ps) line_pass(axes[ps], kinds[ps]);
   }
-  if (fp64) k_gather<double><<<nb, tb, 0, st>>>(P);
-  else k_gather<float><<<nb, tb, 0, st>>>(P);
+  if (fp64) launch_spread_gather<double>(P, pl.order, true, nb, tb, st);
+  else launch_spread_gather<float>(P, pl.order, true, nb, tb, st);
 }
 
 void pme_set_smem_limits() {

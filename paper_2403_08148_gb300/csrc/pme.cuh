@@ -95,13 +95,15 @@ __device__ __forceinline__ double kfac_of<double>(const SysDesc &S, int a) {
 // --------------------------------------------------------------------------
 // spread: eight lanes per charge, lane tz handles the stencil plane tz
 // --------------------------------------------------------------------------
-template <typename R>
+// PO > 0: the spline order as a compile-time constant (every system of the
+// launch has it), so the weight arrays and loops stay in registers.
+template <typename R, int PO = 0>
 __device__ __forceinline__ void dev_spread(const Pool &P, long long g) {
   const long long c = g >> 3;
   const int tz = (int)(g & 7);
   if (c >= P.n_q) return;
   const SysDesc &S = P.sys[P.q_sys[c]];
-  const int p = S.order;
+  const int p = PO > 0 ? PO : S.order;
   if (tz >= p) return;
   const int e = P.qlist[c];
   R x[3], q;
@@ -117,12 +119,18 @@ __device__ __forceinline__ void dev_spread(const Pool &P, long long g) {
   }
   const int K0 = S.K[0], K1 = S.K[1], K2 = S.K[2];
   const int kz = wrap_index(base[2] - tz, K2);
-  const R wz = W[2][tz] * q * R(PmeT<R>::qscale);
+  R w2 = W[2][0];  // W[2][tz] by a select, keeping the weights in registers
+#pragma unroll
+  for (int t = 1; t < 8; ++t)
+    if (t < p && t == tz) w2 = W[2][t];
+  const R wz = w2 * q * R(PmeT<R>::qscale);
   unsigned long long *grid = P.qgrid + S.grid_off;
+#pragma unroll
   for (int ty = 0; ty < p; ++ty) {
     const int ky = wrap_index(base[1] - ty, K1);
     const R wyz = W[1][ty] * wz;
     unsigned long long *row = grid + (long long)K0 * (ky + (long long)K1 * kz);
+#pragma unroll
     for (int tx = 0; tx < p; ++tx) {
       const int kx = wrap_index(base[0] - tx, K0);
       long long v = (long long)llrint(W[0][tx] * wyz);
@@ -136,7 +144,7 @@ __device__ __forceinline__ void dev_spread(const Pool &P, long long g) {
 // --------------------------------------------------------------------------
 // Warp-synchronous: every lane of the warp must call it (lanes past the end
 // pass g beyond the last charge and contribute nothing).
-template <typename R>
+template <typename R, int PO = 0>
 __device__ __forceinline__ void dev_gather(const Pool &P, long long g) {
   using R2 = typename PmeT<R>::R2;
   const long long c = g >> 3;
@@ -144,7 +152,7 @@ __device__ __forceinline__ void dev_gather(const Pool &P, long long g) {
   bool act = c < P.n_q;
   const SysDesc *Sp = act ? &P.sys[P.q_sys[c]] : &P.sys[0];
   const SysDesc &S = *Sp;
-  const int p = S.order;
+  const int p = PO > 0 ? PO : S.order;
   int e = 0;
   if (act) {
     const long long loc = c - S.q_off;
@@ -168,11 +176,19 @@ __device__ __forceinline__ void dev_gather(const Pool &P, long long g) {
     const int kz = wrap_index(base[2] - tz, K2);
     const R2 *grid = (const R2 *)(sizeof(R) == 4 ? (const void *)P.cgrid : (const void *)P.cgrid64) +
                      S.grid_off;
-    const R wz = W[2][tz], dwz = dW[2][tz];
+    R wz = W[2][0], dwz = dW[2][0];  // W[2][tz], dW[2][tz] by a select
+#pragma unroll
+    for (int t = 1; t < 8; ++t)
+      if (t < p && t == tz) {
+        wz = W[2][t];
+        dwz = dW[2][t];
+      }
+#pragma unroll
     for (int ty = 0; ty < p; ++ty) {
       const int ky = wrap_index(base[1] - ty, K1);
       const R2 *row = grid + (long long)K0 * (ky + (long long)K1 * kz);
       R sx = 0, sy = 0, sz = 0;
+#pragma unroll
       for (int tx = 0; tx < p; ++tx) {
         const R v = row[wrap_index(base[0] - tx, K0)].x;
         sx += dW[0][tx] * v;
