@@ -135,7 +135,7 @@ struct SysDesc {
 struct Pool {
   const SysDesc *sys;
   int nsys;
-  int pad;
+  int any_slab;         // some system is a slab (walls, dipole term, images)
   // state (real beads)
   double *pos;          // [3 * N] FP64
   const double *q;      // [N] charge numbers z_i of the real beads

@@ -805,6 +805,8 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   }
   P.sys = d_sys;
   P.q = d_q;
+  P.any_slab = 0;
+  for (auto &S : hsys) P.any_slab |= S.geometry != GCME_BULK;
   P.n_real = nr;
   P.n_ext = ne;
   P.n_cells = ncell;
@@ -929,7 +931,9 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
 // K1, and nothing of it is read by the pair or bonded kernels until the
 // Yeh-Berkowitz and kick kernels: it runs on a side stream forked right
 // after binning and joined before them, so its latency-bound passes overlap
-// the cell sort and fill the SMs the pair kernel leaves idle.
+// the cell sort and fill the SMs the pair kernel leaves idle.  (Forking
+// before binning, with the spread wrapping positions itself, measured
+// slower: the FP64 wraps cost the spread more than the overlap gained.)
 void Engine::fork_pme(const Pool &Q, cudaStream_t st, bool vir, bool timed) {
   cudaEventRecord(fork_ev, st);
   cudaStreamWaitEvent(side_stream, fork_ev, 0);

@@ -23,11 +23,13 @@ void launch_bonded(const Pool &P, bool vir, cudaStream_t st) {
     if (vir) k_bonds<true><<<nb, 256, 0, st>>>(P);
     else k_bonds<false><<<nb, 256, 0, st>>>(P);
   }
-  if (P.n_real > 0) k_walls<<<(int)((P.n_real + 255) / 256), 256, 0, st>>>(P);
+  // walls and the slab dipole exist only in slab geometries
+  if (P.n_real > 0 && P.any_slab) k_walls<<<(int)((P.n_real + 255) / 256), 256, 0, st>>>(P);
 }
 
 void launch_slab_apply(const Pool &P, cudaStream_t st) {
-  if (P.n_real > 0) k_slab_apply<<<(int)((P.n_real + 255) / 256), 256, 0, st>>>(P);
+  if (P.n_real > 0 && P.any_slab)
+    k_slab_apply<<<(int)((P.n_real + 255) / 256), 256, 0, st>>>(P);
 }
 
 void launch_finalize(const Pool &P, bool vir, cudaStream_t st) {
