@@ -395,7 +395,8 @@ int Engine::set_pair_config(int split, int threads, int ctas_per_sm, int nelec) 
 
 bool Engine::plane_fits() const {
   const size_t rsz = fp64 ? sizeof(double2) : sizeof(float2);
-  return plan.plane_elems > 0 && 2 * (size_t)plan.plane_elems * rsz <= kFftSmemLimit;
+  return plan.plane_elems > 0 &&
+         (2 * (size_t)plan.plane_elems + plan.kmax[0] + plan.kmax[1]) * rsz <= kFftSmemLimit;
 }
 
 int Engine::set_fft_plane(bool on) {
@@ -411,7 +412,7 @@ int Engine::set_fft_plane(bool on) {
 int Engine::set_fft_lpb(int axis, int lpb) {
   const size_t rsz = fp64 ? sizeof(double2) : sizeof(float2);
   if (axis < 0 || axis > 2 || lpb < kMinLpb || lpb > 64 ||
-      2 * (size_t)lpb * plan.kmax[axis] * rsz > kFftSmemLimit) {
+      (2 * (size_t)lpb + 1) * plan.kmax[axis] * rsz > kFftSmemLimit) {
     set_error("FFT lines per tile out of range");
     return GCME_ERR_INVALID;
   }

@@ -165,8 +165,10 @@ size_t persistent_smem(const PmePlan &pl, bool species) {
     pair = (pair + 15) / 16 * 16 + sizeof(PairTab) * kMaxTypes * kMaxTypes + kPairCap;
   size_t sort = sizeof(long long) * kSortCap + 16;
   size_t fft = 0;
-  for (int a = 0; a < 3; ++a) fft = std::max(fft, 2 * (size_t)pl.lpb[a] * pl.kmax[a] * sizeof(float2));
-  if (pl.use_plane) fft = std::max(fft, 2 * (size_t)pl.plane_elems * sizeof(float2));
+  for (int a = 0; a < 3; ++a)
+    fft = std::max(fft, (2 * (size_t)pl.lpb[a] + 1) * pl.kmax[a] * sizeof(float2));
+  if (pl.use_plane)
+    fft = std::max(fft, (2 * (size_t)pl.plane_elems + pl.kmax[0] + pl.kmax[1]) * sizeof(float2));
   return std::max(pair, std::max(sort, fft));
 }
 

@@ -56,7 +56,7 @@ void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStrea
   else launch_spread_gather<float>(P, pl.order, false, nb, tb, st);
   const size_t rsz = fp64 ? sizeof(double2) : sizeof(float2);
   auto line_pass = [&](int ax, int kind) {
-    const size_t shm = 2 * (size_t)pl.lpb[ax] * pl.kmax[ax] * rsz;
+    const size_t shm = (2 * (size_t)pl.lpb[ax] + 1) * pl.kmax[ax] * rsz;
     const int nw = pl.nwork[ax];
     if (nw == 0) return;
     if (fp64) {
@@ -68,7 +68,7 @@ void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStrea
     }
   };
   if (pl.use_plane) {
-    const size_t shm = 2 * (size_t)pl.plane_elems * rsz;
+    const size_t shm = (2 * (size_t)pl.plane_elems + pl.kmax[0] + pl.kmax[1]) * rsz;
     if (fp64) k_fft_plane<double, false><<<pl.nplane, 512, shm, st>>>(P, pl.plane_work, pl.nplane);
     else k_fft_plane<float, false><<<pl.nplane, 512, shm, st>>>(P, pl.plane_work, pl.nplane);
     line_pass(2, FFT_FWD_INFL_INV);

@@ -385,7 +385,8 @@ __device__ __forceinline__ R2 *smem_fft(R2 *A, R2 *B, int nl, int K, int ls, int
 
 // One z-plane (x and y passes) of one system by the whole CTA: forward from
 // the fixed-point charge grid (INV = false) or backward (INV = true) on the
-// complex grid.  smem: 2 * K0 * K1 complex values.  Ends with a barrier.
+// complex grid.  smem: 2 * K0 * K1 + K0 + K1 complex values (two plane
+// buffers, then the x and y twiddle tables).  Ends with a barrier.
 template <typename R, bool INV>
 __device__ __forceinline__ void dev_fft_plane(const Pool &P, const int2 *work, int w,
                                               unsigned char *smem_raw) {
@@ -399,6 +400,9 @@ __device__ __forceinline__ void dev_fft_plane(const Pool &P, const int2 *work, i
   const int G2 = K0 * K1;
   const long long base = S.grid_off + (long long)z * G2;
   R2 *A = smem, *B = smem + G2;
+  R2 *tw0 = smem + 2 * G2, *tw1 = tw0 + K0;
+  for (int t = threadIdx.x; t < K0; t += blockDim.x) tw0[t] = tw_all[S.tw_off[0] + t];
+  for (int t = threadIdx.x; t < K1; t += blockDim.x) tw1[t] = tw_all[S.tw_off[1] + t];
   for (int t = threadIdx.x; t < G2; t += blockDim.x) {
     R2 v;
     if (INV) {
@@ -413,22 +417,21 @@ __device__ __forceinline__ void dev_fft_plane(const Pool &P, const int2 *work, i
   const int sgn = INV ? +1 : -1;
   R2 *res;
   if (!INV) {
-    res = smem_fft<R, R2>(A, B, K1, K0, K0, 1, S.radix[0], S.nstage[0], tw_all + S.tw_off[0], sgn);
+    res = smem_fft<R, R2>(A, B, K1, K0, K0, 1, S.radix[0], S.nstage[0], tw0, sgn);
     R2 *other = res == smem ? smem + G2 : smem;
-    res = smem_fft<R, R2>(res, other, K0, K1, 1, K0, S.radix[1], S.nstage[1], tw_all + S.tw_off[1],
-                          sgn);
+    res = smem_fft<R, R2>(res, other, K0, K1, 1, K0, S.radix[1], S.nstage[1], tw1, sgn);
   } else {
-    res = smem_fft<R, R2>(A, B, K0, K1, 1, K0, S.radix[1], S.nstage[1], tw_all + S.tw_off[1], sgn);
+    res = smem_fft<R, R2>(A, B, K0, K1, 1, K0, S.radix[1], S.nstage[1], tw1, sgn);
     R2 *other = res == smem ? smem + G2 : smem;
-    res = smem_fft<R, R2>(res, other, K1, K0, K0, 1, S.radix[0], S.nstage[0], tw_all + S.tw_off[0],
-                          sgn);
+    res = smem_fft<R, R2>(res, other, K1, K0, K0, 1, S.radix[0], S.nstage[0], tw0, sgn);
   }
   for (int t = threadIdx.x; t < G2; t += blockDim.x) cg_all[base + t] = res[t];
   __syncthreads();
 }
 
 // One tile of lpb lines of one system along `axis` by the whole CTA (any
-// block size).  smem: 2 * lpb * kmax complex values.  Ends with a barrier.
+// block size).  smem: (2 * lpb + 1) * kmax complex values (two line buffers,
+// then the axis' twiddle table).  Ends with a barrier.
 template <typename R, bool VIR>
 __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, int w, int axis,
                                              int kind, int lpb, unsigned char *smem_raw) {
@@ -447,6 +450,8 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
   const float inv_K = 1.0f / (float)K, inv_nl = 1.0f / (float)nl, inv_K0 = 1.0f / (float)K0;
   R2 *grid = cg_all + S.grid_off;
   R2 *bufA = smem, *bufB = smem + lpb * K;
+  R2 *tws = smem + 2 * lpb * K;
+  for (int t = tid; t < K; t += nt) tws[t] = tw_all[S.tw_off[axis] + t];
   // ---- load (line index fastest for strided axes: coalesced along x)
   for (int t = tid; t < nl * K; t += nt) {
     int li, k;
@@ -469,7 +474,7 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
     bufA[li * K + k] = v;
   }
   __syncthreads();
-  const R2 *tw = tw_all + S.tw_off[axis];
+  const R2 *tw = tws;
   // one or two passes of stages (forward, then backward for the fused z pass)
   const int npass = (kind == FFT_FWD_INFL_INV) ? 2 : 1;
   double e_loc = 0.0;

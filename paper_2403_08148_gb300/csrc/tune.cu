@@ -200,7 +200,7 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
   for (int a = 0; a < 3; ++a) {
     int bl = plan.lpb[a];
     for (int lpb : {4, 8, 16, 32, 64}) {
-      if (2 * (size_t)lpb * plan.kmax[a] * rsz > kFftSmemLimit) continue;
+      if ((2 * (size_t)lpb + 1) * plan.kmax[a] * rsz > kFftSmemLimit) continue;
       int rc = set_fft_lpb(a, lpb);
       if (rc) return rc;
       const double ms = timed();
