@@ -368,6 +368,16 @@ typedef struct gcme_tuning {
 int gcme_autotune(gcme_sys *sys, const double *d_pos, int32_t flags, gcme_tuning *out,
                   gcme_stream_t stream);
 
+/* Apply given launch shapes without timing (e.g. a tuning recorded
+ * elsewhere, or to pin one path): pair_split, pair_threads, pair_nelec and
+ * pair_ctas_per_sm (27-cell path of cell_factor 1 only; ignored otherwise),
+ * fft_lpb[3] and fft_plane are read, every other field ignored.  A shape out
+ * of range (see gcme_tuning), lines per tile or x-y planes that do not fit in
+ * shared memory return GCME_ERR_INVALID and leave the shapes unchanged.
+ * Results are unchanged except for FP32 summation order. */
+int gcme_apply_tuning(gcme_sys *sys, const gcme_tuning *t);
+int gcme_batch_apply_tuning(gcme_batch *b, const gcme_tuning *t);
+
 /* ---- batch of independent systems ---------------------------------------- */
 
 /* A batch of nsys independent systems stepped together: every phase of the

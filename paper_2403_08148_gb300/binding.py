@@ -68,6 +68,16 @@ class Tuning(ctypes.Structure):
                 ("cell_factor", ctypes.c_int32), ("pair_nelec", ctypes.c_int32),
                 ("forces_ms", ctypes.c_double), ("pme_ms", ctypes.c_double)]
 
+    @classmethod
+    def from_dict(cls, d: dict) -> "Tuning":
+        t = cls()
+        for k in ("pair_split", "pair_threads", "pair_ctas_per_sm", "pair_nelec"):
+            setattr(t, k, int(d[k]))
+        for a in range(3):
+            t.fft_lpb[a] = int(d["fft_lpb"][a])
+        t.fft_plane = int(bool(d["fft_plane"]))
+        return t
+
     def as_dict(self):
         return {"pair_split": self.pair_split, "pair_threads": self.pair_threads,
                 "pair_ctas_per_sm": self.pair_ctas_per_sm, "fft_lpb": list(self.fft_lpb),
@@ -125,6 +135,8 @@ _SIGS = {
     "gcme_batch_phase_ms": ([_vp, _vp, _i32, _vp], ctypes.c_int),
     "gcme_autotune": ([_vp, _vp, _i32, ctypes.POINTER(Tuning), _vp], ctypes.c_int),
     "gcme_batch_autotune": ([_vp, _i32, ctypes.POINTER(Tuning), _vp], ctypes.c_int),
+    "gcme_apply_tuning": ([_vp, ctypes.POINTER(Tuning)], ctypes.c_int),
+    "gcme_batch_apply_tuning": ([_vp, ctypes.POINTER(Tuning)], ctypes.c_int),
     "gcme_debug_barrier_timeout": ([_vp, ctypes.c_double, _vp], ctypes.c_int),
     "gcme_debug_pairs": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
     "gcme_batch_create": ([_vp, _i32, ctypes.POINTER(Params), _vp, _vp, _vp, _vp, _vp,
@@ -351,6 +363,10 @@ class System:
                                     _stream(stream)))
         return t.as_dict()
 
+    def apply_tuning(self, tuning: dict):
+        """Apply launch shapes (the keys of autotune()'s result) without timing."""
+        _check(load().gcme_apply_tuning(self.h, ctypes.byref(Tuning.from_dict(tuning))))
+
     def step_continue(self, d_pos, d_vel, nsteps: int, d_energy=None, stream=None):
         _check(load().gcme_step_continue(self.h, _ptr(d_pos), _ptr(d_vel), int(nsteps),
                                          _ptr(d_energy), _stream(stream)))
@@ -434,6 +450,9 @@ class Batch:
         t = Tuning()
         _check(load().gcme_batch_autotune(self.h, int(flags), ctypes.byref(t), _stream(stream)))
         return t.as_dict()
+
+    def apply_tuning(self, tuning: dict):
+        _check(load().gcme_batch_apply_tuning(self.h, ctypes.byref(Tuning.from_dict(tuning))))
 
     def phase_ms(self):
         ms = np.zeros(6, np.float32)

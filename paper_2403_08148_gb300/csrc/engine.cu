@@ -301,11 +301,15 @@ std::vector<int2> Engine::make_pair_work(int split) const {
   return pw;
 }
 
+// Tiles of lpb lines along `axis`; the z lines of the plane path cover the
+// Hermitian half k0 < K0/2 + 1 of each plane only.
 std::vector<int2> Engine::make_fft_work(int axis, int lpb) const {
   std::vector<int2> w;
+  const bool half = axis == 2 && plan.use_plane;
   for (int s = 0; s < (int)hsys.size(); ++s) {
     const SysDesc &S = hsys[s];
-    const long long nl = (long long)S.K[0] * S.K[1] * S.K[2] / S.K[axis];
+    const long long k0 = half ? S.K[0] / 2 + 1 : S.K[0];
+    const long long nl = k0 * S.K[1] * S.K[2] / S.K[axis];
     const int nt = (int)((nl + lpb - 1) / lpb);
     for (int t = 0; t < nt; ++t) w.push_back(make_int2(s, t));
   }
@@ -405,8 +409,35 @@ int Engine::set_fft_plane(bool on) {
     return GCME_ERR_INVALID;
   }
   plan.use_plane = on ? 1 : 0;
+  // the z-pass tiles follow: half or full spectrum lines
+  std::vector<int2> w = make_fft_work(2, plan.lpb[2]);
+  GCME_CK(cudaMemcpy(const_cast<int2 *>(plan.work[2]), w.data(), sizeof(int2) * w.size(),
+                     cudaMemcpyHostToDevice));
+  plan.nwork[2] = (int)w.size();
   clear_graphs();
   return GCME_OK;
+}
+
+int Engine::apply_tuning(int split, int threads, int ctas_per_sm, int nelec, const int lpb[3],
+                         bool plane) {
+  const bool pair_shapes = cell_factor == 1 && !use_list;
+  const size_t rsz = fp64 ? sizeof(double2) : sizeof(float2);
+  bool ok = !(plane && !plane_fits());
+  for (int a = 0; a < 3; ++a)
+    ok = ok && lpb[a] >= kMinLpb && lpb[a] <= 64 &&
+         (2 * (size_t)lpb[a] + 1) * plan.kmax[a] * rsz <= kFftSmemLimit;
+  if (pair_shapes)
+    ok = ok && (split == 3 || split == 9) && (threads == 128 || threads == 160 || threads == 192) &&
+         ctas_per_sm >= 0 && ctas_per_sm <= 8 && (nelec == 1 || nelec == 2) &&
+         threads / 32 - nelec >= 2;
+  if (!ok) {
+    set_error("launch shapes out of range or larger than shared memory");
+    return GCME_ERR_INVALID;
+  }
+  int rc = pair_shapes ? set_pair_config(split, threads, ctas_per_sm, nelec) : GCME_OK;
+  for (int a = 0; !rc && a < 3; ++a) rc = set_fft_lpb(a, lpb[a]);
+  if (!rc) rc = set_fft_plane(plane);
+  return rc;
 }
 
 int Engine::set_fft_lpb(int axis, int lpb) {
@@ -694,24 +725,26 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     while (lpb > 8 && lpb * plan.kmax[a] > 1024) lpb /= 2;
     plan.lpb[a] = lpb;
   }
-  std::vector<int2> fftw[3];
-  int fft_cap[3];
-  for (int a = 0; a < 3; ++a) {
-    fftw[a] = make_fft_work(a, plan.lpb[a]);
-    plan.nwork[a] = (int)fftw[a].size();
-    fft_cap[a] = (int)make_fft_work(a, kMinLpb).size();
-  }
+  // plane passes: one work item per pair of z-planes (2p, 2p + 1)
   std::vector<int2> planes;
   plan.plane_elems = 0;
   for (int s = 0; s < ns; ++s) {
     plan.plane_elems = std::max(plan.plane_elems, hsys[s].K[0] * hsys[s].K[1]);
-    for (int z = 0; z < hsys[s].K[2]; ++z) planes.push_back(make_int2(s, z));
+    for (int z = 0; z < (hsys[s].K[2] + 1) / 2; ++z) planes.push_back(make_int2(s, z));
   }
   plan.nplane = (int)planes.size();
   plan.order = hsys[0].order;
   for (auto &S : hsys)
     if (S.order != plan.order) plan.order = 0;
+  std::vector<int2> fftw[3];
+  int fft_cap[3];
+  plan.use_plane = 0;  // capacities for the full-spectrum lines
+  for (int a = 0; a < 3; ++a) fft_cap[a] = (int)make_fft_work(a, kMinLpb).size();
   plan.use_plane = plane_fits() ? 1 : 0;
+  for (int a = 0; a < 3; ++a) {
+    fftw[a] = make_fft_work(a, plan.lpb[a]);
+    plan.nwork[a] = (int)fftw[a].size();
+  }
   std::vector<int2> pw = make_pair_work(pair_split);
   n_pair_work = (int)pw.size();
   const int pair_cap = std::max(n_pair_work, (int)make_pair_work(9).size());
@@ -1671,6 +1704,26 @@ int gcme_autotune(gcme_sys *sys, const double *d_pos, int32_t flags, gcme_tuning
   sys->last_pos = sys->last_vel = nullptr;  // forces no longer match a trajectory
   fill_tuning(sys->eng, a, b, hit, out);
   return GCME_OK;
+}
+
+int gcme_apply_tuning(gcme_sys *sys, const gcme_tuning *t) {
+  if (!sys || !t) {
+    set_error("invalid argument to gcme_apply_tuning");
+    return GCME_ERR_INVALID;
+  }
+  GCME_TRY_CK(cudaSetDevice(sys->eng.device));
+  return sys->eng.apply_tuning(t->pair_split, t->pair_threads, t->pair_ctas_per_sm,
+                               t->pair_nelec, t->fft_lpb, t->fft_plane != 0);
+}
+
+int gcme_batch_apply_tuning(gcme_batch *bt, const gcme_tuning *t) {
+  if (!bt || !t) {
+    set_error("invalid argument to gcme_batch_apply_tuning");
+    return GCME_ERR_INVALID;
+  }
+  GCME_TRY_CK(cudaSetDevice(bt->eng.device));
+  return bt->eng.apply_tuning(t->pair_split, t->pair_threads, t->pair_ctas_per_sm,
+                              t->pair_nelec, t->fft_lpb, t->fft_plane != 0);
 }
 
 int gcme_batch_autotune(gcme_batch *bt, int32_t flags, gcme_tuning *out, gcme_stream_t stream) {

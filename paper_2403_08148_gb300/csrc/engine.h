@@ -75,6 +75,9 @@ class Engine {
   int set_fft_lpb(int axis, int lpb);
   bool plane_fits() const;
   int set_fft_plane(bool on);
+  // launch shapes given by the caller (checked before any is changed)
+  int apply_tuning(int split, int threads, int ctas_per_sm, int nelec, const int lpb[3],
+                   bool plane);
   void clear_graphs();
   // time candidate configurations on the current state and keep the
   // fastest (tune.cu); from_cache reports a hit of the tuning cache

@@ -127,7 +127,8 @@ __global__ void __launch_bounds__(128) k_persistent(Pool P, PersistArgs A) {
         dev_fft_plane<float, false>(P, A.plan.plane_work, w, smem);
       if (!grid_barrier(B)) return;
       for (int w = blockIdx.x; w < A.plan.nwork[2]; w += gridDim.x)
-        dev_fft_item<float, false>(P, A.plan.work[2], w, 2, FFT_FWD_INFL_INV, A.plan.lpb[2], smem);
+        dev_fft_item<float, false>(P, A.plan.work[2], w, 2, FFT_FWD_INFL_INV, A.plan.lpb[2], 1,
+                                   smem);
       if (!grid_barrier(B)) return;
       for (int w = blockIdx.x; w < A.plan.nplane; w += gridDim.x)
         dev_fft_plane<float, true>(P, A.plan.plane_work, w, smem);
@@ -138,7 +139,8 @@ __global__ void __launch_bounds__(128) k_persistent(Pool P, PersistArgs A) {
       for (int ps = 0; ps < 5; ++ps) {
         const int ax = axes[ps];
         for (int w = blockIdx.x; w < A.plan.nwork[ax]; w += gridDim.x)
-          dev_fft_item<float, false>(P, A.plan.work[ax], w, ax, kinds[ps], A.plan.lpb[ax], smem);
+          dev_fft_item<float, false>(P, A.plan.work[ax], w, ax, kinds[ps], A.plan.lpb[ax], 0,
+                                     smem);
         if (!grid_barrier(B)) return;
       }
     }

@@ -41,10 +41,10 @@ __global__ void __launch_bounds__(512) k_fft_plane(Pool P, const int2 *work, int
 
 template <typename R, bool VIR>
 __global__ void __launch_bounds__(256) k_fft(Pool P, const int2 *work, int nwork, int axis, int kind,
-                                             int lpb) {
+                                             int lpb, int half) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   for (int w = blockIdx.x; w < nwork; w += gridDim.x)
-    dev_fft_item<R, VIR>(P, work, w, axis, kind, lpb, smem_raw);
+    dev_fft_item<R, VIR>(P, work, w, axis, kind, lpb, half, smem_raw);
 }
 
 void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStream_t st) {
@@ -55,16 +55,18 @@ void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStrea
   if (fp64) launch_spread_gather<double>(P, pl.order, false, nb, tb, st);
   else launch_spread_gather<float>(P, pl.order, false, nb, tb, st);
   const size_t rsz = fp64 ? sizeof(double2) : sizeof(float2);
+  // the z pass of the plane path works on the Hermitian half spectrum
+  const int half = pl.use_plane;
   auto line_pass = [&](int ax, int kind) {
     const size_t shm = (2 * (size_t)pl.lpb[ax] + 1) * pl.kmax[ax] * rsz;
-    const int nw = pl.nwork[ax];
+    const int nw = pl.nwork[ax], lpb = pl.lpb[ax];
     if (nw == 0) return;
     if (fp64) {
-      if (vir) k_fft<double, true><<<nw, 256, shm, st>>>(P, pl.work[ax], nw, ax, kind, pl.lpb[ax]);
-      else k_fft<double, false><<<nw, 256, shm, st>>>(P, pl.work[ax], nw, ax, kind, pl.lpb[ax]);
+      if (vir) k_fft<double, true><<<nw, 256, shm, st>>>(P, pl.work[ax], nw, ax, kind, lpb, half);
+      else k_fft<double, false><<<nw, 256, shm, st>>>(P, pl.work[ax], nw, ax, kind, lpb, half);
     } else {
-      if (vir) k_fft<float, true><<<nw, 256, shm, st>>>(P, pl.work[ax], nw, ax, kind, pl.lpb[ax]);
-      else k_fft<float, false><<<nw, 256, shm, st>>>(P, pl.work[ax], nw, ax, kind, pl.lpb[ax]);
+      if (vir) k_fft<float, true><<<nw, 256, shm, st>>>(P, pl.work[ax], nw, ax, kind, lpb, half);
+      else k_fft<float, false><<<nw, 256, shm, st>>>(P, pl.work[ax], nw, ax, kind, lpb, half);
     }
   };
   if (pl.use_plane) {

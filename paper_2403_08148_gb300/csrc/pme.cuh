@@ -383,10 +383,22 @@ __device__ __forceinline__ R2 *smem_fft(R2 *A, R2 *B, int nl, int K, int ls, int
   return A;
 }
 
-// One z-plane (x and y passes) of one system by the whole CTA: forward from
-// the fixed-point charge grid (INV = false) or backward (INV = true) on the
-// complex grid.  smem: 2 * K0 * K1 + K0 + K1 complex values (two plane
-// buffers, then the x and y twiddle tables).  Ends with a barrier.
+// Two z-planes (x and y passes) of one system by the whole CTA, packed as
+// the real and imaginary parts of one complex plane (both planes are real in
+// position space).  Work item (s, p) covers planes 2p and 2p + 1 (the
+// second absent when K2 is odd and 2p + 1 = K2).
+//
+// Forward (INV = false): Z = FFT2(q_2p + i q_2p+1) from the fixed-point
+// charge grid, then X(k) = (Z(k) + conj Z(-k)) / 2 and
+// Y(k) = (Z(k) - conj Z(-k)) / (2i) are the spectra of the two planes; only
+// the half k0 < K0/2 + 1 is stored (Hermitian symmetry gives the rest), at
+// the usual positions of each plane.
+// Backward (INV = true): the half spectra X, Y of planes 2p, 2p + 1 (z
+// pass done) are completed by X(k) = conj X(-k) for k0 >= K0/2 + 1, and
+// the inverse FFT2 of X + i Y gives plane 2p in its real part and plane
+// 2p + 1 in its imaginary part, written as real values (imaginary 0).
+// smem: 2 * K0 * K1 + K0 + K1 complex values (two plane buffers, then the x
+// and y twiddle tables).  Ends with a barrier.
 template <typename R, bool INV>
 __device__ __forceinline__ void dev_fft_plane(const Pool &P, const int2 *work, int w,
                                               unsigned char *smem_raw) {
@@ -394,11 +406,14 @@ __device__ __forceinline__ void dev_fft_plane(const Pool &P, const int2 *work, i
   R2 *smem = reinterpret_cast<R2 *>(smem_raw);
   R2 *cg_all = (R2 *)(sizeof(R) == 4 ? (void *)P.cgrid : (void *)P.cgrid64);
   const R2 *tw_all = (const R2 *)(sizeof(R) == 4 ? (const void *)P.tw : (const void *)P.tw64);
-  const int s = work[w].x, z = work[w].y;
+  const int s = work[w].x, zp = work[w].y;
   const SysDesc &S = P.sys[s];
   const int K0 = S.K[0], K1 = S.K[1];
-  const int G2 = K0 * K1;
-  const long long base = S.grid_off + (long long)z * G2;
+  const int G2 = K0 * K1, H0 = K0 / 2 + 1;
+  const bool two = 2 * zp + 1 < S.K[2];
+  const long long base0 = S.grid_off + (long long)(2 * zp) * G2;
+  const long long base1 = base0 + G2;
+  const float inv_K0 = 1.0f / (float)K0, inv_H0 = 1.0f / (float)H0;
   R2 *A = smem, *B = smem + G2;
   R2 *tw0 = smem + 2 * G2, *tw1 = tw0 + K0;
   for (int t = threadIdx.x; t < K0; t += blockDim.x) tw0[t] = tw_all[S.tw_off[0] + t];
@@ -406,10 +421,26 @@ __device__ __forceinline__ void dev_fft_plane(const Pool &P, const int2 *work, i
   for (int t = threadIdx.x; t < G2; t += blockDim.x) {
     R2 v;
     if (INV) {
-      v = cg_all[base + t];
+      const int i1 = qdiv(t, K0, inv_K0), i0 = t - i1 * K0;
+      R2 X, Y;
+      Y.x = Y.y = R(0);
+      if (i0 < H0) {
+        X = cg_all[base0 + t];
+        if (two) Y = cg_all[base1 + t];
+      } else {  // mirror of the stored half, conjugated
+        const int m = (K0 - i0) + K0 * (i1 == 0 ? 0 : K1 - i1);
+        X = cg_all[base0 + m];
+        X.y = -X.y;
+        if (two) {
+          Y = cg_all[base1 + m];
+          Y.y = -Y.y;
+        }
+      }
+      v.x = X.x - Y.y;  // X + i Y
+      v.y = X.y + Y.x;
     } else {
-      v.x = (R)((double)(long long)P.qgrid[base + t] * (1.0 / PmeT<R>::qscale));
-      v.y = R(0);
+      v.x = (R)((double)(long long)P.qgrid[base0 + t] * (1.0 / PmeT<R>::qscale));
+      v.y = two ? (R)((double)(long long)P.qgrid[base1 + t] * (1.0 / PmeT<R>::qscale)) : R(0);
     }
     A[t] = v;
   }
@@ -420,21 +451,48 @@ __device__ __forceinline__ void dev_fft_plane(const Pool &P, const int2 *work, i
     res = smem_fft<R, R2>(A, B, K1, K0, K0, 1, S.radix[0], S.nstage[0], tw0, sgn);
     R2 *other = res == smem ? smem + G2 : smem;
     res = smem_fft<R, R2>(res, other, K0, K1, 1, K0, S.radix[1], S.nstage[1], tw1, sgn);
+    for (int t = threadIdx.x; t < H0 * K1; t += blockDim.x) {
+      const int i1 = qdiv(t, H0, inv_H0), i0 = t - i1 * H0;
+      const R2 Z = res[i0 + K0 * i1];
+      const R2 Zm = res[(i0 == 0 ? 0 : K0 - i0) + K0 * (i1 == 0 ? 0 : K1 - i1)];
+      R2 X, Y;
+      X.x = R(0.5) * (Z.x + Zm.x);
+      X.y = R(0.5) * (Z.y - Zm.y);
+      cg_all[base0 + i0 + K0 * i1] = X;
+      if (two) {
+        Y.x = R(0.5) * (Z.y + Zm.y);
+        Y.y = R(0.5) * (Zm.x - Z.x);
+        cg_all[base1 + i0 + K0 * i1] = Y;
+      }
+    }
   } else {
     res = smem_fft<R, R2>(A, B, K0, K1, 1, K0, S.radix[1], S.nstage[1], tw1, sgn);
     R2 *other = res == smem ? smem + G2 : smem;
     res = smem_fft<R, R2>(res, other, K1, K0, K0, 1, S.radix[0], S.nstage[0], tw0, sgn);
+    for (int t = threadIdx.x; t < G2; t += blockDim.x) {
+      const R2 z = res[t];
+      R2 a, b;
+      a.x = z.x;
+      b.x = z.y;
+      a.y = b.y = R(0);
+      cg_all[base0 + t] = a;
+      if (two) cg_all[base1 + t] = b;
+    }
   }
-  for (int t = threadIdx.x; t < G2; t += blockDim.x) cg_all[base + t] = res[t];
   __syncthreads();
 }
 
 // One tile of lpb lines of one system along `axis` by the whole CTA (any
-// block size).  smem: (2 * lpb + 1) * kmax complex values (two line buffers,
+// block size).  half (z lines only): the grid holds the Hermitian half
+// k0 < K0/2 + 1 of every z-plane's spectrum (the packed plane passes), so
+// only those (K0/2 + 1) K1 lines exist; line l maps to k0 = l mod (K0/2 + 1),
+// k1 = l div (K0/2 + 1), and the spectrum's energy and virial count each
+// line with its mirror (weight 2 unless k0 = 0 or 2 k0 = K0).  smem: (2 * lpb + 1) * kmax complex values (two line buffers,
 // then the axis' twiddle table).  Ends with a barrier.
 template <typename R, bool VIR>
 __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, int w, int axis,
-                                             int kind, int lpb, unsigned char *smem_raw) {
+                                             int kind, int lpb, int half,
+                                             unsigned char *smem_raw) {
   using R2 = typename PmeT<R>::R2;
   R2 *smem = reinterpret_cast<R2 *>(smem_raw);
   R2 *cg_all = (R2 *)(sizeof(R) == 4 ? (void *)P.cgrid : (void *)P.cgrid64);
@@ -444,10 +502,20 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
   const SysDesc &S = P.sys[s];
   const int K0 = S.K[0], K1 = S.K[1], K2 = S.K[2];
   const int K = S.K[axis];
-  const int nlines = K0 * K1 * K2 / K;
+  half = half && axis == 2;
+  const int H0 = half ? K0 / 2 + 1 : K0;  // stored k0 extent of a z-plane
+  const int nlines = H0 * K1 * K2 / K;
   const int l0 = tile * lpb;
   const int nl = min(lpb, nlines - l0);
   const float inv_K = 1.0f / (float)K, inv_nl = 1.0f / (float)nl, inv_K0 = 1.0f / (float)K0;
+  const float inv_H0 = 1.0f / (float)H0;
+  // full-grid line index of tile line li (identity unless half)
+  auto full_line = [&](int li) {
+    const int l = l0 + li;
+    if (!half) return l;
+    const int i1 = qdiv(l, H0, inv_H0);
+    return (l - i1 * H0) + K0 * i1;
+  };
   R2 *grid = cg_all + S.grid_off;
   R2 *bufA = smem, *bufB = smem + lpb * K;
   R2 *tws = smem + 2 * lpb * K;
@@ -462,7 +530,7 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
       k = qdiv(t, nl, inv_nl);
       li = t - k * nl;
     }
-    const long long gi = line_elem(axis, K0, K1, l0 + li, k, inv_K0);
+    const long long gi = line_elem(axis, K0, K1, full_line(li), k, inv_K0);
     R2 v;
     if (kind == FFT_FWD_FROM_Q) {
       const long long qv = (long long)P.qgrid[S.grid_off + gi];
@@ -526,7 +594,7 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
       const R ib0 = R(1.0 / S.box[0]), ib1 = R(1.0 / S.box[1]), ib2 = R(1.0 / S.box[2]);
       for (int t = tid; t < nl * K; t += nt) {
         const int li = qdiv(t, K, inv_K), k = t - li * K;
-        const int l = l0 + li;
+        const int l = full_line(li);
         const int i1 = qdiv(l, K0, inv_K0), i0 = l - i1 * K0, i2 = k;
         const int m0 = i0 < (K0 + 1) / 2 ? i0 : i0 - K0;
         const int m1 = i1 < (K1 + 1) / 2 ? i1 : i1 - K1;
@@ -539,7 +607,8 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
         const R mv0 = R(m0) * ib0, mv1 = R(m1) * ib1, mv2 = R(m2) * ib2;
         const R msq = mv0 * mv0 + mv1 * mv1 + mv2 * mv2;
         const R BC = b0[i0] * b1[i1] * b2[i2] * cpref * exp(-pi2k2 * msq) / msq;
-        const double Em = 0.5 * (double)BC * ((double)F.x * F.x + (double)F.y * F.y);
+        const double wgt = (half && i0 != 0 && 2 * i0 != K0) ? 2.0 : 1.0;
+        const double Em = 0.5 * wgt * (double)BC * ((double)F.x * F.x + (double)F.y * F.y);
         e_loc += Em;
         if (VIR) {
           const double fac = 2.0 * (1.0 + (double)pi2k2 * msq) / (double)msq;
@@ -564,7 +633,7 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
       k = qdiv(t, nl, inv_nl);
       li = t - k * nl;
     }
-    grid[line_elem(axis, K0, K1, l0 + li, k, inv_K0)] = bufA[li * K + k];
+    grid[line_elem(axis, K0, K1, full_line(li), k, inv_K0)] = bufA[li * K + k];
   }
   if (kind == FFT_FWD_INFL_INV) {
     const double sc = S.recip_scale;

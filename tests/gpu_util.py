@@ -40,10 +40,12 @@ PAIR_VARIANTS = {"list": (1, 1), "cells": (1, 2), "fine": (2, 2)}
 
 
 def gpu_forces(s: synth.System, precision=0, virial=False, pos=None, cell_factor=0,
-               pair_path=0):
+               pair_path=0, tuning=None):
     import torch
     g = lib()
     sysg = g.System(ctx(), g.params_from(s, precision, cell_factor, pair_path), s.q, s.bonds)
+    if tuning is not None:
+        sysg.apply_tuning(tuning)
     dev = torch.device("cuda:0")
     p = torch.tensor(s.pos if pos is None else pos, dtype=torch.float64, device=dev)
     F = torch.zeros(3 * s.n, dtype=torch.int64, device=dev)

@@ -30,6 +30,7 @@ def _small_cases():
         "neutral_only": synth.make_bulk(500, seed_index=55, charged_frac=0.0, K=(8, 8, 8)),
         "ragged_odd_grid": synth.make_bulk(1000, seed_index=56, charged_frac=0.4,
                                            K=(15, 12, 10)),
+        "odd_planes": synth.make_bulk(900, seed_index=57, charged_frac=0.4, K=(10, 9, 15)),
     }
 
 
@@ -130,6 +131,52 @@ def test_forces_fp64(name):
     out = gpu_forces(s, 1)
     ref = oracle.energy_forces(s)
     _check(s, out, ref, FORCE_RTOL_FP64, ENERGY_RTOL_FP64, 1e-10)
+
+
+def _shapes(plane, lpb):
+    return {"pair_split": 3, "pair_threads": 160, "pair_ctas_per_sm": 0, "pair_nelec": 1,
+            "fft_lpb": [lpb] * 3, "fft_plane": plane}
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", ["odd_planes", "ragged_odd_grid", "slab_pc", "poly_bonds"])
+def test_fft_paths(name, prec):
+    """Both FFT schedules at parity with the oracle: x-y plane passes over
+    pairs of real z-planes packed into one complex plane with the z pass on
+    the Hermitian half spectrum (odd K0, K1 and K2 included: an unpaired
+    last plane, no Nyquist column), and per-axis line passes on the full
+    spectrum, at the smallest and largest tiles.  The reciprocal energies and
+    virials of the schedules agree to the precision's rounding."""
+    s = CASES[name]
+    f_tol, e_tol, t_tol = ((FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6) if prec == 0 else
+                           (FORCE_RTOL_FP64, ENERGY_RTOL_FP64, 1e-10))
+    ref = oracle.energy_forces(s)
+    outs = []
+    for plane, lpb in ((True, 4), (True, 64), (False, 4), (False, 64)):
+        out = gpu_forces(s, prec, virial=True, tuning=_shapes(plane, lpb))
+        _check(s, out, ref, f_tol, e_tol, t_tol)
+        outs.append(out)
+    rtol = 1e-5 if prec == 0 else 1e-12
+    for o in outs[1:]:
+        assert o["energy"]["recip"] == pytest.approx(outs[0]["energy"]["recip"], rel=rtol)
+        wv = np.max(np.abs(outs[0]["virial"]))
+        assert np.max(np.abs(o["virial"] - outs[0]["virial"])) <= rtol * wv
+
+
+def test_apply_tuning_rejects_bad_shapes():
+    g = lib()
+    s = synth.make_bulk(300, seed_index=58, charged_frac=0.2, K=(96, 96, 8))
+    sysg = g.System(ctx(), g.params_from(s, 1), s.q)  # FP64 planes of 96 x 96 need 297 KB
+    with pytest.raises(g.GcmeError):
+        sysg.apply_tuning(_shapes(True, 8))
+    for bad in (dict(fft_lpb=[3, 8, 8]), dict(pair_threads=96), dict(pair_split=4),
+                dict(pair_ctas_per_sm=9), dict(pair_threads=128, pair_nelec=2)):
+        t = _shapes(False, 8)
+        t.update(bad)
+        with pytest.raises(g.GcmeError):
+            sysg.apply_tuning(t)
+    sysg.apply_tuning(_shapes(False, 8))
+    sysg.close()
 
 
 def test_virial_fp32_and_fp64():
