@@ -156,11 +156,14 @@ def test_fft_paths(name, prec):
         out = gpu_forces(s, prec, virial=True, tuning=_shapes(plane, lpb))
         _check(s, out, ref, f_tol, e_tol, t_tol)
         outs.append(out)
-    rtol = 1e-5 if prec == 0 else 1e-12
+    # FP64: the spectrum's energy and virial are summed per warp in 2^-32
+    # fixed point, a few hundred adds whose count differs between schedules
+    rtol, atol = (1e-5, 0.0) if prec == 0 else (1e-12, 1e-8)
     for o in outs[1:]:
-        assert o["energy"]["recip"] == pytest.approx(outs[0]["energy"]["recip"], rel=rtol)
+        assert o["energy"]["recip"] == pytest.approx(outs[0]["energy"]["recip"], rel=rtol,
+                                                     abs=atol)
         wv = np.max(np.abs(outs[0]["virial"]))
-        assert np.max(np.abs(o["virial"] - outs[0]["virial"])) <= rtol * wv
+        assert np.max(np.abs(o["virial"] - outs[0]["virial"])) <= rtol * wv + atol
 
 
 def test_apply_tuning_rejects_bad_shapes():
