@@ -607,15 +607,24 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
         const R mv0 = R(m0) * ib0, mv1 = R(m1) * ib1, mv2 = R(m2) * ib2;
         const R msq = mv0 * mv0 + mv1 * mv1 + mv2 * mv2;
         const R BC = b0[i0] * b1[i1] * b2[i2] * cpref * exp(-pi2k2 * msq) / msq;
-        const double wgt = (half && i0 != 0 && 2 * i0 != K0) ? 2.0 : 1.0;
-        const double Em = 0.5 * wgt * (double)BC * ((double)F.x * F.x + (double)F.y * F.y);
-        e_loc += Em;
+        const bool pair = half && i0 != 0 && 2 * i0 != K0;  // stands for its mirror too
+        const double Em = 0.5 * (double)BC * ((double)F.x * F.x + (double)F.y * F.y);
+        e_loc += pair ? 2.0 * Em : Em;
         if (VIR) {
           const double fac = 2.0 * (1.0 + (double)pi2k2 * msq) / (double)msq;
-          const double mv[3] = {mv0, mv1, mv2};
           const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+          const double mv[3] = {mv0, mv1, mv2};
           for (int q = 0; q < 6; ++q)
             v_loc[q] += Em * ((ia[q] == ib[q] ? 1.0 : 0.0) - fac * mv[ia[q]] * mv[ib[q]]);
+          if (pair) {
+            // the mirror's wave vector: every component negated except a
+            // Nyquist one (index K/2 of an even K is its own mirror, and
+            // keeps the sign convention of m)
+            const double mm[3] = {-(double)mv0, 2 * i1 == K1 ? (double)mv1 : -(double)mv1,
+                                  2 * i2 == K2 ? (double)mv2 : -(double)mv2};
+            for (int q = 0; q < 6; ++q)
+              v_loc[q] += Em * ((ia[q] == ib[q] ? 1.0 : 0.0) - fac * mm[ia[q]] * mm[ib[q]]);
+          }
         }
         F.x *= BC;
         F.y *= BC;
