@@ -34,7 +34,11 @@
  *     layout: fx[0..n), fy[n..2n), fz[2n..3n);
  *   - energies are FP64 arrays of GCME_NTERMS entries (index GCME_E_*);
  *     the virial is 9 FP64 values, W_ab = sum_pairs r_ij,a F_ij,b of the
- *     pair, reciprocal and bond terms;
+ *     pair, reciprocal and bond terms; it is the virial of the physical
+ *     forces in the bulk geometry only (the pressure's); the slab geometries
+ *     return these sums without the wall and Yeh-Berkowitz terms (the
+ *     image-charge geometry's reciprocal part halved like its energy), which
+ *     is not a pressure there;
  *   - work is enqueued on the caller's CUDA stream (NULL = legacy default
  *     stream) and ordered with the caller's other work on that stream.
  */

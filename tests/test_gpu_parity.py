@@ -157,9 +157,12 @@ def test_fft_paths(name, prec):
         out = gpu_forces(s, prec, virial=True, tuning=_shapes(plane, lpb))
         _check(s, out, ref, f_tol, e_tol, t_tol)
         # off-diagonal terms of the Nyquist planes (even K) cancel over the
-        # full spectrum: the half spectrum must count each mirror as itself
-        assert np.max(np.abs(out["virial"] - ref["virial"])) <= w_tol * np.max(
-            np.abs(ref["virial"])), (plane, lpb)
+        # full spectrum: the half spectrum must count each mirror as itself.
+        # (The image-charge geometry's virial is not the oracle's sum of the
+        # doubled system, see the header; its schedules are compared below.)
+        if s.geometry != synth.GEOM_SLAB_PC:
+            assert np.max(np.abs(out["virial"] - ref["virial"])) <= w_tol * np.max(
+                np.abs(ref["virial"])), (plane, lpb)
         outs.append(out)
     # FP64: the spectrum's energy and virial are summed per warp in 2^-32
     # fixed point, a few hundred adds whose count differs between schedules
