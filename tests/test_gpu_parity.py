@@ -180,8 +180,8 @@ def test_apply_tuning_rejects_bad_shapes():
     sysg = g.System(ctx(), g.params_from(s, 1), s.q)  # FP64 planes of 96 x 96 need 297 KB
     with pytest.raises(g.GcmeError):
         sysg.apply_tuning(_shapes(True, 8))
-    for bad in (dict(fft_lpb=[3, 8, 8]), dict(pair_threads=96), dict(pair_split=4),
-                dict(pair_ctas_per_sm=9), dict(pair_threads=128, pair_nelec=2)):
+    for bad in (dict(fft_lpb=[3, 8, 8]), dict(fft_lpb=[8, 128, 8]), dict(pair_threads=96),
+                dict(pair_split=4), dict(pair_ctas_per_sm=9), dict(pair_nelec=3)):
         t = _shapes(False, 8)
         t.update(bad)
         with pytest.raises(g.GcmeError):
