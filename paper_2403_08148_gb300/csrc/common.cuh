@@ -107,6 +107,11 @@ struct SysDesc {
   int frozen_mask;     // bit t: beads of species t do not move
   int pair_nelec;      // electrostatics warps of a packed pair CTA (1 or 2)
   long long tab_off;   // its ntypes x ntypes block of the pooled pair tables
+  // real-space table (FP32 one-species engines): 2 * rtab_n float4 from
+  // rtab_off of Pool::rtab, interval k of u = r^2 at u * rtab_scale in [k, k+1)
+  long long rtab_off;
+  float rtab_scale;    // rtab_n / fl(rc^2)
+  int rtab_n;
   // real-space kernel constants: small-r Taylor series of
   //   g(r) = [erf(beta r) - erf(kappa r)] / r        = sum_k ser_g[k] r^{2k}
   //   h(r) = -g'(r) / r                               = sum_k ser_h[k] r^{2k}
@@ -165,6 +170,7 @@ struct Pool {
   unsigned long long *qgrid;  // fixed-point charge grid
   float2 *cgrid;              // complex grid (FP32 path)
   double2 *cgrid64;           // complex grid (FP64 path)
+  const float4 *rtab;         // real-space g, h tables (FP32 one species), else null
   float2 *tw;                 // twiddles e^{-2 pi i t/K}
   double2 *tw64;
   float *bsp;                 // |b(m)|^2
@@ -216,6 +222,20 @@ __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
+}
+
+// Real-space pair functions g(r) = [erf(beta r) - erf(kappa r)] / r and
+// h(r) = -g'(r) / r at u = r^2 < rc^2 from the system's cubic table in u
+// (Pool::rtab; 2 float4 per interval: g's then h's coefficients in t).
+__device__ __forceinline__ void real_gh_tab(const Pool &P, const SysDesc &S, float r2, float &g,
+                                            float &h) {
+  const float x = r2 * S.rtab_scale;
+  const int k = min((int)x, S.rtab_n - 1);
+  const float t = x - (float)k;
+  const float4 *tab = P.rtab + S.rtab_off + 2 * k;
+  const float4 a = __ldg(tab), b = __ldg(tab + 1);
+  g = fmaf(t, fmaf(t, fmaf(t, a.w, a.z), a.y), a.x);
+  h = fmaf(t, fmaf(t, fmaf(t, b.w, b.z), b.y), b.x);
 }
 
 __device__ __forceinline__ void atomic_add_fixed(unsigned long long *p, double v, double scale) {

@@ -101,6 +101,67 @@ static void real_series(double b, double k, double g[4], double h[3]) {
   h[2] = c * d7 / 7.0;
 }
 
+// F(w) = erf(sqrt w) / sqrt w and its first two derivatives (an entire
+// function of w): the Taylor series (2/sqrt(pi)) sum (-w)^n / (n! (2n + 1))
+// for w < 2, else the closed form and the relations w F' = e^-w/sqrt(pi) - F/2,
+// w F'' = -e^-w/sqrt(pi) - 3 F'/2 (from d erf(sqrt w)/dw = e^-w / sqrt(pi w)).
+static void erf_ratio(double w, double d[3]) {
+  const double c = 2.0 / std::sqrt(kPi);
+  if (w < 2.0) {
+    // term n of F is t_n / (2n + 1) with t_n = (-w)^n / n!; F' and F''
+    // shift the series: F' = -sum t_n / (2n + 3), F'' = sum t_n / (2n + 5)
+    double f0 = 0.0, f1 = 0.0, f2 = 0.0, t = 1.0;
+    for (int n = 0; n < 40; ++n) {
+      f0 += t / (2 * n + 1);
+      f1 -= t / (2 * n + 3);
+      f2 += t / (2 * n + 5);
+      t *= -w / (n + 1);
+    }
+    d[0] = c * f0;
+    d[1] = c * f1;
+    d[2] = c * f2;
+    return;
+  }
+  const double s = std::sqrt(w), e = std::exp(-w) / std::sqrt(kPi);
+  d[0] = std::erf(s) / s;
+  d[1] = (e - 0.5 * d[0]) / w;
+  d[2] = (-e - 1.5 * d[1]) / w;
+}
+
+// Cubic Hermite table of the real-space pair functions in u = r^2 on
+// [0, umax]: g(u) = [erf(beta r) - erf(kappa r)] / r = beta F(beta^2 u) -
+// kappa F(kappa^2 u) and h(u) = -2 dg/du (= -g'(r) / r), nint intervals;
+// entry 2k holds the coefficients of g on interval k in t = u / du - k
+// (c0 + t (c1 + t (c2 + t c3))), entry 2k + 1 those of h.  Exact values and
+// u-derivatives at the nodes (FP64) make the interpolant C1, with an error
+// below du^4 / 384 times the largest fourth u-derivative (about 1e-9 of
+// g(0) for 512 intervals at rc = 3, far below FP32 rounding).
+static void real_table(double beta, double kappa, double umax, int nint, float4 *out) {
+  auto gh = [&](double u, double v[4]) {  // g, dg/du, h, dh/du
+    double fb[3], fk[3];
+    erf_ratio(beta * beta * u, fb);
+    erf_ratio(kappa * kappa * u, fk);
+    const double b2 = beta * beta, k2 = kappa * kappa;
+    v[0] = beta * fb[0] - kappa * fk[0];
+    v[1] = beta * b2 * fb[1] - kappa * k2 * fk[1];
+    const double g2 = beta * b2 * b2 * fb[2] - kappa * k2 * k2 * fk[2];
+    v[2] = -2.0 * v[1];
+    v[3] = -2.0 * g2;
+  };
+  const double du = umax / nint;
+  double a[4], b[4];
+  gh(0.0, a);
+  for (int k = 0; k < nint; ++k) {
+    gh((k + 1) * du, b);
+    for (int f = 0; f < 2; ++f) {  // f = 0: g, f = 1: h
+      const double y0 = a[2 * f], y1 = b[2 * f], d0 = du * a[2 * f + 1], d1 = du * b[2 * f + 1];
+      out[2 * k + f] = make_float4((float)y0, (float)d0, (float)(3.0 * (y1 - y0) - 2.0 * d0 - d1),
+                                   (float)(2.0 * (y0 - y1) + d0 + d1));
+    }
+    for (int t = 0; t < 4; ++t) a[t] = b[t];
+  }
+}
+
 // One species pair's constants (Eq. u_ex with s = sigma_i^2 + sigma_j^2;
 // real-space term with beta_ij = sqrt(pi) / (sqrt(2) a_ij)).
 static void species_pair(double A, double si, double sj, double ai, double aj, double kappa,
@@ -682,6 +743,19 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
         htype[S.ext_off + S.n + k] = htype[S.ext_off + imgs[s][k]];
     }
   }
+  // real-space tables of the FP32 one-species path (per system: its beta,
+  // kappa and cutoff)
+  std::vector<float4> hrtab;
+  if (!fp64 && !species) {
+    for (auto &S : hsys) {
+      S.rtab_n = kRealTabIntervals;
+      S.rtab_off = (long long)hrtab.size();
+      const double umax = (double)S.rc2f;
+      S.rtab_scale = (float)(kRealTabIntervals / umax);
+      hrtab.resize(hrtab.size() + 2 * kRealTabIntervals);
+      real_table(S.beta, S.kappa, umax, kRealTabIntervals, hrtab.data() + S.rtab_off);
+    }
+  }
   // Neighbour lists: FP32 path, 27-cell stencil, and the two-cell build
   // stencil must cover rc + skin (cells of side >= rc >= skin).
   {
@@ -818,6 +892,8 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   }
   PairTab *d_tab = nullptr;
   PairTab64 *d_tab64 = nullptr;
+  float4 *d_rtab = nullptr;
+  cv.add(&d_rtab, (long long)hrtab.size());
   if (species) {
     cv.add(&P.type_u, ne);
     cv.add(&P.type_s, ne);
@@ -851,6 +927,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   plan.plane_work = d_planes;
   P.ptab = d_tab;
   P.ptab64 = d_tab64;
+  P.rtab = hrtab.empty() ? nullptr : d_rtab;
   if (use_list) {
     P.nbr_stride = list_stride;
     P.gate = P.list_flags;
@@ -924,6 +1001,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   GCME_CK(up(pair_work, pw.data(), sizeof(int2) * n_pair_work));
   for (int a = 0; a < 3; ++a) GCME_CK(up(fw[a], fftw[a].data(), sizeof(int2) * plan.nwork[a]));
   GCME_CK(up(d_planes, planes.data(), sizeof(int2) * plan.nplane));
+  if (!hrtab.empty()) GCME_CK(up(d_rtab, hrtab.data(), sizeof(float4) * hrtab.size()));
   if (species) {
     GCME_CK(up(P.type_u, htype.data(), ne));
     GCME_CK(up(P.type_s, htype.data(), ne));  // overwritten by the first cell sort

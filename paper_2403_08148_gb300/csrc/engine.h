@@ -14,6 +14,7 @@ constexpr int kDefaultCellFactor = 1;
 // work items per home cell of the 27-cell pair kernel (3 or 9)
 constexpr int kDefaultPairSplit = 9;
 constexpr int kDefaultPairThreads = 128;
+constexpr int kRealTabIntervals = 512;           // real-space table intervals in r^2
 constexpr int kMinLpb = 4;                       // fewest FFT lines per tile
 constexpr size_t kFftSmemLimit = 200 * 1024;     // dynamic smem of k_fft
 // Verlet-list skin (bead diameters): the list holds every pair within

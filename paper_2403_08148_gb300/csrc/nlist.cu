@@ -265,7 +265,9 @@ __device__ __forceinline__ void list_range(const Pool &P, const SysDesc &S, cons
     if (ELEC && in) {
       const float qq = xi.w * xj.w;
       float gg, hh;
-      if (r2 < 1e-2f) {
+      if (P.rtab) {
+        real_gh_tab(P, S, r2, gg, hh);
+      } else if (r2 < 1e-2f) {
         gg = S.ser_gf[0] + r2 * (S.ser_gf[1] + r2 * (S.ser_gf[2] + r2 * S.ser_gf[3]));
         hh = S.ser_hf[0] + r2 * (S.ser_hf[1] + r2 * S.ser_hf[2]);
       } else {

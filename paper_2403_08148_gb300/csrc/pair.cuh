@@ -174,7 +174,9 @@ __device__ __forceinline__ void pair_elec(const float4 *__restrict__ J, int t0, 
         betaf = T.beta;
       }
       float g, h;
-      if (r2 < 1e-2f) {
+      if (!MT && P.rtab) {
+        real_gh_tab(P, S, r2, g, h);
+      } else if (r2 < 1e-2f) {
         g = sgf[0] + r2 * (sgf[1] + r2 * (sgf[2] + r2 * sgf[3]));
         h = shf[0] + r2 * (shf[1] + r2 * shf[2]);
       } else {
