@@ -26,11 +26,11 @@ __global__ void __launch_bounds__(256) k_cellsort(Pool P) {
   dev_cellsort_block(P, blockIdx.x, key, cnt2);
 }
 
-void launch_bin(const Pool &P, cudaStream_t st) {
+void launch_bin(const Pool &P, cudaStream_t st, bool zero_counts) {
   if (P.n_ext == 0) return;
   const int tb = 256;
   const int nb = (int)((P.n_ext + tb - 1) / tb);
-  cudaMemsetAsync(P.cell_cnt, 0, sizeof(int) * P.n_cells, st);
+  if (zero_counts) cudaMemsetAsync(P.cell_cnt, 0, sizeof(int) * P.n_cells, st);
   k_bin<<<nb, tb, 0, st>>>(P);
 }
 

@@ -119,6 +119,14 @@ struct SysDesc {
   float ser_gf[4], ser_hf[3];
   float betaf, kappaf;
   float gc_c2f;        // -3/(2 s) log2(e): exponent of the core in base 2
+  // FP32 copies for the FP32 kernels (no FP64 arithmetic per thread)
+  float gc_forcef;     // gc_fc gc_pref
+  float gc_halfpref;   // gc_pref / 2
+  float lbf, lb_half;  // lB, lB / 2
+  float pme_cpref;     // lB / (pi V)
+  float pme_pi2k2;     // pi^2 / kappa^2
+  float inv_box[3];    // 1 / L
+  float recip_scalef;
   // cell decomposition: cells of side >= rc / cell_factor; with factor 2 the
   // pair kernel works on blocks of 2 x 2 x 2 cells (nb blocks per axis)
   int cell_factor;
@@ -243,10 +251,40 @@ __device__ __forceinline__ void atomic_add_fixed(unsigned long long *p, double v
   atomicAdd(p, (unsigned long long)q);
 }
 
-__device__ __forceinline__ void atomic_add_fixed_f(unsigned long long *p, float v, float scale) {
-  long long q = __float2ll_rn(v * scale);
-  atomicAdd(p, (unsigned long long)q);
+// Round-to-nearest-even of v as a 64-bit integer (|v| < 2^63), equal to
+// __float2ll_rn(v) but from 32-bit conversions: the FP64 pipe, which the
+// 64-bit conversions use, is a small fraction of the FP32 rate.  With
+// a = |v| = h 2^32 + r, h = floor(a / 2^32) and r = a - h 2^32 are exact
+// floats (r < 2^32 is a multiple of ulp(a)), so rounding r alone rounds a.
+__device__ __forceinline__ long long f2ll_rn(float v) {
+  const float a = fabsf(v);
+  const float h = floorf(a * 2.3283064365386963e-10f);  // a / 2^32, exact
+  const float r = fmaf(-h, 4294967296.0f, a);           // exact, in [0, 2^32)
+  const long long q =
+      (long long)(((unsigned long long)__float2uint_rn(h) << 32) + __float2uint_rn(r));
+  return v < 0.0f ? -q : q;
 }
+
+// q as a float (within one rounding of the nearest float) from 32-bit
+// conversions: |q| = h 2^32 + l, the high word converted exactly and the low
+// word rounded once (error <= 128 <= 2^-25 |q| when h > 0; exact rounding
+// when h = 0).
+__device__ __forceinline__ float ll2f(long long q) {
+  const unsigned long long a = (unsigned long long)(q < 0 ? -q : q);
+  const float f = fmaf(__uint2float_rn((unsigned)(a >> 32)), 4294967296.0f,
+                       __uint2float_rn((unsigned)(a & 0xffffffffull)));
+  return q < 0 ? -f : f;
+}
+
+__device__ __forceinline__ void atomic_add_fixed_f(unsigned long long *p, float v, float scale) {
+  atomicAdd(p, (unsigned long long)f2ll_rn(v * scale));
+}
+
+// Energy-scale fixed point of one term (2^32 units): terms are rounded
+// before any sum, so sums of them are exact and independent of how the
+// terms are grouped into threads, warps and tiles.
+__device__ __forceinline__ long long efix(float v) { return f2ll_rn(v * 4294967296.0f); }
+__device__ __forceinline__ long long efix(double v) { return __double2ll_rn(v * kEScale); }
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {

@@ -162,6 +162,12 @@ static void real_table(double beta, double kappa, double umax, int nint, float4 
   }
 }
 
+// Box-derived FP32 constants of the reciprocal-space kernels.
+static void box_floats(SysDesc &S) {
+  for (int a = 0; a < 3; ++a) S.inv_box[a] = (float)(1.0 / S.box[a]);
+  S.pme_cpref = (float)(S.lB / (kPi * S.V));
+}
+
 // One species pair's constants (Eq. u_ex with s = sigma_i^2 + sigma_j^2;
 // real-space term with beta_ij = sqrt(pi) / (sqrt(2) a_ij)).
 static void species_pair(double A, double si, double sj, double ai, double aj, double kappa,
@@ -337,9 +343,11 @@ void Engine::release() {
   if (side_stream) cudaStreamDestroy(side_stream);
   if (fork_ev) cudaEventDestroy(fork_ev);
   if (join_ev) cudaEventDestroy(join_ev);
+  if (start_ev) cudaEventDestroy(start_ev);
+  if (zero_ev) cudaEventDestroy(zero_ev);
   if (arena_) cudaFree(arena_);
   capture_stream = side_stream = nullptr;
-  fork_ev = join_ev = nullptr;
+  fork_ev = join_ev = start_ev = zero_ev = nullptr;
   arena_ = nullptr;
   P = Pool{};
   hsys.clear();
@@ -693,6 +701,13 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     for (int t = 0; t < 3; ++t) S.ser_hf[t] = (float)S.ser_h[t];
     S.betaf = (float)S.beta;
     S.kappaf = (float)p.kappa;
+    S.gc_forcef = (float)(S.gc_fc * S.gc_pref);
+    S.gc_halfpref = (float)(0.5 * S.gc_pref);
+    S.lbf = (float)p.lB;
+    S.lb_half = (float)(0.5 * p.lB);
+    S.pme_pi2k2 = (float)(kPi * kPi / (p.kappa * p.kappa));
+    S.recip_scalef = (float)S.recip_scale;
+    box_floats(S);
     {
       double qmax = 0.0;
       for (double z : sp.q) qmax = std::max(qmax, std::fabs(z));
@@ -1034,6 +1049,8 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   }
   GCME_CK(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
   GCME_CK(cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming));
+  GCME_CK(cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming));
+  GCME_CK(cudaEventCreateWithFlags(&zero_ev, cudaEventDisableTiming));
   static std::once_flag once[64];
   std::call_once(once[dev & 63], [] { pme_set_smem_limits(); });
   return GCME_OK;
@@ -1046,11 +1063,11 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
 // the cell sort and fill the SMs the pair kernel leaves idle.  (Forking
 // before binning, with the spread wrapping positions itself, measured
 // slower: the FP64 wraps cost the spread more than the overlap gained.)
-void Engine::fork_pme(const Pool &Q, cudaStream_t st, bool vir, bool timed) {
+void Engine::fork_pme(const Pool &Q, cudaStream_t st, bool vir, bool timed, bool zero_grid) {
   cudaEventRecord(fork_ev, st);
   cudaStreamWaitEvent(side_stream, fork_ev, 0);
   if (timed) cudaEventRecordWithFlags(phase_ev[5], side_stream, cudaEventRecordExternal);
-  launch_pme(Q, plan, fp64, vir, side_stream);
+  launch_pme(Q, plan, fp64, vir, side_stream, zero_grid);
   if (timed) cudaEventRecordWithFlags(phase_ev[6], side_stream, cudaEventRecordExternal);
   cudaEventRecord(join_ev, side_stream);
 }
@@ -1110,13 +1127,22 @@ void Engine::enqueue_forces(const Pool &Q, cudaStream_t st, bool vir, bool dbg) 
 void Engine::enqueue_step(const Pool &Q, cudaStream_t st) {
   const bool ev = phase_ev[0] != nullptr;
   if (ev) cudaEventRecordWithFlags(phase_ev[0], st, cudaEventRecordExternal);
+  // the cell counts and the charge grid are free once the previous step
+  // ended: clear them on the side stream while the half kick and drift run
+  cudaEventRecord(start_ev, st);
+  cudaStreamWaitEvent(side_stream, start_ev, 0);
+  cudaMemsetAsync(Q.cell_cnt, 0, sizeof(int) * Q.n_cells, side_stream);
+  if (Q.n_grid > 0 && Q.qgrid)
+    cudaMemsetAsync(Q.qgrid, 0, sizeof(unsigned long long) * Q.n_grid, side_stream);
+  cudaEventRecord(zero_ev, side_stream);
   launch_kick_drift(Q, fp64, st);
   if (ev) cudaEventRecordWithFlags(phase_ev[1], st, cudaEventRecordExternal);
   cudaMemsetAsync(Q.force, 0, sizeof(long long) * 3 * Q.n_real, st);
   cudaMemsetAsync(Q.acc, 0, sizeof(unsigned long long) * Q.nsys * kNacc, st);
   if (use_list) launch_list_check(Q, st);
-  launch_bin(Q, st);
-  fork_pme(Q, st, false, ev);
+  cudaStreamWaitEvent(st, zero_ev, 0);
+  launch_bin(Q, st, false);
+  fork_pme(Q, st, false, ev, false);
   enqueue_sort_pairs(Q, st, false, false, ev);
   launch_bonded(Q, false, st);
   if (ev) cudaEventRecordWithFlags(phase_ev[4], st, cudaEventRecordExternal);
@@ -1431,6 +1457,7 @@ int gcme_system_set_box(gcme_sys *sys, const double *box, gcme_stream_t stream) 
       S.cside[a] = (float)(box[a] / S.nc[a]);
     }
     S.V = box[0] * box[1] * box[2];
+    box_floats(S);
     GCME_TRY_CK(cudaMemcpy(const_cast<SysDesc *>(E.P.sys), &S, sizeof(SysDesc),
                            cudaMemcpyHostToDevice));
     E.request_rebuild(st);

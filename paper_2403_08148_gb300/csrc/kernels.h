@@ -21,7 +21,9 @@ struct PmePlan {
 };
 
 void launch_cells(const Pool &P, cudaStream_t st);  // launch_bin + launch_sort
-void launch_bin(const Pool &P, cudaStream_t st);    // K1: wrap, cell ids, wrapped float4
+// K1: wrap, cell ids, wrapped float4; zero_counts = false when the cell
+// counts were cleared earlier on another stream
+void launch_bin(const Pool &P, cudaStream_t st, bool zero_counts = true);
 void launch_sort(const Pool &P, cudaStream_t st);   // K2: scan, scatter, per-cell order
 // ctas: grid of the 27-cell kernel (CTAs loop over items fetched from
 // *counter, a device int the launch zeroes first)
@@ -35,7 +37,9 @@ void launch_list_check(const Pool &P, cudaStream_t st);
 void launch_list_build(const Pool &P, cudaStream_t st);
 void launch_list_refresh(const Pool &P, cudaStream_t st);
 void launch_pair_list(const Pool &P, bool vir, bool dbg, cudaStream_t st);
-void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStream_t st);
+// zero_grid = false when the charge grid was cleared earlier on this stream
+void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStream_t st,
+                bool zero_grid = true);
 void pme_set_smem_limits();
 void launch_bonded(const Pool &P, bool vir, cudaStream_t st);   // bonds, walls, dipole
 void launch_slab_apply(const Pool &P, cudaStream_t st);         // Yeh-Berkowitz forces

@@ -319,32 +319,32 @@ __device__ __forceinline__ void pair_segment(const float4 *J, int t0, int t1, in
 template <bool VIR, bool MT = false>
 __device__ __forceinline__ void pair_write(const Pool &P, const SysDesc &S, int s, bool valid,
                                            int i, const PairAcc &A) {
-  const float cg = MT ? 1.0f : (float)(S.gc_fc * S.gc_pref);
-  const float lb = (float)S.lB;
+  // FP32 throughout (the FP64 pipe is a small fraction of the FP32 rate):
+  // per-warp sums of FP32 partials, then 64-bit fixed point
+  const float cg = MT ? 1.0f : S.gc_forcef;
+  const float lb = S.lbf;
   if (valid) {
     const int orig = P.sorted_idx[i];
     atomic_add_fixed_f(force_ptr(P, S, orig, 0), -(cg * A.gx + lb * A.fx), (float)kFScale);
     atomic_add_fixed_f(force_ptr(P, S, orig, 1), -(cg * A.gy + lb * A.fy), (float)kFScale);
     atomic_add_fixed_f(force_ptr(P, S, orig, 2), -(cg * A.gz + lb * A.fz), (float)kFScale);
   }
-  double eg = valid ? (MT ? 0.5 : 0.5 * S.gc_pref) * (double)A.eg : 0.0;
-  double er = valid ? 0.5 * S.lB * (double)A.ere : 0.0;
-  eg = warp_sum(eg);
-  er = warp_sum(er);
+  // each lane's partial in fixed point first, then exact integer sums
+  const long long eg = warp_sum(valid ? efix((MT ? 0.5f : S.gc_halfpref) * A.eg) : 0ll);
+  const long long er = warp_sum(valid ? efix(S.lb_half * A.ere) : 0ll);
   unsigned long long *acc = P.acc + (long long)s * kNacc;
   if ((threadIdx.x & 31) == 0) {
-    if (eg != 0.0) atomic_add_fixed(acc + ACC_GC, eg, kEScale);
-    if (er != 0.0) atomic_add_fixed(acc + ACC_REAL, er, kEScale);
+    if (eg) atomicAdd(acc + ACC_GC, (unsigned long long)eg);
+    if (er) atomicAdd(acc + ACC_REAL, (unsigned long long)er);
   }
   if (VIR) {
     // W_ab = 1/2 sum_visits fs d_a d_b  with fs = (3/s) u or lB qq h
-    const double c1 = MT ? 0.5 : 0.5 * S.gc_fc * S.gc_pref, c2 = 0.5 * S.lB;
+    const float c1 = MT ? 0.5f : 0.5f * S.gc_forcef, c2 = S.lb_half;
     const int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      double v = valid ? c1 * (double)A.wg[map[k]] + c2 * (double)A.we[map[k]] : 0.0;
-      v = warp_sum(v);
-      if ((threadIdx.x & 31) == 0) atomic_add_fixed(P.vacc + (long long)s * 9 + k, v, kEScale);
+      const long long v = warp_sum(valid ? efix(c1 * A.wg[map[k]] + c2 * A.we[map[k]]) : 0ll);
+      if ((threadIdx.x & 31) == 0) atomicAdd(P.vacc + (long long)s * 9 + k, (unsigned long long)v);
     }
   }
 }
@@ -803,31 +803,29 @@ __device__ __forceinline__ void dev_pair_fine_item(const Pool &P, const int2 *wo
         }
       }
     }
-    const float cgf = (float)(S.gc_fc * S.gc_pref);
-    const float lb = (float)S.lB;
+    const float cgf = S.gc_forcef;
+    const float lb = S.lbf;
     if (valid) {
       const int orig = P.sorted_idx[i];
       atomic_add_fixed_f(force_ptr(P, S, orig, 0), -(cgf * A.gx + lb * A.fx), (float)kFScale);
       atomic_add_fixed_f(force_ptr(P, S, orig, 1), -(cgf * A.gy + lb * A.fy), (float)kFScale);
       atomic_add_fixed_f(force_ptr(P, S, orig, 2), -(cgf * A.gz + lb * A.fz), (float)kFScale);
     }
-    double eg = valid ? 0.5 * S.gc_pref * (double)A.eg : 0.0;
-    double er = valid ? 0.5 * S.lB * (double)A.ere : 0.0;
-    eg = warp_sum(eg);
-    er = warp_sum(er);
+    const long long eg = warp_sum(valid ? efix(S.gc_halfpref * A.eg) : 0ll);
+    const long long er = warp_sum(valid ? efix(S.lb_half * A.ere) : 0ll);
     unsigned long long *acc = P.acc + (long long)s * kNacc;
     if (lane == 0) {
-      atomic_add_fixed(acc + ACC_GC, eg, kEScale);
-      atomic_add_fixed(acc + ACC_REAL, er, kEScale);
+      atomicAdd(acc + ACC_GC, (unsigned long long)eg);
+      atomicAdd(acc + ACC_REAL, (unsigned long long)er);
     }
     if (VIR) {
-      const double c1 = 0.5 * S.gc_fc * S.gc_pref, c2 = 0.5 * S.lB;
+      const float c1 = 0.5f * S.gc_forcef, c2 = S.lb_half;
       const int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
-        double vv = valid ? c1 * (double)A.wg[map[k]] + c2 * (double)A.we[map[k]] : 0.0;
-        vv = warp_sum(vv);
-        if (lane == 0) atomic_add_fixed(P.vacc + (long long)s * 9 + k, vv, kEScale);
+        const long long vv =
+            warp_sum(valid ? efix(c1 * A.wg[map[k]] + c2 * A.we[map[k]]) : 0ll);
+        if (lane == 0) atomicAdd(P.vacc + (long long)s * 9 + k, (unsigned long long)vv);
       }
     }
   }

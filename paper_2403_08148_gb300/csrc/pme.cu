@@ -47,9 +47,10 @@ __global__ void __launch_bounds__(256) k_fft(Pool P, const int2 *work, int nwork
     dev_fft_item<R, VIR>(P, work, w, axis, kind, lpb, half, smem_raw);
 }
 
-void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStream_t st) {
+void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStream_t st,
+                bool zero_grid) {
   if (P.n_q == 0 || P.n_grid == 0) return;
-  cudaMemsetAsync(P.qgrid, 0, sizeof(unsigned long long) * P.n_grid, st);
+  if (zero_grid) cudaMemsetAsync(P.qgrid, 0, sizeof(unsigned long long) * P.n_grid, st);
   const int tb = 256;
   const int nb = (int)((P.n_q * 8 + tb - 1) / tb);
   if (fp64) launch_spread_gather<double>(P, pl.order, false, nb, tb, st);

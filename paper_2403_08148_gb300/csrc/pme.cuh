@@ -31,6 +31,18 @@ template <> struct PmeT<double> {
   static constexpr double qscale = kQScale64;
 };
 
+// fixed-point grid value -> R, and R -> nearest fixed-point integer; the
+// FP32 forms use no 64-bit conversion (see f2ll_rn)
+template <typename R> __device__ __forceinline__ R grid_value(long long q);
+template <> __device__ __forceinline__ float grid_value<float>(long long q) {
+  return ll2f(q) * (float)(1.0 / kQScale32);
+}
+template <> __device__ __forceinline__ double grid_value<double>(long long q) {
+  return (double)q * (1.0 / kQScale64);
+}
+__device__ __forceinline__ long long to_fixed(float v) { return f2ll_rn(v); }
+__device__ __forceinline__ long long to_fixed(double v) { return (long long)llrint(v); }
+
 template <typename R>
 __device__ __forceinline__ void load_pos(const Pool &P, long long g, R x[3], R &q);
 template <>
@@ -133,7 +145,7 @@ __device__ __forceinline__ void dev_spread(const Pool &P, long long g) {
 #pragma unroll
     for (int tx = 0; tx < p; ++tx) {
       const int kx = wrap_index(base[0] - tx, K0);
-      long long v = (long long)llrint(W[0][tx] * wyz);
+      const long long v = to_fixed(W[0][tx] * wyz);
       atomicAdd(row + kx, (unsigned long long)v);
     }
   }
@@ -210,9 +222,15 @@ __device__ __forceinline__ void dev_gather(const Pool &P, long long g) {
     gz += __shfl_xor_sync(0xffffffffu, gz, o);
   }
   if (act && tz == 0) {
-    atomic_add_fixed(force_ptr(P, S, e, 0), (double)(-q * gx), kFScale);
-    atomic_add_fixed(force_ptr(P, S, e, 1), (double)(-q * gy), kFScale);
-    atomic_add_fixed(force_ptr(P, S, e, 2), (double)(-q * gz), kFScale);
+    if (sizeof(R) == 4) {
+      atomic_add_fixed_f(force_ptr(P, S, e, 0), (float)(-q * gx), (float)kFScale);
+      atomic_add_fixed_f(force_ptr(P, S, e, 1), (float)(-q * gy), (float)kFScale);
+      atomic_add_fixed_f(force_ptr(P, S, e, 2), (float)(-q * gz), (float)kFScale);
+    } else {
+      atomic_add_fixed(force_ptr(P, S, e, 0), (double)(-q * gx), kFScale);
+      atomic_add_fixed(force_ptr(P, S, e, 1), (double)(-q * gy), kFScale);
+      atomic_add_fixed(force_ptr(P, S, e, 2), (double)(-q * gz), kFScale);
+    }
   }
 }
 
@@ -439,8 +457,8 @@ __device__ __forceinline__ void dev_fft_plane(const Pool &P, const int2 *work, i
       v.x = X.x - Y.y;  // X + i Y
       v.y = X.y + Y.x;
     } else {
-      v.x = (R)((double)(long long)P.qgrid[base0 + t] * (1.0 / PmeT<R>::qscale));
-      v.y = two ? (R)((double)(long long)P.qgrid[base1 + t] * (1.0 / PmeT<R>::qscale)) : R(0);
+      v.x = grid_value<R>((long long)P.qgrid[base0 + t]);
+      v.y = two ? grid_value<R>((long long)P.qgrid[base1 + t]) : R(0);
     }
     A[t] = v;
   }
@@ -534,7 +552,7 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
     R2 v;
     if (kind == FFT_FWD_FROM_Q) {
       const long long qv = (long long)P.qgrid[S.grid_off + gi];
-      v.x = (R)((double)qv * (1.0 / PmeT<R>::qscale));
+      v.x = grid_value<R>(qv);
       v.y = R(0);
     } else {
       v = grid[gi];
@@ -545,8 +563,14 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
   const R2 *tw = tws;
   // one or two passes of stages (forward, then backward for the fused z pass)
   const int npass = (kind == FFT_FWD_INFL_INV) ? 2 : 1;
-  double e_loc = 0.0;
-  double v_loc[6] = {0, 0, 0, 0, 0, 0};
+  // spectrum energy and virial: every mode's term in fixed point, summed as
+  // integers (no FP64 arithmetic in FP32 kernels, and sums independent of
+  // the tiling)
+  R sc;
+  if constexpr (sizeof(R) == 4) sc = S.recip_scalef;
+  else sc = S.recip_scale;
+  long long e_loc = 0;
+  long long v_loc[6] = {0, 0, 0, 0, 0, 0};
   for (int pass = 0; pass < npass; ++pass) {
     const int sgn = (kind == FFT_INV || pass == 1) ? +1 : -1;
     int Ns = 1;
@@ -589,9 +613,20 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
                     S.bsp_off[1];
       const R *b2 = (const R *)(sizeof(R) == 4 ? (const void *)P.bsp : (const void *)P.bsp64) +
                     S.bsp_off[2];
-      const R pi2k2 = R(9.8696044010893586188 / (S.kappa * S.kappa));
-      const R cpref = R(S.lB / (3.14159265358979323846 * S.V));
-      const R ib0 = R(1.0 / S.box[0]), ib1 = R(1.0 / S.box[1]), ib2 = R(1.0 / S.box[2]);
+      R pi2k2, cpref, ib0, ib1, ib2;
+      if constexpr (sizeof(R) == 4) {
+        pi2k2 = S.pme_pi2k2;
+        cpref = S.pme_cpref;
+        ib0 = S.inv_box[0];
+        ib1 = S.inv_box[1];
+        ib2 = S.inv_box[2];
+      } else {
+        pi2k2 = R(9.8696044010893586188 / (S.kappa * S.kappa));
+        cpref = R(S.lB / (3.14159265358979323846 * S.V));
+        ib0 = R(1.0 / S.box[0]);
+        ib1 = R(1.0 / S.box[1]);
+        ib2 = R(1.0 / S.box[2]);
+      }
       for (int t = tid; t < nl * K; t += nt) {
         const int li = qdiv(t, K, inv_K), k = t - li * K;
         const int l = full_line(li);
@@ -608,22 +643,21 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
         const R msq = mv0 * mv0 + mv1 * mv1 + mv2 * mv2;
         const R BC = b0[i0] * b1[i1] * b2[i2] * cpref * exp(-pi2k2 * msq) / msq;
         const bool pair = half && i0 != 0 && 2 * i0 != K0;  // stands for its mirror too
-        const double Em = 0.5 * (double)BC * ((double)F.x * F.x + (double)F.y * F.y);
-        e_loc += pair ? 2.0 * Em : Em;
+        const R Em = R(0.5) * sc * BC * (F.x * F.x + F.y * F.y);
+        e_loc += efix(pair ? R(2) * Em : Em);
         if (VIR) {
-          const double fac = 2.0 * (1.0 + (double)pi2k2 * msq) / (double)msq;
+          const R fac = R(2) * (R(1) + pi2k2 * msq) / msq;
           const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
-          const double mv[3] = {mv0, mv1, mv2};
-          for (int q = 0; q < 6; ++q)
-            v_loc[q] += Em * ((ia[q] == ib[q] ? 1.0 : 0.0) - fac * mv[ia[q]] * mv[ib[q]]);
-          if (pair) {
-            // the mirror's wave vector: every component negated except a
-            // Nyquist one (index K/2 of an even K is its own mirror, and
-            // keeps the sign convention of m)
-            const double mm[3] = {-(double)mv0, 2 * i1 == K1 ? (double)mv1 : -(double)mv1,
-                                  2 * i2 == K2 ? (double)mv2 : -(double)mv2};
-            for (int q = 0; q < 6; ++q)
-              v_loc[q] += Em * ((ia[q] == ib[q] ? 1.0 : 0.0) - fac * mm[ia[q]] * mm[ib[q]]);
+          const R mv[3] = {mv0, mv1, mv2};
+          // the mirror's wave vector: every component negated except a
+          // Nyquist one (index K/2 of an even K is its own mirror, and keeps
+          // the sign convention of m)
+          const R mm[3] = {-mv0, 2 * i1 == K1 ? mv1 : -mv1, 2 * i2 == K2 ? mv2 : -mv2};
+          for (int q = 0; q < 6; ++q) {
+            const R d = ia[q] == ib[q] ? R(1) : R(0);
+            R w = Em * (d - fac * mv[ia[q]] * mv[ib[q]]);
+            if (pair) w += Em * (d - fac * mm[ia[q]] * mm[ib[q]]);
+            v_loc[q] += efix(w);
           }
         }
         F.x *= BC;
@@ -645,14 +679,14 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
     grid[line_elem(axis, K0, K1, full_line(li), k, inv_K0)] = bufA[li * K + k];
   }
   if (kind == FFT_FWD_INFL_INV) {
-    const double sc = S.recip_scale;
-    double ev = warp_sum(e_loc * sc);
-    if ((tid & 31) == 0) atomic_add_fixed(P.acc + (long long)s * kNacc + ACC_RECIP, ev, kEScale);
+    const long long ev = warp_sum(e_loc);
+    if ((tid & 31) == 0 && ev)
+      atomicAdd(P.acc + (long long)s * kNacc + ACC_RECIP, (unsigned long long)ev);
     if (VIR) {
       const int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
       for (int q = 0; q < 9; ++q) {
-        double vv = warp_sum(v_loc[map[q]] * sc);
-        if ((tid & 31) == 0) atomic_add_fixed(P.vacc + (long long)s * 9 + q, vv, kEScale);
+        const long long vv = warp_sum(v_loc[map[q]]);
+        if ((tid & 31) == 0 && vv) atomicAdd(P.vacc + (long long)s * 9 + q, (unsigned long long)vv);
       }
     }
   }
