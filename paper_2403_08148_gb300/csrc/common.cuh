@@ -127,6 +127,8 @@ struct SysDesc {
   float pme_pi2k2;     // pi^2 / kappa^2
   float inv_box[3];    // 1 / L
   float recip_scalef;
+  float half_dtf;      // dt / 2
+  float bond_kf, bond_r0f;
   // cell decomposition: cells of side >= rc / cell_factor; with factor 2 the
   // pair kernel works on blocks of 2 x 2 x 2 cells (nb blocks per axis)
   int cell_factor;

@@ -707,6 +707,9 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     S.lb_half = (float)(0.5 * p.lB);
     S.pme_pi2k2 = (float)(kPi * kPi / (p.kappa * p.kappa));
     S.recip_scalef = (float)S.recip_scale;
+    S.half_dtf = (float)(0.5 * p.dt);
+    S.bond_kf = (float)p.bond_k;
+    S.bond_r0f = (float)p.bond_r0;
     box_floats(S);
     {
       double qmax = 0.0;

@@ -9,30 +9,33 @@ namespace gcme {
 // Add v to the accumulator `slot` of system s from every lane of a warp.
 // Lanes of one warp may belong to different systems (bead-parallel kernels
 // over a batch): the warp reduces when all lanes agree, else each lane adds.
-__device__ __forceinline__ void sys_acc_add(const Pool &P, int s, bool act, int slot, double v) {
+// Add one fixed-point term per lane (efix units) to system s's accumulator:
+// one integer warp sum when the warp's lanes share a system.
+__device__ __forceinline__ void sys_acc_add(const Pool &P, int s, bool act, int slot,
+                                            long long v) {
   const unsigned full = 0xffffffffu;
   const int s0 = __shfl_sync(full, s, 0);
   const bool same = __all_sync(full, s == s0);
   if (same) {
-    double t = warp_sum(act ? v : 0.0);
-    if ((threadIdx.x & 31) == 0 && s0 >= 0)
-      atomic_add_fixed(P.acc + (long long)s0 * kNacc + slot, t, kEScale);
-  } else if (act && v != 0.0) {
-    atomic_add_fixed(P.acc + (long long)s * kNacc + slot, v, kEScale);
+    const long long t = warp_sum(act ? v : 0ll);
+    if ((threadIdx.x & 31) == 0 && s0 >= 0 && t)
+      atomicAdd(P.acc + (long long)s0 * kNacc + slot, (unsigned long long)t);
+  } else if (act && v) {
+    atomicAdd(P.acc + (long long)s * kNacc + slot, (unsigned long long)v);
   }
 }
 
-__device__ __forceinline__ void sys_vir_add(const Pool &P, int s, bool act, const double W[9]) {
+__device__ __forceinline__ void sys_vir_add(const Pool &P, int s, bool act, const long long W[9]) {
   const unsigned full = 0xffffffffu;
   const int s0 = __shfl_sync(full, s, 0);
   const bool same = __all_sync(full, s == s0);
   for (int k = 0; k < 9; ++k) {
     if (same) {
-      double t = warp_sum(act ? W[k] : 0.0);
-      if ((threadIdx.x & 31) == 0 && s0 >= 0)
-        atomic_add_fixed(P.vacc + (long long)s0 * 9 + k, t, kEScale);
-    } else if (act) {
-      atomic_add_fixed(P.vacc + (long long)s * 9 + k, W[k], kEScale);
+      const long long t = warp_sum(act ? W[k] : 0ll);
+      if ((threadIdx.x & 31) == 0 && s0 >= 0 && t)
+        atomicAdd(P.vacc + (long long)s0 * 9 + k, (unsigned long long)t);
+    } else if (act && W[k]) {
+      atomicAdd(P.vacc + (long long)s * 9 + k, (unsigned long long)W[k]);
     }
   }
 }
@@ -44,8 +47,8 @@ template <bool VIR>
 __device__ __forceinline__ void dev_bonds(const Pool &P, long long b) {
   const bool act = b < P.n_bond;
   int s = -1;
-  double E = 0.0;
-  double W[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  long long E = 0;
+  long long W[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (act) {
     s = P.bond_sys[b];
     const SysDesc &S = P.sys[s];
@@ -53,35 +56,41 @@ __device__ __forceinline__ void dev_bonds(const Pool &P, long long b) {
     const double *pi = P.pos + 3 * (S.bead_off + ij.x);
     const double *pj = P.pos + 3 * (S.bead_off + ij.y);
     const bool per[3] = {true, true, S.geometry == GCME_BULK};
-    double d[3];
-    double fs;
     if (S.precision == GCME_FP64) {
+      double d[3];
       for (int a = 0; a < 3; ++a) {
         d[a] = pj[a] - pi[a];
         if (per[a]) d[a] -= S.box[a] * rint(d[a] / S.box[a]);
       }
       const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-      fs = S.bond_k * (r - S.bond_r0) / r;
-      E = 0.5 * S.bond_k * (r - S.bond_r0) * (r - S.bond_r0);
-    } else {
-      float df[3];
+      const double fs = S.bond_k * (r - S.bond_r0) / r;
+      E = efix(0.5 * S.bond_k * (r - S.bond_r0) * (r - S.bond_r0));
       for (int a = 0; a < 3; ++a) {
-        df[a] = (float)(pj[a] - pi[a]);
-        if (per[a]) df[a] -= S.boxf[a] * rintf(df[a] / S.boxf[a]);
-        d[a] = df[a];
+        atomic_add_fixed(force_ptr(P, S, ij.x, a), fs * d[a], kFScale);
+        atomic_add_fixed(force_ptr(P, S, ij.y, a), -fs * d[a], kFScale);
       }
-      const float r = sqrtf(df[0] * df[0] + df[1] * df[1] + df[2] * df[2]);
-      const float kf = (float)S.bond_k, r0 = (float)S.bond_r0;
-      fs = (double)(kf * (r - r0) / r);
-      E = (double)(0.5f * kf * (r - r0) * (r - r0));
+      if (VIR)
+        for (int a = 0; a < 3; ++a)
+          for (int c = 0; c < 3; ++c) W[3 * a + c] = efix(-fs * d[a] * d[c]);
+    } else {
+      // FP32 arithmetic on the FP64 difference
+      float d[3];
+      for (int a = 0; a < 3; ++a) {
+        d[a] = (float)(pj[a] - pi[a]);
+        if (per[a]) d[a] -= S.boxf[a] * rintf(d[a] / S.boxf[a]);
+      }
+      const float r = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      const float kf = S.bond_kf, r0 = S.bond_r0f;
+      const float fs = kf * (r - r0) / r;
+      E = efix(0.5f * kf * (r - r0) * (r - r0));
+      for (int a = 0; a < 3; ++a) {
+        atomic_add_fixed_f(force_ptr(P, S, ij.x, a), fs * d[a], (float)kFScale);
+        atomic_add_fixed_f(force_ptr(P, S, ij.y, a), -fs * d[a], (float)kFScale);
+      }
+      if (VIR)
+        for (int a = 0; a < 3; ++a)
+          for (int c = 0; c < 3; ++c) W[3 * a + c] = efix(-fs * d[a] * d[c]);
     }
-    for (int a = 0; a < 3; ++a) {
-      atomic_add_fixed(force_ptr(P, S, ij.x, a), fs * d[a], kFScale);
-      atomic_add_fixed(force_ptr(P, S, ij.y, a), -fs * d[a], kFScale);
-    }
-    if (VIR)
-      for (int a = 0; a < 3; ++a)
-        for (int c = 0; c < 3; ++c) W[3 * a + c] = -fs * d[a] * d[c];
   }
   sys_acc_add(P, s, act, ACC_BOND, E);
   if (VIR) sys_vir_add(P, s, act, W);
@@ -93,7 +102,7 @@ __device__ __forceinline__ void dev_bonds(const Pool &P, long long b) {
 __device__ __forceinline__ void dev_walls(const Pool &P, long long g) {
   bool act = g < P.n_real;
   int s = -1;
-  double Ew = 0.0, Mz = 0.0;
+  long long Ew = 0, Mz = 0;
   bool slab = false, nm = false;
   if (act) {
     s = P.real_sys[g];
@@ -109,19 +118,19 @@ __device__ __forceinline__ void dev_walls(const Pool &P, long long g) {
         if (S.precision == GCME_FP64) {
           const double u0 = c * exp(-1.5 * z * z / S.wall_s2);
           const double u1 = c * exp(-1.5 * h1 * h1 / S.wall_s2);
-          Ew = u0 + u1;
+          Ew = efix(u0 + u1);
           const double fz = 3.0 * z / S.wall_s2 * u0 - 3.0 * h1 / S.wall_s2 * u1;
           atomic_add_fixed(force_ptr(P, S, i, 2), fz, kFScale);
         } else {
           const float zf = (float)z, h1f = (float)h1, s2 = (float)S.wall_s2, cf = (float)c;
           const float u0 = cf * expf(-1.5f * zf * zf / s2);
           const float u1 = cf * expf(-1.5f * h1f * h1f / s2);
-          Ew = (double)(u0 + u1);
+          Ew = efix(u0 + u1);
           const float fz = 3.0f * zf / s2 * u0 - 3.0f * h1f / s2 * u1;
           atomic_add_fixed_f(force_ptr(P, S, i, 2), fz, (float)kFScale);
         }
       }
-      if (nm) Mz = P.q[g] * z;
+      if (nm) Mz = efix(P.q[g] * z);
     }
   }
   sys_acc_add(P, s, act && slab, ACC_WALL, Ew);
@@ -224,6 +233,15 @@ __device__ __forceinline__ void langevin_noise(unsigned long long seed, unsigned
   }
 }
 
+// Fixed-point force component as V (FP32: no 64-bit conversion).
+template <typename V> __device__ __forceinline__ V force_value(long long fq);
+template <> __device__ __forceinline__ float force_value<float>(long long fq) {
+  return ll2f(fq) * (float)(1.0 / kFScale);
+}
+template <> __device__ __forceinline__ double force_value<double>(long long fq) {
+  return (double)fq * (1.0 / kFScale);
+}
+
 // First half of a step, unit masses, FP64 positions.
 //   velocity Verlet:  v += dt/2 F;  x += dt v.
 //   Langevin (BAOAB): v += dt/2 F;  x += dt/2 v;  v = c1 v + c2 z;  x += dt/2 v
@@ -241,7 +259,9 @@ __device__ __forceinline__ void dev_kick_drift(const Pool &P, long long g) {
   V *vel = reinterpret_cast<V *>(P.vel) + 3 * g;
   const int i = (int)(g - S.bead_off);
   if (frozen_bead(P, S, i)) return;
-  const V h = V(0.5 * S.dt);
+  V h;
+  if constexpr (sizeof(V) == 4) h = S.half_dtf;
+  else h = 0.5 * S.dt;
   if (S.langevin) {
     V z[3];
     langevin_noise<V>(S.seed, P.step_ctr[s], (unsigned long long)i, z);
@@ -249,8 +269,7 @@ __device__ __forceinline__ void dev_kick_drift(const Pool &P, long long g) {
     const double hd = 0.5 * S.dt;
     for (int a = 0; a < 3; ++a) {
       const long long fq = *reinterpret_cast<const long long *>(force_ptr(P, S, i, a));
-      const V f = V((double)fq * (1.0 / kFScale));
-      V v = vel[a] + h * f;
+      V v = vel[a] + h * force_value<V>(fq);
       double x = P.pos[3 * g + a] + hd * (double)v;
       v = c1 * v + c2 * z[a];
       vel[a] = v;
@@ -260,8 +279,7 @@ __device__ __forceinline__ void dev_kick_drift(const Pool &P, long long g) {
   }
   for (int a = 0; a < 3; ++a) {
     const long long fq = *reinterpret_cast<const long long *>(force_ptr(P, S, i, a));
-    const V f = V((double)fq * (1.0 / kFScale));
-    V v = vel[a] + h * f;
+    V v = vel[a] + h * force_value<V>(fq);
     vel[a] = v;
     P.pos[3 * g + a] += S.dt * (double)v;
   }
@@ -271,21 +289,24 @@ template <typename V>
 __device__ __forceinline__ void dev_kick(const Pool &P, long long g) {
   const bool act = g < P.n_real;
   int s = -1;
-  double ke = 0.0;
+  long long ke = 0;
   if (act) {
     s = P.real_sys[g];
     const SysDesc &S = P.sys[s];
     V *vel = reinterpret_cast<V *>(P.vel) + 3 * g;
     const int i = (int)(g - S.bead_off);
-    const V h = V(0.5 * S.dt);
+    V h;
+    if constexpr (sizeof(V) == 4) h = S.half_dtf;
+    else h = 0.5 * S.dt;
     const bool frozen = frozen_bead(P, S, i);
+    V v2 = V(0);
     for (int a = 0; a < 3 && !frozen; ++a) {
       const long long fq = *reinterpret_cast<const long long *>(force_ptr(P, S, i, a));
-      const V f = V((double)fq * (1.0 / kFScale));
-      V v = vel[a] + h * f;
+      V v = vel[a] + h * force_value<V>(fq);
       vel[a] = v;
-      ke += 0.5 * (double)v * (double)v;
+      v2 += v * v;
     }
+    ke = efix(V(0.5) * v2);
     // the step is complete: advance the system's step counter (read by the
     // kick-drift kernel of the next step)
     if (i == 0 && P.step_ctr) P.step_ctr[s] += 1;

@@ -323,6 +323,40 @@ __device__ __forceinline__ void dft_small(R2 *v, int Rd, int sgn) {
   }
 }
 
+// One radix-RD butterfly of a Stockham stage: inputs in[r * is], r < RD,
+// times the twiddles w^(k r) (w = tw[twstep], conjugated for sgn > 0), a
+// length-RD DFT, outputs out[q * os].  RD is a compile-time constant so the
+// values stay in registers.
+template <typename R, typename R2, int RD>
+__device__ __forceinline__ void butterfly(const R2 *in, int is, R2 *out, int os, const R2 *tw,
+                                          int k, int twstep, int sgn) {
+  R2 v[RD];
+#pragma unroll
+  for (int r = 0; r < RD; ++r) {
+    R2 x = in[r * is];
+    if (r > 0 && k > 0) {
+      R2 wv = tw[k * r * twstep];  // k r twstep < K: no wrap needed
+      if (sgn > 0) wv.y = -wv.y;
+      x = cmul(x, wv);
+    }
+    v[r] = x;
+  }
+  dft_small<R, R2>(v, RD, sgn);
+#pragma unroll
+  for (int q = 0; q < RD; ++q) out[q * os] = v[q];
+}
+
+template <typename R, typename R2>
+__device__ __forceinline__ void butterfly_rd(int Rd, const R2 *in, int is, R2 *out, int os,
+                                             const R2 *tw, int k, int twstep, int sgn) {
+  switch (Rd) {
+    case 4: butterfly<R, R2, 4>(in, is, out, os, tw, k, twstep, sgn); break;
+    case 2: butterfly<R, R2, 2>(in, is, out, os, tw, k, twstep, sgn); break;
+    case 3: butterfly<R, R2, 3>(in, is, out, os, tw, k, twstep, sgn); break;
+    default: butterfly<R, R2, 5>(in, is, out, os, tw, k, twstep, sgn); break;
+  }
+}
+
 // Quotient a / d for 0 <= a < 2^22 and 1 <= d <= 2^12, from the FP32
 // product a * inv (inv = 1/d rounded): its error is below one unit for these
 // ranges, so one correction step gives the exact quotient.  Replaces integer
@@ -376,21 +410,9 @@ __device__ __forceinline__ R2 *smem_fft(R2 *A, R2 *B, int nl, int K, int ls, int
       }
       const int jq = qdiv(j, Ns, inv_Ns);
       const int k = j - jq * Ns;
-      R2 v[5];
-      const R2 *in = A + li * ls;
-      for (int r = 0; r < Rd; ++r) {
-        R2 x = in[(j + r * T) * es];
-        if (r > 0 && k > 0) {
-          R2 wv = tw[k * r * twstep];  // k r twstep < K: no wrap needed
-          if (sgn > 0) wv.y = -wv.y;
-          x = cmul(x, wv);
-        }
-        v[r] = x;
-      }
-      dft_small<R, R2>(v, Rd, sgn);
-      R2 *out = B + li * ls;
       const int od = jq * Ns * Rd + k;
-      for (int q = 0; q < Rd; ++q) out[(od + q * Ns) * es] = v[q];
+      butterfly_rd<R, R2>(Rd, A + li * ls + j * es, T * es, B + li * ls + od * es, Ns * es, tw, k,
+                          twstep, sgn);
     }
     __syncthreads();
     R2 *tmp = A;
@@ -436,31 +458,49 @@ __device__ __forceinline__ void dev_fft_plane(const Pool &P, const int2 *work, i
   R2 *tw0 = smem + 2 * G2, *tw1 = tw0 + K0;
   for (int t = threadIdx.x; t < K0; t += blockDim.x) tw0[t] = tw_all[S.tw_off[0] + t];
   for (int t = threadIdx.x; t < K1; t += blockDim.x) tw1[t] = tw_all[S.tw_off[1] + t];
-  for (int t = threadIdx.x; t < G2; t += blockDim.x) {
-    R2 v;
-    if (INV) {
-      const int i1 = qdiv(t, K0, inv_K0), i0 = t - i1 * K0;
-      R2 X, Y;
-      Y.x = Y.y = R(0);
-      if (i0 < H0) {
-        X = cg_all[base0 + t];
-        if (two) Y = cg_all[base1 + t];
-      } else {  // mirror of the stored half, conjugated
-        const int m = (K0 - i0) + K0 * (i1 == 0 ? 0 : K1 - i1);
-        X = cg_all[base0 + m];
-        X.y = -X.y;
-        if (two) {
-          Y = cg_all[base1 + m];
-          Y.y = -Y.y;
-        }
+  // kPlaneLoads elements per thread in flight: their global loads are
+  // issued together, then converted and stored to shared memory
+  constexpr int kPlaneLoads = 4;
+  for (int t0 = threadIdx.x; t0 < G2; t0 += kPlaneLoads * blockDim.x) {
+    R2 X[kPlaneLoads], Y[kPlaneLoads];
+    long long qa[kPlaneLoads], qb[kPlaneLoads];
+#pragma unroll
+    for (int u = 0; u < kPlaneLoads; ++u) {
+      const int t = t0 + u * blockDim.x;
+      if (t >= G2) break;
+      if (INV) {
+        const int i1 = qdiv(t, K0, inv_K0), i0 = t - i1 * K0;
+        // stored half, or the conjugate of its mirror
+        const int m = i0 < H0 ? t : (K0 - i0) + K0 * (i1 == 0 ? 0 : K1 - i1);
+        X[u] = cg_all[base0 + m];
+        if (two) Y[u] = cg_all[base1 + m];
+      } else {
+        qa[u] = (long long)P.qgrid[base0 + t];
+        qb[u] = two ? (long long)P.qgrid[base1 + t] : 0ll;
       }
-      v.x = X.x - Y.y;  // X + i Y
-      v.y = X.y + Y.x;
-    } else {
-      v.x = grid_value<R>((long long)P.qgrid[base0 + t]);
-      v.y = two ? grid_value<R>((long long)P.qgrid[base1 + t]) : R(0);
     }
-    A[t] = v;
+#pragma unroll
+    for (int u = 0; u < kPlaneLoads; ++u) {
+      const int t = t0 + u * blockDim.x;
+      if (t >= G2) break;
+      R2 v;
+      if (INV) {
+        const int i0 = t - qdiv(t, K0, inv_K0) * K0;
+        R2 x = X[u], y;
+        if (two) y = Y[u];
+        else y.x = y.y = R(0);
+        if (i0 >= H0) {
+          x.y = -x.y;
+          y.y = -y.y;
+        }
+        v.x = x.x - y.y;  // X + i Y
+        v.y = x.y + y.x;
+      } else {
+        v.x = grid_value<R>(qa[u]);
+        v.y = two ? grid_value<R>(qb[u]) : R(0);
+      }
+      A[t] = v;
+    }
   }
   __syncthreads();
   const int sgn = INV ? +1 : -1;
@@ -538,26 +578,38 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
   R2 *bufA = smem, *bufB = smem + lpb * K;
   R2 *tws = smem + 2 * lpb * K;
   for (int t = tid; t < K; t += nt) tws[t] = tw_all[S.tw_off[axis] + t];
-  // ---- load (line index fastest for strided axes: coalesced along x)
-  for (int t = tid; t < nl * K; t += nt) {
-    int li, k;
-    if (axis == 0) {
-      li = qdiv(t, K, inv_K);
-      k = t - li * K;
-    } else {
-      k = qdiv(t, nl, inv_nl);
-      li = t - k * nl;
+  // ---- load (line index fastest for strided axes: coalesced along x);
+  // kItemLoads elements per thread in flight, then stored to shared memory
+  constexpr int kItemLoads = 4;
+  for (int t0 = tid; t0 < nl * K; t0 += kItemLoads * nt) {
+    R2 v[kItemLoads];
+    int dst[kItemLoads];
+#pragma unroll
+    for (int u = 0; u < kItemLoads; ++u) {
+      const int t = t0 + u * nt;
+      if (t >= nl * K) break;
+      int li, k;
+      if (axis == 0) {
+        li = qdiv(t, K, inv_K);
+        k = t - li * K;
+      } else {
+        k = qdiv(t, nl, inv_nl);
+        li = t - k * nl;
+      }
+      dst[u] = li * K + k;
+      const long long gi = line_elem(axis, K0, K1, full_line(li), k, inv_K0);
+      if (kind == FFT_FWD_FROM_Q) {
+        v[u].x = grid_value<R>((long long)P.qgrid[S.grid_off + gi]);
+        v[u].y = R(0);
+      } else {
+        v[u] = grid[gi];
+      }
     }
-    const long long gi = line_elem(axis, K0, K1, full_line(li), k, inv_K0);
-    R2 v;
-    if (kind == FFT_FWD_FROM_Q) {
-      const long long qv = (long long)P.qgrid[S.grid_off + gi];
-      v.x = grid_value<R>(qv);
-      v.y = R(0);
-    } else {
-      v = grid[gi];
+#pragma unroll
+    for (int u = 0; u < kItemLoads; ++u) {
+      if (t0 + u * nt >= nl * K) break;
+      bufA[dst[u]] = v[u];
     }
-    bufA[li * K + k] = v;
   }
   __syncthreads();
   const R2 *tw = tws;
@@ -583,21 +635,8 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
         const int li = qdiv(t, T, inv_T), j = t - li * T;
         const int jq = qdiv(j, Ns, inv_Ns);
         const int k = j - jq * Ns;
-        R2 v[5];
-        const R2 *in = bufA + li * K;
-        for (int r = 0; r < Rd; ++r) {
-          R2 x = in[j + r * T];
-          if (r > 0 && k > 0) {
-            R2 wv = tw[k * r * twstep];  // k r twstep < K
-            if (sgn > 0) wv.y = -wv.y;
-            x = cmul(x, wv);
-          }
-          v[r] = x;
-        }
-        dft_small<R, R2>(v, Rd, sgn);
-        R2 *out = bufB + li * K;
         const int od = jq * Ns * Rd + k;
-        for (int q = 0; q < Rd; ++q) out[od + q * Ns] = v[q];
+        butterfly_rd<R, R2>(Rd, bufA + li * K + j, T, bufB + li * K + od, Ns, tw, k, twstep, sgn);
       }
       __syncthreads();
       R2 *tmp = bufA;
