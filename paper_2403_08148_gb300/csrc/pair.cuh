@@ -51,6 +51,7 @@ struct PairSeg {
   int self;
   int shifted;
   int qoff;          // packed items: offset of the charged/image beads' float4
+  int nk, bk;        // packed items: real and charged/image beads staged (kept)
 };
 
 // Packed items: the real beads of the staged cells as three coordinate
@@ -617,17 +618,78 @@ __device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *
                                          s_tot);
     return;
   }
-  for (int k = 0; k < nseg; ++k) {
-    const PairSeg &g = seg[k];
-    const int nr = g.n - g.a, n2 = (nr + 1) & ~1;
-    for (int t = tid; t < n2; t += blockDim.x) {
-      const float4 v = t < nr ? P.xyzq_s[g.beg + g.a + t]
-                              : make_float4(1e30f, 1e30f, 1e30f, 0.0f);  // pad: far away
-      sx[g.soff + t] = v.x;
-      sy[g.soff + t] = v.y;
-      sz[g.soff + t] = v.z;
+  // Staging, one warp per segment: only the candidates within rc (+1e-3)
+  // of the home cell's box can be within rc of a home bead, so the others
+  // are dropped here (about 30 % of the 27 cells' beads at cells of side
+  // ~rc), keeping order; the home cell itself is staged whole, in sorted
+  // order (its self-pair test uses the sorted index).
+  {
+    const int nwarp = blockDim.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int hc[3] = {cloc % S.nc[0], (cloc / S.nc[0]) % S.nc[1], cloc / (S.nc[0] * S.nc[1])};
+    float hlo[3], hhi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      hlo[a] = (float)hc[a] * S.cside[a];
+      hhi[a] = hlo[a] + S.cside[a];
     }
-    for (int t = tid; t < g.b; t += blockDim.x) sq[g.qoff + t] = P.xyzq_s[g.beg + t];
+    const float cut2 = S.cull2;
+    const float4 far = make_float4(1e30f, 1e30f, 1e30f, 0.0f);  // pad: far away
+    auto near_home = [&](const float4 &v, const PairSeg &g) {
+      const float e[3] = {v.x + g.sh[0], v.y + g.sh[1], v.z + g.sh[2]};
+      float d2 = 0.0f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float d = fmaxf(0.0f, fmaxf(hlo[a] - e[a], e[a] - hhi[a]));
+        d2 = fmaf(d, d, d2);
+      }
+      return d2 <= cut2;
+    };
+    for (int k = warp; k < nseg; k += nwarp) {
+      PairSeg &g = seg[k];
+      const bool all = g.self;
+      const int nr = g.n - g.a;
+      int kept = 0;
+      for (int t0 = 0; t0 < nr; t0 += 128) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int t = t0 + 32 * u + lane;
+          v[u] = t < nr ? P.xyzq_s[g.beg + g.a + t] : far;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int t = t0 + 32 * u + lane;
+          const bool keep = t < nr && (all || near_home(v[u], g));
+          const unsigned m = __ballot_sync(0xffffffffu, keep);
+          if (keep) {
+            const int p = g.soff + kept + __popc(m & lt);
+            sx[p] = v[u].x;
+            sy[p] = v[u].y;
+            sz[p] = v[u].z;
+          }
+          kept += __popc(m);
+        }
+      }
+      if ((kept & 1) && lane == 0) {
+        sx[g.soff + kept] = far.x;
+        sy[g.soff + kept] = far.y;
+        sz[g.soff + kept] = far.z;
+      }
+      int keptq = 0;
+      for (int t0 = 0; t0 < g.b; t0 += 32) {
+        const int t = t0 + lane;
+        const float4 v = t < g.b ? P.xyzq_s[g.beg + t] : far;
+        const bool keep = t < g.b && (all || near_home(v, g));
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) sq[g.qoff + keptq + __popc(m & lt)] = v;
+        keptq += __popc(m);
+      }
+      if (lane == 0) {
+        g.nk = kept;
+        g.bk = keptq;
+      }
+    }
   }
   __syncthreads();
   const float rc2 = S.rc2f, gcc = S.gc_c2f;
@@ -659,7 +721,7 @@ __device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *
         for (int k = 0; k < 6; ++k) B.wg[k] = make_float2(0.0f, 0.0f);
         for (int k = 0; k < nseg; ++k) {
           const PairSeg g = seg[k];
-          const int n2 = (g.n - g.a + 1) & ~1;
+          const int n2 = (g.nk + 1) & ~1;
           const float *X = sx + g.soff, *Y = sy + g.soff, *Z = sz + g.soff;
           const int j0 = g.beg + g.a;
           if (g.self)
@@ -680,7 +742,7 @@ __device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *
         for (int k = 0; k < nseg; ++k) {
           const PairSeg g = seg[k];
           const float4 *J = sq + g.qoff;
-          const int lo = g.b * ew / nelec, hi = g.b * (ew + 1) / nelec;
+          const int lo = g.bk * ew / nelec, hi = g.bk * (ew + 1) / nelec;
           if (g.self)
             pair_elec<false, true, VIR, false>(J, lo, hi, 0, g.beg, xi, i, g, S, rc2, A, P, s);
           else if (g.shifted)
