@@ -26,6 +26,15 @@ __global__ void __launch_bounds__(256) k_cellsort(Pool P) {
   dev_cellsort_block(P, blockIdx.x, key, cnt2);
 }
 
+__global__ void __launch_bounds__(256) k_cellsort_fused(Pool P) {
+  __shared__ long long key[kSortCap];
+  __shared__ int cnt2[2];
+  __shared__ int red[32];
+  if (blockIdx.x >= P.n_cells) return;
+  if (P.gate && !*P.gate) return;
+  dev_cellsort_fused_block(P, blockIdx.x, key, cnt2, red);
+}
+
 void launch_bin(const Pool &P, cudaStream_t st, bool zero_counts) {
   if (P.n_ext == 0) return;
   const int tb = 256;
@@ -38,6 +47,10 @@ void launch_sort(const Pool &P, cudaStream_t st) {
   if (P.n_ext == 0) return;
   const int tb = 256;
   const int nb = (int)((P.n_ext + tb - 1) / tb);
+  if (P.bucket) {
+    k_cellsort_fused<<<(unsigned)P.n_cells, 256, 0, st>>>(P);
+    return;
+  }
   k_scan<<<1, 1024, 0, st>>>(P.cell_cnt, P.cell_start, P.n_cells, P.gate);
   k_scatter<<<nb, tb, 0, st>>>(P);
   k_cellsort<<<(unsigned)P.n_cells, 256, 0, st>>>(P);

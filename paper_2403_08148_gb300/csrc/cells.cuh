@@ -43,7 +43,10 @@ __device__ __forceinline__ void dev_bin(const Pool &P, long long g) {
     for (int a = 0; a < 3; ++a) P.img_now[3 * g + a] = (int)rint((x[a] - w[a]) / S.box[a]);
   }
   P.cell_of[g] = cell;
-  P.slot[g] = atomicAdd(&P.cell_cnt[S.cell_off + cell], 1);
+  const int slot = atomicAdd(&P.cell_cnt[S.cell_off + cell], 1);
+  P.slot[g] = slot;
+  if (P.bucket && slot < P.bucket_cap)
+    P.bucket[(S.cell_off + cell) * (long long)P.bucket_cap + slot] = e;
 }
 
 // Exclusive scan of the cell counts of all systems by one CTA (any size
@@ -91,14 +94,12 @@ __device__ __forceinline__ void dev_scatter(const Pool &P, long long g) {
   P.sorted_idx[P.cell_start[S.cell_off + P.cell_of[g]] + P.slot[g]] = e;
 }
 
-// One CTA per cell: stable (class, index) order of the cell's beads and the
-// gather of their wrapped positions into sorted order.  key: kSortCap
-// entries of shared memory, cnt2: two shared ints.  Ends with a barrier.
-__device__ __forceinline__ void dev_cellsort_block(const Pool &P, long long cg, long long *key,
-                                                   int *cnt2) {
-  const SysDesc &S = P.sys[P.cell_sys[cg]];
-  int beg = P.cell_start[cg], end = P.cell_start[cg + 1];
-  int cnt = end - beg;
+// One CTA per cell: stable (class, index) order of the cell's beads (sorted
+// slots [beg, beg + cnt), filled in slot order) and the gather of their
+// wrapped positions into sorted order.  key: kSortCap entries of shared
+// memory, cnt2: two shared ints.  Ends with a barrier.
+__device__ __forceinline__ void dev_cellsort_range(const Pool &P, const SysDesc &S, long long cg,
+                                                   int beg, int cnt, long long *key, int *cnt2) {
   if (threadIdx.x == 0) {
     cnt2[0] = 0;
     cnt2[1] = 0;
@@ -158,6 +159,49 @@ __device__ __forceinline__ void dev_cellsort_block(const Pool &P, long long cg, 
     P.cell_nq[cg] = cnt2[1];
   }
   __syncthreads();
+}
+
+__device__ __forceinline__ void dev_cellsort_block(const Pool &P, long long cg, long long *key,
+                                                   int *cnt2) {
+  const SysDesc &S = P.sys[P.cell_sys[cg]];
+  const int beg = P.cell_start[cg];
+  dev_cellsort_range(P, S, cg, beg, P.cell_start[cg + 1] - beg, key, cnt2);
+}
+
+// Scan, scatter and per-cell order in one pass, one CTA per cell (grids of
+// at most kFusedSortCells cells per system): the cell's start is the
+// system's first sorted slot plus the counts of the system's earlier cells
+// (a block sum), its beads come from the bucket written by the binning
+// (or, for a cell holding more than bucket_cap beads, from a search of the
+// system's beads), and the stable (class, index) order follows as in
+// dev_cellsort_range.  red: 32 shared ints.  Ends with a barrier.
+__device__ __forceinline__ void dev_cellsort_fused_block(const Pool &P, long long cg,
+                                                         long long *key, int *cnt2, int *red) {
+  const SysDesc &S = P.sys[P.cell_sys[cg]];
+  int part = 0;
+  for (long long c = S.cell_off + threadIdx.x; c < cg; c += blockDim.x) part += P.cell_cnt[c];
+  part = warp_sum(part);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = part;
+  __syncthreads();
+  int tot = 0;
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += red[k];
+  const int beg = (int)S.ext_off + tot;
+  const int cnt = P.cell_cnt[cg];
+  if (threadIdx.x == 0) {
+    P.cell_start[cg] = beg;
+    if (cg == P.n_cells - 1) P.cell_start[cg + 1] = beg + cnt;
+  }
+  if (cnt <= P.bucket_cap) {
+    const int *b = P.bucket + cg * (long long)P.bucket_cap;
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) P.sorted_idx[beg + t] = b[t];
+  } else {
+    const int cl = (int)(cg - S.cell_off);
+    for (long long g = S.ext_off + threadIdx.x; g < S.ext_off + S.n_ext; g += blockDim.x)
+      if (P.cell_of[g] == cl) P.sorted_idx[beg + P.slot[g]] = (int)(g - S.ext_off);
+  }
+  __syncthreads();
+  dev_cellsort_range(P, S, cg, beg, cnt, key, cnt2);
 }
 
 }  // namespace gcme

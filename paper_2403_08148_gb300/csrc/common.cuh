@@ -176,6 +176,10 @@ struct Pool {
   int *cell_nimg;
   int *cell_nq;
   int *cell_sys;
+  // fused cell sort (small cell grids): bead e of cell c at bucket[c * bucket_cap
+  // + slot] for slot < bucket_cap; null: scan + scatter + sort kernels
+  int *bucket;
+  int bucket_cap;
   // PME
   unsigned long long *qgrid;  // fixed-point charge grid
   float2 *cgrid;              // complex grid (FP32 path)

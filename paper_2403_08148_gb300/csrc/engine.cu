@@ -343,11 +343,9 @@ void Engine::release() {
   if (side_stream) cudaStreamDestroy(side_stream);
   if (fork_ev) cudaEventDestroy(fork_ev);
   if (join_ev) cudaEventDestroy(join_ev);
-  if (start_ev) cudaEventDestroy(start_ev);
-  if (zero_ev) cudaEventDestroy(zero_ev);
   if (arena_) cudaFree(arena_);
   capture_stream = side_stream = nullptr;
-  fork_ev = join_ev = start_ev = zero_ev = nullptr;
+  fork_ev = join_ev = nullptr;
   arena_ = nullptr;
   P = Pool{};
   hsys.clear();
@@ -870,6 +868,21 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   cv.add(&P.img_src, nimg);
   cv.add(&P.cell_cnt, ncell);
   cv.add(&P.cell_start, ncell + 1);
+  // fused cell sort for small per-system grids; bucket capacity twice the
+  // densest expected cell (slabs: the beads fill H of the box height) + 32
+  int bucket_cap = 0;
+  {
+    bool fused = true;
+    double occ = 0.0;
+    for (auto &S : hsys) {
+      fused = fused && S.ncell <= kFusedSortCells;
+      double fill = 1.0;
+      if (S.geometry != GCME_BULK && S.H > 0) fill = std::min(1.0, S.H / S.box[2]);
+      occ = std::max(occ, S.n_ext / (S.ncell * fill));
+    }
+    if (fused) bucket_cap = ((int)std::ceil(2.0 * occ) + 32 + 31) / 32 * 32;
+  }
+  cv.add(&P.bucket, (long long)ncell * bucket_cap);
   cv.add(&P.cell_nimg, ncell);
   cv.add(&P.cell_nq, ncell);
   cv.add(&P.cell_sys, ncell);
@@ -938,6 +951,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   P.n_real = nr;
   P.n_ext = ne;
   P.n_cells = ncell;
+  P.bucket_cap = P.bucket ? bucket_cap : 0;
   P.n_q = nq;
   P.n_bond = nbond;
   P.n_grid = ngrid;
@@ -1031,6 +1045,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     GCME_CK(cudaMemset(P.vel, 0, (fp64 ? 8 : 4) * 3 * nr));
   }
   GCME_CK(cudaMemset(P.force, 0, sizeof(long long) * 3 * nr));
+  if (ngrid > 0) GCME_CK(cudaMemset(P.qgrid, 0, sizeof(unsigned long long) * ngrid));
   GCME_CK(cudaMemset(P.step_ctr, 0, sizeof(unsigned long long) * ns));
   if (use_list) {
     // reference positions ~1e306: the first check requests a build
@@ -1052,8 +1067,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   }
   GCME_CK(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
   GCME_CK(cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming));
-  GCME_CK(cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming));
-  GCME_CK(cudaEventCreateWithFlags(&zero_ev, cudaEventDisableTiming));
+
   static std::once_flag once[64];
   std::call_once(once[dev & 63], [] { pme_set_smem_limits(); });
   return GCME_OK;
@@ -1130,20 +1144,12 @@ void Engine::enqueue_forces(const Pool &Q, cudaStream_t st, bool vir, bool dbg) 
 void Engine::enqueue_step(const Pool &Q, cudaStream_t st) {
   const bool ev = phase_ev[0] != nullptr;
   if (ev) cudaEventRecordWithFlags(phase_ev[0], st, cudaEventRecordExternal);
-  // the cell counts and the charge grid are free once the previous step
-  // ended: clear them on the side stream while the half kick and drift run
-  cudaEventRecord(start_ev, st);
-  cudaStreamWaitEvent(side_stream, start_ev, 0);
-  cudaMemsetAsync(Q.cell_cnt, 0, sizeof(int) * Q.n_cells, side_stream);
-  if (Q.n_grid > 0 && Q.qgrid)
-    cudaMemsetAsync(Q.qgrid, 0, sizeof(unsigned long long) * Q.n_grid, side_stream);
-  cudaEventRecord(zero_ev, side_stream);
+  // no clears on the critical path: the half kick and drift clears the
+  // forces it reads, the energy accumulators and the cell counts, and the
+  // forward FFT pass of every evaluation leaves the charge grid zero
   launch_kick_drift(Q, fp64, st);
   if (ev) cudaEventRecordWithFlags(phase_ev[1], st, cudaEventRecordExternal);
-  cudaMemsetAsync(Q.force, 0, sizeof(long long) * 3 * Q.n_real, st);
-  cudaMemsetAsync(Q.acc, 0, sizeof(unsigned long long) * Q.nsys * kNacc, st);
   if (use_list) launch_list_check(Q, st);
-  cudaStreamWaitEvent(st, zero_ev, 0);
   launch_bin(Q, st, false);
   fork_pme(Q, st, false, ev, false);
   enqueue_sort_pairs(Q, st, false, false, ev);

@@ -59,7 +59,6 @@ class Engine {
   void fork_pme(const Pool &P, cudaStream_t st, bool vir, bool timed, bool zero_grid = true);
   cudaStream_t side_stream = nullptr;  // PME branch
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
-  cudaEvent_t start_ev = nullptr, zero_ev = nullptr;  // early clears on the side stream
 
   // graph of one step for the given state pointers (cached)
   int step_graph(const Pool &P, cudaGraphExec_t *out);

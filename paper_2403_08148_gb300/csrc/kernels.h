@@ -24,7 +24,11 @@ void launch_cells(const Pool &P, cudaStream_t st);  // launch_bin + launch_sort
 // K1: wrap, cell ids, wrapped float4; zero_counts = false when the cell
 // counts were cleared earlier on another stream
 void launch_bin(const Pool &P, cudaStream_t st, bool zero_counts = true);
-void launch_sort(const Pool &P, cudaStream_t st);   // K2: scan, scatter, per-cell order
+// largest per-system cell grid of the fused cell sort (each of its CTAs sums
+// the counts of the system's earlier cells)
+constexpr int kFusedSortCells = 2048;
+// K2: scan, scatter, per-cell order (one fused kernel when P.bucket is set)
+void launch_sort(const Pool &P, cudaStream_t st);
 // ctas: grid of the 27-cell kernel (CTAs loop over items fetched from
 // *counter, a device int the launch zeroes first)
 void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell_factor,
@@ -37,7 +41,8 @@ void launch_list_check(const Pool &P, cudaStream_t st);
 void launch_list_build(const Pool &P, cudaStream_t st);
 void launch_list_refresh(const Pool &P, cudaStream_t st);
 void launch_pair_list(const Pool &P, bool vir, bool dbg, cudaStream_t st);
-// zero_grid = false when the charge grid was cleared earlier on this stream
+// zero_grid = false when the charge grid is known to be zero (the forward FFT
+// pass clears every grid point it reads)
 void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStream_t st,
                 bool zero_grid = true);
 void pme_set_smem_limits();

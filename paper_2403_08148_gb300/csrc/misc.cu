@@ -12,7 +12,14 @@ __global__ void k_slab_apply(Pool P) { dev_slab_apply(P, GCME_TID); }
 template <bool VIR>
 __global__ void k_finalize(Pool P) { dev_finalize<VIR>(P, (int)GCME_TID); }
 template <typename V>
-__global__ void k_kick_drift(Pool P) { dev_kick_drift<V>(P, GCME_TID); }
+__global__ void k_kick_drift(Pool P) {
+  dev_kick_drift<V>(P, GCME_TID);
+  // the step's accumulators and cell counts start from zero (the previous
+  // step has read them)
+  const long long nt = (long long)gridDim.x * blockDim.x;
+  for (long long k = GCME_TID; k < (long long)P.nsys * kNacc; k += nt) P.acc[k] = 0ull;
+  for (long long k = GCME_TID; k < P.n_cells; k += nt) P.cell_cnt[k] = 0;
+}
 template <typename V>
 __global__ void k_kick(Pool P) { dev_kick<V>(P, GCME_TID); }
 #undef GCME_TID

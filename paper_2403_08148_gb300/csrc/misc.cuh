@@ -251,6 +251,8 @@ __device__ __forceinline__ bool frozen_bead(const Pool &P, const SysDesc &S, int
   return S.frozen_mask && ((S.frozen_mask >> P.type_u[S.ext_off + i]) & 1);
 }
 
+// Each bead's force is cleared once read (the step's force evaluation
+// accumulates into it next).
 template <typename V>
 __device__ __forceinline__ void dev_kick_drift(const Pool &P, long long g) {
   if (g >= P.n_real) return;
@@ -258,7 +260,10 @@ __device__ __forceinline__ void dev_kick_drift(const Pool &P, long long g) {
   const SysDesc &S = P.sys[s];
   V *vel = reinterpret_cast<V *>(P.vel) + 3 * g;
   const int i = (int)(g - S.bead_off);
-  if (frozen_bead(P, S, i)) return;
+  if (frozen_bead(P, S, i)) {
+    for (int a = 0; a < 3; ++a) *force_ptr(P, S, i, a) = 0ull;
+    return;
+  }
   V h;
   if constexpr (sizeof(V) == 4) h = S.half_dtf;
   else h = 0.5 * S.dt;
@@ -268,7 +273,9 @@ __device__ __forceinline__ void dev_kick_drift(const Pool &P, long long g) {
     const V c1 = V(S.lgv_c1), c2 = V(S.lgv_c2);
     const double hd = 0.5 * S.dt;
     for (int a = 0; a < 3; ++a) {
-      const long long fq = *reinterpret_cast<const long long *>(force_ptr(P, S, i, a));
+      unsigned long long *fp = force_ptr(P, S, i, a);
+      const long long fq = (long long)*fp;
+      *fp = 0ull;
       V v = vel[a] + h * force_value<V>(fq);
       double x = P.pos[3 * g + a] + hd * (double)v;
       v = c1 * v + c2 * z[a];
@@ -278,7 +285,9 @@ __device__ __forceinline__ void dev_kick_drift(const Pool &P, long long g) {
     return;
   }
   for (int a = 0; a < 3; ++a) {
-    const long long fq = *reinterpret_cast<const long long *>(force_ptr(P, S, i, a));
+    unsigned long long *fp = force_ptr(P, S, i, a);
+    const long long fq = (long long)*fp;
+    *fp = 0ull;
     V v = vel[a] + h * force_value<V>(fq);
     vel[a] = v;
     P.pos[3 * g + a] += S.dt * (double)v;

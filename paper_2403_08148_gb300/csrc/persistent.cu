@@ -77,14 +77,9 @@ __global__ void __launch_bounds__(128) k_persistent(Pool P, PersistArgs A) {
   const long long gthreads = (long long)gridDim.x * blockDim.x;
   const long long gtid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   for (long long step = 0; step < A.nsteps; ++step) {
-    // ---- half kick + drift; clear accumulators, cell counts, charge grid
-    // (each thread clears the forces it has just read)
-    for (long long g = gtid; g < P.n_real; g += gthreads) {
-      dev_kick_drift<float>(P, g);
-      const SysDesc &S = P.sys[P.real_sys[g]];
-      const int i = (int)(g - S.bead_off);
-      for (int a = 0; a < 3; ++a) *force_ptr(P, S, i, a) = 0ull;
-    }
+    // ---- half kick + drift (which clears the forces it has read); clear
+    // accumulators, cell counts, charge grid
+    for (long long g = gtid; g < P.n_real; g += gthreads) dev_kick_drift<float>(P, g);
     for (long long k = gtid; k < (long long)P.nsys * kNacc; k += gthreads) P.acc[k] = 0;
     for (long long k = gtid; k < P.n_cells; k += gthreads) P.cell_cnt[k] = 0;
     for (long long k = gtid; k < P.n_grid; k += gthreads) P.qgrid[k] = 0;

@@ -474,9 +474,11 @@ __device__ __forceinline__ void dev_fft_plane(const Pool &P, const int2 *work, i
         const int m = i0 < H0 ? t : (K0 - i0) + K0 * (i1 == 0 ? 0 : K1 - i1);
         X[u] = cg_all[base0 + m];
         if (two) Y[u] = cg_all[base1 + m];
-      } else {
+      } else {  // read, and leave the grid zero for the next spread
         qa[u] = (long long)P.qgrid[base0 + t];
         qb[u] = two ? (long long)P.qgrid[base1 + t] : 0ll;
+        P.qgrid[base0 + t] = 0ull;
+        if (two) P.qgrid[base1 + t] = 0ull;
       }
     }
 #pragma unroll
@@ -598,9 +600,10 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
       }
       dst[u] = li * K + k;
       const long long gi = line_elem(axis, K0, K1, full_line(li), k, inv_K0);
-      if (kind == FFT_FWD_FROM_Q) {
+      if (kind == FFT_FWD_FROM_Q) {  // read, and leave the grid zero for the next spread
         v[u].x = grid_value<R>((long long)P.qgrid[S.grid_off + gi]);
         v[u].y = R(0);
+        P.qgrid[S.grid_off + gi] = 0ull;
       } else {
         v[u] = grid[gi];
       }
