@@ -24,18 +24,41 @@ __device__ __forceinline__ void dev_bin(const Pool &P, long long g) {
   ext_position(P, S, e, x[0], x[1], x[2]);
   double q = ext_charge(P, S, e);
   double w[3];
+  float wf[3];
   int c[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    w[a] = wrap_coord(x[a], S.box[a]);
-    int k = (int)floor(__dmul_rn(w[a], S.inv_cell[a]));
+    // Wrap: with n the image index this coordinate had at the last binning,
+    // w0 = x - L n (the rule's own two roundings).  If w0 lies in
+    // [L 2^-40, L (1 - 2^-40)] and |n| < 2^10, the rule's floor(x / L) is n
+    // (the roundings of x / L and L n are below L 2^-42 here), so w0 is the
+    // rule's result and the FP64 division is skipped.
+    const double L = S.box[a];
+    const int np = P.wrap_n ? P.wrap_n[3 * g + a] : 0;
+    const double w0 = __dsub_rn(x[a], __dmul_rn(L, (double)np));
+    const double d = L * 9.094947017729282e-13;  // L 2^-40
+    if (np > -1024 && np < 1024 && w0 >= d && w0 <= L - d) {
+      w[a] = w0;
+    } else {
+      double f;
+      w[a] = wrap_coord_n(x[a], L, f);
+      if (P.wrap_n) P.wrap_n[3 * g + a] = (int)fmax(-1073741824.0, fmin(1073741824.0, f));
+    }
+    wf[a] = __double2float_rn(w[a]);
+    // cell: floor(w nc / L) in FP64 (the rule); the FP32 product decides when
+    // it is at least 1e-4 from a cell face (its error is below 2e-5 for
+    // nc <= 256)
+    const float uf = wf[a] * S.inv_cellf[a];
+    int k = (int)floorf(uf);
+    const float fr = uf - (float)k;
+    if (S.nc[a] > 256 || !(fr >= 1e-4f && fr <= 1.0f - 1e-4f))
+      k = (int)floor(__dmul_rn(w[a], S.inv_cell[a]));
     k = k > S.nc[a] - 1 ? S.nc[a] - 1 : k;
     k = k < 0 ? 0 : k;
     c[a] = k;
   }
   int cell = c[0] + S.nc[0] * (c[1] + S.nc[1] * c[2]);
-  P.xyzq_u[g] = make_float4(__double2float_rn(w[0]), __double2float_rn(w[1]),
-                            __double2float_rn(w[2]), (float)q);
+  P.xyzq_u[g] = make_float4(wf[0], wf[1], wf[2], (float)q);
   if (P.xyzq_u64) P.xyzq_u64[g] = make_dpos4(w[0], w[1], w[2], q);
   if (P.img_now) {
     // periodic image index: x = w + img L exactly up to the wrap rule

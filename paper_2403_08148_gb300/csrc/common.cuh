@@ -83,6 +83,7 @@ struct SysDesc {
   // geometry
   double box[3];
   double inv_cell[3];  // nc / L (FP64, the binning rule)
+  float inv_cellf[3];  // FP32 copy (cell index away from cell faces)
   float boxf[3];
   float rc2f;          // fl(rc^2)
   float kfac[3];       // K / L
@@ -180,6 +181,7 @@ struct Pool {
   // + slot] for slot < bucket_cap; null: scan + scatter + sort kernels
   int *bucket;
   int bucket_cap;
+  int *wrap_n;          // [3 * n_ext] periodic image index of each coordinate at the last binning
   // PME
   unsigned long long *qgrid;  // fixed-point charge grid
   float2 *cgrid;              // complex grid (FP32 path)
@@ -306,6 +308,15 @@ __device__ __forceinline__ double wrap_coord(double x, double L) {
   double f = floor(s);
   double t = __dmul_rn(L, f);
   double w = __dsub_rn(x, t);
+  if (w >= L) w = 0.0;
+  if (w < 0.0) w = 0.0;
+  return w;
+}
+
+// The same wrap with the image index f = floor(x / L) it used.
+__device__ __forceinline__ double wrap_coord_n(double x, double L, double &f) {
+  f = floor(__ddiv_rn(x, L));
+  double w = __dsub_rn(x, __dmul_rn(L, f));
   if (w >= L) w = 0.0;
   if (w < 0.0) w = 0.0;
   return w;

@@ -646,6 +646,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
       S.ncell *= S.nc[a];
       S.box[a] = p.box[a];
       S.inv_cell[a] = (double)S.nc[a] / p.box[a];
+      S.inv_cellf[a] = (float)S.inv_cell[a];
       S.boxf[a] = (float)p.box[a];
       S.K[a] = p.K[a];
       S.kfac[a] = (float)((double)p.K[a] / p.box[a]);
@@ -857,6 +858,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   if (fp64) cv.add(&P.xyzq_u64, ne);
   cv.add(&P.cell_of, ne);
   cv.add(&P.slot, ne);
+  cv.add(&P.wrap_n, 3 * ne);
   cv.add(&P.sorted_idx, ne);
   cv.add(&P.sort_tmp, ne);
   cv.add(&P.xyzq_s, ne);
@@ -1046,6 +1048,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   }
   GCME_CK(cudaMemset(P.force, 0, sizeof(long long) * 3 * nr));
   if (ngrid > 0) GCME_CK(cudaMemset(P.qgrid, 0, sizeof(unsigned long long) * ngrid));
+  GCME_CK(cudaMemset(P.wrap_n, 0, sizeof(int) * 3 * ne));
   GCME_CK(cudaMemset(P.step_ctr, 0, sizeof(unsigned long long) * ns));
   if (use_list) {
     // reference positions ~1e306: the first check requests a build
@@ -1461,6 +1464,7 @@ int gcme_system_set_box(gcme_sys *sys, const double *box, gcme_stream_t stream) 
     for (int a = 0; a < 3; ++a) {
       S.box[a] = box[a];
       S.inv_cell[a] = (double)S.nc[a] / box[a];
+      S.inv_cellf[a] = (float)S.inv_cell[a];
       S.boxf[a] = (float)box[a];
       S.kfac[a] = (float)((double)S.K[a] / box[a]);
       S.cside[a] = (float)(box[a] / S.nc[a]);

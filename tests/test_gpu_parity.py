@@ -62,6 +62,55 @@ def test_cell_list_bit_exact(name, factor):
     assert np.array_equal(si.cpu().numpy(), order)
 
 
+def _edge_positions(s, rng):
+    """Coordinates on and next to box and cell faces (one ulp, and the
+    2^-40 L margin of the binning's shortcut), far images (|n| around 2^10)
+    and ordinary ones."""
+    pos = s.pos.copy()
+    nc = oracle.cell_counts(s.box, s.rc)
+    k = 0
+    for a in range(3):
+        L = s.box[a]
+        faces = [m * L for m in range(-3, 4)] + [c * L / nc[a] for c in range(nc[a] + 1)]
+        for f in faces:
+            for v in (f, np.nextafter(f, np.inf), np.nextafter(f, -np.inf),
+                      f + L * 2.0 ** -40, f - L * 2.0 ** -40,
+                      np.nextafter(f + L * 2.0 ** -40, -np.inf), f + 3.7 * L * 2.0 ** -40):
+                pos[k % s.n, a] = v
+                k += 1
+        for m in (1000, 1023, 1024, 1500, -1024, -1500):
+            pos[k % s.n, a] = pos[k % s.n, a] % L + m * L
+            k += 1
+    return pos
+
+
+def test_cell_list_bit_exact_at_faces_and_far_images():
+    """The binning's exact shortcut (a coordinate's image index from the
+    previous binning) against the rule, at the faces of the box and of the
+    cells, with right and wrong previous indices."""
+    import dataclasses
+    import torch
+    g = lib()
+    s = synth.make_bulk(3000, seed_index=59, charged_frac=0.2, K=(12, 12, 12))  # 3^3 cells
+    sysg = g.System(ctx(), g.params_from(s), s.q)
+    info = sysg.info()
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(5)
+    p0 = _edge_positions(s, rng)
+    shifts = rng.integers(-2, 3, size=p0.shape) * s.box  # other images: the stored indices miss
+    for pos in (p0, p0, p0 + shifts, p0):
+        t = dataclasses.replace(s, pos=pos)
+        cs = torch.zeros(info.ncell + 1, dtype=torch.int32, device=dev)
+        si = torch.zeros(info.n_ext, dtype=torch.int32, device=dev)
+        sysg.build_cells(torch.tensor(pos, dtype=torch.float64, device=dev), cs, si)
+        torch.cuda.synchronize()
+        epos, _, _, _ = oracle.electrostatic_beads(t)
+        nc = oracle.cell_counts(s.box, s.rc)
+        _, start, order = oracle.cell_list(epos, s.box, nc, oracle.bead_classes(t))
+        assert np.array_equal(cs.cpu().numpy(), start)
+        assert np.array_equal(si.cpu().numpy(), order)
+
+
 # --------------------------------------------------------------------------
 # K3 neighbour set, bit-exact
 # --------------------------------------------------------------------------
