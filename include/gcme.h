@@ -348,7 +348,7 @@ int gcme_debug_barrier_timeout(gcme_ctx *ctx, double timeout_s, gcme_stream_t st
 
 /* Tuned launch shapes: work items per home cell of the pair kernel (3: 9
  * neighbour cells each; 9: 3 each), pair block size (128, 160 or 192
- * threads) of which pair_nelec (1 or 2) electrostatics warps and the rest
+ * threads) of which pair_nelec (1 to 3) electrostatics warps and the rest
  * Gaussian-core warps, resident pair
  * CTAs per SM fetching work items dynamically (0: one CTA per item), FFT
  * lines per tile per axis, x-y plane passes (1) or per-axis passes (0);

@@ -106,7 +106,7 @@ struct SysDesc {
   int langevin;
   int ntypes;          // species of this system (several-species engines; else 0)
   int frozen_mask;     // bit t: beads of species t do not move
-  int pair_nelec;      // electrostatics warps of a packed pair CTA (1 or 2)
+  int pair_nelec;      // electrostatics warps of a packed pair CTA (1 to 3)
   long long tab_off;   // its ntypes x ntypes block of the pooled pair tables
   // real-space table (FP32 one-species engines): 2 * rtab_n float4 from
   // rtab_off of Pool::rtab, interval k of u = r^2 at u * rtab_scale in [k, k+1)

@@ -440,9 +440,9 @@ void Engine::order_by_cost(std::vector<int2> &pw, int split) const {
 
 int Engine::set_pair_config(int split, int threads, int ctas_per_sm, int nelec) {
   if ((split != 3 && split != 9) || (threads != 128 && threads != 160 && threads != 192) ||
-      ctas_per_sm < 0 || ctas_per_sm > 8 || (nelec != 1 && nelec != 2) ||
+      ctas_per_sm < 0 || ctas_per_sm > 8 || nelec < 1 || nelec > 3 ||
       threads / 32 - nelec < 2) {
-    set_error("pair configuration must be split 3|9, 128|160|192 threads, 1|2 electrostatics "
+    set_error("pair configuration must be split 3|9, 128|160|192 threads, 1..3 electrostatics "
               "warps (at least 2 core warps), 0..8 CTAs per SM");
     return GCME_ERR_INVALID;
   }
@@ -495,7 +495,7 @@ int Engine::apply_tuning(int split, int threads, int ctas_per_sm, int nelec, con
          (2 * (size_t)lpb[a] + 1) * plan.kmax[a] * rsz <= kFftSmemLimit;
   if (pair_shapes)
     ok = ok && (split == 3 || split == 9) && (threads == 128 || threads == 160 || threads == 192) &&
-         ctas_per_sm >= 0 && ctas_per_sm <= 8 && (nelec == 1 || nelec == 2) &&
+         ctas_per_sm >= 0 && ctas_per_sm <= 8 && nelec >= 1 && nelec <= 3 &&
          threads / 32 - nelec >= 2;
   if (!ok) {
     set_error("launch shapes out of range or larger than shared memory");

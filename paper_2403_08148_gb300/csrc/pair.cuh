@@ -564,7 +564,7 @@ __device__ __forceinline__ PairSeg item_segment(const Pool &P, const SysDesc &S,
 
 // Packed variant of dev_pair_f32_item (one species, no debug dump): the
 // core warps run pair_core2 over coordinate arrays, the electrostatics
-// warps (1 or 2, SysDesc::pair_nelec) pair_elec over the staged charged and
+// warps (1 to 3, SysDesc::pair_nelec) pair_elec over the staged charged and
 // image beads, each warp a contiguous part of every cell's candidates and
 // each writing its partial sums (fixed-point atomics add them).  Items whose
 // beads exceed the packed capacities take the scalar path.  smem:
@@ -588,7 +588,7 @@ __device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *
   const SysDesc &S = P.sys[s];
   // warps 0 .. ncore-1: Gaussian core; the last nelec warps split every
   // cell's charged and image candidates into contiguous parts
-  const int nelec = S.pair_nelec > 1 ? 2 : 1;
+  const int nelec = min(max(S.pair_nelec, 1), 3);
   const int ncore = (blockDim.x >> 5) - nelec;
   const bool core_role = warp < ncore;
   const int ew = warp - ncore;

@@ -4,7 +4,7 @@
 // actual system (or batch) at its current positions:
 //   pair kernel (27-cell path): 3 or 9 work items per home cell (9 or 3 neighbour cells
 //                each) x {128 threads with 1 electrostatics warp, 160 with 1
-//                or 2, 192 with 2; the other warps Gaussian core} x {one CTA
+//                or 2, 192 with 2 or 3; the other warps Gaussian core} x {one CTA
 //                per work item, or 5, 6 or 8 resident CTAs per SM fetching
 //                items dynamically so that the remaining slots host the
 //                concurrent PME branch};
@@ -174,7 +174,7 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
   double best = 1e30;
   int bs = pair_split, bt = pair_threads, bc = pair_ctas_per_sm, be = pair_nelec;
   if (cell_factor == 1 && !use_list) {  // with lists the cell kernel only serves overflows
-    const int shapes[4][2] = {{128, 1}, {160, 1}, {160, 2}, {192, 2}};  // threads, elec warps
+    const int shapes[5][2] = {{128, 1}, {160, 1}, {160, 2}, {192, 2}, {192, 3}};  // threads, elec warps
     for (int split : {3, 9})
       for (const auto &sh : shapes)
         for (int ctas : {0, 5, 6, 8}) {

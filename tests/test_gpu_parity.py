@@ -224,6 +224,20 @@ def test_fft_paths(name, prec):
         assert np.max(np.abs(o["virial"] - outs[0]["virial"])) <= rtol * wv + atol
 
 
+@pytest.mark.parametrize("split,threads,nelec,ctas", [
+    (9, 128, 1, 0), (9, 160, 1, 0), (9, 160, 2, 0), (9, 192, 2, 0), (9, 192, 3, 0),
+    (3, 192, 3, 0), (9, 192, 3, 5), (3, 160, 2, 8)])
+def test_pair_shapes_at_parity(split, threads, nelec, ctas):
+    """Every launch shape of the 27-cell kernel (work items per cell, block
+    size, electrostatics warps splitting each cell's charged candidates,
+    static or dynamic CTAs) gives the oracle's forces and energies."""
+    s = CASES["poly_bonds"]
+    t = {"pair_split": split, "pair_threads": threads, "pair_ctas_per_sm": ctas,
+         "pair_nelec": nelec, "fft_lpb": [8, 8, 8], "fft_plane": True}
+    out = gpu_forces(s, 0, tuning=t)
+    _check(s, out, oracle.energy_forces(s), FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
+
+
 def test_apply_tuning_rejects_bad_shapes():
     g = lib()
     s = synth.make_bulk(300, seed_index=58, charged_frac=0.2, K=(96, 96, 8))
@@ -231,7 +245,7 @@ def test_apply_tuning_rejects_bad_shapes():
     with pytest.raises(g.GcmeError):
         sysg.apply_tuning(_shapes(True, 8))
     for bad in (dict(fft_lpb=[3, 8, 8]), dict(fft_lpb=[8, 128, 8]), dict(pair_threads=96),
-                dict(pair_split=4), dict(pair_ctas_per_sm=9), dict(pair_nelec=3)):
+                dict(pair_split=4), dict(pair_ctas_per_sm=9), dict(pair_nelec=4)):
         t = _shapes(False, 8)
         t.update(bad)
         with pytest.raises(g.GcmeError):
@@ -364,7 +378,7 @@ def test_autotune_keeps_parity_and_caches(tmp_path, monkeypatch):
     pos = torch.tensor(s.pos, dtype=torch.float64, device="cuda:0")
     t1 = sysg.autotune(pos)
     assert t1["pair_split"] in (3, 9) and t1["pair_threads"] in (128, 160, 192)
-    assert t1["pair_nelec"] in (1, 2)
+    assert t1["pair_nelec"] in (1, 2, 3)
     lst = g.System(ctx(), g.params_from(s, pair_path=g.GCME_PAIR_LIST), s.q, s.bonds)
     t3 = lst.autotune(pos)  # the list path has a cache entry of its own
     assert not t3["from_cache"]
