@@ -55,9 +55,10 @@ struct PairSeg {
 };
 
 // Packed items: the real beads of the staged cells as three coordinate
-// arrays of kPkCap floats (each cell padded to an even count), the charged
-// and image beads as kPkCapQ float4; this and the scalar items' float4
-// array share one shared-memory block of kPairSmemBytes.
+// arrays of kPkCap floats, the charged and image beads as four arrays (x, y,
+// z, charge) of kPkCapQ floats (each cell padded to an even count in both);
+// this and the scalar items' float4 array share one shared-memory block of
+// kPairSmemBytes.
 constexpr int kPkCap = 1280;
 constexpr int kPkCapQ = 640;
 constexpr int kPairSmemBytes =
@@ -270,6 +271,79 @@ __device__ __forceinline__ void pair_core2(const float *__restrict__ X,
       A.wg[3] = __ffma2_rn(ex, dy, A.wg[3]);
       A.wg[4] = __ffma2_rn(ex, dz, A.wg[4]);
       A.wg[5] = __ffma2_rn(ey, dz, A.wg[5]);
+    }
+  }
+}
+
+// Real-space electrostatics of a charged i over the staged charged and image
+// candidates [t0, t1) held as coordinate and charge arrays (t0, t1 even):
+// the in-cutoff test runs on two candidates per packed FP32x2 instruction
+// (the rounding of the neighbour rule, as in pair_core2) and sets one bit
+// per hit, 64 candidates at a time; the table lookup and the force run over
+// the set bits only.  jsorted0 + t is candidate t's sorted index (self
+// segment, staged whole and in order).
+template <bool SHIFT, bool SELF, bool VIR>
+__device__ __forceinline__ void pair_elec2(const float *__restrict__ X,
+                                           const float *__restrict__ Y,
+                                           const float *__restrict__ Z,
+                                           const float *__restrict__ Q, int t0, int t1,
+                                           int jsorted0, const float4 &xi, int isorted,
+                                           const PairSeg &sg, const SysDesc &S, float rc2,
+                                           PairAcc &A, const Pool &P) {
+  if (xi.w == 0.0f) return;
+  const float2 mx = make_float2(-xi.x, -xi.x), my = make_float2(-xi.y, -xi.y),
+               mz = make_float2(-xi.z, -xi.z);
+  const float2 hx = make_float2(sg.sh[0], sg.sh[0]), hy = make_float2(sg.sh[1], sg.sh[1]),
+               hz = make_float2(sg.sh[2], sg.sh[2]);
+  for (int c0 = t0; c0 < t1; c0 += 64) {
+    const int cn = min(64, t1 - c0);
+    unsigned long long m = 0ull;
+    for (int u = 0; u < cn; u += 2) {
+      float2 dx = __fadd2_rn(*reinterpret_cast<const float2 *>(X + c0 + u), mx);
+      float2 dy = __fadd2_rn(*reinterpret_cast<const float2 *>(Y + c0 + u), my);
+      float2 dz = __fadd2_rn(*reinterpret_cast<const float2 *>(Z + c0 + u), mz);
+      if (SHIFT) {
+        dx = __fadd2_rn(dx, hx);
+        dy = __fadd2_rn(dy, hy);
+        dz = __fadd2_rn(dz, hz);
+      }
+      const float2 r2 =
+          __fadd2_rn(__fadd2_rn(__fmul2_rn(dx, dx), __fmul2_rn(dy, dy)), __fmul2_rn(dz, dz));
+      bool in0 = r2.x < rc2, in1 = r2.y < rc2;
+      if (SELF) {
+        in0 = in0 && (jsorted0 + c0 + u != isorted);
+        in1 = in1 && (jsorted0 + c0 + u + 1 != isorted);
+      }
+      m |= ((unsigned long long)in0 | ((unsigned long long)in1 << 1)) << u;
+    }
+    while (m) {
+      const int u = __ffsll((long long)m) - 1;
+      m &= m - 1ull;
+      const int t = c0 + u;
+      float dx = __fsub_rn(X[t], xi.x), dy = __fsub_rn(Y[t], xi.y), dz = __fsub_rn(Z[t], xi.z);
+      if (SHIFT) {
+        dx = __fadd_rn(dx, sg.sh[0]);
+        dy = __fadd_rn(dy, sg.sh[1]);
+        dz = __fadd_rn(dz, sg.sh[2]);
+      }
+      const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+      float g, h;
+      real_gh_tab(P, S, r2, g, h);
+      const float qq = xi.w * Q[t];
+      A.ere = fmaf(qq, g, A.ere);
+      const float fq = qq * h;
+      A.fx = fmaf(fq, dx, A.fx);
+      A.fy = fmaf(fq, dy, A.fy);
+      A.fz = fmaf(fq, dz, A.fz);
+      if (VIR) {
+        const float ex = fq * dx, ey = fq * dy;
+        A.we[0] = fmaf(ex, dx, A.we[0]);
+        A.we[1] = fmaf(ey, dy, A.we[1]);
+        A.we[2] = fmaf(fq * dz, dz, A.we[2]);
+        A.we[3] = fmaf(ex, dy, A.we[3]);
+        A.we[4] = fmaf(ex, dz, A.we[4]);
+        A.we[5] = fmaf(ey, dz, A.we[5]);
+      }
     }
   }
 }
@@ -576,7 +650,7 @@ __device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *
   float *sx = reinterpret_cast<float *>(smem);
   float *sy = sx + kPkCap;
   float *sz = sy + kPkCap;
-  float4 *sq = reinterpret_cast<float4 *>(sz + kPkCap);
+  float *qx = sz + kPkCap, *qy = qx + kPkCapQ, *qz = qy + kPkCapQ, *qq = qz + kPkCapQ;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int s = work[w].x;
@@ -607,7 +681,7 @@ __device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *
       seg[k].soff = off;
       seg[k].qoff = qoff;
       off += (seg[k].n - seg[k].a + 1) & ~1;
-      qoff += seg[k].b;
+      qoff += (seg[k].b + 1) & ~1;
     }
     s_tot[0] = off;
     s_tot[1] = qoff;
@@ -682,8 +756,20 @@ __device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *
         const float4 v = t < g.b ? P.xyzq_s[g.beg + t] : far;
         const bool keep = t < g.b && (all || near_home(v, g));
         const unsigned m = __ballot_sync(0xffffffffu, keep);
-        if (keep) sq[g.qoff + keptq + __popc(m & lt)] = v;
+        if (keep) {
+          const int p = g.qoff + keptq + __popc(m & lt);
+          qx[p] = v.x;
+          qy[p] = v.y;
+          qz[p] = v.z;
+          qq[p] = v.w;
+        }
         keptq += __popc(m);
+      }
+      if ((keptq & 1) && lane == 0) {
+        qx[g.qoff + keptq] = far.x;
+        qy[g.qoff + keptq] = far.y;
+        qz[g.qoff + keptq] = far.z;
+        qq[g.qoff + keptq] = 0.0f;
       }
       if (lane == 0) {
         g.nk = kept;
@@ -741,14 +827,16 @@ __device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *
       } else {
         for (int k = 0; k < nseg; ++k) {
           const PairSeg g = seg[k];
-          const float4 *J = sq + g.qoff;
-          const int lo = g.bk * ew / nelec, hi = g.bk * (ew + 1) / nelec;
+          // this warp's part of the (even-padded) candidates, on even bounds
+          const int np2 = (g.bk + 1) >> 1;
+          const int lo = 2 * (np2 * ew / nelec), hi = 2 * (np2 * (ew + 1) / nelec);
+          const float *X = qx + g.qoff, *Y = qy + g.qoff, *Z = qz + g.qoff, *Qc = qq + g.qoff;
           if (g.self)
-            pair_elec<false, true, VIR, false>(J, lo, hi, 0, g.beg, xi, i, g, S, rc2, A, P, s);
+            pair_elec2<false, true, VIR>(X, Y, Z, Qc, lo, hi, g.beg, xi, i, g, S, rc2, A, P);
           else if (g.shifted)
-            pair_elec<true, false, VIR, false>(J, lo, hi, 0, g.beg, xi, i, g, S, rc2, A, P, s);
+            pair_elec2<true, false, VIR>(X, Y, Z, Qc, lo, hi, g.beg, xi, i, g, S, rc2, A, P);
           else
-            pair_elec<false, false, VIR, false>(J, lo, hi, 0, g.beg, xi, i, g, S, rc2, A, P, s);
+            pair_elec2<false, false, VIR>(X, Y, Z, Qc, lo, hi, g.beg, xi, i, g, S, rc2, A, P);
         }
       }
       pair_write<VIR>(P, S, s, valid, i, A);
