@@ -474,11 +474,9 @@ __device__ __forceinline__ void dev_fft_plane(const Pool &P, const int2 *work, i
         const int m = i0 < H0 ? t : (K0 - i0) + K0 * (i1 == 0 ? 0 : K1 - i1);
         X[u] = cg_all[base0 + m];
         if (two) Y[u] = cg_all[base1 + m];
-      } else {  // read, and leave the grid zero for the next spread
+      } else {
         qa[u] = (long long)P.qgrid[base0 + t];
         qb[u] = two ? (long long)P.qgrid[base1 + t] : 0ll;
-        P.qgrid[base0 + t] = 0ull;
-        if (two) P.qgrid[base1 + t] = 0ull;
       }
     }
 #pragma unroll
@@ -497,9 +495,11 @@ __device__ __forceinline__ void dev_fft_plane(const Pool &P, const int2 *work, i
         }
         v.x = x.x - y.y;  // X + i Y
         v.y = x.y + y.x;
-      } else {
+      } else {  // and leave the grid zero for the next spread
         v.x = grid_value<R>(qa[u]);
         v.y = two ? grid_value<R>(qb[u]) : R(0);
+        P.qgrid[base0 + t] = 0ull;
+        if (two) P.qgrid[base1 + t] = 0ull;
       }
       A[t] = v;
     }
@@ -586,6 +586,7 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
   for (int t0 = tid; t0 < nl * K; t0 += kItemLoads * nt) {
     R2 v[kItemLoads];
     int dst[kItemLoads];
+    long long gq[kItemLoads], gidx[kItemLoads];
 #pragma unroll
     for (int u = 0; u < kItemLoads; ++u) {
       const int t = t0 + u * nt;
@@ -600,17 +601,18 @@ __device__ __forceinline__ void dev_fft_item(const Pool &P, const int2 *work, in
       }
       dst[u] = li * K + k;
       const long long gi = line_elem(axis, K0, K1, full_line(li), k, inv_K0);
-      if (kind == FFT_FWD_FROM_Q) {  // read, and leave the grid zero for the next spread
-        v[u].x = grid_value<R>((long long)P.qgrid[S.grid_off + gi]);
-        v[u].y = R(0);
-        P.qgrid[S.grid_off + gi] = 0ull;
-      } else {
-        v[u] = grid[gi];
-      }
+      gidx[u] = S.grid_off + gi;
+      if (kind == FFT_FWD_FROM_Q) gq[u] = (long long)P.qgrid[gidx[u]];
+      else v[u] = grid[gi];
     }
 #pragma unroll
     for (int u = 0; u < kItemLoads; ++u) {
       if (t0 + u * nt >= nl * K) break;
+      if (kind == FFT_FWD_FROM_Q) {  // and leave the grid zero for the next spread
+        v[u].x = grid_value<R>(gq[u]);
+        v[u].y = R(0);
+        P.qgrid[gidx[u]] = 0ull;
+      }
       bufA[dst[u]] = v[u];
     }
   }
