@@ -5,7 +5,7 @@
 //   pair kernel (27-cell path): 3 or 9 work items per home cell (9 or 3 neighbour cells
 //                each) x {128 threads with 1 electrostatics warp, 160 with 1
 //                or 2, 192 with 2 or 3; the other warps Gaussian core} x {one CTA
-//                per work item, or 5, 6 or 8 resident CTAs per SM fetching
+//                per work item, or 3, 4, 5, 6 or 8 resident CTAs per SM fetching
 //                items dynamically so that the remaining slots host the
 //                concurrent PME branch};
 //   PME:         lines per FFT tile along each axis in {4, 8, 16, 32, 64}
@@ -163,7 +163,7 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
   // Every candidate is timed on the whole force evaluation (cell list,
   // pair kernel and bonds concurrent with the PME branch), since the
   // concurrency is what the launch shapes trade against each other.
-  const int reps = 7;
+  const int reps = 15;  // median of 15: candidates lie within a few per cent
   // replays of the captured force graph, as production runs it
   cudaGraphExec_t fg = nullptr;
   auto forces = [&] { cudaGraphLaunch(fg, st); };
@@ -177,7 +177,7 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
     const int shapes[5][2] = {{128, 1}, {160, 1}, {160, 2}, {192, 2}, {192, 3}};  // threads, elec warps
     for (int split : {3, 9})
       for (const auto &sh : shapes)
-        for (int ctas : {0, 5, 6, 8}) {
+        for (int ctas : {0, 3, 4, 5, 6, 8}) {
           const int threads = sh[0], nelec = sh[1];
           if (ctas > 40 / (threads / 32)) continue;  // register-limited residency (64 regs)
           int rc = set_pair_config(split, threads, ctas, nelec);
