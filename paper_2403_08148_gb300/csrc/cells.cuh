@@ -17,12 +17,23 @@ constexpr int kSortCap = 1024;
 
 __device__ __forceinline__ void dev_bin(const Pool &P, long long g) {
   if (g >= P.n_ext) return;
+  double x[3], q;
+  if (P.ext_src) {  // position and charge from one index, beside the system lookup
+    const int src = P.ext_src[g];
+    const int r = src < 0 ? -1 - src : src;
+    const double *p = P.pos + 3 * (long long)r;
+    x[0] = p[0];
+    x[1] = p[1];
+    x[2] = src < 0 ? -p[2] : p[2];
+    q = src < 0 ? -P.q[r] : P.q[r];
+  }
   int s = P.ext_sys[g];
   const SysDesc &S = P.sys[s];
   int e = (int)(g - S.ext_off);
-  double x[3];
-  ext_position(P, S, e, x[0], x[1], x[2]);
-  double q = ext_charge(P, S, e);
+  if (!P.ext_src) {
+    ext_position(P, S, e, x[0], x[1], x[2]);
+    q = ext_charge(P, S, e);
+  }
   double w[3];
   float wf[3];
   int c[3];

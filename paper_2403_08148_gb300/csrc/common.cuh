@@ -171,6 +171,7 @@ struct Pool {
   int *qlist;           // local ext index of each charged bead (reals first, then images)
   int *q_sys;
   int *img_src;         // local real index of each image
+  int *ext_src;         // pooled real bead giving each ext bead's position (images: -1 - it)
   // cells
   int *cell_cnt;
   int *cell_start;      // global (pooled) sorted offsets

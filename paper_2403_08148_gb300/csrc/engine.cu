@@ -868,6 +868,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   cv.add(&P.qlist, nq);
   cv.add(&P.q_sys, nq);
   cv.add(&P.img_src, nimg);
+  cv.add(&P.ext_src, ne);
   cv.add(&P.cell_cnt, ncell);
   cv.add(&P.cell_start, ncell + 1);
   // fused cell sort for small per-system grids; bucket capacity twice the
@@ -972,6 +973,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   // ---- host tables -> device
   std::vector<double> hq(nr);
   std::vector<int> h_ext_sys(ne), h_real_sys(nr), h_ql(nq), h_qs(nq), h_img(nimg), h_cs(ncell);
+  std::vector<int> h_ext_src(ne);
   std::vector<int2> h_bonds(nbond);
   std::vector<int> h_bsys(nbond);
   std::vector<float2> htw(fp64 ? 0 : ntw);
@@ -991,6 +993,9 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
       h_qs[S.q_off + k] = s;
     }
     for (int k = 0; k < (int)imgs[s].size(); ++k) h_img[S.img_off + k] = imgs[s][k];
+    for (int e2 = 0; e2 < S.n; ++e2) h_ext_src[S.ext_off + e2] = (int)(S.bead_off + e2);
+    for (int k = 0; k < (int)imgs[s].size(); ++k)
+      h_ext_src[S.ext_off + S.n + k] = -1 - (int)(S.bead_off + imgs[s][k]);
     for (int c = 0; c < S.ncell; ++c) h_cs[S.cell_off + c] = s;
     for (int b = 0; b < S.nbond; ++b) {
       h_bonds[S.bond_off + b] = make_int2(sp.bonds[2 * b], sp.bonds[2 * b + 1]);
@@ -1022,6 +1027,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   GCME_CK(up(P.qlist, h_ql.data(), sizeof(int) * nq));
   GCME_CK(up(P.q_sys, h_qs.data(), sizeof(int) * nq));
   GCME_CK(up(P.img_src, h_img.data(), sizeof(int) * nimg));
+  GCME_CK(up(P.ext_src, h_ext_src.data(), sizeof(int) * ne));
   GCME_CK(up(P.cell_sys, h_cs.data(), sizeof(int) * ncell));
   GCME_CK(up(P.bonds, h_bonds.data(), sizeof(int2) * nbond));
   GCME_CK(up(P.bond_sys, h_bsys.data(), sizeof(int) * nbond));

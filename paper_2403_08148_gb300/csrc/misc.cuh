@@ -256,9 +256,17 @@ __device__ __forceinline__ bool frozen_bead(const Pool &P, const SysDesc &S, int
 template <typename V>
 __device__ __forceinline__ void dev_kick_drift(const Pool &P, long long g) {
   if (g >= P.n_real) return;
+  V *vel = reinterpret_cast<V *>(P.vel) + 3 * g;
+  // the bead's state first: its loads do not wait for the system lookup
+  V v0[3];
+  double x0[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    v0[a] = vel[a];
+    x0[a] = P.pos[3 * g + a];
+  }
   const int s = P.real_sys[g];
   const SysDesc &S = P.sys[s];
-  V *vel = reinterpret_cast<V *>(P.vel) + 3 * g;
   const int i = (int)(g - S.bead_off);
   if (frozen_bead(P, S, i)) {
     for (int a = 0; a < 3; ++a) *force_ptr(P, S, i, a) = 0ull;
@@ -276,8 +284,8 @@ __device__ __forceinline__ void dev_kick_drift(const Pool &P, long long g) {
       unsigned long long *fp = force_ptr(P, S, i, a);
       const long long fq = (long long)*fp;
       *fp = 0ull;
-      V v = vel[a] + h * force_value<V>(fq);
-      double x = P.pos[3 * g + a] + hd * (double)v;
+      V v = v0[a] + h * force_value<V>(fq);
+      double x = x0[a] + hd * (double)v;
       v = c1 * v + c2 * z[a];
       vel[a] = v;
       P.pos[3 * g + a] = x + hd * (double)v;
@@ -288,9 +296,9 @@ __device__ __forceinline__ void dev_kick_drift(const Pool &P, long long g) {
     unsigned long long *fp = force_ptr(P, S, i, a);
     const long long fq = (long long)*fp;
     *fp = 0ull;
-    V v = vel[a] + h * force_value<V>(fq);
+    V v = v0[a] + h * force_value<V>(fq);
     vel[a] = v;
-    P.pos[3 * g + a] += S.dt * (double)v;
+    P.pos[3 * g + a] = x0[a] + S.dt * (double)v;
   }
 }
 
