@@ -134,8 +134,9 @@ static void erf_ratio(double w, double d[3]) {
 // entry 2k holds the coefficients of g on interval k in t = u / du - k
 // (c0 + t (c1 + t (c2 + t c3))), entry 2k + 1 those of h.  Exact values and
 // u-derivatives at the nodes (FP64) make the interpolant C1, with an error
-// below du^4 / 384 times the largest fourth u-derivative (about 1e-9 of
-// g(0) for 512 intervals at rc = 3, far below FP32 rounding).
+// below du^4 / 384 times the largest fourth u-derivative, which grows as
+// beta^8: the caller sizes nint with beta^2 rc^2 (measured against FP64 over
+// [0, 9]: ~1e-7 of the maximum with FP32 evaluation for a = 0.15 .. 0.7 d).
 static void real_table(double beta, double kappa, double umax, int nint, float4 *out) {
   auto gh = [&](double u, double v[4]) {  // g, dg/du, h, dh/du
     double fb[3], fk[3];
@@ -765,12 +766,14 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   std::vector<float4> hrtab;
   if (!fp64 && !species) {
     for (auto &S : hsys) {
-      S.rtab_n = kRealTabIntervals;
-      S.rtab_off = (long long)hrtab.size();
       const double umax = (double)S.rc2f;
-      S.rtab_scale = (float)(kRealTabIntervals / umax);
-      hrtab.resize(hrtab.size() + 2 * kRealTabIntervals);
-      real_table(S.beta, S.kappa, umax, kRealTabIntervals, hrtab.data() + S.rtab_off);
+      const double nd = std::ceil(18.25 * S.beta * S.beta * umax);
+      S.rtab_n = nd > kRealTabMax ? 0 : std::max(kRealTabMin, (int)nd);
+      S.rtab_off = (long long)hrtab.size();
+      if (!S.rtab_n) continue;  // direct evaluation
+      S.rtab_scale = (float)(S.rtab_n / umax);
+      hrtab.resize(hrtab.size() + 2 * (size_t)S.rtab_n);
+      real_table(S.beta, S.kappa, umax, S.rtab_n, hrtab.data() + S.rtab_off);
     }
   }
   // Neighbour lists: FP32 path, 27-cell stencil, and the two-cell build

@@ -14,7 +14,11 @@ constexpr int kDefaultCellFactor = 1;
 // work items per home cell of the 27-cell pair kernel (3 or 9)
 constexpr int kDefaultPairSplit = 9;
 constexpr int kDefaultPairThreads = 128;
-constexpr int kRealTabIntervals = 512;           // real-space table intervals in r^2
+// real-space table intervals in r^2: N = 18.25 beta^2 rc^2 keeps the cubic
+// interpolation error near 1e-7 of g(0) (the error scales as (beta^2 du)^4);
+// at least kRealTabMin, and direct evaluation above kRealTabMax (a < ~0.09 d)
+constexpr int kRealTabMin = 512;
+constexpr int kRealTabMax = 16384;
 constexpr int kMinLpb = 4;                       // fewest FFT lines per tile
 constexpr size_t kFftSmemLimit = 200 * 1024;     // dynamic smem of k_fft
 // Verlet-list skin (bead diameters): the list holds every pair within

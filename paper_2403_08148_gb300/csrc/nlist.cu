@@ -265,21 +265,8 @@ __device__ __forceinline__ void list_range(const Pool &P, const SysDesc &S, cons
     if (ELEC && in) {
       const float qq = xi.w * xj.w;
       float gg, hh;
-      if (P.rtab) {
-        real_gh_tab(P, S, r2, gg, hh);
-      } else if (r2 < 1e-2f) {
-        gg = S.ser_gf[0] + r2 * (S.ser_gf[1] + r2 * (S.ser_gf[2] + r2 * S.ser_gf[3]));
-        hh = S.ser_hf[0] + r2 * (S.ser_hf[1] + r2 * S.ser_hf[2]);
-      } else {
-        const float r = sqrtf(r2);
-        const float rinv = 1.0f / r;
-        const float xb = S.betaf * r, xk = S.kappaf * r;
-        gg = (erfcf(xk) - erfcf(xb)) * rinv;
-        const float eb = ex2_approx(-xb * xb * kLog2e);
-        const float ek = ex2_approx(-xk * xk * kLog2e);
-        const float dd = kTwoOverSqrtPi * (S.betaf * eb - S.kappaf * ek);
-        hh = (gg - dd) * (rinv * rinv);
-      }
+      if (S.rtab_n > 0) real_gh_tab(P, S, r2, gg, hh);
+      else real_gh_direct(r2, S.betaf, S.kappaf, S.ser_gf, S.ser_hf, gg, hh);
       const float lq = lbf * qq;
       A.ee += __float2int_rn(lq * gg);
       fs = fmaf(lq, hh, fs);

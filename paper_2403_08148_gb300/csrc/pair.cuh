@@ -79,6 +79,27 @@ __device__ __forceinline__ float pair_r2(const float4 &xj, const float4 &xi, con
   return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
 }
 
+// g(r) and h(r) of the real-space term evaluated directly: the small-r
+// Taylor series (sgf, shf) while beta r < 0.055 (its truncation error is
+// then below 1e-9 relative), else erfc and exp.
+__device__ __forceinline__ void real_gh_direct(float r2, float betaf, float kappaf,
+                                               const float *sgf, const float *shf, float &g,
+                                               float &h) {
+  if (r2 * (betaf * betaf) < 3e-3f) {
+    g = sgf[0] + r2 * (sgf[1] + r2 * (sgf[2] + r2 * sgf[3]));
+    h = shf[0] + r2 * (shf[1] + r2 * shf[2]);
+  } else {
+    const float r = sqrtf(r2);
+    const float rinv = 1.0f / r;
+    const float xb = betaf * r, xk = kappaf * r;
+    g = (erfcf(xk) - erfcf(xb)) * rinv;
+    const float eb = ex2_approx(-xb * xb * kLog2e);
+    const float ek = ex2_approx(-xk * xk * kLog2e);
+    const float dd = kTwoOverSqrtPi * (betaf * eb - kappaf * ek);
+    h = (g - dd) * (rinv * rinv);
+  }
+}
+
 // Gaussian core over real j in [t0, t1): every lane evaluates every
 // candidate (the exponential is cheap next to the test, so masking beats
 // branching); out-of-cutoff candidates contribute exactly zero.
@@ -176,21 +197,8 @@ __device__ __forceinline__ void pair_elec(const float4 *__restrict__ J, int t0, 
         betaf = T.beta;
       }
       float g, h;
-      if (!MT && P.rtab) {
-        real_gh_tab(P, S, r2, g, h);
-      } else if (r2 < 1e-2f) {
-        g = sgf[0] + r2 * (sgf[1] + r2 * (sgf[2] + r2 * sgf[3]));
-        h = shf[0] + r2 * (shf[1] + r2 * shf[2]);
-      } else {
-        const float r = sqrtf(r2);
-        const float rinv = 1.0f / r;
-        const float xb = betaf * r, xk = S.kappaf * r;
-        g = (erfcf(xk) - erfcf(xb)) * rinv;
-        const float eb = ex2_approx(-xb * xb * kLog2e);
-        const float ek = ex2_approx(-xk * xk * kLog2e);
-        const float dd = kTwoOverSqrtPi * (betaf * eb - S.kappaf * ek);
-        h = (g - dd) * (rinv * rinv);
-      }
+      if (!MT && S.rtab_n > 0) real_gh_tab(P, S, r2, g, h);
+      else real_gh_direct(r2, betaf, S.kappaf, sgf, shf, g, h);
       A.ere = fmaf(qq, g, A.ere);
       const float fq = qq * h;
       A.fx = fmaf(fq, dx, A.fx);
@@ -328,7 +336,8 @@ __device__ __forceinline__ void pair_elec2(const float *__restrict__ X,
       }
       const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
       float g, h;
-      real_gh_tab(P, S, r2, g, h);
+      if (S.rtab_n > 0) real_gh_tab(P, S, r2, g, h);
+      else real_gh_direct(r2, S.betaf, S.kappaf, S.ser_gf, S.ser_hf, g, h);
       const float qq = xi.w * Q[t];
       A.ere = fmaf(qq, g, A.ere);
       const float fq = qq * h;

@@ -238,6 +238,19 @@ def test_pair_shapes_at_parity(split, threads, nelec, ctas):
     _check(s, out, oracle.energy_forces(s), FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
 
 
+@pytest.mark.parametrize("a", [0.12, 0.07])
+def test_small_smearing_radius(a):
+    """Small smearing radii: the real-space table grows with beta^2 rc^2
+    (a = 0.12 d: about 9,000 intervals), and below a ~ 0.09 d the kernels
+    evaluate g and h directly (Taylor series while beta r < 0.055)."""
+    s = synth.make_bulk(1500, seed_index=60, charged_frac=0.3, K=(12, 12, 12))
+    s.a = a
+    for prec, f_tol, e_tol in ((0, FORCE_RTOL_FP32, ENERGY_RTOL_FP32),
+                               (1, FORCE_RTOL_FP64, ENERGY_RTOL_FP64)):
+        out = gpu_forces(s, prec)
+        _check(s, out, oracle.energy_forces(s), f_tol, e_tol, 1e-6 if prec == 0 else 1e-10)
+
+
 def test_apply_tuning_rejects_bad_shapes():
     g = lib()
     s = synth.make_bulk(300, seed_index=58, charged_frac=0.2, K=(96, 96, 8))
