@@ -1,5 +1,6 @@
-// cells.cu -- K1/K2 per-phase kernels: wrap + bin, scan, scatter and the
-// per-cell stable order (bodies in cells.cuh).
+// cells.cu -- K1/K2 per-phase kernels: wrap + bin, then either the fused
+// scan + scatter + per-cell stable order (grids of at most kFusedSortCells
+// cells per system) or the three separate passes (bodies in cells.cuh).
 #include "cells.cuh"
 #include "kernels.h"
 

@@ -3,7 +3,8 @@
 //
 // Cell list of side >= rc (the 27-cell stencil of the pair kernel).  The
 // binning is FP64 and bit-reproducible: wrapped x = x - L floor(x / L) with
-// one rounding per operation, cell = floor(x nc / L) clamped to [0, nc-1].
+// one rounding per operation, cell = floor(x nc / L) clamped to [0, nc-1]
+// (dev_bin reaches the same results by exact shortcuts away from faces).
 // Inside a cell, beads are ordered by (class, index) with class 0 = image,
 // 1 = charged real, 2 = neutral real, so that the pair kernel finds the
 // electrostatic beads (images + charged) and the Gaussian-core beads

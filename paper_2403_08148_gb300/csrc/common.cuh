@@ -244,15 +244,18 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // Real-space pair functions g(r) = [erf(beta r) - erf(kappa r)] / r and
 // h(r) = -g'(r) / r at u = r^2 < rc^2 from the system's cubic table in u
 // (Pool::rtab; 2 float4 per interval: g's then h's coefficients in t).
-__device__ __forceinline__ void real_gh_tab(const Pool &P, const SysDesc &S, float r2, float &g,
-                                            float &h) {
-  const float x = r2 * S.rtab_scale;
-  const int k = min((int)x, S.rtab_n - 1);
+__device__ __forceinline__ void real_gh_tab(const float4 *__restrict__ tab, float scale,
+                                            int nm1, float r2, float &g, float &h) {
+  const float x = r2 * scale;
+  const int k = min((int)x, nm1);
   const float t = x - (float)k;
-  const float4 *tab = P.rtab + S.rtab_off + 2 * k;
-  const float4 a = __ldg(tab), b = __ldg(tab + 1);
+  const float4 a = __ldg(tab + 2 * k), b = __ldg(tab + 2 * k + 1);
   g = fmaf(t, fmaf(t, fmaf(t, a.w, a.z), a.y), a.x);
   h = fmaf(t, fmaf(t, fmaf(t, b.w, b.z), b.y), b.x);
+}
+__device__ __forceinline__ void real_gh_tab(const Pool &P, const SysDesc &S, float r2, float &g,
+                                            float &h) {
+  real_gh_tab(P.rtab + S.rtab_off, S.rtab_scale, S.rtab_n - 1, r2, g, h);
 }
 
 __device__ __forceinline__ void atomic_add_fixed(unsigned long long *p, double v, double scale) {

@@ -289,15 +289,18 @@ __device__ __forceinline__ void pair_core2(const float *__restrict__ X,
 // (the rounding of the neighbour rule, as in pair_core2) and sets one bit
 // per hit, 64 candidates at a time; the table lookup and the force run over
 // the set bits only.  jsorted0 + t is candidate t's sorted index (self
-// segment, staged whole and in order).
-template <bool SHIFT, bool SELF, bool VIR>
-__device__ __forceinline__ void pair_elec2(const float *__restrict__ X,
-                                           const float *__restrict__ Y,
-                                           const float *__restrict__ Z,
-                                           const float *__restrict__ Q, int t0, int t1,
+// segment, staged whole and in order).  TAB: g and h from the system's
+// table (tab, its scale and last interval nm1), else evaluated directly.
+template <bool SHIFT, bool SELF, bool VIR, bool TAB>
+__device__ __forceinline__ void pair_elec2(const float *__restrict__ X, int t0, int t1,
                                            int jsorted0, const float4 &xi, int isorted,
                                            const PairSeg &sg, const SysDesc &S, float rc2,
-                                           PairAcc &A, const Pool &P) {
+                                           PairAcc &A, const float4 *__restrict__ tab,
+                                           float tab_scale, int tab_nm1) {
+  // y, z and charge arrays follow x at fixed strides (one base register)
+  const float *__restrict__ Y = X + kPkCapQ;
+  const float *__restrict__ Z = X + 2 * kPkCapQ;
+  const float *__restrict__ Q = X + 3 * kPkCapQ;
   if (xi.w == 0.0f) return;
   const float2 mx = make_float2(-xi.x, -xi.x), my = make_float2(-xi.y, -xi.y),
                mz = make_float2(-xi.z, -xi.z);
@@ -336,7 +339,7 @@ __device__ __forceinline__ void pair_elec2(const float *__restrict__ X,
       }
       const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
       float g, h;
-      if (S.rtab_n > 0) real_gh_tab(P, S, r2, g, h);
+      if (TAB) real_gh_tab(tab, tab_scale, tab_nm1, r2, g, h);
       else real_gh_direct(r2, S.betaf, S.kappaf, S.ser_gf, S.ser_hf, g, h);
       const float qq = xi.w * Q[t];
       A.ere = fmaf(qq, g, A.ere);
@@ -834,18 +837,36 @@ __device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *
 #pragma unroll
           for (int k = 0; k < 6; ++k) A.wg[k] = B.wg[k].x + B.wg[k].y;
       } else {
+        // the system's real-space table (tab_nm1 < 0: none)
+        const float4 *tab = P.rtab + S.rtab_off;
+        const float tab_scale = S.rtab_scale;
+        const int tab_nm1 = S.rtab_n - 1;
         for (int k = 0; k < nseg; ++k) {
           const PairSeg g = seg[k];
           // this warp's part of the (even-padded) candidates, on even bounds
           const int np2 = (g.bk + 1) >> 1;
           const int lo = 2 * (np2 * ew / nelec), hi = 2 * (np2 * (ew + 1) / nelec);
-          const float *X = qx + g.qoff, *Y = qy + g.qoff, *Z = qz + g.qoff, *Qc = qq + g.qoff;
-          if (g.self)
-            pair_elec2<false, true, VIR>(X, Y, Z, Qc, lo, hi, g.beg, xi, i, g, S, rc2, A, P);
-          else if (g.shifted)
-            pair_elec2<true, false, VIR>(X, Y, Z, Qc, lo, hi, g.beg, xi, i, g, S, rc2, A, P);
-          else
-            pair_elec2<false, false, VIR>(X, Y, Z, Qc, lo, hi, g.beg, xi, i, g, S, rc2, A, P);
+          const float *X = qx + g.qoff;
+          if (tab_nm1 < 0) {  // no table (very small smearing radius)
+            if (g.self)
+              pair_elec2<false, true, VIR, false>(X, lo, hi, g.beg, xi, i, g, S, rc2, A,
+                                                  tab, tab_scale, tab_nm1);
+            else if (g.shifted)
+              pair_elec2<true, false, VIR, false>(X, lo, hi, g.beg, xi, i, g, S, rc2, A,
+                                                  tab, tab_scale, tab_nm1);
+            else
+              pair_elec2<false, false, VIR, false>(X, lo, hi, g.beg, xi, i, g, S, rc2,
+                                                   A, tab, tab_scale, tab_nm1);
+          } else if (g.self) {
+            pair_elec2<false, true, VIR, true>(X, lo, hi, g.beg, xi, i, g, S, rc2, A,
+                                               tab, tab_scale, tab_nm1);
+          } else if (g.shifted) {
+            pair_elec2<true, false, VIR, true>(X, lo, hi, g.beg, xi, i, g, S, rc2, A,
+                                               tab, tab_scale, tab_nm1);
+          } else {
+            pair_elec2<false, false, VIR, true>(X, lo, hi, g.beg, xi, i, g, S, rc2, A,
+                                                tab, tab_scale, tab_nm1);
+          }
         }
       }
       pair_write<VIR>(P, S, s, valid, i, A);
