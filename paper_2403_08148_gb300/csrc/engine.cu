@@ -1059,6 +1059,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   if (ngrid > 0) GCME_CK(cudaMemset(P.qgrid, 0, sizeof(unsigned long long) * ngrid));
   GCME_CK(cudaMemset(P.wrap_n, 0, sizeof(int) * 3 * ne));
   GCME_CK(cudaMemset(P.step_ctr, 0, sizeof(unsigned long long) * ns));
+  GCME_CK(cudaMemset(pair_counter, 0, sizeof(int)));  // each pair launch leaves it zero
   if (use_list) {
     // reference positions ~1e306: the first check requests a build
     GCME_CK(cudaMemset(P.x_ref, 0x7f, sizeof(double) * 3 * nr));
@@ -1132,7 +1133,7 @@ void Engine::enqueue_sort_pairs(const Pool &Q, cudaStream_t st, bool vir, bool d
   if (timed) cudaEventRecordWithFlags(phase_ev[2], st, cudaEventRecordExternal);
   if (use_list) launch_pair_list(Q, vir, dbg, st);
   launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, pair_ctas(), pair_counter,
-              vir, dbg, st);
+              vir, dbg, bonds_in_pair(dbg), st);
   if (timed) cudaEventRecordWithFlags(phase_ev[3], st, cudaEventRecordExternal);
 }
 
@@ -1148,7 +1149,7 @@ void Engine::enqueue_forces(const Pool &Q, cudaStream_t st, bool vir, bool dbg) 
   }
   fork_pme(Q, st, vir, false);
   enqueue_sort_pairs(Q, st, vir, false, false);
-  launch_bonded(Q, vir, st);
+  launch_bonded(Q, vir, !bonds_in_pair(false), st);
   cudaStreamWaitEvent(st, join_ev, 0);
   launch_slab_apply(Q, st);
 }
@@ -1165,7 +1166,7 @@ void Engine::enqueue_step(const Pool &Q, cudaStream_t st) {
   launch_bin(Q, st, false);
   fork_pme(Q, st, false, ev, false);
   enqueue_sort_pairs(Q, st, false, false, ev);
-  launch_bonded(Q, false, st);
+  launch_bonded(Q, false, !bonds_in_pair(false), st);
   if (ev) cudaEventRecordWithFlags(phase_ev[4], st, cudaEventRecordExternal);
   cudaStreamWaitEvent(st, join_ev, 0);
   if (ev) cudaEventRecordWithFlags(phase_ev[7], st, cudaEventRecordExternal);

@@ -108,6 +108,11 @@ class Engine {
   int n_sm = 152;
   int *pair_counter = nullptr;  // dynamic work-item counter of the pair kernel
   int pair_ctas() const { return pair_ctas_per_sm > 0 ? n_sm * pair_ctas_per_sm : 0; }
+  // the FP32 27-cell kernel (one cell per stencil step, no pair dump) also
+  // runs the harmonic bonds, as work items after the cell items
+  bool bonds_in_pair(bool dbg) const {
+    return !fp64 && !dbg && cell_factor == 1 && n_pair_work > 0 && P.n_bond > 0;
+  }
   int device = 0;
   std::vector<SysDesc> hsys;
   Pool P{};  // device pointers of the pooled arrays

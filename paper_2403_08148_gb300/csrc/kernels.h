@@ -30,9 +30,12 @@ constexpr int kFusedSortCells = 2048;
 // K2: scan, scatter, per-cell order (one fused kernel when P.bucket is set)
 void launch_sort(const Pool &P, cudaStream_t st);
 // ctas: grid of the 27-cell kernel (CTAs loop over items fetched from
-// *counter, a device int the launch zeroes first)
+// *counter, a device int that is zero before the launch and that the launch
+// leaves zero).  bonds: the FP32 27-cell kernel also evaluates the harmonic
+// bonds, one bond per thread in work items after the cell items.
 void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell_factor,
-                 int threads, int ctas, int *counter, bool vir, bool dbg, cudaStream_t st);
+                 int threads, int ctas, int *counter, bool vir, bool dbg, bool bonds,
+                 cudaStream_t st);
 // Verlet neighbour list (nlist.cu): rebuild decision (clears the flag,
 // then sets it when a bead moved more than skin/2 since the last build or a
 // rebuild is pending), the gated build, the per-step refresh of the sorted
@@ -46,7 +49,8 @@ void launch_pair_list(const Pool &P, bool vir, bool dbg, cudaStream_t st);
 void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStream_t st,
                 bool zero_grid = true);
 void pme_set_smem_limits();
-void launch_bonded(const Pool &P, bool vir, cudaStream_t st);   // bonds, walls, dipole
+// bonds (unless the pair kernel took them), walls, dipole
+void launch_bonded(const Pool &P, bool vir, bool bonds, cudaStream_t st);
 void launch_slab_apply(const Pool &P, cudaStream_t st);         // Yeh-Berkowitz forces
 void launch_finalize(const Pool &P, bool vir, cudaStream_t st); // energies -> FP64
 void launch_kick_drift(const Pool &P, bool vel64, cudaStream_t st);

@@ -24,8 +24,8 @@ template <typename V>
 __global__ void k_kick(Pool P) { dev_kick<V>(P, GCME_TID); }
 #undef GCME_TID
 
-void launch_bonded(const Pool &P, bool vir, cudaStream_t st) {
-  if (P.n_bond > 0) {
+void launch_bonded(const Pool &P, bool vir, bool bonds, cudaStream_t st) {
+  if (bonds && P.n_bond > 0) {
     int nb = (int)((P.n_bond + 255) / 256);
     if (vir) k_bonds<true><<<nb, 256, 0, st>>>(P);
     else k_bonds<false><<<nb, 256, 0, st>>>(P);

@@ -43,7 +43,8 @@ __device__ __forceinline__ void sys_vir_add(const Pool &P, int s, bool act, cons
 // Harmonic bond u = k/2 (r - r0)^2 on the minimum-image separation (periodic
 // axes only: x, y, z in bulk, x, y in slabs).  FP32 arithmetic on the FP64
 // difference (FP64 throughout for FP64 systems).
-template <bool VIR>
+// F32: the caller runs FP32 systems only (the FP64 branch is not compiled)
+template <bool VIR, bool F32 = false>
 __device__ __forceinline__ void dev_bonds(const Pool &P, long long b) {
   const bool act = b < P.n_bond;
   int s = -1;
@@ -56,7 +57,7 @@ __device__ __forceinline__ void dev_bonds(const Pool &P, long long b) {
     const double *pi = P.pos + 3 * (S.bead_off + ij.x);
     const double *pj = P.pos + 3 * (S.bead_off + ij.y);
     const bool per[3] = {true, true, S.geometry == GCME_BULK};
-    if (S.precision == GCME_FP64) {
+    if (!F32 && S.precision == GCME_FP64) {
       double d[3];
       for (int a = 0; a < 3; ++a) {
         d[a] = pj[a] - pi[a];

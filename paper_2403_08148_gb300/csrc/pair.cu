@@ -2,6 +2,7 @@
 // FP64 pair kernel.
 #include "pair.cuh"
 #include "kernels.h"
+#include "misc.cuh"
 
 #include <algorithm>
 
@@ -12,14 +13,17 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_fine(Pool P, const int2 *
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) dev_pair_fine_item<VIR, DBG>(P, work, w);
 }
 
-// Work items are fetched dynamically from a counter (zeroed before the
-// launch): a CTA takes the next item when it finishes one, so heavy cells do
-// not leave SMs idle at the end, and a grid smaller than the SMs' capacity
-// leaves slots free for the concurrent PME branch.
+// Work items are fetched dynamically from a counter (zero before the launch;
+// the CTA that fetches the last index puts it back to zero, all other CTAs
+// having fetched their final index before it): a CTA takes the next item when
+// it finishes one, so heavy cells do not leave SMs idle at the end, and a grid
+// smaller than the SMs' capacity leaves slots free for the concurrent PME
+// branch.  Items nwork .. nwork + nbi - 1 are harmonic bonds (one per thread),
+// taken last, by CTAs that would otherwise idle at the end of the launch.
 // One species without the debug dump runs the packed item (pair_core2).
 template <bool VIR, bool DBG, bool MT>
 __global__ void __launch_bounds__(192, 5) k_pair_f32(Pool P, const int2 *work, int nwork,
-                                                     int *counter) {
+                                                     int nbi, int *counter) {
   __shared__ __align__(16) unsigned char raw[kPairSmemBytes];
   __shared__ PairSeg seg[9];
   __shared__ int s_total[2];
@@ -28,8 +32,13 @@ __global__ void __launch_bounds__(192, 5) k_pair_f32(Pool P, const int2 *work, i
   __shared__ __align__(16) PairTab stab[MT ? kMaxTypes * kMaxTypes : 1];
   float4 *sj = reinterpret_cast<float4 *>(raw);
   constexpr bool PK = !DBG && !MT;
+  const int ntot = nwork + nbi;
   if (!counter) {  // static: one item per CTA (grid = items)
-    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    for (int w = blockIdx.x; w < ntot; w += gridDim.x) {
+      if (!DBG && w >= nwork) {
+        dev_bonds<VIR, true>(P, (long long)(w - nwork) * blockDim.x + threadIdx.x);
+        continue;
+      }
       if (PK) dev_pair_f32_item_pk<VIR>(P, work, w, raw, seg, s_total);
       else dev_pair_f32_item<VIR, DBG, MT>(P, work, w, sj, seg, s_total, stj, stab);
     }
@@ -39,7 +48,15 @@ __global__ void __launch_bounds__(192, 5) k_pair_f32(Pool P, const int2 *work, i
     if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
     __syncthreads();
     const int w = s_item;
-    if (w >= nwork) break;
+    if (w >= ntot) {
+      if (threadIdx.x == 0 && w == ntot + (int)gridDim.x - 1) atomicExch(counter, 0);
+      break;
+    }
+    if (!DBG && w >= nwork) {
+      dev_bonds<VIR, true>(P, (long long)(w - nwork) * blockDim.x + threadIdx.x);
+      __syncthreads();  // every thread has read s_item before the next fetch
+      continue;
+    }
     if (PK) dev_pair_f32_item_pk<VIR>(P, work, w, raw, seg, s_total);
     else dev_pair_f32_item<VIR, DBG, MT>(P, work, w, sj, seg, s_total, stj, stab);
   }
@@ -175,7 +192,8 @@ __global__ void __launch_bounds__(128) k_pair_f64(Pool P) {
 }
 
 void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell_factor,
-                 int threads, int ctas, int *counter, bool vir, bool dbg, cudaStream_t st) {
+                 int threads, int ctas, int *counter, bool vir, bool dbg, bool bonds,
+                 cudaStream_t st) {
   if (P.n_ext == 0) return;
   if (fp64) {
     int nb = (int)((P.n_ext + 127) / 128);
@@ -192,20 +210,21 @@ void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell
     return;
   }
   const int tb = (threads == 160 || threads == 192) ? threads : 128;
+  const int nbi = (bonds && !dbg) ? (int)((P.n_bond + tb - 1) / tb) : 0;
+  const int ntot = nwork + nbi;
   // ctas <= 0: one CTA per item; else a grid of ctas fetching items
   const bool dyn = ctas > 0;
-  const int grid = dyn ? std::max(1, std::min(nwork, ctas)) : nwork;
-  if (dyn) cudaMemsetAsync(counter, 0, sizeof(int), st);
-  else counter = nullptr;
+  const int grid = dyn ? std::max(1, std::min(ntot, ctas)) : ntot;
+  if (!dyn) counter = nullptr;
   if (P.ptab) {  // several species
-    if (dbg) k_pair_f32<false, true, true><<<grid, tb, 0, st>>>(P, work, nwork, counter);
-    else if (vir) k_pair_f32<true, false, true><<<grid, tb, 0, st>>>(P, work, nwork, counter);
-    else k_pair_f32<false, false, true><<<grid, tb, 0, st>>>(P, work, nwork, counter);
+    if (dbg) k_pair_f32<false, true, true><<<grid, tb, 0, st>>>(P, work, nwork, nbi, counter);
+    else if (vir) k_pair_f32<true, false, true><<<grid, tb, 0, st>>>(P, work, nwork, nbi, counter);
+    else k_pair_f32<false, false, true><<<grid, tb, 0, st>>>(P, work, nwork, nbi, counter);
     return;
   }
-  if (dbg) k_pair_f32<false, true, false><<<grid, tb, 0, st>>>(P, work, nwork, counter);
-  else if (vir) k_pair_f32<true, false, false><<<grid, tb, 0, st>>>(P, work, nwork, counter);
-  else k_pair_f32<false, false, false><<<grid, tb, 0, st>>>(P, work, nwork, counter);
+  if (dbg) k_pair_f32<false, true, false><<<grid, tb, 0, st>>>(P, work, nwork, nbi, counter);
+  else if (vir) k_pair_f32<true, false, false><<<grid, tb, 0, st>>>(P, work, nwork, nbi, counter);
+  else k_pair_f32<false, false, false><<<grid, tb, 0, st>>>(P, work, nwork, nbi, counter);
 }
 
 }  // namespace gcme
