@@ -240,25 +240,41 @@ def run_gcme(args, ws, rank, local):
         starts[k].record(stream)
         sysg.step_continue(pos, vel, 1, E)
         ends[k].record(stream)
-        ends[k].synchronize()
-        ms, nkern = sysg.phase_ms()
-        phase += ms
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
+    nkern = sysg.step_kernels()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     total_ms = float(sum(step_ms))
     total_ms = reduce_max_ms(total_ms, ws)
     if ws > 1:
         torch.distributed.barrier()
     builds = sysg.info().list_builds - builds0
+    # phase breakdown: a separate run with phase timing on (its event nodes
+    # lengthen the step, so the timed steps above run without them)
+    Kp = min(K, 400)
+    sysg.phase_timing(True)
+    sysg.step_continue(pos, vel, 1, E)  # captures the instrumented graph
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    timed_ms = 0.0
+    for k in range(Kp):
+        flush.fill_(float(k))
+        p0.record(stream)
+        sysg.step_continue(pos, vel, 1, E)
+        p1.record(stream)
+        p1.synchronize()
+        timed_ms += p0.elapsed_time(p1)
+        ms, _ = sysg.phase_ms()
+        phase += ms
+    sysg.phase_timing(False)
+    phase /= Kp
+    timed_ms /= Kp
     pairs1, qq1 = count_pairs(g, sysg, s, pos, dev)
     pairs = 0.5 * (pairs0 + pairs1)
     qq = 0.5 * (qq0 + qq1)
     ms_per_step = total_ms / K
     steps_per_s = 1e3 / ms_per_step
     value = job_value(pairs, ms_per_step, ws)
-    phase /= K
     pair_ms = float(phase[2])
 
     # back-to-back (warm L2) steps, context only
@@ -316,6 +332,8 @@ def run_gcme(args, ws, rank, local):
            "phase_ms": dict(zip(("kick_drift", "cells", "pair", "pme_concurrent", "bonded",
                                  "slab_kick_energy"),
                                 [round(float(x), 5) for x in phase])),
+           "phase_note": f"event-timed phases from {Kp} further steps with phase timing on "
+                         f"({timed_ms:.5f} ms per step there: the event nodes lengthen a step)",
            "warm_l2_ms_per_step": warm_ms,
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": s.n * 3 * (8 + 4),
                    "d2h_bytes_per_step": 8 * g.NTERMS,
@@ -407,7 +425,11 @@ def batched_c4(g, ctx, dev, nsteps=500):
                     "pair_interactions_per_s": pairs * nsteps / dt,
                     "ms_per_step": 1e3 * dt / nsteps}
         if mode == 0:
+            b.phase_timing(True)
+            b.step(3, mode)
+            torch.cuda.synchronize()
             ms, nk = b.phase_ms()
+            b.phase_timing(False)
             out[key]["phase_ms"] = [round(float(x), 4) for x in ms]
         b.close()
     return out

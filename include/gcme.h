@@ -280,12 +280,21 @@ int gcme_step_continue(gcme_sys *sys, double *d_pos, void *d_vel, int64_t nsteps
 int gcme_step_f64(gcme_sys *sys, double *d_pos, double *d_vel, int64_t nsteps,
                   double *d_energy, gcme_stream_t stream);
 
+/* Phase timing on (on != 0) or off (the default).  With it on, later step
+ * graphs carry CUDA event nodes between the phases, which lengthen a step
+ * (by ~20 us per step on a GB300 at N = 32,000): for profiling only.  The
+ * setting takes effect at the next gcme_step / gcme_step_continue call.
+ * Errors: INVALID for a NULL system. */
+int gcme_step_phase_timing(gcme_sys *sys, int32_t on);
+
 /* Device time of the phases of the most recent completed step (the caller
  * synchronises first), measured by CUDA events captured in the step graph:
  * h_ms[0] half kick + drift, [1] cell list, [2] pair kernel, [3] PME (a
  * branch on a side stream concurrent with [2] and [4]), [4] bonds/walls,
- * [5] Yeh-Berkowitz + half kick + energies after the join (nphase >= 6).  *kernels
- * (may be NULL) receives the number of kernel launches in one step. */
+ * [5] Yeh-Berkowitz + half kick + energies after the join (nphase >= 6).
+ * INVALID unless the most recent step ran with phase timing on
+ * (gcme_step_phase_timing); h_ms may be NULL to query only *kernels (may be
+ * NULL), the number of kernel launches in one step. */
 #define GCME_NPHASE 6
 int gcme_step_phase_ms(gcme_sys *sys, float *h_ms, int32_t nphase, int32_t *kernels);
 
@@ -411,6 +420,9 @@ int gcme_batch_step(gcme_batch *b, int64_t nsteps, int32_t mode, gcme_stream_t s
 
 /* Autotune a batch on its current state (as gcme_autotune). */
 int gcme_batch_autotune(gcme_batch *b, int32_t flags, gcme_tuning *out, gcme_stream_t stream);
+
+/* Phase timing of a batch's step graphs (mode 0), as gcme_step_phase_timing. */
+int gcme_batch_phase_timing(gcme_batch *b, int32_t on);
 
 /* Phase times of the last batch step, as gcme_step_phase_ms. */
 int gcme_batch_phase_ms(gcme_batch *b, float *h_ms, int32_t nphase, int32_t *kernels);

@@ -133,6 +133,8 @@ _SIGS = {
     "gcme_step_continue": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
     "gcme_step_phase_ms": ([_vp, _vp, _i32, _vp], ctypes.c_int),
     "gcme_batch_phase_ms": ([_vp, _vp, _i32, _vp], ctypes.c_int),
+    "gcme_step_phase_timing": ([_vp, _i32], ctypes.c_int),
+    "gcme_batch_phase_timing": ([_vp, _i32], ctypes.c_int),
     "gcme_autotune": ([_vp, _vp, _i32, ctypes.POINTER(Tuning), _vp], ctypes.c_int),
     "gcme_batch_autotune": ([_vp, _i32, ctypes.POINTER(Tuning), _vp], ctypes.c_int),
     "gcme_apply_tuning": ([_vp, ctypes.POINTER(Tuning)], ctypes.c_int),
@@ -371,12 +373,23 @@ class System:
         _check(load().gcme_step_continue(self.h, _ptr(d_pos), _ptr(d_vel), int(nsteps),
                                          _ptr(d_energy), _stream(stream)))
 
+    def phase_timing(self, on: bool):
+        """Capture later step graphs with (or without) phase event nodes."""
+        _check(load().gcme_step_phase_timing(self.h, int(bool(on))))
+
     def phase_ms(self):
-        """Device ms of the phases of the last step, and kernels per step."""
+        """Device ms of the phases of the last step (phase timing on), and
+        kernels per step."""
         ms = np.zeros(6, np.float32)
         k = np.zeros(1, np.int32)
         _check(load().gcme_step_phase_ms(self.h, ms.ctypes.data, 6, k.ctypes.data))
         return ms, int(k[0])
+
+    def step_kernels(self):
+        """Kernel launches in one step graph."""
+        k = np.zeros(1, np.int32)
+        _check(load().gcme_step_phase_ms(self.h, None, 0, k.ctypes.data))
+        return int(k[0])
 
     def debug_pairs(self, d_pos, d_triples, cap: int, d_count, stream=None):
         _check(load().gcme_debug_pairs(self.h, _ptr(d_pos), _ptr(d_triples), int(cap),
@@ -454,11 +467,19 @@ class Batch:
     def apply_tuning(self, tuning: dict):
         _check(load().gcme_batch_apply_tuning(self.h, ctypes.byref(Tuning.from_dict(tuning))))
 
+    def phase_timing(self, on: bool):
+        _check(load().gcme_batch_phase_timing(self.h, int(bool(on))))
+
     def phase_ms(self):
         ms = np.zeros(6, np.float32)
         k = np.zeros(1, np.int32)
         _check(load().gcme_batch_phase_ms(self.h, ms.ctypes.data, 6, k.ctypes.data))
         return ms, int(k[0])
+
+    def step_kernels(self):
+        k = np.zeros(1, np.int32)
+        _check(load().gcme_batch_phase_ms(self.h, None, 0, k.ctypes.data))
+        return int(k[0])
 
     def pointers(self):
         p, v, e, o = _vp(), _vp(), _vp(), _vp()

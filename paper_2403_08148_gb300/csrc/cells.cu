@@ -6,7 +6,11 @@
 
 namespace gcme {
 
-__global__ void k_bin(Pool P) { dev_bin(P, blockIdx.x * (long long)blockDim.x + threadIdx.x); }
+__global__ void k_bin(Pool P) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (P.nsys == 1 && P.n_ext == P.n_real) dev_bin<true>(P, g);
+  else dev_bin<false>(P, g);
+}
 
 __global__ void __launch_bounds__(1024) k_scan(const int *cnt, int *start, long long n,
                                               const int *gate) {

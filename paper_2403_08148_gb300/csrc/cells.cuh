@@ -16,10 +16,18 @@ namespace gcme {
 
 constexpr int kSortCap = 1024;
 
+// ONE: one system without image beads (ext index = bead index, s = 0).
+template <bool ONE = false>
 __device__ __forceinline__ void dev_bin(const Pool &P, long long g) {
   if (g >= P.n_ext) return;
   double x[3], q;
-  if (P.ext_src) {  // position and charge from one index, beside the system lookup
+  if (ONE) {
+    const double *p = P.pos + 3 * g;
+    x[0] = p[0];
+    x[1] = p[1];
+    x[2] = p[2];
+    q = P.q[g];
+  } else if (P.ext_src) {  // position and charge from one index, beside the system lookup
     const int src = P.ext_src[g];
     const int r = src < 0 ? -1 - src : src;
     const double *p = P.pos + 3 * (long long)r;
@@ -28,10 +36,10 @@ __device__ __forceinline__ void dev_bin(const Pool &P, long long g) {
     x[2] = src < 0 ? -p[2] : p[2];
     q = src < 0 ? -P.q[r] : P.q[r];
   }
-  int s = P.ext_sys[g];
+  const int s = ONE ? 0 : P.ext_sys[g];
   const SysDesc &S = P.sys[s];
-  int e = (int)(g - S.ext_off);
-  if (!P.ext_src) {
+  const int e = ONE ? (int)g : (int)(g - S.ext_off);
+  if (!ONE && !P.ext_src) {
     ext_position(P, S, e, x[0], x[1], x[2]);
     q = ext_charge(P, S, e);
   }

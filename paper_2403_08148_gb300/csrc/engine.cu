@@ -1155,7 +1155,7 @@ void Engine::enqueue_forces(const Pool &Q, cudaStream_t st, bool vir, bool dbg) 
 }
 
 void Engine::enqueue_step(const Pool &Q, cudaStream_t st) {
-  const bool ev = phase_ev[0] != nullptr;
+  const bool ev = phase_timing && phase_ev[0] != nullptr;
   if (ev) cudaEventRecordWithFlags(phase_ev[0], st, cudaEventRecordExternal);
   // no clears on the critical path: the half kick and drift clears the
   // forces it reads, the energy accumulators and the cell counts, and the
@@ -1177,14 +1177,15 @@ void Engine::enqueue_step(const Pool &Q, cudaStream_t st) {
 }
 
 int Engine::step_graph(const Pool &Q, cudaGraphExec_t *out) {
-  auto key = std::make_tuple((void *)Q.pos, (void *)Q.vel, (void *)Q.force, 1);
+  auto key = std::make_tuple((void *)Q.pos, (void *)Q.vel, (void *)Q.force, phase_timing ? 3 : 1);
+  last_step_timed = phase_timing;
   auto it = graphs_.find(key);
   if (it != graphs_.end()) {
     *out = it->second;
     return GCME_OK;
   }
   cudaGraph_t g;
-  if (!phase_ev[0])
+  if (phase_timing && !phase_ev[0])
     for (int k = 0; k < kNPhaseEv; ++k) GCME_CK(cudaEventCreate(&phase_ev[k]));
   GCME_CK(cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal));
   enqueue_step(Q, capture_stream);
@@ -1726,8 +1727,8 @@ int gcme_step_f64(gcme_sys *sys, double *d_pos, double *d_vel, int64_t nsteps, d
 static int phase_ms(Engine &eng, float *h_ms, int32_t nphase, int32_t *kernels) {
   if (kernels) *kernels = eng.step_kernels;
   if (!h_ms) return GCME_OK;
-  if (nphase < 6 || !eng.phase_ev[0]) {
-    set_error("no captured step yet, or output shorter than the phase count");
+  if (nphase < 6 || !eng.phase_ev[0] || !eng.last_step_timed) {
+    set_error("no step with phase timing on yet, or output shorter than the phase count");
     return GCME_ERR_INVALID;
   }
   // [0] kick+drift, [1] cells, [2] pair kernel, [3] PME branch (side
@@ -1745,6 +1746,24 @@ int gcme_step_phase_ms(gcme_sys *sys, float *h_ms, int32_t nphase, int32_t *kern
   }
   GCME_TRY_CK(cudaSetDevice(sys->eng.device));
   return phase_ms(sys->eng, h_ms, nphase, kernels);
+}
+
+int gcme_step_phase_timing(gcme_sys *sys, int32_t on) {
+  if (!sys) {
+    set_error("NULL system");
+    return GCME_ERR_INVALID;
+  }
+  sys->eng.phase_timing = on != 0;
+  return GCME_OK;
+}
+
+int gcme_batch_phase_timing(gcme_batch *b, int32_t on) {
+  if (!b) {
+    set_error("NULL batch");
+    return GCME_ERR_INVALID;
+  }
+  b->eng.phase_timing = on != 0;
+  return GCME_OK;
 }
 
 int gcme_batch_phase_ms(gcme_batch *b, float *h_ms, int32_t nphase, int32_t *kernels) {

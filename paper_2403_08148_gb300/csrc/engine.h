@@ -96,6 +96,11 @@ class Engine {
   static constexpr int kNPhaseEv = 9;
   cudaEvent_t phase_ev[kNPhaseEv] = {};
   int step_kernels = 0;  // kernel nodes in the step graph
+  // phase timing: step graphs captured with event nodes between the phases
+  // (off by default: the event nodes lengthen the step); last_step_timed
+  // tells whether the most recent step graph carried them
+  bool phase_timing = false;
+  bool last_step_timed = false;
   unsigned int *bar_words = nullptr;  // persistent-launch barrier state (4 words)
   bool fp64 = false;
   int cell_factor = 1;  // 1: 27-cell stencil; 2: fine cells with culling

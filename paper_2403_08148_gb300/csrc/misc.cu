@@ -13,7 +13,8 @@ template <bool VIR>
 __global__ void k_finalize(Pool P) { dev_finalize<VIR>(P, (int)GCME_TID); }
 template <typename V>
 __global__ void k_kick_drift(Pool P) {
-  dev_kick_drift<V>(P, GCME_TID);
+  if (P.nsys == 1) dev_kick_drift<V, true>(P, GCME_TID);
+  else dev_kick_drift<V, false>(P, GCME_TID);
   // the step's accumulators and cell counts start from zero (the previous
   // step has read them)
   const long long nt = (long long)gridDim.x * blockDim.x;
@@ -21,7 +22,10 @@ __global__ void k_kick_drift(Pool P) {
   for (long long k = GCME_TID; k < P.n_cells; k += nt) P.cell_cnt[k] = 0;
 }
 template <typename V>
-__global__ void k_kick(Pool P) { dev_kick<V>(P, GCME_TID); }
+__global__ void k_kick(Pool P) {
+  if (P.nsys == 1) dev_kick<V, true>(P, GCME_TID);
+  else dev_kick<V, false>(P, GCME_TID);
+}
 #undef GCME_TID
 
 void launch_bonded(const Pool &P, bool vir, bool bonds, cudaStream_t st) {

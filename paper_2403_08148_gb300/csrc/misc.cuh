@@ -253,24 +253,32 @@ __device__ __forceinline__ bool frozen_bead(const Pool &P, const SysDesc &S, int
 }
 
 // Each bead's force is cleared once read (the step's force evaluation
-// accumulates into it next).
-template <typename V>
+// accumulates into it next).  ONE: the pool holds one system (s = 0, bead
+// offset 0, n = n_real), so the force loads go out with the bead's state
+// instead of after the system lookup.
+template <typename V, bool ONE = false>
 __device__ __forceinline__ void dev_kick_drift(const Pool &P, long long g) {
   if (g >= P.n_real) return;
   V *vel = reinterpret_cast<V *>(P.vel) + 3 * g;
   // the bead's state first: its loads do not wait for the system lookup
   V v0[3];
   double x0[3];
+  long long f1[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     v0[a] = vel[a];
     x0[a] = P.pos[3 * g + a];
+    if (ONE) f1[a] = P.force[(long long)a * P.n_real + g];
   }
-  const int s = P.real_sys[g];
+  const int s = ONE ? 0 : P.real_sys[g];
   const SysDesc &S = P.sys[s];
-  const int i = (int)(g - S.bead_off);
+  const int i = ONE ? (int)g : (int)(g - S.bead_off);
+  auto fptr = [&](int a) {
+    return ONE ? reinterpret_cast<unsigned long long *>(P.force + (long long)a * P.n_real + g)
+               : force_ptr(P, S, i, a);
+  };
   if (frozen_bead(P, S, i)) {
-    for (int a = 0; a < 3; ++a) *force_ptr(P, S, i, a) = 0ull;
+    for (int a = 0; a < 3; ++a) *fptr(a) = 0ull;
     return;
   }
   V h;
@@ -282,8 +290,8 @@ __device__ __forceinline__ void dev_kick_drift(const Pool &P, long long g) {
     const V c1 = V(S.lgv_c1), c2 = V(S.lgv_c2);
     const double hd = 0.5 * S.dt;
     for (int a = 0; a < 3; ++a) {
-      unsigned long long *fp = force_ptr(P, S, i, a);
-      const long long fq = (long long)*fp;
+      unsigned long long *fp = fptr(a);
+      const long long fq = ONE ? f1[a] : (long long)*fp;
       *fp = 0ull;
       V v = v0[a] + h * force_value<V>(fq);
       double x = x0[a] + hd * (double)v;
@@ -294,8 +302,8 @@ __device__ __forceinline__ void dev_kick_drift(const Pool &P, long long g) {
     return;
   }
   for (int a = 0; a < 3; ++a) {
-    unsigned long long *fp = force_ptr(P, S, i, a);
-    const long long fq = (long long)*fp;
+    unsigned long long *fp = fptr(a);
+    const long long fq = ONE ? f1[a] : (long long)*fp;
     *fp = 0ull;
     V v = v0[a] + h * force_value<V>(fq);
     vel[a] = v;
@@ -303,24 +311,32 @@ __device__ __forceinline__ void dev_kick_drift(const Pool &P, long long g) {
   }
 }
 
-template <typename V>
+template <typename V, bool ONE = false>
 __device__ __forceinline__ void dev_kick(const Pool &P, long long g) {
   const bool act = g < P.n_real;
   int s = -1;
   long long ke = 0;
   if (act) {
-    s = P.real_sys[g];
-    const SysDesc &S = P.sys[s];
     V *vel = reinterpret_cast<V *>(P.vel) + 3 * g;
-    const int i = (int)(g - S.bead_off);
+    V v0[3];
+    long long f1[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      v0[a] = vel[a];
+      if (ONE) f1[a] = P.force[(long long)a * P.n_real + g];
+    }
+    s = ONE ? 0 : P.real_sys[g];
+    const SysDesc &S = P.sys[s];
+    const int i = ONE ? (int)g : (int)(g - S.bead_off);
     V h;
     if constexpr (sizeof(V) == 4) h = S.half_dtf;
     else h = 0.5 * S.dt;
     const bool frozen = frozen_bead(P, S, i);
     V v2 = V(0);
     for (int a = 0; a < 3 && !frozen; ++a) {
-      const long long fq = *reinterpret_cast<const long long *>(force_ptr(P, S, i, a));
-      V v = vel[a] + h * force_value<V>(fq);
+      const long long fq =
+          ONE ? f1[a] : *reinterpret_cast<const long long *>(force_ptr(P, S, i, a));
+      V v = v0[a] + h * force_value<V>(fq);
       vel[a] = v;
       v2 += v * v;
     }

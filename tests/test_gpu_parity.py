@@ -379,6 +379,43 @@ def test_step_fp32_polyelectrolyte():
     assert abs(tot_g - tot_o) / abs(tot_o) < 1e-5
 
 
+def test_phase_timing_is_opt_in_and_changes_no_result():
+    """Event nodes between the phases enter the step graph only with phase
+    timing on; the trajectory is bit-identical with and without them."""
+    import torch
+    g = lib()
+    s = CASES["poly_bonds"]
+    dev = torch.device("cuda:0")
+    res = []
+    for on in (False, True):
+        sysg = g.System(ctx(), g.params_from(s, 0), s.q, s.bonds)
+        sysg.phase_timing(on)
+        pos = torch.tensor(s.pos, dtype=torch.float64, device=dev)
+        vel = torch.tensor(s.vel, dtype=torch.float32, device=dev)
+        E = torch.zeros(g.NTERMS, dtype=torch.float64, device=dev)
+        sysg.step(pos, vel, 5, E)
+        torch.cuda.synchronize()
+        nk = sysg.step_kernels()
+        assert nk > 0
+        if on:
+            ms, nk2 = sysg.phase_ms()
+            assert nk2 == nk and np.all(ms >= 0) and ms[2] > 0
+            sysg.phase_timing(False)
+            sysg.step_continue(pos, vel, 1, E)
+            torch.cuda.synchronize()
+            with pytest.raises(g.GcmeError):  # the last step ran without events
+                sysg.phase_ms()
+        else:
+            with pytest.raises(g.GcmeError):
+                sysg.phase_ms()
+            sysg.step_continue(pos, vel, 1, E)
+            torch.cuda.synchronize()
+        res.append([t.cpu().numpy() for t in (pos, vel, E)])
+        sysg.close()
+    for a, b in zip(res[0], res[1]):
+        assert np.array_equal(a, b)
+
+
 def test_autotune_keeps_parity_and_caches(tmp_path, monkeypatch):
     """The autotuner times the candidate launch shapes, applies the fastest
     (results stay within tolerance of the oracle) and records it in the
