@@ -120,6 +120,11 @@ struct SysDesc {
   float ser_gf[4], ser_hf[3];
   float betaf, kappaf;
   float gc_c2f;        // -3/(2 s) log2(e): exponent of the core in base 2
+  // 1 when the core term at rc is below 1e-10 of its contact value: the FP32
+  // one-species kernel then sums the core over every staged neighbour bead
+  // (the beads beyond rc add terms below the FP32 rounding of the sums)
+  // instead of testing r < rc per candidate
+  int gc_tail;
   // FP32 copies for the FP32 kernels (no FP64 arithmetic per thread)
   float gc_forcef;     // gc_fc gc_pref
   float gc_halfpref;   // gc_pref / 2

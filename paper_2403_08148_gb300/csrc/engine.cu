@@ -675,6 +675,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     S.gc_expc = 3.0 / (2.0 * s2);
     S.gc_fc = 3.0 / s2;
     S.gc_c2f = (float)(-S.gc_expc / std::log(2.0));
+    S.gc_tail = std::exp(-S.gc_expc * p.rc * p.rc) < 1e-10 ? 1 : 0;
     double sq = 0.0, born = 0.0;  // sum z^2, sum z^2 / (2 a_i)
     for (int i = 0; i < S.n; ++i) {
       const double z = sp.q[i];

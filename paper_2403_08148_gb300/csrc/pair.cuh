@@ -283,6 +283,49 @@ __device__ __forceinline__ void pair_core2(const float *__restrict__ X,
   }
 }
 
+// Gaussian core of a non-self neighbour cell without the in-cutoff test
+// (SysDesc::gc_tail): every staged bead contributes, those beyond rc with a
+// term below 1e-10 of the contact value (the staging cull keeps beads within
+// rc + 1e-3 of the home cell's box, and pads sit far away: their term is 0).
+// The image shift is applied to xi once, and r^2 is two fused
+// multiply-adds: with no cutoff decision here, no rounding rule has to be
+// followed.
+template <bool VIR>
+__device__ __forceinline__ void pair_core2_tail(const float *__restrict__ X,
+                                                const float *__restrict__ Y,
+                                                const float *__restrict__ Z, int n2,
+                                                const float4 &xi, const PairSeg &sg, float gcc,
+                                                PairAcc2 &A) {
+  const float ox = __fsub_rn(sg.sh[0], xi.x), oy = __fsub_rn(sg.sh[1], xi.y),
+              oz = __fsub_rn(sg.sh[2], xi.z);
+  const float2 mx = make_float2(ox, ox), my = make_float2(oy, oy), mz = make_float2(oz, oz);
+  const float2 g2 = make_float2(gcc, gcc);
+#pragma unroll 2
+  for (int t = 0; t < n2; t += 2) {
+    const float2 dx = __fadd2_rn(*reinterpret_cast<const float2 *>(X + t), mx);
+    const float2 dy = __fadd2_rn(*reinterpret_cast<const float2 *>(Y + t), my);
+    const float2 dz = __fadd2_rn(*reinterpret_cast<const float2 *>(Z + t), mz);
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+    const float2 arg = __fmul2_rn(r2, g2);
+    float2 e;
+    e.x = ex2_approx(arg.x);
+    e.y = ex2_approx(arg.y);
+    A.eg = __fadd2_rn(A.eg, e);
+    A.gx = __ffma2_rn(e, dx, A.gx);
+    A.gy = __ffma2_rn(e, dy, A.gy);
+    A.gz = __ffma2_rn(e, dz, A.gz);
+    if (VIR) {
+      const float2 ex = __fmul2_rn(e, dx), ey = __fmul2_rn(e, dy);
+      A.wg[0] = __ffma2_rn(ex, dx, A.wg[0]);
+      A.wg[1] = __ffma2_rn(ey, dy, A.wg[1]);
+      A.wg[2] = __ffma2_rn(__fmul2_rn(e, dz), dz, A.wg[2]);
+      A.wg[3] = __ffma2_rn(ex, dy, A.wg[3]);
+      A.wg[4] = __ffma2_rn(ex, dz, A.wg[4]);
+      A.wg[5] = __ffma2_rn(ey, dz, A.wg[5]);
+    }
+  }
+}
+
 // Real-space electrostatics of a charged i over the staged charged and image
 // candidates [t0, t1) held as coordinate and charge arrays (t0, t1 even):
 // the in-cutoff test runs on two candidates per packed FP32x2 instruction
@@ -817,6 +860,7 @@ __device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *
         B.eg = B.gx = B.gy = B.gz = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int k = 0; k < 6; ++k) B.wg[k] = make_float2(0.0f, 0.0f);
+        const bool tail = S.gc_tail != 0;
         for (int k = 0; k < nseg; ++k) {
           const PairSeg g = seg[k];
           const int n2 = (g.nk + 1) & ~1;
@@ -824,6 +868,8 @@ __device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *
           const int j0 = g.beg + g.a;
           if (g.self)
             pair_core2<false, true, VIR>(X, Y, Z, n2, j0, xi, i, g, rc2, gcc, B);
+          else if (tail)
+            pair_core2_tail<VIR>(X, Y, Z, n2, xi, g, gcc, B);
           else if (g.shifted)
             pair_core2<true, false, VIR>(X, Y, Z, n2, j0, xi, i, g, rc2, gcc, B);
           else
