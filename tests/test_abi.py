@@ -153,3 +153,14 @@ def test_no_device_reports_error_not_crash(g):
     with pytest.raises(g.GcmeError) as ei:
         g.Context(0)
     assert ei.value.code in (-1, -3)
+
+
+def test_null_handles_are_rejected(g):
+    """Entry points given a NULL system or batch return INVALID (-1) and set
+    a message, with or without a device."""
+    lib = g.load()
+    assert lib.gcme_step_phase_timing(None, 1) == -1
+    assert b"NULL" in lib.gcme_last_error()
+    assert lib.gcme_batch_phase_timing(None, 0) == -1
+    assert lib.gcme_step_phase_ms(None, None, 0, None) == -1
+    assert lib.gcme_batch_phase_ms(None, None, 0, None) == -1
