@@ -2023,6 +2023,8 @@ int gcme_batch_step(gcme_batch *b, int64_t nsteps, int32_t mode, gcme_stream_t s
   if (mode == 0) {
     rc = b->eng.step_graph(Q, &sg);
     if (rc) return rc;
+  } else {
+    b->eng.last_step_timed = false;  // the persistent kernel records no phase events
   }
   if (!b->forces_valid) {
     GCME_TRY_CK(cudaGraphLaunch(fg, st));
