@@ -251,6 +251,19 @@ def test_small_smearing_radius(a):
         _check(s, out, oracle.energy_forces(s), f_tol, e_tol, 1e-6 if prec == 0 else 1e-10)
 
 
+@pytest.mark.parametrize("sigma", [0.5, 0.8])
+def test_gaussian_core_width(sigma):
+    """The FP32 one-species kernel sums the core over every staged bead of the
+    non-self cells only when the core term at rc is below 1e-10 of its
+    contact value (sigma = 0.5 d: 1.9e-12); a wider core (sigma = 0.8 d:
+    2.6e-5 at rc) keeps the per-candidate cutoff test.  Both match the
+    oracle, whose sums stop at rc."""
+    s = synth.make_bulk(1500, seed_index=61, charged_frac=0.3, K=(12, 12, 12))
+    s.sigma = sigma
+    out = gpu_forces(s, 0)
+    _check(s, out, oracle.energy_forces(s), FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
+
+
 def test_apply_tuning_rejects_bad_shapes():
     g = lib()
     s = synth.make_bulk(300, seed_index=58, charged_frac=0.2, K=(96, 96, 8))
