@@ -289,8 +289,9 @@ int gcme_step_phase_timing(gcme_sys *sys, int32_t on);
 
 /* Device time of the phases of the most recent completed step (the caller
  * synchronises first), measured by CUDA events captured in the step graph:
- * h_ms[0] half kick + drift, [1] cell list, [2] pair kernel, [3] PME (a
- * branch on a side stream concurrent with [2] and [4]), [4] bonds/walls,
+ * h_ms[0] half kick + drift, [1] cell list, [2] pair kernel (with the
+ * harmonic bonds on the FP32 27-cell path), [3] PME (a branch on a side
+ * stream concurrent with [2] and [4]), [4] bonds (other paths) and walls,
  * [5] Yeh-Berkowitz + half kick + energies after the join (nphase >= 6).
  * INVALID unless the most recent step ran with phase timing on
  * (gcme_step_phase_timing); h_ms may be NULL to query only *kernels (may be
