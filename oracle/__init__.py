@@ -44,7 +44,6 @@ _lib = None
 
 _D = ctypes.POINTER(ctypes.c_double)
 _I32 = ctypes.POINTER(ctypes.c_int32)
-_I64 = ctypes.POINTER(ctypes.c_int64)
 
 
 def build(force: bool = False) -> str:
@@ -177,21 +176,6 @@ def pairs(pos, q, types, A_tab, sig_tab, a_tab, box, rc, kappa, lB,
     if per_bead:
         out["per_bead"] = eb
     return out
-
-
-def pairs_subset(pos, q, types, A_tab, sig_tab, a_tab, box, rc, kappa, lB, idx):
-    pos = _f64(pos)
-    n = pos.shape[0]
-    idx = np.ascontiguousarray(idx, dtype=np.int64)
-    A_tab = _f64(A_tab)
-    f = np.zeros((idx.shape[0], 3))
-    eb = np.zeros((idx.shape[0], 2))
-    lib().orc_pairs_subset(ctypes.c_int64(n), _p(pos), _p(_f64(q)), _p(_i32(types), _I32),
-                           ctypes.c_int32(A_tab.shape[0]), _p(A_tab), _p(_f64(sig_tab)),
-                           _p(_f64(a_tab)), _p(_f64(box)), ctypes.c_double(rc),
-                           ctypes.c_double(kappa), ctypes.c_double(lB),
-                           ctypes.c_int64(idx.shape[0]), _p(idx, _I64), _p(f), _p(eb))
-    return f, eb
 
 
 def ewald_recip(pos, q, box, kappa, lB, tol=1e-16, forces=True):
@@ -365,14 +349,6 @@ def energy_forces(s: System, pos=None, recip: str = "spme",
     E["virial"] = vir
     E["npairs"] = pr["npairs"]
     return E
-
-
-def forces_subset(s: System, idx, pos=None):
-    """Real-space forces and per-bead pair energies for the beads ``idx``."""
-    pos = s.pos if pos is None else pos
-    epos, eq, etype, _ = electrostatic_beads(s, pos)
-    A_tab, sig, a = _tables(s)
-    return pairs_subset(epos, eq, etype, A_tab, sig, a, s.box, s.rc, s.kappa, s.lB, idx)
 
 
 def mobile(s: System) -> np.ndarray:

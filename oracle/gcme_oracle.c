@@ -306,83 +306,6 @@ void orc_pairs(int64_t n, const double *pos, const double *q, const int32_t *typ
   free(f32);
 }
 
-/* Pair terms for a subset of beads only (forces on beads idx[0..m)). */
-void orc_pairs_subset(int64_t n, const double *pos, const double *q,
-                      const int32_t *type, int32_t nt, const double *A_tab,
-                      const double *sig_tab, const double *a_tab, const double *box,
-                      double rc, double kappa, double lB, int64_t m_idx,
-                      const int64_t *idx, double *f_out, double *eb_out) {
-  double *w = (double *)malloc(sizeof(double) * 3 * (size_t)n);
-  float *f32 = (float *)malloc(sizeof(float) * 3 * (size_t)n);
-  orc_wrap(n, pos, box, w);
-  for (int64_t i = 0; i < 3 * n; ++i) f32[i] = (float)w[i];
-  float Lf[3] = {(float)box[0], (float)box[1], (float)box[2]};
-  float rc2 = (float)(rc * rc);
-  int m[3], minimg[3];
-  for (int a = 0; a < 3; ++a) {
-    m[a] = image_range(box[a], rc);
-    minimg[a] = box[a] >= 2.0 * rc * (1.0 + 1e-4);
-  }
-#pragma omp parallel for schedule(dynamic, 4)
-  for (int64_t s = 0; s < m_idx; ++s) {
-    int64_t i = idx[s];
-    double fi[3] = {0, 0, 0};
-    double eg = 0.0, er = 0.0;
-    int ti = type[i];
-    for (int64_t j = 0; j < n; ++j) {
-      int tj = type[j];
-      double Aij = A_tab[ti * nt + tj];
-      double qq = q[i] * q[j];
-      if (Aij == 0.0 && qq == 0.0) continue;
-      int lo[3], hi[3];
-      for (int a = 0; a < 3; ++a) {
-        if (minimg[a]) {
-          int nn = -(int)nearbyint((w[3 * j + a] - w[3 * i + a]) / box[a]);
-          lo[a] = hi[a] = nn;
-        } else {
-          lo[a] = -m[a];
-          hi[a] = m[a];
-        }
-      }
-      for (int nz = lo[2]; nz <= hi[2]; ++nz)
-        for (int ny = lo[1]; ny <= hi[1]; ++ny)
-          for (int nx = lo[0]; nx <= hi[0]; ++nx) {
-            if (i == j && nx == 0 && ny == 0 && nz == 0) continue;
-            float sh[3] = {(float)nx * Lf[0], (float)ny * Lf[1], (float)nz * Lf[2]};
-            if (!in_cutoff_f32(f32 + 3 * i, f32 + 3 * j, sh, rc2)) continue;
-            double d[3] = {w[3 * j + 0] + nx * box[0] - w[3 * i + 0],
-                           w[3 * j + 1] + ny * box[1] - w[3 * i + 1],
-                           w[3 * j + 2] + nz * box[2] - w[3 * i + 2]};
-            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            double r = sqrt(r2);
-            double fs = 0.0;
-            if (Aij != 0.0) {
-              double sg = sig_tab[ti] * sig_tab[ti] + sig_tab[tj] * sig_tab[tj];
-              double u = Aij * pow(3.0 / (2.0 * ORC_PI * sg), 1.5) * exp(-1.5 * r2 / sg);
-              eg += 0.5 * u;
-              fs += 3.0 / sg * u;
-            }
-            if (qq != 0.0) {
-              double a2 = a_tab[ti] * a_tab[ti] + a_tab[tj] * a_tab[tj];
-              double beta = sqrt(ORC_PI) / (sqrt(2.0) * sqrt(a2));
-              double g, h;
-              real_kernel(beta, kappa, r, &g, &h);
-              er += 0.5 * lB * qq * g;
-              fs += lB * qq * h;
-            }
-            for (int a = 0; a < 3; ++a) fi[a] -= fs * d[a];
-          }
-    }
-    for (int a = 0; a < 3; ++a) f_out[3 * s + a] = fi[a];
-    if (eb_out) {
-      eb_out[2 * s + 0] = eg;
-      eb_out[2 * s + 1] = er;
-    }
-  }
-  free(w);
-  free(f32);
-}
-
 /* ------------------------------------------------------------------------ */
 /* Reciprocal-space term by direct k-sum (the standard point-charge Ewald    */
 /* sum of Eq. ewald, tin-foil boundary, k = 0 excluded).                     */
