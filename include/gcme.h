@@ -245,10 +245,24 @@ int gcme_build_cells(gcme_sys *sys, const double *d_pos, int32_t *d_cell_start,
  *   - every call shares the array and leaves its contents behind: calls
  *     whose work overlaps on the GPU (other streams, other threads) race,
  *     so serialise them;
- *   - no cudaMalloc, cudaFree or other allocating routine is called. */
+ *   - no cudaMalloc, cudaFree or other allocating routine is called, and
+ *     nothing is copied from host memory (the call's constants travel as a
+ *     kernel argument).
+ * ncell follows the rule of gcme_build_cells with cells of side
+ * >= rc / f (f = p->cell_factor, 0 meaning 1):
+ *   ncell = prod_a max(1, floor(box[a] / ((rc / f) (1 + 1e-4)))),
+ * and gcme_cells_noalloc_size returns it without touching the GPU. */
 int gcme_build_cells_noalloc(const gcme_params *p, int64_t n, const double *d_pos,
                              const double *d_q, int32_t *d_cell_start,
                              int32_t *d_sorted_idx, gcme_stream_t stream);
+
+/* Host-only size query for gcme_build_cells_noalloc (no counterpart in the
+ * paper): writes to *ncell the number of cells that call would use for n
+ * beads with parameters *p, so that a caller that cannot create a system
+ * (creating one allocates) can size d_cell_start[ncell + 1].  Applies the
+ * same checks as the build (maxima, geometry, cell_factor) and returns
+ * INVALID with the same messages; no CUDA call is made. */
+int gcme_cells_noalloc_size(const gcme_params *p, int64_t n, int64_t *ncell);
 
 /* Forces, energies and virial at positions d_pos[n*3] (FP64, any image).
  * d_force[3n] (fixed point, SoA), d_energy[GCME_NTERMS], d_virial[9]; any

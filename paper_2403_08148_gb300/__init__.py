@@ -6,7 +6,7 @@ those calls.  There is no CPU fallback: without the built library every
 entry point raises.
 """
 from .binding import (Batch, Context, GcmeError, Params, Server, System, load,  # noqa: F401
-                      build_cells_noalloc,
+                      build_cells_noalloc, cells_noalloc_size,
                       params_from, validate, FORCE_SCALE, NTERMS, TERM_NAMES,
                       GCME_BULK, GCME_SLAB_NONMETAL, GCME_SLAB_IMAGE, GCME_FP32, GCME_FP64,
                       GCME_PAIR_AUTO, GCME_PAIR_LIST, GCME_PAIR_CELLS)

@@ -127,6 +127,8 @@ _SIGS = {
     "gcme_forces": ([_vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "gcme_build_cells_noalloc": ([ctypes.POINTER(Params), _i64, _vp, _vp, _vp, _vp, _vp],
                                  ctypes.c_int),
+    "gcme_cells_noalloc_size": ([ctypes.POINTER(Params), _i64, ctypes.POINTER(ctypes.c_int64)],
+                                ctypes.c_int),
     "gcme_forces_to_f64": ([_vp, _vp, _vp, _vp], ctypes.c_int),
     "gcme_step": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
     "gcme_step_f64": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
@@ -261,6 +263,14 @@ def build_cells_noalloc(params: Params, n: int, d_pos, d_q, d_cell_start, d_sort
     _check(load().gcme_build_cells_noalloc(ctypes.byref(params), int(n), _ptr(d_pos), _ptr(d_q),
                                            _ptr(d_cell_start), _ptr(d_sorted_idx),
                                            _stream(stream)))
+
+
+def cells_noalloc_size(params: Params, n: int) -> int:
+    """Cells gcme_build_cells_noalloc would use (host only, no GPU call):
+    the cell-start buffer it writes holds this many + 1 entries."""
+    out = ctypes.c_int64(0)
+    _check(load().gcme_cells_noalloc_size(ctypes.byref(params), int(n), ctypes.byref(out)))
+    return int(out.value)
 
 
 class Context:

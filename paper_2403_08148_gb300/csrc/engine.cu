@@ -641,14 +641,10 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     S.pair_split = pair_split;
     S.pair_nelec = pair_nelec;
     for (int a = 0; a < 3; ++a) {
-      S.nc[a] = std::max(1, (int)std::floor(p.box[a] / ((p.rc / cell_factor) * (1.0 + 1e-4))));
+      S.nc[a] = cells_per_axis(p.box[a], p.rc, cell_factor);
       S.nb[a] = (S.nc[a] + 1) / 2;
-      S.cside[a] = (float)(p.box[a] / S.nc[a]);
       S.ncell *= S.nc[a];
-      S.box[a] = p.box[a];
-      S.inv_cell[a] = (double)S.nc[a] / p.box[a];
-      S.inv_cellf[a] = (float)S.inv_cell[a];
-      S.boxf[a] = (float)p.box[a];
+      set_cell_box_axis(S, a, p.box[a]);
       S.K[a] = p.K[a];
       S.kfac[a] = (float)((double)p.K[a] / p.box[a]);
       S.tw_off[a] = ntw;
@@ -1459,7 +1455,7 @@ int gcme_system_set_box(gcme_sys *sys, const double *box, gcme_stream_t stream) 
       set_error("gcme_system_set_box: box side shorter than the cutoff");
       return GCME_ERR_INVALID;
     }
-    nc[a] = std::max(1, (int)std::floor(box[a] / ((rc / E.cell_factor) * (1.0 + 1e-4))));
+    nc[a] = cells_per_axis(box[a], rc, E.cell_factor);
   }
   cudaStream_t st = (cudaStream_t)stream;
   GCME_TRY_CK(cudaSetDevice(E.device));
@@ -1474,12 +1470,8 @@ int gcme_system_set_box(gcme_sys *sys, const double *box, gcme_stream_t stream) 
     GCME_TRY_CK(cudaStreamSynchronize(st));
     SysDesc &S = E.hsys[0];
     for (int a = 0; a < 3; ++a) {
-      S.box[a] = box[a];
-      S.inv_cell[a] = (double)S.nc[a] / box[a];
-      S.inv_cellf[a] = (float)S.inv_cell[a];
-      S.boxf[a] = (float)box[a];
+      set_cell_box_axis(S, a, box[a]);
       S.kfac[a] = (float)((double)S.K[a] / box[a]);
-      S.cside[a] = (float)(box[a] / S.nc[a]);
     }
     S.V = box[0] * box[1] * box[2];
     box_floats(S);

@@ -1,5 +1,7 @@
 // engine.h -- host-side batch engine behind the C ABI.
 #pragma once
+#include <algorithm>
+#include <cmath>
 #include <map>
 #include <string>
 #include <tuple>
@@ -26,6 +28,25 @@ constexpr size_t kFftSmemLimit = 200 * 1024;     // dynamic smem of k_fft
 constexpr double kListSkin = 0.4;
 
 void set_error(const std::string &msg);
+
+// Cells along a box side L: the most cells of side >= rc / factor (with a
+// 1e-4 margin), so that the 27-cell stencil (factor 1) or the 125-cell
+// stencil (factor 2) holds every pair within rc.
+inline int cells_per_axis(double L, double rc, int factor) {
+  return std::max(1, (int)std::floor(L / ((rc / factor) * (1.0 + 1e-4))));
+}
+
+// Box-derived cell fields of axis a for the cell count S.nc[a]: box side
+// (FP64 and FP32), nc / L for the binning rule (FP64 and its FP32 copy for
+// the shortcut away from cell faces) and the cell side.  Every path that
+// fills a SysDesc for binning goes through here.
+inline void set_cell_box_axis(SysDesc &S, int a, double L) {
+  S.box[a] = L;
+  S.boxf[a] = (float)L;
+  S.inv_cell[a] = (double)S.nc[a] / L;
+  S.inv_cellf[a] = (float)S.inv_cell[a];
+  S.cside[a] = (float)(L / S.nc[a]);
+}
 
 struct SysSpec {
   gcme_params p;

@@ -9,6 +9,8 @@
 // file-scope device array of fixed size (kNoAllocBytes, held by every GPU
 // that loads the library until the process exits).  The caller still owns
 // the inputs (positions, charges) and the outputs (cell starts, order).
+// gcme_cells_noalloc_size tells such a caller, without touching the GPU,
+// how long its cell-start buffer must be.
 #include <mutex>
 #include <string>
 
@@ -61,16 +63,12 @@ int noalloc_scratch(int dev, unsigned char **out) {
   return GCME_OK;
 }
 
-}  // namespace
-}  // namespace gcme
-
-using namespace gcme;
-
-extern "C" int gcme_build_cells_noalloc(const gcme_params *p, int64_t n, const double *d_pos,
-                                        const double *d_q, int32_t *d_cell_start,
-                                        int32_t *d_sorted_idx, gcme_stream_t stream) {
-  if (!p || !d_pos || !d_q || !d_cell_start || !d_sorted_idx || n < 1) {
-    set_error("invalid argument to gcme_build_cells_noalloc");
+// Checks shared by the size query and the build: the parameters, the bead
+// count and the cell grid against the fixed maxima; fills the descriptor's
+// cell grid and box fields (the same helpers as the allocating path).
+int noalloc_geometry(const gcme_params *p, int64_t n, SysDesc &S, long long &ncell) {
+  if (!p || n < 1) {
+    set_error("gcme_build_cells_noalloc: NULL parameters or n < 1");
     return GCME_ERR_INVALID;
   }
   if (n > kNoAllocMaxBeads) {
@@ -95,23 +93,19 @@ extern "C" int gcme_build_cells_noalloc(const gcme_params *p, int64_t n, const d
     return GCME_ERR_INVALID;
   }
   const int factor = p->cell_factor ? p->cell_factor : kDefaultCellFactor;
-  SysDesc S{};
-  long long ncell = 1;
+  ncell = 1;
   for (int a = 0; a < 3; ++a) {
     if (!(p->box[a] >= p->rc * (1.0 + 1e-4))) {
       set_error("gcme_build_cells_noalloc: box side shorter than the cutoff");
       return GCME_ERR_INVALID;
     }
-    const double nc = std::floor(p->box[a] / ((p->rc / factor) * (1.0 + 1e-4)));
-    if (nc > (double)kNoAllocMaxCells) {
+    if (p->box[a] / ((p->rc / factor) * (1.0 + 1e-4)) > (double)kNoAllocMaxCells) {
       set_error("gcme_build_cells_noalloc: too many cells");
       return GCME_ERR_INVALID;
     }
-    S.nc[a] = std::max(1, (int)nc);
+    S.nc[a] = cells_per_axis(p->box[a], p->rc, factor);
     ncell *= S.nc[a];
-    S.box[a] = p->box[a];
-    S.inv_cell[a] = (double)S.nc[a] / p->box[a];
-    S.boxf[a] = (float)p->box[a];
+    set_cell_box_axis(S, a, p->box[a]);
   }
   if (ncell > kNoAllocMaxCells) {
     set_error("gcme_build_cells_noalloc: " + std::to_string(ncell) +
@@ -121,7 +115,51 @@ extern "C" int gcme_build_cells_noalloc(const gcme_params *p, int64_t n, const d
   S.n = (int)n;
   S.n_ext = (int)n;
   S.ncell = (int)ncell;
+  S.cell_factor = factor;
   S.geometry = p->geometry;
+  return GCME_OK;
+}
+
+// Writes the call's descriptor (a kernel argument, copied at launch) into
+// the scratch and clears the per-bead and per-cell system tables (all zero
+// for one system): nothing is copied from host memory.
+__global__ void k_noalloc_init(SysDesc S, SysDesc *dst, int *ext_sys, int n, int *cell_sys,
+                               int ncell) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g == 0) *dst = S;
+  for (int k = g; k < n; k += gridDim.x * blockDim.x) ext_sys[k] = 0;
+  for (int k = g; k < ncell; k += gridDim.x * blockDim.x) cell_sys[k] = 0;
+}
+
+}  // namespace
+}  // namespace gcme
+
+using namespace gcme;
+
+extern "C" int gcme_cells_noalloc_size(const gcme_params *p, int64_t n, int64_t *ncell) {
+  if (!ncell) {
+    set_error("gcme_cells_noalloc_size: NULL output");
+    return GCME_ERR_INVALID;
+  }
+  SysDesc S{};
+  long long nc = 0;
+  const int rc = noalloc_geometry(p, n, S, nc);
+  if (rc) return rc;
+  *ncell = nc;
+  return GCME_OK;
+}
+
+extern "C" int gcme_build_cells_noalloc(const gcme_params *p, int64_t n, const double *d_pos,
+                                        const double *d_q, int32_t *d_cell_start,
+                                        int32_t *d_sorted_idx, gcme_stream_t stream) {
+  if (!d_pos || !d_q || !d_cell_start || !d_sorted_idx) {
+    set_error("invalid argument to gcme_build_cells_noalloc");
+    return GCME_ERR_INVALID;
+  }
+  SysDesc S{};
+  long long ncell = 0;
+  int rc = noalloc_geometry(p, n, S, ncell);
+  if (rc) return rc;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) {
@@ -129,7 +167,7 @@ extern "C" int gcme_build_cells_noalloc(const gcme_params *p, int64_t n, const d
     return GCME_ERR_CUDA;
   }
   unsigned char *base = nullptr;
-  int rc = noalloc_scratch(dev, &base);
+  rc = noalloc_scratch(dev, &base);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   Pool Q{};
@@ -152,22 +190,22 @@ extern "C" int gcme_build_cells_noalloc(const gcme_params *p, int64_t n, const d
   Q.n_real = n;
   Q.n_ext = n;
   Q.n_cells = ncell;
-  // every call shares the scratch: the descriptor and the per-bead and
-  // per-cell system tables (all zero for one system) are rewritten here,
-  // the cell counts are cleared by launch_cells
-#define NA_CK(call)                                                      \
-  do {                                                                   \
-    cudaError_t _e = (call);                                             \
-    if (_e != cudaSuccess) {                                             \
-      set_error(std::string(#call) + ": " + cudaGetErrorString(_e));     \
-      return GCME_ERR_CUDA;                                              \
-    }                                                                    \
-  } while (0)
-  NA_CK(cudaMemcpyAsync(base + kOffDesc, &S, sizeof(SysDesc), cudaMemcpyHostToDevice, st));
-  NA_CK(cudaMemsetAsync(Q.ext_sys, 0, sizeof(int) * n, st));
-  NA_CK(cudaMemsetAsync(Q.cell_sys, 0, sizeof(int) * ncell, st));
+  // every call shares the scratch: the descriptor and the system tables are
+  // rewritten here, the cell counts are cleared by launch_cells
+  const long long span = std::max<long long>(n, ncell);
+  const int nb = (int)std::min<long long>(1024, (span + 255) / 256);
+  k_noalloc_init<<<nb, 256, 0, st>>>(S, reinterpret_cast<SysDesc *>(base + kOffDesc), Q.ext_sys,
+                                      (int)n, Q.cell_sys, (int)ncell);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("k_noalloc_init: ") + cudaGetErrorString(e));
+    return GCME_ERR_CUDA;
+  }
   launch_cells(Q, st);
-  NA_CK(cudaGetLastError());
-#undef NA_CK
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("gcme_build_cells_noalloc: ") + cudaGetErrorString(e));
+    return GCME_ERR_CUDA;
+  }
   return GCME_OK;
 }

@@ -16,15 +16,18 @@
 //   d_a = fl(fl(x_j,a - x_i,a) + fl(n_a L_a)),
 //   r2 = fl(fl(fl(d_x^2) + fl(d_y^2)) + fl(d_z^2)),  in iff r2 < fl(rc^2).
 //
-// FP32 path: one CTA of 128 threads per (home cell, z-offset) work item.
-// The 9 neighbour cells of that z-slab are staged in shared memory as
-// float4 (x, y, z, q) and every thread (one home bead) streams over them.
-// Within a cell the images, charged and neutral beads are contiguous, so the
-// core loop runs over the real beads and the electrostatic loop over the
-// charged ones without per-pair class tests; the core is evaluated for every
-// candidate (masked), the electrostatics only for the hits of a 64-bit
-// in-cutoff mask.  Forces are summed in FP32 per thread, then added to the
-// 64-bit fixed-point accumulators; energies are reduced per warp in FP64.
+// FP32 path (27-cell stencil): one work item is a home cell and 3 (or 9) of
+// its neighbour cells; a CTA of 128-192 threads stages the item's
+// candidates in shared memory and splits into roles: Gaussian-core warps
+// (one home bead per lane, two candidates per packed FP32x2 instruction over
+// coordinate arrays) and 1-3 electrostatics warps (the charged home beads
+// over the charged and image candidates, a 64-bit in-cutoff mask per 64
+// candidates, then the real-space term from a per-system table for the
+// hits only).  Within a cell the images, charged and neutral beads are
+// contiguous, so no per-pair class test is needed.  Forces are summed in
+// FP32 per lane and added to 64-bit fixed-point accumulators; each lane's
+// energy and virial partials are rounded to 2^-32 fixed point and summed as
+// integers (order-independent, no FP64 arithmetic).
 #pragma once
 #include "common.cuh"
 

@@ -56,7 +56,7 @@ size_t footprint(const SysSpec &sp) {
   long long ne = n + nimg, nqe = nq + nimg;
   long long ncell = 1;
   for (int a = 0; a < 3; ++a)
-    ncell *= std::max(1, (int)std::floor(p.box[a] / (p.rc * (1.0 + 1e-4))));
+    ncell *= cells_per_axis(p.box[a], p.rc, 1);
   long long G = (long long)p.K[0] * p.K[1] * p.K[2];
   bool f64 = p.precision == GCME_FP64;
   size_t b = 0;

@@ -164,3 +164,32 @@ def test_null_handles_are_rejected(g):
     assert lib.gcme_batch_phase_timing(None, 0) == -1
     assert lib.gcme_step_phase_ms(None, None, 0, None) == -1
     assert lib.gcme_batch_phase_ms(None, None, 0, None) == -1
+
+
+def test_noalloc_size_query_is_host_only(g):
+    """gcme_cells_noalloc_size follows the cell rule of the header,
+    ncell = prod_a max(1, floor(L_a / ((rc / f) (1 + 1e-4)))), for both cell
+    factors, rejects what the allocation-free build rejects, and makes no
+    CUDA call (it runs here without a device)."""
+    import math
+    for s in (synth.make_polyelectrolyte(20, 25, 4000, seed_index=60, K=(24, 24, 24)),
+              synth.make_slab_fluid(synth.GEOM_SLAB_NM, 2500, charged_frac=0.2, seed_index=61)):
+        for f in (0, 1, 2):
+            p = g.params_from(s, cell_factor=f)
+            want = 1
+            for a in range(3):
+                want *= max(1, math.floor(s.box[a] / ((s.rc / (f or 1)) * (1.0 + 1e-4))))
+            assert g.cells_noalloc_size(p, s.n) == want
+    s = synth.make_bulk(1000, seed_index=62)
+    with pytest.raises(g.GcmeError, match="exceeds the maximum"):
+        g.cells_noalloc_size(g.params_from(s), 70000)
+    with pytest.raises(g.GcmeError, match="image-charge"):
+        g.cells_noalloc_size(g.params_from(synth.make_slab_fluid(synth.GEOM_SLAB_PC, 900)), 900)
+    p = g.params_from(s)
+    p.cell_factor = 3
+    with pytest.raises(g.GcmeError, match="cell_factor"):
+        g.cells_noalloc_size(p, s.n)
+    p = g.params_from(s)
+    p.box[0] = 1e6
+    with pytest.raises(g.GcmeError, match="cells"):
+        g.cells_noalloc_size(p, s.n)
