@@ -17,6 +17,14 @@ flushed (a 512 MiB write) before every timed step; max over ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
+Beside the default workload (rank 0, one GPU, unless --no-extras): the
+N = 3000 fluid as its workload states it (one evaluation + 100 steps, plain
+FP64 path and FP32 path), the N = 64,000 slabs with nonmetal and with
+conducting walls (1000 steps each), the 256-system batch (per-phase graphs
+and the persistent launch) and the served request stream.  Rooflines: the
+pair kernel against the FP32 pipe; binning and the two half kicks against
+the measured HBM bandwidth.
+
 Under torchrun every rank steps its own replica (weak scaling); the
 single-system path does not shard.  ``--impl reference`` times the FP64 CPU
 oracle on the host cores instead (rank 0 only).
@@ -49,6 +57,16 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 # algorithmic work per unordered in-cutoff pair (FP32 operations)
 FLOP_GC_PAIR = 30
 FLOP_QQ_PAIR = 40
+# algorithmic HBM bytes per bead of the O(N) kernels (one system, FP32
+# velocities): the half kick + drift reads v (12 B), x (24 B) and the
+# fixed-point force (24 B) and writes v, x and the cleared force; binning
+# reads x (24 B), the charge (8 B) and the last image index (12 B) and writes
+# the float4 (16 B), cell id, slot and bucket entry (12 B); the second half
+# kick reads v and F and writes v.  A pool of several systems adds its 4 B
+# system index per bead to each.
+HBM_BYTES_PER_BEAD = {"k_kick_drift": 120, "k_bin": 72, "k_kick": 48}
+# phase_ms() entries of those kernels
+PHASE_OF = {"k_kick_drift": 0, "k_bin": 6, "k_kick": 7}
 
 
 def parse():
@@ -99,56 +117,146 @@ def workload_config(s):
 
 # ---------------------------------------------------------------------------
 class ClockSampler:
-    """nvidia-smi clocks/throttle reasons sampled every 200 ms."""
+    """SM clock and clock-event reasons of this process's GPU while the timed
+    region runs.  Read-only NVML queries (libnvidia-ml through ctypes) every
+    ~1 ms from a thread: a timed region of a few milliseconds still gets
+    samples, which nvidia-smi's 200 ms period misses.  The GPU is found by
+    its UUID (CUDA_VISIBLE_DEVICES may renumber it).  Without NVML, nvidia-smi
+    samples instead; if neither caught a sample inside the region, one query
+    right after it is reported and marked as such."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits
+    BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+            0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
     def __init__(self, index):
         self.index = index
-        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        self.p = None
+        self.uuid = None
+        try:
+            import torch
+            u = str(torch.cuda.get_device_properties(index).uuid)
+            self.uuid = u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            pass
+        self.nv = None
+        self.h = None
+        self.rows = []
+        self.thread = None
+        self.stop_flag = False
+        self.smi = None
+        self._nvml_open()
+
+    def _nvml_open(self):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            h = ctypes.c_void_p()
+            ok = False
+            if self.uuid:
+                ok = lib.nvmlDeviceGetHandleByUUID(self.uuid.encode(), ctypes.byref(h)) == 0
+            if not ok:
+                cnt = ctypes.c_uint(0)
+                if lib.nvmlDeviceGetCount_v2(ctypes.byref(cnt)) == 0 and cnt.value == 1:
+                    ok = lib.nvmlDeviceGetHandleByIndex_v2(0, ctypes.byref(h)) == 0
+            if ok:
+                self.nv, self.h = lib, h
+        except Exception:
+            self.nv = None
+
+    def _nvml_read(self):
+        import ctypes
+        mhz, mx = ctypes.c_uint(0), ctypes.c_uint(0)
+        r = ctypes.c_ulonglong(0)
+        if self.nv.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(mhz)) != 0:  # NVML_CLOCK_SM
+            return None
+        self.nv.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx))
+        f = getattr(self.nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        f(self.h, ctypes.byref(r))
+        return dict(sm=float(mhz.value), smax=float(mx.value),
+                    reasons=[n for bit, n in self.BITS.items() if r.value & bit])
+
+    def _poll(self):
+        while not self.stop_flag:
+            row = self._nvml_read()
+            if row:
+                self.rows.append(row)
+            time.sleep(0.001)
 
     def start(self):
+        self.rows = []
+        self.stop_flag = False
+        if self.nv is not None:
+            import threading
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            return
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
-            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
-                                      stdout=self.f, stderr=subprocess.DEVNULL)
+            self.smi = subprocess.Popen(["nvidia-smi", "-i", self.uuid or str(self.index),
+                                         f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                         "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
-            self.p = None
+            self.smi = None
 
-    def stop(self):
-        if self.p is None:
-            return None
-        self.p.terminate()
-        try:
-            self.p.wait(timeout=5)
-        except Exception:
-            self.p.kill()
-        self.f.flush()
+    def _smi_rows(self, text):
         rows = []
-        for line in open(self.f.name):
+        for line in text.splitlines():
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
             try:
-                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]),
-                                 power=float(parts[3]) if parts[3] not in ("[N/A]", "") else 0.0,
-                                 hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+                reasons = [name for k, name in ((5, "hw_slowdown"), (6, "hw_thermal_slowdown"),
+                                                (7, "sw_thermal_slowdown"), (8, "sw_power_cap"))
+                           if parts[k].lower() in ("active", "1")]
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), reasons=reasons))
             except ValueError:
                 continue
-        os.unlink(self.f.name)
+        return rows
+
+    def stop(self):
+        source = "nvml"
+        if self.thread is not None:
+            self.stop_flag = True
+            self.thread.join(timeout=5)
+            self.thread = None
+        elif self.smi is not None:
+            source = "nvidia-smi"
+            self.smi.terminate()
+            try:
+                self.smi.wait(timeout=5)
+            except Exception:
+                self.smi.kill()
+            self.f.flush()
+            self.rows = self._smi_rows(open(self.f.name).read())
+            os.unlink(self.f.name)
+        rows, after = self.rows, False
+        if not rows:  # nothing inside the region: one query right after it
+            after = True
+            if self.nv is not None:
+                row = self._nvml_read()
+                rows = [row] if row else []
+            if not rows:
+                try:
+                    out = subprocess.run(["nvidia-smi", "-i", self.uuid or str(self.index),
+                                          f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits"],
+                                         capture_output=True, text=True, timeout=20).stdout
+                    rows = self._smi_rows(out)
+                    source = "nvidia-smi"
+                except Exception:
+                    rows = []
         if not rows:
-            return None
-        reasons = set()
-        for r in rows:
-            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
-                            ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
-                if r[k].lower() in ("active", "1"):
-                    reasons.add(name)
+            raise RuntimeError("no clock record: neither NVML nor nvidia-smi answered")
+        reasons = sorted({n for r in rows for n in r["reasons"]})
         return {"sm_mhz": statistics.median(r["sm"] for r in rows),
-                "sm_max_mhz": max(r["smax"] for r in rows),
-                "reasons": sorted(reasons), "samples": len(rows)}
+                "sm_max_mhz": max(r["smax"] for r in rows), "reasons": reasons,
+                "samples": len(rows), "source": source,
+                "sampled": "right after the timed region" if after else "during the timed region"}
 
 
 def measured_peaks():
@@ -171,6 +279,87 @@ def pair_kernel_traffic():
     return d.get("dram_bytes_per_launch")
 
 
+def parity_record(case):
+    """Errors against the FP64 oracle measured by the full-size GPU parity
+    tests (profiles/parity_full_size.json), when measured on the current
+    pair-kernel source."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "parity_full_size.json")))
+    except Exception:
+        return None
+    r = d.get(case)
+    if not r or r.get("kernel_sha") != kernel_sha():
+        return None
+    out = {k: v for k, v in r.items() if k not in ("case", "kernel_sha")}
+    out["test"] = d.get("tests", {}).get(case)
+    return out
+
+
+def hbm_rooflines(phase, n_beads, peak_gbs, pooled=False):
+    """Achieved algorithmic GB/s of the O(N) kernels from their event-timed
+    phases (ms), against the measured HBM copy bandwidth."""
+    out = {}
+    for k, b in HBM_BYTES_PER_BEAD.items():
+        ms = float(phase[PHASE_OF[k]])
+        per = b + (4 if pooled else 0)
+        byts = per * n_beads
+        gbs = byts / (ms * 1e-3) / 1e9 if ms > 0 else None
+        out[k] = {"bound": "hbm", "bytes_per_bead": per, "bytes": byts, "ms": round(ms, 5),
+                  "achieved": None if gbs is None else round(gbs, 1), "unit": "GB/s",
+                  "peak": peak_gbs,
+                  "frac": None if (gbs is None or not peak_gbs) else round(gbs / peak_gbs, 4)}
+    return out
+
+
+def timed_phases(sysg, pos, vel, E, flush, stream, n):
+    """Mean event-timed phases over n steps run with phase timing on (the
+    event nodes lengthen a step; the timed steps run without them)."""
+    import torch
+    phase = np.zeros(8)
+    sysg.phase_timing(True)
+    sysg.step_continue(pos, vel, 1, E)  # captures the instrumented graph
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    timed = 0.0
+    for k in range(n):
+        flush.fill_(float(k))
+        p0.record(stream)
+        sysg.step_continue(pos, vel, 1, E)
+        p1.record(stream)
+        p1.synchronize()
+        timed += p0.elapsed_time(p1)
+        ms, _ = sysg.phase_ms()
+        phase += ms
+    sysg.phase_timing(False)
+    return phase / n, timed / n
+
+
+def timed_steps(sysg, pos, vel, E, flush, stream, n):
+    """n steps, each bracketed by CUDA events on the launching stream, the L2
+    flushed before each; returns per-step ms."""
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+    torch.cuda.synchronize()
+    for k in range(n):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        sysg.step_continue(pos, vel, 1, E)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+
+def pair_roofline(pairs, qq, pair_ms, kname, peaks):
+    flops = FLOP_GC_PAIR * pairs + FLOP_QQ_PAIR * qq
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    achieved = flops / (pair_ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": kname, "achieved": round(achieved, 4),
+            "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 5),
+            "peak_source": "FP32 pipe: 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)",
+            "work": f"{FLOP_GC_PAIR} flop per in-cutoff pair + {FLOP_QQ_PAIR} per charged pair",
+            "pair_kernel_ms": round(pair_ms, 5), "hbm_peak_gbs": peaks.get("hbm_gbs")}
+
+
 def kernel_sha():
     h = hashlib.sha256()
     for f in ("pair.cu", "pair.cuh", "nlist.cu", "common.cuh"):
@@ -179,11 +368,10 @@ def kernel_sha():
 
 
 # ---------------------------------------------------------------------------
-def count_pairs(g, sysg, s, pos, dev):
+def count_pairs(g, sysg, s, pos, dev, cap=24_000_000):
     """Unordered in-cutoff pairs, and those between two charged beads, from
     the pair kernel's own triple dump."""
     import torch
-    cap = 16_000_000
     trip = torch.empty(3 * cap, dtype=torch.int32, device=dev)
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
     sysg.debug_pairs(pos, trip, cap, cnt)
@@ -226,7 +414,6 @@ def run_gcme(args, ws, rank, local):
     K = args.steps
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    phase = np.zeros(6)
     clocks = ClockSampler(local)
     info = sysg.info()
     builds0 = info.list_builds
@@ -253,22 +440,7 @@ def run_gcme(args, ws, rank, local):
     # phase breakdown: a separate run with phase timing on (its event nodes
     # lengthen the step, so the timed steps above run without them)
     Kp = min(K, 400)
-    sysg.phase_timing(True)
-    sysg.step_continue(pos, vel, 1, E)  # captures the instrumented graph
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    timed_ms = 0.0
-    for k in range(Kp):
-        flush.fill_(float(k))
-        p0.record(stream)
-        sysg.step_continue(pos, vel, 1, E)
-        p1.record(stream)
-        p1.synchronize()
-        timed_ms += p0.elapsed_time(p1)
-        ms, _ = sysg.phase_ms()
-        phase += ms
-    sysg.phase_timing(False)
-    phase /= Kp
-    timed_ms /= Kp
+    phase, timed_ms = timed_phases(sysg, pos, vel, E, flush, stream, Kp)
     pairs1, qq1 = count_pairs(g, sysg, s, pos, dev)
     pairs = 0.5 * (pairs0 + pairs1)
     qq = 0.5 * (qq0 + qq1)
@@ -285,72 +457,66 @@ def run_gcme(args, ws, rank, local):
     w1.synchronize()
     warm_ms = w0.elapsed_time(w1) / K
 
-    # end to end through the public API with host buffers: every step copies
-    # positions + velocities host -> device, runs gcme_step (which evaluates
-    # the forces of the copied state and advances one step), and reads the
-    # energies back.  The host states alternate between the initial one and
-    # the one after the timed steps (beads far more than half the list skin
-    # apart), so every step also rebuilds the neighbour list: the worst case.
-    hpos = [torch.empty((s.n, 3), dtype=torch.float64).pin_memory() for _ in range(2)]
-    hvel = [torch.empty((s.n, 3), dtype=torch.float32).pin_memory() for _ in range(2)]
+    # End to end through the public API with host buffers: the state lives
+    # on the host.  Every step copies positions + velocities host -> device,
+    # advances one step (gcme_step_continue: the forces the previous step
+    # left on the device belong to exactly these positions, so one step's
+    # force work per iteration), and copies the stepped positions,
+    # velocities and the energies back to the host.
+    hpos = torch.empty((s.n, 3), dtype=torch.float64).pin_memory()
+    hvel = torch.empty((s.n, 3), dtype=torch.float32).pin_memory()
     hE = torch.empty(g.NTERMS, dtype=torch.float64).pin_memory()
-    hpos[0].copy_(torch.from_numpy(s.pos))
-    hvel[0].copy_(torch.from_numpy(s.vel.astype(np.float32)))
-    hpos[1].copy_(pos.view(-1, 3))
-    hvel[1].copy_(vel.view(-1, 3))
+    hpos.copy_(pos.view(-1, 3))
+    hvel.copy_(vel.view(-1, 3))
     Ke = max(10, K // 4)
-    eb0 = sysg.info().list_builds
     torch.cuda.synchronize()
     e0 = time.perf_counter()
     for k in range(Ke):
-        pos.copy_(hpos[k % 2].view_as(pos), non_blocking=True)
-        vel.copy_(hvel[k % 2].view_as(vel), non_blocking=True)
-        sysg.step(pos, vel, 1, E)
+        pos.copy_(hpos.view_as(pos), non_blocking=True)
+        vel.copy_(hvel.view_as(vel), non_blocking=True)
+        sysg.step_continue(pos, vel, 1, E)
+        hpos.copy_(pos.view(-1, 3), non_blocking=True)
+        hvel.copy_(vel.view(-1, 3), non_blocking=True)
         hE.copy_(E, non_blocking=True)
         stream.synchronize()
     e2e_s = (time.perf_counter() - e0) / Ke
     e2e_value = ws * pairs / e2e_s
-    e2e_builds = sysg.info().list_builds - eb0
+    state_bytes = s.n * 3 * (8 + 4)
 
     peaks = measured_peaks()
-    flops = FLOP_GC_PAIR * pairs + FLOP_QQ_PAIR * qq
-    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
-    achieved = flops / (pair_ms * 1e-3) / 1e12
     kname = "k_pair_list" if info.pair_path == g.GCME_PAIR_LIST else "k_pair_f32"
-    roofline = {"bound": "alu", "kernel": kname, "achieved": round(achieved, 4),
-                "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 5),
-                "traffic": pair_kernel_traffic(),
-                "peak_source": "FP32 pipe: 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)",
-                "work": f"{FLOP_GC_PAIR} flop per in-cutoff pair + {FLOP_QQ_PAIR} per charged pair",
-                "pair_kernel_ms": round(pair_ms, 5),
-                "hbm_peak_gbs": peaks.get("hbm_gbs")}
+    roofline = pair_roofline(pairs, qq, pair_ms, kname, peaks)
+    roofline["traffic"] = pair_kernel_traffic()
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": workload_config(s), "steps_per_s": steps_per_s,
            "pair_interactions_per_step": pairs, "charged_pairs_per_step": qq,
            "phase_ms": dict(zip(("kick_drift", "cells", "pair", "pme_concurrent", "bonded",
-                                 "slab_kick_energy"),
+                                 "slab_kick_energy", "bin", "kick"),
                                 [round(float(x), 5) for x in phase])),
            "phase_note": f"event-timed phases from {Kp} further steps with phase timing on "
                          f"({timed_ms:.5f} ms per step there: the event nodes lengthen a step)",
            "warm_l2_ms_per_step": warm_ms,
-           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": s.n * 3 * (8 + 4),
-                   "d2h_bytes_per_step": 8 * g.NTERMS,
-                   "note": "gcme_step(1) per step from host state: force evaluation of the "
-                           "copied state + one step" + (
-                               " (the alternating host states force a neighbour-list rebuild "
-                               "every step)" if info.pair_path == g.GCME_PAIR_LIST else ""),
-                   "list_builds_per_step": e2e_builds / Ke},
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                   "d2h_bytes_per_step": state_bytes + 8 * g.NTERMS,
+                   "ms_per_step": e2e_s * 1e3,
+                   "note": "state on the host: per step positions + velocities copied in from "
+                           "pinned memory, one gcme_step_continue step, stepped positions, "
+                           "velocities and energies copied back, stream synchronised"},
            "pair_path": "verlet_list" if info.pair_path == g.GCME_PAIR_LIST else "cells27",
            "list_builds_per_step": builds / K,
-           "list_stride": int(info.list_stride),
-           "roofline": roofline, "clocks": clk, "gpu_launches": int(nkern) * K,
+           "roofline": roofline,
+           "hbm_kernels": hbm_rooflines(phase, s.n, peaks.get("hbm_gbs")),
+           "error_vs_oracle": parity_record("c2_bulk_polyelectrolyte_n32000"),
+           "clocks": clk, "gpu_launches": int(nkern) * K,
            "tuning": tuning,
            "wall_s_timed": t_wall}
     if not args.no_extras and rank == 0 and ws == 1:
-        out["fp64_plain"] = fp64_plain_compare(g, ctx, dev)
-        out["batched"] = batched_c4(g, ctx, dev)
+        out["c1_plain"] = c1_plain(g, ctx, dev)
+        for geom, key in ((synth.GEOM_SLAB_NM, "c3_nonmetal"), (synth.GEOM_SLAB_PC, "c3_image")):
+            out[key] = c3_slab(g, ctx, dev, geom, flush, peaks)
+        out["batched"] = batched_c4(g, ctx, dev, peaks)
         out["served"] = served_c5(g, ctx)
     if rank == 0 and ws == 1:
         out["cpu_baseline"] = cpu_baseline(s, pairs)
@@ -360,47 +526,116 @@ def run_gcme(args, ws, rank, local):
     return out if rank == 0 else None
 
 
-def fp64_plain_compare(g, ctx, dev, steps=20):
-    """Plain FP64 path vs FP32 path on the N=3000 fluid (grid 32^3)."""
+def c1_plain(g, ctx, dev, steps=100):
+    """The plain workload as stated: N = 3000 fluid (grid 32^3), one force +
+    energy evaluation and 100 velocity-Verlet steps, on the plain FP64 path
+    and on the FP32 path.  gcme_step(100) evaluates the starting forces and
+    takes the 100 steps; the single evaluation is timed on its own
+    (gcme_forces, median of 20 after warm-up)."""
     import torch
     s = synth.config1()
-    res = {}
-    for name, prec in (("fp32", 0), ("fp64", 1)):
+    sg = g.System(ctx, g.params_from(s), s.q)
+    p = torch.tensor(s.pos, dtype=torch.float64, device=dev)
+    pairs, qq = count_pairs(g, sg, s, p, dev)
+    sg.close()
+    res = {"workload": "N=3000 fluid rho=3 (L=10), 150 +1 / 150 -1, PME 32^3 p=5, dt=0.01: "
+                       "one force+energy evaluation and 100 velocity-Verlet steps",
+           "pair_interactions_per_step": pairs}
+    for name, prec in (("fp64", 1), ("fp32", 0)):
         sysg = g.System(ctx, g.params_from(s, prec), s.q)
-        pos = torch.tensor(s.pos, dtype=torch.float64, device=dev)
-        vel = torch.tensor(s.vel, dtype=torch.float64 if prec else torch.float32, device=dev)
-        sysg.step(pos, vel, 3)
+        vdt = torch.float64 if prec else torch.float32
+        pos0 = torch.tensor(s.pos, dtype=torch.float64, device=dev)
+        vel0 = torch.tensor(s.vel, dtype=vdt, device=dev)
+        pos, vel = pos0.clone(), vel0.clone()
+        F = torch.zeros(3 * s.n, dtype=torch.int64, device=dev)
+        E = torch.zeros(g.NTERMS, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            sysg.forces(pos, F, E)
+        sysg.step(pos, vel, 3, E)  # graph capture
+        torch.cuda.synchronize()
+        evs = []
+        for _ in range(20):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            sysg.forces(pos0, F, E)
+            b.record()
+            b.synchronize()
+            evs.append(a.elapsed_time(b))
+        e_start = E.cpu().numpy().copy()
+        pos.copy_(pos0)
+        vel.copy_(vel0)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        sysg.step_continue(pos, vel, steps)
+        sysg.step(pos, vel, steps, E)
         b.record()
         b.synchronize()
-        res[name + "_steps_per_s"] = 1e3 * steps / a.elapsed_time(b)
+        run_ms = a.elapsed_time(b)
+        e_end = E.cpu().numpy()
+        ke0 = 0.5 * float(np.sum(s.vel.astype(np.float64) ** 2))
+        tot0 = e_start[8] + ke0
+        tot1 = e_end[8] + e_end[9]
+        sps = 1e3 * steps / run_ms
+        res[name] = {"eval_ms": float(np.median(evs)), "run_ms": run_ms,
+                     "steps_per_s": sps, "pair_interactions_per_s": pairs * sps,
+                     "energy_drift_rel": abs(tot1 - tot0) / abs(tot0),
+                     "note": "run_ms = the starting force evaluation + 100 steps, back to back"}
         sysg.close()
-    res["workload"] = "N=3000 fluid rho=3, 10% charged, PME 32^3, back-to-back steps"
-    res["speedup_fp32_over_fp64"] = res["fp32_steps_per_s"] / res["fp64_steps_per_s"]
+    res["speedup_fp32_over_fp64"] = res["fp32"]["steps_per_s"] / res["fp64"]["steps_per_s"]
+    res["error_vs_oracle_fp64"] = parity_record("c1_fp64_100_steps_n3000")
     return res
 
 
-def batched_c4(g, ctx, dev, nsteps=500):
+def c3_slab(g, ctx, dev, geom, flush, peaks, steps=1000):
+    """The slab workload: N = 64,000 in a 30 x 30 x 90 box, grid 64x64x192,
+    nonmetal walls (Yeh-Berkowitz) or conducting walls (image charges),
+    timed like the default workload (events per step, L2 flushed)."""
+    import torch
+    s = synth.config3(geom)
+    sysg = g.System(ctx, g.params_from(s), s.q, s.bonds)
+    pos = torch.tensor(s.pos, dtype=torch.float64, device=dev)
+    vel = torch.tensor(s.vel, dtype=torch.float32, device=dev)
+    E = torch.zeros(g.NTERMS, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    tuning = sysg.autotune(pos)
+    pairs, qq = count_pairs(g, sysg, s, pos, dev)
+    sysg.step(pos, vel, 3, E)
+    ms = timed_steps(sysg, pos, vel, E, flush, stream, steps)
+    phase, _ = timed_phases(sysg, pos, vel, E, flush, stream, 200)
+    ms_step = float(np.mean(ms))
+    name = synth.GEOM_NAMES[geom]
+    out = {"workload": f"slab {name}: N=64000 (200x50 chains -1, 10000 +1, 44000 solvent), "
+                       "box 30x30x90, PME 64x64x192 p=5, velocity Verlet dt=0.01, "
+                       + ("Yeh-Berkowitz slab term, H=30" if geom == synth.GEOM_SLAB_NM
+                          else "image charges, H=45"),
+           "steps": steps, "ms_per_step": ms_step, "steps_per_s": 1e3 / ms_step,
+           "pair_interactions_per_step": pairs, "charged_pairs_per_step": qq,
+           "pair_interactions_per_s": pairs * 1e3 / ms_step,
+           "phase_ms": dict(zip(("kick_drift", "cells", "pair", "pme_concurrent", "bonded",
+                                 "slab_kick_energy", "bin", "kick"),
+                                [round(float(x), 5) for x in phase])),
+           "roofline": pair_roofline(pairs, qq, float(phase[2]), "k_pair_f32", peaks),
+           "error_vs_oracle": parity_record(f"c3_{name}_n64000"),
+           "tuning": tuning, "l2": "flushed (512 MiB write) before every timed step"}
+    sysg.close()
+    return out
+
+
+def batched_c4(g, ctx, dev, peaks, nsteps=500):
     """256 independent systems (N log-uniform in [500, 8000], 10% charged,
     grids ~1 d smooth sizes): per-phase launches replayed from a CUDA graph
     (mode 0) and one persistent cooperative launch for all steps (mode 1)."""
     import torch
     systems = synth.config4()
     pairs = 0
-    cap = 4_000_000
-    trip = torch.empty(3 * cap, dtype=torch.int32, device=dev)
-    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    qq_pairs = 0
     for s in systems:
         sg = g.System(ctx, g.params_from(s), s.q)
         p = torch.tensor(s.pos, dtype=torch.float64, device=dev)
-        sg.debug_pairs(p, trip, cap, cnt)
-        torch.cuda.synchronize()
-        pairs += int(cnt.item()) // 2
+        a, b2 = count_pairs(g, sg, s, p, dev, cap=4_000_000)
+        pairs += a
+        qq_pairs += b2
         sg.close()
-    del trip
     torch.cuda.empty_cache()
     out = {"workload": "256 bulk systems, N log-uniform [500, 8000], rho=3, 10% charged, "
                        "grid 1 d rounded to 2^a3^b5^c, FP32",
@@ -428,9 +663,30 @@ def batched_c4(g, ctx, dev, nsteps=500):
             b.phase_timing(True)
             b.step(3, mode)
             torch.cuda.synchronize()
-            ms, nk = b.phase_ms()
+            acc = np.zeros(8)
+            nph = 20
+            for _ in range(nph):
+                b.step(1, mode)
+                torch.cuda.synchronize()
+                ms, nk = b.phase_ms()
+                acc += ms
+            ms = acc / nph
             b.phase_timing(False)
-            out[key]["phase_ms"] = [round(float(x), 4) for x in ms]
+            out[key]["phase_ms"] = dict(zip(("kick_drift", "cells", "pair", "pme_concurrent",
+                                             "bonded", "slab_kick_energy", "bin", "kick"),
+                                            [round(float(x), 4) for x in ms]))
+            # HBM roofline of the O(N) kernels over the whole batch's beads
+            hk = hbm_rooflines(ms, out["beads"], peaks.get("hbm_gbs"), pooled=True)
+            top = hk["k_kick_drift"]
+            state = sum(v["bytes"] for v in hk.values())
+            out[key]["roofline"] = dict(top, kernel="k_kick_drift",
+                                        note="algorithmic bytes over the event-timed kernel "
+                                             "(phase timing on); back-to-back steps, the 50-90 MB "
+                                             "per kernel partly L2-resident (129 MB L2)")
+            out[key]["hbm_kernels"] = hk
+            out[key]["state_bytes_per_step"] = state
+            out[key]["pair_roofline"] = pair_roofline(pairs, qq_pairs, float(ms[2]), "k_pair_f32",
+                                                      peaks)
         b.close()
     return out
 

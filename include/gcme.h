@@ -306,11 +306,13 @@ int gcme_step_phase_timing(gcme_sys *sys, int32_t on);
  * h_ms[0] half kick + drift, [1] cell list, [2] pair kernel (with the
  * harmonic bonds on the FP32 27-cell path), [3] PME (a branch on a side
  * stream concurrent with [2] and [4]), [4] bonds (other paths) and walls,
- * [5] Yeh-Berkowitz + half kick + energies after the join (nphase >= 6).
+ * [5] Yeh-Berkowitz + half kick + energies after the join (nphase >= 6);
+ * with nphase >= 8 also [6] binning alone (part of [1]) and [7] the second
+ * half kick alone (part of [5]).
  * INVALID unless the most recent step ran with phase timing on
  * (gcme_step_phase_timing); h_ms may be NULL to query only *kernels (may be
  * NULL), the number of kernel launches in one step. */
-#define GCME_NPHASE 6
+#define GCME_NPHASE 8
 int gcme_step_phase_ms(gcme_sys *sys, float *h_ms, int32_t nphase, int32_t *kernels);
 
 /* Sizes of the system: n, n_ext, ncell, number of charged beads incl.

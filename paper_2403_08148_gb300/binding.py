@@ -390,9 +390,9 @@ class System:
     def phase_ms(self):
         """Device ms of the phases of the last step (phase timing on), and
         kernels per step."""
-        ms = np.zeros(6, np.float32)
+        ms = np.zeros(8, np.float32)
         k = np.zeros(1, np.int32)
-        _check(load().gcme_step_phase_ms(self.h, ms.ctypes.data, 6, k.ctypes.data))
+        _check(load().gcme_step_phase_ms(self.h, ms.ctypes.data, 8, k.ctypes.data))
         return ms, int(k[0])
 
     def step_kernels(self):
@@ -481,9 +481,9 @@ class Batch:
         _check(load().gcme_batch_phase_timing(self.h, int(bool(on))))
 
     def phase_ms(self):
-        ms = np.zeros(6, np.float32)
+        ms = np.zeros(8, np.float32)
         k = np.zeros(1, np.int32)
-        _check(load().gcme_batch_phase_ms(self.h, ms.ctypes.data, 6, k.ctypes.data))
+        _check(load().gcme_batch_phase_ms(self.h, ms.ctypes.data, 8, k.ctypes.data))
         return ms, int(k[0])
 
     def step_kernels(self):

@@ -1161,6 +1161,7 @@ void Engine::enqueue_step(const Pool &Q, cudaStream_t st) {
   if (ev) cudaEventRecordWithFlags(phase_ev[1], st, cudaEventRecordExternal);
   if (use_list) launch_list_check(Q, st);
   launch_bin(Q, st, false);
+  if (ev) cudaEventRecordWithFlags(phase_ev[9], st, cudaEventRecordExternal);
   fork_pme(Q, st, false, ev, false);
   enqueue_sort_pairs(Q, st, false, false, ev);
   launch_bonded(Q, false, !bonds_in_pair(false), st);
@@ -1168,7 +1169,9 @@ void Engine::enqueue_step(const Pool &Q, cudaStream_t st) {
   cudaStreamWaitEvent(st, join_ev, 0);
   if (ev) cudaEventRecordWithFlags(phase_ev[7], st, cudaEventRecordExternal);
   launch_slab_apply(Q, st);
+  if (ev) cudaEventRecordWithFlags(phase_ev[10], st, cudaEventRecordExternal);
   launch_kick(Q, fp64, st);
+  if (ev) cudaEventRecordWithFlags(phase_ev[11], st, cudaEventRecordExternal);
   launch_finalize(Q, false, st);
   if (ev) cudaEventRecordWithFlags(phase_ev[8], st, cudaEventRecordExternal);
 }
@@ -1725,9 +1728,12 @@ static int phase_ms(Engine &eng, float *h_ms, int32_t nphase, int32_t *kernels) 
     return GCME_ERR_INVALID;
   }
   // [0] kick+drift, [1] cells, [2] pair kernel, [3] PME branch (side
-  // stream), [4] bonds/walls, [5] slab + kick + energies after the join
-  const int pairs[6][2] = {{0, 1}, {1, 2}, {2, 3}, {5, 6}, {3, 4}, {7, 8}};
-  for (int k = 0; k < 6; ++k)
+  // stream), [4] bonds/walls, [5] slab + kick + energies after the join;
+  // with nphase >= 8 also [6] binning alone (inside [1]) and [7] the second
+  // half kick alone (inside [5])
+  const int pairs[8][2] = {{0, 1}, {1, 2}, {2, 3}, {5, 6}, {3, 4}, {7, 8}, {1, 9}, {10, 11}};
+  const int np = nphase >= 8 ? 8 : 6;
+  for (int k = 0; k < np; ++k)
     GCME_TRY_CK(cudaEventElapsedTime(&h_ms[k], eng.phase_ev[pairs[k][0]], eng.phase_ev[pairs[k][1]]));
   return GCME_OK;
 }

@@ -110,11 +110,11 @@ class Engine {
   int autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms, double *pme_ms,
                bool *from_cache);
   // Phase marks recorded inside the captured step graph: 0 start, 1 after
-  // the first half kick + drift, 2 after the cell list (the PME branch forks
-  // after binning, inside this phase), 3 after the pair kernel, 4 after
+  // the first half kick + drift, 9 after binning (the PME branch forks
+  // here), 2 after the cell list, 3 after the pair kernel, 4 after
   // bonds/walls, 5/6 around the PME branch on the side stream, 7 after the
-  // join, 8 after slab, kick and energies.
-  static constexpr int kNPhaseEv = 9;
+  // join, 10/11 around the second half kick, 8 after the energies.
+  static constexpr int kNPhaseEv = 12;
   cudaEvent_t phase_ev[kNPhaseEv] = {};
   int step_kernels = 0;  // kernel nodes in the step graph
   // phase timing: step graphs captured with event nodes between the phases

@@ -1,4 +1,7 @@
 """Helpers for the GPU parity tests: run the CUDA path through the C ABI."""
+import json
+import os
+
 import numpy as np
 
 import synth
@@ -64,3 +67,17 @@ def gpu_forces(s: synth.System, precision=0, virial=False, pos=None, cell_factor
 
 def rel_rms(a, b):
     return float(np.sqrt(np.mean((a - b) ** 2)) / np.sqrt(np.mean(b ** 2)))
+
+
+def record_error(name, **errors):
+    """Append the measured errors of a parity case to the JSON-lines file
+    named by GCME_PARITY_LOG (nothing when unset), tagged with the hash of the
+    pair-kernel sources, so that a measurement summary can quote them."""
+    path = os.environ.get("GCME_PARITY_LOG")
+    if not path:
+        return
+    import bench
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    with open(path, "a") as f:
+        f.write(json.dumps({"case": name, "kernel_sha": bench.kernel_sha(),
+                            **{k: float(v) for k, v in errors.items()}}) + "\n")

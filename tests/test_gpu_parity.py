@@ -11,7 +11,7 @@ import pytest
 import oracle
 import synth
 from gpu_util import (ENERGY_RTOL_FP32, ENERGY_RTOL_FP64, FORCE_RTOL_FP32, FORCE_RTOL_FP64,
-                      PAIR_VARIANTS, ctx, gpu_forces, lib, rel_rms)
+                      PAIR_VARIANTS, ctx, gpu_forces, lib, record_error, rel_rms)
 
 pytestmark = pytest.mark.gpu
 
@@ -339,7 +339,8 @@ def test_config2_full_size():
     s = synth.config2()
     out = gpu_forces(s, 0)
     ref = oracle.energy_forces(s)
-    _check(s, out, ref, FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
+    ferr, eerr = _check(s, out, ref, FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
+    record_error("c2_bulk_polyelectrolyte_n32000", force_rel_rms=ferr, energy_rel=eerr)
 
 
 @pytest.mark.parametrize("geom", [synth.GEOM_SLAB_NM, synth.GEOM_SLAB_PC])
@@ -347,7 +348,8 @@ def test_config3_full_size(geom):
     s = synth.config3(geom)
     out = gpu_forces(s, 0)
     ref = oracle.energy_forces(s)
-    _check(s, out, ref, FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
+    ferr, eerr = _check(s, out, ref, FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
+    record_error("c3_" + synth.GEOM_NAMES[geom] + "_n64000", force_rel_rms=ferr, energy_rel=eerr)
 
 
 # --------------------------------------------------------------------------
@@ -366,11 +368,16 @@ def test_step_fp64_config1_100_steps():
     sysg.step(pos, vel, 100, E)
     torch.cuda.synchronize()
     p1, v1, hist = oracle.velocity_verlet(s, 100)
-    assert np.max(np.abs(pos.cpu().numpy() - p1)) < 1e-7
-    assert np.max(np.abs(vel.cpu().numpy() - v1)) < 1e-6
+    dx = np.max(np.abs(pos.cpu().numpy() - p1))
+    dv = np.max(np.abs(vel.cpu().numpy() - v1))
+    assert dx < 1e-7
+    assert dv < 1e-6
     e = E.cpu().numpy()
-    assert abs(e[8] - hist[-1]["potential"]) / abs(hist[-1]["potential"]) < ENERGY_RTOL_FP64 * 100
+    epot = abs(e[8] - hist[-1]["potential"]) / abs(hist[-1]["potential"])
+    assert epot < ENERGY_RTOL_FP64 * 100
     assert abs(e[9] - hist[-1]["kinetic"]) / abs(hist[-1]["kinetic"]) < 1e-7
+    record_error("c1_fp64_100_steps_n3000", max_position_dev=dx, max_velocity_dev=dv,
+                 energy_rel=epot)
 
 
 def test_step_fp32_polyelectrolyte():
