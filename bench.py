@@ -377,8 +377,18 @@ def count_pairs(g, sysg, s, pos, dev, cap=24_000_000):
     sysg.debug_pairs(pos, trip, cap, cnt)
     torch.cuda.synchronize()
     k = int(cnt.item())
-    t = trip[: 3 * min(k, cap)].view(-1, 3)
-    qd = torch.tensor(s.q, dtype=torch.float32, device=dev)
+    if k > cap:
+        raise RuntimeError(f"pair dump of {k} triples exceeds its buffer of {cap}")
+    t = trip[: 3 * k].view(-1, 3)
+    # charges of the extended beads: the reals, then (conducting slab) one
+    # image per charged bead in index order, with the opposite charge
+    q = np.asarray(s.q, dtype=np.float64)
+    if s.geometry == synth.GEOM_SLAB_PC:
+        q = np.concatenate([q, -q[q != 0]])
+    lo, hi = int(t[:, :2].min().item()), int(t[:, :2].max().item())
+    if lo < 0 or hi >= q.shape[0]:
+        raise RuntimeError(f"pair dump index out of range [{lo}, {hi}] for {q.shape[0]} beads")
+    qd = torch.tensor(q, dtype=torch.float32, device=dev)
     qq = int(((qd[t[:, 0].long()] != 0) & (qd[t[:, 1].long()] != 0)).sum().item())
     del trip
     torch.cuda.empty_cache()
