@@ -440,11 +440,18 @@ void Engine::order_by_cost(std::vector<int2> &pw, int split) const {
 }
 
 int Engine::set_pair_config(int split, int threads, int ctas_per_sm, int nelec) {
-  if ((split != 3 && split != 9) || (threads != 128 && threads != 160 && threads != 192) ||
-      ctas_per_sm < 0 || ctas_per_sm > 8 || nelec < 1 || nelec > 3 ||
-      threads / 32 - nelec < 2) {
-    set_error("pair configuration must be split 3|9, 128|160|192 threads, 1..3 electrostatics "
-              "warps (at least 2 core warps), 0..8 CTAs per SM");
+  // nelec 0: one warp per work item (64, 96 or 128 threads, at most 28
+  // resident warps per SM by shared memory)
+  const bool warp_items = nelec == 0;
+  const bool ok_warp = warp_items && (threads == 64 || threads == 96 || threads == 128) &&
+                       ctas_per_sm >= 1 && ctas_per_sm * (threads / 32) <= 28;
+  const bool ok_cta = !warp_items && (threads == 128 || threads == 160 || threads == 192) &&
+                      ctas_per_sm >= 0 && ctas_per_sm <= 8 && nelec <= 3 &&
+                      threads / 32 - nelec >= 2;
+  if ((split != 3 && split != 9) || !(ok_warp || ok_cta)) {
+    set_error("pair configuration must be split 3|9 and either 128|160|192 threads, 1..3 "
+              "electrostatics warps (at least 2 core warps), 0..8 CTAs per SM, or warp items "
+              "(0 electrostatics warps): 64|96|128 threads, 1..28 resident warps per SM");
     return GCME_ERR_INVALID;
   }
   pair_ctas_per_sm = ctas_per_sm;
@@ -1130,7 +1137,7 @@ void Engine::enqueue_sort_pairs(const Pool &Q, cudaStream_t st, bool vir, bool d
   if (timed) cudaEventRecordWithFlags(phase_ev[2], st, cudaEventRecordExternal);
   if (use_list) launch_pair_list(Q, vir, dbg, st);
   launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, pair_ctas(), pair_counter,
-              vir, dbg, bonds_in_pair(dbg), st);
+              vir, dbg, bonds_in_pair(dbg), st, pair_nelec == 0);
   if (timed) cudaEventRecordWithFlags(phase_ev[3], st, cudaEventRecordExternal);
 }
 

@@ -1,6 +1,7 @@
 // pair.cu -- K3 per-phase kernels (FP32 body in pair.cuh) and the plain
 // FP64 pair kernel.
 #include "pair.cuh"
+#include "pair_warp.cuh"
 #include "kernels.h"
 #include "misc.cuh"
 
@@ -59,6 +60,35 @@ __global__ void __launch_bounds__(192, 5) k_pair_f32(Pool P, const int2 *work, i
     }
     if (PK) dev_pair_f32_item_pk<VIR>(P, work, w, raw, seg, s_total);
     else dev_pair_f32_item<VIR, DBG, MT>(P, work, w, sj, seg, s_total, stj, stab);
+  }
+}
+
+// One warp per work item (pair_warp.cuh): each warp fetches items from the
+// counter by itself (the warp that fetches the last index puts the counter
+// back to zero, every other warp having made its final fetch before it);
+// items nwork .. nwork + nbi - 1 are harmonic bonds, 32 per item.  Dynamic
+// shared memory: one WarpSmem per warp.
+template <bool VIR>
+__global__ void __launch_bounds__(128, 7) k_pair_warp(Pool P, const int2 *work, int nwork,
+                                                     int nbi, int *counter) {
+  extern __shared__ __align__(16) unsigned char wsm[];
+  const int lane = threadIdx.x & 31;
+  WarpSmem &W = reinterpret_cast<WarpSmem *>(wsm)[threadIdx.x >> 5];
+  const int ntot = nwork + nbi;
+  const int nwarps = (int)gridDim.x * (int)(blockDim.x >> 5);
+  while (true) {
+    int w = 0;
+    if (lane == 0) w = atomicAdd(counter, 1);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if (w >= ntot) {
+      if (lane == 0 && w == ntot + nwarps - 1) atomicExch(counter, 0);
+      break;
+    }
+    if (w >= nwork) {
+      dev_bonds<VIR, true>(P, (long long)(w - nwork) * 32 + lane);
+      continue;
+    }
+    dev_pair_warp_item<VIR>(P, work, w, W, lane);
   }
 }
 
@@ -193,7 +223,7 @@ __global__ void __launch_bounds__(128) k_pair_f64(Pool P) {
 
 void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell_factor,
                  int threads, int ctas, int *counter, bool vir, bool dbg, bool bonds,
-                 cudaStream_t st) {
+                 cudaStream_t st, bool warp_items) {
   if (P.n_ext == 0) return;
   if (fp64) {
     int nb = (int)((P.n_ext + 127) / 128);
@@ -207,6 +237,17 @@ void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell
     if (dbg) k_pair_fine<false, true><<<nwork, kPairThreads, 0, st>>>(P, work, nwork);
     else if (vir) k_pair_fine<true, false><<<nwork, kPairThreads, 0, st>>>(P, work, nwork);
     else k_pair_fine<false, false><<<nwork, kPairThreads, 0, st>>>(P, work, nwork);
+    return;
+  }
+  if (warp_items && !dbg && !P.ptab && ctas > 0 && counter) {
+    const int tb = (threads == 64 || threads == 96) ? threads : 128;
+    const int nbi = bonds ? (int)((P.n_bond + 31) / 32) : 0;
+    const int ntot = nwork + nbi;
+    const int wpc = tb / 32;
+    const int grid = std::max(1, std::min(ctas, (ntot + wpc - 1) / wpc));
+    const size_t shm = sizeof(WarpSmem) * wpc;
+    if (vir) k_pair_warp<true><<<grid, tb, shm, st>>>(P, work, nwork, nbi, counter);
+    else k_pair_warp<false><<<grid, tb, shm, st>>>(P, work, nwork, nbi, counter);
     return;
   }
   const int tb = (threads == 160 || threads == 192) ? threads : 128;

@@ -7,7 +7,8 @@
 //                or 2, 192 with 2 or 3; the other warps Gaussian core} x {one CTA
 //                per work item, or 3, 4, 5, 6 or 8 resident CTAs per SM fetching
 //                items dynamically so that the remaining slots host the
-//                concurrent PME branch};
+//                concurrent PME branch}, and one warp per work item
+//                (CTAs of 4 warps, 3-7 per SM, or of 2 warps, 8-14 per SM);
 //   PME:         lines per FFT tile along each axis in {4, 8, 16, 32, 64}
 //                (shared memory permitting), one axis at a time, and x-y
 //                plane passes (one CTA per z-plane) vs per-axis passes;
@@ -174,12 +175,17 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
   double best = 1e30;
   int bs = pair_split, bt = pair_threads, bc = pair_ctas_per_sm, be = pair_nelec;
   if (cell_factor == 1 && !use_list) {  // with lists the cell kernel only serves overflows
-    const int shapes[5][2] = {{128, 1}, {160, 1}, {160, 2}, {192, 2}, {192, 3}};  // threads, elec warps
+    // threads, electrostatics warps (0: one warp per work item)
+    const int shapes[7][2] = {{128, 1}, {160, 1}, {160, 2}, {192, 2}, {192, 3}, {128, 0}, {64, 0}};
     for (int split : {3, 9})
       for (const auto &sh : shapes)
-        for (int ctas : {0, 3, 4, 5, 6, 8}) {
+        for (int ctas : {0, 3, 4, 5, 6, 7, 8, 10, 12, 14}) {
           const int threads = sh[0], nelec = sh[1];
-          if (ctas > 40 / (threads / 32)) continue;  // register-limited residency (64 regs)
+          if (nelec > 0 && (ctas > 8 || ctas == 7 || ctas > 40 / (threads / 32)))
+            continue;  // register-limited residency (64 regs)
+          if (nelec == 0 && (ctas < 3 || ctas * (threads / 32) > 28 ||
+                             (threads == 64 && ctas < 8)))
+            continue;  // shared-memory-limited residency
           int rc = set_pair_config(split, threads, ctas, nelec);
           if (rc) return rc;
           const double ms = timed();

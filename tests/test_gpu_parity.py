@@ -226,11 +226,13 @@ def test_fft_paths(name, prec):
 
 @pytest.mark.parametrize("split,threads,nelec,ctas", [
     (9, 128, 1, 0), (9, 160, 1, 0), (9, 160, 2, 0), (9, 192, 2, 0), (9, 192, 3, 0),
-    (3, 192, 3, 0), (9, 192, 3, 5), (3, 160, 2, 8)])
+    (3, 192, 3, 0), (9, 192, 3, 5), (3, 160, 2, 8),
+    (9, 128, 0, 7), (3, 128, 0, 3), (9, 64, 0, 12), (9, 96, 0, 9)])
 def test_pair_shapes_at_parity(split, threads, nelec, ctas):
     """Every launch shape of the 27-cell kernel (work items per cell, block
     size, electrostatics warps splitting each cell's charged candidates,
-    static or dynamic CTAs) gives the oracle's forces and energies."""
+    static or dynamic CTAs, or one warp per work item) gives the oracle's
+    forces and energies."""
     s = CASES["poly_bonds"]
     t = {"pair_split": split, "pair_threads": threads, "pair_ctas_per_sm": ctas,
          "pair_nelec": nelec, "fft_lpb": [8, 8, 8], "fft_plane": True}
@@ -260,8 +262,38 @@ def test_gaussian_core_width(sigma):
     oracle, whose sums stop at rc."""
     s = synth.make_bulk(1500, seed_index=61, charged_frac=0.3, K=(12, 12, 12))
     s.sigma = sigma
-    out = gpu_forces(s, 0)
-    _check(s, out, oracle.energy_forces(s), FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
+    for t in (None, WARP_ITEMS):
+        out = gpu_forces(s, 0, tuning=t)
+        _check(s, out, oracle.energy_forces(s), FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
+
+
+WARP_ITEMS = {"pair_split": 9, "pair_threads": 128, "pair_ctas_per_sm": 7, "pair_nelec": 0,
+              "fft_lpb": [8, 8, 8], "fft_plane": True}
+
+
+@pytest.mark.parametrize("geom", [synth.GEOM_BULK, synth.GEOM_SLAB_PC])
+@pytest.mark.parametrize("sigma", [0.5, 0.8])
+def test_warp_items_in_rounds(geom, sigma):
+    """One warp per work item when an item's candidates exceed the warp's
+    shared-memory capacity: a box of one cell per axis (every neighbour cell
+    is the home cell or its periodic image), about 500 real and 150 charged
+    beads per cell, so every item is staged and evaluated in rounds, the home
+    cell itself split over rounds.  With sigma = 0.5 d the core runs without
+    the cutoff test and takes off the home bead's own term; with 0.8 d it
+    keeps the test and excludes the home bead by index.  The conducting slab
+    adds image beads to the charged lists."""
+    if geom == synth.GEOM_BULK:
+        s = synth.make_bulk(520, seed_index=63, charged_frac=0.3, K=(10, 10, 10))
+    else:
+        s = synth.make_slab_fluid(synth.GEOM_SLAB_PC, 600, charged_frac=0.3, seed_index=64)
+    s.sigma = sigma
+    for t in (WARP_ITEMS, dict(WARP_ITEMS, pair_split=3, pair_ctas_per_sm=3)):
+        out = gpu_forces(s, 0, virial=geom == synth.GEOM_BULK, tuning=t)
+        ref = oracle.energy_forces(s)
+        _check(s, out, ref, FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
+        if geom == synth.GEOM_BULK:
+            assert np.max(np.abs(out["virial"] - ref["virial"])) <= 1e-5 * np.max(
+                np.abs(ref["virial"]))
 
 
 def test_apply_tuning_rejects_bad_shapes():
@@ -271,7 +303,10 @@ def test_apply_tuning_rejects_bad_shapes():
     with pytest.raises(g.GcmeError):
         sysg.apply_tuning(_shapes(True, 8))
     for bad in (dict(fft_lpb=[3, 8, 8]), dict(fft_lpb=[8, 128, 8]), dict(pair_threads=96),
-                dict(pair_split=4), dict(pair_ctas_per_sm=9), dict(pair_nelec=4)):
+                dict(pair_split=4), dict(pair_ctas_per_sm=9), dict(pair_nelec=4),
+                dict(pair_nelec=0, pair_ctas_per_sm=0), dict(pair_nelec=0, pair_threads=160,
+                                                             pair_ctas_per_sm=4),
+                dict(pair_nelec=0, pair_threads=128, pair_ctas_per_sm=8)):
         t = _shapes(False, 8)
         t.update(bad)
         with pytest.raises(g.GcmeError):
@@ -447,8 +482,8 @@ def test_autotune_keeps_parity_and_caches(tmp_path, monkeypatch):
     sysg = g.System(ctx(), g.params_from(s), s.q, s.bonds)
     pos = torch.tensor(s.pos, dtype=torch.float64, device="cuda:0")
     t1 = sysg.autotune(pos)
-    assert t1["pair_split"] in (3, 9) and t1["pair_threads"] in (128, 160, 192)
-    assert t1["pair_nelec"] in (1, 2, 3)
+    assert t1["pair_split"] in (3, 9) and t1["pair_threads"] in (64, 128, 160, 192)
+    assert t1["pair_nelec"] in (0, 1, 2, 3)
     lst = g.System(ctx(), g.params_from(s, pair_path=g.GCME_PAIR_LIST), s.q, s.bonds)
     t3 = lst.autotune(pos)  # the list path has a cache entry of its own
     assert not t3["from_cache"]
