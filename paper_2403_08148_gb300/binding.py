@@ -66,6 +66,7 @@ class Tuning(ctypes.Structure):
                 ("pair_ctas_per_sm", ctypes.c_int32), ("fft_lpb", ctypes.c_int32 * 3),
                 ("fft_plane", ctypes.c_int32), ("from_cache", ctypes.c_int32),
                 ("cell_factor", ctypes.c_int32), ("pair_nelec", ctypes.c_int32),
+                ("pair_chunks", ctypes.c_int32),
                 ("forces_ms", ctypes.c_double), ("pme_ms", ctypes.c_double)]
 
     @classmethod
@@ -73,6 +74,7 @@ class Tuning(ctypes.Structure):
         t = cls()
         for k in ("pair_split", "pair_threads", "pair_ctas_per_sm", "pair_nelec"):
             setattr(t, k, int(d[k]))
+        t.pair_chunks = int(d.get("pair_chunks", 0))
         for a in range(3):
             t.fft_lpb[a] = int(d["fft_lpb"][a])
         t.fft_plane = int(bool(d["fft_plane"]))
@@ -83,7 +85,8 @@ class Tuning(ctypes.Structure):
                 "pair_ctas_per_sm": self.pair_ctas_per_sm, "fft_lpb": list(self.fft_lpb),
                 "fft_plane": bool(self.fft_plane),
                 "from_cache": bool(self.from_cache), "cell_factor": self.cell_factor,
-                "pair_nelec": self.pair_nelec, "forces_ms": self.forces_ms,
+                "pair_nelec": self.pair_nelec, "pair_chunks": self.pair_chunks,
+                "forces_ms": self.forces_ms,
                 "pme_ms": self.pme_ms}
 
 

@@ -139,6 +139,8 @@ struct SysDesc {
   // pair kernel works on blocks of 2 x 2 x 2 cells (nb blocks per axis)
   int cell_factor;
   int pair_split;      // work items per home cell: 3 (9 neighbour cells each) or 9 (3 each)
+  int pair_nch;        // warp items: items per (home cell, part), each taking every
+                       // pair_nch-th chunk of 32 home beads (1 for CTA items)
   int nb[3];
   float cside[3];      // cell side L / nc (FP32, for bounding-box culling)
   float cull2;         // (rc + 1e-3)^2: cells farther than this are skipped

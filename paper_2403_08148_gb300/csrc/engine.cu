@@ -355,18 +355,39 @@ void Engine::release() {
   snap_nq.clear();
 }
 
-std::vector<int2> Engine::make_pair_work(int split) const {
-  // (system, cell * split + part) for the 27-cell kernel, or
-  // (system, block * 3 + z-part) for the fine-cell kernel
+std::vector<int2> Engine::make_pair_work(int split, bool chunked) const {
+  // (system, cell * split + part) for the 27-cell kernel (times pair_nch plus
+  // the chunk group for warp items), or (system, block * 3 + z-part) for the
+  // fine-cell kernel
   std::vector<int2> pw;
   for (int s = 0; s < (int)hsys.size(); ++s) {
     const SysDesc &S = hsys[s];
     const int nitem = cell_factor == 2 ? S.nb[0] * S.nb[1] * S.nb[2] : S.ncell;
     const int parts = cell_factor == 2 ? 3 : split;
+    const int nch = chunked ? S.pair_nch : 1;
     for (int c = 0; c < nitem; ++c)
-      for (int k = 0; k < parts; ++k) pw.push_back(make_int2(s, c * parts + k));
+      for (int k = 0; k < parts; ++k)
+        for (int h = 0; h < nch; ++h) pw.push_back(make_int2(s, (c * parts + k) * nch + h));
   }
   return pw;
+}
+
+int Engine::chunks_of(int s) const {
+  if (pair_chunks > 0) return std::min(kMaxPairChunks, pair_chunks);
+  const SysDesc &S = hsys[s];
+  double med = (double)S.n / std::max(1, S.ncell);
+  if ((long long)snap_cnt.size() >= S.cell_off + S.ncell) {
+    std::vector<int> r;
+    for (int c = 0; c < S.ncell; ++c) {
+      const int k = snap_cnt[S.cell_off + c] - snap_nimg[S.cell_off + c];
+      if (k > 0) r.push_back(k);
+    }
+    if (!r.empty()) {
+      std::nth_element(r.begin(), r.begin() + r.size() / 2, r.end());
+      med = r[r.size() / 2];
+    }
+  }
+  return std::max(1, std::min(kMaxPairChunks, (int)std::ceil(med / 32.0)));
 }
 
 // Tiles of lpb lines along `axis`; the z lines of the plane path cover the
@@ -411,12 +432,13 @@ int Engine::snapshot_cells(cudaStream_t st) {
 // last CTAs of the 27-cell kernel are short ones.  Cost of an item: its real
 // home beads x the real beads it stages (Gaussian core) + 4 x its charged
 // home beads x the charged and image beads it stages (electrostatics).
-void Engine::order_by_cost(std::vector<int2> &pw, int split) const {
+void Engine::order_by_cost(std::vector<int2> &pw, int split, bool chunked) const {
   if (snap_cnt.empty() || cell_factor != 1) return;
   std::vector<std::pair<long long, int>> key(pw.size());
   for (size_t w = 0; w < pw.size(); ++w) {
     const SysDesc &S = hsys[pw[w].x];
-    const int cloc = pw[w].y / split, part = pw[w].y % split;
+    const int base = chunked ? pw[w].y / S.pair_nch : pw[w].y;
+    const int cloc = base / split, part = base % split;
     const int cx = cloc % S.nc[0], cy = (cloc / S.nc[0]) % S.nc[1], cz = cloc / (S.nc[0] * S.nc[1]);
     const long long hg = S.cell_off + cloc;
     const long long hreal = snap_cnt[hg] - snap_nimg[hg], hq = snap_nq[hg] - snap_nimg[hg];
@@ -439,31 +461,40 @@ void Engine::order_by_cost(std::vector<int2> &pw, int split) const {
   pw.swap(out);
 }
 
-int Engine::set_pair_config(int split, int threads, int ctas_per_sm, int nelec) {
-  // nelec 0: one warp per work item (64, 96 or 128 threads, at most 28
-  // resident warps per SM by shared memory)
-  const bool warp_items = nelec == 0;
-  const bool ok_warp = warp_items && (threads == 64 || threads == 96 || threads == 128) &&
+// Valid shapes of the 27-cell FP32 kernel: split 3 or 9 and either CTA
+// items (128, 160 or 192 threads, 1-3 electrostatics warps and at least 2
+// core warps, 0-8 resident CTAs per SM) or, with nelec 0, one warp per item
+// (64, 96 or 128 threads, at most 28 resident warps per SM by shared memory).
+static bool pair_shape_ok(int split, int threads, int ctas_per_sm, int nelec) {
+  const bool ok_warp = nelec == 0 && (threads == 64 || threads == 96 || threads == 128) &&
                        ctas_per_sm >= 1 && ctas_per_sm * (threads / 32) <= 28;
-  const bool ok_cta = !warp_items && (threads == 128 || threads == 160 || threads == 192) &&
-                      ctas_per_sm >= 0 && ctas_per_sm <= 8 && nelec <= 3 &&
-                      threads / 32 - nelec >= 2;
-  if ((split != 3 && split != 9) || !(ok_warp || ok_cta)) {
+  const bool ok_cta = nelec >= 1 && nelec <= 3 &&
+                      (threads == 128 || threads == 160 || threads == 192) &&
+                      ctas_per_sm >= 0 && ctas_per_sm <= 8 && threads / 32 - nelec >= 2;
+  return (split == 3 || split == 9) && (ok_warp || ok_cta);
+}
+
+int Engine::set_pair_config(int split, int threads, int ctas_per_sm, int nelec, int chunks) {
+  if (!pair_shape_ok(split, threads, ctas_per_sm, nelec) || chunks < 0 ||
+      chunks > kMaxPairChunks) {
     set_error("pair configuration must be split 3|9 and either 128|160|192 threads, 1..3 "
               "electrostatics warps (at least 2 core warps), 0..8 CTAs per SM, or warp items "
               "(0 electrostatics warps): 64|96|128 threads, 1..28 resident warps per SM");
     return GCME_ERR_INVALID;
   }
   pair_ctas_per_sm = ctas_per_sm;
-  std::vector<int2> pw = make_pair_work(split);
-  order_by_cost(pw, split);
+  const bool chunked = nelec == 0;
+  pair_chunks = chunked ? chunks : 0;
+  for (int s = 0; s < (int)hsys.size(); ++s) {
+    hsys[s].pair_split = split;
+    hsys[s].pair_nelec = nelec;
+    hsys[s].pair_nch = chunked ? chunks_of(s) : 1;
+  }
+  std::vector<int2> pw = make_pair_work(split, chunked);
+  order_by_cost(pw, split, chunked);
   pair_split = split;
   pair_threads = threads;
   pair_nelec = nelec;
-  for (auto &S : hsys) {
-    S.pair_split = split;
-    S.pair_nelec = nelec;
-  }
   GCME_CK(cudaMemcpy(const_cast<SysDesc *>(P.sys), hsys.data(), sizeof(SysDesc) * hsys.size(),
                      cudaMemcpyHostToDevice));
   GCME_CK(cudaMemcpy(pair_work, pw.data(), sizeof(int2) * pw.size(), cudaMemcpyHostToDevice));
@@ -494,7 +525,7 @@ int Engine::set_fft_plane(bool on) {
 }
 
 int Engine::apply_tuning(int split, int threads, int ctas_per_sm, int nelec, const int lpb[3],
-                         bool plane) {
+                         bool plane, int chunks) {
   const bool pair_shapes = cell_factor == 1 && !use_list;
   const size_t rsz = fp64 ? sizeof(double2) : sizeof(float2);
   bool ok = !(plane && !plane_fits());
@@ -502,14 +533,13 @@ int Engine::apply_tuning(int split, int threads, int ctas_per_sm, int nelec, con
     ok = ok && lpb[a] >= kMinLpb && lpb[a] <= 64 &&
          (2 * (size_t)lpb[a] + 1) * plan.kmax[a] * rsz <= kFftSmemLimit;
   if (pair_shapes)
-    ok = ok && (split == 3 || split == 9) && (threads == 128 || threads == 160 || threads == 192) &&
-         ctas_per_sm >= 0 && ctas_per_sm <= 8 && nelec >= 1 && nelec <= 3 &&
-         threads / 32 - nelec >= 2;
+    ok = ok && pair_shape_ok(split, threads, ctas_per_sm, nelec) && chunks >= 0 &&
+         chunks <= kMaxPairChunks;
   if (!ok) {
     set_error("launch shapes out of range or larger than shared memory");
     return GCME_ERR_INVALID;
   }
-  int rc = pair_shapes ? set_pair_config(split, threads, ctas_per_sm, nelec) : GCME_OK;
+  int rc = pair_shapes ? set_pair_config(split, threads, ctas_per_sm, nelec, chunks) : GCME_OK;
   for (int a = 0; !rc && a < 3; ++a) rc = set_fft_lpb(a, lpb[a]);
   if (!rc) rc = set_fft_plane(plane);
   return rc;
@@ -647,6 +677,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     S.cell_factor = cell_factor;
     S.pair_split = pair_split;
     S.pair_nelec = pair_nelec;
+    S.pair_nch = 1;
     for (int a = 0; a < 3; ++a) {
       S.nc[a] = cells_per_axis(p.box[a], p.rc, cell_factor);
       S.nb[a] = (S.nc[a] + 1) / 2;
@@ -845,7 +876,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   }
   std::vector<int2> pw = make_pair_work(pair_split);
   n_pair_work = (int)pw.size();
-  const int pair_cap = std::max(n_pair_work, (int)make_pair_work(9).size());
+  const int pair_cap = std::max(n_pair_work, kMaxPairChunks * (int)make_pair_work(9).size());
 
   // ---- device arena
   Carver cv;
@@ -1494,12 +1525,12 @@ int gcme_system_set_box(gcme_sys *sys, const double *box, gcme_stream_t stream) 
   // carried over); the state lives in the caller's buffers
   GCME_TRY_CK(cudaStreamSynchronize(st));
   const int split = E.pair_split, threads = E.pair_threads, ctas = E.pair_ctas_per_sm,
-            nelec = E.pair_nelec;
+            nelec = E.pair_nelec, chunks = E.pair_chunks;
   E.release();
   E.pair_split = split;
   int rc2 = E.build(E.device, {sys->spec}, false);
   if (rc2) return rc2;
-  return E.set_pair_config(split, threads, ctas, nelec);
+  return E.set_pair_config(split, threads, ctas, nelec, chunks);
 }
 
 int gcme_pressure(gcme_sys *sys, const double *d_pos, double kT, double *h_pressure,
@@ -1833,6 +1864,7 @@ static void fill_tuning(const Engine &eng, double pair_ms, double pme_ms, bool h
   out->pair_threads = eng.pair_threads;
   out->pair_ctas_per_sm = eng.pair_ctas_per_sm;
   out->pair_nelec = eng.pair_nelec;
+  out->pair_chunks = eng.pair_chunks;
   for (int a = 0; a < 3; ++a) out->fft_lpb[a] = eng.plan.lpb[a];
   out->fft_plane = eng.plan.use_plane;
   out->from_cache = hit ? 1 : 0;
@@ -1866,7 +1898,7 @@ int gcme_apply_tuning(gcme_sys *sys, const gcme_tuning *t) {
   }
   GCME_TRY_CK(cudaSetDevice(sys->eng.device));
   return sys->eng.apply_tuning(t->pair_split, t->pair_threads, t->pair_ctas_per_sm,
-                               t->pair_nelec, t->fft_lpb, t->fft_plane != 0);
+                               t->pair_nelec, t->fft_lpb, t->fft_plane != 0, t->pair_chunks);
 }
 
 int gcme_batch_apply_tuning(gcme_batch *bt, const gcme_tuning *t) {
@@ -1876,7 +1908,7 @@ int gcme_batch_apply_tuning(gcme_batch *bt, const gcme_tuning *t) {
   }
   GCME_TRY_CK(cudaSetDevice(bt->eng.device));
   return bt->eng.apply_tuning(t->pair_split, t->pair_threads, t->pair_ctas_per_sm,
-                              t->pair_nelec, t->fft_lpb, t->fft_plane != 0);
+                              t->pair_nelec, t->fft_lpb, t->fft_plane != 0, t->pair_chunks);
 }
 
 int gcme_batch_autotune(gcme_batch *bt, int32_t flags, gcme_tuning *out, gcme_stream_t stream) {
@@ -2045,7 +2077,8 @@ int gcme_batch_step(gcme_batch *b, int64_t nsteps, int32_t mode, gcme_stream_t s
   }
   if (nsteps == 0) return GCME_OK;
   int lr = launch_persistent(b->eng.cell_only(Q), b->eng.pair_work, b->eng.n_pair_work, b->eng.cell_factor,
-                             b->eng.plan, nsteps, b->eng.bar_words, 2.0, st);
+                             b->eng.plan, nsteps, b->eng.bar_words, 2.0, st,
+                             b->eng.pair_nelec == 0);
   if (lr != 0) {
     cudaError_t e = cudaGetLastError();
     set_error(std::string("persistent cooperative launch failed: ") + cudaGetErrorString(e));

@@ -16,6 +16,7 @@ constexpr int kDefaultCellFactor = 1;
 // work items per home cell of the 27-cell pair kernel (3 or 9)
 constexpr int kDefaultPairSplit = 9;
 constexpr int kDefaultPairThreads = 128;
+constexpr int kMaxPairChunks = 4;  // warp items per (home cell, part), at most
 // real-space table intervals in r^2: N = 18.25 beta^2 rc^2 keeps the cubic
 // interpolation error near 1e-7 of g(0) (the error scales as (beta^2 du)^4);
 // at least kRealTabMin, and direct evaluation above kRealTabMax (a < ~0.09 d)
@@ -90,20 +91,27 @@ class Engine {
   int forces_graph(const Pool &P, cudaGraphExec_t *out);
 
   int nsys() const { return (int)hsys.size(); }
-  std::vector<int2> make_pair_work(int split) const;
+  // (system, code) pair work items: code = cell * split + part, times
+  // S.pair_nch plus the chunk group when chunked (warp items)
+  std::vector<int2> make_pair_work(int split, bool chunked = false) const;
+  // chunk groups per (home cell, part) of warp items for system s:
+  // pair_chunks when set, else the median real-bead count of its non-empty
+  // cells in chunks of 32 (from the last cell snapshot, else n / ncell),
+  // 1..kMaxPairChunks
+  int chunks_of(int s) const;
   std::vector<int2> make_fft_work(int axis, int lpb) const;
-  int set_pair_config(int split, int threads, int ctas_per_sm, int nelec = 1);
+  int set_pair_config(int split, int threads, int ctas_per_sm, int nelec = 1, int chunks = 0);
   // cell occupancy of the last cell sort (host copy) and the work-item
   // order it implies (heaviest first)
   int snapshot_cells(cudaStream_t st);
-  void order_by_cost(std::vector<int2> &pw, int split) const;
+  void order_by_cost(std::vector<int2> &pw, int split, bool chunked = false) const;
   std::vector<int> snap_cnt, snap_nimg, snap_nq;
   int set_fft_lpb(int axis, int lpb);
   bool plane_fits() const;
   int set_fft_plane(bool on);
   // launch shapes given by the caller (checked before any is changed)
   int apply_tuning(int split, int threads, int ctas_per_sm, int nelec, const int lpb[3],
-                   bool plane);
+                   bool plane, int chunks = 0);
   void clear_graphs();
   // time candidate configurations on the current state and keep the
   // fastest (tune.cu); from_cache reports a hit of the tuning cache
@@ -129,7 +137,8 @@ class Engine {
   bool species = false;   // several species: per-pair constants from tables
   int pair_split = 0;   // 3 or 9 work items per home cell (0: default)
   int pair_threads = kDefaultPairThreads;  // 128, 160 or 192 threads per pair CTA
-  int pair_nelec = 1;  // of which electrostatics warps (1 or 2)
+  int pair_nelec = 1;  // of which electrostatics warps (1 to 3; 0: one warp per item)
+  int pair_chunks = 0;  // warp items per (home cell, part): 1..4, 0 automatic
   int pair_ctas_per_sm = 0;  // 0: one CTA per work item; else resident CTAs per SM fetching items
   int n_sm = 152;
   int *pair_counter = nullptr;  // dynamic work-item counter of the pair kernel

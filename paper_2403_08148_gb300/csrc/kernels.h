@@ -58,11 +58,12 @@ void launch_finalize(const Pool &P, bool vir, cudaStream_t st); // energies -> F
 void launch_kick_drift(const Pool &P, bool vel64, cudaStream_t st);
 void launch_kick(const Pool &P, bool vel64, cudaStream_t st);
 // one cooperative launch of nsteps steps of the whole batch (FP32); the
-// four words at bar_words hold the barrier state and the error word
+// four words at bar_words hold the barrier state and the error word;
+// warp_items: the pair work list holds warp items (one warp per item)
 int launch_persistent(const Pool &P, const int2 *pair_work, int n_pair_work, int cell_factor,
                       const PmePlan &pl,
                       long long nsteps, unsigned int *bar_words, double timeout_s,
-                      cudaStream_t st);
+                      cudaStream_t st, bool warp_items = false);
 int launch_barrier_probe(unsigned int *bar_words, double timeout_s, cudaStream_t st);
 void launch_force_to_f64(const long long *f, double *out, long long n3, cudaStream_t st);
 void launch_scale(double *x, long long n3, double s, cudaStream_t st);  // x *= s

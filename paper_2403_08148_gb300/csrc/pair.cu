@@ -64,8 +64,9 @@ __global__ void __launch_bounds__(192, 5) k_pair_f32(Pool P, const int2 *work, i
 }
 
 // One warp per work item (pair_warp.cuh): each warp fetches items from the
-// counter by itself (the warp that fetches the last index puts the counter
-// back to zero, every other warp having made its final fetch before it);
+// counter by itself, the next index while it works on the current one (the
+// warp that fetches the last index puts the counter back to zero, every
+// other warp having made its final fetch before it);
 // items nwork .. nwork + nbi - 1 are harmonic bonds, 32 per item.  Dynamic
 // shared memory: one WarpSmem per warp.
 template <bool VIR>
@@ -76,19 +77,20 @@ __global__ void __launch_bounds__(128, 7) k_pair_warp(Pool P, const int2 *work, 
   WarpSmem &W = reinterpret_cast<WarpSmem *>(wsm)[threadIdx.x >> 5];
   const int ntot = nwork + nbi;
   const int nwarps = (int)gridDim.x * (int)(blockDim.x >> 5);
+  int w = 0;
+  if (lane == 0) w = atomicAdd(counter, 1);
+  w = __shfl_sync(0xffffffffu, w, 0);
   while (true) {
-    int w = 0;
-    if (lane == 0) w = atomicAdd(counter, 1);
-    w = __shfl_sync(0xffffffffu, w, 0);
     if (w >= ntot) {
       if (lane == 0 && w == ntot + nwarps - 1) atomicExch(counter, 0);
       break;
     }
-    if (w >= nwork) {
-      dev_bonds<VIR, true>(P, (long long)(w - nwork) * 32 + lane);
-      continue;
-    }
-    dev_pair_warp_item<VIR>(P, work, w, W, lane);
+    // the next item's index, fetched now: its round trip overlaps this item
+    int wn = 0;
+    if (lane == 0) wn = atomicAdd(counter, 1);
+    if (w >= nwork) dev_bonds<VIR, true>(P, (long long)(w - nwork) * 32 + lane);
+    else dev_pair_warp_item<VIR>(P, work, w, W, lane);
+    w = __shfl_sync(0xffffffffu, wn, 0);
   }
 }
 

@@ -26,6 +26,12 @@
 // is exactly 1 (the distance is exactly 0), which is taken off the energy sum
 // and adds nothing to force or virial.  Otherwise the neighbour rule of
 // pair.cuh decides each pair.  Electrostatics: always the neighbour rule.
+//
+// Items per (home cell, part): SysDesc::pair_nch, item h taking the home
+// chunks h, h + pair_nch, ...: more, shorter items than warps resident, so
+// that warps fetching items dynamically even out the heavy cells (a single
+// warp cannot fill an SM's issue slots, so one long item sets the launch's
+// end).  Each item stages its neighbour beads itself.
 #pragma once
 #include "pair.cuh"
 
@@ -190,18 +196,19 @@ __device__ __forceinline__ int wstage(const Pool &P, long long gbeg, int &t, int
   return kept;
 }
 
-// Evaluate every chunk of 32 home real beads over the staged pieces and
-// write the partial sums.  Warp-synchronous.
+// Evaluate the item's chunks of 32 home real beads (chunks ch, ch + nch, ...)
+// over the staged pieces and write the partial sums.  Warp-synchronous.
 template <bool VIR>
 __device__ __forceinline__ void wflush(const Pool &P, const SysDesc &S, int s, int rbeg, int hend,
-                                       int nqr, int npr, int npq, WarpSmem &W, int lane) {
+                                       int nqr, int ch, int nch, int npr, int npq, WarpSmem &W,
+                                       int lane) {
   __syncwarp();
   const float rc2 = S.rc2f, gcc = S.gc_c2f;
   const bool tail = S.gc_tail != 0;
   const float4 *tab = P.rtab + S.rtab_off;
   const float tab_scale = S.rtab_scale;
   const int tab_nm1 = S.rtab_n - 1;
-  for (int c0 = 0; c0 < hend - rbeg; c0 += 32) {
+  for (int c0 = 32 * ch; c0 < hend - rbeg; c0 += 32 * nch) {
     const int ih = c0 + lane;  // home index among the cell's real beads
     const int i = rbeg + ih;
     const bool valid = i < hend;
@@ -285,14 +292,15 @@ __device__ __forceinline__ void dev_pair_warp_item(const Pool &P, const int2 *wo
   const int s = work[w].x, code = work[w].y;
   if (P.list_ovf && !P.list_ovf[s]) return;  // lists: only systems whose lists overflowed
   const SysDesc &S = P.sys[s];
-  const int split = S.pair_split;
-  const int cloc = code / split, part = code % split;
+  const int split = S.pair_split, nch = S.pair_nch;
+  const int base = code / nch, ch = code - base * nch;  // chunk group
+  const int cloc = base / split, part = base % split;
   const int nseg = 27 / split;
   const long long hg = S.cell_off + cloc;
   const int hbeg = P.cell_start[hg], hend = P.cell_start[hg + 1];
   const int himg = P.cell_nimg[hg], hq = P.cell_nq[hg];
   const int rbeg = hbeg + himg;
-  if (hend <= rbeg) return;  // no real home beads
+  if (hend - rbeg <= 32 * ch) return;  // no home chunk for this group
   const int nqr = hbeg + hq - rbeg;
   if (lane < nseg) W.seg[lane] = item_segment(P, S, cloc, part, lane);
   float lo[3], hi[3];
@@ -351,12 +359,12 @@ __device__ __forceinline__ void dev_pair_warp_item(const Pool &P, const int2 *wo
         }
       }
       if (tr < nr || tq < nb) {  // a capacity is reached: evaluate this round
-        wflush<VIR>(P, S, s, rbeg, hend, nqr, npr, npq, W, lane);
+        wflush<VIR>(P, S, s, rbeg, hend, nqr, ch, nch, npr, npq, W, lane);
         usedr = usedq = npr = npq = 0;
       }
     }
   }
-  if (npr + npq > 0) wflush<VIR>(P, S, s, rbeg, hend, nqr, npr, npq, W, lane);
+  if (npr + npq > 0) wflush<VIR>(P, S, s, rbeg, hend, nqr, ch, nch, npr, npq, W, lane);
 }
 
 }  // namespace gcme

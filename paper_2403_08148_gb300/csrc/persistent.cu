@@ -12,6 +12,7 @@
 #include "kernels.h"
 #include "misc.cuh"
 #include "pair.cuh"
+#include "pair_warp.cuh"
 #include "pme.cuh"
 
 #include <algorithm>
@@ -59,6 +60,7 @@ struct PersistArgs {
   const int2 *pair_work;
   int n_pair_work;
   int cell_factor;
+  int warp_items;  // the pair work list holds warp items (pair_warp.cuh)
   PmePlan plan;
   long long nsteps;
   Barrier bar;
@@ -107,11 +109,19 @@ __global__ void __launch_bounds__(128) k_persistent(Pool P, PersistArgs A) {
       const size_t toff = (kPairSmemBytes + sizeof(PairSeg) * 9 + 16 + 15) / 16 * 16;
       PairTab *stab = reinterpret_cast<PairTab *>(smem + toff);
       unsigned char *stj = smem + toff + sizeof(PairTab) * kMaxTypes * kMaxTypes;
-      for (int w = blockIdx.x; w < A.n_pair_work; w += gridDim.x) {
-        if (P.ptab)
-          dev_pair_f32_item<false, false, true>(P, A.pair_work, w, sj, seg, st, stj, stab);
-        else
-          dev_pair_f32_item_pk<false>(P, A.pair_work, w, smem, seg, st);
+      if (A.warp_items) {  // one warp per work item (pair_warp.cuh)
+        WarpSmem &W = reinterpret_cast<WarpSmem *>(smem)[threadIdx.x >> 5];
+        const int nw = (int)gridDim.x * (int)(blockDim.x >> 5);
+        for (int w = blockIdx.x * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
+             w < A.n_pair_work; w += nw)
+          dev_pair_warp_item<false>(P, A.pair_work, w, W, (int)(threadIdx.x & 31));
+      } else {
+        for (int w = blockIdx.x; w < A.n_pair_work; w += gridDim.x) {
+          if (P.ptab)
+            dev_pair_f32_item<false, false, true>(P, A.pair_work, w, sj, seg, st, stj, stab);
+          else
+            dev_pair_f32_item_pk<false>(P, A.pair_work, w, smem, seg, st);
+        }
       }
     }
     for (long long g = gtid; g < P.n_q * 8; g += gthreads) dev_spread<float, 0>(P, g);
@@ -156,8 +166,9 @@ __global__ void __launch_bounds__(128) k_persistent(Pool P, PersistArgs A) {
 }
 #undef GRID_LOOP
 
-size_t persistent_smem(const PmePlan &pl, bool species) {
+size_t persistent_smem(const PmePlan &pl, bool species, bool warp_items) {
   size_t pair = kPairSmemBytes + sizeof(PairSeg) * 9 + 16;
+  if (warp_items) pair = std::max(pair, 4 * sizeof(WarpSmem));  // 128 threads = 4 warps
   if (species)
     pair = (pair + 15) / 16 * 16 + sizeof(PairTab) * kMaxTypes * kMaxTypes + kPairCap;
   size_t sort = sizeof(long long) * kSortCap + 16;
@@ -171,8 +182,9 @@ size_t persistent_smem(const PmePlan &pl, bool species) {
 
 int launch_persistent(const Pool &P, const int2 *pair_work, int n_pair_work, int cell_factor,
                       const PmePlan &pl, long long nsteps, unsigned int *bar_words, double timeout_s,
-                      cudaStream_t st) {
-  const size_t smem = persistent_smem(pl, P.ptab != nullptr);
+                      cudaStream_t st, bool warp_items) {
+  warp_items = warp_items && !P.ptab && cell_factor == 1;
+  const size_t smem = persistent_smem(pl, P.ptab != nullptr, warp_items);
   cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int dev = 0, nsm = 0, per_sm = 0, clock_khz = 0;
   cudaGetDevice(&dev);
@@ -184,6 +196,7 @@ int launch_persistent(const Pool &P, const int2 *pair_work, int n_pair_work, int
   A.pair_work = pair_work;
   A.n_pair_work = n_pair_work;
   A.cell_factor = cell_factor;
+  A.warp_items = warp_items ? 1 : 0;
   A.plan = pl;
   A.nsteps = nsteps;
   A.bar.count = bar_words;

@@ -45,7 +45,7 @@ std::string cache_path() {
 }
 
 struct Tuned {
-  int split = 0, threads = 0, ctas = 0, lpb[3] = {0, 0, 0}, plane = 0, nelec = 1;
+  int split = 0, threads = 0, ctas = 0, lpb[3] = {0, 0, 0}, plane = 0, nelec = 1, chunks = 0;
   double pair_ms = 0, pme_ms = 0;
 };
 
@@ -68,6 +68,8 @@ bool cache_lookup(const std::string &key, Tuned *t) {
                     &x.pair_ms, &x.pme_ms) == 9) {
       const char *e = std::strstr(line.c_str(), "\"pair_nelec\":");
       if (e && std::sscanf(e, "\"pair_nelec\": %d", &x.nelec) != 1) x.nelec = 1;
+      const char *h = std::strstr(line.c_str(), "\"pair_chunks\":");
+      if (!h || std::sscanf(h, "\"pair_chunks\": %d", &x.chunks) != 1) x.chunks = 0;
       *t = x;  // the last entry for a key wins
       found = true;
     }
@@ -83,9 +85,10 @@ void cache_store(const std::string &key, const Tuned &t) {
   std::snprintf(buf, sizeof buf,
                 "{\"key\": \"%s\", \"pair_split\": %d, \"pair_threads\": %d, "
                 "\"pair_ctas_per_sm\": %d, \"fft_lpb\": [%d, %d, %d], \"fft_plane\": %d, "
-                "\"forces_ms\": %.6f, \"pme_ms\": %.6f, \"pair_nelec\": %d}\n",
+                "\"forces_ms\": %.6f, \"pme_ms\": %.6f, \"pair_nelec\": %d, "
+                "\"pair_chunks\": %d}\n",
                 key.c_str(), t.split, t.threads, t.ctas, t.lpb[0], t.lpb[1], t.lpb[2], t.plane,
-                t.pair_ms, t.pme_ms, t.nelec);
+                t.pair_ms, t.pme_ms, t.nelec, t.chunks);
   f << buf;
 }
 
@@ -151,7 +154,7 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
     if (rc0) return rc0;
   }
   if (!remeasure && !no_cache && cache_lookup(key.str(), &t)) {
-    int rc = set_pair_config(t.split, t.threads, t.ctas, t.nelec);
+    int rc = set_pair_config(t.split, t.threads, t.ctas, t.nelec, t.chunks);
     for (int a = 0; !rc && a < 3; ++a) rc = set_fft_lpb(a, t.lpb[a]);
     if (!rc) rc = set_fft_plane(t.plane != 0);
     if (!rc) {
@@ -173,7 +176,8 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
     return time_ms(st, reps, forces);
   };
   double best = 1e30;
-  int bs = pair_split, bt = pair_threads, bc = pair_ctas_per_sm, be = pair_nelec;
+  int bs = pair_split, bt = pair_threads, bc = pair_ctas_per_sm, be = pair_nelec,
+      bh = pair_chunks;
   if (cell_factor == 1 && !use_list) {  // with lists the cell kernel only serves overflows
     // threads, electrostatics warps (0: one warp per work item)
     const int shapes[7][2] = {{128, 1}, {160, 1}, {160, 2}, {192, 2}, {192, 3}, {128, 0}, {64, 0}};
@@ -183,21 +187,25 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
           const int threads = sh[0], nelec = sh[1];
           if (nelec > 0 && (ctas > 8 || ctas == 7 || ctas > 40 / (threads / 32)))
             continue;  // register-limited residency (64 regs)
-          if (nelec == 0 && (ctas < 3 || ctas * (threads / 32) > 28 ||
+          if (nelec == 0 && (split == 3 || ctas < 3 || ctas * (threads / 32) > 28 ||
                              (threads == 64 && ctas < 8)))
-            continue;  // shared-memory-limited residency
-          int rc = set_pair_config(split, threads, ctas, nelec);
-          if (rc) return rc;
-          const double ms = timed();
-          if (ms < best) {
-            best = ms;
-            bs = split;
-            bt = threads;
-            bc = ctas;
-            be = nelec;
+            continue;  // shared-memory-limited residency; 9-cell items exceed a warp's slice
+          for (int chunks : {1, 0}) {  // warp items: whole home cells, or split by chunks
+            if (nelec > 0 && chunks == 1) continue;
+            int rc = set_pair_config(split, threads, ctas, nelec, chunks);
+            if (rc) return rc;
+            const double ms = timed();
+            if (ms < best) {
+              best = ms;
+              bs = split;
+              bt = threads;
+              bc = ctas;
+              be = nelec;
+              bh = chunks;
+            }
           }
         }
-    int rc = set_pair_config(bs, bt, bc, be);
+    int rc = set_pair_config(bs, bt, bc, be, bh);
     if (rc) return rc;
   } else {
     best = timed();
@@ -236,6 +244,7 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
   t.threads = pair_threads;
   t.ctas = pair_ctas_per_sm;
   t.nelec = pair_nelec;
+  t.chunks = pair_chunks;
   t.plane = plan.use_plane;
   for (int a = 0; a < 3; ++a) t.lpb[a] = plan.lpb[a];
   t.pair_ms = best;

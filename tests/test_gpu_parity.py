@@ -287,7 +287,8 @@ def test_warp_items_in_rounds(geom, sigma):
     else:
         s = synth.make_slab_fluid(synth.GEOM_SLAB_PC, 600, charged_frac=0.3, seed_index=64)
     s.sigma = sigma
-    for t in (WARP_ITEMS, dict(WARP_ITEMS, pair_split=3, pair_ctas_per_sm=3)):
+    for t in (WARP_ITEMS, dict(WARP_ITEMS, pair_chunks=1), dict(WARP_ITEMS, pair_chunks=4),
+              dict(WARP_ITEMS, pair_split=3, pair_ctas_per_sm=3)):
         out = gpu_forces(s, 0, virial=geom == synth.GEOM_BULK, tuning=t)
         ref = oracle.energy_forces(s)
         _check(s, out, ref, FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
@@ -306,7 +307,8 @@ def test_apply_tuning_rejects_bad_shapes():
                 dict(pair_split=4), dict(pair_ctas_per_sm=9), dict(pair_nelec=4),
                 dict(pair_nelec=0, pair_ctas_per_sm=0), dict(pair_nelec=0, pair_threads=160,
                                                              pair_ctas_per_sm=4),
-                dict(pair_nelec=0, pair_threads=128, pair_ctas_per_sm=8)):
+                dict(pair_nelec=0, pair_threads=128, pair_ctas_per_sm=8),
+                dict(pair_nelec=0, pair_ctas_per_sm=4, pair_chunks=5)):
         t = _shapes(False, 8)
         t.update(bad)
         with pytest.raises(g.GcmeError):
