@@ -7,6 +7,7 @@
 namespace gcme {
 
 __global__ void k_bin(Pool P) {
+  pdl_begin();
   const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (P.nsys == 1 && P.n_ext == P.n_real) dev_bin<true>(P, g);
   else dev_bin<false>(P, g);
@@ -15,17 +16,20 @@ __global__ void k_bin(Pool P) {
 __global__ void __launch_bounds__(1024) k_scan(const int *cnt, int *start, long long n,
                                               const int *gate) {
   __shared__ long long warp_tot[32];
+  pdl_begin();
   if (gate && !*gate) return;
   dev_scan_block(cnt, start, n, warp_tot);
 }
 
 __global__ void k_scatter(Pool P) {
+  pdl_begin();
   dev_scatter(P, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
 __global__ void __launch_bounds__(256) k_cellsort(Pool P) {
   __shared__ long long key[kSortCap];
   __shared__ int cnt2[2];
+  pdl_begin();
   if (blockIdx.x >= P.n_cells) return;
   if (P.gate && !*P.gate) return;
   dev_cellsort_block(P, blockIdx.x, key, cnt2);
@@ -35,6 +39,7 @@ __global__ void __launch_bounds__(256) k_cellsort_fused(Pool P) {
   __shared__ long long key[kSortCap];
   __shared__ int cnt2[2];
   __shared__ int red[32];
+  pdl_begin();
   if (blockIdx.x >= P.n_cells) return;
   if (P.gate && !*P.gate) return;
   dev_cellsort_fused_block(P, blockIdx.x, key, cnt2, red);
@@ -45,7 +50,7 @@ void launch_bin(const Pool &P, cudaStream_t st, bool zero_counts) {
   const int tb = 256;
   const int nb = (int)((P.n_ext + tb - 1) / tb);
   if (zero_counts) cudaMemsetAsync(P.cell_cnt, 0, sizeof(int) * P.n_cells, st);
-  k_bin<<<nb, tb, 0, st>>>(P);
+  launch_k(k_bin, nb, tb, 0, st, P);
 }
 
 void launch_sort(const Pool &P, cudaStream_t st) {
@@ -53,12 +58,13 @@ void launch_sort(const Pool &P, cudaStream_t st) {
   const int tb = 256;
   const int nb = (int)((P.n_ext + tb - 1) / tb);
   if (P.bucket) {
-    k_cellsort_fused<<<(unsigned)P.n_cells, 256, 0, st>>>(P);
+    launch_k(k_cellsort_fused, (unsigned)P.n_cells, 256, 0, st, P);
     return;
   }
-  k_scan<<<1, 1024, 0, st>>>(P.cell_cnt, P.cell_start, P.n_cells, P.gate);
-  k_scatter<<<nb, tb, 0, st>>>(P);
-  k_cellsort<<<(unsigned)P.n_cells, 256, 0, st>>>(P);
+  launch_k(k_scan, 1, 1024, 0, st, (const int *)P.cell_cnt, P.cell_start, (long long)P.n_cells,
+           (const int *)P.gate);
+  launch_k(k_scatter, nb, tb, 0, st, P);
+  launch_k(k_cellsort, (unsigned)P.n_cells, 256, 0, st, P);
 }
 
 void launch_cells(const Pool &P, cudaStream_t st) {

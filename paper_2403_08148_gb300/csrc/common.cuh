@@ -242,6 +242,19 @@ struct Pool {
 // ---------------------------------------------------------------------------
 // device helpers
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch: a kernel launched with launch_k (kernels.h)
+// may start while its predecessor in the stream finishes.  pdl_wait() blocks
+// until that predecessor grid has completed and its writes are visible (a
+// no-op for a plain launch), so every kernel calls it before touching
+// memory; pdl_trigger() lets the next kernel's launch begin now (else it
+// begins when this grid's blocks have exited).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
+__device__ __forceinline__ void pdl_begin() {
+  pdl_wait();
+  pdl_trigger();
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

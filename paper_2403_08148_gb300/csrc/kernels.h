@@ -4,6 +4,27 @@
 
 namespace gcme {
 
+// Launch with programmatic stream serialization (captured into graphs as
+// programmatic edges): the kernel may be launched before its predecessor in
+// the stream has finished, hiding the launch latency; it must call
+// pdl_wait() (common.cuh) before it reads or writes memory.
+template <typename... K, typename... A>
+inline cudaError_t launch_k(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem,
+                            cudaStream_t st, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<K>(args)...);
+}
+
+
 // FFT work per axis: int2 (system, tile of lpb lines), lines per tile and
 // the largest grid extent along that axis over the batch.
 struct PmePlan {

@@ -6,13 +6,26 @@ namespace gcme {
 
 #define GCME_TID (blockIdx.x * (long long)blockDim.x + threadIdx.x)
 template <bool VIR>
-__global__ void k_bonds(Pool P) { dev_bonds<VIR>(P, GCME_TID); }
-__global__ void k_walls(Pool P) { dev_walls(P, GCME_TID); }
-__global__ void k_slab_apply(Pool P) { dev_slab_apply(P, GCME_TID); }
+__global__ void k_bonds(Pool P) {
+  pdl_begin();
+  dev_bonds<VIR>(P, GCME_TID);
+}
+__global__ void k_walls(Pool P) {
+  pdl_begin();
+  dev_walls(P, GCME_TID);
+}
+__global__ void k_slab_apply(Pool P) {
+  pdl_begin();
+  dev_slab_apply(P, GCME_TID);
+}
 template <bool VIR>
-__global__ void k_finalize(Pool P) { dev_finalize<VIR>(P, (int)GCME_TID); }
+__global__ void k_finalize(Pool P) {
+  pdl_begin();
+  dev_finalize<VIR>(P, (int)GCME_TID);
+}
 template <typename V>
 __global__ void k_kick_drift(Pool P) {
+  pdl_begin();
   if (P.nsys == 1) dev_kick_drift<V, true>(P, GCME_TID);
   else dev_kick_drift<V, false>(P, GCME_TID);
   // the step's accumulators and cell counts start from zero (the previous
@@ -23,6 +36,7 @@ __global__ void k_kick_drift(Pool P) {
 }
 template <typename V>
 __global__ void k_kick(Pool P) {
+  pdl_begin();
   if (P.nsys == 1) dev_kick<V, true>(P, GCME_TID);
   else dev_kick<V, false>(P, GCME_TID);
 }
@@ -31,36 +45,36 @@ __global__ void k_kick(Pool P) {
 void launch_bonded(const Pool &P, bool vir, bool bonds, cudaStream_t st) {
   if (bonds && P.n_bond > 0) {
     int nb = (int)((P.n_bond + 255) / 256);
-    if (vir) k_bonds<true><<<nb, 256, 0, st>>>(P);
-    else k_bonds<false><<<nb, 256, 0, st>>>(P);
+    if (vir) launch_k(k_bonds<true>, nb, 256, 0, st, P);
+    else launch_k(k_bonds<false>, nb, 256, 0, st, P);
   }
   // walls and the slab dipole exist only in slab geometries
-  if (P.n_real > 0 && P.any_slab) k_walls<<<(int)((P.n_real + 255) / 256), 256, 0, st>>>(P);
+  if (P.n_real > 0 && P.any_slab) launch_k(k_walls, (int)((P.n_real + 255) / 256), 256, 0, st, P);
 }
 
 void launch_slab_apply(const Pool &P, cudaStream_t st) {
   if (P.n_real > 0 && P.any_slab)
-    k_slab_apply<<<(int)((P.n_real + 255) / 256), 256, 0, st>>>(P);
+    launch_k(k_slab_apply, (int)((P.n_real + 255) / 256), 256, 0, st, P);
 }
 
 void launch_finalize(const Pool &P, bool vir, cudaStream_t st) {
   int nb = (P.nsys + 127) / 128;
-  if (vir) k_finalize<true><<<nb, 128, 0, st>>>(P);
-  else k_finalize<false><<<nb, 128, 0, st>>>(P);
+  if (vir) launch_k(k_finalize<true>, nb, 128, 0, st, P);
+  else launch_k(k_finalize<false>, nb, 128, 0, st, P);
 }
 
 void launch_kick_drift(const Pool &P, bool vel64, cudaStream_t st) {
   if (P.n_real == 0) return;
   int nb = (int)((P.n_real + 255) / 256);
-  if (vel64) k_kick_drift<double><<<nb, 256, 0, st>>>(P);
-  else k_kick_drift<float><<<nb, 256, 0, st>>>(P);
+  if (vel64) launch_k(k_kick_drift<double>, nb, 256, 0, st, P);
+  else launch_k(k_kick_drift<float>, nb, 256, 0, st, P);
 }
 
 void launch_kick(const Pool &P, bool vel64, cudaStream_t st) {
   if (P.n_real == 0) return;
   int nb = (int)((P.n_real + 255) / 256);
-  if (vel64) k_kick<double><<<nb, 256, 0, st>>>(P);
-  else k_kick<float><<<nb, 256, 0, st>>>(P);
+  if (vel64) launch_k(k_kick<double>, nb, 256, 0, st, P);
+  else launch_k(k_kick<float>, nb, 256, 0, st, P);
 }
 
 __global__ void k_force_to_f64(const long long *f, double *out, long long n3) {

@@ -11,6 +11,7 @@ namespace gcme {
 
 template <bool VIR, bool DBG>
 __global__ void __launch_bounds__(kPairThreads) k_pair_fine(Pool P, const int2 *work, int nwork) {
+  pdl_wait();
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) dev_pair_fine_item<VIR, DBG>(P, work, w);
 }
 
@@ -33,6 +34,9 @@ __global__ void __launch_bounds__(192, 5) k_pair_f32(Pool P, const int2 *work, i
   __shared__ __align__(16) PairTab stab[MT ? kMaxTypes * kMaxTypes : 1];
   float4 *sj = reinterpret_cast<float4 *>(raw);
   constexpr bool PK = !DBG && !MT;
+  // no early trigger: the kernels after this one would wait on SM slots the
+  // concurrent PME branch can use
+  pdl_wait();
   const int ntot = nwork + nbi;
   if (!counter) {  // static: one item per CTA (grid = items)
     for (int w = blockIdx.x; w < ntot; w += gridDim.x) {
@@ -64,9 +68,8 @@ __global__ void __launch_bounds__(192, 5) k_pair_f32(Pool P, const int2 *work, i
 }
 
 // One warp per work item (pair_warp.cuh): each warp fetches items from the
-// counter by itself, the next index while it works on the current one (the
-// warp that fetches the last index puts the counter back to zero, every
-// other warp having made its final fetch before it);
+// counter by itself (the warp that fetches the last index puts the counter
+// back to zero, every other warp having made its final fetch before it);
 // items nwork .. nwork + nbi - 1 are harmonic bonds, 32 per item.  Dynamic
 // shared memory: one WarpSmem per warp.
 template <bool VIR>
@@ -75,22 +78,21 @@ __global__ void __launch_bounds__(128, 7) k_pair_warp(Pool P, const int2 *work, 
   extern __shared__ __align__(16) unsigned char wsm[];
   const int lane = threadIdx.x & 31;
   WarpSmem &W = reinterpret_cast<WarpSmem *>(wsm)[threadIdx.x >> 5];
+  pdl_wait();
   const int ntot = nwork + nbi;
   const int nwarps = (int)gridDim.x * (int)(blockDim.x >> 5);
-  int w = 0;
-  if (lane == 0) w = atomicAdd(counter, 1);
-  w = __shfl_sync(0xffffffffu, w, 0);
   while (true) {
+    // one item at a time: fetching the next one early would let the warps
+    // that start first take items from the warps that start later
+    int w = 0;
+    if (lane == 0) w = atomicAdd(counter, 1);
+    w = __shfl_sync(0xffffffffu, w, 0);
     if (w >= ntot) {
       if (lane == 0 && w == ntot + nwarps - 1) atomicExch(counter, 0);
       break;
     }
-    // the next item's index, fetched now: its round trip overlaps this item
-    int wn = 0;
-    if (lane == 0) wn = atomicAdd(counter, 1);
     if (w >= nwork) dev_bonds<VIR, true>(P, (long long)(w - nwork) * 32 + lane);
     else dev_pair_warp_item<VIR>(P, work, w, W, lane);
-    w = __shfl_sync(0xffffffffu, wn, 0);
   }
 }
 
@@ -101,6 +103,7 @@ __global__ void __launch_bounds__(128, 7) k_pair_warp(Pool P, const int2 *work, 
 // ---------------------------------------------------------------------------
 template <bool VIR, bool DBG>
 __global__ void __launch_bounds__(128) k_pair_f64(Pool P) {
+  pdl_wait();
   const long long gs = blockIdx.x * (long long)blockDim.x + threadIdx.x;  // sorted slot
   double eg = 0.0, er = 0.0;
   double W[9];
@@ -229,16 +232,16 @@ void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell
   if (P.n_ext == 0) return;
   if (fp64) {
     int nb = (int)((P.n_ext + 127) / 128);
-    if (dbg) k_pair_f64<false, true><<<nb, 128, 0, st>>>(P);
-    else if (vir) k_pair_f64<true, false><<<nb, 128, 0, st>>>(P);
-    else k_pair_f64<false, false><<<nb, 128, 0, st>>>(P);
+    if (dbg) launch_k(k_pair_f64<false, true>, nb, 128, 0, st, P);
+    else if (vir) launch_k(k_pair_f64<true, false>, nb, 128, 0, st, P);
+    else launch_k(k_pair_f64<false, false>, nb, 128, 0, st, P);
     return;
   }
   if (nwork == 0) return;
   if (cell_factor == 2) {
-    if (dbg) k_pair_fine<false, true><<<nwork, kPairThreads, 0, st>>>(P, work, nwork);
-    else if (vir) k_pair_fine<true, false><<<nwork, kPairThreads, 0, st>>>(P, work, nwork);
-    else k_pair_fine<false, false><<<nwork, kPairThreads, 0, st>>>(P, work, nwork);
+    if (dbg) launch_k(k_pair_fine<false, true>, nwork, kPairThreads, 0, st, P, work, nwork);
+    else if (vir) launch_k(k_pair_fine<true, false>, nwork, kPairThreads, 0, st, P, work, nwork);
+    else launch_k(k_pair_fine<false, false>, nwork, kPairThreads, 0, st, P, work, nwork);
     return;
   }
   if (warp_items && !dbg && !P.ptab && ctas > 0 && counter) {
@@ -248,8 +251,8 @@ void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell
     const int wpc = tb / 32;
     const int grid = std::max(1, std::min(ctas, (ntot + wpc - 1) / wpc));
     const size_t shm = sizeof(WarpSmem) * wpc;
-    if (vir) k_pair_warp<true><<<grid, tb, shm, st>>>(P, work, nwork, nbi, counter);
-    else k_pair_warp<false><<<grid, tb, shm, st>>>(P, work, nwork, nbi, counter);
+    if (vir) launch_k(k_pair_warp<true>, grid, tb, shm, st, P, work, nwork, nbi, counter);
+    else launch_k(k_pair_warp<false>, grid, tb, shm, st, P, work, nwork, nbi, counter);
     return;
   }
   const int tb = (threads == 160 || threads == 192) ? threads : 128;
@@ -260,14 +263,14 @@ void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell
   const int grid = dyn ? std::max(1, std::min(ntot, ctas)) : ntot;
   if (!dyn) counter = nullptr;
   if (P.ptab) {  // several species
-    if (dbg) k_pair_f32<false, true, true><<<grid, tb, 0, st>>>(P, work, nwork, nbi, counter);
-    else if (vir) k_pair_f32<true, false, true><<<grid, tb, 0, st>>>(P, work, nwork, nbi, counter);
-    else k_pair_f32<false, false, true><<<grid, tb, 0, st>>>(P, work, nwork, nbi, counter);
+    if (dbg) launch_k(k_pair_f32<false, true, true>, grid, tb, 0, st, P, work, nwork, nbi, counter);
+    else if (vir) launch_k(k_pair_f32<true, false, true>, grid, tb, 0, st, P, work, nwork, nbi, counter);
+    else launch_k(k_pair_f32<false, false, true>, grid, tb, 0, st, P, work, nwork, nbi, counter);
     return;
   }
-  if (dbg) k_pair_f32<false, true, false><<<grid, tb, 0, st>>>(P, work, nwork, nbi, counter);
-  else if (vir) k_pair_f32<true, false, false><<<grid, tb, 0, st>>>(P, work, nwork, nbi, counter);
-  else k_pair_f32<false, false, false><<<grid, tb, 0, st>>>(P, work, nwork, nbi, counter);
+  if (dbg) launch_k(k_pair_f32<false, true, false>, grid, tb, 0, st, P, work, nwork, nbi, counter);
+  else if (vir) launch_k(k_pair_f32<true, false, false>, grid, tb, 0, st, P, work, nwork, nbi, counter);
+  else launch_k(k_pair_f32<false, false, false>, grid, tb, 0, st, P, work, nwork, nbi, counter);
 }
 
 }  // namespace gcme

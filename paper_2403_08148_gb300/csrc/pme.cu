@@ -6,11 +6,13 @@ namespace gcme {
 
 template <typename R, int PO>
 __global__ void k_spread(Pool P) {
+  pdl_begin();
   dev_spread<R, PO>(P, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
 template <typename R, int PO>
 __global__ void k_gather(Pool P) {
+  pdl_begin();
   dev_gather<R, PO>(P, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
@@ -21,8 +23,8 @@ static void launch_spread_gather(const Pool &P, int order, bool gather, int nb, 
                                  cudaStream_t st) {
 #define GCME_SG(PO)                                          \
   do {                                                       \
-    if (gather) k_gather<R, PO><<<nb, tb, 0, st>>>(P);       \
-    else k_spread<R, PO><<<nb, tb, 0, st>>>(P);              \
+    if (gather) launch_k(k_gather<R, PO>, nb, tb, 0, st, P); \
+    else launch_k(k_spread<R, PO>, nb, tb, 0, st, P);        \
   } while (0)
   switch (order) {
     case 4: GCME_SG(4); break;
@@ -36,6 +38,7 @@ static void launch_spread_gather(const Pool &P, int order, bool gather, int nb, 
 template <typename R, bool INV>
 __global__ void __launch_bounds__(512) k_fft_plane(Pool P, const int2 *work, int nwork) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_begin();
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) dev_fft_plane<R, INV>(P, work, w, smem_raw);
 }
 
@@ -43,6 +46,7 @@ template <typename R, bool VIR>
 __global__ void __launch_bounds__(256) k_fft(Pool P, const int2 *work, int nwork, int axis, int kind,
                                              int lpb, int half) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_begin();
   for (int w = blockIdx.x; w < nwork; w += gridDim.x)
     dev_fft_item<R, VIR>(P, work, w, axis, kind, lpb, half, smem_raw);
 }
@@ -63,20 +67,20 @@ void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStrea
     const int nw = pl.nwork[ax], lpb = pl.lpb[ax];
     if (nw == 0) return;
     if (fp64) {
-      if (vir) k_fft<double, true><<<nw, 256, shm, st>>>(P, pl.work[ax], nw, ax, kind, lpb, half);
-      else k_fft<double, false><<<nw, 256, shm, st>>>(P, pl.work[ax], nw, ax, kind, lpb, half);
+      if (vir) launch_k(k_fft<double, true>, nw, 256, shm, st, P, pl.work[ax], nw, ax, kind, lpb, half);
+      else launch_k(k_fft<double, false>, nw, 256, shm, st, P, pl.work[ax], nw, ax, kind, lpb, half);
     } else {
-      if (vir) k_fft<float, true><<<nw, 256, shm, st>>>(P, pl.work[ax], nw, ax, kind, lpb, half);
-      else k_fft<float, false><<<nw, 256, shm, st>>>(P, pl.work[ax], nw, ax, kind, lpb, half);
+      if (vir) launch_k(k_fft<float, true>, nw, 256, shm, st, P, pl.work[ax], nw, ax, kind, lpb, half);
+      else launch_k(k_fft<float, false>, nw, 256, shm, st, P, pl.work[ax], nw, ax, kind, lpb, half);
     }
   };
   if (pl.use_plane) {
     const size_t shm = (2 * (size_t)pl.plane_elems + pl.kmax[0] + pl.kmax[1]) * rsz;
-    if (fp64) k_fft_plane<double, false><<<pl.nplane, 512, shm, st>>>(P, pl.plane_work, pl.nplane);
-    else k_fft_plane<float, false><<<pl.nplane, 512, shm, st>>>(P, pl.plane_work, pl.nplane);
+    if (fp64) launch_k(k_fft_plane<double, false>, pl.nplane, 512, shm, st, P, pl.plane_work, pl.nplane);
+    else launch_k(k_fft_plane<float, false>, pl.nplane, 512, shm, st, P, pl.plane_work, pl.nplane);
     line_pass(2, FFT_FWD_INFL_INV);
-    if (fp64) k_fft_plane<double, true><<<pl.nplane, 512, shm, st>>>(P, pl.plane_work, pl.nplane);
-    else k_fft_plane<float, true><<<pl.nplane, 512, shm, st>>>(P, pl.plane_work, pl.nplane);
+    if (fp64) launch_k(k_fft_plane<double, true>, pl.nplane, 512, shm, st, P, pl.plane_work, pl.nplane);
+    else launch_k(k_fft_plane<float, true>, pl.nplane, 512, shm, st, P, pl.plane_work, pl.nplane);
   } else {
     const int axes[5] = {0, 1, 2, 1, 0};
     const int kinds[5] = {FFT_FWD_FROM_Q, FFT_FWD, FFT_FWD_INFL_INV, FFT_INV, FFT_INV};
