@@ -732,7 +732,12 @@ def served_c5(g, ctx, n_req=40, rate=200.0, steps=1000, chunk=100):
                 "makespan_s": span, "bead_steps_per_s": beadsteps / span,
                 "steps_per_s": len(reqs) * steps / span,
                 "completed_per_s": len(reqs) / span, "peak_active": st["peak_active"],
-                "chunks": st["chunks"]}
+                "chunks": st["chunks"], "engines_built": st["engines_built"],
+                "build_ms_per_engine": st["build_us"] / 1e3 / max(1, st["engines_built"]),
+                "build_s_total": st["build_us"] / 1e6, "chunk_wait_s_total": st["wait_us"] / 1e6,
+                "build_note": "pooled engines for a new active set are built and captured on "
+                              "the host while the running chunk is on the GPU (except the "
+                              "first); chunk_wait is the worker's time waiting for chunks"}
     reqs = synth.config5_requests(n_req, rate=rate, steps=steps)
     offered = run(reqs)
     offered["offered_rate_per_s"] = rate

@@ -494,8 +494,11 @@ int gcme_cancel(gcme_server *srv, uint64_t ticket);
 /* Block until every submitted request has finished (or timeout_s passes). */
 int gcme_server_drain(gcme_server *srv, double timeout_s);
 /* Counters: [0] admitted, [1] completed, [2] rejected, [3] chunks run,
- * [4] bead-steps done, [5] peak active, [6] peak bytes in use. */
-int gcme_server_stats(gcme_server *srv, int64_t *out7);
+ * [4] bead-steps done, [5] peak active, [6] peak bytes in use, [7] pooled
+ * engines built for a new active set, [8] host microseconds spent building
+ * them (overlapping the running chunk except for the first), [9] host
+ * microseconds waiting for chunks to finish. */
+int gcme_server_stats(gcme_server *srv, int64_t *out10);
 
 #ifdef __cplusplus
 }

@@ -564,7 +564,8 @@ class Server:
         _check(load().gcme_server_drain(self.h, float(timeout_s)))
 
     def stats(self):
-        out = np.zeros(7, np.int64)
+        out = np.zeros(10, np.int64)
         _check(load().gcme_server_stats(self.h, out.ctypes.data))
         return dict(zip(("admitted", "completed", "rejected", "chunks", "bead_steps",
-                         "peak_active", "peak_bytes"), out.tolist()))
+                         "peak_active", "peak_bytes", "engines_built", "build_us", "wait_us"),
+                        out.tolist()))

@@ -2077,8 +2077,7 @@ int gcme_batch_step(gcme_batch *b, int64_t nsteps, int32_t mode, gcme_stream_t s
   }
   if (nsteps == 0) return GCME_OK;
   int lr = launch_persistent(b->eng.cell_only(Q), b->eng.pair_work, b->eng.n_pair_work, b->eng.cell_factor,
-                             b->eng.plan, nsteps, b->eng.bar_words, 2.0, st,
-                             b->eng.pair_nelec == 0);
+                             b->eng.plan, nsteps, b->eng.bar_words, 2.0, st, true);
   if (lr != 0) {
     cudaError_t e = cudaGetLastError();
     set_error(std::string("persistent cooperative launch failed: ") + cudaGetErrorString(e));

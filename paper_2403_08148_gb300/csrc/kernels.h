@@ -80,7 +80,10 @@ void launch_kick_drift(const Pool &P, bool vel64, cudaStream_t st);
 void launch_kick(const Pool &P, bool vel64, cudaStream_t st);
 // one cooperative launch of nsteps steps of the whole batch (FP32); the
 // four words at bar_words hold the barrier state and the error word;
-// warp_items: the pair work list holds warp items (one warp per item)
+// warp_items: the pair phase runs one warp per work item (pair_warp.cuh;
+// one-species 27-cell batches): the work list of CTA items is the list of
+// warp items with one chunk group per (home cell, part), so either list
+// serves
 int launch_persistent(const Pool &P, const int2 *pair_work, int n_pair_work, int cell_factor,
                       const PmePlan &pl,
                       long long nsteps, unsigned int *bar_words, double timeout_s,

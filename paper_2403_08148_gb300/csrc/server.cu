@@ -5,12 +5,13 @@
 // one pooled batch engine and repeatedly runs chunks of steps over all of
 // them; between chunks it retires finished requests (device -> host copy of
 // their final state) and admits queued ones whose device footprint fits the
-// memory budget and a free slot.  A change of the active set rebuilds the
-// pooled layout and carries the state of continuing systems over with
-// device-to-device copies, so their trajectories are unaffected: every
-// kernel's arithmetic for a system depends only on that system, and all
-// accumulation is fixed point, so a request's result is bit-identical alone
-// and in any mix.
+// memory budget and a free slot.  A change of the active set moves to a new
+// pooled layout, built and captured on the host while the current chunk
+// runs on the GPU, and carries the state of continuing systems over with
+// device-to-device copies ordered after the chunk, so their trajectories are
+// unaffected: every kernel's arithmetic for a system depends only on that
+// system, and all accumulation is fixed point, so a request's result is
+// bit-identical alone and in any mix.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -39,6 +40,7 @@ struct Req {
   std::vector<double> pos;
   std::vector<float> vel;
   int64_t nsteps = 0, done = 0;
+  int64_t done_at_hand_over = 0;  // worker's copy of done, taken under the lock
   int32_t status = 1;  // 1 queued, 2 running, 0 done, <0 error
   bool cancel = false;
   size_t bytes = 0;
@@ -90,67 +92,105 @@ struct gcme_server {
   std::thread worker;
   cudaStream_t stream = nullptr;
   std::unique_ptr<Engine> eng;
+  std::unique_ptr<Engine> eng_keep;  // replaced engine, freed after the stream's work on it
   std::vector<uint64_t> eng_members;
+  std::vector<unsigned long long> ctr_staging;
   bool forces_valid = false;
   int64_t st_admitted = 0, st_completed = 0, st_rejected = 0, st_chunks = 0, st_beadsteps = 0,
-          st_peak_active = 0, st_peak_bytes = 0;
+          st_peak_active = 0, st_peak_bytes = 0, st_rebuilds = 0;
+  double st_rebuild_s = 0.0, st_wait_s = 0.0;
   std::string worker_error;
 
   void run();
-  int rebuild(const std::vector<uint64_t> &members);
+  std::unique_ptr<Engine> make_engine(const std::vector<Req *> &members, int *rc);
+  void hand_over(Engine &ne, const std::vector<Req *> &members, int64_t ahead);
+  void admit_into(std::vector<uint64_t> &set, size_t used);
 };
 
-// Rebuild the pooled engine for a new active set, carrying device state of
-// systems that stay active.
-int gcme_server::rebuild(const std::vector<uint64_t> &members) {
+// A pooled engine for an active set, with its step and force graphs
+// captured (host work: it runs while the previous chunk is on the GPU; the
+// engine's setup copies use the legacy stream, which a non-blocking stream's
+// work does not wait for, and vice versa).
+std::unique_ptr<Engine> gcme_server::make_engine(const std::vector<Req *> &members, int *rc) {
   std::vector<SysSpec> specs;
-  for (uint64_t t : members) specs.push_back(reqs[t]->spec);
+  for (const Req *r : members) specs.push_back(r->spec);
   std::unique_ptr<Engine> ne(new Engine);
-  int rc = ne->build(device, specs, true);
-  if (rc) return rc;
+  *rc = ne->build(device, specs, true);
+  if (*rc) return nullptr;
+  cudaGraphExec_t g;
+  *rc = ne->forces_graph(ne->P, &g);
+  if (!*rc) *rc = ne->step_graph(ne->P, &g);
+  return *rc ? nullptr : std::move(ne);
+}
+
+// Enqueue on `stream` the state of every member into engine ne: a device
+// copy from the current engine for members that continue, the submitted
+// host state for new ones; each member keeps its own step counter (the
+// Langevin noise counter): its steps done, plus `ahead` for continuing
+// members (the steps of the chunk on the stream before these copies).
+// Ordered after the work already on the stream.
+void gcme_server::hand_over(Engine &ne, const std::vector<Req *> &members, int64_t ahead) {
+  ctr_staging.resize(members.size());
   for (size_t k = 0; k < members.size(); ++k) {
-    const uint64_t t = members[k];
-    Req &r = *reqs[t];
-    const long long off = ne->bead_off[k], n = r.spec.n;
-    auto it = std::find(eng_members.begin(), eng_members.end(), t);
+    Req &r = *members[k];
+    const long long off = ne.bead_off[k], n = r.spec.n;
+    auto it = std::find(eng_members.begin(), eng_members.end(), r.ticket);
+    ctr_staging[k] = (unsigned long long)(r.done_at_hand_over +
+                                          (eng && it != eng_members.end() ? ahead : 0));
     if (eng && it != eng_members.end()) {
       const long long ooff = eng->bead_off[it - eng_members.begin()];
-      cudaMemcpyAsync(ne->P.pos + 3 * off, eng->P.pos + 3 * ooff, sizeof(double) * 3 * n,
+      cudaMemcpyAsync(ne.P.pos + 3 * off, eng->P.pos + 3 * ooff, sizeof(double) * 3 * n,
                       cudaMemcpyDeviceToDevice, stream);
-      cudaMemcpyAsync(reinterpret_cast<float *>(ne->P.vel) + 3 * off,
+      cudaMemcpyAsync(reinterpret_cast<float *>(ne.P.vel) + 3 * off,
                       reinterpret_cast<float *>(eng->P.vel) + 3 * ooff, sizeof(float) * 3 * n,
                       cudaMemcpyDeviceToDevice, stream);
     } else {
-      cudaMemcpyAsync(ne->P.pos + 3 * off, r.pos.data(), sizeof(double) * 3 * n,
+      cudaMemcpyAsync(ne.P.pos + 3 * off, r.pos.data(), sizeof(double) * 3 * n,
                       cudaMemcpyHostToDevice, stream);
-      cudaMemcpyAsync(reinterpret_cast<float *>(ne->P.vel) + 3 * off, r.vel.data(),
+      cudaMemcpyAsync(reinterpret_cast<float *>(ne.P.vel) + 3 * off, r.vel.data(),
                       sizeof(float) * 3 * n, cudaMemcpyHostToDevice, stream);
     }
   }
-  // step counters: each request continues its own (the Langevin noise counter)
-  std::vector<unsigned long long> ctr(members.size());
-  for (size_t k = 0; k < members.size(); ++k) ctr[k] = (unsigned long long)reqs[members[k]]->done;
-  cudaMemcpyAsync(ne->P.step_ctr, ctr.data(), sizeof(unsigned long long) * ctr.size(),
-                  cudaMemcpyHostToDevice, stream);
-  cudaError_t e = cudaStreamSynchronize(stream);
-  if (e != cudaSuccess) {
-    set_error(std::string("server rebuild: ") + cudaGetErrorString(e));
-    return GCME_ERR_CUDA;
-  }
-  eng = std::move(ne);
-  eng_members = members;
-  forces_valid = false;
-  st_peak_bytes = std::max<int64_t>(st_peak_bytes, (int64_t)eng->scratch_bytes);
-  return GCME_OK;
+  cudaMemcpyAsync(ne.P.step_ctr, ctr_staging.data(),
+                  sizeof(unsigned long long) * ctr_staging.size(), cudaMemcpyHostToDevice, stream);
 }
 
+// Admit queued requests (FIFO) while slots and the memory budget allow,
+// given the bytes already held; called with the lock held.
+void gcme_server::admit_into(std::vector<uint64_t> &set, size_t used) {
+  while (!queue.empty() && (int)set.size() < max_active) {
+    Req &r = *reqs[queue.front()];
+    if (r.cancel) {
+      r.status = GCME_ERR_INVALID;
+      r.t_done = now_s();
+      queue.pop_front();
+      cv_done.notify_all();
+      continue;
+    }
+    if (used + r.bytes > budget) break;
+    used += r.bytes;
+    r.status = 2;
+    r.t_admit = now_s();
+    set.push_back(queue.front());
+    queue.pop_front();
+    ++st_admitted;
+  }
+}
+
+// The worker: one chunk of steps of the active set at a time.  While a
+// chunk runs on the GPU the worker decides the next active set (the members
+// that do not finish in this chunk, then queued requests as memory allows)
+// and, when it differs, builds and captures the next pooled engine; the
+// hand-over of the state (device copies, new requests' host state), the copy
+// out of finished members and the next chunk follow on the same stream,
+// with one synchronisation per chunk.
 void gcme_server::run() {
   cudaSetDevice(device);
   std::unique_lock<std::mutex> lk(mu);
   while (true) {
     cv.wait(lk, [&] { return stop || !queue.empty() || !active.empty(); });
     if (stop) break;
-    // ---- retire cancelled
+    // ---- retire cancelled, admit
     for (auto it = active.begin(); it != active.end();) {
       Req &r = *reqs[*it];
       if (r.cancel) {
@@ -162,35 +202,40 @@ void gcme_server::run() {
         ++it;
       }
     }
-    // ---- admit (FIFO) while slots and memory allow
-    size_t used = 0;
-    for (uint64_t t : active) used += reqs[t]->bytes;
-    while (!queue.empty() && (int)active.size() < max_active) {
-      Req &r = *reqs[queue.front()];
-      if (r.cancel) {
-        r.status = GCME_ERR_INVALID;
-        r.t_done = now_s();
-        queue.pop_front();
-        cv_done.notify_all();
-        continue;
-      }
-      if (used + r.bytes > budget) break;
-      used += r.bytes;
-      r.status = 2;
-      r.t_admit = now_s();
-      active.push_back(queue.front());
-      queue.pop_front();
-      ++st_admitted;
+    // with an engine ready for the active set, newcomers wait for the next
+    // chunk's overlapped decision instead of forcing a build here
+    if (active.empty() || active != eng_members || !eng) {
+      size_t used = 0;
+      for (uint64_t t : active) used += reqs[t]->bytes;
+      admit_into(active, used);
     }
     if (active.empty()) continue;
     st_peak_active = std::max<int64_t>(st_peak_active, (int64_t)active.size());
-    std::vector<uint64_t> members = active;
+    const std::vector<uint64_t> members = active;
+    std::vector<Req *> mreq;  // pointers stay valid: active requests are not erased
     int64_t steps = chunk;
-    for (uint64_t t : members) steps = std::min(steps, reqs[t]->nsteps - reqs[t]->done);
-    const bool changed = members != eng_members;
+    for (uint64_t t : members) {
+      Req *r = reqs[t].get();
+      r->done_at_hand_over = r->done;
+      mreq.push_back(r);
+      steps = std::min(steps, r->nsteps - r->done);
+    }
     lk.unlock();
     int rc = GCME_OK;
-    if (changed) rc = rebuild(members);
+    if (members != eng_members) {  // first chunk, or after a cancellation or an error
+      const double t0 = now_s();
+      std::unique_ptr<Engine> ne = make_engine(mreq, &rc);
+      if (!rc) hand_over(*ne, mreq, 0);
+      st_rebuild_s += now_s() - t0;
+      ++st_rebuilds;
+      if (!rc) {
+        eng_keep = std::move(eng);  // freed after the next synchronisation
+        eng = std::move(ne);
+        eng_members = members;
+        forces_valid = false;
+      }
+    }
+    // ---- the chunk (asynchronous)
     if (rc == GCME_OK && steps > 0) {
       cudaGraphExec_t fg, sg;
       rc = eng->forces_graph(eng->P, &fg);
@@ -200,34 +245,64 @@ void gcme_server::run() {
         forces_valid = true;
       }
       for (int64_t k = 0; !rc && k < steps; ++k) cudaGraphLaunch(sg, stream);
-      cudaError_t e = cudaStreamSynchronize(stream);
-      if (e != cudaSuccess) {
-        set_error(std::string("server chunk: ") + cudaGetErrorString(e));
-        rc = GCME_ERR_CUDA;
-      }
     }
-    // ---- copy out finished systems
+    // ---- meanwhile: the next active set and its engine
     std::vector<char> fin(members.size(), 0);
-    if (rc == GCME_OK) {
-      std::vector<double> E((size_t)GCME_NTERMS * members.size());
-      cudaMemcpy(E.data(), eng->P.energy, sizeof(double) * E.size(), cudaMemcpyDeviceToHost);
-      for (size_t k = 0; k < members.size(); ++k) {
-        Req &r = *reqs[members[k]];
-        if (r.done + steps >= r.nsteps) {
-          fin[k] = 1;
-          const long long off = eng->bead_off[k], n = r.spec.n;
-          cudaMemcpy(r.pos.data(), eng->P.pos + 3 * off, sizeof(double) * 3 * n,
-                     cudaMemcpyDeviceToHost);
-          cudaMemcpy(r.vel.data(), reinterpret_cast<float *>(eng->P.vel) + 3 * off,
-                     sizeof(float) * 3 * n, cudaMemcpyDeviceToHost);
-          std::memcpy(r.energy, &E[(size_t)GCME_NTERMS * k], sizeof(double) * GCME_NTERMS);
-        }
+    std::vector<uint64_t> next;
+    std::vector<Req *> nreq;
+    size_t next_used = 0;
+    lk.lock();
+    for (size_t k = 0; k < members.size(); ++k) {
+      Req &r = *mreq[k];
+      fin[k] = r.done + steps >= r.nsteps;
+      if (!fin[k] && !r.cancel) {
+        next.push_back(members[k]);
+        next_used += r.bytes;
       }
     }
+    if (rc == GCME_OK) admit_into(next, next_used);
+    for (uint64_t t : next) {
+      Req *r = reqs[t].get();
+      r->done_at_hand_over = r->done;
+      nreq.push_back(r);
+    }
+    lk.unlock();
+    std::unique_ptr<Engine> ne;
+    if (rc == GCME_OK && !next.empty() && next != members) {
+      const double t0 = now_s();
+      ne = make_engine(nreq, &rc);
+      st_rebuild_s += now_s() - t0;
+      ++st_rebuilds;
+    }
+    // ---- on the stream after the chunk: copy out finished members, hand
+    // the state over to the next engine; then wait once
+    std::vector<double> E((size_t)GCME_NTERMS * members.size());
+    if (rc == GCME_OK) {
+      cudaMemcpyAsync(E.data(), eng->P.energy, sizeof(double) * E.size(), cudaMemcpyDeviceToHost,
+                      stream);
+      for (size_t k = 0; k < members.size(); ++k) {
+        if (!fin[k]) continue;
+        Req &r = *mreq[k];
+        const long long off = eng->bead_off[k], n = r.spec.n;
+        cudaMemcpyAsync(r.pos.data(), eng->P.pos + 3 * off, sizeof(double) * 3 * n,
+                        cudaMemcpyDeviceToHost, stream);
+        cudaMemcpyAsync(r.vel.data(), reinterpret_cast<float *>(eng->P.vel) + 3 * off,
+                        sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, stream);
+      }
+      if (ne) hand_over(*ne, nreq, steps);  // continuing members: steps done after this chunk
+    }
+    const double tw = now_s();
+    cudaError_t e = cudaStreamSynchronize(stream);
+    st_wait_s += now_s() - tw;
+    if (rc == GCME_OK && e != cudaSuccess) {
+      set_error(std::string("server chunk: ") + cudaGetErrorString(e));
+      rc = GCME_ERR_CUDA;
+    }
+    eng_keep.reset();  // an engine replaced before this chunk is idle now
     lk.lock();
     ++st_chunks;
     for (size_t k = 0; k < members.size(); ++k) {
-      Req &r = *reqs[members[k]];
+      Req &r = *mreq[k];
       if (rc != GCME_OK) {
         r.status = rc;
         r.t_done = now_s();
@@ -236,21 +311,38 @@ void gcme_server::run() {
       r.done += steps;
       st_beadsteps += steps * r.spec.n;
       if (fin[k]) {
+        std::memcpy(r.energy, &E[(size_t)GCME_NTERMS * k], sizeof(double) * GCME_NTERMS);
         r.status = 0;
         r.t_done = now_s();
         ++st_completed;
+      } else if (std::find(next.begin(), next.end(), members[k]) == next.end()) {
+        r.status = GCME_ERR_INVALID;  // cancelled while its chunk ran
+        r.t_done = now_s();
       }
     }
     if (rc != GCME_OK) {
       worker_error = gcme_last_error();
+      for (Req *rp : nreq) {  // admitted for the next chunk: failed too
+        Req &r = *rp;
+        if (r.status == 2) {
+          r.status = rc;
+          r.t_done = now_s();
+        }
+      }
       active.clear();
       eng.reset();
+      ne.reset();
       eng_members.clear();
     } else {
-      active.erase(std::remove_if(active.begin(), active.end(),
-                                  [&](uint64_t t) { return reqs[t]->status == 0; }),
-                   active.end());
+      active = next;
+      if (ne) {
+        eng.swap(ne);  // ne now holds the old engine, idle after the wait above
+        eng_members = next;
+        forces_valid = false;
+        st_peak_bytes = std::max<int64_t>(st_peak_bytes, (int64_t)eng->scratch_bytes);
+      }
     }
+    ne.reset();
     cv_done.notify_all();
   }
 }
@@ -406,19 +498,22 @@ int gcme_server_drain(gcme_server *srv, double timeout_s) {
   return GCME_OK;
 }
 
-int gcme_server_stats(gcme_server *srv, int64_t *out7) {
-  if (!srv || !out7) {
+int gcme_server_stats(gcme_server *srv, int64_t *out10) {
+  if (!srv || !out10) {
     set_error("NULL argument");
     return GCME_ERR_INVALID;
   }
   std::lock_guard<std::mutex> g(srv->mu);
-  out7[0] = srv->st_admitted;
-  out7[1] = srv->st_completed;
-  out7[2] = srv->st_rejected;
-  out7[3] = srv->st_chunks;
-  out7[4] = srv->st_beadsteps;
-  out7[5] = srv->st_peak_active;
-  out7[6] = srv->st_peak_bytes;
+  out10[0] = srv->st_admitted;
+  out10[1] = srv->st_completed;
+  out10[2] = srv->st_rejected;
+  out10[3] = srv->st_chunks;
+  out10[4] = srv->st_beadsteps;
+  out10[5] = srv->st_peak_active;
+  out10[6] = srv->st_peak_bytes;
+  out10[7] = srv->st_rebuilds;
+  out10[8] = (int64_t)(srv->st_rebuild_s * 1e6);
+  out10[9] = (int64_t)(srv->st_wait_s * 1e6);
   return GCME_OK;
 }
 
