@@ -384,10 +384,14 @@ int gcme_debug_barrier_timeout(gcme_ctx *ctx, double timeout_s, gcme_stream_t st
  * same warp, 64, 96 or 128 threads per CTA, pair_ctas_per_sm >= 1 resident
  * CTAs with at most 28 warps per SM); its items are split by chunks of 32
  * home beads into pair_chunks items per (home cell, part): 1 to 4, or 0 for
- * the median real-bead count of the system's non-empty cells / 32. */
+ * the median real-bead count of the system's non-empty cells / 32.
+ * spread_cells = 1 spreads the charges (FP32, 27-cell path without lists)
+ * cell by cell through a brick of the grid in shared memory, the PME branch
+ * then starting after the cell sort; 0 spreads each charge straight to the
+ * grid in global memory, the branch starting after binning. */
 typedef struct gcme_tuning {
   int32_t pair_split, pair_threads, pair_ctas_per_sm, fft_lpb[3], fft_plane, from_cache,
-      cell_factor, pair_nelec, pair_chunks;
+      cell_factor, pair_nelec, pair_chunks, spread_cells;
   double forces_ms, pme_ms;
 } gcme_tuning;
 
@@ -405,7 +409,7 @@ int gcme_autotune(gcme_sys *sys, const double *d_pos, int32_t flags, gcme_tuning
 
 /* Apply given launch shapes without timing (e.g. a tuning recorded
  * elsewhere, or to pin one path): pair_split, pair_threads, pair_nelec,
- * pair_chunks and pair_ctas_per_sm (27-cell path of cell_factor 1 only; ignored otherwise),
+ * pair_chunks, spread_cells and pair_ctas_per_sm (27-cell path of cell_factor 1 only; ignored otherwise),
  * fft_lpb[3] and fft_plane are read, every other field ignored.  A shape out
  * of range (see gcme_tuning), lines per tile or x-y planes that do not fit in
  * shared memory return GCME_ERR_INVALID and leave the shapes unchanged.

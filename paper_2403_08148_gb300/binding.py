@@ -66,7 +66,7 @@ class Tuning(ctypes.Structure):
                 ("pair_ctas_per_sm", ctypes.c_int32), ("fft_lpb", ctypes.c_int32 * 3),
                 ("fft_plane", ctypes.c_int32), ("from_cache", ctypes.c_int32),
                 ("cell_factor", ctypes.c_int32), ("pair_nelec", ctypes.c_int32),
-                ("pair_chunks", ctypes.c_int32),
+                ("pair_chunks", ctypes.c_int32), ("spread_cells", ctypes.c_int32),
                 ("forces_ms", ctypes.c_double), ("pme_ms", ctypes.c_double)]
 
     @classmethod
@@ -75,6 +75,7 @@ class Tuning(ctypes.Structure):
         for k in ("pair_split", "pair_threads", "pair_ctas_per_sm", "pair_nelec"):
             setattr(t, k, int(d[k]))
         t.pair_chunks = int(d.get("pair_chunks", 0))
+        t.spread_cells = int(bool(d.get("spread_cells", False)))
         for a in range(3):
             t.fft_lpb[a] = int(d["fft_lpb"][a])
         t.fft_plane = int(bool(d["fft_plane"]))
@@ -86,6 +87,7 @@ class Tuning(ctypes.Structure):
                 "fft_plane": bool(self.fft_plane),
                 "from_cache": bool(self.from_cache), "cell_factor": self.cell_factor,
                 "pair_nelec": self.pair_nelec, "pair_chunks": self.pair_chunks,
+                "spread_cells": bool(self.spread_cells),
                 "forces_ms": self.forces_ms,
                 "pme_ms": self.pme_ms}
 

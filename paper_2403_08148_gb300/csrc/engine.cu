@@ -524,8 +524,18 @@ int Engine::set_fft_plane(bool on) {
   return GCME_OK;
 }
 
+int Engine::set_spread_cells(bool on) {
+  if (on && !cell_spread_ok()) {
+    set_error("the cell spread needs the FP32 27-cell path without neighbour lists");
+    return GCME_ERR_INVALID;
+  }
+  plan.cell_spread = on ? 1 : 0;
+  clear_graphs();
+  return GCME_OK;
+}
+
 int Engine::apply_tuning(int split, int threads, int ctas_per_sm, int nelec, const int lpb[3],
-                         bool plane, int chunks) {
+                         bool plane, int chunks, bool spread_cells) {
   const bool pair_shapes = cell_factor == 1 && !use_list;
   const size_t rsz = fp64 ? sizeof(double2) : sizeof(float2);
   bool ok = !(plane && !plane_fits());
@@ -535,6 +545,7 @@ int Engine::apply_tuning(int split, int threads, int ctas_per_sm, int nelec, con
   if (pair_shapes)
     ok = ok && pair_shape_ok(split, threads, ctas_per_sm, nelec) && chunks >= 0 &&
          chunks <= kMaxPairChunks;
+  ok = ok && !(spread_cells && !cell_spread_ok());
   if (!ok) {
     set_error("launch shapes out of range or larger than shared memory");
     return GCME_ERR_INVALID;
@@ -542,6 +553,7 @@ int Engine::apply_tuning(int split, int threads, int ctas_per_sm, int nelec, con
   int rc = pair_shapes ? set_pair_config(split, threads, ctas_per_sm, nelec, chunks) : GCME_OK;
   for (int a = 0; !rc && a < 3; ++a) rc = set_fft_lpb(a, lpb[a]);
   if (!rc) rc = set_fft_plane(plane);
+  if (!rc) rc = set_spread_cells(spread_cells);
   return rc;
 }
 
@@ -865,6 +877,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   plan.order = hsys[0].order;
   for (auto &S : hsys)
     if (S.order != plan.order) plan.order = 0;
+  plan.cell_spread = 0;  // charges straight to the global grid unless tuned otherwise
   std::vector<int2> fftw[3];
   int fft_cap[3];
   plan.use_plane = 0;  // capacities for the full-spectrum lines
@@ -1159,12 +1172,15 @@ long long Engine::list_builds() {
 // Cell sort and pair kernels.  With lists: the sort and the list build run
 // only on rebuild steps (device flag), the refresh every step, then the
 // list kernel, and the 27-cell kernel for the systems whose lists overflowed.
-void Engine::enqueue_sort_pairs(const Pool &Q, cudaStream_t st, bool vir, bool dbg, bool timed) {
+void Engine::enqueue_sort_pairs(const Pool &Q, cudaStream_t st, bool vir, bool dbg, bool timed,
+                                int fork) {
   launch_sort(Q, st);
   if (use_list) {
     launch_list_build(Q, st);
     launch_list_refresh(Q, st);
   }
+  // the cell spread reads the sorted cell lists: the PME branch forks here
+  if (fork) fork_pme(Q, st, vir, timed, fork > 1);
   if (timed) cudaEventRecordWithFlags(phase_ev[2], st, cudaEventRecordExternal);
   if (use_list) launch_pair_list(Q, vir, dbg, st);
   launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, pair_ctas(), pair_counter,
@@ -1182,8 +1198,8 @@ void Engine::enqueue_forces(const Pool &Q, cudaStream_t st, bool vir, bool dbg) 
     enqueue_sort_pairs(Q, st, vir, true, false);
     return;
   }
-  fork_pme(Q, st, vir, false);
-  enqueue_sort_pairs(Q, st, vir, false, false);
+  if (!plan.cell_spread) fork_pme(Q, st, vir, false);
+  enqueue_sort_pairs(Q, st, vir, false, false, plan.cell_spread ? 2 : 0);
   launch_bonded(Q, vir, !bonds_in_pair(false), st);
   cudaStreamWaitEvent(st, join_ev, 0);
   launch_slab_apply(Q, st);
@@ -1200,8 +1216,8 @@ void Engine::enqueue_step(const Pool &Q, cudaStream_t st) {
   if (use_list) launch_list_check(Q, st);
   launch_bin(Q, st, false);
   if (ev) cudaEventRecordWithFlags(phase_ev[9], st, cudaEventRecordExternal);
-  fork_pme(Q, st, false, ev, false);
-  enqueue_sort_pairs(Q, st, false, false, ev);
+  if (!plan.cell_spread) fork_pme(Q, st, false, ev, false);
+  enqueue_sort_pairs(Q, st, false, false, ev, plan.cell_spread ? 1 : 0);
   launch_bonded(Q, false, !bonds_in_pair(false), st);
   if (ev) cudaEventRecordWithFlags(phase_ev[4], st, cudaEventRecordExternal);
   cudaStreamWaitEvent(st, join_ev, 0);
@@ -1865,6 +1881,7 @@ static void fill_tuning(const Engine &eng, double pair_ms, double pme_ms, bool h
   out->pair_ctas_per_sm = eng.pair_ctas_per_sm;
   out->pair_nelec = eng.pair_nelec;
   out->pair_chunks = eng.pair_chunks;
+  out->spread_cells = eng.plan.cell_spread;
   for (int a = 0; a < 3; ++a) out->fft_lpb[a] = eng.plan.lpb[a];
   out->fft_plane = eng.plan.use_plane;
   out->from_cache = hit ? 1 : 0;
@@ -1898,7 +1915,8 @@ int gcme_apply_tuning(gcme_sys *sys, const gcme_tuning *t) {
   }
   GCME_TRY_CK(cudaSetDevice(sys->eng.device));
   return sys->eng.apply_tuning(t->pair_split, t->pair_threads, t->pair_ctas_per_sm,
-                               t->pair_nelec, t->fft_lpb, t->fft_plane != 0, t->pair_chunks);
+                               t->pair_nelec, t->fft_lpb, t->fft_plane != 0, t->pair_chunks,
+                               t->spread_cells != 0);
 }
 
 int gcme_batch_apply_tuning(gcme_batch *bt, const gcme_tuning *t) {
@@ -1908,7 +1926,8 @@ int gcme_batch_apply_tuning(gcme_batch *bt, const gcme_tuning *t) {
   }
   GCME_TRY_CK(cudaSetDevice(bt->eng.device));
   return bt->eng.apply_tuning(t->pair_split, t->pair_threads, t->pair_ctas_per_sm,
-                              t->pair_nelec, t->fft_lpb, t->fft_plane != 0, t->pair_chunks);
+                              t->pair_nelec, t->fft_lpb, t->fft_plane != 0, t->pair_chunks,
+                              t->spread_cells != 0);
 }
 
 int gcme_batch_autotune(gcme_batch *bt, int32_t flags, gcme_tuning *out, gcme_stream_t stream) {
@@ -2077,7 +2096,8 @@ int gcme_batch_step(gcme_batch *b, int64_t nsteps, int32_t mode, gcme_stream_t s
   }
   if (nsteps == 0) return GCME_OK;
   int lr = launch_persistent(b->eng.cell_only(Q), b->eng.pair_work, b->eng.n_pair_work, b->eng.cell_factor,
-                             b->eng.plan, nsteps, b->eng.bar_words, 2.0, st, true);
+                             b->eng.plan, nsteps, b->eng.bar_words, 2.0, st,
+                             b->eng.pair_nelec == 0);
   if (lr != 0) {
     cudaError_t e = cudaGetLastError();
     set_error(std::string("persistent cooperative launch failed: ") + cudaGetErrorString(e));

@@ -74,8 +74,11 @@ class Engine {
   void enqueue_forces(const Pool &P, cudaStream_t st, bool vir, bool dbg);
   // enqueue one velocity-Verlet step (forces at P.pos must be current)
   void enqueue_step(const Pool &P, cudaStream_t st);
-  // cell sort (gated by the rebuild flag with lists) and the pair kernels
-  void enqueue_sort_pairs(const Pool &P, cudaStream_t st, bool vir, bool dbg, bool timed);
+  // cell sort (gated by the rebuild flag with lists) and the pair kernels;
+  // fork > 0: fork the PME branch after the sort (1: grid known to be zero,
+  // 2: clear it first)
+  void enqueue_sort_pairs(const Pool &P, cudaStream_t st, bool vir, bool dbg, bool timed,
+                          int fork = 0);
   // make the next force evaluation rebuild the neighbour lists (after the
   // cell order was changed outside the list path)
   void request_rebuild(cudaStream_t st);
@@ -111,7 +114,11 @@ class Engine {
   int set_fft_plane(bool on);
   // launch shapes given by the caller (checked before any is changed)
   int apply_tuning(int split, int threads, int ctas_per_sm, int nelec, const int lpb[3],
-                   bool plane, int chunks = 0);
+                   bool plane, int chunks = 0, bool spread_cells = false);
+  // charges spread cell by cell through shared memory (FP32 27-cell path
+  // without lists), else straight to the global grid
+  bool cell_spread_ok() const { return !fp64 && cell_factor == 1 && !use_list; }
+  int set_spread_cells(bool on);
   void clear_graphs();
   // time candidate configurations on the current state and keep the
   // fastest (tune.cu); from_cache reports a hit of the tuning cache

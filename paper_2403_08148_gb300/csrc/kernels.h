@@ -39,6 +39,9 @@ struct PmePlan {
   int use_plane;
   int plane_elems;  // largest K0 * K1 of the batch
   int order;        // B-spline order shared by every system, else 0
+  // FP32 spread by cells of the sorted cell list through shared memory
+  // (k_spread_cells): the PME branch then starts after the cell sort
+  int cell_spread;
 };
 
 void launch_cells(const Pool &P, cudaStream_t st);  // launch_bin + launch_sort
@@ -81,9 +84,8 @@ void launch_kick(const Pool &P, bool vel64, cudaStream_t st);
 // one cooperative launch of nsteps steps of the whole batch (FP32); the
 // four words at bar_words hold the barrier state and the error word;
 // warp_items: the pair phase runs one warp per work item (pair_warp.cuh;
-// one-species 27-cell batches): the work list of CTA items is the list of
-// warp items with one chunk group per (home cell, part), so either list
-// serves
+// one-species 27-cell batches), as the per-phase launches do under the same
+// launch shapes (the same kernel path gives the same roundings)
 int launch_persistent(const Pool &P, const int2 *pair_work, int n_pair_work, int cell_factor,
                       const PmePlan &pl,
                       long long nsteps, unsigned int *bar_words, double timeout_s,

@@ -73,7 +73,7 @@ struct PersistArgs {
                  _lim = ((n) + 31) / 32 * 32;                                        \
        i - threadIdx.x % 32 < _lim; i += (long long)gridDim.x * blockDim.x)
 
-__global__ void __launch_bounds__(128, 4) k_persistent(Pool P, PersistArgs A) {
+__global__ void __launch_bounds__(128) k_persistent(Pool P, PersistArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Barrier &B = A.bar;
   const long long gthreads = (long long)gridDim.x * blockDim.x;

@@ -10,6 +10,14 @@ __global__ void k_spread(Pool P) {
   dev_spread<R, PO>(P, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
+// one CTA per cell of the sorted cell list (FP32 path)
+template <int PO>
+__global__ void __launch_bounds__(128) k_spread_cells(Pool P) {
+  __shared__ SpreadSmem sm;
+  pdl_begin();
+  dev_spread_cell<PO>(P, blockIdx.x, sm);
+}
+
 template <typename R, int PO>
 __global__ void k_gather(Pool P) {
   pdl_begin();
@@ -57,8 +65,19 @@ void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStrea
   if (zero_grid) cudaMemsetAsync(P.qgrid, 0, sizeof(unsigned long long) * P.n_grid, st);
   const int tb = 256;
   const int nb = (int)((P.n_q * 8 + tb - 1) / tb);
-  if (fp64) launch_spread_gather<double>(P, pl.order, false, nb, tb, st);
-  else launch_spread_gather<float>(P, pl.order, false, nb, tb, st);
+  if (fp64) {
+    launch_spread_gather<double>(P, pl.order, false, nb, tb, st);
+  } else if (pl.cell_spread && P.n_cells > 0) {
+    const unsigned nc = (unsigned)P.n_cells;
+    switch (pl.order) {
+      case 4: launch_k(k_spread_cells<4>, nc, 128, 0, st, P); break;
+      case 5: launch_k(k_spread_cells<5>, nc, 128, 0, st, P); break;
+      case 6: launch_k(k_spread_cells<6>, nc, 128, 0, st, P); break;
+      default: launch_k(k_spread_cells<0>, nc, 128, 0, st, P); break;
+    }
+  } else {
+    launch_spread_gather<float>(P, pl.order, false, nb, tb, st);
+  }
   const size_t rsz = fp64 ? sizeof(double2) : sizeof(float2);
   // the z pass of the plane path works on the Hermitian half spectrum
   const int half = pl.use_plane;

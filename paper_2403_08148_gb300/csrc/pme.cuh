@@ -152,6 +152,124 @@ __device__ __forceinline__ void dev_spread(const Pool &P, long long g) {
 }
 
 // --------------------------------------------------------------------------
+// spread by cells through shared memory (FP32 path): one CTA per cell of the
+// sorted cell list spreads the cell's charged and image beads into a brick
+// of the grid held in shared memory with 64-bit integer atomics, then adds
+// the brick's nonzero points to the global grid (one fixed-point atomic per
+// point, consecutive along x).  Every contribution is rounded to fixed point
+// exactly as in dev_spread and all sums are integer, so the grid is the same
+// bit for bit as dev_spread's, whatever the order.  A cell with more than
+// kSpreadQ charges, or whose charges span a brick larger than kSpreadBrick
+// points, is spread straight to the global grid.
+// --------------------------------------------------------------------------
+constexpr int kSpreadQ = 128;
+constexpr int kSpreadBrick = 4096;
+constexpr int kSpreadMaxOrder = 8;
+
+struct SpreadSmem {
+  unsigned long long brick[kSpreadBrick];
+  float w[kSpreadQ][3][kSpreadMaxOrder];
+  float q[kSpreadQ];
+  int base[kSpreadQ][3];
+  int lo[3], hi[3];
+};
+
+template <int PO>
+__device__ __forceinline__ void dev_spread_cell(const Pool &P, long long c, SpreadSmem &sm) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const SysDesc &S = P.sys[P.cell_sys[c]];
+  const int p = PO > 0 ? PO : S.order;
+  const int beg = P.cell_start[c], nq = P.cell_nq[c];  // images and charged reals
+  if (nq == 0) return;
+  const int K0 = S.K[0], K1 = S.K[1], K2 = S.K[2];
+  unsigned long long *grid = P.qgrid + S.grid_off;
+  const float scale = (float)PmeT<float>::qscale;
+  if (nq > kSpreadQ) {  // straight to the global grid, one thread per (charge, z-plane)
+    for (int idx = tid; idx < nq * p; idx += nt) {
+      const int k = idx / p, tz = idx - k * p;
+      const float4 v = P.xyzq_s[beg + k];
+      const float x[3] = {v.x, v.y, v.z};
+      float W[3][kSpreadMaxOrder];
+      int b[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float u = x[a] * S.kfac[a];
+        const float fl = floorf(u);
+        b[a] = (int)fl;
+        bspline_weights<float>(p, u - fl, W[a], (float *)nullptr);
+      }
+      const float wz = W[2][tz] * v.w * scale;
+      const int kz = wrap_index(b[2] - tz, K2);
+      for (int ty = 0; ty < p; ++ty) {
+        const float wyz = W[1][ty] * wz;
+        unsigned long long *row = grid + (long long)K0 * (wrap_index(b[1] - ty, K1) + (long long)K1 * kz);
+        for (int tx = 0; tx < p; ++tx)
+          atomicAdd(row + wrap_index(b[0] - tx, K0), (unsigned long long)to_fixed(W[0][tx] * wyz));
+      }
+    }
+    return;
+  }
+  if (tid < 3) {
+    sm.lo[tid] = 1 << 30;
+    sm.hi[tid] = -(1 << 30);
+  }
+  __syncthreads();
+  for (int k = tid; k < nq; k += nt) {  // weights and bases of each charge
+    const float4 v = P.xyzq_s[beg + k];
+    const float x[3] = {v.x, v.y, v.z};
+    sm.q[k] = v.w;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float u = x[a] * S.kfac[a];
+      const float fl = floorf(u);
+      const int b = (int)fl;
+      sm.base[k][a] = b;
+      bspline_weights<float>(p, u - fl, sm.w[k][a], (float *)nullptr);
+      atomicMin(&sm.lo[a], b);
+      atomicMax(&sm.hi[a], b);
+    }
+  }
+  __syncthreads();
+  // brick: grid points base - t (t < p) of every charge, from lo - (p - 1)
+  const int E0 = sm.hi[0] - sm.lo[0] + p, E1 = sm.hi[1] - sm.lo[1] + p,
+            E2 = sm.hi[2] - sm.lo[2] + p;
+  const int o0 = sm.lo[0] - (p - 1), o1 = sm.lo[1] - (p - 1), o2 = sm.lo[2] - (p - 1);
+  const int npts = E0 * E1 * E2;
+  if (npts > kSpreadBrick) {  // charges spread over a wide brick: global atomics
+    for (int idx = tid; idx < nq * p * p * p; idx += nt) {
+      const int k = idx / (p * p * p), r = idx - k * p * p * p;
+      const int tz = r / (p * p), ty = (r / p) % p, tx = r % p;
+      const float wyz = sm.w[k][1][ty] * (sm.w[k][2][tz] * sm.q[k] * scale);
+      const long long gi = wrap_index(sm.base[k][0] - tx, K0) +
+                           (long long)K0 * (wrap_index(sm.base[k][1] - ty, K1) +
+                                            (long long)K1 * wrap_index(sm.base[k][2] - tz, K2));
+      atomicAdd(grid + gi, (unsigned long long)to_fixed(sm.w[k][0][tx] * wyz));
+    }
+    return;
+  }
+  for (int i = tid; i < npts; i += nt) sm.brick[i] = 0ull;
+  __syncthreads();
+  for (int idx = tid; idx < nq * p * p * p; idx += nt) {
+    const int k = idx / (p * p * p), r = idx - k * p * p * p;
+    const int tz = r / (p * p), ty = (r / p) % p, tx = r % p;
+    // the same roundings as dev_spread: (W_x (W_y (W_z q scale)))
+    const float wyz = sm.w[k][1][ty] * (sm.w[k][2][tz] * sm.q[k] * scale);
+    const int li = (sm.base[k][0] - tx - o0) + E0 * ((sm.base[k][1] - ty - o1) +
+                                                      E1 * (sm.base[k][2] - tz - o2));
+    atomicAdd(&sm.brick[li], (unsigned long long)to_fixed(sm.w[k][0][tx] * wyz));
+  }
+  __syncthreads();
+  for (int i = tid; i < npts; i += nt) {
+    const unsigned long long v = sm.brick[i];
+    if (v == 0ull) continue;
+    const int ex = i % E0, ey = (i / E0) % E1, ez = i / (E0 * E1);
+    const long long gi = wrap_index(o0 + ex, K0) +
+                         (long long)K0 * (wrap_index(o1 + ey, K1) + (long long)K1 * wrap_index(o2 + ez, K2));
+    atomicAdd(grid + gi, v);
+  }
+}
+
+// --------------------------------------------------------------------------
 // gather: eight lanes per charged real bead, reduced with shuffles
 // --------------------------------------------------------------------------
 // Warp-synchronous: every lane of the warp must call it (lanes past the end

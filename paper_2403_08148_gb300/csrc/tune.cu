@@ -10,8 +10,10 @@
 //                concurrent PME branch}, and one warp per work item
 //                (CTAs of 4 warps, 3-7 per SM, or of 2 warps, 8-14 per SM);
 //   PME:         lines per FFT tile along each axis in {4, 8, 16, 32, 64}
-//                (shared memory permitting), one axis at a time, and x-y
-//                plane passes (one CTA per z-plane) vs per-axis passes;
+//                (shared memory permitting), one axis at a time, x-y
+//                plane passes (one CTA per z-plane) vs per-axis passes, and
+//                the charge spread by cells through shared memory vs
+//                straight to the global grid;
 // each candidate timed on replays of the captured force-evaluation graph.
 // The fastest configuration is kept and recorded in a JSON-lines cache
 // (GCME_TUNE_CACHE, else $HOME/.cache/gcme_tune.jsonl) keyed by the GPU
@@ -45,7 +47,8 @@ std::string cache_path() {
 }
 
 struct Tuned {
-  int split = 0, threads = 0, ctas = 0, lpb[3] = {0, 0, 0}, plane = 0, nelec = 1, chunks = 0;
+  int split = 0, threads = 0, ctas = 0, lpb[3] = {0, 0, 0}, plane = 0, nelec = 1, chunks = 0,
+      spread = 0;
   double pair_ms = 0, pme_ms = 0;
 };
 
@@ -70,6 +73,8 @@ bool cache_lookup(const std::string &key, Tuned *t) {
       if (e && std::sscanf(e, "\"pair_nelec\": %d", &x.nelec) != 1) x.nelec = 1;
       const char *h = std::strstr(line.c_str(), "\"pair_chunks\":");
       if (!h || std::sscanf(h, "\"pair_chunks\": %d", &x.chunks) != 1) x.chunks = 0;
+      const char *sc = std::strstr(line.c_str(), "\"spread_cells\":");
+      if (!sc || std::sscanf(sc, "\"spread_cells\": %d", &x.spread) != 1) x.spread = 0;
       *t = x;  // the last entry for a key wins
       found = true;
     }
@@ -86,9 +91,9 @@ void cache_store(const std::string &key, const Tuned &t) {
                 "{\"key\": \"%s\", \"pair_split\": %d, \"pair_threads\": %d, "
                 "\"pair_ctas_per_sm\": %d, \"fft_lpb\": [%d, %d, %d], \"fft_plane\": %d, "
                 "\"forces_ms\": %.6f, \"pme_ms\": %.6f, \"pair_nelec\": %d, "
-                "\"pair_chunks\": %d}\n",
+                "\"pair_chunks\": %d, \"spread_cells\": %d}\n",
                 key.c_str(), t.split, t.threads, t.ctas, t.lpb[0], t.lpb[1], t.lpb[2], t.plane,
-                t.pair_ms, t.pme_ms, t.nelec, t.chunks);
+                t.pair_ms, t.pme_ms, t.nelec, t.chunks, t.spread);
   f << buf;
 }
 
@@ -157,6 +162,7 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
     int rc = set_pair_config(t.split, t.threads, t.ctas, t.nelec, t.chunks);
     for (int a = 0; !rc && a < 3; ++a) rc = set_fft_lpb(a, t.lpb[a]);
     if (!rc) rc = set_fft_plane(t.plane != 0);
+    if (!rc) rc = set_spread_cells(t.spread != 0 && cell_spread_ok());
     if (!rc) {
       *pair_ms = t.pair_ms;
       *pme_ms = t.pme_ms;
@@ -234,6 +240,14 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
     if (ms < best) best = ms;
     else if ((rc = set_fft_plane(cur)) != GCME_OK) return rc;
   }
+  if (cell_spread_ok()) {  // spread through shared memory by cells vs straight to the grid
+    const bool cur = plan.cell_spread != 0;
+    int rc = set_spread_cells(!cur);
+    if (rc) return rc;
+    const double ms = timed();
+    if (ms < best) best = ms;
+    else if ((rc = set_spread_cells(cur)) != GCME_OK) return rc;
+  }
   const double pme_best = time_ms(st, reps, [&] { launch_pme(Q, plan, fp64, false, st); });
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -245,6 +259,7 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
   t.ctas = pair_ctas_per_sm;
   t.nelec = pair_nelec;
   t.chunks = pair_chunks;
+  t.spread = plan.cell_spread;
   t.plane = plan.use_plane;
   for (int a = 0; a < 3; ++a) t.lpb[a] = plan.lpb[a];
   t.pair_ms = best;

@@ -297,6 +297,23 @@ def test_warp_items_in_rounds(geom, sigma):
                 np.abs(ref["virial"]))
 
 
+@pytest.mark.parametrize("name", ["poly_bonds", "slab_pc", "odd_planes", "tiny_box_n120",
+                                  "neutral_only"])
+def test_cell_spread_same_grid_as_direct_spread(name):
+    """The charge spread cell by cell through shared memory rounds every
+    contribution as the direct spread does and sums integers, so forces and
+    energies are the same bit for bit; both match the oracle."""
+    s = CASES[name]
+    base = {"pair_split": 9, "pair_threads": 160, "pair_ctas_per_sm": 0, "pair_nelec": 2,
+            "fft_lpb": [8, 8, 8], "fft_plane": True}
+    a = gpu_forces(s, 0, virial=True, tuning=dict(base, spread_cells=False))
+    b = gpu_forces(s, 0, virial=True, tuning=dict(base, spread_cells=True))
+    assert np.array_equal(a["fixed"], b["fixed"])
+    assert a["energy"] == b["energy"]
+    assert np.array_equal(a["virial"], b["virial"])
+    _check(s, b, oracle.energy_forces(s), FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
+
+
 def test_apply_tuning_rejects_bad_shapes():
     g = lib()
     s = synth.make_bulk(300, seed_index=58, charged_frac=0.2, K=(96, 96, 8))
@@ -308,7 +325,8 @@ def test_apply_tuning_rejects_bad_shapes():
                 dict(pair_nelec=0, pair_ctas_per_sm=0), dict(pair_nelec=0, pair_threads=160,
                                                              pair_ctas_per_sm=4),
                 dict(pair_nelec=0, pair_threads=128, pair_ctas_per_sm=8),
-                dict(pair_nelec=0, pair_ctas_per_sm=4, pair_chunks=5)):
+                dict(pair_nelec=0, pair_ctas_per_sm=4, pair_chunks=5),
+                dict(spread_cells=True)):  # FP64 system: no cell spread
         t = _shapes(False, 8)
         t.update(bad)
         with pytest.raises(g.GcmeError):
