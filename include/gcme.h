@@ -378,8 +378,9 @@ int gcme_debug_barrier_timeout(gcme_ctx *ctx, double timeout_s, gcme_stream_t st
  * Gaussian-core warps, resident pair
  * CTAs per SM fetching work items dynamically (0: one CTA per item), FFT
  * lines per tile per axis, x-y plane passes (1) or per-axis passes (0);
- * device times of a whole force evaluation and of
- * the PME branch alone with the chosen shapes.
+ * forces_ms: device time of one whole step (the step graph, on which the
+ * candidates are timed) and pme_ms of the PME branch alone, with the chosen
+ * shapes.
  * pair_nelec = 0 selects one warp per work item instead (both terms by the
  * same warp, 64, 96 or 128 threads per CTA, pair_ctas_per_sm >= 1 resident
  * CTAs with at most 28 warps per SM); its items are split by chunks of 32
@@ -399,7 +400,9 @@ typedef struct gcme_tuning {
 #define GCME_TUNE_NO_CACHE 2  /* neither read nor write the cache file   */
 
 /* Time the candidate shapes on this system at positions d_pos (CUDA events
- * on `stream`), keep the fastest and record it in the tuning cache
+ * on `stream`; replays of the step graph on a scratch copy of the state
+ * started from rest, the system's step counter restored afterwards), keep
+ * the fastest and record it in the tuning cache
  * (GCME_TUNE_CACHE, else $HOME/.cache/gcme_tune.jsonl) keyed by GPU name and
  * workload shape; a cached entry is applied without timing.  Results of
  * later calls are unchanged except for FP32 summation order.  A following
