@@ -364,6 +364,18 @@ int gcme_system_set_step_count(gcme_sys *sys, int64_t steps, gcme_stream_t strea
 int gcme_debug_pairs(gcme_sys *sys, const double *d_pos, int32_t *d_triples,
                      int64_t cap, int64_t *d_count, gcme_stream_t stream);
 
+/* Debug: the smooth-PME grids of the reciprocal part of Eq. ewald (Essmann
+ * et al. 1995) at d_pos, for checking the FFT passes on their own: d_q[G]
+ * the spread charge grid Q (FP64 from the fixed-point grid), d_phi[G] the
+ * convolution theta * Q = F^-1[B C F(Q)] after the forward transform, the
+ * influence function and the backward transform (transforms unnormalised,
+ * so d_phi is K0 K1 K2 times the normalised convolution).  G = K0 K1 K2,
+ * index kx + K0 (ky + K1 kz); either output may be NULL, not both.  Uses
+ * the system's accumulators: a following gcme_step_continue needs a
+ * gcme_step first.  Errors: INVALID, CUDA. */
+int gcme_debug_pme_grids(gcme_sys *sys, const double *d_pos, double *d_q, double *d_phi,
+                         gcme_stream_t stream);
+
 /* Debug: launch a grid barrier that one CTA never reaches, so every other
  * CTA's bounded wait (timeout_s seconds, at most 10) runs out; returns
  * GCME_ERR_TIMEOUT when the kernel reported the timeout as designed.  Used

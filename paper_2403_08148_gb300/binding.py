@@ -129,6 +129,7 @@ _SIGS = {
                             ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32),
                             _vp], ctypes.c_int),
     "gcme_build_cells": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "gcme_debug_pme_grids": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "gcme_forces": ([_vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "gcme_build_cells_noalloc": ([ctypes.POINTER(Params), _i64, _vp, _vp, _vp, _vp, _vp],
                                  ctypes.c_int),
@@ -405,6 +406,11 @@ class System:
         k = np.zeros(1, np.int32)
         _check(load().gcme_step_phase_ms(self.h, None, 0, k.ctypes.data))
         return int(k[0])
+
+    def debug_pme_grids(self, d_pos, d_q=None, d_phi=None, stream=None):
+        """Charge grid Q and theta * Q (gcme_debug_pme_grids), FP64 device arrays."""
+        _check(load().gcme_debug_pme_grids(self.h, _ptr(d_pos), _ptr(d_q), _ptr(d_phi),
+                                           _stream(stream)))
 
     def debug_pairs(self, d_pos, d_triples, cap: int, d_count, stream=None):
         _check(load().gcme_debug_pairs(self.h, _ptr(d_pos), _ptr(d_triples), int(cap),

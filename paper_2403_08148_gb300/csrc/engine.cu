@@ -1872,6 +1872,27 @@ int gcme_debug_pairs(gcme_sys *sys, const double *d_pos, int32_t *d_triples, int
   return check_launch("gcme_debug_pairs");
 }
 
+int gcme_debug_pme_grids(gcme_sys *sys, const double *d_pos, double *d_q, double *d_phi,
+                         gcme_stream_t stream) {
+  if (!sys || !d_pos || (!d_q && !d_phi)) {
+    set_error("invalid argument to gcme_debug_pme_grids");
+    return GCME_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  Engine &E = sys->eng;
+  GCME_TRY_CK(cudaSetDevice(E.device));
+  Pool Q = E.P;
+  Q.pos = const_cast<double *>(d_pos);
+  launch_bin(Q, st);
+  if (E.plan.cell_spread) launch_sort(E.cell_only(Q), st);
+  launch_pme_spread(Q, E.plan, E.fp64, st, true);
+  launch_grids_to_f64(Q, E.fp64, d_q, nullptr, st);
+  launch_pme_fft(Q, E.plan, E.fp64, false, st);
+  launch_grids_to_f64(Q, E.fp64, nullptr, d_phi, st);
+  sys->last_pos = sys->last_vel = nullptr;  // the accumulators were used
+  return check_launch("gcme_debug_pme_grids");
+}
+
 // ---- autotuner -------------------------------------------------------------
 static void fill_tuning(const Engine &eng, double pair_ms, double pme_ms, bool hit,
                         gcme_tuning *out) {

@@ -74,6 +74,16 @@ void launch_pair_list(const Pool &P, bool vir, bool dbg, cudaStream_t st);
 // pass clears every grid point it reads)
 void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStream_t st,
                 bool zero_grid = true);
+// its three stages: spread into the charge grid, the FFT passes with the
+// influence function (the forward pass leaves the charge grid zero, the
+// last pass leaves theta * Q in the real parts of the complex grid), gather
+void launch_pme_spread(const Pool &P, const PmePlan &pl, bool fp64, cudaStream_t st,
+                       bool zero_grid);
+void launch_pme_fft(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStream_t st);
+void launch_pme_gather(const Pool &P, const PmePlan &pl, bool fp64, cudaStream_t st);
+// the charge grid (times 1 / qscale) and the real parts of the complex grid
+// as FP64 arrays of P.n_grid values (either may be NULL)
+void launch_grids_to_f64(const Pool &P, bool fp64, double *d_q, double *d_phi, cudaStream_t st);
 void pme_set_smem_limits();
 // bonds (unless the pair kernel took them), walls, dipole
 void launch_bonded(const Pool &P, bool vir, bool bonds, cudaStream_t st);

@@ -59,8 +59,8 @@ __global__ void __launch_bounds__(256) k_fft(Pool P, const int2 *work, int nwork
     dev_fft_item<R, VIR>(P, work, w, axis, kind, lpb, half, smem_raw);
 }
 
-void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStream_t st,
-                bool zero_grid) {
+void launch_pme_spread(const Pool &P, const PmePlan &pl, bool fp64, cudaStream_t st,
+                       bool zero_grid) {
   if (P.n_q == 0 || P.n_grid == 0) return;
   if (zero_grid) cudaMemsetAsync(P.qgrid, 0, sizeof(unsigned long long) * P.n_grid, st);
   const int tb = 256;
@@ -78,6 +78,10 @@ void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStrea
   } else {
     launch_spread_gather<float>(P, pl.order, false, nb, tb, st);
   }
+}
+
+void launch_pme_fft(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStream_t st) {
+  if (P.n_q == 0 || P.n_grid == 0) return;
   const size_t rsz = fp64 ? sizeof(double2) : sizeof(float2);
   // the z pass of the plane path works on the Hermitian half spectrum
   const int half = pl.use_plane;
@@ -105,8 +109,43 @@ void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStrea
     const int kinds[5] = {FFT_FWD_FROM_Q, FFT_FWD, FFT_FWD_INFL_INV, FFT_INV, FFT_INV};
     for (int ps = 0; ps < 5; ++ps) line_pass(axes[ps], kinds[ps]);
   }
+}
+
+void launch_pme_gather(const Pool &P, const PmePlan &pl, bool fp64, cudaStream_t st) {
+  if (P.n_q == 0 || P.n_grid == 0) return;
+  const int tb = 256;
+  const int nb = (int)((P.n_q * 8 + tb - 1) / tb);
   if (fp64) launch_spread_gather<double>(P, pl.order, true, nb, tb, st);
   else launch_spread_gather<float>(P, pl.order, true, nb, tb, st);
+}
+
+void launch_pme(const Pool &P, const PmePlan &pl, bool fp64, bool vir, cudaStream_t st,
+                bool zero_grid) {
+  launch_pme_spread(P, pl, fp64, st, zero_grid);
+  launch_pme_fft(P, pl, fp64, vir, st);
+  launch_pme_gather(P, pl, fp64, st);
+}
+
+// Grids as FP64 for inspection: the fixed-point charge grid times
+// 1 / qscale, and the real parts of the complex grid.
+__global__ void k_qgrid_to_f64(const unsigned long long *q, double *out, long long n, double inv) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g < n) out[g] = (double)(long long)q[g] * inv;
+}
+template <typename R2>
+__global__ void k_cgrid_real(const R2 *c, double *out, long long n) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g < n) out[g] = (double)c[g].x;
+}
+
+void launch_grids_to_f64(const Pool &P, bool fp64, double *d_q, double *d_phi, cudaStream_t st) {
+  const long long n = P.n_grid;
+  const int nb = (int)((n + 255) / 256);
+  if (d_q) k_qgrid_to_f64<<<nb, 256, 0, st>>>(P.qgrid, d_q, n, fp64 ? 1.0 / kQScale64 : 1.0 / kQScale32);
+  if (d_phi) {
+    if (fp64) k_cgrid_real<double2><<<nb, 256, 0, st>>>(P.cgrid64, d_phi, n);
+    else k_cgrid_real<float2><<<nb, 256, 0, st>>>(P.cgrid, d_phi, n);
+  }
 }
 
 void pme_set_smem_limits() {
