@@ -694,148 +694,140 @@ __device__ __forceinline__ PairSeg item_segment(const Pool &P, const SysDesc &S,
   return g;
 }
 
-// Packed variant of dev_pair_f32_item (one species, no debug dump): the
-// core warps run pair_core2 over coordinate arrays, the electrostatics
-// warps (1 to 3, SysDesc::pair_nelec) pair_elec over the staged charged and
-// image beads, each warp a contiguous part of every cell's candidates and
-// each writing its partial sums (fixed-point atomics add them).  Items whose
-// beads exceed the packed capacities take the scalar path.  smem:
-// kPairSmemBytes; seg[9]; s_tot[2].  Ends with a barrier.
-template <bool VIR>
-__device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *work, int w,
-                                                     unsigned char *smem, PairSeg *seg,
-                                                     int *s_tot) {
+// Packed items (one species, no debug dump), in three parts shared by the
+// CTA kernel and the pipelined kernel: the staged-array layout and offsets,
+// the culled staging of one segment by one warp, and the evaluation by the
+// role warps.  The core warps run pair_core2 over coordinate arrays, the
+// electrostatics warps (1 to 3, SysDesc::pair_nelec) pair_elec2 over the
+// staged charged and image beads, each warp a contiguous part of every
+// cell's candidates and each writing its partial sums (fixed-point atomics
+// add them).
+
+// Offsets of each segment in the packed arrays (real beads and charged /
+// image beads, each segment even-padded); returns false when the item's
+// beads exceed the capacities.  One thread.
+__device__ __forceinline__ bool pk_offsets(PairSeg *seg, int nseg, int *s_tot) {
+  int off = 0, qoff = 0;
+  for (int k = 0; k < nseg; ++k) {
+    seg[k].soff = off;
+    seg[k].qoff = qoff;
+    off += (seg[k].n - seg[k].a + 1) & ~1;
+    qoff += (seg[k].b + 1) & ~1;
+  }
+  s_tot[0] = off;
+  s_tot[1] = qoff;
+  return off <= kPkCap && qoff <= kPkCapQ;
+}
+
+// Staging of segment g by one warp: only the candidates within rc (+1e-3) of
+// the home cell's box [hlo, hhi] can be within rc of a home bead, so the
+// others are dropped (about 30 % of the 27 cells' beads at cells of side
+// ~rc), keeping order; the home cell itself is staged whole, in sorted order
+// (its self-pair test uses the sorted index).  Sets g.nk and g.bk.
+__device__ __forceinline__ void pk_stage_segment(const Pool &P, PairSeg &g, const float hlo[3],
+                                                 const float hhi[3], float cut2,
+                                                 unsigned char *smem, int lane) {
   float *sx = reinterpret_cast<float *>(smem);
   float *sy = sx + kPkCap;
   float *sz = sy + kPkCap;
   float *qx = sz + kPkCap, *qy = qx + kPkCapQ, *qz = qy + kPkCapQ, *qq = qz + kPkCapQ;
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
-  const int s = work[w].x;
-  const int code = work[w].y;
-  if (P.list_ovf && !P.list_ovf[s]) {
-    __syncthreads();
-    return;
-  }
-  const SysDesc &S = P.sys[s];
-  // warps 0 .. ncore-1: Gaussian core; the last nelec warps split every
-  // cell's charged and image candidates into contiguous parts
-  const int nelec = min(max(S.pair_nelec, 1), 3);
-  const int ncore = (blockDim.x >> 5) - nelec;
-  const bool core_role = warp < ncore;
-  const int ew = warp - ncore;
-  const int split = S.pair_split;
-  const int cloc = code / split, part = code % split;
-  const int nseg = 27 / split;
-  const long long hg = S.cell_off + cloc;
-  const int hbeg = P.cell_start[hg], hend = P.cell_start[hg + 1];
-  const int himg = P.cell_nimg[hg], hq = P.cell_nq[hg];
-  const int rbeg = hbeg + himg;
-  if (tid < nseg) seg[tid] = item_segment(P, S, cloc, part, tid);
-  __syncthreads();
-  if (tid == 0) {
-    int off = 0, qoff = 0;
-    for (int k = 0; k < nseg; ++k) {
-      seg[k].soff = off;
-      seg[k].qoff = qoff;
-      off += (seg[k].n - seg[k].a + 1) & ~1;
-      qoff += (seg[k].b + 1) & ~1;
-    }
-    s_tot[0] = off;
-    s_tot[1] = qoff;
-  }
-  __syncthreads();
-  if (s_tot[0] > kPkCap || s_tot[1] > kPkCapQ) {
-    dev_pair_f32_item<VIR, false, false>(P, work, w, reinterpret_cast<float4 *>(smem), seg,
-                                         s_tot);
-    return;
-  }
-  // Staging, one warp per segment: only the candidates within rc (+1e-3)
-  // of the home cell's box can be within rc of a home bead, so the others
-  // are dropped here (about 30 % of the 27 cells' beads at cells of side
-  // ~rc), keeping order; the home cell itself is staged whole, in sorted
-  // order (its self-pair test uses the sorted index).
-  {
-    const int nwarp = blockDim.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
-    const int hc[3] = {cloc % S.nc[0], (cloc / S.nc[0]) % S.nc[1], cloc / (S.nc[0] * S.nc[1])};
-    float hlo[3], hhi[3];
+  const unsigned lt = (1u << lane) - 1u;
+  const float4 far = make_float4(1e30f, 1e30f, 1e30f, 0.0f);  // pad: far away
+  auto near_home = [&](const float4 &v) {
+    const float e[3] = {v.x + g.sh[0], v.y + g.sh[1], v.z + g.sh[2]};
+    float d2 = 0.0f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      hlo[a] = (float)hc[a] * S.cside[a];
-      hhi[a] = hlo[a] + S.cside[a];
+      const float d = fmaxf(0.0f, fmaxf(hlo[a] - e[a], e[a] - hhi[a]));
+      d2 = fmaf(d, d, d2);
     }
-    const float cut2 = S.cull2;
-    const float4 far = make_float4(1e30f, 1e30f, 1e30f, 0.0f);  // pad: far away
-    auto near_home = [&](const float4 &v, const PairSeg &g) {
-      const float e[3] = {v.x + g.sh[0], v.y + g.sh[1], v.z + g.sh[2]};
-      float d2 = 0.0f;
+    return d2 <= cut2;
+  };
+  const bool all = g.self;
+  const int nr = g.n - g.a;
+  int kept = 0;
+  for (int t0 = 0; t0 < nr; t0 += 128) {
+    float4 v[4];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const float d = fmaxf(0.0f, fmaxf(hlo[a] - e[a], e[a] - hhi[a]));
-        d2 = fmaf(d, d, d2);
-      }
-      return d2 <= cut2;
-    };
-    for (int k = warp; k < nseg; k += nwarp) {
-      PairSeg &g = seg[k];
-      const bool all = g.self;
-      const int nr = g.n - g.a;
-      int kept = 0;
-      for (int t0 = 0; t0 < nr; t0 += 128) {
-        float4 v[4];
+    for (int u = 0; u < 4; ++u) {
+      const int t = t0 + 32 * u + lane;
+      v[u] = t < nr ? P.xyzq_s[g.beg + g.a + t] : far;
+    }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int t = t0 + 32 * u + lane;
-          v[u] = t < nr ? P.xyzq_s[g.beg + g.a + t] : far;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int t = t0 + 32 * u + lane;
-          const bool keep = t < nr && (all || near_home(v[u], g));
-          const unsigned m = __ballot_sync(0xffffffffu, keep);
-          if (keep) {
-            const int p = g.soff + kept + __popc(m & lt);
-            sx[p] = v[u].x;
-            sy[p] = v[u].y;
-            sz[p] = v[u].z;
-          }
-          kept += __popc(m);
-        }
+    for (int u = 0; u < 4; ++u) {
+      const int t = t0 + 32 * u + lane;
+      const bool keep = t < nr && (all || near_home(v[u]));
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (keep) {
+        const int p = g.soff + kept + __popc(m & lt);
+        sx[p] = v[u].x;
+        sy[p] = v[u].y;
+        sz[p] = v[u].z;
       }
-      if ((kept & 1) && lane == 0) {
-        sx[g.soff + kept] = far.x;
-        sy[g.soff + kept] = far.y;
-        sz[g.soff + kept] = far.z;
-      }
-      int keptq = 0;
-      for (int t0 = 0; t0 < g.b; t0 += 32) {
-        const int t = t0 + lane;
-        const float4 v = t < g.b ? P.xyzq_s[g.beg + t] : far;
-        const bool keep = t < g.b && (all || near_home(v, g));
-        const unsigned m = __ballot_sync(0xffffffffu, keep);
-        if (keep) {
-          const int p = g.qoff + keptq + __popc(m & lt);
-          qx[p] = v.x;
-          qy[p] = v.y;
-          qz[p] = v.z;
-          qq[p] = v.w;
-        }
-        keptq += __popc(m);
-      }
-      if ((keptq & 1) && lane == 0) {
-        qx[g.qoff + keptq] = far.x;
-        qy[g.qoff + keptq] = far.y;
-        qz[g.qoff + keptq] = far.z;
-        qq[g.qoff + keptq] = 0.0f;
-      }
-      if (lane == 0) {
-        g.nk = kept;
-        g.bk = keptq;
-      }
+      kept += __popc(m);
     }
   }
-  __syncthreads();
+  if ((kept & 1) && lane == 0) {
+    sx[g.soff + kept] = far.x;
+    sy[g.soff + kept] = far.y;
+    sz[g.soff + kept] = far.z;
+  }
+  int keptq = 0;
+  for (int t0 = 0; t0 < g.b; t0 += 32) {
+    const int t = t0 + lane;
+    const float4 v = t < g.b ? P.xyzq_s[g.beg + t] : far;
+    const bool keep = t < g.b && (all || near_home(v));
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+      const int p = g.qoff + keptq + __popc(m & lt);
+      qx[p] = v.x;
+      qy[p] = v.y;
+      qz[p] = v.z;
+      qq[p] = v.w;
+    }
+    keptq += __popc(m);
+  }
+  if ((keptq & 1) && lane == 0) {
+    qx[g.qoff + keptq] = far.x;
+    qy[g.qoff + keptq] = far.y;
+    qz[g.qoff + keptq] = far.z;
+    qq[g.qoff + keptq] = 0.0f;
+  }
+  if (lane == 0) {
+    g.nk = kept;
+    g.bk = keptq;
+  }
+}
+
+// The home cell's box (for the staging cull).
+__device__ __forceinline__ void pk_home_box(const SysDesc &S, int cloc, float hlo[3],
+                                            float hhi[3]) {
+  const int hc[3] = {cloc % S.nc[0], (cloc / S.nc[0]) % S.nc[1], cloc / (S.nc[0] * S.nc[1])};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    hlo[a] = (float)hc[a] * S.cside[a];
+    hhi[a] = hlo[a] + S.cside[a];
+  }
+}
+
+// Evaluation of one staged item by the role warps: rt is the thread's index
+// among the nrole threads that take part (warps 0 .. ncore-1 of them core,
+// the last nelec electrostatics).  Warp-synchronous per warp; no CTA barrier.
+template <bool VIR>
+__device__ __forceinline__ void pk_compute(const Pool &P, const SysDesc &S, int s, int hbeg,
+                                           int hend, int himg, int hq, const PairSeg *seg,
+                                           int nseg, const unsigned char *smem, int rt,
+                                           int nrole) {
+  const float *sx = reinterpret_cast<const float *>(smem);
+  const float *sy = sx + kPkCap;
+  const float *sz = sy + kPkCap;
+  const float *qx = sz + kPkCap;
+  const int warp = rt >> 5, lane = rt & 31;
+  const int nelec = min(max(S.pair_nelec, 1), 3);
+  const int ncore = (nrole >> 5) - nelec;
+  const bool core_role = warp < ncore;
+  const int ew = warp - ncore;
+  const int rbeg = hbeg + himg;
   const float rc2 = S.rc2f, gcc = S.gc_c2f;
   const int nreal = hend - rbeg, nqr = hbeg + hq - rbeg;
   const int ncore_chunks = (nreal + 32 * ncore - 1) / (32 * ncore);
@@ -845,7 +837,7 @@ __device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *
     int i;
     bool valid;
     if (core_role) {
-      i = rbeg + c * 32 * ncore + tid;
+      i = rbeg + c * 32 * ncore + rt;
       valid = i < hend;
     } else {
       i = rbeg + c * 32 + lane;
@@ -921,6 +913,47 @@ __device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *
       pair_write<VIR>(P, S, s, valid, i, A);
     }
   }
+}
+
+// Packed variant of dev_pair_f32_item, one CTA per item: items whose beads
+// exceed the packed capacities take the scalar path.  smem: kPairSmemBytes;
+// seg[9]; s_tot[2].  Ends with a barrier.
+template <bool VIR>
+__device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *work, int w,
+                                                     unsigned char *smem, PairSeg *seg,
+                                                     int *s_tot) {
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int s = work[w].x;
+  const int code = work[w].y;
+  if (P.list_ovf && !P.list_ovf[s]) {
+    __syncthreads();
+    return;
+  }
+  const SysDesc &S = P.sys[s];
+  const int split = S.pair_split;
+  const int cloc = code / split, part = code % split;
+  const int nseg = 27 / split;
+  const long long hg = S.cell_off + cloc;
+  const int hbeg = P.cell_start[hg], hend = P.cell_start[hg + 1];
+  const int himg = P.cell_nimg[hg], hq = P.cell_nq[hg];
+  if (tid < nseg) seg[tid] = item_segment(P, S, cloc, part, tid);
+  __syncthreads();
+  if (tid == 0) pk_offsets(seg, nseg, s_tot);
+  __syncthreads();
+  if (s_tot[0] > kPkCap || s_tot[1] > kPkCapQ) {
+    dev_pair_f32_item<VIR, false, false>(P, work, w, reinterpret_cast<float4 *>(smem), seg,
+                                         s_tot);
+    return;
+  }
+  {
+    float hlo[3], hhi[3];
+    pk_home_box(S, cloc, hlo, hhi);
+    const int nwarp = blockDim.x >> 5;
+    for (int k = warp; k < nseg; k += nwarp) pk_stage_segment(P, seg[k], hlo, hhi, S.cull2, smem, lane);
+  }
+  __syncthreads();
+  pk_compute<VIR>(P, S, s, hbeg, hend, himg, hq, seg, nseg, smem, tid, blockDim.x);
   __syncthreads();
 }
 
