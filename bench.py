@@ -362,7 +362,7 @@ def pair_roofline(pairs, qq, pair_ms, kname, peaks):
 
 def kernel_sha():
     h = hashlib.sha256()
-    for f in ("pair.cu", "pair.cuh", "nlist.cu", "common.cuh"):
+    for f in ("pair.cu", "pair.cuh", "pair_warp.cuh", "nlist.cu", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2403_08148_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

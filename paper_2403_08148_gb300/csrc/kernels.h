@@ -50,7 +50,7 @@ void launch_cells(const Pool &P, cudaStream_t st);  // launch_bin + launch_sort
 void launch_bin(const Pool &P, cudaStream_t st, bool zero_counts = true);
 // largest per-system cell grid of the fused cell sort (each of its CTAs sums
 // the counts of the system's earlier cells)
-constexpr int kFusedSortCells = 2048;
+constexpr int kFusedSortCells = 4096;
 // K2: scan, scatter, per-cell order (one fused kernel when P.bucket is set)
 void launch_sort(const Pool &P, cudaStream_t st);
 // ctas: grid of the 27-cell kernel (CTAs loop over items fetched from
