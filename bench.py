@@ -77,6 +77,11 @@ def parse():
     ap.add_argument("--impl", default="gcme", choices=["gcme", "reference"])
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-plain, batched and served side measurements")
+    ap.add_argument("--workload", default="polyelectrolyte",
+                    choices=["polyelectrolyte", "slab-nonmetal", "slab-image"],
+                    help="system of the main timed steps: the N=32,000 bulk polyelectrolyte "
+                         "(default) or an N=64,000 slab (for profiling those; the default run "
+                         "times the slabs as side legs)")
     return ap.parse_args()
 
 
@@ -107,10 +112,26 @@ def job_value(units_per_step: float, ms_per_step: float, ws: int) -> float:
     return ws * units_per_step * 1e3 / ms_per_step
 
 
-def workload_config(s):
-    return {"workload": "bulk polyelectrolyte N=32000 rho=3 (100x50 chains -1, 5000 +1, "
-                        "22000 solvent), rc=3, PME 64^3 p=5, velocity Verlet dt=0.01",
-            "n_beads": s.n, "box": float(s.box[0]), "grid": list(s.K), "cutoff": s.rc,
+WORKLOAD_TEXT = {
+    "polyelectrolyte": "bulk polyelectrolyte N=32000 rho=3 (100x50 chains -1, 5000 +1, "
+                       "22000 solvent), rc=3, PME 64^3 p=5, velocity Verlet dt=0.01",
+    "slab-nonmetal": "slab N=64000 (200x50 chains -1, 10000 +1, 44000 solvent), box 30x30x90, "
+                     "nonmetal walls (Yeh-Berkowitz, H=30), rc=3, PME 64x64x192 p=5, dt=0.01",
+    "slab-image": "slab N=64000 (200x50 chains -1, 10000 +1, 44000 solvent), box 30x30x90, "
+                  "conducting walls (image charges, H=45), rc=3, PME 64x64x192 p=5, dt=0.01"}
+
+
+def workload_system(name):
+    if name == "slab-nonmetal":
+        return synth.config3(synth.GEOM_SLAB_NM)
+    if name == "slab-image":
+        return synth.config3(synth.GEOM_SLAB_PC)
+    return synth.config2()
+
+
+def workload_config(s, name="polyelectrolyte"):
+    return {"workload": WORKLOAD_TEXT[name],
+            "n_beads": s.n, "box": [float(x) for x in s.box], "grid": list(s.K), "cutoff": s.rc,
             "kappa": round(s.kappa, 6), "bonds": int(s.bonds.shape[0]),
             "charged": s.n_charged, "l2": "flushed (512 MiB write) before every timed step"}
 
@@ -266,15 +287,15 @@ def measured_peaks():
         return {}
 
 
-def pair_kernel_traffic():
+def pair_kernel_traffic(workload="polyelectrolyte"):
     """DRAM bytes per pair-kernel launch from the committed ncu summary, if
-    it was taken on the current kernel source."""
+    it was taken on the current kernel source and the same workload."""
     path = os.path.join(ROOT, "profiles", "pair_kernel_traffic.json")
     try:
         d = json.load(open(path))
     except Exception:
         return None
-    if d.get("kernel_sha") != kernel_sha():
+    if d.get("kernel_sha") != kernel_sha() or d.get("workload", "polyelectrolyte") != workload:
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -405,7 +426,7 @@ def run_gcme(args, ws, rank, local):
     dev = torch.device(f"cuda:{local}")
     g.builder.build() if hasattr(g, "builder") else None
     g.load()
-    s = synth.config2()
+    s = workload_system(args.workload)
     ctx = g.Context(local)
     sysg = g.System(ctx, g.params_from(s), s.q, s.bonds)
     pos0 = torch.tensor(s.pos, dtype=torch.float64, device=dev)
@@ -494,13 +515,14 @@ def run_gcme(args, ws, rank, local):
     state_bytes = s.n * 3 * (8 + 4)
 
     peaks = measured_peaks()
-    kname = "k_pair_list" if info.pair_path == g.GCME_PAIR_LIST else "k_pair_f32"
+    kname = ("k_pair_list" if info.pair_path == g.GCME_PAIR_LIST
+             else "k_pair_warp" if tuning.get("pair_nelec") == 0 else "k_pair_f32")
     roofline = pair_roofline(pairs, qq, pair_ms, kname, peaks)
-    roofline["traffic"] = pair_kernel_traffic()
+    roofline["traffic"] = pair_kernel_traffic(args.workload)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": workload_config(s), "steps_per_s": steps_per_s,
+           "config": workload_config(s, args.workload), "steps_per_s": steps_per_s,
            "pair_interactions_per_step": pairs, "charged_pairs_per_step": qq,
            "phase_ms": dict(zip(("kick_drift", "cells", "pair", "pme_concurrent", "bonded",
                                  "slab_kick_energy", "bin", "kick"),
@@ -518,18 +540,23 @@ def run_gcme(args, ws, rank, local):
            "list_builds_per_step": builds / K,
            "roofline": roofline,
            "hbm_kernels": hbm_rooflines(phase, s.n, peaks.get("hbm_gbs")),
-           "error_vs_oracle": parity_record("c2_bulk_polyelectrolyte_n32000"),
+           "error_vs_oracle": parity_record({"polyelectrolyte": "c2_bulk_polyelectrolyte_n32000",
+                                             "slab-nonmetal": "c3_slab_nm_n64000",
+                                             "slab-image": "c3_slab_pc_n64000"}[args.workload]),
            "clocks": clk, "gpu_launches": int(nkern) * K,
            "tuning": tuning,
            "wall_s_timed": t_wall}
-    if not args.no_extras and rank == 0 and ws == 1:
+    if not args.no_extras and rank == 0 and ws == 1 and args.workload == "polyelectrolyte":
         out["c1_plain"] = c1_plain(g, ctx, dev)
         for geom, key in ((synth.GEOM_SLAB_NM, "c3_nonmetal"), (synth.GEOM_SLAB_PC, "c3_image")):
             out[key] = c3_slab(g, ctx, dev, geom, flush, peaks)
         out["batched"] = batched_c4(g, ctx, dev, peaks)
         out["served"] = served_c5(g, ctx)
     if rank == 0 and ws == 1:
-        out["cpu_baseline"] = cpu_baseline(s, pairs)
+        out["cpu_baseline"] = cpu_baseline(
+            s, pairs, what={"polyelectrolyte": "N=32000 polyelectrolyte",
+                            "slab-nonmetal": "N=64000 nonmetal slab",
+                            "slab-image": "N=64000 image-charge slab"}[args.workload])
     del flush
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -624,7 +651,9 @@ def c3_slab(g, ctx, dev, geom, flush, peaks, steps=1000):
            "phase_ms": dict(zip(("kick_drift", "cells", "pair", "pme_concurrent", "bonded",
                                  "slab_kick_energy", "bin", "kick"),
                                 [round(float(x), 5) for x in phase])),
-           "roofline": pair_roofline(pairs, qq, float(phase[2]), "k_pair_f32", peaks),
+           "roofline": pair_roofline(pairs, qq, float(phase[2]),
+                                     "k_pair_warp" if tuning.get("pair_nelec") == 0
+                                     else "k_pair_f32", peaks),
            "error_vs_oracle": parity_record(f"c3_{name}_n64000"),
            "tuning": tuning, "l2": "flushed (512 MiB write) before every timed step"}
     sysg.close()
@@ -754,7 +783,7 @@ def served_c5(g, ctx, n_req=40, rate=200.0, steps=1000, chunk=100):
                     "the second run offers 70% of the measured capacity"}
 
 
-def cpu_baseline(s, pairs, budget_s=12.0):
+def cpu_baseline(s, pairs, budget_s=12.0, what="N=32000 polyelectrolyte"):
     """The oracle as it stands on the host cores: full force evaluations of
     the same system (O(N^2) pair sum + FP64 SPME with direct DFTs)."""
     import oracle
@@ -768,7 +797,7 @@ def cpu_baseline(s, pairs, budget_s=12.0):
             break
     dt = (time.perf_counter() - t0) / n
     return {"value": pairs / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{n} full force evaluations of the N=32000 polyelectrolyte "
+            "sample": f"{n} full force evaluations of the {what} "
                       f"({dt:.2f} s each; one evaluation = one step's force work)"}
 
 

@@ -333,8 +333,8 @@ __device__ __forceinline__ void pair_core2_tail(const float *__restrict__ X,
 // candidates [t0, t1) held as coordinate and charge arrays (t0, t1 even):
 // the in-cutoff test runs on two candidates per packed FP32x2 instruction
 // (the rounding of the neighbour rule, as in pair_core2) and sets one bit
-// per hit, 64 candidates at a time; the table lookup and the force run over
-// the set bits only.  jsorted0 + t is candidate t's sorted index (self
+// per hit, 32 candidates at a time (32-bit masks: no 64-bit shifts or bit
+// scans); the table lookup and the force run over the set bits only.  jsorted0 + t is candidate t's sorted index (self
 // segment, staged whole and in order).  TAB: g and h from the system's
 // table (tab, its scale and last interval nm1), else evaluated directly.
 template <bool SHIFT, bool SELF, bool VIR, bool TAB>
@@ -352,9 +352,9 @@ __device__ __forceinline__ void pair_elec2(const float *__restrict__ X, int t0, 
                mz = make_float2(-xi.z, -xi.z);
   const float2 hx = make_float2(sg.sh[0], sg.sh[0]), hy = make_float2(sg.sh[1], sg.sh[1]),
                hz = make_float2(sg.sh[2], sg.sh[2]);
-  for (int c0 = t0; c0 < t1; c0 += 64) {
-    const int cn = min(64, t1 - c0);
-    unsigned long long m = 0ull;
+  for (int c0 = t0; c0 < t1; c0 += 32) {
+    const int cn = min(32, t1 - c0);
+    unsigned m = 0u;
     for (int u = 0; u < cn; u += 2) {
       float2 dx = __fadd2_rn(*reinterpret_cast<const float2 *>(X + c0 + u), mx);
       float2 dy = __fadd2_rn(*reinterpret_cast<const float2 *>(Y + c0 + u), my);
@@ -371,11 +371,11 @@ __device__ __forceinline__ void pair_elec2(const float *__restrict__ X, int t0, 
         in0 = in0 && (jsorted0 + c0 + u != isorted);
         in1 = in1 && (jsorted0 + c0 + u + 1 != isorted);
       }
-      m |= ((unsigned long long)in0 | ((unsigned long long)in1 << 1)) << u;
+      m |= ((unsigned)in0 | ((unsigned)in1 << 1)) << u;
     }
     while (m) {
-      const int u = __ffsll((long long)m) - 1;
-      m &= m - 1ull;
+      const int u = __ffs((int)m) - 1;
+      m &= m - 1u;
       const int t = c0 + u;
       float dx = __fsub_rn(X[t], xi.x), dy = __fsub_rn(Y[t], xi.y), dz = __fsub_rn(Z[t], xi.z);
       if (SHIFT) {
