@@ -43,6 +43,22 @@ __device__ __forceinline__ void dev_bin(const Pool &P, long long g) {
     ext_position(P, S, e, x[0], x[1], x[2]);
     q = ext_charge(P, S, e);
   }
+  // the system's constants into registers first: each is then one load in
+  // flight with the positions, not a round trip behind the previous axis
+  // (the rare store to wrap_n below would otherwise keep later loads behind it)
+  double Lb[3], icell[3];
+  float icellf[3];
+  int ncs[3], np3[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    Lb[a] = S.box[a];
+    icell[a] = S.inv_cell[a];
+    icellf[a] = S.inv_cellf[a];
+    ncs[a] = S.nc[a];
+    np3[a] = P.wrap_n ? P.wrap_n[3 * g + a] : 0;
+  }
+  const long long cell_off = S.cell_off;
+  const int sn = S.n;
   double w[3];
   float wf[3];
   int c[3];
@@ -53,8 +69,8 @@ __device__ __forceinline__ void dev_bin(const Pool &P, long long g) {
     // [L 2^-40, L (1 - 2^-40)] and |n| < 2^10, the rule's floor(x / L) is n
     // (the roundings of x / L and L n are below L 2^-42 here), so w0 is the
     // rule's result and the FP64 division is skipped.
-    const double L = S.box[a];
-    const int np = P.wrap_n ? P.wrap_n[3 * g + a] : 0;
+    const double L = Lb[a];
+    const int np = np3[a];
     const double w0 = __dsub_rn(x[a], __dmul_rn(L, (double)np));
     const double d = L * 9.094947017729282e-13;  // L 2^-40
     if (np > -1024 && np < 1024 && w0 >= d && w0 <= L - d) {
@@ -68,28 +84,32 @@ __device__ __forceinline__ void dev_bin(const Pool &P, long long g) {
     // cell: floor(w nc / L) in FP64 (the rule); the FP32 product decides when
     // it is at least 1e-4 from a cell face (its error is below 2e-5 for
     // nc <= 256)
-    const float uf = wf[a] * S.inv_cellf[a];
+    const float uf = wf[a] * icellf[a];
     int k = (int)floorf(uf);
     const float fr = uf - (float)k;
-    if (S.nc[a] > 256 || !(fr >= 1e-4f && fr <= 1.0f - 1e-4f))
-      k = (int)floor(__dmul_rn(w[a], S.inv_cell[a]));
-    k = k > S.nc[a] - 1 ? S.nc[a] - 1 : k;
+    if (ncs[a] > 256 || !(fr >= 1e-4f && fr <= 1.0f - 1e-4f))
+      k = (int)floor(__dmul_rn(w[a], icell[a]));
+    k = k > ncs[a] - 1 ? ncs[a] - 1 : k;
     k = k < 0 ? 0 : k;
     c[a] = k;
   }
-  int cell = c[0] + S.nc[0] * (c[1] + S.nc[1] * c[2]);
+  int cell = c[0] + ncs[0] * (c[1] + ncs[1] * c[2]);
   P.xyzq_u[g] = make_float4(wf[0], wf[1], wf[2], (float)q);
   if (P.xyzq_u64) P.xyzq_u64[g] = make_dpos4(w[0], w[1], w[2], q);
   if (P.img_now) {
     // periodic image index: x = w + img L exactly up to the wrap rule
 #pragma unroll
-    for (int a = 0; a < 3; ++a) P.img_now[3 * g + a] = (int)rint((x[a] - w[a]) / S.box[a]);
+    for (int a = 0; a < 3; ++a) P.img_now[3 * g + a] = (int)rint((x[a] - w[a]) / Lb[a]);
   }
   P.cell_of[g] = cell;
-  const int slot = atomicAdd(&P.cell_cnt[S.cell_off + cell], 1);
+  const int slot = atomicAdd(&P.cell_cnt[cell_off + cell], 1);
   P.slot[g] = slot;
-  if (P.bucket && slot < P.bucket_cap)
-    P.bucket[(S.cell_off + cell) * (long long)P.bucket_cap + slot] = e;
+  if (P.bucket && slot < P.bucket_cap) {
+    const long long b = (cell_off + cell) * (long long)P.bucket_cap + slot;
+    const int cls = e >= sn ? 0 : ((float)q != 0.0f ? 1 : 2);
+    P.bucket[b] = e | (cls << 30);
+    P.bucket_pos[b] = make_float4(wf[0], wf[1], wf[2], (float)q);
+  }
 }
 
 // Exclusive scan of the cell counts of all systems by one CTA (any size
@@ -217,27 +237,68 @@ __device__ __forceinline__ void dev_cellsort_block(const Pool &P, long long cg, 
 // (a block sum), its beads come from the bucket written by the binning
 // (or, for a cell holding more than bucket_cap beads, from a search of the
 // system's beads), and the stable (class, index) order follows as in
-// dev_cellsort_range.  red: 32 shared ints.  Ends with a barrier.
+// dev_cellsort_range.  A cell within both the bucket and kSortCap is ranked
+// straight from its bucket entries (class and index) and written from its
+// bucket positions, with no round trip through the sorted index.  red: 32
+// shared ints.  Ends with a barrier.
 __device__ __forceinline__ void dev_cellsort_fused_block(const Pool &P, long long cg,
                                                          long long *key, int *cnt2, int *red) {
   const SysDesc &S = P.sys[P.cell_sys[cg]];
+  const int cnt = P.cell_cnt[cg];
+  const bool direct = cnt <= P.bucket_cap && cnt <= kSortCap;
+  const int *b = P.bucket + cg * (long long)P.bucket_cap;
+  if (threadIdx.x == 0) {
+    cnt2[0] = 0;
+    cnt2[1] = 0;
+  }
   int part = 0;
   for (long long c = S.cell_off + threadIdx.x; c < cg; c += blockDim.x) part += P.cell_cnt[c];
   part = warp_sum(part);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) red[wid] = part;
+  if (direct) {
+    __syncthreads();  // counters cleared
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      const unsigned be = (unsigned)b[t];
+      const unsigned cls = be >> 30;
+      key[t] = ((long long)cls << 32) | (be & 0x3fffffffu);
+      if (cls == 0) atomicAdd(&cnt2[0], 1);
+      if (cls <= 1) atomicAdd(&cnt2[1], 1);
+    }
+  }
   __syncthreads();
   int tot = 0;
   for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += red[k];
   const int beg = (int)S.ext_off + tot;
-  const int cnt = P.cell_cnt[cg];
   if (threadIdx.x == 0) {
     P.cell_start[cg] = beg;
     if (cg == P.n_cells - 1) P.cell_start[cg + 1] = beg + cnt;
   }
+  if (direct) {
+    const float4 *bp = P.bucket_pos + cg * (long long)P.bucket_cap;
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      const long long k = key[t];
+      const float4 v = bp[t];
+      int rank = 0;
+      for (int u = 0; u < cnt; ++u) rank += key[u] < k;
+      const int e = (int)(k & 0xffffffffLL);
+      const long long dst = beg + rank;
+      P.sorted_idx[dst] = e;
+      P.xyzq_s[dst] = v;
+      if (P.xyzq_s64) P.xyzq_s64[dst] = P.xyzq_u64[S.ext_off + e];
+      if (P.type_s) P.type_s[dst] = P.type_u[S.ext_off + e];
+    }
+    if (threadIdx.x == 0) {
+      P.cell_nimg[cg] = cnt2[0];
+      P.cell_nq[cg] = cnt2[1];
+    }
+    __syncthreads();
+    return;
+  }
   if (cnt <= P.bucket_cap) {
     const int *b = P.bucket + cg * (long long)P.bucket_cap;
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) P.sorted_idx[beg + t] = b[t];
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x)
+      P.sorted_idx[beg + t] = (int)((unsigned)b[t] & 0x3fffffffu);
   } else {
     const int cl = (int)(cg - S.cell_off);
     for (long long g = S.ext_off + threadIdx.x; g < S.ext_off + S.n_ext; g += blockDim.x)

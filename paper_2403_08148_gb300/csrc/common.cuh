@@ -186,8 +186,11 @@ struct Pool {
   int *cell_nq;
   int *cell_sys;
   // fused cell sort (small cell grids): bead e of cell c at bucket[c * bucket_cap
-  // + slot] for slot < bucket_cap; null: scan + scatter + sort kernels
+  // + slot] for slot < bucket_cap, as e | class << 30 (class 0 image, 1 charged
+  // real, 2 neutral real), its wrapped FP32 position and charge at the same
+  // place of bucket_pos; null: scan + scatter + sort kernels
   int *bucket;
+  float4 *bucket_pos;
   int bucket_cap;
   int *wrap_n;          // [3 * n_ext] periodic image index of each coordinate at the last binning
   // PME

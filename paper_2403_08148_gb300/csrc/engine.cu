@@ -929,7 +929,8 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     bool fused = true;
     double occ = 0.0;
     for (auto &S : hsys) {
-      fused = fused && S.ncell <= kFusedSortCells;
+      // (bucket entries carry the class in their top two bits)
+      fused = fused && S.ncell <= kFusedSortCells && S.n_ext < (1LL << 30);
       double fill = 1.0;
       if (S.geometry != GCME_BULK && S.H > 0) fill = std::min(1.0, S.H / S.box[2]);
       occ = std::max(occ, S.n_ext / (S.ncell * fill));
@@ -937,6 +938,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     if (fused) bucket_cap = ((int)std::ceil(2.0 * occ) + 32 + 31) / 32 * 32;
   }
   cv.add(&P.bucket, (long long)ncell * bucket_cap);
+  cv.add(&P.bucket_pos, (long long)ncell * bucket_cap);
   cv.add(&P.cell_nimg, ncell);
   cv.add(&P.cell_nq, ncell);
   cv.add(&P.cell_sys, ncell);

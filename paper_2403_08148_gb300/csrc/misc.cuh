@@ -301,13 +301,14 @@ __device__ __forceinline__ void dev_kick_drift(const Pool &P, long long g) {
     }
     return;
   }
+  const double dt = S.dt;  // read before the stores below (no reload per axis)
   for (int a = 0; a < 3; ++a) {
     unsigned long long *fp = fptr(a);
     const long long fq = ONE ? f1[a] : (long long)*fp;
     *fp = 0ull;
     V v = v0[a] + h * force_value<V>(fq);
     vel[a] = v;
-    P.pos[3 * g + a] = x0[a] + S.dt * (double)v;
+    P.pos[3 * g + a] = x0[a] + dt * (double)v;
   }
 }
 

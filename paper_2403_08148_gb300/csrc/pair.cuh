@@ -21,7 +21,7 @@
 // candidates in shared memory and splits into roles: Gaussian-core warps
 // (one home bead per lane, two candidates per packed FP32x2 instruction over
 // coordinate arrays) and 1-3 electrostatics warps (the charged home beads
-// over the charged and image candidates, a 64-bit in-cutoff mask per 64
+// over the charged and image candidates, a 32-bit in-cutoff mask per 32
 // candidates, then the real-space term from a per-system table for the
 // hits only).  Within a cell the images, charged and neutral beads are
 // contiguous, so no per-pair class test is needed.  Forces are summed in
@@ -329,14 +329,83 @@ __device__ __forceinline__ void pair_core2_tail(const float *__restrict__ X,
   }
 }
 
+// The real-space term of a charged home bead with the candidates c0 + u, u
+// a set bit of m (each in range by the neighbour rule, decided before): g
+// and h from the system's table (TAB; r^2 a rounding above rc^2 takes the
+// last interval a hair beyond its end) or evaluated directly, the energy,
+// force and virial summed WITHOUT the home bead's own charge (elec_scale
+// applies it once per home bead).  xs is the home bead's position minus the
+// segment's image shift, so that d = x_j - xs; d and r^2 are recomputed here
+// with fused operations: they set the values of the terms, not the
+// decision, which followed the exact rounding rule.
+template <bool VIR, bool TAB>
+__device__ __forceinline__ void elec_hits(unsigned m, int c0, const float *__restrict__ X,
+                                          const float *__restrict__ Y,
+                                          const float *__restrict__ Z,
+                                          const float *__restrict__ Q, float xsx, float xsy,
+                                          float xsz, const SysDesc &S, PairAcc &A,
+                                          const float4 *__restrict__ tab, float tab_scale,
+                                          int tab_nm1) {
+  // two hits per pass: two independent load-table-force chains in flight
+  // (an odd last hit pairs with itself at zero charge)
+  while (m) {
+    const int u0 = 31 - __clz(m);  // highest set bit first
+    m ^= 1u << u0;
+    const bool two = m != 0u;
+    const int u1 = two ? 31 - __clz(m) : u0;
+    if (two) m ^= 1u << u1;
+    const int ta = c0 + u0, tb = c0 + u1;
+    const float dxa = X[ta] - xsx, dya = Y[ta] - xsy, dza = Z[ta] - xsz;
+    const float dxb = X[tb] - xsx, dyb = Y[tb] - xsy, dzb = Z[tb] - xsz;
+    const float r2a = fmaf(dxa, dxa, fmaf(dya, dya, dza * dza));
+    const float r2b = fmaf(dxb, dxb, fmaf(dyb, dyb, dzb * dzb));
+    float ga, ha, gb, hb;
+    if (TAB) {
+      real_gh_tab(tab, tab_scale, tab_nm1, r2a, ga, ha);
+      real_gh_tab(tab, tab_scale, tab_nm1, r2b, gb, hb);
+    } else {
+      real_gh_direct(r2a, S.betaf, S.kappaf, S.ser_gf, S.ser_hf, ga, ha);
+      real_gh_direct(r2b, S.betaf, S.kappaf, S.ser_gf, S.ser_hf, gb, hb);
+    }
+    const float qa = Q[ta], qb = two ? Q[tb] : 0.0f;
+    A.ere = fmaf(qb, gb, fmaf(qa, ga, A.ere));
+    const float fa = qa * ha, fb = qb * hb;
+    A.fx = fmaf(fb, dxb, fmaf(fa, dxa, A.fx));
+    A.fy = fmaf(fb, dyb, fmaf(fa, dya, A.fy));
+    A.fz = fmaf(fb, dzb, fmaf(fa, dza, A.fz));
+    if (VIR) {
+      const float exa = fa * dxa, eya = fa * dya, exb = fb * dxb, eyb = fb * dyb;
+      A.we[0] = fmaf(exb, dxb, fmaf(exa, dxa, A.we[0]));
+      A.we[1] = fmaf(eyb, dyb, fmaf(eya, dya, A.we[1]));
+      A.we[2] = fmaf(fb * dzb, dzb, fmaf(fa * dza, dza, A.we[2]));
+      A.we[3] = fmaf(exb, dyb, fmaf(exa, dya, A.we[3]));
+      A.we[4] = fmaf(exb, dzb, fmaf(exa, dza, A.we[4]));
+      A.we[5] = fmaf(eyb, dzb, fmaf(eya, dza, A.we[5]));
+    }
+  }
+}
+
+// The home bead's charge on its real-space sums (after its last elec_hits).
+template <bool VIR>
+__device__ __forceinline__ void elec_scale(PairAcc &A, float qi) {
+  A.ere *= qi;
+  A.fx *= qi;
+  A.fy *= qi;
+  A.fz *= qi;
+  if (VIR)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) A.we[k] *= qi;
+}
+
 // Real-space electrostatics of a charged i over the staged charged and image
 // candidates [t0, t1) held as coordinate and charge arrays (t0, t1 even):
 // the in-cutoff test runs on two candidates per packed FP32x2 instruction
 // (the rounding of the neighbour rule, as in pair_core2) and sets one bit
 // per hit, 32 candidates at a time (32-bit masks: no 64-bit shifts or bit
-// scans); the table lookup and the force run over the set bits only.  jsorted0 + t is candidate t's sorted index (self
-// segment, staged whole and in order).  TAB: g and h from the system's
-// table (tab, its scale and last interval nm1), else evaluated directly.
+// scans); elec_hits evaluates the set bits.  jsorted0 + t is candidate t's
+// sorted index (self segment, staged whole and in order).  TAB: g and h
+// from the system's table (tab, its scale and last interval nm1), else
+// evaluated directly.
 template <bool SHIFT, bool SELF, bool VIR, bool TAB>
 __device__ __forceinline__ void pair_elec2(const float *__restrict__ X, int t0, int t1,
                                            int jsorted0, const float4 &xi, int isorted,
@@ -373,36 +442,9 @@ __device__ __forceinline__ void pair_elec2(const float *__restrict__ X, int t0, 
       }
       m |= ((unsigned)in0 | ((unsigned)in1 << 1)) << u;
     }
-    while (m) {
-      const int u = __ffs((int)m) - 1;
-      m &= m - 1u;
-      const int t = c0 + u;
-      float dx = __fsub_rn(X[t], xi.x), dy = __fsub_rn(Y[t], xi.y), dz = __fsub_rn(Z[t], xi.z);
-      if (SHIFT) {
-        dx = __fadd_rn(dx, sg.sh[0]);
-        dy = __fadd_rn(dy, sg.sh[1]);
-        dz = __fadd_rn(dz, sg.sh[2]);
-      }
-      const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-      float g, h;
-      if (TAB) real_gh_tab(tab, tab_scale, tab_nm1, r2, g, h);
-      else real_gh_direct(r2, S.betaf, S.kappaf, S.ser_gf, S.ser_hf, g, h);
-      const float qq = xi.w * Q[t];
-      A.ere = fmaf(qq, g, A.ere);
-      const float fq = qq * h;
-      A.fx = fmaf(fq, dx, A.fx);
-      A.fy = fmaf(fq, dy, A.fy);
-      A.fz = fmaf(fq, dz, A.fz);
-      if (VIR) {
-        const float ex = fq * dx, ey = fq * dy;
-        A.we[0] = fmaf(ex, dx, A.we[0]);
-        A.we[1] = fmaf(ey, dy, A.we[1]);
-        A.we[2] = fmaf(fq * dz, dz, A.we[2]);
-        A.we[3] = fmaf(ex, dy, A.we[3]);
-        A.we[4] = fmaf(ex, dz, A.we[4]);
-        A.we[5] = fmaf(ey, dz, A.we[5]);
-      }
-    }
+    elec_hits<VIR, TAB>(m, c0, X, Y, Z, Q, SHIFT ? xi.x - sg.sh[0] : xi.x,
+                        SHIFT ? xi.y - sg.sh[1] : xi.y, SHIFT ? xi.z - sg.sh[2] : xi.z, S, A, tab,
+                        tab_scale, tab_nm1);
   }
 }
 
@@ -436,7 +478,12 @@ __device__ __forceinline__ void pair_segment(const float4 *J, int t0, int t1, in
                                              int isorted, const SysDesc &S, float rc2, float gcc,
                                              PairAcc &A, const Pool &P, int s) {
   const int a0 = max(t0, min(t1, sg.a)), b0 = max(t0, min(t1, sg.b));
-#define GCME_SEG(SHIFT, SELF)                                                                      pair_core<SHIFT, SELF, VIR, DBG>(J, a0, t1, jsorted0, xi, isorted, sg, rc2, gcc, A, P, s);       if (anyq)                                                                                          pair_elec<SHIFT, SELF, VIR, DBG>(J, t0, b0, a0, jsorted0, xi, isorted, sg, S, rc2, A, P, s);   if (DBG) pair_dump_images<SHIFT>(J, t0, a0, jsorted0, xi, isorted, sg, rc2, P, s);
+#define GCME_SEG(SHIFT, SELF)                                                               \
+  pair_core<SHIFT, SELF, VIR, DBG>(J, a0, t1, jsorted0, xi, isorted, sg, rc2, gcc, A, P, s);  \
+  if (anyq)                                                                                   \
+    pair_elec<SHIFT, SELF, VIR, DBG>(J, t0, b0, a0, jsorted0, xi, isorted, sg, S, rc2, A, P,  \
+                                     s);                                                      \
+  if (DBG) pair_dump_images<SHIFT>(J, t0, a0, jsorted0, xi, isorted, sg, rc2, P, s);
   if (sg.self) {
     GCME_SEG(false, true)
   } else if (sg.shifted) {
@@ -909,6 +956,7 @@ __device__ __forceinline__ void pk_compute(const Pool &P, const SysDesc &S, int 
                                                 tab, tab_scale, tab_nm1);
           }
         }
+        elec_scale<VIR>(A, xi.w);
       }
       pair_write<VIR>(P, S, s, valid, i, A);
     }
@@ -950,7 +998,8 @@ __device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *
     float hlo[3], hhi[3];
     pk_home_box(S, cloc, hlo, hhi);
     const int nwarp = blockDim.x >> 5;
-    for (int k = warp; k < nseg; k += nwarp) pk_stage_segment(P, seg[k], hlo, hhi, S.cull2, smem, lane);
+    for (int k = warp; k < nseg; k += nwarp)
+      pk_stage_segment(P, seg[k], hlo, hhi, S.cull2, smem, lane);
   }
   __syncthreads();
   pk_compute<VIR>(P, S, s, hbeg, hend, himg, hq, seg, nseg, smem, tid, blockDim.x);
@@ -1027,7 +1076,8 @@ __device__ __forceinline__ void dev_pair_fine_item(const Pool &P, const int2 *wo
 #pragma unroll
     for (int k = 0; k < 6; ++k) A.wg[k] = A.we[k] = 0.0f;
     for (int uz = z0; uz < z1; ++uz) {
-      const float gz_ = fmaxf(0.0f, fmaxf(uz * S.cside[2] - bmax[2], bmin[2] - (uz + 1) * S.cside[2]));
+      const float gz_ =
+          fmaxf(0.0f, fmaxf(uz * S.cside[2] - bmax[2], bmin[2] - (uz + 1) * S.cside[2]));
       const float dz2 = gz_ * gz_;
       if (dz2 > S.cull2) continue;
       for (int uy = lo[1] - 2; uy < lo[1] + wd[1] + 2; ++uy) {

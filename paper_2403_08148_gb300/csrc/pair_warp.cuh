@@ -91,36 +91,9 @@ __device__ __forceinline__ void welec(const float *__restrict__ X, const float *
       }
       m |= ((unsigned)in0 | ((unsigned)in1 << 1)) << u;
     }
-    while (m) {
-      const int u = __ffs((int)m) - 1;
-      m &= m - 1u;
-      const int t = c0 + u;
-      float dx = __fsub_rn(X[t], xi.x), dy = __fsub_rn(Y[t], xi.y), dz = __fsub_rn(Z[t], xi.z);
-      if (SHIFT) {
-        dx = __fadd_rn(dx, g.sh[0]);
-        dy = __fadd_rn(dy, g.sh[1]);
-        dz = __fadd_rn(dz, g.sh[2]);
-      }
-      const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-      float gg, h;
-      if (TAB) real_gh_tab(tab, tab_scale, tab_nm1, r2, gg, h);
-      else real_gh_direct(r2, S.betaf, S.kappaf, S.ser_gf, S.ser_hf, gg, h);
-      const float qq = xi.w * Q[t];
-      A.ere = fmaf(qq, gg, A.ere);
-      const float fq = qq * h;
-      A.fx = fmaf(fq, dx, A.fx);
-      A.fy = fmaf(fq, dy, A.fy);
-      A.fz = fmaf(fq, dz, A.fz);
-      if (VIR) {
-        const float ex = fq * dx, ey = fq * dy;
-        A.we[0] = fmaf(ex, dx, A.we[0]);
-        A.we[1] = fmaf(ey, dy, A.we[1]);
-        A.we[2] = fmaf(fq * dz, dz, A.we[2]);
-        A.we[3] = fmaf(ex, dy, A.we[3]);
-        A.we[4] = fmaf(ex, dz, A.we[4]);
-        A.we[5] = fmaf(ey, dz, A.we[5]);
-      }
-    }
+    elec_hits<VIR, TAB>(m, c0, X, Y, Z, Q, SHIFT ? xi.x - g.sh[0] : xi.x,
+                        SHIFT ? xi.y - g.sh[1] : xi.y, SHIFT ? xi.z - g.sh[2] : xi.z, S, A, tab,
+                        tab_scale, tab_nm1);
   }
 }
 
@@ -259,26 +232,27 @@ __device__ __forceinline__ void wflush(const Pool &P, const SysDesc &S, int s, i
                     *Q = W.qq + pc.soff;
         if (tab_nm1 >= 0) {
           if (g.self)
-            welec<false, true, VIR, true>(X, Y, Z, Q, n2, pc.jsorted0, xi, i, g, S, rc2, A, tab,
-                                          tab_scale, tab_nm1);
+            welec<false, true, VIR, true>(X, Y, Z, Q, n2, pc.jsorted0, xi, i, g,
+                                          S, rc2, A, tab, tab_scale, tab_nm1);
           else if (g.shifted)
-            welec<true, false, VIR, true>(X, Y, Z, Q, n2, 0, xi, i, g, S, rc2, A, tab, tab_scale,
-                                          tab_nm1);
+            welec<true, false, VIR, true>(X, Y, Z, Q, n2, 0, xi, i, g,
+                                          S, rc2, A, tab, tab_scale, tab_nm1);
           else
-            welec<false, false, VIR, true>(X, Y, Z, Q, n2, 0, xi, i, g, S, rc2, A, tab,
-                                           tab_scale, tab_nm1);
+            welec<false, false, VIR, true>(X, Y, Z, Q, n2, 0, xi, i, g,
+                                           S, rc2, A, tab, tab_scale, tab_nm1);
         } else {  // no table (very small smearing radius)
           if (g.self)
-            welec<false, true, VIR, false>(X, Y, Z, Q, n2, pc.jsorted0, xi, i, g, S, rc2, A, tab,
-                                           tab_scale, tab_nm1);
+            welec<false, true, VIR, false>(X, Y, Z, Q, n2, pc.jsorted0, xi, i, g,
+                                           S, rc2, A, tab, tab_scale, tab_nm1);
           else if (g.shifted)
-            welec<true, false, VIR, false>(X, Y, Z, Q, n2, 0, xi, i, g, S, rc2, A, tab,
-                                           tab_scale, tab_nm1);
+            welec<true, false, VIR, false>(X, Y, Z, Q, n2, 0, xi, i, g,
+                                           S, rc2, A, tab, tab_scale, tab_nm1);
           else
-            welec<false, false, VIR, false>(X, Y, Z, Q, n2, 0, xi, i, g, S, rc2, A, tab,
-                                            tab_scale, tab_nm1);
+            welec<false, false, VIR, false>(X, Y, Z, Q, n2, 0, xi, i, g,
+                                            S, rc2, A, tab, tab_scale, tab_nm1);
         }
       }
+      elec_scale<VIR>(A, xi.w);
     }
     pair_write<VIR>(P, S, s, valid, i, A);
   }
