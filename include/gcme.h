@@ -401,10 +401,15 @@ int gcme_debug_barrier_timeout(gcme_ctx *ctx, double timeout_s, gcme_stream_t st
  * spread_cells = 1 spreads the charges (FP32, 27-cell path without lists)
  * cell by cell through a brick of the grid in shared memory, the PME branch
  * then starting after the cell sort; 0 spreads each charge straight to the
- * grid in global memory, the branch starting after binning. */
+ * grid in global memory, the branch starting after binning.
+ * pair_group = 2 or 3 (split 9 CTA items only) lets one work item take
+ * that many consecutive home cells along x in every system with at least
+ * pair_group + 2 cells along x (others keep one home cell per item): the
+ * pair_group + 2 cells of a neighbour row are staged once for all of them;
+ * 1 (or 0 when applying) one home cell per item. */
 typedef struct gcme_tuning {
   int32_t pair_split, pair_threads, pair_ctas_per_sm, fft_lpb[3], fft_plane, from_cache,
-      cell_factor, pair_nelec, pair_chunks, spread_cells;
+      cell_factor, pair_nelec, pair_chunks, spread_cells, pair_group;
   double forces_ms, pme_ms;
 } gcme_tuning;
 
@@ -424,7 +429,8 @@ int gcme_autotune(gcme_sys *sys, const double *d_pos, int32_t flags, gcme_tuning
 
 /* Apply given launch shapes without timing (e.g. a tuning recorded
  * elsewhere, or to pin one path): pair_split, pair_threads, pair_nelec,
- * pair_chunks, spread_cells and pair_ctas_per_sm (27-cell path of cell_factor 1 only; ignored otherwise),
+ * pair_chunks, pair_group, spread_cells and pair_ctas_per_sm (27-cell path
+ * of cell_factor 1 only; ignored otherwise),
  * fft_lpb[3] and fft_plane are read, every other field ignored.  A shape out
  * of range (see gcme_tuning), lines per tile or x-y planes that do not fit in
  * shared memory return GCME_ERR_INVALID and leave the shapes unchanged.

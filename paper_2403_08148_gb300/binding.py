@@ -67,6 +67,7 @@ class Tuning(ctypes.Structure):
                 ("fft_plane", ctypes.c_int32), ("from_cache", ctypes.c_int32),
                 ("cell_factor", ctypes.c_int32), ("pair_nelec", ctypes.c_int32),
                 ("pair_chunks", ctypes.c_int32), ("spread_cells", ctypes.c_int32),
+                ("pair_group", ctypes.c_int32),
                 ("forces_ms", ctypes.c_double), ("pme_ms", ctypes.c_double)]
 
     @classmethod
@@ -75,6 +76,7 @@ class Tuning(ctypes.Structure):
         for k in ("pair_split", "pair_threads", "pair_ctas_per_sm", "pair_nelec"):
             setattr(t, k, int(d[k]))
         t.pair_chunks = int(d.get("pair_chunks", 0))
+        t.pair_group = int(d.get("pair_group", 1))
         t.spread_cells = int(bool(d.get("spread_cells", False)))
         for a in range(3):
             t.fft_lpb[a] = int(d["fft_lpb"][a])
@@ -87,6 +89,7 @@ class Tuning(ctypes.Structure):
                 "fft_plane": bool(self.fft_plane),
                 "from_cache": bool(self.from_cache), "cell_factor": self.cell_factor,
                 "pair_nelec": self.pair_nelec, "pair_chunks": self.pair_chunks,
+                "pair_group": self.pair_group,
                 "spread_cells": bool(self.spread_cells),
                 "forces_ms": self.forces_ms,
                 "pme_ms": self.pme_ms}

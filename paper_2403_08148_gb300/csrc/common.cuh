@@ -139,6 +139,7 @@ struct SysDesc {
   // pair kernel works on blocks of 2 x 2 x 2 cells (nb blocks per axis)
   int cell_factor;
   int pair_split;      // work items per home cell: 3 (9 neighbour cells each) or 9 (3 each)
+  int pair_group;      // CTA items of split 9: consecutive home cells along x per item (1-3)
   int pair_nch;        // warp items: items per (home cell, part), each taking every
                        // pair_nch-th chunk of 32 home beads (1 for CTA items)
   int nb[3];

@@ -355,13 +355,20 @@ void Engine::release() {
   snap_nq.clear();
 }
 
-std::vector<int2> Engine::make_pair_work(int split, bool chunked) const {
+std::vector<int2> Engine::make_pair_work(int split, bool chunked, int group) const {
   // (system, cell * split + part) for the 27-cell kernel (times pair_nch plus
-  // the chunk group for warp items), or (system, block * 3 + z-part) for the
-  // fine-cell kernel
+  // the chunk group for warp items; (row group * 9 + part) for items of
+  // `group` home cells), or (system, block * 3 + z-part) for the fine-cell
+  // kernel
   std::vector<int2> pw;
   for (int s = 0; s < (int)hsys.size(); ++s) {
     const SysDesc &S = hsys[s];
+    if (group_of(s, group) > 1 && cell_factor == 1) {
+      const int ngroups = (S.nc[0] + group - 1) / group * S.nc[1] * S.nc[2];
+      for (int gi = 0; gi < ngroups; ++gi)
+        for (int k = 0; k < 9; ++k) pw.push_back(make_int2(s, gi * 9 + k));
+      continue;
+    }
     const int nitem = cell_factor == 2 ? S.nb[0] * S.nb[1] * S.nb[2] : S.ncell;
     const int parts = cell_factor == 2 ? 3 : split;
     const int nch = chunked ? S.pair_nch : 1;
@@ -432,15 +439,13 @@ int Engine::snapshot_cells(cudaStream_t st) {
 // last CTAs of the 27-cell kernel are short ones.  Cost of an item: its real
 // home beads x the real beads it stages (Gaussian core) + 4 x its charged
 // home beads x the charged and image beads it stages (electrostatics).
-void Engine::order_by_cost(std::vector<int2> &pw, int split, bool chunked) const {
+void Engine::order_by_cost(std::vector<int2> &pw, int split, bool chunked, int group) const {
   if (snap_cnt.empty() || cell_factor != 1) return;
   std::vector<std::pair<long long, int>> key(pw.size());
-  for (size_t w = 0; w < pw.size(); ++w) {
-    const SysDesc &S = hsys[pw[w].x];
-    const int base = chunked ? pw[w].y / S.pair_nch : pw[w].y;
-    const int cloc = base / split, part = base % split;
-    const int cx = cloc % S.nc[0], cy = (cloc / S.nc[0]) % S.nc[1], cz = cloc / (S.nc[0] * S.nc[1]);
-    const long long hg = S.cell_off + cloc;
+  // estimated cost of home cell (cx, cy, cz) against its neighbour cells of
+  // `part`: pairs of the Gaussian core + 4 x those of the electrostatics
+  auto cell_cost = [&](const SysDesc &S, int cx, int cy, int cz, int part) {
+    const long long hg = S.cell_off + cx + S.nc[0] * (cy + S.nc[1] * cz);
     const long long hreal = snap_cnt[hg] - snap_nimg[hg], hq = snap_nq[hg] - snap_nimg[hg];
     const int dz = (split == 3 ? part : part / 3) - 1;
     long long sreal = 0, sq = 0;
@@ -453,7 +458,24 @@ void Engine::order_by_cost(std::vector<int2> &pw, int split, bool chunked) const
       sreal += snap_cnt[cg] - snap_nimg[cg];
       sq += snap_nq[cg];
     }
-    key[w] = {-(hreal * sreal + 4 * hq * sq), (int)w};
+    return hreal * sreal + 4 * hq * sq;
+  };
+  for (size_t w = 0; w < pw.size(); ++w) {
+    const SysDesc &S = hsys[pw[w].x];
+    long long cost = 0;
+    if (group_of(pw[w].x, group) > 1) {
+      const int ngx = (S.nc[0] + group - 1) / group;
+      const int gi = pw[w].y / 9, part = pw[w].y % 9;
+      const int x0 = (gi % ngx) * group, cy = (gi / ngx) % S.nc[1], cz = gi / (ngx * S.nc[1]);
+      for (int x = x0; x < std::min(x0 + group, S.nc[0]); ++x)
+        cost += cell_cost(S, x, cy, cz, part);
+    } else {
+      const int base = chunked ? pw[w].y / S.pair_nch : pw[w].y;
+      const int cloc = base / split, part = base % split;
+      cost = cell_cost(S, cloc % S.nc[0], (cloc / S.nc[0]) % S.nc[1],
+                       cloc / (S.nc[0] * S.nc[1]), part);
+    }
+    key[w] = {-cost, (int)w};
   }
   std::stable_sort(key.begin(), key.end());
   std::vector<int2> out(pw.size());
@@ -474,12 +496,31 @@ static bool pair_shape_ok(int split, int threads, int ctas_per_sm, int nelec) {
   return (split == 3 || split == 9) && (ok_warp || ok_cta);
 }
 
-int Engine::set_pair_config(int split, int threads, int ctas_per_sm, int nelec, int chunks) {
+// Home cells per CTA item: 1, or 2..3 with split 9 CTA items on the 27-cell
+// stencil.  A system takes the group when it has at least group + 2 cells
+// along x (the staged cells of an item are then distinct), else one home
+// cell per item.
+bool Engine::pair_group_ok(int split, int nelec, int group) const {
+  if (group == 1) return true;
+  return group >= 2 && group <= 3 && split == 9 && nelec >= 1 && cell_factor == 1;
+}
+
+int Engine::group_of(int s, int group) const {
+  return group > 1 && hsys[s].nc[0] >= group + 2 ? group : 1;
+}
+
+int Engine::set_pair_config(int split, int threads, int ctas_per_sm, int nelec, int chunks,
+                            int group) {
   if (!pair_shape_ok(split, threads, ctas_per_sm, nelec) || chunks < 0 ||
       chunks > kMaxPairChunks) {
     set_error("pair configuration must be split 3|9 and either 128|160|192 threads, 1..3 "
               "electrostatics warps (at least 2 core warps), 0..8 CTAs per SM, or warp items "
               "(0 electrostatics warps): 64|96|128 threads, 1..28 resident warps per SM");
+    return GCME_ERR_INVALID;
+  }
+  if (!pair_group_ok(split, nelec, group)) {
+    set_error("pair_group must be 1, or 2..3 with split 9 CTA items (1..3 electrostatics "
+              "warps)");
     return GCME_ERR_INVALID;
   }
   pair_ctas_per_sm = ctas_per_sm;
@@ -489,12 +530,16 @@ int Engine::set_pair_config(int split, int threads, int ctas_per_sm, int nelec, 
     hsys[s].pair_split = split;
     hsys[s].pair_nelec = nelec;
     hsys[s].pair_nch = chunked ? chunks_of(s) : 1;
+    hsys[s].pair_group = group_of(s, group);
   }
-  std::vector<int2> pw = make_pair_work(split, chunked);
-  order_by_cost(pw, split, chunked);
+  std::vector<int2> pw = make_pair_work(split, chunked, group);
+  order_by_cost(pw, split, chunked, group);
   pair_split = split;
   pair_threads = threads;
   pair_nelec = nelec;
+  pair_group = group;
+  pair_groups_on = false;
+  for (int s = 0; s < (int)hsys.size(); ++s) pair_groups_on |= hsys[s].pair_group > 1;
   GCME_CK(cudaMemcpy(const_cast<SysDesc *>(P.sys), hsys.data(), sizeof(SysDesc) * hsys.size(),
                      cudaMemcpyHostToDevice));
   GCME_CK(cudaMemcpy(pair_work, pw.data(), sizeof(int2) * pw.size(), cudaMemcpyHostToDevice));
@@ -535,7 +580,7 @@ int Engine::set_spread_cells(bool on) {
 }
 
 int Engine::apply_tuning(int split, int threads, int ctas_per_sm, int nelec, const int lpb[3],
-                         bool plane, int chunks, bool spread_cells) {
+                         bool plane, int chunks, bool spread_cells, int group) {
   const bool pair_shapes = cell_factor == 1 && !use_list;
   const size_t rsz = fp64 ? sizeof(double2) : sizeof(float2);
   bool ok = !(plane && !plane_fits());
@@ -544,13 +589,14 @@ int Engine::apply_tuning(int split, int threads, int ctas_per_sm, int nelec, con
          (2 * (size_t)lpb[a] + 1) * plan.kmax[a] * rsz <= kFftSmemLimit;
   if (pair_shapes)
     ok = ok && pair_shape_ok(split, threads, ctas_per_sm, nelec) && chunks >= 0 &&
-         chunks <= kMaxPairChunks;
+         chunks <= kMaxPairChunks && pair_group_ok(split, nelec, group);
   ok = ok && !(spread_cells && !cell_spread_ok());
   if (!ok) {
     set_error("launch shapes out of range or larger than shared memory");
     return GCME_ERR_INVALID;
   }
-  int rc = pair_shapes ? set_pair_config(split, threads, ctas_per_sm, nelec, chunks) : GCME_OK;
+  int rc = pair_shapes ? set_pair_config(split, threads, ctas_per_sm, nelec, chunks, group)
+                       : GCME_OK;
   for (int a = 0; !rc && a < 3; ++a) rc = set_fft_lpb(a, lpb[a]);
   if (!rc) rc = set_fft_plane(plane);
   if (!rc) rc = set_spread_cells(spread_cells);
@@ -690,6 +736,7 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
     S.pair_split = pair_split;
     S.pair_nelec = pair_nelec;
     S.pair_nch = 1;
+    S.pair_group = 1;
     for (int a = 0; a < 3; ++a) {
       S.nc[a] = cells_per_axis(p.box[a], p.rc, cell_factor);
       S.nb[a] = (S.nc[a] + 1) / 2;
@@ -1185,8 +1232,8 @@ void Engine::enqueue_sort_pairs(const Pool &Q, cudaStream_t st, bool vir, bool d
   if (fork) fork_pme(Q, st, vir, timed, fork > 1);
   if (timed) cudaEventRecordWithFlags(phase_ev[2], st, cudaEventRecordExternal);
   if (use_list) launch_pair_list(Q, vir, dbg, st);
-  launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, pair_ctas(), pair_counter,
-              vir, dbg, bonds_in_pair(dbg), st, pair_nelec == 0);
+  launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, pair_ctas(),
+              pair_counter, vir, dbg, bonds_in_pair(dbg), st, pair_nelec == 0, pair_groups_on);
   if (timed) cudaEventRecordWithFlags(phase_ev[3], st, cudaEventRecordExternal);
 }
 
@@ -1543,12 +1590,12 @@ int gcme_system_set_box(gcme_sys *sys, const double *box, gcme_stream_t stream) 
   // carried over); the state lives in the caller's buffers
   GCME_TRY_CK(cudaStreamSynchronize(st));
   const int split = E.pair_split, threads = E.pair_threads, ctas = E.pair_ctas_per_sm,
-            nelec = E.pair_nelec, chunks = E.pair_chunks;
+            nelec = E.pair_nelec, chunks = E.pair_chunks, group = E.pair_group;
   E.release();
   E.pair_split = split;
   int rc2 = E.build(E.device, {sys->spec}, false);
   if (rc2) return rc2;
-  return E.set_pair_config(split, threads, ctas, nelec, chunks);
+  return E.set_pair_config(split, threads, ctas, nelec, chunks, group);
 }
 
 int gcme_pressure(gcme_sys *sys, const double *d_pos, double kT, double *h_pressure,
@@ -1904,6 +1951,7 @@ static void fill_tuning(const Engine &eng, double pair_ms, double pme_ms, bool h
   out->pair_ctas_per_sm = eng.pair_ctas_per_sm;
   out->pair_nelec = eng.pair_nelec;
   out->pair_chunks = eng.pair_chunks;
+  out->pair_group = eng.pair_group;
   out->spread_cells = eng.plan.cell_spread;
   for (int a = 0; a < 3; ++a) out->fft_lpb[a] = eng.plan.lpb[a];
   out->fft_plane = eng.plan.use_plane;
@@ -1939,7 +1987,7 @@ int gcme_apply_tuning(gcme_sys *sys, const gcme_tuning *t) {
   GCME_TRY_CK(cudaSetDevice(sys->eng.device));
   return sys->eng.apply_tuning(t->pair_split, t->pair_threads, t->pair_ctas_per_sm,
                                t->pair_nelec, t->fft_lpb, t->fft_plane != 0, t->pair_chunks,
-                               t->spread_cells != 0);
+                               t->spread_cells != 0, t->pair_group > 1 ? t->pair_group : 1);
 }
 
 int gcme_batch_apply_tuning(gcme_batch *bt, const gcme_tuning *t) {
@@ -1950,7 +1998,7 @@ int gcme_batch_apply_tuning(gcme_batch *bt, const gcme_tuning *t) {
   GCME_TRY_CK(cudaSetDevice(bt->eng.device));
   return bt->eng.apply_tuning(t->pair_split, t->pair_threads, t->pair_ctas_per_sm,
                               t->pair_nelec, t->fft_lpb, t->fft_plane != 0, t->pair_chunks,
-                              t->spread_cells != 0);
+                              t->spread_cells != 0, t->pair_group > 1 ? t->pair_group : 1);
 }
 
 int gcme_batch_autotune(gcme_batch *bt, int32_t flags, gcme_tuning *out, gcme_stream_t stream) {

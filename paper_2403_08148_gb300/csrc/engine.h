@@ -95,26 +95,32 @@ class Engine {
 
   int nsys() const { return (int)hsys.size(); }
   // (system, code) pair work items: code = cell * split + part, times
-  // S.pair_nch plus the chunk group when chunked (warp items)
-  std::vector<int2> make_pair_work(int split, bool chunked = false) const;
+  // S.pair_nch plus the chunk group when chunked (warp items); group > 1
+  // (CTA items of split 9): code = row group * 9 + part, row groups of
+  // `group` consecutive home cells along x
+  std::vector<int2> make_pair_work(int split, bool chunked = false, int group = 1) const;
   // chunk groups per (home cell, part) of warp items for system s:
   // pair_chunks when set, else the median real-bead count of its non-empty
   // cells in chunks of 32 (from the last cell snapshot, else n / ncell),
   // 1..kMaxPairChunks
   int chunks_of(int s) const;
   std::vector<int2> make_fft_work(int axis, int lpb) const;
-  int set_pair_config(int split, int threads, int ctas_per_sm, int nelec = 1, int chunks = 0);
+  int set_pair_config(int split, int threads, int ctas_per_sm, int nelec = 1, int chunks = 0,
+                      int group = 1);
+  bool pair_group_ok(int split, int nelec, int group) const;
+  int group_of(int s, int group) const;  // system s's home cells per item
   // cell occupancy of the last cell sort (host copy) and the work-item
   // order it implies (heaviest first)
   int snapshot_cells(cudaStream_t st);
-  void order_by_cost(std::vector<int2> &pw, int split, bool chunked = false) const;
+  void order_by_cost(std::vector<int2> &pw, int split, bool chunked = false,
+                     int group = 1) const;
   std::vector<int> snap_cnt, snap_nimg, snap_nq;
   int set_fft_lpb(int axis, int lpb);
   bool plane_fits() const;
   int set_fft_plane(bool on);
   // launch shapes given by the caller (checked before any is changed)
   int apply_tuning(int split, int threads, int ctas_per_sm, int nelec, const int lpb[3],
-                   bool plane, int chunks = 0, bool spread_cells = false);
+                   bool plane, int chunks = 0, bool spread_cells = false, int group = 1);
   // charges spread cell by cell through shared memory (FP32 27-cell path
   // without lists), else straight to the global grid
   bool cell_spread_ok() const { return !fp64 && cell_factor == 1 && !use_list; }
@@ -146,6 +152,9 @@ class Engine {
   int pair_threads = kDefaultPairThreads;  // 128, 160 or 192 threads per pair CTA
   int pair_nelec = 1;  // of which electrostatics warps (1 to 3; 0: one warp per item)
   int pair_chunks = 0;  // warp items per (home cell, part): 1..4, 0 automatic
+  int pair_group = 1;   // CTA items of split 9: home cells along x per item (1..3), for
+                        // systems with at least pair_group + 2 cells along x
+  bool pair_groups_on = false;  // some system takes items of several home cells
   int pair_ctas_per_sm = 0;  // 0: one CTA per work item; else resident CTAs per SM fetching items
   int n_sm = 152;
   int *pair_counter = nullptr;  // dynamic work-item counter of the pair kernel

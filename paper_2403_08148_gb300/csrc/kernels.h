@@ -58,10 +58,11 @@ void launch_sort(const Pool &P, cudaStream_t st);
 // leaves zero).  bonds: the FP32 27-cell kernel also evaluates the harmonic
 // bonds, one bond per thread in work items after the cell items.
 // warp_items: the FP32 one-species kernel with one warp per work item
-// (pair_warp.cuh; ctas > 0 required), else one CTA per work item.
+// (pair_warp.cuh; ctas > 0 required), else one CTA per work item; groups:
+// CTA items of several home cells (SysDesc::pair_group > 1 in some system).
 void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell_factor,
                  int threads, int ctas, int *counter, bool vir, bool dbg, bool bonds,
-                 cudaStream_t st, bool warp_items = false);
+                 cudaStream_t st, bool warp_items = false, bool groups = false);
 // Verlet neighbour list (nlist.cu): rebuild decision (clears the flag,
 // then sets it when a bead moved more than skin/2 since the last build or a
 // rebuild is pending), the gated build, the per-step refresh of the sorted

@@ -22,12 +22,13 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_fine(Pool P, const int2 *
 // smaller than the SMs' capacity leaves slots free for the concurrent PME
 // branch.  Items nwork .. nwork + nbi - 1 are harmonic bonds (one per thread),
 // taken last, by CTAs that would otherwise idle at the end of the launch.
-// One species without the debug dump runs the packed item (pair_core2).
-template <bool VIR, bool DBG, bool MT>
+// One species without the debug dump runs the packed item (pair_core2), of
+// one home cell, or of several along x when GRP (SysDesc::pair_group).
+template <bool VIR, bool DBG, bool MT, bool GRP = false>
 __global__ void __launch_bounds__(192, 5) k_pair_f32(Pool P, const int2 *work, int nwork,
                                                      int nbi, int *counter) {
   __shared__ __align__(16) unsigned char raw[kPairSmemBytes];
-  __shared__ PairSeg seg[9];
+  __shared__ PairSeg seg[kItemSegs];
   __shared__ int s_total[2];
   __shared__ int s_item;
   __shared__ unsigned char stj[MT ? kPairCap : 1];
@@ -44,7 +45,8 @@ __global__ void __launch_bounds__(192, 5) k_pair_f32(Pool P, const int2 *work, i
         dev_bonds<VIR, true>(P, (long long)(w - nwork) * blockDim.x + threadIdx.x);
         continue;
       }
-      if (PK) dev_pair_f32_item_pk<VIR>(P, work, w, raw, seg, s_total);
+      if (PK && GRP) dev_pair_f32_item_grp<VIR>(P, work, w, raw, seg, s_total);
+      else if (PK) dev_pair_f32_item_pk<VIR>(P, work, w, raw, seg, s_total);
       else dev_pair_f32_item<VIR, DBG, MT>(P, work, w, sj, seg, s_total, stj, stab);
     }
     return;
@@ -62,7 +64,8 @@ __global__ void __launch_bounds__(192, 5) k_pair_f32(Pool P, const int2 *work, i
       __syncthreads();  // every thread has read s_item before the next fetch
       continue;
     }
-    if (PK) dev_pair_f32_item_pk<VIR>(P, work, w, raw, seg, s_total);
+    if (PK && GRP) dev_pair_f32_item_grp<VIR>(P, work, w, raw, seg, s_total);
+    else if (PK) dev_pair_f32_item_pk<VIR>(P, work, w, raw, seg, s_total);
     else dev_pair_f32_item<VIR, DBG, MT>(P, work, w, sj, seg, s_total, stj, stab);
   }
 }
@@ -228,7 +231,7 @@ __global__ void __launch_bounds__(128) k_pair_f64(Pool P) {
 
 void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell_factor,
                  int threads, int ctas, int *counter, bool vir, bool dbg, bool bonds,
-                 cudaStream_t st, bool warp_items) {
+                 cudaStream_t st, bool warp_items, bool groups) {
   if (P.n_ext == 0) return;
   if (fp64) {
     int nb = (int)((P.n_ext + 127) / 128);
@@ -262,15 +265,18 @@ void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell
   const bool dyn = ctas > 0;
   const int grid = dyn ? std::max(1, std::min(ntot, ctas)) : ntot;
   if (!dyn) counter = nullptr;
+  auto go = [&](auto kern) { launch_k(kern, grid, tb, 0, st, P, work, nwork, nbi, counter); };
   if (P.ptab) {  // several species
-    if (dbg) launch_k(k_pair_f32<false, true, true>, grid, tb, 0, st, P, work, nwork, nbi, counter);
-    else if (vir) launch_k(k_pair_f32<true, false, true>, grid, tb, 0, st, P, work, nwork, nbi, counter);
-    else launch_k(k_pair_f32<false, false, true>, grid, tb, 0, st, P, work, nwork, nbi, counter);
+    if (dbg) go(k_pair_f32<false, true, true>);
+    else if (vir) go(k_pair_f32<true, false, true>);
+    else go(k_pair_f32<false, false, true>);
     return;
   }
-  if (dbg) launch_k(k_pair_f32<false, true, false>, grid, tb, 0, st, P, work, nwork, nbi, counter);
-  else if (vir) launch_k(k_pair_f32<true, false, false>, grid, tb, 0, st, P, work, nwork, nbi, counter);
-  else launch_k(k_pair_f32<false, false, false>, grid, tb, 0, st, P, work, nwork, nbi, counter);
+  if (dbg) go(k_pair_f32<false, true, false>);
+  else if (groups && vir) go(k_pair_f32<true, false, false, true>);
+  else if (groups) go(k_pair_f32<false, false, false, true>);
+  else if (vir) go(k_pair_f32<true, false, false>);
+  else go(k_pair_f32<false, false, false>);
 }
 
 }  // namespace gcme

@@ -63,6 +63,9 @@ struct PairSeg {
 // this and the scalar items' float4 array share one shared-memory block of
 // kPairSmemBytes.
 constexpr int kPkCap = 1280;
+// segments of a CTA work item in shared memory: up to 9 staged, then up to
+// 3 home cells (packed items)
+constexpr int kItemSegs = 12;
 constexpr int kPkCapQ = 640;
 constexpr int kPairSmemBytes =
     (16 * kPairCap > 12 * kPkCap + 16 * kPkCapQ) ? 16 * kPairCap : 12 * kPkCap + 16 * kPkCapQ;
@@ -560,9 +563,87 @@ __device__ __forceinline__ void pair_role_range(bool core_role, const float4 *J,
 #undef GCME_ROLE
 }
 
-// One work item by the whole CTA: a home cell and 9 (split 3) or 3
-// (split 9) of its 27 neighbour cells.  Shared memory: sj[kPairCap],
-// seg[9], s_total[1].  Ends with a barrier.
+// Cell (x, y, z) of system S, each coordinate at most one period outside
+// [0, nc), as a segment: its sorted range and class boundaries, image code
+// and periodic shift; self = 0.
+__device__ __forceinline__ PairSeg cell_segment(const Pool &P, const SysDesc &S, int x, int y,
+                                                int z) {
+  const int ncv[3] = {S.nc[0], S.nc[1], S.nc[2]};
+  const int u[3] = {x, y, z};
+  int v[3], nn[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    nn[a] = floor_div(u[a], ncv[a]);
+    v[a] = u[a] - nn[a] * ncv[a];
+  }
+  const long long cg = S.cell_off + v[0] + ncv[0] * (v[1] + ncv[1] * v[2]);
+  PairSeg g;
+  g.beg = P.cell_start[cg];
+  g.n = P.cell_start[cg + 1] - g.beg;
+  g.a = P.cell_nimg[cg];
+  g.b = P.cell_nq[cg];
+  g.code = (nn[0] + 1) + 3 * (nn[1] + 1) + 9 * (nn[2] + 1);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) g.sh[a] = (float)nn[a] * S.boxf[a];
+  g.self = 0;
+  g.shifted = (nn[0] != 0 || nn[1] != 0 || nn[2] != 0);
+  g.soff = 0;
+  g.qoff = 0;
+  return g;
+}
+
+// Segment k of a work item of the 27-cell kernel with one home cell (split
+// 3: the 9 cells at dz = part - 1; split 9: the 3 cells along x at dy, dz =
+// part % 3 - 1, part / 3 - 1), with its periodic shift.
+__device__ __forceinline__ PairSeg item_segment(const Pool &P, const SysDesc &S, int cloc,
+                                                int part, int k) {
+  const int split = S.pair_split;
+  const int nc0 = S.nc[0], nc1 = S.nc[1];
+  const int cx = cloc % nc0, cy = (cloc / nc0) % nc1, cz = cloc / (nc0 * nc1);
+  const int dzo = (split == 3 ? part : part / 3) - 1;
+  const int dxo = k % 3 - 1, dyo = split == 3 ? k / 3 - 1 : part % 3 - 1;
+  PairSeg g = cell_segment(P, S, cx + dxo, cy + dyo, cz + dzo);
+  g.self = (dxo == 0 && dyo == 0 && dzo == 0);
+  return g;
+}
+
+// The home cells of a CTA work item: x0 .. x0 + nhome - 1 of the x-row
+// (y, z), and its part.  SysDesc::pair_group = G > 1 (split 9 only): code =
+// (row group) * 9 + part with ceil(nc_x / G) groups of G consecutive home
+// cells per row, the last one shorter; its segments are the nhome + 2
+// cells x0 - 1 .. x0 + nhome of the row (y + dy, z + dz), distinct because
+// nc_x >= G + 2, and each home cell pairs with the three of them around
+// it.  G = 1: code = cell * split + part.
+struct ItemCells {
+  int x0, y, z, nhome, part;
+};
+__device__ __forceinline__ ItemCells item_cells(const SysDesc &S, int code) {
+  const int G = S.pair_group > 1 ? S.pair_group : 1;
+  ItemCells c;
+  if (G == 1) {
+    const int split = S.pair_split;
+    const int cloc = code / split;
+    c.part = code % split;
+    c.x0 = cloc % S.nc[0];
+    c.y = (cloc / S.nc[0]) % S.nc[1];
+    c.z = cloc / (S.nc[0] * S.nc[1]);
+    c.nhome = 1;
+  } else {
+    const int ngx = (S.nc[0] + G - 1) / G;
+    const int gi = code / 9;
+    c.part = code % 9;
+    c.x0 = (gi % ngx) * G;
+    c.y = (gi / ngx) % S.nc[1];
+    c.z = gi / (ngx * S.nc[1]);
+    c.nhome = min(G, S.nc[0] - c.x0);
+  }
+  return c;
+}
+
+// One home cell of a work item by the whole CTA (code = cell * split +
+// part): the home cell and 9 (split 3) or 3 (split 9) of its 27 neighbour
+// cells.  Shared memory: sj[kPairCap], seg[9], s_total[1].  Ends with a
+// barrier.
 //
 // Warp roles: warps 0 .. W-2 take the home cell's real beads 32 per warp
 // (Gaussian core over the staged real beads); warp W-1 takes its charged
@@ -573,17 +654,14 @@ __device__ __forceinline__ void pair_role_range(bool core_role, const float4 *J,
 // MT: stj[kPairCap] (species of the staged beads) and stab[nt * nt] (the
 // system's pair table) in shared memory as well.
 template <bool VIR, bool DBG, bool MT = false>
-__device__ __forceinline__ void dev_pair_f32_item(const Pool &P, const int2 *work, int w,
-                                                  float4 *sj, PairSeg *seg, int *s_total_p,
-                                                  unsigned char *stj = nullptr,
-                                                  PairTab *stab = nullptr) {
+__device__ __forceinline__ void dev_pair_f32_cell(const Pool &P, int s, int code, float4 *sj,
+                                                  PairSeg *seg, int *s_total_p,
+                                                  unsigned char *stj, PairTab *stab) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int ncore = (blockDim.x >> 5) - 1;  // core warps
   const bool core_role = warp < ncore;
   int &s_total = *s_total_p;
-  const int s = work[w].x;
-  const int code = work[w].y;
   // with neighbour lists, only the systems whose lists overflowed come here
   if (P.list_ovf && !P.list_ovf[s]) {
     __syncthreads();
@@ -707,39 +785,33 @@ __device__ __forceinline__ void dev_pair_f32_item(const Pool &P, const int2 *wor
   __syncthreads();
 }
 
-// Segment k of a work item of the 27-cell kernel (split 3: the 9 cells at
-// dz = part - 1; split 9: the 3 cells along x at dy, dz = part % 3 - 1,
-// part / 3 - 1), with its periodic shift.
-__device__ __forceinline__ PairSeg item_segment(const Pool &P, const SysDesc &S, int cloc,
-                                                int part, int k) {
-  const int split = S.pair_split;
-  const int nc0 = S.nc[0], nc1 = S.nc[1], nc2 = S.nc[2];
-  const int cx = cloc % nc0, cy = (cloc / nc0) % nc1, cz = cloc / (nc0 * nc1);
-  const int dzo = (split == 3 ? part : part / 3) - 1;
-  const int dxo = k % 3 - 1, dyo = split == 3 ? k / 3 - 1 : part % 3 - 1;
-  const int u[3] = {cx + dxo, cy + dyo, cz + dzo};
-  const int ncv[3] = {nc0, nc1, nc2};
-  int v[3], nn[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    nn[a] = floor_div(u[a], ncv[a]);
-    v[a] = u[a] - nn[a] * ncv[a];
+// One work item (system wk.x, code wk.y) on the scalar path: each of its
+// home cells in turn (one unless SysDesc::pair_group > 1).  Ends with a
+// barrier.
+template <bool VIR, bool DBG, bool MT = false>
+__device__ __forceinline__ void dev_pair_f32_item(const Pool &P, int2 wk, float4 *sj,
+                                                  PairSeg *seg, int *s_total,
+                                                  unsigned char *stj = nullptr,
+                                                  PairTab *stab = nullptr) {
+  const SysDesc &S = P.sys[wk.x];
+  if (S.pair_group <= 1) {
+    dev_pair_f32_cell<VIR, DBG, MT>(P, wk.x, wk.y, sj, seg, s_total, stj, stab);
+    return;
   }
-  const long long cg = S.cell_off + v[0] + nc0 * (v[1] + nc1 * v[2]);
-  PairSeg g;
-  g.beg = P.cell_start[cg];
-  g.n = P.cell_start[cg + 1] - g.beg;
-  g.a = P.cell_nimg[cg];
-  g.b = P.cell_nq[cg];
-  g.code = (nn[0] + 1) + 3 * (nn[1] + 1) + 9 * (nn[2] + 1);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) g.sh[a] = (float)nn[a] * S.boxf[a];
-  g.self = (dxo == 0 && dyo == 0 && dzo == 0);
-  g.shifted = (nn[0] != 0 || nn[1] != 0 || nn[2] != 0);
-  g.soff = 0;
-  g.qoff = 0;
-  return g;
+  const ItemCells c = item_cells(S, wk.y);
+  for (int h = 0; h < c.nhome; ++h) {
+    const int cloc = c.x0 + h + S.nc[0] * (c.y + S.nc[1] * c.z);
+    dev_pair_f32_cell<VIR, DBG, MT>(P, wk.x, cloc * 9 + c.part, sj, seg, s_total, stj, stab);
+  }
 }
+template <bool VIR, bool DBG, bool MT = false>
+__device__ __forceinline__ void dev_pair_f32_item(const Pool &P, const int2 *work, int w,
+                                                  float4 *sj, PairSeg *seg, int *s_total,
+                                                  unsigned char *stj = nullptr,
+                                                  PairTab *stab = nullptr) {
+  dev_pair_f32_item<VIR, DBG, MT>(P, work[w], sj, seg, s_total, stj, stab);
+}
+
 
 // Packed items (one species, no debug dump), in three parts shared by the
 // CTA kernel and the pipelined kernel: the staged-array layout and offsets,
@@ -846,25 +918,30 @@ __device__ __forceinline__ void pk_stage_segment(const Pool &P, PairSeg &g, cons
   }
 }
 
-// The home cell's box (for the staging cull).
-__device__ __forceinline__ void pk_home_box(const SysDesc &S, int cloc, float hlo[3],
+// The box of the item's home cells x0 .. x0 + nhome - 1 of row (y, z), for
+// the staging cull.
+__device__ __forceinline__ void pk_home_box(const SysDesc &S, const ItemCells &c, float hlo[3],
                                             float hhi[3]) {
-  const int hc[3] = {cloc % S.nc[0], (cloc / S.nc[0]) % S.nc[1], cloc / (S.nc[0] * S.nc[1])};
+  const int lo[3] = {c.x0, c.y, c.z}, w[3] = {c.nhome, 1, 1};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    hlo[a] = (float)hc[a] * S.cside[a];
-    hhi[a] = hlo[a] + S.cside[a];
+    hlo[a] = (float)lo[a] * S.cside[a];
+    hhi[a] = hlo[a] + (float)w[a] * S.cside[a];
   }
 }
 
 // Evaluation of one staged item by the role warps: rt is the thread's index
 // among the nrole threads that take part (warps 0 .. ncore-1 of them core,
 // the last nelec electrostatics).  Warp-synchronous per warp; no CTA barrier.
-template <bool VIR>
+//
+// GRP (items of several home cells): the self segment is seg[selfk] (each
+// home cell's own among the staged cells around it); else the one flagged
+// self.
+template <bool VIR, bool GRP = false>
 __device__ __forceinline__ void pk_compute(const Pool &P, const SysDesc &S, int s, int hbeg,
                                            int hend, int himg, int hq, const PairSeg *seg,
-                                           int nseg, const unsigned char *smem, int rt,
-                                           int nrole) {
+                                           int nseg, int selfk, const unsigned char *smem,
+                                           int rt, int nrole) {
   const float *sx = reinterpret_cast<const float *>(smem);
   const float *sy = sx + kPkCap;
   const float *sz = sy + kPkCap;
@@ -908,7 +985,7 @@ __device__ __forceinline__ void pk_compute(const Pool &P, const SysDesc &S, int 
           const int n2 = (g.nk + 1) & ~1;
           const float *X = sx + g.soff, *Y = sy + g.soff, *Z = sz + g.soff;
           const int j0 = g.beg + g.a;
-          if (g.self)
+          if (GRP ? k == selfk : g.self != 0)
             pair_core2<false, true, VIR>(X, Y, Z, n2, j0, xi, i, g, rc2, gcc, B);
           else if (tail)
             pair_core2_tail<VIR>(X, Y, Z, n2, xi, g, gcc, B);
@@ -936,7 +1013,7 @@ __device__ __forceinline__ void pk_compute(const Pool &P, const SysDesc &S, int 
           const int lo = 2 * (np2 * ew / nelec), hi = 2 * (np2 * (ew + 1) / nelec);
           const float *X = qx + g.qoff;
           if (tab_nm1 < 0) {  // no table (very small smearing radius)
-            if (g.self)
+            if (GRP ? k == selfk : g.self != 0)
               pair_elec2<false, true, VIR, false>(X, lo, hi, g.beg, xi, i, g, S, rc2, A,
                                                   tab, tab_scale, tab_nm1);
             else if (g.shifted)
@@ -945,7 +1022,7 @@ __device__ __forceinline__ void pk_compute(const Pool &P, const SysDesc &S, int 
             else
               pair_elec2<false, false, VIR, false>(X, lo, hi, g.beg, xi, i, g, S, rc2,
                                                    A, tab, tab_scale, tab_nm1);
-          } else if (g.self) {
+          } else if (GRP ? k == selfk : g.self != 0) {
             pair_elec2<false, true, VIR, true>(X, lo, hi, g.beg, xi, i, g, S, rc2, A,
                                                tab, tab_scale, tab_nm1);
           } else if (g.shifted) {
@@ -963,9 +1040,10 @@ __device__ __forceinline__ void pk_compute(const Pool &P, const SysDesc &S, int 
   }
 }
 
-// Packed variant of dev_pair_f32_item, one CTA per item: items whose beads
-// exceed the packed capacities take the scalar path.  smem: kPairSmemBytes;
-// seg[9]; s_tot[2].  Ends with a barrier.
+// Packed variant of dev_pair_f32_item, one CTA per item of one home cell
+// (SysDesc::pair_group 1): items whose beads exceed the packed capacities
+// take the scalar path.  smem: kPairSmemBytes; seg[kItemSegs]; s_tot[2].
+// Ends with a barrier.
 template <bool VIR>
 __device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *work, int w,
                                                      unsigned char *smem, PairSeg *seg,
@@ -990,19 +1068,95 @@ __device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *
   if (tid == 0) pk_offsets(seg, nseg, s_tot);
   __syncthreads();
   if (s_tot[0] > kPkCap || s_tot[1] > kPkCapQ) {
-    dev_pair_f32_item<VIR, false, false>(P, work, w, reinterpret_cast<float4 *>(smem), seg,
-                                         s_tot);
+    dev_pair_f32_cell<VIR, false, false>(P, s, code, reinterpret_cast<float4 *>(smem), seg,
+                                         s_tot, nullptr, nullptr);
     return;
   }
   {
     float hlo[3], hhi[3];
-    pk_home_box(S, cloc, hlo, hhi);
+    ItemCells ic;
+    ic.x0 = cloc % S.nc[0];
+    ic.y = (cloc / S.nc[0]) % S.nc[1];
+    ic.z = cloc / (S.nc[0] * S.nc[1]);
+    ic.nhome = 1;
+    pk_home_box(S, ic, hlo, hhi);
     const int nwarp = blockDim.x >> 5;
     for (int k = warp; k < nseg; k += nwarp)
       pk_stage_segment(P, seg[k], hlo, hhi, S.cull2, smem, lane);
   }
   __syncthreads();
-  pk_compute<VIR>(P, S, s, hbeg, hend, himg, hq, seg, nseg, smem, tid, blockDim.x);
+  pk_compute<VIR>(P, S, s, hbeg, hend, himg, hq, seg, nseg, -1, smem, tid, blockDim.x);
+  __syncthreads();
+}
+
+// The scalar path for a packed item over capacity, out of line: its
+// registers are its own, so that the rare fallback does not raise the
+// packed path's register pressure.
+template <bool VIR>
+__device__ __noinline__ void pair_item_scalar(const Pool &P, int2 wk, float4 *sj, PairSeg *seg,
+                                              int *s_tot) {
+  dev_pair_f32_item<VIR, false, false>(P, wk, sj, seg, s_tot);
+}
+
+// The same for items of several home cells (SysDesc::pair_group > 1 in some
+// system; systems with pair_group 1 take their single home cell here too):
+// an item stages the nhome + 2 cells of its row once, culled against the
+// box of all its home cells (the home cells themselves staged whole in the
+// centre part), and evaluates each home cell over the three staged cells
+// around it.  seg[kItemSegs]: staged segments from 0, the home cells from 9.
+template <bool VIR>
+__device__ __forceinline__ void dev_pair_f32_item_grp(const Pool &P, const int2 *work, int w,
+                                                      unsigned char *smem, PairSeg *seg,
+                                                      int *s_tot) {
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int s = work[w].x;
+  const int code = work[w].y;
+  if (P.list_ovf && !P.list_ovf[s]) {
+    __syncthreads();
+    return;
+  }
+  const SysDesc &S = P.sys[s];
+  const int split = S.pair_split;
+  const ItemCells ic = item_cells(S, code);
+  const int nseg = split == 3 ? 9 : ic.nhome + 2;
+  const bool centre = ic.part == (split == 3 ? 1 : 4);
+  if (tid < nseg) {
+    if (ic.nhome == 1) {
+      seg[tid] = item_segment(P, S, ic.x0 + S.nc[0] * (ic.y + S.nc[1] * ic.z), ic.part, tid);
+    } else {
+      PairSeg g = cell_segment(P, S, ic.x0 - 1 + tid, ic.y + ic.part % 3 - 1,
+                               ic.z + ic.part / 3 - 1);
+      g.self = centre && tid >= 1 && tid <= ic.nhome;  // a home cell: staged whole
+      seg[tid] = g;
+    }
+  } else if (tid >= 32 && tid < 32 + ic.nhome) {
+    seg[9 + tid - 32] = cell_segment(P, S, ic.x0 + tid - 32, ic.y, ic.z);
+  }
+  __syncthreads();
+  if (tid == 0) pk_offsets(seg, nseg, s_tot);
+  __syncthreads();
+  if (s_tot[0] > kPkCap || s_tot[1] > kPkCapQ) {
+    pair_item_scalar<VIR>(P, work[w], reinterpret_cast<float4 *>(smem), seg, s_tot);
+    return;
+  }
+  {
+    float hlo[3], hhi[3];
+    pk_home_box(S, ic, hlo, hhi);
+    const int nwarp = blockDim.x >> 5;
+    for (int k = warp; k < nseg; k += nwarp)
+      pk_stage_segment(P, seg[k], hlo, hhi, S.cull2, smem, lane);
+  }
+  __syncthreads();
+  // one home cell: every staged segment, its own the self segment; several:
+  // the three staged cells around home cell h
+  const int selfk = centre ? (split == 3 ? 4 : 1) : -1;
+  const int wseg = ic.nhome == 1 ? nseg : 3;
+  for (int h = 0; h < ic.nhome; ++h) {
+    const PairSeg &hc = seg[9 + h];
+    pk_compute<VIR, true>(P, S, s, hc.beg, hc.beg + hc.n, hc.a, hc.b, seg + h, wseg, selfk, smem,
+                          tid, blockDim.x);
+  }
   __syncthreads();
 }
 

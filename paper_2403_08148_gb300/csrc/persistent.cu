@@ -104,9 +104,10 @@ __global__ void __launch_bounds__(128) k_persistent(Pool P, PersistArgs A) {
     } else {
       float4 *sj = reinterpret_cast<float4 *>(smem);
       PairSeg *seg = reinterpret_cast<PairSeg *>(smem + kPairSmemBytes);
-      int *st = reinterpret_cast<int *>(smem + kPairSmemBytes + sizeof(PairSeg) * 9);
+      int *st =
+          reinterpret_cast<int *>(smem + kPairSmemBytes + sizeof(PairSeg) * kItemSegs);
       // several species: the table (16-byte aligned) and the staged species
-      const size_t toff = (kPairSmemBytes + sizeof(PairSeg) * 9 + 16 + 15) / 16 * 16;
+      const size_t toff = (kPairSmemBytes + sizeof(PairSeg) * kItemSegs + 16 + 15) / 16 * 16;
       PairTab *stab = reinterpret_cast<PairTab *>(smem + toff);
       unsigned char *stj = smem + toff + sizeof(PairTab) * kMaxTypes * kMaxTypes;
       if (A.warp_items) {  // one warp per work item (pair_warp.cuh)
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(128) k_persistent(Pool P, PersistArgs A) {
           if (P.ptab)
             dev_pair_f32_item<false, false, true>(P, A.pair_work, w, sj, seg, st, stj, stab);
           else
-            dev_pair_f32_item_pk<false>(P, A.pair_work, w, smem, seg, st);
+            dev_pair_f32_item_grp<false>(P, A.pair_work, w, smem, seg, st);
         }
       }
     }
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(128) k_persistent(Pool P, PersistArgs A) {
 #undef GRID_LOOP
 
 size_t persistent_smem(const PmePlan &pl, bool species, bool warp_items) {
-  size_t pair = kPairSmemBytes + sizeof(PairSeg) * 9 + 16;
+  size_t pair = kPairSmemBytes + sizeof(PairSeg) * kItemSegs + 16;
   if (warp_items) pair = std::max(pair, 4 * sizeof(WarpSmem));  // 128 threads = 4 warps
   if (species)
     pair = (pair + 15) / 16 * 16 + sizeof(PairTab) * kMaxTypes * kMaxTypes + kPairCap;

@@ -9,6 +9,8 @@
 //                items dynamically so that the remaining slots host the
 //                concurrent PME branch}, and one warp per work item
 //                (CTAs of 4 warps, 3-7 per SM, or of 2 warps, 8-14 per SM);
+//                then, for the fastest CTA-item shape of split 9, items of 2
+//                or 3 consecutive home cells along x;
 //   PME:         lines per FFT tile along each axis in {4, 8, 16, 32, 64}
 //                (shared memory permitting), one axis at a time, x-y
 //                plane passes (one CTA per z-plane) vs per-axis passes, and
@@ -57,7 +59,7 @@ std::string cache_path() {
 
 struct Tuned {
   int split = 0, threads = 0, ctas = 0, lpb[3] = {0, 0, 0}, plane = 0, nelec = 1, chunks = 0,
-      spread = 0;
+      spread = 0, group = 1;
   double pair_ms = 0, pme_ms = 0;
 };
 
@@ -84,6 +86,8 @@ bool cache_lookup(const std::string &key, Tuned *t) {
       if (!h || std::sscanf(h, "\"pair_chunks\": %d", &x.chunks) != 1) x.chunks = 0;
       const char *sc = std::strstr(line.c_str(), "\"spread_cells\":");
       if (!sc || std::sscanf(sc, "\"spread_cells\": %d", &x.spread) != 1) x.spread = 0;
+      const char *gr = std::strstr(line.c_str(), "\"pair_group\":");
+      if (!gr || std::sscanf(gr, "\"pair_group\": %d", &x.group) != 1) x.group = 1;
       *t = x;  // the last entry for a key wins
       found = true;
     }
@@ -100,9 +104,9 @@ void cache_store(const std::string &key, const Tuned &t) {
                 "{\"key\": \"%s\", \"pair_split\": %d, \"pair_threads\": %d, "
                 "\"pair_ctas_per_sm\": %d, \"fft_lpb\": [%d, %d, %d], \"fft_plane\": %d, "
                 "\"forces_ms\": %.6f, \"pme_ms\": %.6f, \"pair_nelec\": %d, "
-                "\"pair_chunks\": %d, \"spread_cells\": %d}\n",
+                "\"pair_chunks\": %d, \"spread_cells\": %d, \"pair_group\": %d}\n",
                 key.c_str(), t.split, t.threads, t.ctas, t.lpb[0], t.lpb[1], t.lpb[2], t.plane,
-                t.pair_ms, t.pme_ms, t.nelec, t.chunks, t.spread);
+                t.pair_ms, t.pme_ms, t.nelec, t.chunks, t.spread, t.group);
   f << buf;
 }
 
@@ -168,7 +172,7 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
     if (rc0) return rc0;
   }
   if (!remeasure && !no_cache && cache_lookup(key.str(), &t)) {
-    int rc = set_pair_config(t.split, t.threads, t.ctas, t.nelec, t.chunks);
+    int rc = set_pair_config(t.split, t.threads, t.ctas, t.nelec, t.chunks, t.group);
     for (int a = 0; !rc && a < 3; ++a) rc = set_fft_lpb(a, t.lpb[a]);
     if (!rc) rc = set_fft_plane(t.plane != 0);
     if (!rc) rc = set_spread_cells(t.spread != 0 && cell_spread_ok());
@@ -222,7 +226,7 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
   auto timed = [&]() -> double { return timed_n(reps); };
   double best = 1e30;
   int bs = pair_split, bt = pair_threads, bc = pair_ctas_per_sm, be = pair_nelec,
-      bh = pair_chunks;
+      bh = pair_chunks, bg = pair_group;
   struct Cand {
     double ms;
     int split, threads, ctas, nelec, chunks;
@@ -262,9 +266,42 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
         bc = c.ctas;
         be = c.nelec;
         bh = c.chunks;
+        bg = 1;
       }
     }
-    int rc = set_pair_config(bs, bt, bc, be, bh);
+    // items of 2 or 3 home cells along x for the fastest CTA-item shape of
+    // split 9, around its resident CTAs per SM (larger items, fewer of them)
+    for (const Cand &c : cands) {
+      if (c.split != 9 || c.nelec < 1) continue;
+      for (int group : {2, 3}) {
+        bool any = false;  // some system takes the group
+        for (int s = 0; s < nsys(); ++s) any = any || group_of(s, group) > 1;
+        if (!any) continue;
+        const int opts[4] = {0, c.ctas - 1, c.ctas, c.ctas + 1};
+        for (int q = 0; q < 4; ++q) {
+          const int ctas = opts[q];
+          bool seen = false;
+          for (int r = 0; r < q; ++r) seen = seen || opts[r] == ctas;
+          if (seen || ctas < 0 || ctas == 1 || ctas == 2 || ctas == 7 || ctas > 8 ||
+              ctas > 40 / (c.threads / 32))
+            continue;  // as in the search above
+          int rc = set_pair_config(9, c.threads, ctas, c.nelec, 0, group);
+          if (rc) return rc;
+          const double ms = timed_n(3 * reps);
+          if (ms < best) {
+            best = ms;
+            bs = 9;
+            bt = c.threads;
+            bc = ctas;
+            be = c.nelec;
+            bh = 0;
+            bg = group;
+          }
+        }
+      }
+      break;  // the fastest such shape only (candidates are sorted)
+    }
+    int rc = set_pair_config(bs, bt, bc, be, bh, bg);
     if (rc) return rc;
   } else {
     best = timed();
@@ -316,6 +353,7 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
   t.ctas = pair_ctas_per_sm;
   t.nelec = pair_nelec;
   t.chunks = pair_chunks;
+  t.group = pair_group;
   t.spread = plan.cell_spread;
   t.plane = plan.use_plane;
   for (int a = 0; a < 3; ++a) t.lpb[a] = plan.lpb[a];

@@ -240,6 +240,56 @@ def test_pair_shapes_at_parity(split, threads, nelec, ctas):
     _check(s, out, oracle.energy_forces(s), FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
 
 
+@pytest.mark.parametrize("geom", [synth.GEOM_BULK, synth.GEOM_SLAB_PC])
+@pytest.mark.parametrize("threads,nelec,ctas,group", [
+    (160, 2, 5, 2), (192, 3, 0, 3), (128, 1, 4, 3), (160, 1, 0, 2)])
+def test_pair_group_items_at_parity(geom, threads, nelec, ctas, group):
+    """CTA work items of 2 or 3 consecutive home cells along x: 5 cells per
+    axis (the last group of 3 is ragged: 3 + 2), the row's staged cells
+    shared by the home cells, forces, energies and virial at parity with the
+    oracle, and the neighbour set (debug triples, scalar path over the same
+    items) bit-exact.  The conducting slab adds images to the charged
+    candidates."""
+    import torch
+    g = lib()
+    if geom not in _GROUP_CASES:
+        if geom == synth.GEOM_BULK:
+            s = synth.make_bulk(12000, seed_index=65, charged_frac=0.3, K=(20, 20, 20))
+        else:
+            s = synth.make_slab_fluid(synth.GEOM_SLAB_PC, 16000, charged_frac=0.2,
+                                      seed_index=66, aspect=0.5)
+        epos, _, _, n = oracle.electrostatic_beads(s)
+        want = oracle.pair_set(epos, s.box, s.rc)
+        _GROUP_CASES[geom] = (s, oracle.energy_forces(s), np.unique(want[want[:, 0] < n], axis=0))
+    s, ref, want = _GROUP_CASES[geom]
+    t = {"pair_split": 9, "pair_threads": threads, "pair_ctas_per_sm": ctas,
+         "pair_nelec": nelec, "pair_group": group, "fft_lpb": [8, 8, 8], "fft_plane": True}
+    out = gpu_forces(s, 0, virial=geom == synth.GEOM_BULK, tuning=t)
+    _check(s, out, ref, FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
+    if geom == synth.GEOM_BULK:
+        assert np.max(np.abs(out["virial"] - ref["virial"])) <= 1e-5 * np.max(
+            np.abs(ref["virial"]))
+    sysg = g.System(ctx(), g.params_from(s), s.q, s.bonds)
+    assert sysg.info().pair_path == g.GCME_PAIR_CELLS
+    sysg.apply_tuning(t)
+    dev = torch.device("cuda:0")
+    pos = torch.tensor(s.pos, dtype=torch.float64, device=dev)
+    cap = 12_000_000
+    trip = torch.zeros(3 * cap, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    sysg.debug_pairs(pos, trip, cap, cnt)
+    torch.cuda.synchronize()
+    k = int(cnt.item())
+    assert k <= cap
+    got = np.unique(trip[: 3 * k].cpu().numpy().reshape(-1, 3), axis=0)
+    assert got.shape[0] == k, "duplicate triples"
+    assert np.array_equal(got, want)
+    sysg.close()
+
+
+_GROUP_CASES = {}  # geometry -> (system, oracle forces, oracle neighbour set)
+
+
 @pytest.mark.parametrize("a", [0.12, 0.07])
 def test_small_smearing_radius(a):
     """Small smearing radii: the real-space table grows with beta^2 rc^2
@@ -326,6 +376,8 @@ def test_apply_tuning_rejects_bad_shapes():
                                                              pair_ctas_per_sm=4),
                 dict(pair_nelec=0, pair_threads=128, pair_ctas_per_sm=8),
                 dict(pair_nelec=0, pair_ctas_per_sm=4, pair_chunks=5),
+                dict(pair_group=4), dict(pair_group=2, pair_split=3),
+                dict(pair_group=2, pair_nelec=0, pair_threads=128, pair_ctas_per_sm=4),
                 dict(spread_cells=True)):  # FP64 system: no cell spread
         t = _shapes(False, 8)
         t.update(bad)
