@@ -439,7 +439,8 @@ int Engine::snapshot_cells(cudaStream_t st) {
 // last CTAs of the 27-cell kernel are short ones.  Cost of an item: its real
 // home beads x the real beads it stages (Gaussian core) + 4 x its charged
 // home beads x the charged and image beads it stages (electrostatics).
-void Engine::order_by_cost(std::vector<int2> &pw, int split, bool chunked, int group) const {
+void Engine::order_by_cost(std::vector<int2> &pw, int split, bool chunked, int group,
+                           int tail) const {
   if (snap_cnt.empty() || cell_factor != 1) return;
   std::vector<std::pair<long long, int>> key(pw.size());
   // estimated cost of home cell (cx, cy, cz) against its neighbour cells of
@@ -481,6 +482,36 @@ void Engine::order_by_cost(std::vector<int2> &pw, int split, bool chunked, int g
   std::vector<int2> out(pw.size());
   for (size_t w = 0; w < pw.size(); ++w) out[w] = pw[key[w].second];
   pw.swap(out);
+  if (group <= 1 || tail <= 0) return;
+  // The cheapest items of several home cells, from the end of the list,
+  // become single-cell items (code -1 - (cell * 9 + part)) until `tail`
+  // single-cell items end the list: the launch then ends on small items,
+  // which even out the CTAs' finishing times.
+  std::vector<std::pair<long long, int2>> singles;
+  size_t k = pw.size();
+  while (k > 0 && (int)singles.size() < tail) {
+    const int2 it = pw[--k];
+    const SysDesc &S = hsys[it.x];
+    if (group_of(it.x, group) <= 1) {  // a system of one home cell per item
+      const int cloc = it.y / split, part = it.y % split;
+      singles.push_back({cell_cost(S, cloc % S.nc[0], (cloc / S.nc[0]) % S.nc[1],
+                                   cloc / (S.nc[0] * S.nc[1]), part), it});
+      continue;
+    }
+    const int ngx = (S.nc[0] + group - 1) / group;
+    const int gi = it.y / 9, part = it.y % 9;
+    const int x0 = (gi % ngx) * group, cy = (gi / ngx) % S.nc[1], cz = gi / (ngx * S.nc[1]);
+    for (int x = x0; x < std::min(x0 + group, S.nc[0]); ++x) {
+      const int cloc = x + S.nc[0] * (cy + S.nc[1] * cz);
+      singles.push_back({cell_cost(S, x, cy, cz, part), make_int2(it.x, -1 - (cloc * 9 + part))});
+    }
+  }
+  std::stable_sort(singles.begin(), singles.end(),
+                   [](const std::pair<long long, int2> &a, const std::pair<long long, int2> &b) {
+                     return a.first > b.first;
+                   });
+  pw.resize(k);
+  for (const auto &sv : singles) pw.push_back(sv.second);
 }
 
 // Valid shapes of the 27-cell FP32 kernel: split 3 or 9 and either CTA
@@ -533,7 +564,10 @@ int Engine::set_pair_config(int split, int threads, int ctas_per_sm, int nelec, 
     hsys[s].pair_group = group_of(s, group);
   }
   std::vector<int2> pw = make_pair_work(split, chunked, group);
-  order_by_cost(pw, split, chunked, group);
+  // with items of several home cells: two single-cell items per resident CTA
+  // at the end of the list
+  order_by_cost(pw, split, chunked, group,
+                2 * (ctas_per_sm > 0 ? ctas_per_sm : kTailCtasPerSm) * n_sm);
   pair_split = split;
   pair_threads = threads;
   pair_nelec = nelec;

@@ -16,6 +16,8 @@ constexpr int kDefaultCellFactor = 1;
 // work items per home cell of the 27-cell pair kernel (3 or 9)
 constexpr int kDefaultPairSplit = 9;
 constexpr int kDefaultPairThreads = 128;
+constexpr int kTailCtasPerSm = 5;  // resident pair CTAs per SM assumed for the single-cell
+                                   // tail of one-CTA-per-item launches
 constexpr int kMaxPairChunks = 4;  // warp items per (home cell, part), at most
 // real-space table intervals in r^2: N = 18.25 beta^2 rc^2 keeps the cubic
 // interpolation error near 1e-7 of g(0) (the error scales as (beta^2 du)^4);
@@ -112,8 +114,9 @@ class Engine {
   // cell occupancy of the last cell sort (host copy) and the work-item
   // order it implies (heaviest first)
   int snapshot_cells(cudaStream_t st);
-  void order_by_cost(std::vector<int2> &pw, int split, bool chunked = false,
-                     int group = 1) const;
+  // (group > 1: then `tail` single-cell items at the end of the list)
+  void order_by_cost(std::vector<int2> &pw, int split, bool chunked = false, int group = 1,
+                     int tail = 0) const;
   std::vector<int> snap_cnt, snap_nimg, snap_nq;
   int set_fft_lpb(int axis, int lpb);
   bool plane_fits() const;

@@ -613,15 +613,17 @@ __device__ __forceinline__ PairSeg item_segment(const Pool &P, const SysDesc &S,
 // cells per row, the last one shorter; its segments are the nhome + 2
 // cells x0 - 1 .. x0 + nhome of the row (y + dy, z + dz), distinct because
 // nc_x >= G + 2, and each home cell pairs with the three of them around
-// it.  G = 1: code = cell * split + part.
+// it; code < 0: the single home cell -1 - code = cell * 9 + part (the
+// items that end the list).  G = 1: code = cell * split + part.
 struct ItemCells {
   int x0, y, z, nhome, part;
 };
 __device__ __forceinline__ ItemCells item_cells(const SysDesc &S, int code) {
   const int G = S.pair_group > 1 ? S.pair_group : 1;
   ItemCells c;
-  if (G == 1) {
+  if (G == 1 || code < 0) {
     const int split = S.pair_split;
+    if (code < 0) code = -1 - code;
     const int cloc = code / split;
     c.part = code % split;
     c.x0 = cloc % S.nc[0];
@@ -794,8 +796,9 @@ __device__ __forceinline__ void dev_pair_f32_item(const Pool &P, int2 wk, float4
                                                   unsigned char *stj = nullptr,
                                                   PairTab *stab = nullptr) {
   const SysDesc &S = P.sys[wk.x];
-  if (S.pair_group <= 1) {
-    dev_pair_f32_cell<VIR, DBG, MT>(P, wk.x, wk.y, sj, seg, s_total, stj, stab);
+  if (S.pair_group <= 1 || wk.y < 0) {  // one home cell (code -1 - code' ending a group list)
+    dev_pair_f32_cell<VIR, DBG, MT>(P, wk.x, wk.y < 0 ? -1 - wk.y : wk.y, sj, seg, s_total, stj,
+                                    stab);
     return;
   }
   const ItemCells c = item_cells(S, wk.y);

@@ -43,14 +43,19 @@ PAIR_VARIANTS = {"list": (1, 1), "cells": (1, 2), "fine": (2, 2)}
 
 
 def gpu_forces(s: synth.System, precision=0, virial=False, pos=None, cell_factor=0,
-               pair_path=0, tuning=None):
+               pair_path=0, tuning=None, snapshot=False):
+    """Forces, energies (and virial) of s through one System; snapshot: run
+    the autotuner first (uncached), whose cell snapshot orders the work
+    items by cost, before the given tuning is applied."""
     import torch
     g = lib()
     sysg = g.System(ctx(), g.params_from(s, precision, cell_factor, pair_path), s.q, s.bonds)
-    if tuning is not None:
-        sysg.apply_tuning(tuning)
     dev = torch.device("cuda:0")
     p = torch.tensor(s.pos if pos is None else pos, dtype=torch.float64, device=dev)
+    if snapshot:
+        sysg.autotune(p, flags=2)  # GCME_TUNE_NO_CACHE
+    if tuning is not None:
+        sysg.apply_tuning(tuning)
     F = torch.zeros(3 * s.n, dtype=torch.int64, device=dev)
     E = torch.zeros(g.NTERMS, dtype=torch.float64, device=dev)
     W = torch.zeros(9, dtype=torch.float64, device=dev) if virial else None

@@ -241,15 +241,17 @@ def test_pair_shapes_at_parity(split, threads, nelec, ctas):
 
 
 @pytest.mark.parametrize("geom", [synth.GEOM_BULK, synth.GEOM_SLAB_PC])
-@pytest.mark.parametrize("threads,nelec,ctas,group", [
-    (160, 2, 5, 2), (192, 3, 0, 3), (128, 1, 4, 3), (160, 1, 0, 2)])
-def test_pair_group_items_at_parity(geom, threads, nelec, ctas, group):
+@pytest.mark.parametrize("threads,nelec,ctas,group,snap", [
+    (160, 2, 5, 2, False), (192, 3, 0, 3, False), (128, 1, 4, 3, True), (160, 1, 0, 2, True)])
+def test_pair_group_items_at_parity(geom, threads, nelec, ctas, group, snap):
     """CTA work items of 2 or 3 consecutive home cells along x: 5 cells per
     axis (the last group of 3 is ragged: 3 + 2), the row's staged cells
     shared by the home cells, forces, energies and virial at parity with the
     oracle, and the neighbour set (debug triples, scalar path over the same
-    items) bit-exact.  The conducting slab adds images to the charged
-    candidates."""
+    items) bit-exact.  With a cell snapshot (snap) the items are ordered by
+    cost and the cheapest end the list as single home cells (negative
+    codes), two per resident CTA.  The conducting slab adds images to the
+    charged candidates."""
     import torch
     g = lib()
     if geom not in _GROUP_CASES:
@@ -264,16 +266,18 @@ def test_pair_group_items_at_parity(geom, threads, nelec, ctas, group):
     s, ref, want = _GROUP_CASES[geom]
     t = {"pair_split": 9, "pair_threads": threads, "pair_ctas_per_sm": ctas,
          "pair_nelec": nelec, "pair_group": group, "fft_lpb": [8, 8, 8], "fft_plane": True}
-    out = gpu_forces(s, 0, virial=geom == synth.GEOM_BULK, tuning=t)
+    out = gpu_forces(s, 0, virial=geom == synth.GEOM_BULK, tuning=t, snapshot=snap)
     _check(s, out, ref, FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
     if geom == synth.GEOM_BULK:
         assert np.max(np.abs(out["virial"] - ref["virial"])) <= 1e-5 * np.max(
             np.abs(ref["virial"]))
     sysg = g.System(ctx(), g.params_from(s), s.q, s.bonds)
     assert sysg.info().pair_path == g.GCME_PAIR_CELLS
-    sysg.apply_tuning(t)
     dev = torch.device("cuda:0")
     pos = torch.tensor(s.pos, dtype=torch.float64, device=dev)
+    if snap:
+        sysg.autotune(pos, flags=2)  # GCME_TUNE_NO_CACHE
+    sysg.apply_tuning(t)
     cap = 12_000_000
     trip = torch.zeros(3 * cap, dtype=torch.int32, device=dev)
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
