@@ -398,6 +398,12 @@ int gcme_debug_barrier_timeout(gcme_ctx *ctx, double timeout_s, gcme_stream_t st
  * CTAs with at most 28 warps per SM); its items are split by chunks of 32
  * home beads into pair_chunks items per (home cell, part): 1 to 4, or 0 for
  * the median real-bead count of the system's non-empty cells / 32.
+ * pair_nelec = -1 to -3 (CTA items, 128, 160 or 192 threads) lets every warp
+ * of a CTA take the item's tasks in turn: chunks of 32 home beads for the
+ * Gaussian core, then chunks of 32 charged home beads in -pair_nelec parts
+ * of the charged candidates (the sums of the static split with that many
+ * electrostatics warps, which a cell with many beads would leave partly
+ * idle).
  * spread_cells = 1 spreads the charges (FP32, 27-cell path without lists)
  * cell by cell through a brick of the grid in shared memory, the PME branch
  * then starting after the cell sort; 0 spreads each charge straight to the

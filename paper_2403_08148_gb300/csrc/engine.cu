@@ -524,7 +524,11 @@ static bool pair_shape_ok(int split, int threads, int ctas_per_sm, int nelec) {
   const bool ok_cta = nelec >= 1 && nelec <= 3 &&
                       (threads == 128 || threads == 160 || threads == 192) &&
                       ctas_per_sm >= 0 && ctas_per_sm <= 8 && threads / 32 - nelec >= 2;
-  return (split == 3 || split == 9) && (ok_warp || ok_cta);
+  // tasks taken dynamically, the charged candidates in -nelec parts
+  const bool ok_dyn = nelec <= -1 && nelec >= -3 &&
+                      (threads == 128 || threads == 160 || threads == 192) &&
+                      ctas_per_sm >= 0 && ctas_per_sm <= 8;
+  return (split == 3 || split == 9) && (ok_warp || ok_cta || ok_dyn);
 }
 
 // Home cells per CTA item: 1, or 2..3 with split 9 CTA items on the 27-cell
@@ -533,7 +537,7 @@ static bool pair_shape_ok(int split, int threads, int ctas_per_sm, int nelec) {
 // cell per item.
 bool Engine::pair_group_ok(int split, int nelec, int group) const {
   if (group == 1) return true;
-  return group >= 2 && group <= 3 && split == 9 && nelec >= 1 && cell_factor == 1;
+  return group >= 2 && group <= 3 && split == 9 && nelec != 0 && cell_factor == 1;
 }
 
 int Engine::group_of(int s, int group) const {
@@ -545,8 +549,10 @@ int Engine::set_pair_config(int split, int threads, int ctas_per_sm, int nelec, 
   if (!pair_shape_ok(split, threads, ctas_per_sm, nelec) || chunks < 0 ||
       chunks > kMaxPairChunks) {
     set_error("pair configuration must be split 3|9 and either 128|160|192 threads, 1..3 "
-              "electrostatics warps (at least 2 core warps), 0..8 CTAs per SM, or warp items "
-              "(0 electrostatics warps): 64|96|128 threads, 1..28 resident warps per SM");
+              "electrostatics warps (at least 2 core warps) or -1..-3 (tasks taken "
+              "dynamically, the charged candidates in that many parts), 0..8 CTAs per SM, "
+              "or warp items (0 electrostatics warps): 64|96|128 threads, 1..28 resident "
+              "warps per SM");
     return GCME_ERR_INVALID;
   }
   if (!pair_group_ok(split, nelec, group)) {
@@ -1267,7 +1273,8 @@ void Engine::enqueue_sort_pairs(const Pool &Q, cudaStream_t st, bool vir, bool d
   if (timed) cudaEventRecordWithFlags(phase_ev[2], st, cudaEventRecordExternal);
   if (use_list) launch_pair_list(Q, vir, dbg, st);
   launch_pair(Q, pair_work, n_pair_work, fp64, cell_factor, pair_threads, pair_ctas(),
-              pair_counter, vir, dbg, bonds_in_pair(dbg), st, pair_nelec == 0, pair_groups_on);
+              pair_counter, vir, dbg, bonds_in_pair(dbg), st, pair_nelec == 0, pair_groups_on,
+              pair_nelec < 0);
   if (timed) cudaEventRecordWithFlags(phase_ev[3], st, cudaEventRecordExternal);
 }
 
@@ -2202,7 +2209,7 @@ int gcme_batch_step(gcme_batch *b, int64_t nsteps, int32_t mode, gcme_stream_t s
   if (nsteps == 0) return GCME_OK;
   int lr = launch_persistent(b->eng.cell_only(Q), b->eng.pair_work, b->eng.n_pair_work, b->eng.cell_factor,
                              b->eng.plan, nsteps, b->eng.bar_words, 2.0, st,
-                             b->eng.pair_nelec == 0);
+                             b->eng.pair_nelec == 0, b->eng.pair_nelec < 0);
   if (lr != 0) {
     cudaError_t e = cudaGetLastError();
     set_error(std::string("persistent cooperative launch failed: ") + cudaGetErrorString(e));

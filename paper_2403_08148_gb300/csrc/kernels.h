@@ -59,10 +59,13 @@ void launch_sort(const Pool &P, cudaStream_t st);
 // bonds, one bond per thread in work items after the cell items.
 // warp_items: the FP32 one-species kernel with one warp per work item
 // (pair_warp.cuh; ctas > 0 required), else one CTA per work item; groups:
-// CTA items of several home cells (SysDesc::pair_group > 1 in some system).
+// CTA items of several home cells (SysDesc::pair_group > 1 in some system);
+// dyn: the warps of a CTA take each item's tasks dynamically
+// (SysDesc::pair_nelec < 0).
 void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell_factor,
                  int threads, int ctas, int *counter, bool vir, bool dbg, bool bonds,
-                 cudaStream_t st, bool warp_items = false, bool groups = false);
+                 cudaStream_t st, bool warp_items = false, bool groups = false,
+                 bool dyn = false);
 // Verlet neighbour list (nlist.cu): rebuild decision (clears the flag,
 // then sets it when a bead moved more than skin/2 since the last build or a
 // rebuild is pending), the gated build, the per-step refresh of the sorted
@@ -96,11 +99,12 @@ void launch_kick(const Pool &P, bool vel64, cudaStream_t st);
 // four words at bar_words hold the barrier state and the error word;
 // warp_items: the pair phase runs one warp per work item (pair_warp.cuh;
 // one-species 27-cell batches), as the per-phase launches do under the same
-// launch shapes (the same kernel path gives the same roundings)
+// launch shapes (the same kernel path gives the same roundings); dyn: the
+// CTA items' tasks taken dynamically (SysDesc::pair_nelec < 0)
 int launch_persistent(const Pool &P, const int2 *pair_work, int n_pair_work, int cell_factor,
                       const PmePlan &pl,
                       long long nsteps, unsigned int *bar_words, double timeout_s,
-                      cudaStream_t st, bool warp_items = false);
+                      cudaStream_t st, bool warp_items = false, bool dyn = false);
 int launch_barrier_probe(unsigned int *bar_words, double timeout_s, cudaStream_t st);
 void launch_force_to_f64(const long long *f, double *out, long long n3, cudaStream_t st);
 void launch_scale(double *x, long long n3, double s, cudaStream_t st);  // x *= s

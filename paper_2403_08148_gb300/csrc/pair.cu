@@ -23,14 +23,17 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_fine(Pool P, const int2 *
 // branch.  Items nwork .. nwork + nbi - 1 are harmonic bonds (one per thread),
 // taken last, by CTAs that would otherwise idle at the end of the launch.
 // One species without the debug dump runs the packed item (pair_core2), of
-// one home cell, or of several along x when GRP (SysDesc::pair_group).
-template <bool VIR, bool DBG, bool MT, bool GRP = false>
+// one home cell, or of several along x when GRP (SysDesc::pair_group); DYN
+// (SysDesc::pair_nelec < 0): the warps of a CTA take each item's tasks
+// dynamically (pk_compute).
+template <bool VIR, bool DBG, bool MT, bool GRP = false, bool DYN = false>
 __global__ void __launch_bounds__(192, 5) k_pair_f32(Pool P, const int2 *work, int nwork,
                                                      int nbi, int *counter) {
   __shared__ __align__(16) unsigned char raw[kPairSmemBytes];
   __shared__ PairSeg seg[kItemSegs];
   __shared__ int s_total[2];
   __shared__ int s_item;
+  __shared__ int s_task[DYN ? 3 : 1];
   __shared__ unsigned char stj[MT ? kPairCap : 1];
   __shared__ __align__(16) PairTab stab[MT ? kMaxTypes * kMaxTypes : 1];
   float4 *sj = reinterpret_cast<float4 *>(raw);
@@ -45,8 +48,8 @@ __global__ void __launch_bounds__(192, 5) k_pair_f32(Pool P, const int2 *work, i
         dev_bonds<VIR, true>(P, (long long)(w - nwork) * blockDim.x + threadIdx.x);
         continue;
       }
-      if (PK && GRP) dev_pair_f32_item_grp<VIR>(P, work, w, raw, seg, s_total);
-      else if (PK) dev_pair_f32_item_pk<VIR>(P, work, w, raw, seg, s_total);
+      if (PK && GRP) dev_pair_f32_item_grp<VIR, DYN>(P, work, w, raw, seg, s_total, s_task);
+      else if (PK) dev_pair_f32_item_pk<VIR, DYN>(P, work, w, raw, seg, s_total, s_task);
       else dev_pair_f32_item<VIR, DBG, MT>(P, work, w, sj, seg, s_total, stj, stab);
     }
     return;
@@ -64,8 +67,8 @@ __global__ void __launch_bounds__(192, 5) k_pair_f32(Pool P, const int2 *work, i
       __syncthreads();  // every thread has read s_item before the next fetch
       continue;
     }
-    if (PK && GRP) dev_pair_f32_item_grp<VIR>(P, work, w, raw, seg, s_total);
-    else if (PK) dev_pair_f32_item_pk<VIR>(P, work, w, raw, seg, s_total);
+    if (PK && GRP) dev_pair_f32_item_grp<VIR, DYN>(P, work, w, raw, seg, s_total, s_task);
+    else if (PK) dev_pair_f32_item_pk<VIR, DYN>(P, work, w, raw, seg, s_total, s_task);
     else dev_pair_f32_item<VIR, DBG, MT>(P, work, w, sj, seg, s_total, stj, stab);
   }
 }
@@ -231,7 +234,7 @@ __global__ void __launch_bounds__(128) k_pair_f64(Pool P) {
 
 void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell_factor,
                  int threads, int ctas, int *counter, bool vir, bool dbg, bool bonds,
-                 cudaStream_t st, bool warp_items, bool groups) {
+                 cudaStream_t st, bool warp_items, bool groups, bool dyn) {
   if (P.n_ext == 0) return;
   if (fp64) {
     int nb = (int)((P.n_ext + 127) / 128);
@@ -262,9 +265,9 @@ void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell
   const int nbi = (bonds && !dbg) ? (int)((P.n_bond + tb - 1) / tb) : 0;
   const int ntot = nwork + nbi;
   // ctas <= 0: one CTA per item; else a grid of ctas fetching items
-  const bool dyn = ctas > 0;
-  const int grid = dyn ? std::max(1, std::min(ntot, ctas)) : ntot;
-  if (!dyn) counter = nullptr;
+  const bool fetch = ctas > 0;
+  const int grid = fetch ? std::max(1, std::min(ntot, ctas)) : ntot;
+  if (!fetch) counter = nullptr;
   auto go = [&](auto kern) { launch_k(kern, grid, tb, 0, st, P, work, nwork, nbi, counter); };
   if (P.ptab) {  // several species
     if (dbg) go(k_pair_f32<false, true, true>);
@@ -273,6 +276,10 @@ void launch_pair(const Pool &P, const int2 *work, int nwork, bool fp64, int cell
     return;
   }
   if (dbg) go(k_pair_f32<false, true, false>);
+  else if (dyn && groups && vir) go(k_pair_f32<true, false, false, true, true>);
+  else if (dyn && groups) go(k_pair_f32<false, false, false, true, true>);
+  else if (dyn && vir) go(k_pair_f32<true, false, false, false, true>);
+  else if (dyn) go(k_pair_f32<false, false, false, false, true>);
   else if (groups && vir) go(k_pair_f32<true, false, false, true>);
   else if (groups) go(k_pair_f32<false, false, false, true>);
   else if (vir) go(k_pair_f32<true, false, false>);

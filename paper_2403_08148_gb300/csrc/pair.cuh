@@ -940,11 +940,20 @@ __device__ __forceinline__ void pk_home_box(const SysDesc &S, const ItemCells &c
 // GRP (items of several home cells): the self segment is seg[selfk] (each
 // home cell's own among the staged cells around it); else the one flagged
 // self.
-template <bool VIR, bool GRP = false>
+//
+// DYN (SysDesc::pair_nelec = -e): the item's work as tasks that every warp
+// takes from the shared-memory counter *s_task (zero before the item):
+// first the Gaussian-core chunks of 32 home beads (all real candidates),
+// then each chunk of 32 charged home beads in e parts of the charged
+// candidates.  A task computes what the role warp of the static split with
+// e electrostatics warps computes for it, so the sums are the same; the
+// warps stay busy when a cell needs more core chunks than there are core
+// warps, or more than one electrostatics chunk.
+template <bool VIR, bool GRP = false, bool DYN = false>
 __device__ __forceinline__ void pk_compute(const Pool &P, const SysDesc &S, int s, int hbeg,
                                            int hend, int himg, int hq, const PairSeg *seg,
                                            int nseg, int selfk, const unsigned char *smem,
-                                           int rt, int nrole) {
+                                           int rt, int nrole, int *s_task = nullptr) {
   const float *sx = reinterpret_cast<const float *>(smem);
   const float *sy = sx + kPkCap;
   const float *sz = sy + kPkCap;
@@ -957,19 +966,9 @@ __device__ __forceinline__ void pk_compute(const Pool &P, const SysDesc &S, int 
   const int rbeg = hbeg + himg;
   const float rc2 = S.rc2f, gcc = S.gc_c2f;
   const int nreal = hend - rbeg, nqr = hbeg + hq - rbeg;
-  const int ncore_chunks = (nreal + 32 * ncore - 1) / (32 * ncore);
-  const int nel_chunks = (nqr + 31) / 32;
-  const int nchunk = max(ncore_chunks, nel_chunks);
-  for (int c = 0; c < nchunk; ++c) {
-    int i;
-    bool valid;
-    if (core_role) {
-      i = rbeg + c * 32 * ncore + rt;
-      valid = i < hend;
-    } else {
-      i = rbeg + c * 32 + lane;
-      valid = i < hbeg + hq;
-    }
+  // one chunk of home beads of one role (crole: the Gaussian core, else the
+  // electrostatics, part ep of nep): this thread's home bead i
+  auto task = [&](bool crole, int i, bool valid, int ep, int nep) {
     const float4 xi = valid ? P.xyzq_s[i] : make_float4(1e30f, 1e30f, 1e30f, 0.0f);
     const bool busy = __any_sync(0xffffffffu, valid);
     PairAcc A;
@@ -977,7 +976,7 @@ __device__ __forceinline__ void pk_compute(const Pool &P, const SysDesc &S, int 
 #pragma unroll
     for (int k = 0; k < 6; ++k) A.wg[k] = A.we[k] = 0.0f;
     if (busy) {
-      if (core_role) {
+      if (crole) {
         PairAcc2 B;
         B.eg = B.gx = B.gy = B.gz = make_float2(0.0f, 0.0f);
 #pragma unroll
@@ -1013,7 +1012,7 @@ __device__ __forceinline__ void pk_compute(const Pool &P, const SysDesc &S, int 
           const PairSeg g = seg[k];
           // this warp's part of the (even-padded) candidates, on even bounds
           const int np2 = (g.bk + 1) >> 1;
-          const int lo = 2 * (np2 * ew / nelec), hi = 2 * (np2 * (ew + 1) / nelec);
+          const int lo = 2 * (np2 * ep / nep), hi = 2 * (np2 * (ep + 1) / nep);
           const float *X = qx + g.qoff;
           if (tab_nm1 < 0) {  // no table (very small smearing radius)
             if (GRP ? k == selfk : g.self != 0)
@@ -1040,6 +1039,34 @@ __device__ __forceinline__ void pk_compute(const Pool &P, const SysDesc &S, int 
       }
       pair_write<VIR>(P, S, s, valid, i, A);
     }
+  };
+  if (DYN) {
+    const int ne = min(max(-S.pair_nelec, 1), 3);  // electrostatics parts per chunk
+    const int nc = (nreal + 31) >> 5, ntask = nc + ne * ((nqr + 31) >> 5);
+    int t = lane == 0 ? atomicAdd(s_task, 1) : 0;
+    t = __shfl_sync(0xffffffffu, t, 0);
+    while (t < ntask) {
+      const bool core_role = t < nc;
+      const int c = core_role ? t : (t - nc) / ne;
+      const int i = rbeg + 32 * c + lane;
+      task(core_role, i, i < (core_role ? hend : hbeg + hq), core_role ? 0 : (t - nc) - c * ne,
+           ne);
+      t = lane == 0 ? atomicAdd(s_task, 1) : 0;
+      t = __shfl_sync(0xffffffffu, t, 0);
+    }
+    return;
+  }
+  const int ncore_chunks = (nreal + 32 * ncore - 1) / (32 * ncore);
+  const int nel_chunks = (nqr + 31) / 32;
+  const int nchunk = max(ncore_chunks, nel_chunks);
+  for (int c = 0; c < nchunk; ++c) {
+    if (core_role) {
+      const int i = rbeg + c * 32 * ncore + rt;
+      task(true, i, i < hend, ew, nelec);
+    } else {
+      const int i = rbeg + c * 32 + lane;
+      task(false, i, i < hbeg + hq, ew, nelec);
+    }
   }
 }
 
@@ -1047,10 +1074,12 @@ __device__ __forceinline__ void pk_compute(const Pool &P, const SysDesc &S, int 
 // (SysDesc::pair_group 1): items whose beads exceed the packed capacities
 // take the scalar path.  smem: kPairSmemBytes; seg[kItemSegs]; s_tot[2].
 // Ends with a barrier.
-template <bool VIR>
+//
+// DYN: the warps take the item's tasks from s_task[0] (pk_compute).
+template <bool VIR, bool DYN = false>
 __device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *work, int w,
                                                      unsigned char *smem, PairSeg *seg,
-                                                     int *s_tot) {
+                                                     int *s_tot, int *s_task = nullptr) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int s = work[w].x;
@@ -1059,6 +1088,7 @@ __device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *
     __syncthreads();
     return;
   }
+  if (DYN && tid == 0) s_task[0] = 0;
   const SysDesc &S = P.sys[s];
   const int split = S.pair_split;
   const int cloc = code / split, part = code % split;
@@ -1088,7 +1118,8 @@ __device__ __forceinline__ void dev_pair_f32_item_pk(const Pool &P, const int2 *
       pk_stage_segment(P, seg[k], hlo, hhi, S.cull2, smem, lane);
   }
   __syncthreads();
-  pk_compute<VIR>(P, S, s, hbeg, hend, himg, hq, seg, nseg, -1, smem, tid, blockDim.x);
+  pk_compute<VIR, false, DYN>(P, S, s, hbeg, hend, himg, hq, seg, nseg, -1, smem, tid,
+                              blockDim.x, s_task);
   __syncthreads();
 }
 
@@ -1107,10 +1138,12 @@ __device__ __noinline__ void pair_item_scalar(const Pool &P, int2 wk, float4 *sj
 // box of all its home cells (the home cells themselves staged whole in the
 // centre part), and evaluates each home cell over the three staged cells
 // around it.  seg[kItemSegs]: staged segments from 0, the home cells from 9.
-template <bool VIR>
+//
+// DYN: the warps take the tasks of home cell h from s_task[h] (pk_compute).
+template <bool VIR, bool DYN = false>
 __device__ __forceinline__ void dev_pair_f32_item_grp(const Pool &P, const int2 *work, int w,
                                                       unsigned char *smem, PairSeg *seg,
-                                                      int *s_tot) {
+                                                      int *s_tot, int *s_task = nullptr) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int s = work[w].x;
@@ -1119,6 +1152,7 @@ __device__ __forceinline__ void dev_pair_f32_item_grp(const Pool &P, const int2 
     __syncthreads();
     return;
   }
+  if (DYN && tid < 3) s_task[tid] = 0;
   const SysDesc &S = P.sys[s];
   const int split = S.pair_split;
   const ItemCells ic = item_cells(S, code);
@@ -1157,8 +1191,8 @@ __device__ __forceinline__ void dev_pair_f32_item_grp(const Pool &P, const int2 
   const int wseg = ic.nhome == 1 ? nseg : 3;
   for (int h = 0; h < ic.nhome; ++h) {
     const PairSeg &hc = seg[9 + h];
-    pk_compute<VIR, true>(P, S, s, hc.beg, hc.beg + hc.n, hc.a, hc.b, seg + h, wseg, selfk, smem,
-                          tid, blockDim.x);
+    pk_compute<VIR, true, DYN>(P, S, s, hc.beg, hc.beg + hc.n, hc.a, hc.b, seg + h, wseg, selfk,
+                               smem, tid, blockDim.x, DYN ? s_task + h : nullptr);
   }
   __syncthreads();
 }

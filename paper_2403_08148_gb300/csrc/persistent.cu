@@ -61,6 +61,7 @@ struct PersistArgs {
   int n_pair_work;
   int cell_factor;
   int warp_items;  // the pair work list holds warp items (pair_warp.cuh)
+  int dyn;         // CTA items' tasks taken dynamically (SysDesc::pair_nelec < 0)
   PmePlan plan;
   long long nsteps;
   Barrier bar;
@@ -107,7 +108,8 @@ __global__ void __launch_bounds__(128) k_persistent(Pool P, PersistArgs A) {
       int *st =
           reinterpret_cast<int *>(smem + kPairSmemBytes + sizeof(PairSeg) * kItemSegs);
       // several species: the table (16-byte aligned) and the staged species
-      const size_t toff = (kPairSmemBytes + sizeof(PairSeg) * kItemSegs + 16 + 15) / 16 * 16;
+      int *stask = st + 2;  // three task counters
+      const size_t toff = (kPairSmemBytes + sizeof(PairSeg) * kItemSegs + 32 + 15) / 16 * 16;
       PairTab *stab = reinterpret_cast<PairTab *>(smem + toff);
       unsigned char *stj = smem + toff + sizeof(PairTab) * kMaxTypes * kMaxTypes;
       if (A.warp_items) {  // one warp per work item (pair_warp.cuh)
@@ -120,6 +122,8 @@ __global__ void __launch_bounds__(128) k_persistent(Pool P, PersistArgs A) {
         for (int w = blockIdx.x; w < A.n_pair_work; w += gridDim.x) {
           if (P.ptab)
             dev_pair_f32_item<false, false, true>(P, A.pair_work, w, sj, seg, st, stj, stab);
+          else if (A.dyn)
+            dev_pair_f32_item_grp<false, true>(P, A.pair_work, w, smem, seg, st, stask);
           else
             dev_pair_f32_item_grp<false>(P, A.pair_work, w, smem, seg, st);
         }
@@ -168,7 +172,7 @@ __global__ void __launch_bounds__(128) k_persistent(Pool P, PersistArgs A) {
 #undef GRID_LOOP
 
 size_t persistent_smem(const PmePlan &pl, bool species, bool warp_items) {
-  size_t pair = kPairSmemBytes + sizeof(PairSeg) * kItemSegs + 16;
+  size_t pair = kPairSmemBytes + sizeof(PairSeg) * kItemSegs + 32;
   if (warp_items) pair = std::max(pair, 4 * sizeof(WarpSmem));  // 128 threads = 4 warps
   if (species)
     pair = (pair + 15) / 16 * 16 + sizeof(PairTab) * kMaxTypes * kMaxTypes + kPairCap;
@@ -183,7 +187,7 @@ size_t persistent_smem(const PmePlan &pl, bool species, bool warp_items) {
 
 int launch_persistent(const Pool &P, const int2 *pair_work, int n_pair_work, int cell_factor,
                       const PmePlan &pl, long long nsteps, unsigned int *bar_words, double timeout_s,
-                      cudaStream_t st, bool warp_items) {
+                      cudaStream_t st, bool warp_items, bool dyn) {
   warp_items = warp_items && !P.ptab && cell_factor == 1;
   const size_t smem = persistent_smem(pl, P.ptab != nullptr, warp_items);
   cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -198,6 +202,7 @@ int launch_persistent(const Pool &P, const int2 *pair_work, int n_pair_work, int
   A.n_pair_work = n_pair_work;
   A.cell_factor = cell_factor;
   A.warp_items = warp_items ? 1 : 0;
+  A.dyn = dyn && !P.ptab && cell_factor == 1 ? 1 : 0;
   A.plan = pl;
   A.nsteps = nsteps;
   A.bar.count = bar_words;

@@ -7,7 +7,9 @@
 //                or 2, 192 with 2 or 3; the other warps Gaussian core} x {one CTA
 //                per work item, or 3, 4, 5, 6 or 8 resident CTAs per SM fetching
 //                items dynamically so that the remaining slots host the
-//                concurrent PME branch}, and one warp per work item
+//                concurrent PME branch}, the same CTAs with every warp
+//                taking the items' tasks (core chunks, parts of charged
+//                chunks) dynamically, and one warp per work item
 //                (CTAs of 4 warps, 3-7 per SM, or of 2 warps, 8-14 per SM);
 //                then, for the fastest CTA-item shape of split 9, items of 2
 //                or 3 consecutive home cells along x;
@@ -233,13 +235,15 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
   };
   std::vector<Cand> cands;
   if (cell_factor == 1 && !use_list) {  // with lists the cell kernel only serves overflows
-    // threads, electrostatics warps (0: one warp per work item)
-    const int shapes[7][2] = {{128, 1}, {160, 1}, {160, 2}, {192, 2}, {192, 3}, {128, 0}, {64, 0}};
+    // threads, electrostatics warps (0: one warp per work item; negative:
+    // every warp takes tasks, the charged candidates in that many parts)
+    const int shapes[12][2] = {{128, 1},  {160, 1},  {160, 2},  {192, 2},  {192, 3},  {128, 0},
+                               {64, 0},   {128, -1}, {128, -2}, {160, -2}, {192, -2}, {192, -3}};
     for (int split : {3, 9})
       for (const auto &sh : shapes)
         for (int ctas : {0, 3, 4, 5, 6, 7, 8, 10, 12, 14}) {
           const int threads = sh[0], nelec = sh[1];
-          if (nelec > 0 && (ctas > 8 || ctas == 7 || ctas > 40 / (threads / 32)))
+          if (nelec != 0 && (ctas > 8 || ctas == 7 || ctas > 40 / (threads / 32)))
             continue;  // register-limited residency (64 regs)
           if (nelec == 0 && (split == 3 || ctas < 3 || ctas * (threads / 32) > 28 ||
                              (threads == 64 && ctas < 8)))
@@ -272,7 +276,7 @@ int Engine::autotune(const Pool &Q, cudaStream_t st, int flags, double *pair_ms,
     // items of 2 or 3 home cells along x for the fastest CTA-item shape of
     // split 9, around its resident CTAs per SM (larger items, fewer of them)
     for (const Cand &c : cands) {
-      if (c.split != 9 || c.nelec < 1) continue;
+      if (c.split != 9 || c.nelec == 0) continue;
       for (int group : {2, 3}) {
         bool any = false;  // some system takes the group
         for (int s = 0; s < nsys(); ++s) any = any || group_of(s, group) > 1;

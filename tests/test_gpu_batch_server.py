@@ -30,9 +30,11 @@ def _params(g, s, path=0, gamma=0.0, seed=0):
     return g.params_from(s, pair_path=path, gamma=gamma, kT=1.0, seed=seed)
 
 
-def _single_run(g, s, nsteps, path=0, gamma=0.0, seed=0):
+def _single_run(g, s, nsteps, path=0, gamma=0.0, seed=0, tuning=None):
     import torch
     sysg = g.System(ctx(), _params(g, s, path, gamma, seed), s.q, s.bonds)
+    if tuning is not None:
+        sysg.apply_tuning(tuning)
     pos = torch.tensor(s.pos, dtype=torch.float64, device="cuda:0")
     vel = torch.tensor(s.vel, dtype=torch.float32, device="cuda:0")
     E = torch.zeros(g.NTERMS, dtype=torch.float64, device="cuda:0")
@@ -61,6 +63,34 @@ def test_batch_matches_single_systems(mode, path, gamma):
     for k, s in enumerate(systems):
         lo, hi = b.offsets[k], b.offsets[k + 1]
         p1, v1, e1 = _single_run(g, s, 12, path, gamma, 100 + k)
+        assert np.array_equal(pos[lo:hi], p1), f"system {k} positions differ"
+        assert np.array_equal(vel[lo:hi], v1), f"system {k} velocities differ"
+        assert np.allclose(E[k], e1, rtol=1e-9, atol=1e-9)
+
+
+ITEM_TASKS = {"pair_split": 9, "pair_threads": 160, "pair_ctas_per_sm": 5, "pair_nelec": -2,
+              "fft_lpb": [8, 8, 8], "fft_plane": True}
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_matches_single_systems_item_tasks(mode):
+    """Every warp taking the items' tasks (pair_nelec -2): a thread's sums
+    depend only on its system's items and the two parts of the charged
+    candidates, not on the warps of the CTA, so each trajectory is the same
+    bit for bit alone and in the batch, per-phase graphs or the persistent
+    launch (128-thread CTAs there, 160 here)."""
+    g = lib()
+    systems = _mixed_systems()
+    b = g.Batch(ctx(), [_params(g, s, 2, 0.0, 100 + k) for k, s in enumerate(systems)],
+                [s.q for s in systems], [s.bonds for s in systems])
+    b.apply_tuning(ITEM_TASKS)
+    b.set_state(np.concatenate([s.pos for s in systems]),
+                np.concatenate([s.vel for s in systems]).astype(np.float32))
+    b.step(12, mode)
+    pos, vel, E = b.get_state()
+    for k, s in enumerate(systems):
+        lo, hi = b.offsets[k], b.offsets[k + 1]
+        p1, v1, e1 = _single_run(g, s, 12, 2, 0.0, 100 + k, tuning=ITEM_TASKS)
         assert np.array_equal(pos[lo:hi], p1), f"system {k} positions differ"
         assert np.array_equal(vel[lo:hi], v1), f"system {k} velocities differ"
         assert np.allclose(E[k], e1, rtol=1e-9, atol=1e-9)

@@ -227,12 +227,13 @@ def test_fft_paths(name, prec):
 @pytest.mark.parametrize("split,threads,nelec,ctas", [
     (9, 128, 1, 0), (9, 160, 1, 0), (9, 160, 2, 0), (9, 192, 2, 0), (9, 192, 3, 0),
     (3, 192, 3, 0), (9, 192, 3, 5), (3, 160, 2, 8),
-    (9, 128, 0, 7), (3, 128, 0, 3), (9, 64, 0, 12), (9, 96, 0, 9)])
+    (9, 128, 0, 7), (3, 128, 0, 3), (9, 64, 0, 12), (9, 96, 0, 9),
+    (9, 160, -2, 5), (9, 128, -1, 6), (9, 192, -3, 4), (3, 192, -2, 0)])
 def test_pair_shapes_at_parity(split, threads, nelec, ctas):
     """Every launch shape of the 27-cell kernel (work items per cell, block
-    size, electrostatics warps splitting each cell's charged candidates,
-    static or dynamic CTAs, or one warp per work item) gives the oracle's
-    forces and energies."""
+    size, electrostatics warps splitting each cell's charged candidates or
+    every warp taking the item's tasks, static or dynamic CTAs, or one warp
+    per work item) gives the oracle's forces and energies."""
     s = CASES["poly_bonds"]
     t = {"pair_split": split, "pair_threads": threads, "pair_ctas_per_sm": ctas,
          "pair_nelec": nelec, "fft_lpb": [8, 8, 8], "fft_plane": True}
@@ -242,7 +243,8 @@ def test_pair_shapes_at_parity(split, threads, nelec, ctas):
 
 @pytest.mark.parametrize("geom", [synth.GEOM_BULK, synth.GEOM_SLAB_PC])
 @pytest.mark.parametrize("threads,nelec,ctas,group,snap", [
-    (160, 2, 5, 2, False), (192, 3, 0, 3, False), (128, 1, 4, 3, True), (160, 1, 0, 2, True)])
+    (160, 2, 5, 2, False), (192, 3, 0, 3, False), (128, 1, 4, 3, True), (160, 1, 0, 2, True),
+    (160, -2, 5, 2, True), (128, -1, 0, 3, False)])
 def test_pair_group_items_at_parity(geom, threads, nelec, ctas, group, snap):
     """CTA work items of 2 or 3 consecutive home cells along x: 5 cells per
     axis (the last group of 3 is ragged: 3 + 2), the row's staged cells
@@ -368,6 +370,35 @@ def test_cell_spread_same_grid_as_direct_spread(name):
     _check(s, b, oracle.energy_forces(s), FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
 
 
+@pytest.mark.parametrize("name", ["poly_bonds", "slab_nm", "slab_pc", "tiny_box_n120",
+                                  "neutral_only", "dense_one_cell"])
+def test_item_tasks_same_sums_as_role_warps(name):
+    """Every warp taking the item's tasks (pair_nelec = -e: chunks of 32
+    home beads for the core, chunks of 32 charged home beads in e parts)
+    gives each thread the partial sums of the static role split with e
+    electrostatics warps, so forces, energies and virial are the same bit for
+    bit, whatever the CTA's warp count; both item splits, items of two home
+    cells, and the dense one-cell box over the staged capacity (both take the
+    scalar path there); at parity with the oracle."""
+    if name == "dense_one_cell":
+        s = synth.make_bulk(500, seed_index=69, charged_frac=0.6, K=(8, 8, 8))
+    else:
+        s = CASES[name]
+    vir = s.geometry == synth.GEOM_BULK
+    ref = oracle.energy_forces(s)
+    base = {"fft_lpb": [8, 8, 8], "fft_plane": True}
+    for split, group in ((9, 1), (3, 1), (9, 2)):
+        for e, th_static, th_dyn, ctas in ((2, 160, 128, 5), (1, 128, 192, 0), (3, 192, 160, 4)):
+            t = dict(base, pair_split=split, pair_group=group, pair_ctas_per_sm=ctas)
+            a = gpu_forces(s, 0, virial=vir, tuning=dict(t, pair_threads=th_static, pair_nelec=e))
+            b = gpu_forces(s, 0, virial=vir, tuning=dict(t, pair_threads=th_dyn, pair_nelec=-e))
+            assert np.array_equal(a["fixed"], b["fixed"]), (split, group, e)
+            assert a["energy"] == b["energy"]
+            if vir:
+                assert np.array_equal(a["virial"], b["virial"])
+        _check(s, b, ref, FORCE_RTOL_FP32, ENERGY_RTOL_FP32, 1e-6)
+
+
 def test_apply_tuning_rejects_bad_shapes():
     g = lib()
     s = synth.make_bulk(300, seed_index=58, charged_frac=0.2, K=(96, 96, 8))
@@ -382,6 +413,8 @@ def test_apply_tuning_rejects_bad_shapes():
                 dict(pair_nelec=0, pair_ctas_per_sm=4, pair_chunks=5),
                 dict(pair_group=4), dict(pair_group=2, pair_split=3),
                 dict(pair_group=2, pair_nelec=0, pair_threads=128, pair_ctas_per_sm=4),
+                dict(pair_nelec=-4), dict(pair_nelec=-1, pair_threads=64),
+                dict(pair_nelec=-2, pair_ctas_per_sm=9),
                 dict(spread_cells=True)):  # FP64 system: no cell spread
         t = _shapes(False, 8)
         t.update(bad)
@@ -559,7 +592,7 @@ def test_autotune_keeps_parity_and_caches(tmp_path, monkeypatch):
     pos = torch.tensor(s.pos, dtype=torch.float64, device="cuda:0")
     t1 = sysg.autotune(pos)
     assert t1["pair_split"] in (3, 9) and t1["pair_threads"] in (64, 128, 160, 192)
-    assert t1["pair_nelec"] in (0, 1, 2, 3)
+    assert t1["pair_nelec"] in (-3, -2, -1, 0, 1, 2, 3)
     lst = g.System(ctx(), g.params_from(s, pair_path=g.GCME_PAIR_LIST), s.q, s.bonds)
     t3 = lst.autotune(pos)  # the list path has a cache entry of its own
     assert not t3["from_cache"]
