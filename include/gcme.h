@@ -294,6 +294,26 @@ int gcme_step_continue(gcme_sys *sys, double *d_pos, void *d_vel, int64_t nsteps
 int gcme_step_f64(gcme_sys *sys, double *d_pos, double *d_vel, int64_t nsteps,
                   double *d_energy, gcme_stream_t stream);
 
+#define GCME_STEP_CONTINUE 1 /* gcme_step_host: reuse the last call's forces */
+
+/* nsteps of velocity Verlet, as gcme_step, on a state held
+ * on the host: h_pos[n*3] (FP64, not wrapped) and h_vel[n*3] (FP32) are
+ * copied to device copies the system keeps, stepped, and copied back in
+ * place, with the energies of the final state to h_energy[GCME_NTERMS] (may
+ * be NULL).  The buffers must be page-locked (cudaHostAlloc, or
+ * cudaHostRegister'ed); others return INVALID.  The copies and the steps are
+ * enqueued on `stream` (for nsteps = 1 as one captured graph per set of host
+ * buffers) and the call returns at once: synchronise the stream before
+ * reading or changing the host buffers.  Without flags the forces at the
+ * copied-in positions are evaluated first (as gcme_step); with
+ * GCME_STEP_CONTINUE they are the forces the previous call on the same host
+ * buffers left, valid when the caller has not changed the state since (as
+ * gcme_step_continue; other buffers return INVALID).  The first call on a
+ * system allocates its device copies (OOM on failure); FP64 systems return
+ * INVALID.  Results are those of gcme_step on the same state bit for bit. */
+int gcme_step_host(gcme_sys *sys, double *h_pos, float *h_vel, int64_t nsteps, double *h_energy,
+                   int32_t flags, gcme_stream_t stream);
+
 /* Phase timing on (on != 0) or off (the default).  With it on, later step
  * graphs carry CUDA event nodes between the phases, which lengthen a step
  * (by ~20 us per step on a GB300 at N = 32,000): for profiling only.  The

@@ -18,6 +18,7 @@ from . import builder as _build
 GCME_BULK, GCME_SLAB_NONMETAL, GCME_SLAB_IMAGE = 0, 1, 2
 GCME_FP32, GCME_FP64 = 0, 1
 GCME_PAIR_AUTO, GCME_PAIR_LIST, GCME_PAIR_CELLS = 0, 1, 2
+GCME_STEP_CONTINUE = 1
 MAX_TYPES = 8
 NTERMS = 10
 TERM_NAMES = ("gc", "real", "recip", "corr", "self", "slab", "wall", "bond",
@@ -142,6 +143,7 @@ _SIGS = {
     "gcme_step": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
     "gcme_step_f64": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
     "gcme_step_continue": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
+    "gcme_step_host": ([_vp, _vp, _vp, _i64, _vp, ctypes.c_int32, _vp], ctypes.c_int),
     "gcme_step_phase_ms": ([_vp, _vp, _i32, _vp], ctypes.c_int),
     "gcme_batch_phase_ms": ([_vp, _vp, _i32, _vp], ctypes.c_int),
     "gcme_step_phase_timing": ([_vp, _i32], ctypes.c_int),
@@ -387,6 +389,15 @@ class System:
     def apply_tuning(self, tuning: dict):
         """Apply launch shapes (the keys of autotune()'s result) without timing."""
         _check(load().gcme_apply_tuning(self.h, ctypes.byref(Tuning.from_dict(tuning))))
+
+    def step_host(self, h_pos, h_vel, nsteps: int, h_energy=None, cont: bool = False,
+                  stream=None):
+        """gcme_step_host: the state in page-locked host memory (pinned CPU
+        tensors), copied in, stepped and copied back on `stream`; synchronise
+        before reading it.  cont: reuse the previous call's forces."""
+        _check(load().gcme_step_host(self.h, _ptr(h_pos), _ptr(h_vel), int(nsteps),
+                                     _ptr(h_energy), GCME_STEP_CONTINUE if cont else 0,
+                                     _stream(stream)))
 
     def step_continue(self, d_pos, d_vel, nsteps: int, d_energy=None, stream=None):
         _check(load().gcme_step_continue(self.h, _ptr(d_pos), _ptr(d_vel), int(nsteps),

@@ -1355,6 +1355,46 @@ int Engine::step_graph(const Pool &Q, cudaGraphExec_t *out) {
   return GCME_OK;
 }
 
+int Engine::host_graph(const Pool &Q, const double *h_pos, const float *h_vel,
+                       double *h_energy, bool cont, int part, cudaGraphExec_t *out) {
+  auto key = std::make_tuple((void *)h_pos, (void *)h_vel, (void *)h_energy,
+                             16 + 4 * part + 2 * (int)cont + (int)phase_timing);
+  if (part == 3) last_step_timed = phase_timing;
+  auto it = graphs_.find(key);
+  if (it != graphs_.end()) {
+    *out = it->second;
+    return GCME_OK;
+  }
+  if (phase_timing && !phase_ev[0])
+    for (int k = 0; k < kNPhaseEv; ++k) GCME_CK(cudaEventCreate(&phase_ev[k]));
+  const size_t n3 = 3 * (size_t)n_real;
+  cudaStream_t cs = capture_stream;
+  cudaGraph_t g;
+  GCME_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  // the SMs move the state over the CPU-GPU link (one kernel each way, no
+  // copy-engine nodes between the step's kernels)
+  if (part & 1) {
+    launch_state_copy(h_pos, h_vel, Q.pos, reinterpret_cast<float *>(Q.vel), (long long)n3,
+                      nullptr, nullptr, cs);
+    if (!cont) {
+      enqueue_forces(Q, cs, false, false);
+      launch_finalize(Q, false, cs);
+    }
+  }
+  if (part == 3) enqueue_step(Q, cs);
+  if (part & 2)
+    launch_state_copy(Q.pos, reinterpret_cast<const float *>(Q.vel), const_cast<double *>(h_pos),
+                      const_cast<float *>(h_vel), (long long)n3, h_energy ? Q.energy : nullptr,
+                      h_energy, cs);
+  GCME_CK(cudaStreamEndCapture(cs, &g));
+  cudaGraphExec_t ge;
+  GCME_CK(cudaGraphInstantiate(&ge, g, 0));
+  graph_objs_.push_back(g);
+  graphs_[key] = ge;
+  *out = ge;
+  return GCME_OK;
+}
+
 int Engine::forces_graph(const Pool &Q, cudaGraphExec_t *out) {
   auto key = std::make_tuple((void *)Q.pos, (void *)Q.vel, (void *)Q.force, 2);
   auto it = graphs_.find(key);
@@ -1388,12 +1428,20 @@ struct gcme_sys {
   gcme_params p;
   SysSpec spec;               // as created (the box follows set_box)
   double *saved_pos = nullptr;  // barostat: positions before a volume move
+  // device copies of a host-held state (gcme_step_host), allocated by its
+  // first call
+  double *hd_pos = nullptr;
+  float *hd_vel = nullptr;
   ~gcme_sys() {
     if (saved_pos) cudaFree(saved_pos);
+    if (hd_pos) cudaFree(hd_pos);
+    if (hd_vel) cudaFree(hd_vel);
   }
   // buffers of the last gcme_step call: the internal force array then holds
   // F at their current positions, so a continuation can skip that evaluation
   const void *last_pos = nullptr, *last_vel = nullptr;
+  // host buffers of the last gcme_step_host call (the same for its continuation)
+  const void *last_hpos = nullptr, *last_hvel = nullptr;
 };
 
 struct gcme_batch {
@@ -1802,6 +1850,69 @@ static int continue_steps(gcme_sys *sys, double *d_pos, void *d_vel, int64_t nst
     GCME_TRY_CK(cudaMemcpyAsync(d_energy, Q.energy, sizeof(double) * GCME_NTERMS,
                                 cudaMemcpyDeviceToDevice, st));
   return check_launch("gcme_step_continue");
+}
+
+static bool is_pinned(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+int gcme_step_host(gcme_sys *sys, double *h_pos, float *h_vel, int64_t nsteps, double *h_energy,
+                   int32_t flags, gcme_stream_t stream) {
+  if (!sys || !h_pos || !h_vel || nsteps < 0 || (flags & ~GCME_STEP_CONTINUE)) {
+    set_error("invalid argument to gcme_step_host");
+    return GCME_ERR_INVALID;
+  }
+  if (sys->eng.fp64) {
+    set_error("gcme_step_host steps FP32 systems");
+    return GCME_ERR_INVALID;
+  }
+  GCME_TRY_CK(cudaSetDevice(sys->eng.device));
+  if (!is_pinned(h_pos) || !is_pinned(h_vel) || (h_energy && !is_pinned(h_energy))) {
+    set_error("gcme_step_host: host buffers must be page-locked (cudaHostAlloc or "
+              "cudaHostRegister)");
+    return GCME_ERR_INVALID;
+  }
+  const bool cont = (flags & GCME_STEP_CONTINUE) != 0;
+  if (cont && (h_pos != sys->last_hpos || h_vel != sys->last_hvel)) {
+    set_error("gcme_step_host: no preceding call on these host buffers to continue");
+    return GCME_ERR_INVALID;
+  }
+  const size_t n3 = 3 * (size_t)sys->eng.hsys[0].n;
+  if (!sys->hd_pos) {
+    if (cudaMalloc(&sys->hd_pos, sizeof(double) * n3) != cudaSuccess ||
+        cudaMalloc(&sys->hd_vel, sizeof(float) * n3) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("gcme_step_host: device state allocation failed");
+      return GCME_ERR_OOM;
+    }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  Pool Q = sys->eng.P;
+  Q.pos = sys->hd_pos;
+  Q.vel = sys->hd_vel;
+  Engine &E = sys->eng;
+  cudaGraphExec_t g;
+  int rc;
+  if (nsteps == 1) {
+    if ((rc = E.host_graph(Q, h_pos, h_vel, h_energy, cont, 3, &g))) return rc;
+    GCME_TRY_CK(cudaGraphLaunch(g, st));
+  } else {
+    cudaGraphExec_t sg;
+    if ((rc = E.host_graph(Q, h_pos, h_vel, h_energy, cont, 1, &g))) return rc;
+    if ((rc = E.step_graph(Q, &sg))) return rc;
+    GCME_TRY_CK(cudaGraphLaunch(g, st));
+    for (int64_t k = 0; k < nsteps; ++k) GCME_TRY_CK(cudaGraphLaunch(sg, st));
+    if ((rc = E.host_graph(Q, h_pos, h_vel, h_energy, cont, 2, &g))) return rc;
+    GCME_TRY_CK(cudaGraphLaunch(g, st));
+  }
+  sys->last_hpos = h_pos;
+  sys->last_hvel = h_vel;
+  return check_launch("gcme_step_host");
 }
 
 int gcme_step_continue(gcme_sys *sys, double *d_pos, void *d_vel, int64_t nsteps,

@@ -94,6 +94,12 @@ class Engine {
   // graph of one step for the given state pointers (cached)
   int step_graph(const Pool &P, cudaGraphExec_t *out);
   int forces_graph(const Pool &P, cudaGraphExec_t *out);
+  // state on the host (page-locked h_pos[3n], h_vel[3n], h_energy or NULL),
+  // P.pos / P.vel the device copies: part 1 copies the state in (and, unless
+  // cont, evaluates the starting forces), part 2 copies the state and the
+  // energies out, part 3 is both around one step (cached per host buffers)
+  int host_graph(const Pool &P, const double *h_pos, const float *h_vel, double *h_energy,
+                 bool cont, int part, cudaGraphExec_t *out);
 
   int nsys() const { return (int)hsys.size(); }
   // (system, code) pair work items: code = cell * split + part, times

@@ -107,6 +107,10 @@ int launch_persistent(const Pool &P, const int2 *pair_work, int n_pair_work, int
                       cudaStream_t st, bool warp_items = false, bool dyn = false);
 int launch_barrier_probe(unsigned int *bar_words, double timeout_s, cudaStream_t st);
 void launch_force_to_f64(const long long *f, double *out, long long n3, cudaStream_t st);
+// copy of the state (and the energies when se is set) by the SMs, either
+// side in page-locked host memory (read or written directly by the GPU)
+void launch_state_copy(const double *sp, const float *sv, double *dp, float *dv, long long n3,
+                       const double *se, double *de, cudaStream_t st);
 void launch_scale(double *x, long long n3, double s, cudaStream_t st);  // x *= s
 
 }  // namespace gcme

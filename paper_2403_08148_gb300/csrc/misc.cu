@@ -1,5 +1,8 @@
 // misc.cu -- K9-K12 per-phase kernels (bodies in misc.cuh).
 #include "kernels.h"
+
+#include <algorithm>
+#include <cstdint>
 #include "misc.cuh"
 
 namespace gcme {
@@ -84,6 +87,39 @@ __global__ void k_force_to_f64(const long long *f, double *out, long long n3) {
 
 void launch_force_to_f64(const long long *f, double *out, long long n3, cudaStream_t st) {
   if (n3 > 0) k_force_to_f64<<<(int)((n3 + 255) / 256), 256, 0, st>>>(f, out, n3);
+}
+
+// The state (positions FP64, velocities FP32, n3 values each) and the
+// energies copied by the SMs, one side of them page-locked host memory
+// (gcme_step_host; the GPU reads and writes it directly, over the coherent
+// CPU-GPU link of a Grace system): 16-byte vectors where both addresses
+// allow, else single values.
+__global__ void k_state_copy(const double *__restrict__ sp, const float *__restrict__ sv,
+                             double *__restrict__ dp, float *__restrict__ dv, long long n3,
+                             const double *__restrict__ se, double *__restrict__ de) {
+  pdl_wait();
+  const long long g0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long gs = (long long)gridDim.x * blockDim.x;
+  const bool vp = ((reinterpret_cast<uintptr_t>(sp) | reinterpret_cast<uintptr_t>(dp)) & 15) == 0;
+  const bool vv = ((reinterpret_cast<uintptr_t>(sv) | reinterpret_cast<uintptr_t>(dv)) & 15) == 0;
+  const long long np2 = vp ? n3 / 2 : 0, nv4 = vv ? n3 / 4 : 0;
+  for (long long k = g0; k < np2; k += gs)
+    reinterpret_cast<double2 *>(dp)[k] = reinterpret_cast<const double2 *>(sp)[k];
+  for (long long k = 2 * np2 + g0; k < n3; k += gs) dp[k] = sp[k];
+  for (long long k = g0; k < nv4; k += gs)
+    reinterpret_cast<float4 *>(dv)[k] = reinterpret_cast<const float4 *>(sv)[k];
+  for (long long k = 4 * nv4 + g0; k < n3; k += gs) dv[k] = sv[k];
+  if (se && g0 < GCME_NTERMS) de[g0] = se[g0];
+}
+
+void launch_state_copy(const double *sp, const float *sv, double *dp, float *dv, long long n3,
+                       const double *se, double *de, cudaStream_t st) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long long want = (n3 / 2 + 255) / 256;  // about one 16-byte vector per thread
+  const int nb = (int)std::max(1LL, std::min(want, 4LL * nsm));
+  launch_k(k_state_copy, nb, 256, 0, st, sp, sv, dp, dv, n3, se, de);
 }
 
 // isotropic scaling of positions with the box (barostat volume moves)

@@ -164,6 +164,8 @@ def test_null_handles_are_rejected(g):
     assert lib.gcme_batch_phase_timing(None, 0) == -1
     assert lib.gcme_step_phase_ms(None, None, 0, None) == -1
     assert lib.gcme_batch_phase_ms(None, None, 0, None) == -1
+    assert lib.gcme_step_host(None, None, None, 1, None, 0, None) == -1
+    assert b"gcme_step_host" in lib.gcme_last_error()
 
 
 def test_noalloc_size_query_is_host_only(g):

@@ -543,6 +543,42 @@ def test_step_fp32_polyelectrolyte():
     assert abs(tot_g - tot_o) / abs(tot_o) < 1e-5
 
 
+def test_step_host_same_as_device_step():
+    """The state held on the host (gcme_step_host: page-locked buffers
+    copied in, stepped and copied back in one captured graph) follows the
+    device-buffer path bit for bit: a first call with the force evaluation,
+    then continued calls of one step and of several steps, against gcme_step
+    and gcme_step_continue on device buffers; unpinned buffers and a
+    continuation on other buffers are rejected."""
+    import torch
+    g = lib()
+    s = CASES["poly_bonds"]
+    dev = torch.device("cuda:0")
+    a = g.System(ctx(), g.params_from(s), s.q, s.bonds)
+    b = g.System(ctx(), g.params_from(s), s.q, s.bonds)
+    pos = torch.tensor(s.pos, dtype=torch.float64, device=dev)
+    vel = torch.tensor(s.vel, dtype=torch.float32, device=dev)
+    E = torch.zeros(g.NTERMS, dtype=torch.float64, device=dev)
+    hpos = torch.tensor(s.pos, dtype=torch.float64).pin_memory()
+    hvel = torch.tensor(s.vel, dtype=torch.float32).pin_memory()
+    hE = torch.zeros(g.NTERMS, dtype=torch.float64).pin_memory()
+    a.step(pos, vel, 3, E)
+    b.step_host(hpos, hvel, 3, hE)
+    for k in range(4):
+        a.step_continue(pos, vel, 1 if k % 2 == 0 else 2, E)
+        b.step_host(hpos, hvel, 1 if k % 2 == 0 else 2, hE, cont=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(hpos.numpy(), pos.cpu().numpy())
+    assert np.array_equal(hvel.numpy(), vel.cpu().numpy())
+    assert np.array_equal(hE.numpy(), E.cpu().numpy())
+    with pytest.raises(g.GcmeError):
+        b.step_host(np.zeros_like(s.pos), np.zeros(s.vel.shape, np.float32), 1)
+    with pytest.raises(g.GcmeError):
+        b.step_host(hpos.clone().pin_memory(), hvel, 1, cont=True)
+    a.close()
+    b.close()
+
+
 def test_phase_timing_is_opt_in_and_changes_no_result():
     """Event nodes between the phases enter the step graph only with phase
     timing on; the trajectory is bit-identical with and without them."""
