@@ -235,6 +235,13 @@ struct Pool {
   const int *gate;     // if set, the cell-sort kernels run only when *gate != 0
   double half_skin2;   // (skin / 2)^2: displacement that forces a rebuild
   unsigned long long *step_ctr;  // [nsys] steps taken by each system (Langevin counter)
+  // Per-system step limits (the server's pooled engines; null elsewhere): a
+  // system whose step counter has reached step_stop[s] is held (the half
+  // kick and drift clears its forces but moves nothing, the second half kick
+  // leaves its velocities and its counter), while the others step on;
+  // held[s] carries the decision of the step's first kernel to its last.
+  const unsigned long long *step_stop;
+  unsigned char *held;
   // several species: species of each ext bead (images: their source's),
   // the same in sorted order, and the pooled per-system pair tables
   unsigned char *type_u;

@@ -1048,6 +1048,8 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   cv.add(&pair_work, pair_cap);
   cv.add(&bar_words, 4);
   cv.add(&P.step_ctr, ns);
+  cv.add(&step_stop_buf, ns);
+  cv.add(&P.held, ns);
   cv.add(&pair_counter, 1);
   int2 *fw[3];
   for (int a = 0; a < 3; ++a) cv.add(&fw[a], fft_cap[a]);
@@ -1196,6 +1198,8 @@ int Engine::build(int dev, const std::vector<SysSpec> &specs, bool own_state) {
   if (ngrid > 0) GCME_CK(cudaMemset(P.qgrid, 0, sizeof(unsigned long long) * ngrid));
   GCME_CK(cudaMemset(P.wrap_n, 0, sizeof(int) * 3 * ne));
   GCME_CK(cudaMemset(P.step_ctr, 0, sizeof(unsigned long long) * ns));
+  GCME_CK(cudaMemset(P.held, 0, ns));
+  P.step_stop = nullptr;  // no step limits unless enable_step_limits()
   GCME_CK(cudaMemset(pair_counter, 0, sizeof(int)));  // each pair launch leaves it zero
   if (use_list) {
     // reference positions ~1e306: the first check requests a build
@@ -1353,6 +1357,11 @@ int Engine::step_graph(const Pool &Q, cudaGraphExec_t *out) {
   graphs_[key] = ge;
   *out = ge;
   return GCME_OK;
+}
+
+void Engine::enable_step_limits() {
+  P.step_stop = step_stop_buf;
+  clear_graphs();  // the kernels take the pool by value
 }
 
 int Engine::host_graph(const Pool &Q, const double *h_pos, const float *h_vel,

@@ -153,6 +153,11 @@ class Engine {
   bool phase_timing = false;
   bool last_step_timed = false;
   unsigned int *bar_words = nullptr;  // persistent-launch barrier state (4 words)
+  // per-system step limits (Pool::step_stop; the server's engines): a device
+  // array of nsys counters the caller fills; enable_step_limits() makes the
+  // step kernels hold each system at its limit
+  unsigned long long *step_stop_buf = nullptr;
+  void enable_step_limits();
   bool fp64 = false;
   int cell_factor = 1;  // 1: 27-cell stencil; 2: fine cells with culling
   bool use_list = false;  // FP32 pair terms over Verlet neighbour lists

@@ -277,7 +277,12 @@ __device__ __forceinline__ void dev_kick_drift(const Pool &P, long long g) {
     return ONE ? reinterpret_cast<unsigned long long *>(P.force + (long long)a * P.n_real + g)
                : force_ptr(P, S, i, a);
   };
-  if (frozen_bead(P, S, i)) {
+  bool held = false;  // a system that has taken its steps (step limits)
+  if (P.step_stop) {
+    held = P.step_ctr[s] >= P.step_stop[s];
+    if (i == 0) P.held[s] = held ? 1 : 0;
+  }
+  if (held || frozen_bead(P, S, i)) {
     for (int a = 0; a < 3; ++a) *fptr(a) = 0ull;
     return;
   }
@@ -333,8 +338,12 @@ __device__ __forceinline__ void dev_kick(const Pool &P, long long g) {
     if constexpr (sizeof(V) == 4) h = S.half_dtf;
     else h = 0.5 * S.dt;
     const bool frozen = frozen_bead(P, S, i);
+    // held (step limits): the state stays, its kinetic energy is reported
+    const bool held = P.step_stop && P.held[s];
     V v2 = V(0);
-    for (int a = 0; a < 3 && !frozen; ++a) {
+    if (held)
+      for (int a = 0; a < 3 && !frozen; ++a) v2 += v0[a] * v0[a];
+    for (int a = 0; a < 3 && !frozen && !held; ++a) {
       const long long fq =
           ONE ? f1[a] : *reinterpret_cast<const long long *>(force_ptr(P, S, i, a));
       V v = v0[a] + h * force_value<V>(fq);
@@ -344,7 +353,7 @@ __device__ __forceinline__ void dev_kick(const Pool &P, long long g) {
     ke = efix(V(0.5) * v2);
     // the step is complete: advance the system's step counter (read by the
     // kick-drift kernel of the next step)
-    if (i == 0 && P.step_ctr) P.step_ctr[s] += 1;
+    if (i == 0 && P.step_ctr && !held) P.step_ctr[s] += 1;
   }
   sys_acc_add(P, s, act, ACC_KIN, ke);
 }

@@ -3,9 +3,10 @@
 // Requests are trajectory segments (n beads, nsteps of velocity Verlet).
 // A worker thread keeps an active set of systems resident on the device in
 // one pooled batch engine and repeatedly runs chunks of steps over all of
-// them; between chunks it retires finished requests (device -> host copy of
-// their final state) and admits queued ones whose device footprint fits the
-// memory budget and a free slot.  A change of the active set moves to a new
+// them (each member held at its own step count once it has taken its
+// segment, while the others step on); between chunks it retires finished
+// requests (device -> host copy of their final state) and admits queued
+// ones whose device footprint fits the memory budget and a free slot.  A change of the active set moves to a new
 // pooled layout, built and captured on the host while the current chunk
 // runs on the GPU, and carries the state of continuing systems over with
 // device-to-device copies ordered after the chunk, so their trajectories are
@@ -94,7 +95,7 @@ struct gcme_server {
   std::unique_ptr<Engine> eng;
   std::unique_ptr<Engine> eng_keep;  // replaced engine, freed after the stream's work on it
   std::vector<uint64_t> eng_members;
-  std::vector<unsigned long long> ctr_staging;
+  std::vector<unsigned long long> ctr_staging, stop_staging;
   bool forces_valid = false;
   int64_t st_admitted = 0, st_completed = 0, st_rejected = 0, st_chunks = 0, st_beadsteps = 0,
           st_peak_active = 0, st_peak_bytes = 0, st_rebuilds = 0;
@@ -117,6 +118,7 @@ std::unique_ptr<Engine> gcme_server::make_engine(const std::vector<Req *> &membe
   std::unique_ptr<Engine> ne(new Engine);
   *rc = ne->build(device, specs, true);
   if (*rc) return nullptr;
+  ne->enable_step_limits();  // each member stops at its own step count
   cudaGraphExec_t g;
   *rc = ne->forces_graph(ne->P, &g);
   if (!*rc) *rc = ne->step_graph(ne->P, &g);
@@ -153,6 +155,13 @@ void gcme_server::hand_over(Engine &ne, const std::vector<Req *> &members, int64
   }
   cudaMemcpyAsync(ne.P.step_ctr, ctr_staging.data(),
                   sizeof(unsigned long long) * ctr_staging.size(), cudaMemcpyHostToDevice, stream);
+  // each member's step limit: its segment's length in the same count
+  stop_staging.resize(members.size());
+  for (size_t k = 0; k < members.size(); ++k)
+    stop_staging[k] = (unsigned long long)members[k]->nsteps;
+  cudaMemcpyAsync(ne.step_stop_buf, stop_staging.data(),
+                  sizeof(unsigned long long) * stop_staging.size(), cudaMemcpyHostToDevice,
+                  stream);
 }
 
 // Admit queued requests (FIFO) while slots and the memory budget allow,
@@ -213,13 +222,16 @@ void gcme_server::run() {
     st_peak_active = std::max<int64_t>(st_peak_active, (int64_t)active.size());
     const std::vector<uint64_t> members = active;
     std::vector<Req *> mreq;  // pointers stay valid: active requests are not erased
-    int64_t steps = chunk;
+    // a chunk runs until its longest remaining segment ends or for `chunk`
+    // steps; members with fewer steps left are held at their own count
+    int64_t maxrem = 0;
     for (uint64_t t : members) {
       Req *r = reqs[t].get();
       r->done_at_hand_over = r->done;
       mreq.push_back(r);
-      steps = std::min(steps, r->nsteps - r->done);
+      maxrem = std::max(maxrem, r->nsteps - r->done);
     }
+    const int64_t steps = std::min<int64_t>(chunk, maxrem);
     lk.unlock();
     int rc = GCME_OK;
     if (members != eng_members) {  // first chunk, or after a cancellation or an error
@@ -308,8 +320,9 @@ void gcme_server::run() {
         r.t_done = now_s();
         continue;
       }
-      r.done += steps;
-      st_beadsteps += steps * r.spec.n;
+      const int64_t took = std::min(steps, r.nsteps - r.done);  // held after its count
+      r.done += took;
+      st_beadsteps += took * r.spec.n;
       if (fin[k]) {
         std::memcpy(r.energy, &E[(size_t)GCME_NTERMS * k], sizeof(double) * GCME_NTERMS);
         r.status = 0;

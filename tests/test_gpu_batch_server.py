@@ -174,6 +174,43 @@ def test_server_result_same_alone_and_in_mix(gamma):
     srv.close()
 
 
+def test_server_holds_each_member_at_its_own_step_count():
+    """Requests of 7, 23 and 50 steps admitted together run as one chunk of 50
+    steps: each member is held at its own count (forces cleared, state and
+    step counter kept) while the others step on, so the chunk is not cut to
+    the shortest segment, and each result is the same bit for bit as the
+    request run alone (two chunks at most: the worker may start the first
+    chunk before the later requests arrive; cut to the shortest remaining
+    segment it would take three or more).
+    """
+    g = lib()
+    systems = [synth.make_bulk(600 + 200 * k, seed_index=92 + k, charged_frac=0.2,
+                               K=(10, 10, 10)) for k in range(3)]
+    lengths = (7, 23, 50)
+
+    def run(pairs):
+        srv = g.Server(ctx(), 2 << 30, chunk_steps=50)
+        ts = [srv.submit(_params(g, s, gamma=1.0, seed=s.n), s.pos, s.vel.astype(np.float32),
+                         s.q, n, s.bonds) for s, n in pairs]
+        srv.drain(120)
+        out = []
+        for t, (s, n) in zip(ts, pairs):
+            r, p, v = srv.poll(t, want_state=True)
+            assert r.status == 0 and r.steps_done == n
+            out.append((p, v, np.array(r.energy)))
+        st = srv.stats()
+        srv.close()
+        return out, st
+
+    mix, st = run(list(zip(systems, lengths)))
+    assert st["chunks"] <= 2
+    for k, (s, n) in enumerate(zip(systems, lengths)):
+        alone, _ = run([(s, n)])
+        assert np.array_equal(mix[k][0], alone[0][0]), f"request {k} positions differ"
+        assert np.array_equal(mix[k][1], alone[0][1]), f"request {k} velocities differ"
+        assert np.allclose(mix[k][2], alone[0][2], rtol=1e-9, atol=1e-9)
+
+
 def test_server_admission_and_rejection():
     """Host-side fault handling: malformed requests are rejected at submit,
     a request larger than the budget is refused, cancelled tickets never
