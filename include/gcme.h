@@ -509,9 +509,12 @@ int gcme_batch_pointers(gcme_batch *b, double **d_pos, float **d_vel,
 
 /* A continuous-batching request server.  A host thread owns a pool of
  * hbm_budget bytes; requests are admitted when their footprint fits, their
- * state stays on the device, and every chunk of `chunk_steps` steps runs all
- * admitted systems in one batched launch sequence.  Requests that arrive
- * while others run are admitted at the next chunk boundary. */
+ * state stays on the device, and every chunk of `chunk_steps` steps (fewer
+ * when every admitted request ends sooner) runs all admitted systems in one
+ * batched launch sequence; a request with fewer steps left than the chunk
+ * is held at its own count (its state unchanged) while the others step on.
+ * Requests that arrive while others run are admitted at the next chunk
+ * boundary.  Each result is the same bit for bit as the request run alone. */
 typedef struct gcme_request {
   gcme_params params;
   int64_t n;
