@@ -722,8 +722,9 @@ def batched_c4(g, ctx, dev, peaks, nsteps=500):
                                              "per kernel partly L2-resident (129 MB L2)")
             out[key]["hbm_kernels"] = hk
             out[key]["state_bytes_per_step"] = state
-            out[key]["pair_roofline"] = pair_roofline(pairs, qq_pairs, float(ms[2]), "k_pair_f32",
-                                                      peaks)
+            out[key]["pair_roofline"] = pair_roofline(
+                pairs, qq_pairs, float(ms[2]),
+                "k_pair_warp" if tuned.get("pair_nelec") == 0 else "k_pair_f32", peaks)
         b.close()
     return out
 

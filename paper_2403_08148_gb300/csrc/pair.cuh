@@ -252,7 +252,7 @@ __device__ __forceinline__ void pair_core2(const float *__restrict__ X,
   const float2 hx = make_float2(sg.sh[0], sg.sh[0]), hy = make_float2(sg.sh[1], sg.sh[1]),
                hz = make_float2(sg.sh[2], sg.sh[2]);
   const float2 g2 = make_float2(gcc, gcc);
-#pragma unroll 2
+#pragma unroll 4
   for (int t = 0; t < n2; t += 2) {
     float2 dx = __fadd2_rn(*reinterpret_cast<const float2 *>(X + t), mx);
     float2 dy = __fadd2_rn(*reinterpret_cast<const float2 *>(Y + t), my);
@@ -306,7 +306,7 @@ __device__ __forceinline__ void pair_core2_tail(const float *__restrict__ X,
               oz = __fsub_rn(sg.sh[2], xi.z);
   const float2 mx = make_float2(ox, ox), my = make_float2(oy, oy), mz = make_float2(oz, oz);
   const float2 g2 = make_float2(gcc, gcc);
-#pragma unroll 2
+#pragma unroll 4
   for (int t = 0; t < n2; t += 2) {
     const float2 dx = __fadd2_rn(*reinterpret_cast<const float2 *>(X + t), mx);
     const float2 dy = __fadd2_rn(*reinterpret_cast<const float2 *>(Y + t), my);
